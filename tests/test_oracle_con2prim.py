@@ -1,0 +1,164 @@
+"""Pins for the oracle's four conserved->primitive solvers (Sec. 3): round trips against the
+exact prim->cons map, the paper's accuracy study on its (gamma, P) grid (Sec. 3.3), iteration
+counts, the zero-momentum case and invalid input."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import workloads as wl
+from tests import mp_reference as mpr
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "con2prim_accuracy_envelope.json")
+
+
+def spec_for(eos, c2p, max_iter=0, gamma_ad=5.0 / 3.0):
+    return dict(dim=1, degree=0, n_elem=[1], eos=eos, gamma_ad=gamma_ad, c2p=c2p,
+                c2p_max_iter=max_iter)
+
+
+def exact_cons(eos, gamma_ad, W):
+    """Conserved states from Eq. primitive_to_conserved at 40 digits, rounded once."""
+    return np.array([[float(x) for x in mpr.prim2cons(eos, gamma_ad, W[:, k])]
+                     for k in range(W.shape[1])]).T
+
+
+def vel_err(Wr, W):
+    v = np.linalg.norm(W[1:4], axis=0)
+    return np.linalg.norm(Wr[1:4] - W[1:4], axis=0) / np.where(v > 0, v, 1.0)
+
+
+@pytest.fixture(scope="module")
+def moderate_box():
+    """gamma in [1, 10], Theta in [1e-3, 1e3], rho in [1e-3, 1e3]."""
+    W = wl.random_primitive_states(400, seed=11)
+    return W, {"ideal": exact_cons("ideal", 5.0 / 3.0, W), "tm": exact_cons("tm", 5.0 / 3.0, W)}
+
+
+@pytest.mark.parametrize("eos,c2p", [("ideal", "iterative"), ("tm", "analytic"), ("tm", "iterative")])
+def test_round_trip_well_conditioned_solvers(moderate_box, eos, c2p):
+    W, U = moderate_box
+    Wr, it, st = oracle.con2prim(spec_for(eos, c2p), U[eos])
+    assert st["c2p_nonconverged"] == 0 and st["c2p_invalid_input"] == 0
+    assert vel_err(Wr, W).max() < 2e-13
+    assert (np.abs(Wr[0] - W[0]) / W[0]).max() < 5e-13
+    # pressure: conditioning of E - S.v - rho for cold, fast states (P / (tau + |S|) small)
+    kappa = (U[eos][4] + np.linalg.norm(U[eos][1:4], axis=0)) / W[4]
+    assert (np.abs(Wr[4] - W[4]) / W[4] / kappa).max() < 1e-14
+
+
+@pytest.mark.parametrize("eos,c2p", [("ideal", "analytic"), ("ideal", "iterative"),
+                                     ("tm", "analytic"), ("tm", "iterative")])
+def test_backward_error(moderate_box, eos, c2p):
+    """The recovered primitive reproduces the conserved state (exact prim->cons at 40 digits)."""
+    W, U = moderate_box
+    Wr, _, _ = oracle.con2prim(spec_for(eos, c2p), U[eos])
+    # the closed-form quartic route loses digits on hot, fast states (Sec. 3.3 reports its
+    # error growing with gamma); on this machine its backward error stays below 1e-7
+    tol = 1e-7 if c2p == "analytic" and eos == "ideal" else 1e-13
+    Ur = exact_cons(eos, 5.0 / 3.0, Wr)
+    scale = U[eos][0] + U[eos][4] + np.linalg.norm(U[eos][1:4], axis=0)
+    assert (np.abs(Ur - U[eos]).max(axis=0) / scale).max() < tol
+
+
+def test_solvers_agree(moderate_box):
+    W, U = moderate_box
+    a, _, _ = oracle.con2prim(spec_for("ideal", "analytic"), U["ideal"])
+    i, _, _ = oracle.con2prim(spec_for("ideal", "iterative"), U["ideal"])
+    assert vel_err(a, i).max() < 1e-8
+    a, _, _ = oracle.con2prim(spec_for("tm", "analytic"), U["tm"])
+    i, _, _ = oracle.con2prim(spec_for("tm", "iterative"), U["tm"])
+    assert vel_err(a, i).max() < 1e-13
+
+
+@pytest.fixture(scope="module")
+def e2():
+    W, lor, P_si = wl.e2_grid()
+    Wf = W.reshape(5, -1)
+    G = np.tile(lor, 25)
+    return Wf, G, {"ideal": exact_cons("ideal", 5.0 / 3.0, Wf), "tm": exact_cons("tm", 5.0 / 3.0, Wf)}
+
+
+def _v_err(Wr, Wf):
+    v = Wf[1]
+    return np.where(v > 0, np.abs(Wr[1] - v) / np.where(v > 0, v, 1.0), np.abs(Wr[1]))
+
+
+def test_e2_grid_ideal_analytic_envelope(e2):
+    """Sec. 3.3: the analytic ideal solver recovers v to ~1e-15 below gamma = 3, losing
+    accuracy roughly as a power law to ~1e-10 at gamma = 100."""
+    claims = json.load(open(GOLDEN))["claims"]
+    Wf, G, U = e2
+    Wr, _, st = oracle.con2prim(spec_for("ideal", "analytic"), U["ideal"])
+    err = _v_err(Wr, Wf)
+    assert st["c2p_nonconverged"] == 0
+    assert err[G < 3].max() < 100 * claims["ideal_analytic_gamma_below_3_max_rel_err_v"]
+    assert err[G == 100].max() < 10 * claims["ideal_analytic_gamma_100_rel_err_v_order"]
+    assert err[G == 100].max() > 1e-3 * claims["ideal_analytic_gamma_100_rel_err_v_order"]
+
+
+def test_e2_grid_ideal_iterative_iteration_claims(e2):
+    """Sec. 3.3: 6 Newton iterations reach machine precision for gamma < 10; 12 reach it for
+    every gamma <= 100."""
+    Wf, G, U = e2
+    W6, _, _ = oracle.con2prim(spec_for("ideal", "iterative", 6), U["ideal"])
+    W12, it, _ = oracle.con2prim(spec_for("ideal", "iterative", 12), U["ideal"])
+    assert _v_err(W6, Wf)[G < 10].max() < 4e-15
+    assert _v_err(W12, Wf).max() < 4e-15
+    assert it.max() <= 12
+
+
+def test_e2_grid_taub_matthews(e2):
+    """Sec. 3.3: the TM analytic solver is near machine precision everywhere; Brent's method
+    needs tens of iterations (the paper tests 25 and 50)."""
+    Wf, G, U = e2
+    Wa, _, _ = oracle.con2prim(spec_for("tm", "analytic"), U["tm"])
+    Wi, it, st = oracle.con2prim(spec_for("tm", "iterative"), U["tm"])
+    assert _v_err(Wa, Wf).max() < 1e-14
+    assert _v_err(Wi, Wf).max() < 1e-14
+    assert st["c2p_nonconverged"] == 0
+    assert 10 <= it.mean() <= 50 and it.max() <= 60
+
+
+@pytest.mark.parametrize("eos,c2p", [("ideal", "analytic"), ("ideal", "iterative"),
+                                     ("tm", "analytic"), ("tm", "iterative")])
+def test_zero_momentum(eos, c2p):
+    W = np.array([[2.0], [0.0], [0.0], [0.0], [0.3]])
+    U = exact_cons(eos, 5.0 / 3.0, W)
+    Wr, _, st = oracle.con2prim(spec_for(eos, c2p), U)
+    assert np.all(Wr[1:4] == 0.0)
+    assert abs(Wr[0, 0] - 2.0) < 1e-15 and abs(Wr[4, 0] - 0.3) < 1e-14
+    assert st["c2p_nonconverged"] == 0
+
+
+@pytest.mark.parametrize("eos,c2p", [("ideal", "iterative"), ("tm", "iterative")])
+def test_small_momentum_series(eos, c2p):
+    """xi below the series threshold: the small-xi series of Eq. iterative_cubic_approximation
+    (ideal) and Brent (TM) still recover v to machine precision."""
+    W = np.array([[1.0, 1.0], [1e-7, 3e-6], [0.0, 0.0], [0.0, 0.0], [1.0, 1e-6]])
+    U = exact_cons(eos, 5.0 / 3.0, W)
+    Wr, _, _ = oracle.con2prim(spec_for(eos, c2p), U)
+    assert vel_err(Wr, W).max() < 1e-12
+
+
+def test_invalid_input_is_counted():
+    U = np.array([[-1.0, 1.0, 1.0, np.nan, 1.0],
+                  [0.0, 0.0, 2.0, 0.0, 0.0],
+                  [0.0, 0.0, 0.0, 0.0, 0.0],
+                  [0.0, 0.0, 0.0, 0.0, 0.0],
+                  [1.0, -0.5, 0.5, 1.0, 0.1]])
+    for eos in ("ideal", "tm"):
+        for c2p in ("analytic", "iterative"):
+            Wr, _, st = oracle.con2prim(spec_for(eos, c2p), U)
+            assert st["c2p_invalid_input"] == 4
+            assert np.all(np.isnan(Wr[:, :4]))
+            assert np.all(np.isfinite(Wr[:, 4]))
+
+
+def test_iteration_cap_counts_nonconvergence():
+    W = wl.random_primitive_states(50, seed=5, gamma_max=50.0)
+    U = exact_cons("tm", 5.0 / 3.0, W)
+    _, it, st = oracle.con2prim(spec_for("tm", "iterative", 3), U)
+    assert st["c2p_nonconverged"] > 0 and it.max() == 3

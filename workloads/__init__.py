@@ -1,0 +1,292 @@
+"""Seeded synthetic inputs shared by the CUDA path, the oracle, the tests and the benchmark.
+
+This module holds problem descriptions (mesh, equation of state, boundary
+conditions, time integrator) and initial primitive fields as functions of the
+node coordinates.  It holds none of the method's arithmetic: no
+prim->cons map, no con2prim, no flux, no basis.  Each side computes its own
+node coordinates and its own conserved state from the primitive fields given
+here.
+
+A problem description is a plain dict:
+  dim, degree, n_elem, lo, hi, eos ('ideal' | 'tm'), gamma_ad,
+  c2p ('analytic' | 'iterative' | 'default'), c2p_max_iter, flux ('llf' | 'hll'),
+  rk_stages, bc [(lo, hi) per dim: 'periodic' | 'dirichlet' | 'outflow'],
+  bc_state [[(rho, vx, vy, vz, P) low, high] per dim], enforce, cfl.
+
+The workloads follow the problems of the paper:
+  blast_wave      -- 1D relativistic blast wave (Sec. 4.2, problem 1)
+  advected_wave   -- 2D smooth density wave, periodic (smooth convergence case)
+  kh2d            -- 2D relativistic Kelvin-Helmholtz, double shear layer (Sec. 4.4 set-up
+                     recast as periodic with two layers), Taub-Matthews EOS
+  kh3d            -- 3D high-Lorentz-factor Kelvin-Helmholtz, Taub-Matthews EOS
+  e2_grid         -- the 25 x 25 (gamma, P) grid of the con2prim accuracy study (Sec. 3.3)
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+KH3D_SEED = 2205000950
+
+
+# --------------------------------------------------------------------------
+# Problem descriptions
+# --------------------------------------------------------------------------
+
+def blast_wave(n: int = 128, degree: int = 1, p_left: float = 13.33, p_right: float = 1e-6,
+               flux: str = "llf") -> dict:
+    """1D blast wave on [0, 1], interface x = 0.5, Gamma = 5/3, Dirichlet ends, SSPRK2,
+    CFL 0.2, to t = 0.4 (Sec. 4.2 problem 1 with pressures 13.33 and 1e-6)."""
+    left = (10.0, 0.0, 0.0, 0.0, p_left)
+    right = (1.0, 0.0, 0.0, 0.0, p_right)
+    return dict(name="blast_wave_1d", dim=1, degree=degree, n_elem=[n], lo=[0.0], hi=[1.0],
+                eos="ideal", gamma_ad=5.0 / 3.0, c2p="iterative", flux=flux, rk_stages=2,
+                bc=[("dirichlet", "dirichlet")], bc_state=[[left, right]], enforce=True,
+                cfl=0.2, t_final=0.4, left=left, right=right)
+
+
+def advected_wave(n: int = 512, degree: int = 3, flux: str = "llf", c2p: str = "default") -> dict:
+    """2D advected density wave on the periodic unit square, Gamma = 4/3, SSPRK3."""
+    return dict(name="advected_wave_2d", dim=2, degree=degree, n_elem=[n, n], lo=[0.0, 0.0],
+                hi=[1.0, 1.0], eos="ideal", gamma_ad=4.0 / 3.0, c2p=c2p, flux=flux,
+                rk_stages=3, bc=[("periodic", "periodic")] * 2, enforce=True, cfl=0.2)
+
+
+def kh2d(nx: int = 256, ny: int = 512, degree: int = 3, flux: str = "hll",
+         c2p: str = "default") -> dict:
+    """2D relativistic Kelvin-Helmholtz, Taub-Matthews EOS, [-0.5,0.5] x [-1,1], periodic."""
+    return dict(name="kh_2d", dim=2, degree=degree, n_elem=[nx, ny], lo=[-0.5, -1.0],
+                hi=[0.5, 1.0], eos="tm", gamma_ad=4.0 / 3.0, c2p=c2p, flux=flux, rk_stages=3,
+                bc=[("periodic", "periodic")] * 2, enforce=True, cfl=0.2, amplitude=0.01)
+
+
+def kh3d(n: int = 128, degree: int = 3, flux: str = "hll", c2p: str = "default") -> dict:
+    """3D high-Lorentz-factor Kelvin-Helmholtz on the periodic unit cube, Taub-Matthews EOS."""
+    return dict(name="kh_3d", dim=3, degree=degree, n_elem=[n, n, n], lo=[0.0] * 3,
+                hi=[1.0] * 3, eos="tm", gamma_ad=4.0 / 3.0, c2p=c2p, flux=flux, rk_stages=3,
+                bc=[("periodic", "periodic")] * 3, enforce=True, cfl=0.2, seed=KH3D_SEED)
+
+
+def shape(spec: dict):
+    """(total elements, nodes per element)."""
+    dim = int(spec["dim"])
+    return int(np.prod([int(v) for v in spec["n_elem"][:dim]])), (int(spec["degree"]) + 1) ** dim
+
+
+# --------------------------------------------------------------------------
+# Initial primitive fields W = (rho, vx, vy, vz, P) at given coordinates
+# --------------------------------------------------------------------------
+
+def blast_wave_ic(spec: dict, X: np.ndarray) -> np.ndarray:
+    x = X[0]
+    W = np.empty((5,) + x.shape)
+    left, right = spec["left"], spec["right"]
+    for v in range(5):
+        W[v] = np.where(x < 0.5, left[v], right[v])
+    return W
+
+
+def advected_wave_ic(spec: dict, X: np.ndarray, t: float = 0.0) -> np.ndarray:
+    """rho = 1 + 0.5 sin(2 pi (x + y - (vx + vy) t)), v = (0.5, 0.5)/sqrt(2), P = 1."""
+    x, y = X[0], X[1]
+    vx = vy = 0.5 / math.sqrt(2.0)
+    W = np.empty((5,) + x.shape)
+    W[0] = 1.0 + 0.5 * np.sin(2.0 * np.pi * (x + y - (vx + vy) * t))
+    W[1] = vx
+    W[2] = vy
+    W[3] = 0.0
+    W[4] = 1.0
+    return W
+
+
+def _double_layer(y, a=0.01):
+    """+1 inside 0 < y < 1, -1 inside -1 < y < 0 (period 2), tanh layers of width a."""
+    return np.tanh(y / a) - np.tanh((y - 1.0) / a) - np.tanh((y + 1.0) / a)
+
+
+def kh2d_ic(spec: dict, X: np.ndarray, amplitude: float | None = None) -> np.ndarray:
+    """v_x = 0.5 f(y), rho = 0.55 + 0.45 f(y) (1 and 0.1), P = 1,
+    v_y = A sin(2 pi x) exp(-y^2 / 0.01)."""
+    A = spec.get("amplitude", 0.01) if amplitude is None else amplitude
+    x, y = X[0], X[1]
+    f = _double_layer(y)
+    W = np.empty((5,) + x.shape)
+    W[0] = 0.55 + 0.45 * f
+    W[1] = 0.5 * f
+    W[2] = A * np.sin(2.0 * np.pi * x) * np.exp(-y * y / 0.01)
+    W[3] = 0.0
+    W[4] = 1.0
+    return W
+
+
+def _modes(rng, kmax2):
+    ks = [(i, j, k) for i in range(-2, 3) for j in range(-2, 3) for k in range(-2, 3)
+          if 0 < i * i + j * j + k * k <= kmax2]
+    phases = rng.uniform(0.0, 2.0 * np.pi, size=len(ks))
+    return np.array(ks, dtype=np.float64), phases
+
+
+def _mode_sum(ks, phases, x, y, z):
+    s = np.zeros_like(x)
+    for (kx, ky, kz), ph in zip(ks, phases):
+        s += np.sin(2.0 * np.pi * (kx * x + ky * y + kz * z) + ph)
+    return s / len(ks)
+
+
+def kh3d_ic(spec: dict, X: np.ndarray) -> np.ndarray:
+    """Shear v_x = +-0.9 between layers at y = 0.25 and 0.75, a seeded perturbation of
+    amplitude 1e-3 in (v_y, v_z), and a seeded smooth bulk boost in the 4-velocity u_z
+    scaled so that the largest Lorentz factor on a fixed 64^3 sample grid is 10.
+    Built in the 4-velocity u so that every state is subluminal."""
+    rng = np.random.default_rng(spec.get("seed", KH3D_SEED))
+    kp, php = _modes(rng, 4)
+    kq, phq = _modes(rng, 4)
+    kb, phb = _modes(rng, 2)
+
+    def fields(x, y, z, boost):
+        f = np.tanh((y - 0.25) / 0.01) - np.tanh((y - 0.75) / 0.01) - 1.0
+        ux = 0.9 / math.sqrt(1.0 - 0.81) * f
+        uy = 1e-3 * _mode_sum(kp, php, x, y, z)
+        uz = 1e-3 * _mode_sum(kq, phq, x, y, z) + boost * _mode_sum(kb, phb, x, y, z)
+        return f, ux, uy, uz
+
+    g = (np.arange(64) + 0.5) / 64.0
+    gx, gy, gz = np.meshgrid(g, g, g, indexing="ij")
+
+    def max_gamma(boost):
+        _, ux, uy, uz = fields(gx, gy, gz, boost)
+        return float(np.sqrt(1.0 + ux * ux + uy * uy + uz * uz).max())
+
+    lo, hi = 0.0, 100.0
+    for _ in range(200):
+        mid = 0.5 * (lo + hi)
+        if max_gamma(mid) < 10.0:
+            lo = mid
+        else:
+            hi = mid
+    boost = 0.5 * (lo + hi)
+    f, ux, uy, uz = fields(X[0], X[1], X[2], boost)
+    lor = np.sqrt(1.0 + ux * ux + uy * uy + uz * uz)
+    W = np.empty((5,) + X[0].shape)
+    W[0] = 0.55 + 0.45 * f
+    W[1] = ux / lor
+    W[2] = uy / lor
+    W[3] = uz / lor
+    W[4] = 1.0
+    return W
+
+
+def initial_primitive(spec: dict, X: np.ndarray) -> np.ndarray:
+    name = spec["name"]
+    if name == "blast_wave_1d":
+        return blast_wave_ic(spec, X)
+    if name == "advected_wave_2d":
+        return advected_wave_ic(spec, X)
+    if name == "kh_2d":
+        return kh2d_ic(spec, X)
+    if name == "kh_3d":
+        return kh3d_ic(spec, X)
+    if name == "smooth_random":
+        return smooth_random_ic(spec, X)
+    raise KeyError(name)
+
+
+# --------------------------------------------------------------------------
+# Seeded random inputs for parity tests
+# --------------------------------------------------------------------------
+
+def smooth_random(dim: int, n_elem, degree: int, eos: str = "ideal", seed: int = 0,
+                  flux: str = "llf", c2p: str = "default", vmax: float = 0.6,
+                  bc=None, rk_stages: int = 3) -> dict:
+    """A periodic box with a seeded smooth random primitive field (a few Fourier modes):
+    rho in about [0.3, 1.7], |v| up to vmax, P in about [0.2, 1.8]."""
+    bc = bc or [("periodic", "periodic")] * dim
+    return dict(name="smooth_random", dim=dim, degree=degree, n_elem=list(n_elem),
+                lo=[0.0] * dim, hi=[1.0] * dim, eos=eos, gamma_ad=5.0 / 3.0 if eos == "ideal" else 4.0 / 3.0,
+                c2p=c2p, flux=flux, rk_stages=rk_stages, bc=bc, enforce=True, cfl=0.2, seed=seed,
+                vmax=vmax, bc_state=[[(1.0, 0.1, 0.0, 0.0, 1.0), (0.5, -0.1, 0.0, 0.0, 0.5)]] * dim)
+
+
+def smooth_random_ic(spec: dict, X: np.ndarray) -> np.ndarray:
+    rng = np.random.default_rng(spec.get("seed", 0))
+    dim = X.shape[0]
+    coords = [X[d] for d in range(dim)]
+    out = np.empty((5,) + X[0].shape)
+
+    def field():
+        s = np.zeros_like(coords[0])
+        for _ in range(3):
+            k = rng.integers(-2, 3, size=dim)
+            if not np.any(k):
+                k[0] = 1
+            ph = rng.uniform(0, 2 * np.pi)
+            amp = rng.uniform(0.3, 1.0)
+            s += amp * np.sin(2 * np.pi * sum(k[d] * coords[d] for d in range(dim)) + ph)
+        return s / 3.0
+
+    out[0] = 1.0 + 0.7 * field()
+    vx, vy, vz = field(), field(), field()
+    vmag = np.sqrt(vx * vx + vy * vy + vz * vz)
+    scale = spec.get("vmax", 0.6) / max(float(vmag.max()), 1e-30)
+    out[1], out[2], out[3] = vx * scale, vy * scale, vz * scale
+    out[4] = 1.0 + 0.8 * field()
+    return out
+
+
+def random_primitive_states(n: int, seed: int = 0, gamma_max: float = 10.0,
+                            theta_range=(1e-3, 1e3), rho_range=(1e-3, 1e3)) -> np.ndarray:
+    """n seeded primitive states (rho, vx, vy, vz, P): log-uniform rho, Theta = P/rho and
+    gamma in [1, gamma_max], isotropic velocity direction."""
+    rng = np.random.default_rng(seed)
+    rho = 10.0 ** rng.uniform(np.log10(rho_range[0]), np.log10(rho_range[1]), n)
+    th = 10.0 ** rng.uniform(np.log10(theta_range[0]), np.log10(theta_range[1]), n)
+    lor = 10.0 ** rng.uniform(0.0, np.log10(gamma_max), n)
+    beta = np.sqrt(1.0 - 1.0 / (lor * lor))
+    d = rng.normal(size=(3, n))
+    d /= np.linalg.norm(d, axis=0)
+    W = np.empty((5, n))
+    W[0] = rho
+    W[1:4] = beta * d
+    W[4] = rho * th
+    return W
+
+
+def e2_grid():
+    """The (gamma, P) grid of the con2prim accuracy study: 25 log-spaced Lorentz factors
+    in [1, 100] and 25 log-spaced pressures in [1e5, 1e10] N/m^2 with D = 1 kg/m^3 and
+    c = 3e8 m/s (Sec. 3.3), in units c = 1: P -> P/c^2, rho = D/gamma, v along x.
+    Returns (W (5, 25, 25), gamma (25,), P_si (25,)) indexed [pressure, gamma]."""
+    c = 3e8
+    lor = np.logspace(0.0, 2.0, 25)
+    P_si = np.logspace(5.0, 10.0, 25)
+    G, P = np.meshgrid(lor, P_si / (c * c))
+    W = np.zeros((5, 25, 25))
+    W[0] = 1.0 / G
+    W[1] = np.sqrt(1.0 - 1.0 / (G * G))
+    W[4] = P
+    return W, lor, P_si
+
+
+def random_conserved_cells(n_cells: int, nodes: int, seed: int = 0, bad_fraction: float = 0.3,
+                           bad_mean_fraction: float = 0.05):
+    """Seeded conserved nodal states U (5, n_cells, nodes) built directly in (D, S, tau):
+    each cell is a random mean plus nodal deviations large enough that roughly
+    `bad_fraction` of the cells hold nodes outside the admissible set; about
+    `bad_mean_fraction` of the cells are centred outside it.  Used to exercise the
+    physicality operator."""
+    rng = np.random.default_rng(seed)
+    U = np.empty((5, n_cells, nodes))
+    D0 = rng.uniform(0.5, 2.0, (n_cells, 1))
+    S0 = rng.normal(0.0, 0.5, (3, n_cells, 1)) * D0
+    margin0 = rng.uniform(0.2, 1.0, (n_cells, 1)) * D0
+    centred_out = rng.uniform(size=(n_cells, 1)) < bad_mean_fraction
+    margin0 = np.where(centred_out, -rng.uniform(0.05, 0.3, (n_cells, 1)) * D0, margin0)
+    bad = rng.uniform(size=(n_cells, 1)) < bad_fraction
+    amp = np.where(bad, 1.5, 0.05)
+    U[0] = D0 + amp * rng.normal(0.0, 0.6, (n_cells, nodes)) * D0
+    U[1:4] = S0 + amp * rng.normal(0.0, 0.6, (3, n_cells, nodes)) * D0
+    # tau so that E = tau + D sits near sqrt(D^2 + S^2) + margin
+    Smag = np.sqrt(U[1] ** 2 + U[2] ** 2 + U[3] ** 2)
+    U[4] = np.sqrt(U[0] ** 2 + Smag ** 2) - U[0] + margin0 + amp * rng.normal(0.0, 0.8, (n_cells, nodes)) * D0
+    return U
