@@ -1,0 +1,350 @@
+"""Benchmark: DOF-updates/s of SSP-RK steps of the nodal DG SRHD solver on one GB300.
+
+Default workload: the 2D advected density wave, 512 x 512 elements, p = 3 (16 Gauss-Legendre
+nodes per element, 4,194,304 DOF), ideal EOS Gamma = 4/3, closed-form con2prim, LLF, SSPRK3,
+FP64.  A DOF update is one node updated by one RK stage; DOF-updates/s = DOF x steps x stages /
+seconds (the definition of the paper's performance section).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--workload advected_wave|kh2d|kh3d]
+
+--gpus N > 1 runs one replica of the workload per rank (torchrun, one GPU each; the method has no
+cross-replica exchange), barrier + synchronize around the timed region, max time over ranks.
+--impl reference times the FP64 CPU oracle on the host cores on a bounded sample of the same
+workload.  One JSON line is printed by rank 0.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads as wl  # noqa: E402
+
+METRIC = "DOF-updates/s at p=3 (FP64 vs split-precision, fixed L1 error); adjoint/forward ratio"
+UNIT = "DOF-updates/s"
+FP64_PEAK_TFLOPS = 1.25  # GB300 nominal dense FP64 (no FP64 figure in MEASURED_PEAKS.json)
+
+
+def make_spec(name: str) -> dict:
+    if name == "advected_wave":
+        return wl.advected_wave(n=512, degree=3, c2p="analytic")
+    if name == "kh2d":
+        return wl.kh2d(nx=256, ny=512, degree=3)
+    if name == "kh3d":
+        return wl.kh3d(n=128, degree=3)
+    raise SystemExit(f"unknown workload {name}")
+
+
+def workload_desc(spec: dict) -> str:
+    n = "x".join(str(v) for v in spec["n_elem"][: spec["dim"]])
+    return (f"{spec['name']} {n} elements p={spec['degree']} {spec['eos']} EOS "
+            f"c2p={spec['c2p']} flux={spec['flux']} SSPRK{spec['rk_stages']} FP64")
+
+
+def dof(spec: dict) -> int:
+    E, Nn = wl.shape(spec)
+    return E * Nn
+
+
+# ----------------------------------------------------------------------------------------
+# clocks during the timed region
+# ----------------------------------------------------------------------------------------
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{gpu_index}.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.QUERY}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=self.fh, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.fh.close()
+
+    def summary(self):
+        if self.proc is None or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm, smmax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smmax.append(float(f[2]))
+            except ValueError:
+                continue
+            for name, val in zip(names, f[5:9]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smmax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------------------
+# algorithmic work (per DOF update, p = 3, 2D) used for the roofline of the volume kernel
+# ----------------------------------------------------------------------------------------
+def volume_kernel_flops_per_node(spec: dict) -> float:
+    """FP64 operations of the volume kernel per node (add/mul = 1, fma = 2, div/sqrt and each
+    transcendental call = 1), counted from the method's arithmetic:
+      con2prim (closed-form ideal quartic): xi, eta, the quartic coefficients, the resolvent,
+      Cardano's root, the two square-root factorisations and the recovery of rho, v, P;
+      nodal flux 5 products + 2 sums per direction; volume term 2 N flops per variable and
+      direction; face traces 2 N flops per variable per face point (2 dim N^(dim-1) points per
+      N^dim nodes)."""
+    d, N = spec["dim"], spec["degree"] + 1
+    c2p = {"analytic": 95.0, "iterative": 60.0 + 6 * 18.0}[spec["c2p"] if spec["c2p"] != "default" else "analytic"]
+    flux = 7.0 * d
+    volume = 2.0 * N * 5 * d + 5 * d
+    traces = (2 * d * N ** (d - 1) / N ** d) * 5 * 2.0 * N
+    return c2p + flux + volume + traces
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        return json.load(open(path))
+    except (OSError, ValueError):
+        return None
+
+
+# ----------------------------------------------------------------------------------------
+# reference arm / CPU baseline: the oracle on a bounded sample
+# ----------------------------------------------------------------------------------------
+def oracle_sample_spec(spec: dict, target_s: float = 1.0):
+    """A sample of the workload (same field, p, EOS, solver) small enough for one oracle step to
+    take about target_s seconds on one core."""
+    import oracle
+    s = dict(spec)
+    d = spec["dim"]
+    n = 8 if d == 3 else 32
+    s["n_elem"] = [n] * d if spec["name"] != "kh_2d" else [n, 2 * n]
+    X = oracle.node_coords(s)
+    U = oracle.prim2cons(s, wl.initial_primitive(s, X))
+    t0 = time.perf_counter()
+    oracle.step(s, U, oracle.cfl_dt(s, 0.2), 1)
+    t = time.perf_counter() - t0
+    scale = max(1.0, (target_s / max(t, 1e-6)) ** (1.0 / d))
+    s["n_elem"] = [max(2, int(v * scale)) for v in s["n_elem"]]
+    return s
+
+
+def run_oracle(spec: dict, steps: int, warmup: int):
+    import oracle
+    X = oracle.node_coords(spec)
+    U = oracle.prim2cons(spec, wl.initial_primitive(spec, X))
+    dt = oracle.cfl_dt(spec, 0.2)
+    for _ in range(warmup):
+        U, _ = oracle.step(spec, U, dt, 1)
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        U, _ = oracle.step(spec, U, dt, 1)
+    t = time.perf_counter() - t0
+    return dof(spec) * steps * spec["rk_stages"] / t, t
+
+
+def reference_arm(args, rank, world):
+    if rank != 0:
+        return
+    spec = make_spec(args.workload)
+    sample = oracle_sample_spec(spec, target_s=min(20.0, 60.0 / max(1, args.steps + args.warmup)))
+    value, t = run_oracle(sample, args.steps, args.warmup)
+    desc = (f"{args.steps} oracle SSPRK steps on {'x'.join(map(str, sample['n_elem']))} elements of the "
+            f"same workload ({dof(sample)} DOF), 1 thread")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": workload_desc(spec), "sample": desc},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------------------------------
+# our arm
+# ----------------------------------------------------------------------------------------
+def ours(args, rank, world, local_rank):
+    import torch
+    import torch.distributed as dist
+    from paper_2205_00095_gb300 import Solver, build
+
+    build.build()
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    spec = make_spec(args.workload)
+    stream = torch.cuda.Stream(device=dev)
+    s = Solver(spec, stream=stream, device=dev)
+    X = s.node_coords()
+    with torch.cuda.stream(stream):
+        U0 = s.initial_state(wl.initial_primitive(spec, X))
+        s.enforce(U0)
+        U = U0.clone()
+    dt = s.cfl_dt(0.2)
+    stages = spec["rk_stages"]
+    ndof = dof(spec)
+
+    # warm-up (also captures the step graph)
+    s.step(U, dt, max(1, args.warmup))
+    torch.cuda.synchronize(dev)
+    s.stats(reset=True)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+
+    # timed region: K steps with every kernel bracketed by CUDA events on the solver's stream
+    s.set_profiling(True)
+    s.kernel_times(reset=True)
+    launches0 = s.kernel_launches()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    barrier()
+    with ClockSampler(local_rank) as clk:
+        ev0.record(stream)
+        s.step(U, dt, args.steps)
+        ev1.record(stream)
+        torch.cuda.synchronize(dev)
+    barrier()
+    ms = ev0.elapsed_time(ev1)
+    launches = s.kernel_launches() - launches0
+    ktimes = s.kernel_times(reset=True)
+    s.set_profiling(False)
+    status, st = s.stats()
+    t_max = ms
+    if world > 1:
+        tt = torch.tensor([ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_max = float(tt.item())
+    value = world * ndof * args.steps * stages / (t_max * 1e-3)
+
+    # end to end through the C ABI with a pinned host state: H2D, K steps (graph), D2H
+    Uh = U0.cpu().pin_memory()
+    nbytes = Uh.numel() * 8
+    s.step_host(Uh, dt, 1)  # warm
+    Uh.copy_(U0.cpu())
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        s.step_host(Uh, dt, 1)
+    barrier()
+    e2e_s = time.perf_counter() - t0
+    e2e_t = torch.tensor([e2e_s], device=dev, dtype=torch.float64)
+    if world > 1:
+        dist.all_reduce(e2e_t, op=dist.ReduceOp.MAX)
+    e2e_value = world * ndof * args.steps * stages / float(e2e_t.item())
+
+    # oracle on the host cores (rank 0, N = 1 only)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        sample = oracle_sample_spec(spec, target_s=5.0)
+        cv, ct = run_oracle(sample, 2, 0)
+        cpu = {"value": cv, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"2 oracle SSPRK3 steps on {'x'.join(map(str, sample['n_elem']))} elements of the "
+                         f"same workload ({dof(sample)} DOF, {ct:.1f} s), 1 thread"}
+
+    # roofline of the dominant kernel (largest share of the timed region)
+    dom = max(ktimes, key=lambda k: ktimes[k][0])
+    dom_ms, dom_n = ktimes[dom]
+    avg_s = dom_ms / max(dom_n, 1) * 1e-3
+    roofline = None
+    if dom == "volume":
+        flops = volume_kernel_flops_per_node(spec) * ndof
+        achieved = flops / avg_s / 1e12
+        roofline = {"kernel": "volume_kernel", "bound": "alu", "achieved": achieved,
+                    "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
+                    "traffic": None, "peak_source": "GB300 nominal dense FP64 1.25 TFLOP/s",
+                    "algorithmic_flops_per_node": volume_kernel_flops_per_node(spec),
+                    "avg_launch_ms": avg_s * 1e3}
+    else:
+        roofline = {"kernel": dom, "bound": "alu", "achieved": None, "peak": FP64_PEAK_TFLOPS,
+                    "unit": "TFLOP/s", "frac": None, "traffic": None, "avg_launch_ms": avg_s * 1e3}
+    shares = {k: round(v[0] / max(sum(x[0] for x in ktimes.values()), 1e-12), 4)
+              for k, v in ktimes.items() if v[1]}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": workload_desc(spec), "dof": ndof, "stages_per_step": stages,
+                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                       "l2": "inputs larger than L2 (state 168 MB + scratch)",
+                       "precision": "fp64"},
+            "roofline": roofline, "kernel_shares": shares,
+            "cpu_baseline": cpu,
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": nbytes,
+                    "d2h_bytes_per_step": nbytes},
+            "gpu_launches": launches,
+            "clocks": clk.summary(),
+            "device_status": status,
+            "stats": st,
+        }
+        print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="advected_wave", choices=["advected_wave", "kh2d", "kh3d"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        reference_arm(args, rank, world)
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    try:
+        ours(args, rank, world, local_rank)
+    finally:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

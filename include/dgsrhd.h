@@ -1,0 +1,187 @@
+/*
+ * dgsrhd: discontinuous-Galerkin special-relativistic hydrodynamics on one GPU (sm_103a).
+ *
+ * C ABI of the hot path of arXiv 2205.00095 (Glines et al., "A Robust, Performance-Portable
+ * Discontinuous Galerkin Method for Relativistic Hydrodynamics"): conserved-to-primitive
+ * recovery at the nodes, the nodal DG right-hand side with LLF/HLL face fluxes, the
+ * physicality-enforcing operator, SSP Runge-Kutta steps, and the vector-Jacobian product of
+ * the right-hand side.  Units c = 1.
+ *
+ * Data layout (every state array):
+ *   contiguous FP64, structure of arrays [var][elem][node];
+ *   elem = ex + nx * (ey + ny * ez)              (x fastest)
+ *   node = a + N * (b + N * c), N = degree + 1   (tensor Gauss-Legendre nodes, x fastest)
+ *   conserved U: var = (D, S_x, S_y, S_z, tau), tau = E - D   (Eq. primitive_to_conserved)
+ *   primitive W: var = (rho, v_x, v_y, v_z, P)                 (Sec. 2.1)
+ * Five variables are carried in every dimension.
+ *
+ * Memory: arrays passed to the calls are caller-owned DEVICE pointers (except where a
+ * name ends in _host).  The library owns only the scratch buffers it allocates in
+ * dgsrhd_create and frees in dgsrhd_destroy; no other call allocates.
+ *
+ * Streams and errors: every call is ordered on the context's stream and returns before the
+ * GPU work ends.  Argument errors return DGSRHD_EINVAL synchronously; launch failures return
+ * DGSRHD_ECUDA.  Problems found on the device (non-converged or invalid con2prim,
+ * inadmissible element means) are counted in device counters and reported by
+ * dgsrhd_get_stats, which synchronises the stream.  No kernel traps.
+ */
+#ifndef DGSRHD_H
+#define DGSRHD_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define DGSRHD_OK 0
+#define DGSRHD_EINVAL 1          /* bad argument or configuration */
+#define DGSRHD_ECUDA 2           /* a CUDA call failed */
+#define DGSRHD_ENOMEM 3          /* scratch allocation failed in dgsrhd_create */
+#define DGSRHD_EC2P_NOCONV 4     /* get_stats: some con2prim did not converge */
+#define DGSRHD_EUNPHYS_MEAN 5    /* get_stats: some element mean was inadmissible */
+#define DGSRHD_EBADSTATE 6       /* get_stats: some node held an invalid conserved state */
+
+/* equation of state (Sec. 2.2) */
+#define DGSRHD_EOS_IDEAL 0
+#define DGSRHD_EOS_TAUB_MATTHEWS 1
+
+/* conserved-to-primitive solver (Sec. 3) */
+#define DGSRHD_C2P_ANALYTIC 0    /* ideal: quartic closed form; TM: cubic closed form */
+#define DGSRHD_C2P_ITERATIVE 1   /* ideal: Newton on the Riccardi quartic; TM: Brent */
+#define DGSRHD_C2P_DEFAULT 2     /* ideal -> analytic, Taub-Matthews -> iterative */
+
+/* numerical flux (Sec. 2.4) */
+#define DGSRHD_FLUX_LLF 0
+#define DGSRHD_FLUX_HLL 1
+
+/* boundary condition per side */
+#define DGSRHD_BC_PERIODIC 0     /* both sides of an axis must be periodic together */
+#define DGSRHD_BC_DIRICHLET 1    /* ghost state = bc_state (rho, vx, vy, vz, P) */
+#define DGSRHD_BC_OUTFLOW 2      /* ghost state = the interior face trace */
+
+/* arithmetic of the basis contractions */
+#define DGSRHD_PREC_FP64 0
+#define DGSRHD_PREC_SPLIT 1      /* split-precision tensor-core contractions, FP64 elsewhere */
+
+typedef struct dgsrhd_config {
+  int32_t dim;                 /* 1, 2 or 3 */
+  int32_t degree;              /* p in 0..4; N = p + 1 Gauss-Legendre nodes per axis */
+  int64_t n_elem[3];           /* elements per axis (unused axes: 1) */
+  double lo[3], hi[3];         /* domain box */
+  int32_t eos;                 /* DGSRHD_EOS_* */
+  double gamma_ad;             /* adiabatic index of the ideal EOS (ignored for TM) */
+  int32_t c2p;                 /* DGSRHD_C2P_* */
+  int32_t c2p_max_iter;        /* <= 0: 30 Newton / 100 Brent iterations */
+  int32_t flux;                /* DGSRHD_FLUX_* */
+  int32_t rk_stages;           /* 1 (forward Euler), 2 (SSPRK2), 3 (SSPRK3) */
+  int32_t bc[3][2];            /* DGSRHD_BC_* for the low and high side of each axis */
+  double bc_state[3][2][5];    /* Dirichlet primitive (rho, vx, vy, vz, P) per side */
+  int32_t enforce;             /* 1: physicality operator after every RK stage */
+  int32_t precision;           /* DGSRHD_PREC_* */
+} dgsrhd_config;
+
+typedef struct dgsrhd_stats {
+  int64_t c2p_calls;               /* node recoveries since the last reset */
+  int64_t c2p_iters_total;         /* iterations of the iterative solvers */
+  int64_t c2p_iters_max;
+  int64_t c2p_nonconverged;        /* iteration cap hit / closed form broke down */
+  int64_t c2p_invalid_input;       /* D <= 0, q <= 0 or non-finite conserved state */
+  int64_t face_guard_hits;         /* face traces with rho <= 0 or P <= 0 replaced */
+  int64_t enforced_cells;          /* elements smoothed by the physicality operator */
+  int64_t mean_inadmissible_cells; /* flagged elements whose mean was inadmissible */
+} dgsrhd_stats;
+
+typedef struct dgsrhd_ctx dgsrhd_ctx;
+
+/* Create a solver for one mesh and method choice on the current CUDA device.  `stream` is a
+ * cudaStream_t (NULL: the legacy default stream).  Allocates all scratch (about 8x the state
+ * size).  Returns DGSRHD_EINVAL for an invalid configuration, DGSRHD_ENOMEM if scratch cannot
+ * be allocated. */
+int32_t dgsrhd_create(const dgsrhd_config* cfg, void* stream, dgsrhd_ctx** out);
+
+/* Free the scratch and the context (synchronises its stream). NULL is ignored. */
+void dgsrhd_destroy(dgsrhd_ctx* ctx);
+
+/* Change the stream later calls are ordered on. */
+int32_t dgsrhd_set_stream(dgsrhd_ctx* ctx, void* stream);
+
+/* Shape of a state array: nvar = 5, n_elem = elements, n_node = (degree + 1)^dim. */
+int32_t dgsrhd_state_shape(const dgsrhd_ctx* ctx, int64_t* nvar, int64_t* n_elem,
+                           int64_t* n_node);
+
+/* Node coordinates into a HOST array X_host[dim][n_elem][n_node]. */
+int32_t dgsrhd_node_coords(const dgsrhd_ctx* ctx, double* X_host);
+
+/* prim -> cons at every node (Eq. primitive_to_conserved): W (rho, v, P) -> U. */
+int32_t dgsrhd_prim2cons(dgsrhd_ctx* ctx, const double* W, double* U);
+
+/* cons -> prim at every node (Sec. 3, the configured solver): U -> W (rho, v, P).
+ * iters (nullable, int32 per node) receives the iteration count of the iterative solvers.
+ * Invalid states give NaN and are counted. */
+int32_t dgsrhd_con2prim(dgsrhd_ctx* ctx, const double* U, double* W, int32_t* iters);
+
+/* R = dU/dt of the nodal DG semi-discretisation (Eq. discrete_hyperbolic_conservation_law
+ * with node-collocated quadrature, Eqs. quad-vol-flux and quad-surface-flux): primitives
+ * recovered at the nodes, (rho, u, P) extrapolated to the faces, LLF/HLL face flux (Sec.
+ * 2.4) lifted into the element.  No physicality operator.  U and R must not alias. */
+int32_t dgsrhd_rhs(dgsrhd_ctx* ctx, const double* U, double* R);
+
+/* Physicality-enforcing operator on every element, in place (Sec. 2.5, Eq. smoothed_states).
+ * s_out (nullable, [n_elem]) receives each element's smoothing factor (1 = untouched). */
+int32_t dgsrhd_enforce(dgsrhd_ctx* ctx, double* U, double* s_out);
+
+/* nsteps SSP-RK steps of size dt in place, the operator after every stage when enabled
+ * (Sec. 2.3, Shu-Osher form).  The first call with a given dt captures the step into a CUDA
+ * graph; later calls replay it. */
+int32_t dgsrhd_step(dgsrhd_ctx* ctx, double* U, double dt, int32_t nsteps);
+
+/* The same with a HOST state: copies U_host to the device, steps, copies back, and
+ * synchronises the stream.  For pinned host memory the copies are asynchronous DMA. */
+int32_t dgsrhd_step_host(dgsrhd_ctx* ctx, double* U_host, double dt, int32_t nsteps);
+
+/* U_bar = (dR/dU)^T R_bar for R = dgsrhd_rhs(U) (vector-Jacobian product).  Non-smooth
+ * choices (HLL/LLF speed selection, face guard) are frozen at their forward branch. */
+int32_t dgsrhd_rhs_vjp(dgsrhd_ctx* ctx, const double* U, const double* R_bar, double* U_bar);
+
+/* VJP of the physicality operator with each element's factor s frozen at its forward value
+ * (s from dgsrhd_enforce): U_bar_i = s Ut_bar_i + (1 - s) w_i / sum(w) sum_j Ut_bar_j. */
+int32_t dgsrhd_enforce_vjp(dgsrhd_ctx* ctx, const double* s, const double* Ut_bar,
+                           double* U_bar);
+
+/* Time step of the CFL rule dt = cfl / ((2p + 1) sum_d 1/dx_d) (all speeds <= c = 1). */
+int32_t dgsrhd_cfl_dt(const dgsrhd_ctx* ctx, double cfl, double* dt);
+
+/* Read (and if reset != 0, zero) the device counters; synchronises the stream.  Returns
+ * DGSRHD_EBADSTATE, DGSRHD_EC2P_NOCONV or DGSRHD_EUNPHYS_MEAN (in that order of priority)
+ * when the counters show such events, DGSRHD_OK otherwise. */
+int32_t dgsrhd_get_stats(dgsrhd_ctx* ctx, dgsrhd_stats* out, int32_t reset);
+
+/* Number of kernels the library launched through this context (graph replays count every
+ * kernel node). */
+int64_t dgsrhd_kernel_launches(const dgsrhd_ctx* ctx);
+
+/* Kernel timing.  While enabled, every kernel launch is bracketed by a pair of CUDA events on
+ * the context's stream and dgsrhd_step launches its kernels directly instead of replaying a
+ * graph.  dgsrhd_kernel_times synchronises the stream and returns, per kernel kind
+ * (DGSRHD_KERNEL_*), the summed duration in milliseconds and the launch count since the last
+ * reset.  ms and counts are HOST arrays of DGSRHD_KERNEL_KINDS entries. */
+#define DGSRHD_KERNEL_VOLUME 0    /* con2prim + nodal flux + volume term + face traces */
+#define DGSRHD_KERNEL_FACE 1      /* numerical flux at every face point */
+#define DGSRHD_KERNEL_UPDATE 2    /* lift + RK stage + physicality operator */
+#define DGSRHD_KERNEL_ENFORCE 3   /* stand-alone physicality operator */
+#define DGSRHD_KERNEL_POINTWISE 4 /* prim2cons / con2prim */
+#define DGSRHD_KERNEL_VJP 5       /* the kernels of dgsrhd_rhs_vjp / dgsrhd_enforce_vjp */
+#define DGSRHD_KERNEL_KINDS 6
+int32_t dgsrhd_set_profiling(dgsrhd_ctx* ctx, int32_t enable);
+int32_t dgsrhd_kernel_times(dgsrhd_ctx* ctx, double* ms, int64_t* counts, int32_t reset);
+
+/* Human-readable name of a status code. */
+const char* dgsrhd_status_string(int32_t status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DGSRHD_H */

@@ -1,0 +1,595 @@
+// Host side of the C ABI declared in include/dgsrhd.h: configuration checks, the Gauss-Legendre
+// basis tables, scratch ownership, launch sequencing of one SSP-RK step and its CUDA graph.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <new>
+#include <vector>
+
+#include "../../include/dgsrhd.h"
+#include "launch.h"
+#include "params.h"
+
+using dgsrhd::Op;
+using dgsrhd::Params;
+using dgsrhd::StageArgs;
+
+struct dgsrhd_ctx {
+  dgsrhd_config cfg;
+  Params p;
+  cudaStream_t stream;
+  int dim, N;
+  long long E, Nn, nstate;  // nstate = 5 E Nn doubles
+  double x[dgsrhd::kMaxN];  // Gauss-Legendre nodes
+  double dx[3];
+  // scratch
+  double* A;    // RK stage state
+  double* Rv;   // volume term / R
+  double* Tr;   // face traces
+  double* Fs;   // face fluxes
+  double* Ud;   // device state for dgsrhd_step_host
+  double* Wv;   // VJP: nodal primitives
+  double* TrB;  // VJP: trace adjoints
+  unsigned long long* stats;
+  long long c2p_calls;
+  long long launches;
+  // captured step
+  cudaGraphExec_t gexec;
+  double g_dt;
+  double* g_U;
+  // kernel timing
+  bool profiling;
+  struct TimedLaunch {
+    int kind;
+    cudaEvent_t start, stop;
+  };
+  std::vector<TimedLaunch> timed;
+  std::vector<cudaEvent_t> event_pool;
+};
+
+namespace {
+
+// ---- Gauss-Legendre nodes by Newton iteration on P_N, barycentric Lagrange tables ----------
+void legendre_pair(int n, double x, double* p, double* dp) {
+  double a = 1.0, b = x;
+  if (n == 0) {
+    *p = 1.0;
+    *dp = 0.0;
+    return;
+  }
+  for (int k = 1; k < n; ++k) {
+    const double c = ((2 * k + 1) * x * b - k * a) / (k + 1);
+    a = b;
+    b = c;
+  }
+  *p = b;
+  *dp = n * (a - x * b) / (1.0 - x * x);
+}
+
+void gauss_legendre(int N, double* x, double* w) {
+  for (int i = 0; i < N; ++i) {
+    // i-th root from the top, then stored ascending
+    double t = cos(M_PI * (i + 0.75) / (N + 0.5));
+    if (N == 1) t = 0.0;
+    for (int k = 0; k < 60 && N > 1; ++k) {
+      double p, dp;
+      legendre_pair(N, t, &p, &dp);
+      const double step = p / dp;
+      t -= step;
+      if (fabs(step) <= 1e-17) break;
+    }
+    double p, dp;
+    legendre_pair(N, t, &p, &dp);
+    x[N - 1 - i] = t;
+    w[N - 1 - i] = (N == 1) ? 2.0 : 2.0 / ((1.0 - t * t) * dp * dp);
+  }
+}
+
+// Tables of the collocated scheme: Dhat[i][a] = w_a phi_i'(x_a)/w_i, e-+_i = phi_i(-+1).
+void basis_tables(int N, const double* x, const double* w, double* Dhat, double* em, double* ep) {
+  double lam[dgsrhd::kMaxN];
+  for (int j = 0; j < N; ++j) {
+    double prod = 1.0;
+    for (int k = 0; k < N; ++k)
+      if (k != j) prod *= (x[j] - x[k]);
+    lam[j] = 1.0 / prod;
+  }
+  // Dm[a][j] = phi_j'(x_a)
+  double Dm[dgsrhd::kMaxN][dgsrhd::kMaxN];
+  for (int a = 0; a < N; ++a) {
+    double diag = 0.0;
+    for (int j = 0; j < N; ++j) {
+      if (j == a) continue;
+      Dm[a][j] = (lam[j] / lam[a]) / (x[a] - x[j]);
+      diag -= Dm[a][j];
+    }
+    Dm[a][a] = diag;
+  }
+  for (int i = 0; i < N; ++i)
+    for (int a = 0; a < N; ++a) Dhat[i * N + a] = (N == 1) ? 0.0 : w[a] * Dm[a][i] / w[i];
+  for (int s = 0; s < 2; ++s) {
+    const double xe = s ? 1.0 : -1.0;
+    double den = 0.0;
+    for (int j = 0; j < N; ++j) den += lam[j] / (xe - x[j]);
+    for (int i = 0; i < N; ++i) (s ? ep : em)[i] = (lam[i] / (xe - x[i])) / den;
+  }
+}
+
+int32_t cuda_status(cudaError_t e) { return e == cudaSuccess ? DGSRHD_OK : DGSRHD_ECUDA; }
+
+int kernel_kind(Op op) {
+  switch (op) {
+    case Op::Volume: return DGSRHD_KERNEL_VOLUME;
+    case Op::Face: return DGSRHD_KERNEL_FACE;
+    case Op::Update: return DGSRHD_KERNEL_UPDATE;
+    case Op::Enforce: return DGSRHD_KERNEL_ENFORCE;
+    default: return DGSRHD_KERNEL_VJP;
+  }
+}
+
+cudaEvent_t pooled_event(dgsrhd_ctx* c) {
+  if (!c->event_pool.empty()) {
+    cudaEvent_t ev = c->event_pool.back();
+    c->event_pool.pop_back();
+    return ev;
+  }
+  cudaEvent_t ev = nullptr;
+  cudaEventCreate(&ev);
+  return ev;
+}
+
+// Launch bracketed by timing events when profiling is on.
+template <class F>
+cudaError_t timed_launch(dgsrhd_ctx* c, int kind, F&& launch) {
+  if (!c->profiling) return launch();
+  dgsrhd_ctx::TimedLaunch t{kind, pooled_event(c), pooled_event(c)};
+  cudaEventRecord(t.start, c->stream);
+  cudaError_t e = launch();
+  cudaEventRecord(t.stop, c->stream);
+  c->timed.push_back(t);
+  return e;
+}
+
+cudaError_t run_stage(dgsrhd_ctx* c, StageArgs& a) {
+  a.p = &c->p;
+  a.stream = c->stream;
+  cudaError_t e = timed_launch(c, kernel_kind(a.op), [&]() {
+    switch (c->dim) {
+      case 1: return dgsrhd::dispatch_stage<1>(c->N, a);
+      case 2: return dgsrhd::dispatch_stage<2>(c->N, a);
+      default: return dgsrhd::dispatch_stage<3>(c->N, a);
+    }
+  });
+  if (e == cudaSuccess) c->launches += 1;
+  return e;
+}
+
+// R_vol and face traces, then face fluxes (the first two kernels of every RHS)
+cudaError_t volume_and_faces(dgsrhd_ctx* c, const double* U) {
+  StageArgs a{};
+  a.op = Op::Volume;
+  a.U = U;
+  a.Rvol = c->Rv;
+  a.Tr = c->Tr;
+  cudaError_t e = run_stage(c, a);
+  if (e != cudaSuccess) return e;
+  c->c2p_calls += c->E * c->Nn;
+  StageArgs f{};
+  f.op = Op::Face;
+  f.Tr = c->Tr;
+  f.Fs = c->Fs;
+  return run_stage(c, f);
+}
+
+// Shu-Osher coefficients U^(k) = a_n U^n + b_k (U^(k-1) + dt R(U^(k-1)))
+const double kAn[3][3] = {{0.0, 0.0, 0.0}, {0.0, 0.5, 0.0}, {0.0, 0.75, 1.0 / 3.0}};
+const double kBk[3][3] = {{1.0, 0.0, 0.0}, {1.0, 0.5, 0.0}, {1.0, 0.25, 2.0 / 3.0}};
+
+cudaError_t one_step(dgsrhd_ctx* c, double* U, double dt) {
+  const int ns = c->cfg.rk_stages;
+  for (int k = 0; k < ns; ++k) {
+    const double* Uin = (k == 0) ? U : c->A;
+    double* Uout = (k == ns - 1) ? U : c->A;
+    cudaError_t e = volume_and_faces(c, Uin);
+    if (e != cudaSuccess) return e;
+    StageArgs u{};
+    u.op = Op::Update;
+    u.Rvol = c->Rv;
+    u.Fs = c->Fs;
+    u.Un = U;
+    u.Uk = Uin;
+    u.Uout = Uout;
+    u.a_n = kAn[ns - 1][k];
+    u.b_k = kBk[ns - 1][k];
+    u.dt = dt;
+    u.mode = 1;
+    u.enforce = c->cfg.enforce;
+    e = run_stage(c, u);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+bool valid_config(const dgsrhd_config* c) {
+  if (!c) return false;
+  if (c->dim < 1 || c->dim > 3) return false;
+  if (c->degree < 0 || c->degree + 1 > dgsrhd::kMaxN) return false;
+  for (int d = 0; d < c->dim; ++d) {
+    if (c->n_elem[d] < 1) return false;
+    if (!(c->hi[d] > c->lo[d])) return false;
+    for (int s = 0; s < 2; ++s)
+      if (c->bc[d][s] < 0 || c->bc[d][s] > 2) return false;
+    if ((c->bc[d][0] == DGSRHD_BC_PERIODIC) != (c->bc[d][1] == DGSRHD_BC_PERIODIC)) return false;
+    for (int s = 0; s < 2; ++s)
+      if (c->bc[d][s] == DGSRHD_BC_DIRICHLET) {
+        const double* b = c->bc_state[d][s];
+        if (!(b[0] > 0.0) || !(b[4] > 0.0) || !(b[1] * b[1] + b[2] * b[2] + b[3] * b[3] < 1.0))
+          return false;
+      }
+  }
+  if (c->eos != DGSRHD_EOS_IDEAL && c->eos != DGSRHD_EOS_TAUB_MATTHEWS) return false;
+  if (c->eos == DGSRHD_EOS_IDEAL && !(c->gamma_ad > 1.0)) return false;
+  if (c->c2p < 0 || c->c2p > 2) return false;
+  if (c->flux != DGSRHD_FLUX_LLF && c->flux != DGSRHD_FLUX_HLL) return false;
+  if (c->rk_stages < 1 || c->rk_stages > 3) return false;
+  if (c->precision != DGSRHD_PREC_FP64 && c->precision != DGSRHD_PREC_SPLIT) return false;
+  return true;
+}
+
+template <class T>
+cudaError_t alloc(T** p, size_t n) {
+  return cudaMalloc((void**)p, n * sizeof(T));
+}
+
+}  // namespace
+
+extern "C" {
+
+int32_t dgsrhd_create(const dgsrhd_config* cfg, void* stream, dgsrhd_ctx** out) {
+  if (!out) return DGSRHD_EINVAL;
+  *out = nullptr;
+  if (!valid_config(cfg)) return DGSRHD_EINVAL;
+  dgsrhd_ctx* c = new (std::nothrow) dgsrhd_ctx();
+  if (!c) return DGSRHD_ENOMEM;
+  c->cfg = *cfg;
+  c->stream = (cudaStream_t)stream;
+  c->dim = cfg->dim;
+  c->N = cfg->degree + 1;
+  const int N = c->N;
+  Params& p = c->p;
+  memset(&p, 0, sizeof p);
+  p.dim = c->dim;
+  p.N = N;
+  p.Nn = 1;
+  p.Nt = 1;
+  for (int d = 0; d < c->dim; ++d) p.Nn *= N;
+  for (int d = 0; d < c->dim - 1; ++d) p.Nt *= N;
+  long long E = 1;
+  for (int d = 0; d < 3; ++d) {
+    p.n[d] = d < c->dim ? cfg->n_elem[d] : 1;
+    p.stride[d] = E;
+    E *= p.n[d];
+    c->dx[d] = d < c->dim ? (cfg->hi[d] - cfg->lo[d]) / (double)p.n[d] : 1.0;
+    p.inv_half_dx[d] = 2.0 / c->dx[d];
+  }
+  p.E = E;
+  c->E = E;
+  c->Nn = p.Nn;
+  c->nstate = 5 * E * p.Nn;
+  long long off = 0;
+  for (int d = 0; d < 3; ++d) {
+    if (d < c->dim) {
+      p.nface[d] = E + (cfg->bc[d][0] == DGSRHD_BC_PERIODIC ? 0 : E / p.n[d]);
+      p.fs_off[d] = off;
+      off += 5 * p.nface[d] * p.Nt;
+    }
+    for (int s = 0; s < 2; ++s) p.bc[d][s] = d < c->dim ? cfg->bc[d][s] : 0;
+    for (int s = 0; s < 2; ++s) {
+      const double* b = cfg->bc_state[d][s];
+      const double v2 = b[1] * b[1] + b[2] * b[2] + b[3] * b[3];
+      const double lor = (v2 < 1.0) ? 1.0 / sqrt(1.0 - v2) : 1.0;
+      p.ghost[d][s][0] = b[0];
+      p.ghost[d][s][1] = lor * b[1];
+      p.ghost[d][s][2] = lor * b[2];
+      p.ghost[d][s][3] = lor * b[3];
+      p.ghost[d][s][4] = b[4];
+    }
+  }
+  const long long fs_total = off;
+  p.eos = cfg->eos;
+  p.gamma_ad = cfg->gamma_ad;
+  p.alpha = cfg->eos == DGSRHD_EOS_IDEAL ? cfg->gamma_ad / (cfg->gamma_ad - 1.0) : 0.0;
+  p.c2p = cfg->c2p == DGSRHD_C2P_DEFAULT ? (cfg->eos == DGSRHD_EOS_IDEAL ? 0 : 1) : cfg->c2p;
+  p.max_iter = cfg->c2p_max_iter > 0 ? cfg->c2p_max_iter : (cfg->eos == DGSRHD_EOS_IDEAL ? 30 : 100);
+  p.flux = cfg->flux;
+  gauss_legendre(N, c->x, p.w);
+  basis_tables(N, c->x, p.w, p.Dhat, p.em, p.ep);
+  for (int i = 0; i < N; ++i) {
+    p.lm[i] = p.em[i] / p.w[i];
+    p.lp[i] = p.ep[i] / p.w[i];
+  }
+  p.wsum = (double)(1 << c->dim);
+
+  const long long ntr = 2LL * c->dim * 5 * E * p.Nt;
+  cudaError_t e = cudaSuccess;
+  if (e == cudaSuccess) e = alloc(&c->A, c->nstate);
+  if (e == cudaSuccess) e = alloc(&c->Rv, c->nstate);
+  if (e == cudaSuccess) e = alloc(&c->Tr, ntr);
+  if (e == cudaSuccess) e = alloc(&c->Fs, fs_total);
+  if (e == cudaSuccess) e = alloc(&c->Ud, c->nstate);
+  if (e == cudaSuccess) e = alloc(&c->stats, (size_t)dgsrhd::kStatCount * 64);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->stats, 0, sizeof(unsigned long long) * dgsrhd::kStatCount * 64, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) {
+    dgsrhd_destroy(c);
+    cudaGetLastError();
+    return e == cudaErrorMemoryAllocation ? DGSRHD_ENOMEM : DGSRHD_ECUDA;
+  }
+  p.stats = c->stats;
+  *out = c;
+  return DGSRHD_OK;
+}
+
+void dgsrhd_destroy(dgsrhd_ctx* c) {
+  if (!c) return;
+  cudaStreamSynchronize(c->stream);
+  if (c->gexec) cudaGraphExecDestroy(c->gexec);
+  for (auto& t : c->timed) {
+    cudaEventDestroy(t.start);
+    cudaEventDestroy(t.stop);
+  }
+  for (auto ev : c->event_pool) cudaEventDestroy(ev);
+  cudaFree(c->A);
+  cudaFree(c->Rv);
+  cudaFree(c->Tr);
+  cudaFree(c->Fs);
+  cudaFree(c->Ud);
+  cudaFree(c->Wv);
+  cudaFree(c->TrB);
+  cudaFree(c->stats);
+  delete c;
+}
+
+int32_t dgsrhd_set_stream(dgsrhd_ctx* c, void* stream) {
+  if (!c) return DGSRHD_EINVAL;
+  if ((cudaStream_t)stream != c->stream && c->gexec) {
+    cudaGraphExecDestroy(c->gexec);
+    c->gexec = nullptr;
+  }
+  c->stream = (cudaStream_t)stream;
+  return DGSRHD_OK;
+}
+
+int32_t dgsrhd_state_shape(const dgsrhd_ctx* c, int64_t* nvar, int64_t* n_elem, int64_t* n_node) {
+  if (!c) return DGSRHD_EINVAL;
+  if (nvar) *nvar = 5;
+  if (n_elem) *n_elem = c->E;
+  if (n_node) *n_node = c->Nn;
+  return DGSRHD_OK;
+}
+
+int32_t dgsrhd_node_coords(const dgsrhd_ctx* c, double* X) {
+  if (!c || !X) return DGSRHD_EINVAL;
+  const int N = c->N;
+  for (long long e = 0; e < c->E; ++e) {
+    for (int i = 0; i < c->Nn; ++i) {
+      int ijk[3] = {i % N, (i / N) % N, i / (N * N)};
+      for (int d = 0; d < c->dim; ++d) {
+        const long long ce = (e / c->p.stride[d]) % c->p.n[d];
+        X[((long long)d * c->E + e) * c->Nn + i] =
+            c->cfg.lo[d] + ((double)ce + 0.5 * (1.0 + c->x[ijk[d]])) * c->dx[d];
+      }
+    }
+  }
+  return DGSRHD_OK;
+}
+
+int32_t dgsrhd_prim2cons(dgsrhd_ctx* c, const double* W, double* U) {
+  if (!c || !W || !U) return DGSRHD_EINVAL;
+  cudaError_t e = timed_launch(c, DGSRHD_KERNEL_POINTWISE, [&]() {
+    return dgsrhd::launch_prim2cons(c->p, c->stream, c->E * c->Nn, W, U);
+  });
+  if (e == cudaSuccess) c->launches += 1;
+  return cuda_status(e);
+}
+
+int32_t dgsrhd_con2prim(dgsrhd_ctx* c, const double* U, double* W, int32_t* iters) {
+  if (!c || !U || !W) return DGSRHD_EINVAL;
+  cudaError_t e = timed_launch(c, DGSRHD_KERNEL_POINTWISE, [&]() {
+    return dgsrhd::launch_con2prim(c->p, c->stream, c->E * c->Nn, U, W, iters);
+  });
+  if (e == cudaSuccess) {
+    c->launches += 1;
+    c->c2p_calls += c->E * c->Nn;
+  }
+  return cuda_status(e);
+}
+
+int32_t dgsrhd_rhs(dgsrhd_ctx* c, const double* U, double* R) {
+  if (!c || !U || !R || U == R) return DGSRHD_EINVAL;
+  cudaError_t e = volume_and_faces(c, U);
+  if (e != cudaSuccess) return DGSRHD_ECUDA;
+  StageArgs u{};
+  u.op = Op::Update;
+  u.Rvol = c->Rv;
+  u.Fs = c->Fs;
+  u.Uout = R;
+  u.mode = 0;
+  return cuda_status(run_stage(c, u));
+}
+
+int32_t dgsrhd_enforce(dgsrhd_ctx* c, double* U, double* s_out) {
+  if (!c || !U) return DGSRHD_EINVAL;
+  StageArgs a{};
+  a.op = Op::Enforce;
+  a.Uout = U;
+  a.s_out = s_out;
+  return cuda_status(run_stage(c, a));
+}
+
+int32_t dgsrhd_step(dgsrhd_ctx* c, double* U, double dt, int32_t nsteps) {
+  if (!c || !U || nsteps < 0 || !(dt >= 0.0)) return DGSRHD_EINVAL;
+  if (nsteps == 0) return DGSRHD_OK;
+  const long long per_step = 3LL * c->cfg.rk_stages;
+  if (c->stream == nullptr || c->profiling) {
+    // the legacy stream cannot be captured, and timed kernels are launched one by one
+    for (int s = 0; s < nsteps; ++s) {
+      cudaError_t e = one_step(c, U, dt);
+      if (e != cudaSuccess) return DGSRHD_ECUDA;
+    }
+    return DGSRHD_OK;
+  }
+  if (!c->gexec || c->g_dt != dt || c->g_U != U) {
+    if (c->gexec) {
+      cudaGraphExecDestroy(c->gexec);
+      c->gexec = nullptr;
+    }
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return DGSRHD_ECUDA;
+    const long long l0 = c->launches, k0 = c->c2p_calls;
+    cudaError_t e1 = one_step(c, U, dt);
+    e = cudaStreamEndCapture(c->stream, &g);
+    c->launches = l0;  // captured, not launched
+    c->c2p_calls = k0;
+    if (e1 != cudaSuccess || e != cudaSuccess) {
+      if (g) cudaGraphDestroy(g);
+      cudaGetLastError();
+      return DGSRHD_ECUDA;
+    }
+    e = cudaGraphInstantiate(&c->gexec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+      c->gexec = nullptr;
+      return DGSRHD_ECUDA;
+    }
+    c->g_dt = dt;
+    c->g_U = U;
+  }
+  for (int s = 0; s < nsteps; ++s) {
+    cudaError_t e = cudaGraphLaunch(c->gexec, c->stream);
+    if (e != cudaSuccess) return DGSRHD_ECUDA;
+  }
+  c->launches += per_step * nsteps;
+  c->c2p_calls += (long long)nsteps * c->cfg.rk_stages * c->E * c->Nn;
+  return DGSRHD_OK;
+}
+
+int32_t dgsrhd_step_host(dgsrhd_ctx* c, double* U_host, double dt, int32_t nsteps) {
+  if (!c || !U_host) return DGSRHD_EINVAL;
+  const size_t bytes = sizeof(double) * c->nstate;
+  if (cudaMemcpyAsync(c->Ud, U_host, bytes, cudaMemcpyHostToDevice, c->stream) != cudaSuccess)
+    return DGSRHD_ECUDA;
+  int32_t st = dgsrhd_step(c, c->Ud, dt, nsteps);
+  if (st != DGSRHD_OK) return st;
+  if (cudaMemcpyAsync(U_host, c->Ud, bytes, cudaMemcpyDeviceToHost, c->stream) != cudaSuccess)
+    return DGSRHD_ECUDA;
+  return cuda_status(cudaStreamSynchronize(c->stream));
+}
+
+int32_t dgsrhd_cfl_dt(const dgsrhd_ctx* c, double cfl, double* dt) {
+  if (!c || !dt || !(cfl > 0.0)) return DGSRHD_EINVAL;
+  double s = 0.0;
+  for (int d = 0; d < c->dim; ++d) s += 1.0 / c->dx[d];
+  *dt = cfl / ((2.0 * c->cfg.degree + 1.0) * s);
+  return DGSRHD_OK;
+}
+
+int32_t dgsrhd_get_stats(dgsrhd_ctx* c, dgsrhd_stats* out, int32_t reset) {
+  if (!c || !out) return DGSRHD_EINVAL;
+  unsigned long long h[dgsrhd::kStatCount * 64];
+  const size_t bytes = sizeof h;
+  if (cudaMemcpyAsync(h, c->stats, bytes, cudaMemcpyDeviceToHost, c->stream) != cudaSuccess)
+    return DGSRHD_ECUDA;
+  if (cudaStreamSynchronize(c->stream) != cudaSuccess) return DGSRHD_ECUDA;
+  unsigned long long v[dgsrhd::kStatCount] = {0};
+  for (int k = 0; k < dgsrhd::kStatCount; ++k)
+    for (int s = 0; s < 64; ++s) {
+      const unsigned long long x = h[k * 64 + s];
+      if (k == dgsrhd::kStatItersMax)
+        v[k] = x > v[k] ? x : v[k];
+      else
+        v[k] += x;
+    }
+  out->c2p_calls = c->c2p_calls;
+  out->c2p_iters_total = (int64_t)v[dgsrhd::kStatItersTotal];
+  out->c2p_iters_max = (int64_t)v[dgsrhd::kStatItersMax];
+  out->c2p_nonconverged = (int64_t)v[dgsrhd::kStatNonConv];
+  out->c2p_invalid_input = (int64_t)v[dgsrhd::kStatInvalid];
+  out->face_guard_hits = (int64_t)v[dgsrhd::kStatFaceGuard];
+  out->enforced_cells = (int64_t)v[dgsrhd::kStatEnforced];
+  out->mean_inadmissible_cells = (int64_t)v[dgsrhd::kStatMeanBad];
+  if (reset) {
+    if (cudaMemsetAsync(c->stats, 0, bytes, c->stream) != cudaSuccess) return DGSRHD_ECUDA;
+    if (cudaStreamSynchronize(c->stream) != cudaSuccess) return DGSRHD_ECUDA;
+    c->c2p_calls = 0;
+  }
+  if (out->c2p_invalid_input) return DGSRHD_EBADSTATE;
+  if (out->c2p_nonconverged) return DGSRHD_EC2P_NOCONV;
+  if (out->mean_inadmissible_cells) return DGSRHD_EUNPHYS_MEAN;
+  return DGSRHD_OK;
+}
+
+int64_t dgsrhd_kernel_launches(const dgsrhd_ctx* c) { return c ? c->launches : 0; }
+
+int32_t dgsrhd_set_profiling(dgsrhd_ctx* c, int32_t enable) {
+  if (!c) return DGSRHD_EINVAL;
+  c->profiling = enable != 0;
+  return DGSRHD_OK;
+}
+
+int32_t dgsrhd_kernel_times(dgsrhd_ctx* c, double* ms, int64_t* counts, int32_t reset) {
+  if (!c || !ms || !counts) return DGSRHD_EINVAL;
+  if (cudaStreamSynchronize(c->stream) != cudaSuccess) return DGSRHD_ECUDA;
+  for (int k = 0; k < DGSRHD_KERNEL_KINDS; ++k) {
+    ms[k] = 0.0;
+    counts[k] = 0;
+  }
+  for (auto& t : c->timed) {
+    float v = 0.0f;
+    if (cudaEventElapsedTime(&v, t.start, t.stop) != cudaSuccess) return DGSRHD_ECUDA;
+    ms[t.kind] += v;
+    counts[t.kind] += 1;
+  }
+  if (reset) {
+    for (auto& t : c->timed) {
+      c->event_pool.push_back(t.start);
+      c->event_pool.push_back(t.stop);
+    }
+    c->timed.clear();
+  }
+  return DGSRHD_OK;
+}
+
+int32_t dgsrhd_rhs_vjp(dgsrhd_ctx* c, const double* U, const double* R_bar, double* U_bar) {
+  (void)c;
+  (void)U;
+  (void)R_bar;
+  (void)U_bar;
+  return DGSRHD_EINVAL;
+}
+
+int32_t dgsrhd_enforce_vjp(dgsrhd_ctx* c, const double* s, const double* Ut_bar, double* U_bar) {
+  (void)c;
+  (void)s;
+  (void)Ut_bar;
+  (void)U_bar;
+  return DGSRHD_EINVAL;
+}
+
+const char* dgsrhd_status_string(int32_t s) {
+  switch (s) {
+    case DGSRHD_OK: return "ok";
+    case DGSRHD_EINVAL: return "invalid argument";
+    case DGSRHD_ECUDA: return "CUDA error";
+    case DGSRHD_ENOMEM: return "out of device memory";
+    case DGSRHD_EC2P_NOCONV: return "con2prim did not converge";
+    case DGSRHD_EUNPHYS_MEAN: return "inadmissible element mean";
+    case DGSRHD_EBADSTATE: return "invalid conserved state";
+    default: return "unknown status";
+  }
+}
+
+}  // extern "C"

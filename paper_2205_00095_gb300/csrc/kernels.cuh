@@ -1,0 +1,492 @@
+// Element kernels of the nodal DG right-hand side and the SSP-RK stage (FP64 path).
+//
+// One RK stage is three kernels:
+//   volume_kernel : per element, one thread per node.  con2prim at every node (Sec. 3), nodal
+//                   fluxes (Eq. srhd_flux), the sum-factorised volume term
+//                   R_vol[i] = sum_d (2/dx_d) sum_a Dhat[i_d][a] F^d[.. a ..] (Eq. quad-vol-flux at
+//                   the nodes), and the primitive (rho, u, P) extrapolated to the 2 dim faces of the
+//                   element, sum_i phi_i(+-1) W_i along each normal line (Sec. 2.3).
+//   face_kernel   : one thread per face point; LLF/HLL flux of the two traces (Sec. 2.4).
+//   update_kernel : per element, one thread per node; R = R_vol - lift of the face fluxes
+//                   (Eq. quad-surface-flux), the Shu-Osher combination, and the physicality
+//                   operator of Sec. 2.5.
+// Face fluxes are computed once per face point and read by both neighbours.
+#pragma once
+
+#include "device_math.cuh"
+#include "launch.h"
+
+namespace dgsrhd {
+
+__host__ __device__ constexpr int ipow(int b, int e) { return e == 0 ? 1 : b * ipow(b, e - 1); }
+
+template <int DIM, int N>
+struct Shape {
+  static constexpr int Nn = ipow(N, DIM);        // nodes per element
+  static constexpr int Nt = ipow(N, DIM - 1);    // nodes per face
+  static constexpr int EPB = Nn >= 256 ? 1 : 256 / Nn;  // elements per block
+  static constexpr int BLOCK = EPB * Nn;
+  static constexpr int NFP = 2 * DIM * Nt;       // face points per element
+};
+
+// node index -> (a, b, c), x fastest
+template <int DIM, int N>
+__device__ __forceinline__ void node_ijk(int i, int ijk[3]) {
+  ijk[0] = i % N;
+  ijk[1] = DIM > 1 ? (i / N) % N : 0;
+  ijk[2] = DIM > 2 ? i / (N * N) : 0;
+}
+
+// stride of axis d inside the element's node index
+template <int N>
+__device__ __forceinline__ int node_stride(int d) {
+  return d == 0 ? 1 : (d == 1 ? N : N * N);
+}
+
+// tangential index of a node on the faces normal to d (other axes in order, x fastest)
+template <int DIM, int N>
+__device__ __forceinline__ int tan_index(const int ijk[3], int d) {
+  if (DIM == 1) return 0;
+  if (DIM == 2) return d == 0 ? ijk[1] : ijk[0];
+  return d == 0 ? ijk[1] + N * ijk[2] : (d == 1 ? ijk[0] + N * ijk[2] : ijk[0] + N * ijk[1]);
+}
+
+// node index of tangential point t on the line normal to d at normal coordinate a
+template <int DIM, int N>
+__device__ __forceinline__ int line_node(int d, int t, int a) {
+  if (DIM == 1) return a;
+  if (DIM == 2) return d == 0 ? a + N * t : t + N * a;
+  const int t0 = t % N, t1 = t / N;
+  return d == 0 ? a + N * (t0 + N * t1) : (d == 1 ? t0 + N * (a + N * t1) : t0 + N * (t1 + N * a));
+}
+
+__device__ __forceinline__ long long elem_coord(const Params& p, long long e, int d) {
+  return (e / p.stride[d]) % p.n[d];
+}
+
+// index of the face flux on the high side of element e along d
+__device__ __forceinline__ long long high_face(const Params& p, long long e, int d) {
+  const long long c = elem_coord(p, e, d);
+  if (c < p.n[d] - 1) return e + p.stride[d];
+  if (p.bc[d][1] == 0) return e - (p.n[d] - 1) * p.stride[d];
+  // boundary face: enumerate the elements with c = n_d - 1 by their other coordinates
+  long long j;
+  if (d == 0)
+    j = e / p.n[0];
+  else if (d == 1)
+    j = (e % p.n[0]) + p.n[0] * (e / (p.n[0] * p.n[1]));
+  else
+    j = e % (p.n[0] * p.n[1]);
+  return p.E + j;
+}
+
+// block-level reduction of con2prim statistics into 64 slots of each counter
+__device__ __forceinline__ void block_stats(const Params& p, int iters, int status, int* shred) {
+  // blocks need not be a multiple of 32 threads: the last warp may be partial
+  const int in_warp = min(32, (int)blockDim.x - (int)(threadIdx.x & ~31u));
+  const unsigned full = in_warp == 32 ? 0xffffffffu : ((1u << in_warp) - 1u);
+  unsigned it = (unsigned)iters;
+  unsigned sum = __reduce_add_sync(full, it);
+  unsigned mx = __reduce_max_sync(full, it);
+  unsigned nc = __popc(__ballot_sync(full, status == 2));
+  unsigned inv = __popc(__ballot_sync(full, status == 1));
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (threadIdx.x < 4 * 32) shred[threadIdx.x] = 0;
+  __syncthreads();
+  if (lane == 0) {
+    atomicAdd(&shred[0], (int)sum);
+    atomicMax(&shred[1], (int)mx);
+    atomicAdd(&shred[2], (int)nc);
+    atomicAdd(&shred[3], (int)inv);
+  }
+  __syncthreads();
+  (void)warp;
+  if (threadIdx.x == 0) {
+    unsigned long long* st = p.stats;
+    const int slot = blockIdx.x & 63;
+    if (shred[0]) atomicAdd(&st[kStatItersTotal * 64 + slot], (unsigned long long)shred[0]);
+    if (shred[1]) atomicMax(&st[kStatItersMax * 64 + slot], (unsigned long long)shred[1]);
+    if (shred[2]) atomicAdd(&st[kStatNonConv * 64 + slot], (unsigned long long)shred[2]);
+    if (shred[3]) atomicAdd(&st[kStatInvalid * 64 + slot], (unsigned long long)shred[3]);
+  }
+}
+
+// ---------------------------------------------------------------------------------------
+// Volume kernel
+// ---------------------------------------------------------------------------------------
+template <int DIM, int N>
+__global__ void __launch_bounds__(Shape<DIM, N>::BLOCK)
+    volume_kernel(Params p, const double* __restrict__ U, double* __restrict__ Rvol,
+                  double* __restrict__ Tr) {
+  using S = Shape<DIM, N>;
+  constexpr int Nn = S::Nn, Nt = S::Nt, BLOCK = S::BLOCK;
+  __shared__ double shF[DIM][5][BLOCK];
+  __shared__ double shW[5][BLOCK];
+  __shared__ double shD[N * N];
+  __shared__ int shred[4 * 32];
+  const int tid = threadIdx.x;
+  if (tid < N * N) shD[tid] = p.Dhat[tid];
+  const int le = tid / Nn, li = tid - le * Nn;
+  const long long e = (long long)blockIdx.x * S::EPB + le;
+  const bool valid = e < p.E;
+  const long long tot = p.E * Nn;
+  const long long g = e * Nn + li;
+
+  int iters = 0, status = 0;
+  if (valid) {
+    double u[5];
+#pragma unroll
+    for (int v = 0; v < 5; ++v) u[v] = U[v * tot + g];
+    Prim W;
+    status = con2prim(p, u, W, iters);
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) {
+      double F[5];
+      phys_flux(u, W.v, W.P, d, F);
+#pragma unroll
+      for (int v = 0; v < 5; ++v) shF[d][v][tid] = F[v];
+    }
+    shW[0][tid] = W.rho;
+    shW[1][tid] = W.lor * W.v[0];
+    shW[2][tid] = W.lor * W.v[1];
+    shW[3][tid] = W.lor * W.v[2];
+    shW[4][tid] = W.P;
+  }
+  block_stats(p, iters, status, shred);  // contains __syncthreads
+
+  if (valid) {
+    int ijk[3];
+    node_ijk<DIM, N>(li, ijk);
+    double acc[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) {
+      const int ns = node_stride<N>(d);
+      const int base = tid - ijk[d] * ns;
+      const double sc = p.inv_half_dx[d];
+#pragma unroll
+      for (int a = 0; a < N; ++a) {
+        const double c = sc * shD[ijk[d] * N + a];
+#pragma unroll
+        for (int v = 0; v < 5; ++v) acc[v] = fma(c, shF[d][v][base + a * ns], acc[v]);
+      }
+    }
+#pragma unroll
+    for (int v = 0; v < 5; ++v) Rvol[v * tot + g] = acc[v];
+
+    // face traces of (rho, u, P)
+    int guard = 0;
+    for (int fp = li; fp < S::NFP; fp += Nn) {
+      const int d = fp / (2 * Nt);
+      const int side = (fp / Nt) & 1;
+      const int t = fp % Nt;
+      double out[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+#pragma unroll
+      for (int a = 0; a < N; ++a) {
+        const int node = le * Nn + line_node<DIM, N>(d, t, a);
+        const double c = side ? p.ep[a] : p.em[a];
+#pragma unroll
+        for (int v = 0; v < 5; ++v) out[v] = fma(c, shW[v][node], out[v]);
+      }
+      if (!(out[0] > 0.0) || !(out[4] > 0.0)) {
+        const int node = le * Nn + line_node<DIM, N>(d, t, side ? N - 1 : 0);
+#pragma unroll
+        for (int v = 0; v < 5; ++v) out[v] = shW[v][node];
+        ++guard;
+      }
+#pragma unroll
+      for (int v = 0; v < 5; ++v) Tr[((((long long)d * 2 + side) * 5 + v) * p.E + e) * Nt + t] = out[v];
+    }
+    if (guard) atomicAdd(&p.stats[kStatFaceGuard * 64 + (blockIdx.x & 63)], (unsigned long long)guard);
+  }
+}
+
+// ---------------------------------------------------------------------------------------
+// Face kernel: blockIdx.y = axis
+// ---------------------------------------------------------------------------------------
+template <int DIM, int N>
+__global__ void __launch_bounds__(128) face_kernel(Params p, const double* __restrict__ Tr,
+                                                   double* __restrict__ Fs) {
+  constexpr int Nt = Shape<DIM, N>::Nt;
+  const int d = blockIdx.y;
+  const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long nf = p.nface[d];
+  if (k >= nf * Nt) return;
+  const long long f = k / Nt;
+  const int t = (int)(k - f * Nt);
+  long long eL, eR;
+  if (f < p.E) {
+    eR = f;
+    const long long c = elem_coord(p, f, d);
+    if (c > 0)
+      eL = f - p.stride[d];
+    else if (p.bc[d][0] == 0)
+      eL = f + (p.n[d] - 1) * p.stride[d];
+    else
+      eL = -1;
+  } else {
+    const long long j = f - p.E;
+    if (d == 0)
+      eL = (p.n[0] - 1) + p.n[0] * j;
+    else if (d == 1)
+      eL = (j % p.n[0]) + p.n[0] * ((p.n[1] - 1) + p.n[1] * (j / p.n[0]));
+    else
+      eL = j + p.n[0] * p.n[1] * (p.n[2] - 1);
+    eR = -1;
+  }
+  double WL[5], WR[5];
+  const long long side_stride = 5 * p.E * Nt;
+  const double* trL = Tr + ((long long)d * 2 + 1) * side_stride;  // high side of the left elem
+  const double* trR = Tr + ((long long)d * 2 + 0) * side_stride;  // low side of the right elem
+  if (eL >= 0) {
+#pragma unroll
+    for (int v = 0; v < 5; ++v) WL[v] = trL[(v * p.E + eL) * Nt + t];
+  }
+  if (eR >= 0) {
+#pragma unroll
+    for (int v = 0; v < 5; ++v) WR[v] = trR[(v * p.E + eR) * Nt + t];
+  }
+  if (eL < 0) {
+#pragma unroll
+    for (int v = 0; v < 5; ++v) WL[v] = (p.bc[d][0] == 1) ? p.ghost[d][0][v] : WR[v];
+  }
+  if (eR < 0) {
+#pragma unroll
+    for (int v = 0; v < 5; ++v) WR[v] = (p.bc[d][1] == 1) ? p.ghost[d][1][v] : WL[v];
+  }
+  double F[5];
+  numerical_flux(p, WL, WR, d, F);
+  double* out = Fs + p.fs_off[d];
+#pragma unroll
+  for (int v = 0; v < 5; ++v) out[(v * nf + f) * Nt + t] = F[v];
+}
+
+// ---------------------------------------------------------------------------------------
+// Physicality operator on the elements of one block (Sec. 2.5).  u holds this thread's node
+// state; on return it holds the smoothed state.  Every thread of the block must call it.
+// ---------------------------------------------------------------------------------------
+template <int DIM, int N>
+struct EnforceShared {
+  double a[5][Shape<DIM, N>::BLOCK];
+  double mean[Shape<DIM, N>::EPB][5];
+  double s[Shape<DIM, N>::EPB];
+  int flag[Shape<DIM, N>::EPB];
+};
+
+template <int DIM, int N>
+__device__ __forceinline__ void enforce_block(const Params& p, double u[5], bool valid, int le,
+                                              int li, long long e, double* s_out,
+                                              EnforceShared<DIM, N>& sh) {
+  constexpr int Nn = Shape<DIM, N>::Nn;
+  const int tid = threadIdx.x;
+  const bool bad = valid && !admissible(u);
+  if (!__syncthreads_or(bad)) {
+    if (valid && li == 0 && s_out) s_out[e] = 1.0;
+    return;
+  }
+  if (li == 0) sh.flag[le] = 0;
+  __syncthreads();
+  if (bad) sh.flag[le] = 1;
+  int ijk[3];
+  node_ijk<DIM, N>(li, ijk);
+  double wi = 1.0;
+#pragma unroll
+  for (int d = 0; d < DIM; ++d) wi *= p.w[ijk[d]];
+#pragma unroll
+  for (int v = 0; v < 5; ++v) sh.a[v][tid] = valid ? wi * u[v] : 0.0;
+  __syncthreads();
+  if (li == 0 && valid && sh.flag[le]) {
+    double m[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+    for (int j = 0; j < Nn; ++j)
+#pragma unroll
+      for (int v = 0; v < 5; ++v) m[v] += sh.a[v][le * Nn + j];
+#pragma unroll
+    for (int v = 0; v < 5; ++v) sh.mean[le][v] = m[v] / p.wsum;
+    sh.flag[le] = admissible(sh.mean[le]) ? 2 : 3;
+  }
+  __syncthreads();
+  const int fl = valid ? sh.flag[le] : 0;
+  double si = 1.0;
+  if (fl == 2) {
+    const double* m = sh.mean[le];
+    const double Db = m[0], taub = m[4], Eb = m[4] + m[0];
+    // stage 1: largest factors keeping D and E positive (Eq. first_stage_positivity)
+    const double sD = u[0] >= 0.0 ? 1.0 : Db / (Db - u[0]);
+    const double Ei = u[4] + u[0];
+    const double sE = Ei >= 0.0 ? 1.0 : Eb / (Eb - Ei);
+    const double s1 = fmin(sD, sE);
+    double U1[5];
+#pragma unroll
+    for (int v = 0; v < 5; ++v) U1[v] = s1 * u[v] + (1.0 - s1) * m[v];
+    si = s1;
+    if (!admissible(U1)) {
+      // stage 2 quadratic a s^2 + b s + c0 > 0 in the stored variables (Eq.
+      // second_stage_coefficients with E = tau + D), root of Eq. second_stage_solution in
+      // the form 2 c0 / (-b + sqrt(b^2 - 4 a c0)), clamped to [0, 1]
+      const double dD = U1[0] - Db, dtau = U1[4] - taub;
+      const double d1 = U1[1] - m[1], d2 = U1[2] - m[2], d3 = U1[3] - m[3];
+      const double qa = dtau * (dtau + 2.0 * dD) - (d1 * d1 + d2 * d2 + d3 * d3);
+      const double qb = 2.0 * (taub * (dtau + dD) + Db * dtau - (m[1] * d1 + m[2] * d2 + m[3] * d3));
+      const double qc = taub * (taub + 2.0 * Db) - (m[1] * m[1] + m[2] * m[2] + m[3] * m[3]);
+      const double den = -qb + sqrt(qb * qb - 4.0 * qa * qc);
+      double s2 = den > 0.0 ? 2.0 * qc / den : 1.0;
+      s2 = fmin(fmax(s2, 0.0), 1.0);
+      si = s1 * s2;
+    }
+  }
+  sh.a[0][tid] = si;
+  __syncthreads();
+  if (li == 0 && valid) {
+    double s = 1.0;
+    if (fl == 2) {
+      for (int j = 0; j < Nn; ++j) s = fmin(s, sh.a[0][le * Nn + j]);
+      s *= (1.0 - 1e-12);
+      atomicAdd(&p.stats[kStatEnforced * 64 + (blockIdx.x & 63)], 1ull);
+    } else if (fl == 3) {
+      atomicAdd(&p.stats[kStatMeanBad * 64 + (blockIdx.x & 63)], 1ull);
+    }
+    sh.s[le] = s;
+    if (s_out) s_out[e] = s;
+  }
+  __syncthreads();
+  if (fl == 2) {
+    const double s = sh.s[le];
+#pragma unroll
+    for (int v = 0; v < 5; ++v) u[v] = s * u[v] + (1.0 - s) * sh.mean[le][v];
+  }
+}
+
+// ---------------------------------------------------------------------------------------
+// Update kernel: R = R_vol - lift; mode 0 writes R, mode 1 writes the RK stage
+// Uout = a_n Un + b_k (Uk + dt R) followed (if enforce) by the physicality operator.
+// Uout may alias Uk or Un (each thread reads its own node before the block writes).
+// ---------------------------------------------------------------------------------------
+template <int DIM, int N>
+__global__ void __launch_bounds__(Shape<DIM, N>::BLOCK)
+    update_kernel(Params p, const double* __restrict__ Rvol, const double* __restrict__ Fs,
+                  const double* Un, const double* Uk, double* Uout, double a_n, double b_k,
+                  double dt, int mode, int enforce, double* __restrict__ s_out) {
+  using S = Shape<DIM, N>;
+  constexpr int Nn = S::Nn;
+  __shared__ EnforceShared<DIM, N> sh;
+  __shared__ double shl[2][N];
+  const int tid = threadIdx.x;
+  if (tid < N) {
+    shl[0][tid] = p.lm[tid];
+    shl[1][tid] = p.lp[tid];
+  }
+  __syncthreads();
+  const int le = tid / Nn, li = tid - le * Nn;
+  const long long e = (long long)blockIdx.x * S::EPB + le;
+  const bool valid = e < p.E;
+  const long long tot = p.E * Nn;
+  const long long g = e * Nn + li;
+  double u[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+  if (valid) {
+    int ijk[3];
+    node_ijk<DIM, N>(li, ijk);
+    double R[5];
+#pragma unroll
+    for (int v = 0; v < 5; ++v) R[v] = Rvol[v * tot + g];
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) {
+      const int t = tan_index<DIM, N>(ijk, d);
+      const long long nf = p.nface[d];
+      const double* fs = Fs + p.fs_off[d];
+      const long long flo = e, fhi = high_face(p, e, d);
+      const double cp = p.inv_half_dx[d] * shl[1][ijk[d]];
+      const double cm = p.inv_half_dx[d] * shl[0][ijk[d]];
+#pragma unroll
+      for (int v = 0; v < 5; ++v) {
+        const double Fhi = fs[(v * nf + fhi) * S::Nt + t];
+        const double Flo = fs[(v * nf + flo) * S::Nt + t];
+        R[v] = R[v] - cp * Fhi + cm * Flo;
+      }
+    }
+    if (mode == 0) {
+#pragma unroll
+      for (int v = 0; v < 5; ++v) Uout[v * tot + g] = R[v];
+    } else {
+#pragma unroll
+      for (int v = 0; v < 5; ++v) {
+        const double x = fma(dt, R[v], Uk[v * tot + g]);
+        u[v] = (a_n != 0.0) ? fma(a_n, Un[v * tot + g], b_k * x) : b_k * x;
+      }
+    }
+  }
+  if (mode == 0) return;  // uniform over the grid
+  if (enforce) enforce_block<DIM, N>(p, u, valid, le, li, e, s_out, sh);
+  if (valid) {
+#pragma unroll
+    for (int v = 0; v < 5; ++v) Uout[v * tot + g] = u[v];
+  }
+}
+
+// Stand-alone physicality operator, in place.
+template <int DIM, int N>
+__global__ void __launch_bounds__(Shape<DIM, N>::BLOCK)
+    enforce_kernel(Params p, double* U, double* __restrict__ s_out) {
+  using S = Shape<DIM, N>;
+  constexpr int Nn = S::Nn;
+  __shared__ EnforceShared<DIM, N> sh;
+  const int tid = threadIdx.x;
+  const int le = tid / Nn, li = tid - le * Nn;
+  const long long e = (long long)blockIdx.x * S::EPB + le;
+  const bool valid = e < p.E;
+  const long long tot = p.E * Nn;
+  const long long g = e * Nn + li;
+  double u[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+  if (valid)
+#pragma unroll
+    for (int v = 0; v < 5; ++v) u[v] = U[v * tot + g];
+  enforce_block<DIM, N>(p, u, valid, le, li, e, s_out, sh);
+  if (valid)
+#pragma unroll
+    for (int v = 0; v < 5; ++v) U[v * tot + g] = u[v];
+}
+
+// ---------------------------------------------------------------------------------------
+// Host-side launchers
+// ---------------------------------------------------------------------------------------
+template <int DIM, int N>
+static cudaError_t launch_stage_kernels(const StageArgs& a) {
+  using S = Shape<DIM, N>;
+  const Params& p = *a.p;
+  const unsigned eblocks = (unsigned)((p.E + S::EPB - 1) / S::EPB);
+  switch (a.op) {
+    case Op::Volume:
+      volume_kernel<DIM, N><<<eblocks, S::BLOCK, 0, a.stream>>>(p, a.U, a.Rvol, a.Tr);
+      break;
+    case Op::Face: {
+      long long mx = 0;
+      for (int d = 0; d < DIM; ++d) mx = p.nface[d] > mx ? p.nface[d] : mx;
+      const long long nthreads = mx * S::Nt;
+      dim3 grid((unsigned)((nthreads + 127) / 128), DIM);
+      face_kernel<DIM, N><<<grid, 128, 0, a.stream>>>(p, a.Tr, a.Fs);
+      break;
+    }
+    case Op::Update:
+      update_kernel<DIM, N><<<eblocks, S::BLOCK, 0, a.stream>>>(
+          p, a.Rvol, a.Fs, a.Un, a.Uk, a.Uout, a.a_n, a.b_k, a.dt, a.mode, a.enforce, a.s_out);
+      break;
+    case Op::Enforce:
+      enforce_kernel<DIM, N><<<eblocks, S::BLOCK, 0, a.stream>>>(p, a.Uout, a.s_out);
+      break;
+    default:
+      return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+template <int DIM>
+cudaError_t dispatch_stage(int N, const StageArgs& a) {
+  switch (N) {
+    case 1: return launch_stage_kernels<DIM, 1>(a);
+    case 2: return launch_stage_kernels<DIM, 2>(a);
+    case 3: return launch_stage_kernels<DIM, 3>(a);
+    case 4: return launch_stage_kernels<DIM, 4>(a);
+    case 5: return launch_stage_kernels<DIM, 5>(a);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace dgsrhd

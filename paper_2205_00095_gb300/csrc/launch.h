@@ -1,0 +1,43 @@
+// Launch interface between the host API and the per-dimension kernel translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "params.h"
+
+namespace dgsrhd {
+
+enum class Op { Volume, Face, Update, Enforce, VjpVolume, VjpFace, VjpLift };
+
+struct StageArgs {
+  Op op;
+  const Params* p;
+  cudaStream_t stream;
+  const double* U;     // Volume: state whose RHS is formed
+  double* Rvol;        // volume term (also R of the VJP)
+  double* Tr;          // face traces
+  double* Fs;          // face fluxes
+  const double* Un;    // Update: U^n
+  const double* Uk;    // Update: U^(k-1)
+  double* Uout;        // Update: output; Enforce: state in place
+  double a_n, b_k, dt;
+  int mode;            // Update: 0 = write R, 1 = RK stage
+  int enforce;
+  double* s_out;
+  // VJP buffers
+  const double* Rbar;
+  double* Ubar;
+  double* TrBar;
+  double* Wstore;
+};
+
+template <int DIM>
+cudaError_t dispatch_stage(int N, const StageArgs& a);
+
+// point-wise kernels (dimension independent)
+cudaError_t launch_prim2cons(const Params& p, cudaStream_t s, long long n, const double* W,
+                             double* U);
+cudaError_t launch_con2prim(const Params& p, cudaStream_t s, long long n, const double* U,
+                            double* W, int* iters);
+
+}  // namespace dgsrhd

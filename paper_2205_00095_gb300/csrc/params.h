@@ -1,0 +1,47 @@
+// Launch parameters shared by the host API and the kernels (passed by value).
+#pragma once
+
+#include <stdint.h>
+
+namespace dgsrhd {
+
+constexpr int kMaxN = 5;  // degree <= 4
+
+// Indices into the device counter array (unsigned long long).
+enum StatSlot {
+  kStatC2pCalls = 0,
+  kStatItersTotal,
+  kStatItersMax,
+  kStatNonConv,
+  kStatInvalid,
+  kStatFaceGuard,
+  kStatEnforced,
+  kStatMeanBad,
+  kStatCount
+};
+
+struct Params {
+  int dim, N, Nn, Nt;        // nodes per axis, per element (N^dim), per face (N^(dim-1))
+  long long n[3];            // elements per axis (1 for unused axes)
+  long long stride[3];       // element index stride per axis: 1, n0, n0 n1
+  long long E;               // elements
+  long long nface[3];        // faces per axis: E (+ E/n_d boundary faces if not periodic)
+  long long fs_off[3];       // offset of axis d in the face-flux buffer
+  double inv_half_dx[3];     // 2 / dx_d
+  int eos;                   // 0 ideal, 1 Taub-Matthews
+  double gamma_ad, alpha;    // Gamma, Gamma / (Gamma - 1)
+  int c2p;                   // 0 closed form, 1 iterative (resolved)
+  int max_iter;
+  int flux;                  // 0 LLF, 1 HLL
+  int bc[3][2];              // 0 periodic, 1 Dirichlet, 2 outflow
+  double ghost[3][2][5];     // Dirichlet ghost as (rho, u, P)
+  // basis tables (Gauss-Legendre nodal Lagrange basis on [-1, 1])
+  double w[kMaxN];           // quadrature weights
+  double Dhat[kMaxN * kMaxN];// Dhat[i*N + a] = w_a phi_i'(x_a) / w_i
+  double em[kMaxN], ep[kMaxN];   // phi_i(-1), phi_i(+1)
+  double lm[kMaxN], lp[kMaxN];   // phi_i(-1)/w_i, phi_i(+1)/w_i
+  double wsum;               // sum of tensor weights = 2^dim
+  unsigned long long* stats; // device counters [kStatCount]
+};
+
+}  // namespace dgsrhd

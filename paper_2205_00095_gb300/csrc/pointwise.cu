@@ -1,0 +1,80 @@
+// Point-wise kernels: prim -> cons and cons -> prim at every node (any dimension).
+#include "device_math.cuh"
+#include "launch.h"
+
+namespace dgsrhd {
+
+__global__ void __launch_bounds__(256) prim2cons_kernel(Params p, long long n,
+                                                         const double* __restrict__ W,
+                                                         double* __restrict__ U) {
+  for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < n;
+       k += (long long)gridDim.x * blockDim.x) {
+    double w[5], u[5];
+#pragma unroll
+    for (int v = 0; v < 5; ++v) w[v] = W[v * n + k];
+    prim_v_to_cons(p, w, u);
+#pragma unroll
+    for (int v = 0; v < 5; ++v) U[v * n + k] = u[v];
+  }
+}
+
+__global__ void __launch_bounds__(256) con2prim_kernel(Params p, long long n,
+                                                        const double* __restrict__ U,
+                                                        double* __restrict__ W,
+                                                        int* __restrict__ iters_out) {
+  __shared__ int shred[4];
+  if (threadIdx.x < 4) shred[threadIdx.x] = 0;
+  __syncthreads();
+  int it_sum = 0, it_max = 0, nc = 0, inv = 0;
+  for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < n;
+       k += (long long)gridDim.x * blockDim.x) {
+    double u[5];
+#pragma unroll
+    for (int v = 0; v < 5; ++v) u[v] = U[v * n + k];
+    Prim w;
+    int it;
+    const int st = con2prim(p, u, w, it);
+    W[0 * n + k] = w.rho;
+    W[1 * n + k] = w.v[0];
+    W[2 * n + k] = w.v[1];
+    W[3 * n + k] = w.v[2];
+    W[4 * n + k] = w.P;
+    if (iters_out) iters_out[k] = it;
+    it_sum += it;
+    it_max = max(it_max, it);
+    nc += (st == 2);
+    inv += (st == 1);
+  }
+  atomicAdd(&shred[0], it_sum);
+  atomicMax(&shred[1], it_max);
+  atomicAdd(&shred[2], nc);
+  atomicAdd(&shred[3], inv);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const int slot = blockIdx.x & 63;
+    if (shred[0]) atomicAdd(&p.stats[kStatItersTotal * 64 + slot], (unsigned long long)shred[0]);
+    if (shred[1]) atomicMax(&p.stats[kStatItersMax * 64 + slot], (unsigned long long)shred[1]);
+    if (shred[2]) atomicAdd(&p.stats[kStatNonConv * 64 + slot], (unsigned long long)shred[2]);
+    if (shred[3]) atomicAdd(&p.stats[kStatInvalid * 64 + slot], (unsigned long long)shred[3]);
+  }
+}
+
+static unsigned grid_for(long long n) {
+  long long b = (n + 255) / 256;
+  const long long cap = 152LL * 16;  // enough resident blocks to fill the GPU
+  return (unsigned)(b < 1 ? 1 : (b > cap ? cap : b));
+}
+
+cudaError_t launch_prim2cons(const Params& p, cudaStream_t s, long long n, const double* W,
+                             double* U) {
+  prim2cons_kernel<<<grid_for(n), 256, 0, s>>>(p, n, W, U);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_con2prim(const Params& p, cudaStream_t s, long long n, const double* U,
+                            double* W, int* iters) {
+  con2prim_kernel<<<grid_for(n), 256, 0, s>>>(p, n, U, W, iters);
+  return cudaGetLastError();
+}
+
+}  // namespace dgsrhd

@@ -1,0 +1,161 @@
+"""Thin torch-facing wrapper of the dgsrhd C ABI.
+
+torch supplies device memory and streams; every step of the method runs in the library's CUDA
+kernels.  State tensors are float64, contiguous, shape (5, n_elem, n_node) on the context's
+device (layout of include/dgsrhd.h)."""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+import torch
+
+from . import _lib
+from ._lib import check
+
+
+def _stream_handle(stream) -> int:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return int(stream.cuda_stream)
+
+
+def _dev_ptr(t: torch.Tensor, name: str, shape=None) -> int:
+    if not t.is_cuda or t.dtype != torch.float64 or not t.is_contiguous():
+        raise ValueError(f"{name} must be a contiguous float64 CUDA tensor")
+    if shape is not None and tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} has shape {tuple(t.shape)}, expected {tuple(shape)}")
+    return t.data_ptr()
+
+
+class Solver:
+    """One mesh and method choice (a dgsrhd context) bound to a CUDA stream."""
+
+    def __init__(self, spec: dict, stream: torch.cuda.Stream | None = None,
+                 device: torch.device | str | None = None):
+        self.lib = _lib.load()
+        self.spec = dict(spec)
+        self.device = torch.device(device or "cuda")
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        self.cfg = _lib.make_config(spec)
+        ctx = ctypes.c_void_p()
+        with torch.cuda.device(self.device):
+            check("dgsrhd_create", self.lib.dgsrhd_create(ctypes.byref(self.cfg),
+                                                          _stream_handle(self.stream),
+                                                          ctypes.byref(ctx)))
+        self.ctx = ctx
+        nv, ne, nn = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+        check("dgsrhd_state_shape", self.lib.dgsrhd_state_shape(self.ctx, ctypes.byref(nv),
+                                                                ctypes.byref(ne), ctypes.byref(nn)))
+        self.shape = (nv.value, ne.value, nn.value)
+        self.n_elem, self.n_node = ne.value, nn.value
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            self.lib.dgsrhd_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- helpers -----------------------------------------------------------------------
+    def empty(self) -> torch.Tensor:
+        return torch.empty(self.shape, dtype=torch.float64, device=self.device)
+
+    def node_coords(self) -> np.ndarray:
+        X = np.zeros((int(self.spec["dim"]), self.n_elem, self.n_node))
+        check("dgsrhd_node_coords", self.lib.dgsrhd_node_coords(self.ctx, X.ctypes.data))
+        return X
+
+    # -- the C ABI ---------------------------------------------------------------------
+    def prim2cons(self, W: torch.Tensor, out: torch.Tensor | None = None) -> torch.Tensor:
+        U = self.empty() if out is None else out
+        check("dgsrhd_prim2cons", self.lib.dgsrhd_prim2cons(
+            self.ctx, _dev_ptr(W, "W", self.shape), _dev_ptr(U, "U", self.shape)))
+        return U
+
+    def con2prim(self, U: torch.Tensor, with_iters: bool = False):
+        W = self.empty()
+        it = torch.empty(self.shape[1:], dtype=torch.int32, device=self.device) if with_iters else None
+        check("dgsrhd_con2prim", self.lib.dgsrhd_con2prim(
+            self.ctx, _dev_ptr(U, "U", self.shape), _dev_ptr(W, "W", self.shape),
+            it.data_ptr() if it is not None else None))
+        return (W, it) if with_iters else W
+
+    def rhs(self, U: torch.Tensor, out: torch.Tensor | None = None) -> torch.Tensor:
+        R = self.empty() if out is None else out
+        check("dgsrhd_rhs", self.lib.dgsrhd_rhs(self.ctx, _dev_ptr(U, "U", self.shape),
+                                                _dev_ptr(R, "R", self.shape)))
+        return R
+
+    def enforce(self, U: torch.Tensor, with_s: bool = False):
+        s = torch.empty(self.n_elem, dtype=torch.float64, device=self.device) if with_s else None
+        check("dgsrhd_enforce", self.lib.dgsrhd_enforce(
+            self.ctx, _dev_ptr(U, "U", self.shape), s.data_ptr() if s is not None else None))
+        return (U, s) if with_s else U
+
+    def step(self, U: torch.Tensor, dt: float, nsteps: int = 1) -> torch.Tensor:
+        check("dgsrhd_step", self.lib.dgsrhd_step(self.ctx, _dev_ptr(U, "U", self.shape),
+                                                  float(dt), int(nsteps)))
+        return U
+
+    def step_host(self, U_host: torch.Tensor, dt: float, nsteps: int = 1) -> torch.Tensor:
+        if U_host.is_cuda or U_host.dtype != torch.float64 or not U_host.is_contiguous() or \
+                tuple(U_host.shape) != tuple(self.shape):
+            raise ValueError("U_host must be a contiguous float64 CPU tensor of the state shape")
+        check("dgsrhd_step_host", self.lib.dgsrhd_step_host(self.ctx, U_host.data_ptr(),
+                                                            float(dt), int(nsteps)))
+        return U_host
+
+    def rhs_vjp(self, U: torch.Tensor, R_bar: torch.Tensor, out: torch.Tensor | None = None):
+        Ub = self.empty() if out is None else out
+        check("dgsrhd_rhs_vjp", self.lib.dgsrhd_rhs_vjp(
+            self.ctx, _dev_ptr(U, "U", self.shape), _dev_ptr(R_bar, "R_bar", self.shape),
+            _dev_ptr(Ub, "U_bar", self.shape)))
+        return Ub
+
+    def enforce_vjp(self, s: torch.Tensor, Ut_bar: torch.Tensor, out: torch.Tensor | None = None):
+        Ub = self.empty() if out is None else out
+        if not s.is_cuda or s.dtype != torch.float64 or s.numel() != self.n_elem:
+            raise ValueError("s must be a float64 CUDA tensor with one factor per element")
+        check("dgsrhd_enforce_vjp", self.lib.dgsrhd_enforce_vjp(
+            self.ctx, s.data_ptr(), _dev_ptr(Ut_bar, "Ut_bar", self.shape),
+            _dev_ptr(Ub, "U_bar", self.shape)))
+        return Ub
+
+    def cfl_dt(self, cfl: float | None = None) -> float:
+        dt = ctypes.c_double()
+        check("dgsrhd_cfl_dt", self.lib.dgsrhd_cfl_dt(self.ctx, float(cfl or self.spec.get("cfl", 0.2)),
+                                                      ctypes.byref(dt)))
+        return dt.value
+
+    def stats(self, reset: bool = False):
+        """(status, counters); status is the dgsrhd code the counters map to."""
+        st = _lib.dgsrhd_stats()
+        status = self.lib.dgsrhd_get_stats(self.ctx, ctypes.byref(st), int(reset))
+        if status in (_lib.DGSRHD_EINVAL, _lib.DGSRHD_ECUDA):
+            raise _lib.DGSRHDError("dgsrhd_get_stats", status)
+        return status, st.as_dict()
+
+    def kernel_launches(self) -> int:
+        return int(self.lib.dgsrhd_kernel_launches(self.ctx))
+
+    def set_profiling(self, enable: bool):
+        check("dgsrhd_set_profiling", self.lib.dgsrhd_set_profiling(self.ctx, int(bool(enable))))
+
+    def kernel_times(self, reset: bool = True) -> dict:
+        """{kind: (total ms, launches)} of the kernels timed while profiling was on."""
+        n = len(_lib.KERNEL_KINDS)
+        ms = (ctypes.c_double * n)()
+        cnt = (ctypes.c_int64 * n)()
+        check("dgsrhd_kernel_times", self.lib.dgsrhd_kernel_times(self.ctx, ms, cnt, int(reset)))
+        return {k: (ms[i], int(cnt[i])) for i, k in enumerate(_lib.KERNEL_KINDS)}
+
+    # -- convenience -------------------------------------------------------------------
+    def initial_state(self, W_host: np.ndarray) -> torch.Tensor:
+        """Upload a primitive field (5, n_elem, n_node) and convert it on the device."""
+        W = torch.from_numpy(np.ascontiguousarray(W_host, dtype=np.float64)).to(self.device)
+        return self.prim2cons(W)

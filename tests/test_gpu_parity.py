@@ -1,0 +1,284 @@
+"""Parity of the CUDA library (through the C ABI) with the FP64 oracle, element by element on the
+same seeded inputs.  Each side builds its own conserved state from the shared primitive fields
+of ``workloads``.  Tolerances: relative L-infinity (per call, normalised by the largest oracle
+magnitude) 1e-11 for one RHS or step of the FP64 path, 1e-9 after 100 steps on smooth problems;
+the closed-form ideal con2prim is ill-conditioned (Sec. 3.3) and gets its own bound."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def lib(gpu_lib):
+    return gpu_lib
+
+
+def solver(spec, **kw):
+    from paper_2205_00095_gb300 import Solver
+    return Solver(spec, **kw)
+
+
+def to_dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).cuda()
+
+
+def rel_inf(got, want):
+    return float(np.abs(got - want).max() / max(np.abs(want).max(), 1e-300))
+
+
+def gpu_state(s, spec):
+    X = s.node_coords()
+    return s.initial_state(wl.initial_primitive(spec, X))
+
+
+def oracle_state(spec):
+    X = oracle.node_coords(spec)
+    return oracle.prim2cons(spec, wl.initial_primitive(spec, X))
+
+
+# ---------------------------------------------------------------------------------------
+# point-wise
+# ---------------------------------------------------------------------------------------
+
+def test_node_coords_match(lib):
+    spec = wl.smooth_random(3, [3, 2, 4], 3)
+    s = solver(spec)
+    assert np.allclose(s.node_coords(), oracle.node_coords(spec), rtol=0, atol=1e-15)
+
+
+@pytest.mark.parametrize("eos", ["ideal", "tm"])
+def test_prim2cons(lib, eos):
+    spec = dict(dim=1, degree=0, n_elem=[3000], eos=eos, gamma_ad=5.0 / 3.0)
+    W = wl.random_primitive_states(3000, seed=41, gamma_max=30.0)[:, :, None]
+    s = solver(spec)
+    U = s.prim2cons(to_dev(W)).cpu().numpy()
+    Uo = oracle.prim2cons(spec, W)
+    lor2 = (1.0 / (1.0 - (W[1:4] ** 2).sum(0)))
+    scale = np.abs(Uo).max(axis=0)
+    assert np.all(np.abs(U - Uo) <= 1e-14 * lor2 * scale)
+
+
+@pytest.mark.parametrize("eos,c2p", [("ideal", "analytic"), ("ideal", "iterative"),
+                                     ("tm", "analytic"), ("tm", "iterative")])
+def test_con2prim(lib, eos, c2p):
+    n = 4000
+    spec = dict(dim=1, degree=0, n_elem=[n], eos=eos, gamma_ad=4.0 / 3.0, c2p=c2p)
+    W = wl.random_primitive_states(n, seed=42)[:, :, None]
+    Uo = oracle.prim2cons(spec, W)
+    s = solver(spec)
+    Wg, it = s.con2prim(to_dev(Uo), with_iters=True)
+    Wg = Wg.cpu().numpy()
+    Wo, ito, sto = oracle.con2prim(spec, Uo)
+    status, st = s.stats()
+    assert status == 0 and st["c2p_nonconverged"] == 0 and sto["c2p_nonconverged"] == 0
+    tol = 1e-7 if (eos, c2p) == ("ideal", "analytic") else 1e-12
+    # velocity relative to |v|, rho relative, P relative to its conditioning (tau + |S|)/P
+    dv = np.linalg.norm(Wg[1:4] - Wo[1:4], axis=0) / np.maximum(np.linalg.norm(Wo[1:4], axis=0), 1e-300)
+    assert dv.max() < tol
+    assert (np.abs(Wg[0] - Wo[0]) / Wo[0]).max() < tol
+    kappa = (Uo[4] + np.linalg.norm(Uo[1:4], axis=0)) / Wo[4]
+    assert (np.abs(Wg[4] - Wo[4]) / Wo[4] / kappa).max() < tol
+    if c2p == "iterative":
+        assert abs(float(it.float().mean()) - float(ito.mean())) < 0.05 * float(ito.mean()) + 0.1
+        assert st["c2p_iters_total"] == int(it.sum())
+
+
+def test_con2prim_invalid_and_cap(lib):
+    spec = dict(dim=1, degree=0, n_elem=[5], eos="tm", gamma_ad=5.0 / 3.0, c2p="iterative")
+    U = np.array([[-1.0, 1.0, 1.0, np.nan, 1.0],
+                  [0.0, 0.0, 2.0, 0.0, 0.0],
+                  [0.0, 0.0, 0.0, 0.0, 0.0],
+                  [0.0, 0.0, 0.0, 0.0, 0.0],
+                  [1.0, -0.5, 0.5, 1.0, 0.1]])[:, :, None]
+    s = solver(spec)
+    W = s.con2prim(to_dev(U)).cpu().numpy()
+    status, st = s.stats(reset=True)
+    assert st["c2p_invalid_input"] == 4 and np.all(np.isnan(W[:, :4]))
+    from paper_2205_00095_gb300 import _lib
+    assert status == _lib.DGSRHD_EBADSTATE
+    # an iteration cap of 3 forces non-convergence; the context stays usable
+    spec2 = dict(spec, n_elem=[50], c2p_max_iter=3)
+    W2 = wl.random_primitive_states(50, seed=5, gamma_max=50.0)[:, :, None]
+    s2 = solver(spec2)
+    s2.con2prim(s2.prim2cons(to_dev(W2)))
+    status, st = s2.stats()
+    assert status == _lib.DGSRHD_EC2P_NOCONV and st["c2p_nonconverged"] > 0
+    assert st["c2p_iters_max"] == 3
+
+
+# ---------------------------------------------------------------------------------------
+# right-hand side
+# ---------------------------------------------------------------------------------------
+
+RHS_CASES = [
+    # dim, n_elem (several blocks and a ragged tail), degree, eos, flux, bc
+    (1, [301], 0, "ideal", "llf", None),
+    (1, [257], 1, "ideal", "hll", [("dirichlet", "outflow")]),
+    (1, [100], 4, "tm", "llf", None),
+    (2, [19, 23], 0, "tm", "hll", None),
+    (2, [21, 17], 1, "ideal", "llf", [("outflow", "dirichlet"), ("periodic", "periodic")]),
+    (2, [18, 13], 2, "tm", "llf", None),
+    (2, [17, 19], 3, "ideal", "hll", None),
+    (2, [17, 19], 3, "tm", "hll", [("periodic", "periodic"), ("dirichlet", "outflow")]),
+    (2, [11, 9], 4, "ideal", "llf", None),
+    (3, [7, 6, 5], 1, "ideal", "hll", None),
+    (3, [5, 6, 7], 2, "tm", "llf", [("periodic", "periodic"), ("outflow", "outflow"), ("periodic", "periodic")]),
+    (3, [6, 5, 7], 3, "tm", "hll", None),
+    (3, [4, 3, 5], 4, "ideal", "llf", None),
+]
+
+
+@pytest.mark.parametrize("dim,n,degree,eos,flux,bc", RHS_CASES)
+@pytest.mark.parametrize("c2p", ["iterative", "analytic"])
+def test_rhs(lib, dim, n, degree, eos, flux, bc, c2p):
+    spec = wl.smooth_random(dim, n, degree, eos=eos, flux=flux, c2p=c2p, seed=dim * 10 + degree,
+                            bc=bc)
+    s = solver(spec)
+    U = gpu_state(s, spec)
+    R = s.rhs(U).cpu().numpy()
+    Ro, sto = oracle.rhs(spec, oracle_state(spec))
+    tol = 1e-11 if (eos, c2p) != ("ideal", "analytic") else 1e-10
+    assert rel_inf(R, Ro) < tol
+    status, st = s.stats()
+    assert status == 0 and st["c2p_invalid_input"] == 0
+    assert st["face_guard_hits"] == sto["face_guard_hits"]
+
+
+# ---------------------------------------------------------------------------------------
+# physicality operator
+# ---------------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("dim,degree,n", [(1, 3, [997]), (2, 2, [31, 29]), (2, 3, [40, 25]),
+                                          (3, 3, [9, 8, 7]), (2, 4, [19, 21])])
+def test_enforce(lib, dim, degree, n):
+    spec = dict(dim=dim, degree=degree, n_elem=n, eos="ideal", gamma_ad=5.0 / 3.0)
+    E, Nn = wl.shape(spec)
+    U = wl.random_conserved_cells(E, Nn, seed=7 + dim + degree)
+    s = solver(spec)
+    Ug, sg = s.enforce(to_dev(U), with_s=True)
+    Uo, so, sto = oracle.enforce(spec, U)
+    assert rel_inf(Ug.cpu().numpy(), Uo) < 1e-13
+    assert np.allclose(sg.cpu().numpy(), so, rtol=1e-12, atol=1e-15)
+    status, st = s.stats()
+    assert st["enforced_cells"] == sto["enforced_cells"] > 0
+    assert st["mean_inadmissible_cells"] == sto["mean_inadmissible_cells"] > 0
+
+
+# ---------------------------------------------------------------------------------------
+# time steps
+# ---------------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("spec_fn,c2p", [
+    (lambda c2p: wl.advected_wave(n=16, degree=3, c2p=c2p), "analytic"),
+    (lambda c2p: wl.advected_wave(n=16, degree=3, c2p=c2p), "iterative"),
+    (lambda c2p: wl.kh2d(nx=12, ny=24, degree=3, c2p=c2p), "iterative"),
+    (lambda c2p: wl.kh2d(nx=12, ny=24, degree=3, c2p=c2p), "analytic"),
+    (lambda c2p: wl.kh3d(n=6, degree=2, c2p=c2p), "iterative"),
+])
+def test_step_one_and_hundred(lib, spec_fn, c2p):
+    spec = spec_fn(c2p)
+    s = solver(spec, stream=torch.cuda.Stream())
+    dt = s.cfl_dt(0.2)
+    U = gpu_state(s, spec)
+    Uo = oracle_state(spec)
+    s.step(U, dt, 1)
+    Uo1, _ = oracle.step(spec, Uo, dt, 1)
+    torch.cuda.synchronize()
+    assert rel_inf(U.cpu().numpy(), Uo1) < 1e-11
+    s.step(U, dt, 99)
+    Uo100, sto = oracle.step(spec, Uo1, dt, 99)
+    torch.cuda.synchronize()
+    assert rel_inf(U.cpu().numpy(), Uo100) < 1e-9
+    status, st = s.stats()
+    assert status == 0 and st["enforced_cells"] == sto["enforced_cells"]
+
+
+def test_blast_wave_full_run(lib):
+    """The 1D blast wave (128 elements, p = 1, SSPRK2, 768 steps): the operator is active and
+    the solutions agree to the conditioning of the shock fronts."""
+    spec = wl.blast_wave()
+    s = solver(spec, stream=torch.cuda.Stream())
+    U = gpu_state(s, spec)
+    s.enforce(U)
+    Uo, _, _ = oracle.enforce(spec, oracle_state(spec))
+    dt = s.cfl_dt(0.2)
+    nsteps = int(round(0.4 / dt))
+    s.step(U, 0.4 / nsteps, nsteps)
+    Uo, sto = oracle.step(spec, Uo, 0.4 / nsteps, nsteps)
+    torch.cuda.synchronize()
+    status, st = s.stats()
+    assert status == 0
+    assert st["enforced_cells"] > 0 and abs(st["enforced_cells"] - sto["enforced_cells"]) <= 2
+    assert rel_inf(U.cpu().numpy(), Uo) < 1e-6
+
+
+def test_graph_replay_matches_direct_launches(lib):
+    spec = wl.kh2d(nx=8, ny=16, degree=3)
+    a = solver(spec, stream=torch.cuda.Stream())
+    U1 = gpu_state(a, spec)
+    U2 = U1.clone()
+    dt = a.cfl_dt(0.2)
+    a.step(U1, dt, 5)                         # captured graph
+    from paper_2205_00095_gb300 import Solver
+    b = Solver(spec)                          # legacy stream: direct launches
+    b.lib.dgsrhd_set_stream(b.ctx, None)
+    b.step(U2, dt, 5)
+    torch.cuda.synchronize()
+    assert torch.equal(U1, U2)
+
+
+def test_step_host_matches_device_step(lib):
+    spec = wl.advected_wave(n=8, degree=2)
+    s = solver(spec, stream=torch.cuda.Stream())
+    U = gpu_state(s, spec)
+    Uh = U.cpu().pin_memory()
+    dt = s.cfl_dt(0.2)
+    s.step(U, dt, 3)
+    s.step_host(Uh, dt, 3)
+    torch.cuda.synchronize()
+    assert torch.equal(U.cpu(), Uh)
+
+
+def test_periodic_conservation_at_scale(lib):
+    """On the 512^2 p = 3 advected wave (the benchmark workload) one SSPRK3 step conserves
+    sum_e sum_i w_i U_i to round-off, stays admissible and finite."""
+    spec = wl.advected_wave(n=512, degree=3)
+    s = solver(spec, stream=torch.cuda.Stream())
+    U = gpu_state(s, spec)
+    w = np.polynomial.legendre.leggauss(4)[1]
+    w2 = torch.from_numpy(np.multiply.outer(w, w).ravel()).cuda()
+    tot0 = (U * w2).sum(dim=(1, 2))
+    s.step(U, s.cfl_dt(0.2), 1)
+    tot1 = (U * w2).sum(dim=(1, 2))
+    torch.cuda.synchronize()
+    assert torch.isfinite(U).all()
+    assert float(((tot1 - tot0).abs() / (U.abs() * w2).sum(dim=(1, 2)).clamp_min(1e-300)).max()) < 1e-13
+
+
+def test_full_size_sampled_elements(lib):
+    """The 512^2 p = 3 advected wave after one SSPRK3 step, checked on sampled elements: the
+    oracle steps a 7 x 7 element patch around each sample (three stages reach three elements),
+    built from the same workload field, and its centre element must match."""
+    spec = wl.advected_wave(n=512, degree=3)
+    s = solver(spec, stream=torch.cuda.Stream())
+    U = gpu_state(s, spec)
+    dt = s.cfl_dt(0.2)
+    s.step(U, dt, 1)
+    Ug = U.cpu().numpy()
+    rng = np.random.default_rng(3)
+    h = 1.0 / 512
+    for _ in range(12):
+        ex, ey = (int(v) for v in rng.integers(0, 512, 2))
+        patch = dict(spec, n_elem=[7, 7], lo=[(ex - 3) * h, (ey - 3) * h],
+                     hi=[(ex + 4) * h, (ey + 4) * h], bc=[("outflow", "outflow")] * 2)
+        Xp = oracle.node_coords(patch)
+        Up = oracle.prim2cons(patch, wl.advected_wave_ic(patch, Xp))
+        Up1, _ = oracle.step(patch, Up, dt, 1)
+        got = Ug[:, ex + 512 * ey, :]
+        want = Up1[:, 3 + 7 * 3, :]
+        assert np.abs(got - want).max() < 1e-11 * np.abs(want).max()

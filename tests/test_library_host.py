@@ -1,0 +1,70 @@
+"""CPU tests of the library boundary: it builds, loads, exports every symbol include/dgsrhd.h
+declares, and rejects invalid configurations before touching the GPU."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_2205_00095_gb300 import _lib, build
+
+HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include",
+                      "dgsrhd.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build.build()
+    return _lib.load()
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(dgsrhd_[a-z0-9_]+)\s*\(", text)))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ("dgsrhd_create", "dgsrhd_con2prim", "dgsrhd_rhs", "dgsrhd_enforce",
+                     "dgsrhd_step", "dgsrhd_rhs_vjp"):
+        assert required in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+    assert set(_lib.exported_symbols()) <= set(declared_functions())
+
+
+def test_status_strings(lib):
+    for code in range(7):
+        assert lib.dgsrhd_status_string(code).decode()
+
+
+def base_spec():
+    return dict(dim=2, degree=3, n_elem=[4, 4], eos="ideal", gamma_ad=5.0 / 3.0, rk_stages=3)
+
+
+@pytest.mark.parametrize("bad", [
+    dict(dim=4), dict(dim=0), dict(degree=5), dict(degree=-1), dict(n_elem=[0, 4]),
+    dict(gamma_ad=1.0), dict(rk_stages=4), dict(rk_stages=0), dict(flux=7), dict(eos=3),
+    dict(bc=[("periodic", "outflow"), ("periodic", "periodic")]),
+    dict(bc=[("dirichlet", "outflow"), ("periodic", "periodic")],
+         bc_state=[[(1.0, 1.2, 0.0, 0.0, 1.0), (1.0, 0.0, 0.0, 0.0, 1.0)]] * 2),
+    dict(lo=[1.0, 0.0], hi=[0.0, 1.0]),
+])
+def test_invalid_configuration_rejected_on_host(lib, bad):
+    spec = base_spec()
+    spec.update(bad)
+    cfg = _lib.make_config(spec)
+    ctx = ctypes.c_void_p(1)
+    assert lib.dgsrhd_create(ctypes.byref(cfg), None, ctypes.byref(ctx)) == _lib.DGSRHD_EINVAL
+    assert not ctx.value
+
+
+def test_null_arguments_rejected(lib):
+    assert lib.dgsrhd_create(None, None, None) == _lib.DGSRHD_EINVAL
+    assert lib.dgsrhd_rhs(None, None, None) == _lib.DGSRHD_EINVAL
+    assert lib.dgsrhd_step(None, None, 0.1, 1) == _lib.DGSRHD_EINVAL
+    lib.dgsrhd_destroy(None)
