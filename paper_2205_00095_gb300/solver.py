@@ -2,7 +2,12 @@
 
 torch supplies device memory and streams; every step of the method runs in the library's CUDA
 kernels.  State tensors are float64, contiguous, shape (5, n_elem, n_node) on the context's
-device (layout of include/dgsrhd.h)."""
+device (layout of include/dgsrhd.h).
+
+Stream contract: every call is ordered on ``Solver.stream``.  Outputs are allocated on that
+stream; inputs must be ready on it (create them under ``torch.cuda.stream(solver.stream)`` or
+synchronise first), and results must be synchronised (``solver.stream.synchronize()``) before
+they are read on another stream or on the host."""
 from __future__ import annotations
 
 import ctypes
@@ -63,7 +68,8 @@ class Solver:
 
     # -- helpers -----------------------------------------------------------------------
     def empty(self) -> torch.Tensor:
-        return torch.empty(self.shape, dtype=torch.float64, device=self.device)
+        with torch.cuda.stream(self.stream):
+            return torch.empty(self.shape, dtype=torch.float64, device=self.device)
 
     def node_coords(self) -> np.ndarray:
         X = np.zeros((int(self.spec["dim"]), self.n_elem, self.n_node))
@@ -79,7 +85,8 @@ class Solver:
 
     def con2prim(self, U: torch.Tensor, with_iters: bool = False):
         W = self.empty()
-        it = torch.empty(self.shape[1:], dtype=torch.int32, device=self.device) if with_iters else None
+        with torch.cuda.stream(self.stream):
+            it = torch.empty(self.shape[1:], dtype=torch.int32, device=self.device) if with_iters else None
         check("dgsrhd_con2prim", self.lib.dgsrhd_con2prim(
             self.ctx, _dev_ptr(U, "U", self.shape), _dev_ptr(W, "W", self.shape),
             it.data_ptr() if it is not None else None))
@@ -92,7 +99,8 @@ class Solver:
         return R
 
     def enforce(self, U: torch.Tensor, with_s: bool = False):
-        s = torch.empty(self.n_elem, dtype=torch.float64, device=self.device) if with_s else None
+        with torch.cuda.stream(self.stream):
+            s = torch.empty(self.n_elem, dtype=torch.float64, device=self.device) if with_s else None
         check("dgsrhd_enforce", self.lib.dgsrhd_enforce(
             self.ctx, _dev_ptr(U, "U", self.shape), s.data_ptr() if s is not None else None))
         return (U, s) if with_s else U
@@ -157,5 +165,9 @@ class Solver:
     # -- convenience -------------------------------------------------------------------
     def initial_state(self, W_host: np.ndarray) -> torch.Tensor:
         """Upload a primitive field (5, n_elem, n_node) and convert it on the device."""
-        W = torch.from_numpy(np.ascontiguousarray(W_host, dtype=np.float64)).to(self.device)
+        with torch.cuda.stream(self.stream):
+            W = torch.from_numpy(np.ascontiguousarray(W_host, dtype=np.float64)).to(self.device)
         return self.prim2cons(W)
+
+    def synchronize(self):
+        self.stream.synchronize()

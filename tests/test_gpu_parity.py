@@ -24,7 +24,9 @@ def solver(spec, **kw):
 
 
 def to_dev(a):
-    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).cuda()
+    t = torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).cuda()
+    torch.cuda.synchronize()
+    return t
 
 
 def rel_inf(got, want):
@@ -33,7 +35,9 @@ def rel_inf(got, want):
 
 def gpu_state(s, spec):
     X = s.node_coords()
-    return s.initial_state(wl.initial_primitive(spec, X))
+    U = s.initial_state(wl.initial_primitive(spec, X))
+    s.synchronize()
+    return U
 
 
 def oracle_state(spec):
@@ -265,10 +269,12 @@ def test_periodic_conservation_at_scale(lib):
     spec = wl.advected_wave(n=512, degree=3)
     s = solver(spec, stream=torch.cuda.Stream())
     U = gpu_state(s, spec)
+    s.synchronize()
     w = np.polynomial.legendre.leggauss(4)[1]
     w2 = torch.from_numpy(np.multiply.outer(w, w).ravel()).cuda()
     tot0 = (U * w2).sum(dim=(1, 2))
     s.step(U, s.cfl_dt(0.2), 1)
+    s.synchronize()
     tot1 = (U * w2).sum(dim=(1, 2))
     torch.cuda.synchronize()
     assert torch.isfinite(U).all()
@@ -284,6 +290,7 @@ def test_full_size_sampled_elements(lib):
     U = gpu_state(s, spec)
     dt = s.cfl_dt(0.2)
     s.step(U, dt, 1)
+    s.synchronize()
     Ug = U.cpu().numpy()
     rng = np.random.default_rng(3)
     h = 1.0 / 512
