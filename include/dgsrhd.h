@@ -177,6 +177,34 @@ int64_t dgsrhd_kernel_launches(const dgsrhd_ctx* ctx);
 int32_t dgsrhd_set_profiling(dgsrhd_ctx* ctx, int32_t enable);
 int32_t dgsrhd_kernel_times(dgsrhd_ctx* ctx, double* ms, int64_t* counts, int32_t reset);
 
+/* dgsrhd_rhs without any device allocation, for callers that cannot allocate GPU memory
+ * themselves and cannot let a library do it either: code running under a host framework that
+ * owns all device memory, code that must not trigger the implicit synchronisation or failure of
+ * cudaMalloc (inside another library's callback, or with device memory fully reserved), or
+ * deployments that must fix their device footprint at load time.  The paper has no
+ * counterpart; this is a deployment variant of the right-hand side.
+ *
+ * Computes R = dU/dt exactly as dgsrhd_rhs does for the configuration `cfg`, on `stream`
+ * (a cudaStream_t, NULL = legacy default stream), with no context.  U (input) and R (output)
+ * are caller-owned device arrays in the state layout above; they must not alias.  The scratch
+ * is a fixed 64 MiB array in device global memory (8,388,608 doubles) that every GPU loading
+ * the library holds until the process exits.  A configuration needs
+ *   5 E Nn + 10 dim E Nt + 5 Nt sum_d nface_d + 512 doubles,
+ * with Nn = (p+1)^dim, Nt = (p+1)^(dim-1) and nface_d = E (periodic axis) or E + E/n_d; a
+ * larger mesh, an invalid configuration or a NULL/aliased array returns DGSRHD_EINVAL before
+ * any GPU work.  No call allocates: no cudaMalloc, no cudaFree, no allocating library routine.
+ *
+ * The first call on each device (with that device current) looks up the array's device address
+ * and caches it; make that first call before any stream capture.  All calls share the one array
+ * and leave their intermediate results in it, so calls whose GPU work can overlap (different
+ * streams, or several host threads) race and must be serialised by the caller.
+ *
+ * stats_out (nullable, HOST): when given, the call synchronises `stream`, fills the con2prim and
+ * face-guard counters of this call and returns DGSRHD_EBADSTATE / DGSRHD_EC2P_NOCONV as
+ * dgsrhd_get_stats would; when NULL the call returns as soon as the kernels are queued. */
+int32_t dgsrhd_rhs_noalloc(const dgsrhd_config* cfg, void* stream, const double* U, double* R,
+                           dgsrhd_stats* stats_out);
+
 /* Human-readable name of a status code. */
 const char* dgsrhd_status_string(int32_t status);
 

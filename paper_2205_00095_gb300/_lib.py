@@ -94,6 +94,7 @@ def load() -> ctypes.CDLL:
         "dgsrhd_set_profiling": (i32, [vp, i32]),
         "dgsrhd_kernel_times": (i32, [vp, P(d), P(i64), i32]),
         "dgsrhd_status_string": (ctypes.c_char_p, [i32]),
+        "dgsrhd_rhs_noalloc": (i32, [P(dgsrhd_config), vp, vp, vp, P(dgsrhd_stats)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -111,6 +112,7 @@ def exported_symbols():
         "dgsrhd_enforce", "dgsrhd_step", "dgsrhd_step_host", "dgsrhd_rhs_vjp",
         "dgsrhd_enforce_vjp", "dgsrhd_cfl_dt", "dgsrhd_get_stats", "dgsrhd_kernel_launches",
         "dgsrhd_set_profiling", "dgsrhd_kernel_times", "dgsrhd_status_string",
+        "dgsrhd_rhs_noalloc",
     ]
 
 

@@ -593,3 +593,69 @@ const char* dgsrhd_status_string(int32_t s) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------------------
+// Launch parameters straight from a configuration, for callers without a context (the
+// static-scratch right-hand side).  Same tables and layout as dgsrhd_create.
+// ---------------------------------------------------------------------------------------
+namespace dgsrhd {
+
+bool params_from_config(const dgsrhd_config* cfg, Params* out, long long* n_trace,
+                        long long* n_face_flux) {
+  if (!valid_config(cfg) || !out) return false;
+  Params p;
+  memset(&p, 0, sizeof p);
+  const int dim = cfg->dim, N = cfg->degree + 1;
+  p.dim = dim;
+  p.N = N;
+  p.Nn = 1;
+  p.Nt = 1;
+  for (int d = 0; d < dim; ++d) p.Nn *= N;
+  for (int d = 0; d < dim - 1; ++d) p.Nt *= N;
+  long long E = 1;
+  for (int d = 0; d < 3; ++d) {
+    p.n[d] = d < dim ? cfg->n_elem[d] : 1;
+    p.stride[d] = E;
+    E *= p.n[d];
+    const double dx = d < dim ? (cfg->hi[d] - cfg->lo[d]) / (double)p.n[d] : 1.0;
+    p.inv_half_dx[d] = 2.0 / dx;
+  }
+  p.E = E;
+  long long off = 0;
+  for (int d = 0; d < 3; ++d) {
+    if (d < dim) {
+      p.nface[d] = E + (cfg->bc[d][0] == DGSRHD_BC_PERIODIC ? 0 : E / p.n[d]);
+      p.fs_off[d] = off;
+      off += 5 * p.nface[d] * p.Nt;
+    }
+    for (int s = 0; s < 2; ++s) {
+      p.bc[d][s] = d < dim ? cfg->bc[d][s] : 0;
+      const double* b = cfg->bc_state[d][s];
+      const double v2 = b[1] * b[1] + b[2] * b[2] + b[3] * b[3];
+      const double lor = (v2 < 1.0) ? 1.0 / sqrt(1.0 - v2) : 1.0;
+      p.ghost[d][s][0] = b[0];
+      for (int k = 1; k < 4; ++k) p.ghost[d][s][k] = lor * b[k];
+      p.ghost[d][s][4] = b[4];
+    }
+  }
+  p.eos = cfg->eos;
+  p.gamma_ad = cfg->gamma_ad;
+  p.alpha = cfg->eos == DGSRHD_EOS_IDEAL ? cfg->gamma_ad / (cfg->gamma_ad - 1.0) : 0.0;
+  p.c2p = cfg->c2p == DGSRHD_C2P_DEFAULT ? (cfg->eos == DGSRHD_EOS_IDEAL ? 0 : 1) : cfg->c2p;
+  p.max_iter = cfg->c2p_max_iter > 0 ? cfg->c2p_max_iter : (cfg->eos == DGSRHD_EOS_IDEAL ? 30 : 100);
+  p.flux = cfg->flux;
+  double x[kMaxN];
+  gauss_legendre(N, x, p.w);
+  basis_tables(N, x, p.w, p.Dhat, p.em, p.ep);
+  for (int i = 0; i < N; ++i) {
+    p.lm[i] = p.em[i] / p.w[i];
+    p.lp[i] = p.ep[i] / p.w[i];
+  }
+  p.wsum = (double)(1 << dim);
+  *out = p;
+  if (n_trace) *n_trace = 2LL * dim * 5 * E * p.Nt;
+  if (n_face_flux) *n_face_flux = off;
+  return true;
+}
+
+}  // namespace dgsrhd

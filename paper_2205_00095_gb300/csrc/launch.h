@@ -41,3 +41,12 @@ cudaError_t launch_con2prim(const Params& p, cudaStream_t s, long long n, const 
                             double* W, int* iters);
 
 }  // namespace dgsrhd
+
+struct dgsrhd_config;
+
+namespace dgsrhd {
+// Launch parameters of a configuration without a context; false for an invalid one.
+// n_trace / n_face_flux receive the sizes (in doubles) of the trace and face-flux buffers.
+bool params_from_config(const ::dgsrhd_config* cfg, Params* out, long long* n_trace,
+                        long long* n_face_flux);
+}  // namespace dgsrhd
