@@ -35,13 +35,13 @@ UNIT = "DOF-updates/s"
 FP64_PEAK_TFLOPS = 1.25  # GB300 nominal dense FP64 (no FP64 figure in MEASURED_PEAKS.json)
 
 
-def make_spec(name: str) -> dict:
+def make_spec(name: str, c2p: str | None = None) -> dict:
     if name == "advected_wave":
-        return wl.advected_wave(n=512, degree=3, c2p="analytic")
+        return wl.advected_wave(n=512, degree=3, c2p=c2p or "analytic")
     if name == "kh2d":
-        return wl.kh2d(nx=256, ny=512, degree=3)
+        return wl.kh2d(nx=256, ny=512, degree=3, c2p=c2p or "default")
     if name == "kh3d":
-        return wl.kh3d(n=128, degree=3)
+        return wl.kh3d(n=128, degree=3, c2p=c2p or "default")
     raise SystemExit(f"unknown workload {name}")
 
 
@@ -131,6 +131,23 @@ def volume_kernel_flops_per_node(spec: dict) -> float:
     return c2p + flux + volume + traces
 
 
+def measured_traffic(kernel: str, workload_name: str):
+    """DRAM bytes (read + write) per launch of `kernel` from the committed ncu capture of this
+    workload, or None when there is none or the kernel sources changed since it was taken."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "dram_traffic_advected_wave_512x512_p3.json")
+    if workload_name != "advected_wave" or not os.path.exists(path):
+        return None
+    d = json.load(open(path))
+    h = hashlib.sha1()
+    for f in d["source_files"]:
+        h.update(open(os.path.join(ROOT, f), "rb").read())
+    if h.hexdigest() != d["source_sha1"] or kernel not in d["kernels"]:
+        return None
+    k = d["kernels"][kernel]
+    return k["dram_bytes_read"] + k["dram_bytes_write"]
+
+
 def load_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -177,7 +194,7 @@ def run_oracle(spec: dict, steps: int, warmup: int):
 def reference_arm(args, rank, world):
     if rank != 0:
         return
-    spec = make_spec(args.workload)
+    spec = make_spec(args.workload, args.c2p)
     sample = oracle_sample_spec(spec, target_s=min(20.0, 60.0 / max(1, args.steps + args.warmup)))
     value, t = run_oracle(sample, args.steps, args.warmup)
     desc = (f"{args.steps} oracle SSPRK steps on {'x'.join(map(str, sample['n_elem']))} elements of the "
@@ -204,7 +221,7 @@ def ours(args, rank, world, local_rank):
     build.build()
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
-    spec = make_spec(args.workload)
+    spec = make_spec(args.workload, args.c2p)
     stream = torch.cuda.Stream(device=dev)
     s = Solver(spec, stream=stream, device=dev)
     X = s.node_coords()
@@ -289,7 +306,8 @@ def ours(args, rank, world, local_rank):
         achieved = flops / avg_s / 1e12
         roofline = {"kernel": "volume_kernel", "bound": "alu", "achieved": achieved,
                     "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
-                    "traffic": None, "peak_source": "GB300 nominal dense FP64 1.25 TFLOP/s",
+                    "traffic": measured_traffic("volume_kernel", args.workload),
+                    "peak_source": "GB300 nominal dense FP64 1.25 TFLOP/s (DFMA probe measured 1.256)",
                     "algorithmic_flops_per_node": volume_kernel_flops_per_node(spec),
                     "avg_launch_ms": avg_s * 1e3}
     else:
@@ -325,6 +343,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="advected_wave", choices=["advected_wave", "kh2d", "kh3d"])
+    ap.add_argument("--c2p", default=None, choices=["analytic", "iterative", "default"],
+                    help="con2prim solver (default: the workload's)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end timing")
     args = ap.parse_args()

@@ -202,6 +202,8 @@ int or_prim2cons(const or_config *c, int64_t n, const double *W, double *U) {
   return 0;
 }
 
+static int admissible_parts(double D, double S2, double tau);
+
 /* ------------------------------------------------------------------------ */
 /* cons -> prim (Sec. 3)                                                     */
 /* ------------------------------------------------------------------------ */
@@ -378,8 +380,7 @@ static int con2prim_point(const or_config *c, const double U[5], double W[5], in
   double E = tau + D;
   double S2 = Sx * Sx + Sy * Sy + Sz * Sz;
   *iters = 0;
-  if (!(D > 0.0) || !(tau - S2 / (D + sqrt(D * D + S2)) > 0.0) || !isfinite(S2) ||
-      !isfinite(tau)) {
+  if (!admissible_parts(D, S2, tau) || !isfinite(S2) || !isfinite(tau)) {
     for (int v = 0; v < 5; ++v) W[v] = NAN;
     return 1;
   }
@@ -782,17 +783,16 @@ int or_rhs(const or_config *c, const double *U, double *R, or_stats *st) {
 /* ------------------------------------------------------------------------ */
 
 /* Admissible set (Eq. physicality): D > 0 and q = E - sqrt(D^2 + |S|^2) > 0.
- * Readings: the sign under the root is the one of
- * Eq. smoothed_state_physicality; q is evaluated in the stored variables as
- * q = tau - |S|^2 / (D + sqrt(D^2 + |S|^2)), the same number without the
- * cancellation of D against the root (cold states have tau << D). */
-static double q_of(const double U[5]) {
-  double D = U[0], S2 = U[1] * U[1] + U[2] * U[2] + U[3] * U[3];
-  return U[4] - S2 / (D + sqrt(D * D + S2));
+ * Readings: the sign under the root is the one of Eq. smoothed_state_physicality.  With
+ * E = tau + D and D > 0, q > 0 holds exactly when E > 0 and E^2 > D^2 + |S|^2, i.e. when
+ * tau > 0 and tau (tau + 2 D) > |S|^2; the test is made in that form (stored variables, no
+ * cancellation of D against the root for cold states with tau << D, no root). */
+static int admissible_parts(double D, double S2, double tau) {
+  return D > 0.0 && tau > 0.0 && tau * (tau + 2.0 * D) > S2;
 }
 
 static int admissible(const double U[5]) {
-  return U[0] > 0.0 && q_of(U) > 0.0;
+  return admissible_parts(U[0], U[1] * U[1] + U[2] * U[2] + U[3] * U[3], U[4]);
 }
 
 /* Largest s in [0, 1] with s X + (1 - s) Xbar >= 0, for Xbar > 0. */

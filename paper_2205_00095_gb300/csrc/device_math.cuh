@@ -40,38 +40,6 @@ __device__ __forceinline__ EosEval eos_eval(const Params& p, double rho, double 
   return r;
 }
 
-// Face / node state in the interpolated primitive (rho, u, P), u = gamma v.
-struct ConsFlux {
-  double U[5];
-  double v[3];
-  double P;
-  double lor;  // Lorentz factor
-  double cs2;
-};
-
-// prim (rho, u, P) -> conserved state, 3-velocity and sound speed.
-// tau = gamma^2 rho h - P - D  written as  D u^2/(gamma + 1) + gamma^2 rho (h - 1) - P.
-__device__ __forceinline__ void prim_u_to_cons(const Params& p, const double Wu[5], ConsFlux& c) {
-  const double rho = Wu[0], P = Wu[4];
-  const double u2 = Wu[1] * Wu[1] + Wu[2] * Wu[2] + Wu[3] * Wu[3];
-  const double lor = sqrt(1.0 + u2);
-  const double ilor = 1.0 / lor;
-  const EosEval e = eos_eval(p, rho, P);
-  const double D = lor * rho;
-  const double rhoh_lor = rho * (1.0 + e.hm1) * lor;  // S = rho h gamma u
-  c.U[0] = D;
-  c.U[1] = rhoh_lor * Wu[1];
-  c.U[2] = rhoh_lor * Wu[2];
-  c.U[3] = rhoh_lor * Wu[3];
-  c.U[4] = D * u2 / (lor + 1.0) + lor * lor * rho * e.hm1 - P;
-  c.v[0] = Wu[1] * ilor;
-  c.v[1] = Wu[2] * ilor;
-  c.v[2] = Wu[3] * ilor;
-  c.P = P;
-  c.lor = lor;
-  c.cs2 = e.cs2;
-}
-
 // prim (rho, v, P) -> cons; same arithmetic with gamma from v.
 __device__ __forceinline__ void prim_v_to_cons(const Params& p, const double W[5], double U[5]) {
   const double v2 = W[1] * W[1] + W[2] * W[2] + W[3] * W[3];
@@ -87,16 +55,31 @@ __device__ __forceinline__ void prim_v_to_cons(const Params& p, const double W[5
 }
 
 // ---------------------------------------------------------------------------------------
-// Admissible set (Eq. physicality): D > 0 and q = E - sqrt(D^2 + |S|^2) > 0, evaluated as
-// q = tau - |S|^2 / (D + sqrt(D^2 + |S|^2)) (no cancellation of D against the root).
+// Admissible set (Eq. physicality): D > 0 and q = E - sqrt(D^2 + |S|^2) > 0.  With E = tau + D
+// and D > 0 this holds exactly when tau > 0 and tau (tau + 2 D) > |S|^2: no root, no division,
+// no cancellation of D for cold states.
 // ---------------------------------------------------------------------------------------
-__device__ __forceinline__ double q_func(double D, double S2, double tau) {
-  return tau - S2 / (D + sqrt(fma(D, D, S2)));
+__device__ __forceinline__ bool admissible_parts(double D, double S2, double tau) {
+  return D > 0.0 && tau > 0.0 && tau * (tau + 2.0 * D) > S2;
 }
 
 __device__ __forceinline__ bool admissible(const double U[5]) {
-  const double S2 = U[1] * U[1] + U[2] * U[2] + U[3] * U[3];
-  return U[0] > 0.0 && q_func(U[0], S2, U[4]) > 0.0;
+  return admissible_parts(U[0], U[1] * U[1] + U[2] * U[2] + U[3] * U[3], U[4]);
+}
+
+// Cube root: FP32 reciprocal cube root as the seed, two division-free Newton steps in FP64 on
+// r = a^(-1/3) (r <- r + r (1 - a r^3) / 3, quadratic convergence from ~1e-7), then a r^2.
+// Arguments outside the FP32-normal range use the library cube root.
+__device__ __forceinline__ double cbrt_newton(double a) {
+  const double aa = fabs(a);
+  if (!(aa > 1e-30 && aa < 1e30)) return cbrt(a);
+  double r = (double)rcbrtf((float)aa);
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {
+    const double e = fma(-aa * r, r * r, 1.0);
+    r = fma(r * (1.0 / 3.0), e, r);
+  }
+  return copysign(aa * r * r, a);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -124,7 +107,7 @@ __device__ __forceinline__ double beta_ideal_closed_form(double G, double xi, do
     x = 2.0 * pow(R * R - T, 1.0 / 6.0) * cos(atan2(sqrt(-T), R) * (1.0 / 3.0)) - i1 * (1.0 / 3.0);
   } else {
     const double sT = sqrt(T);
-    x = cbrt(R + sT) + cbrt(R - sT) - i1 * (1.0 / 3.0);
+    x = cbrt_newton(R + sT) + cbrt_newton(R - sT) - i1 * (1.0 / 3.0);
   }
   const double B = 0.5 * (a3 + sqrt(a3 * a3 - 4.0 * a2 + 4.0 * x));
   const double C = 0.5 * (x - sqrt(x * x - 4.0 * a0));
@@ -134,6 +117,9 @@ __device__ __forceinline__ double beta_ideal_closed_form(double G, double xi, do
 // Ideal EOS, Newton-Raphson on the Riccardi quartic in w, beta = 2w/(1 + w^2)
 // (Eqs. iterative_quartic_unknown, iterative_quartic), started from the small-xi series of
 // Eq. iterative_cubic_approximation; stop at |dw| <= 1e-14 w; for xi < 1e-4 the series.
+// The iterations run first in FP32 (FP32 issues 58x faster than FP64 on this GPU) until the
+// step is below 1e-6 w, then continue in FP64 from that iterate to the FP64 stop rule;
+// `iters` counts both phases and max_iter caps their sum.
 __device__ __forceinline__ double w_ideal_newton(double al, double xi, double eta, int max_iter,
                                                  int& iters, bool& conv) {
   const double k1 = al * eta - 1.0;
@@ -145,21 +131,36 @@ __device__ __forceinline__ double w_ideal_newton(double al, double xi, double et
   iters = 0;
   conv = true;
   if (xi < 1e-4) return series;
-  double w = fmin(fmax(series, 1e-300), 1.0 - 1e-15);
   const double c4 = (al - 1.0) * xi, c3 = -2.0 * (al * eta + 1.0), c2 = 2.0 * (al + 1.0) * xi,
                c1 = -2.0 * k1, c0 = c4;
+  // FP32 phase
+  const float f4 = (float)c4, f3 = (float)c3, f2 = (float)c2, f1 = (float)c1, f0 = (float)c0;
+  float wf = fminf(fmaxf((float)series, 1e-30f), 1.0f - 6e-8f);
+  int it = 0;
+  const int max32 = max_iter - 2;  // the FP64 phase keeps at least two iterations
+  while (it < max32) {
+    const float Pw = fmaf(fmaf(fmaf(fmaf(f4, wf, f3), wf, f2), wf, f1), wf, f0);
+    const float dP = fmaf(fmaf(fmaf(4.0f * f4, wf, 3.0f * f3), wf, 2.0f * f2), wf, f1);
+    const float dw = Pw / dP;
+    wf -= dw;
+    ++it;
+    if (!(fabsf(dw) > 1e-6f * wf)) break;  // also leaves on NaN
+  }
+  double w = (wf > 0.0f && wf < 1.0f) ? (double)wf : fmin(fmax(series, 1e-300), 1.0 - 1e-15);
+  // FP64 phase
   conv = false;
-  for (int it = 1; it <= max_iter; ++it) {
+  while (it < max_iter) {
     const double Pw = fma(fma(fma(fma(c4, w, c3), w, c2), w, c1), w, c0);
     const double dP = fma(fma(fma(4.0 * c4, w, 3.0 * c3), w, 2.0 * c2), w, c1);
     const double dw = Pw / dP;
     w -= dw;
-    iters = it;
+    ++it;
     if (fabs(dw) <= 1e-14 * w) {
       conv = true;
       break;
     }
   }
+  iters = it;
   return w;
 }
 
@@ -198,34 +199,22 @@ __device__ __forceinline__ double W_tm_closed_form(double xi, double eta) {
     W = 2.0 * sqrt(-Q) * cos(iota * (1.0 / 3.0)) - c.c1 * (1.0 / 3.0);
   } else {
     const double sd = sqrt(d);
-    W = -c.c1 * (1.0 / 3.0) + cbrt(R + sd) + cbrt(R - sd);
+    W = -c.c1 * (1.0 / 3.0) + cbrt_newton(R + sd) + cbrt_newton(R - sd);
   }
   return fmax(W, 0.0);
 }
 
-// Taub-Matthews iterative: Brent's zero finder (Brent 1973) on the cubic, bracketed by
-// gamma in [1, 200] with the upper end multiplied by 4 (at most 10 times) until the sign
-// changes; tolerance 2 eps |b| + 1e-300.
-static __device__ __noinline__ double W_tm_brent(double xi, double eta, int max_iter, int& iters,
-                                          bool& conv) {
-  const Cubic cc = tm_cubic(xi, eta);
-  double a = 0.0, b = 200.0 * 200.0 - 1.0;
-  double fa = cubic_at(cc, a), fb = cubic_at(cc, b);
-  iters = 0;
+// Brent's zero finder (Brent 1973) on the cubic over the bracket [a, b] with f(a) f(b) <= 0,
+// tolerance 2 eps |b| + tiny, at most max_iter iterations; T is float or double.
+template <typename T>
+__device__ __forceinline__ T brent_cubic(T c1, T c2, T c3, T a, T b, T fa, T fb, int max_iter,
+                                         T eps, T tiny, int& iters, bool& conv) {
+  auto f = [&](T W) { return ((W + c1) * W + c2) * W + c3; };
+  T c = a, fc = fa, d = b - a, e = d;
   conv = false;
-  if (fa == 0.0) {
-    conv = true;
-    return 0.0;
-  }
-  for (int k = 0; k < 10 && fa * fb > 0.0; ++k) {
-    b *= 4.0;
-    fb = cubic_at(cc, b);
-  }
-  if (fa * fb > 0.0) return __longlong_as_double(0x7ff8000000000000LL);
-  double c = a, fc = fa, d = b - a, e = d;
   for (int it = 1; it <= max_iter; ++it) {
     iters = it;
-    if (fb * fc > 0.0) {
+    if (fb * fc > T(0)) {
       c = a;
       fc = fa;
       d = b - a;
@@ -239,28 +228,28 @@ static __device__ __noinline__ double W_tm_brent(double xi, double eta, int max_
       fb = fc;
       fc = fa;
     }
-    const double tol = 2.0 * 2.220446049250313e-16 * fabs(b) + 1e-300;
-    const double m = 0.5 * (c - b);
-    if (fabs(m) <= tol || fb == 0.0) {
+    const T tol = T(2) * eps * fabs(b) + tiny;
+    const T m = T(0.5) * (c - b);
+    if (fabs(m) <= tol || fb == T(0)) {
       conv = true;
       return b;
     }
     if (fabs(e) >= tol && fabs(fa) > fabs(fb)) {
-      const double s = fb / fa;
-      double pp, qq;
+      const T s = fb / fa;
+      T pp, qq;
       if (a == c) {
-        pp = 2.0 * m * s;
-        qq = 1.0 - s;
+        pp = T(2) * m * s;
+        qq = T(1) - s;
       } else {
-        const double q1 = fa / fc, r1 = fb / fc;
-        pp = s * (2.0 * m * q1 * (q1 - r1) - (b - a) * (r1 - 1.0));
-        qq = (q1 - 1.0) * (r1 - 1.0) * (s - 1.0);
+        const T q1 = fa / fc, r1 = fb / fc;
+        pp = s * (T(2) * m * q1 * (q1 - r1) - (b - a) * (r1 - T(1)));
+        qq = (q1 - T(1)) * (r1 - T(1)) * (s - T(1));
       }
-      if (pp > 0.0)
+      if (pp > T(0))
         qq = -qq;
       else
         pp = -pp;
-      if (2.0 * pp < fmin(3.0 * m * qq - fabs(tol * qq), fabs(e * qq))) {
+      if (T(2) * pp < fmin(T(3) * m * qq - fabs(tol * qq), fabs(e * qq))) {
         e = d;
         d = pp / qq;
       } else {
@@ -273,10 +262,58 @@ static __device__ __noinline__ double W_tm_brent(double xi, double eta, int max_
     }
     a = b;
     fa = fb;
-    b += (fabs(d) > tol) ? d : (m > 0.0 ? tol : -tol);
-    fb = cubic_at(cc, b);
+    b += (fabs(d) > tol) ? d : (m > T(0) ? tol : -tol);
+    fb = f(b);
   }
   return b;
+}
+
+// Taub-Matthews iterative (Sec. 3.2): Brent on the cubic, bracketed by gamma in [1, 200]
+// with the upper end multiplied by 4 (at most 10 times) until the sign changes.  The solve
+// runs in FP32 first; FP64 Brent then starts from the bracket W32 (1 -+ 1e-4) when the
+// cubic changes sign across it, and from the full bracket otherwise.  `iters` counts both
+// phases and max_iter caps their sum.
+static __device__ __noinline__ double W_tm_brent(double xi, double eta, int max_iter, int& iters,
+                                                 bool& conv) {
+  const Cubic cc = tm_cubic(xi, eta);
+  iters = 0;
+  conv = false;
+  const double f0 = cubic_at(cc, 0.0);
+  if (f0 == 0.0) {
+    conv = true;
+    return 0.0;
+  }
+  double hi = 200.0 * 200.0 - 1.0, fhi = cubic_at(cc, hi);
+  for (int k = 0; k < 10 && f0 * fhi > 0.0; ++k) {
+    hi *= 4.0;
+    fhi = cubic_at(cc, hi);
+  }
+  if (f0 * fhi > 0.0) return __longlong_as_double(0x7ff8000000000000LL);
+  // FP32 phase on the paper's bracket
+  const float g1 = (float)cc.c1, g2 = (float)cc.c2, g3 = (float)cc.c3;
+  auto ff = [&](float W) { return ((W + g1) * W + g2) * W + g3; };
+  int it32 = 0;
+  bool conv32 = false;
+  const int max32 = max_iter > 2 ? max_iter - 2 : 1;  // the FP64 phase keeps the rest
+  const float W32 = brent_cubic<float>(g1, g2, g3, 0.0f, (float)hi, ff(0.0f), ff((float)hi), max32,
+                                       1.1920929e-07f, 1e-37f, it32, conv32);
+  // FP64 phase
+  double a = 0.0, b = hi, fa = f0, fb = fhi;
+  if (conv32 && W32 > 0.0f) {
+    const double lo2 = (double)W32 * (1.0 - 1e-4), hi2 = (double)W32 * (1.0 + 1e-4);
+    const double flo = cubic_at(cc, lo2), fhi2 = cubic_at(cc, hi2);
+    if (flo * fhi2 <= 0.0) {
+      a = lo2;
+      b = hi2;
+      fa = flo;
+      fb = fhi2;
+    }
+  }
+  int it64 = 0;
+  const double W = brent_cubic<double>(cc.c1, cc.c2, cc.c3, a, b, fa, fb, max_iter - it32,
+                                       2.220446049250313e-16, 1e-300, it64, conv);
+  iters = it32 + it64;
+  return W;
 }
 
 // Result of one recovery.
@@ -291,12 +328,13 @@ __device__ __forceinline__ int con2prim(const Params& p, const double U[5], Prim
   const double S2 = U[1] * U[1] + U[2] * U[2] + U[3] * U[3];
   iters = 0;
   const double nanv = __longlong_as_double(0x7ff8000000000000LL);
-  if (!(D > 0.0) || !(q_func(D, S2, tau) > 0.0) || !isfinite(S2) || !isfinite(tau)) {
+  if (!admissible_parts(D, S2, tau) || !isfinite(S2) || !isfinite(tau)) {
     W.rho = W.v[0] = W.v[1] = W.v[2] = W.P = W.lor = nanv;
     return 1;
   }
   const double iD = 1.0 / D;
-  const double S = sqrt(S2);
+  const double rS = (S2 > 0.0) ? rsqrt(S2) : 0.0;  // 1/|S|
+  const double S = S2 * rS;
   const double xi = S * iD;
   const double eta = fma(tau, iD, 1.0);
   // beta = |v|, ginv = 1/gamma, omg = 1 - 1/gamma (cancellation-free per method)
@@ -329,7 +367,7 @@ __device__ __forceinline__ int con2prim(const Params& p, const double U[5], Prim
     omg = Wl * ginv / (lor + 1.0);
   }
   const double rho = D * ginv;
-  const double vs = (S2 == 0.0) ? 0.0 : beta / S;  // v = beta S / |S|
+  const double vs = beta * rS;  // v = beta S / |S|
   W.v[0] = vs * U[1];
   W.v[1] = vs * U[2];
   W.v[2] = vs * U[3];
@@ -365,30 +403,89 @@ __device__ __forceinline__ void phys_flux(const double U[5], const double v[3], 
   F[4] = (U[4] + P) * vd;
 }
 
-// lambda_pm = (v_d +- sqrt(sig (1 - v_d^2 + sig))) / (1 + sig), sig = cs2/(gamma^2 (1 - cs2)).
-__device__ __forceinline__ void wavespeeds(const ConsFlux& c, int d, double& lm, double& lp) {
-  const double sig = c.cs2 / (c.lor * c.lor * (1.0 - c.cs2));
-  const double vd = c.v[d];
-  const double r = sqrt(sig * (1.0 - vd * vd + sig));
-  const double i = 1.0 / (1.0 + sig);
-  lm = (vd - r) * i;
-  lp = (vd + r) * i;
+// Face state from the interpolated primitive (rho, u, P): conserved state, 3-velocity, and the
+// sound-speed ratio sig = cs^2 / (gamma^2 (1 - cs^2)) of Sec. 2.4 kept as the fraction A / B,
+// with both scaled by rho so that the ideal EOS needs no division:
+//   ideal: A = Gamma P,          B = gamma^2 (rho + alpha P - Gamma P)
+//   TM:    A = P (3 P + 5 s),    B = gamma^2 (12 P^2 + 2 rho^2 + 12 P s - A),  s = sqrt(P^2 + 4 rho^2 / 9)
+// (cs^2 = Gamma Theta / h, resp. the Taub-Matthews ratio, multiplied through by rho or rho^2).
+struct FaceState {
+  double U[5];
+  double v[3];
+  double P;
+  double A, B;
+};
+
+__device__ __forceinline__ void face_state(const Params& p, const double Wu[5], FaceState& c) {
+  const double rho = Wu[0], P = Wu[4];
+  const double u2 = Wu[1] * Wu[1] + Wu[2] * Wu[2] + Wu[3] * Wu[3];
+  const double q = 1.0 + u2;
+  const double ilor = rsqrt(q);
+  const double lor = q * ilor;
+  const double lor2 = q;  // gamma^2 = 1 + u^2
+  double rho_hm1;         // rho (h - 1)
+  if (p.eos == 0) {
+    rho_hm1 = p.alpha * P;
+    c.A = p.gamma_ad * P;
+    c.B = lor2 * (rho + rho_hm1 - c.A);
+  } else {
+    const double sg = sqrt(fma(P, P, (4.0 / 9.0) * rho * rho));
+    rho_hm1 = 2.5 * P + 1.5 * P * P / (sg + (2.0 / 3.0) * rho);
+    c.A = P * fma(3.0, P, 5.0 * sg);
+    c.B = lor2 * (fma(12.0 * P, P + sg, 2.0 * rho * rho) - c.A);
+  }
+  const double D = lor * rho;
+  const double rhoh_lor = (rho + rho_hm1) * lor;  // S = rho h gamma u
+  c.U[0] = D;
+  c.U[1] = rhoh_lor * Wu[1];
+  c.U[2] = rhoh_lor * Wu[2];
+  c.U[3] = rhoh_lor * Wu[3];
+  c.U[4] = D * u2 / (lor + 1.0) + lor2 * rho_hm1 - P;
+  c.v[0] = Wu[1] * ilor;
+  c.v[1] = Wu[2] * ilor;
+  c.v[2] = Wu[3] * ilor;
+  c.P = P;
 }
 
-// Numerical flux between face states given as (rho, u, P).  HLL: S_L = min(lambda_L, 0),
-// S_R = max(lambda_R, 0), (S_R F_L - S_L F_R + S_L S_R (U_R - U_L)) / (S_R - S_L) (the
-// average when both vanish); LLF: (F_L + F_R)/2 - a (U_R - U_L)/2, a = max |lambda|.
+// lambda_pm = (v_d +- sqrt(sig (1 - v_d^2 + sig))) / (1 + sig) with sig = A / B, evaluated as
+// (v_d B +- sqrt(A (B (1 - v_d^2) + A))) / (A + B): one root and one division for both.
+template <int D>
+__device__ __forceinline__ void wavespeeds_ab(const FaceState& c, double& lm, double& lp) {
+  const double vd = c.v[D];
+  const double r = sqrt(c.A * fma(c.B, fma(-vd, vd, 1.0), c.A));
+  const double i = 1.0 / (c.A + c.B);
+  lm = (vd * c.B - r) * i;
+  lp = (vd * c.B + r) * i;
+}
+
+template <int D>
+__device__ __forceinline__ void phys_flux_dir(const double U[5], const double v[3], double P,
+                                              double F[5]) {
+  const double vd = v[D];
+  F[0] = U[0] * vd;
+  F[1] = U[1] * vd;
+  F[2] = U[2] * vd;
+  F[3] = U[3] * vd;
+  F[1 + D] += P;
+  F[4] = (U[4] + P) * vd;
+}
+
+// Numerical flux along axis D between face states given as (rho, u, P).  HLL: S_L =
+// min(lambda_L, 0), S_R = max(lambda_R, 0), (S_R F_L - S_L F_R + S_L S_R (U_R - U_L)) /
+// (S_R - S_L) (the average when both vanish); LLF: (F_L + F_R)/2 - a (U_R - U_L)/2 with
+// a = max |lambda|.
+template <int D>
 __device__ __forceinline__ void numerical_flux(const Params& p, const double WL[5],
-                                               const double WR[5], int d, double Fs[5]) {
-  ConsFlux L, R;
-  prim_u_to_cons(p, WL, L);
-  prim_u_to_cons(p, WR, R);
+                                               const double WR[5], double Fs[5]) {
+  FaceState L, R;
+  face_state(p, WL, L);
+  face_state(p, WR, R);
   double FL[5], FR[5];
-  phys_flux(L.U, L.v, L.P, d, FL);
-  phys_flux(R.U, R.v, R.P, d, FR);
+  phys_flux_dir<D>(L.U, L.v, L.P, FL);
+  phys_flux_dir<D>(R.U, R.v, R.P, FR);
   double lmL, lpL, lmR, lpR;
-  wavespeeds(L, d, lmL, lpL);
-  wavespeeds(R, d, lmR, lpR);
+  wavespeeds_ab<D>(L, lmL, lpL);
+  wavespeeds_ab<D>(R, lmR, lpR);
   const double lamL = fmin(lmL, lmR), lamR = fmax(lpL, lpR);
   if (p.flux == 1) {
     const double sL = fmin(lamL, 0.0), sR = fmax(lamR, 0.0);

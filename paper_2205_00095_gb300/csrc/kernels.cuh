@@ -201,33 +201,32 @@ __global__ void __launch_bounds__(Shape<DIM, N>::BLOCK)
 }
 
 // ---------------------------------------------------------------------------------------
-// Face kernel: blockIdx.y = axis
+// Face kernel: blockIdx.y = axis; each axis runs its own instantiation of the face point so
+// that every index into the state is known at compile time.
 // ---------------------------------------------------------------------------------------
-template <int DIM, int N>
-__global__ void __launch_bounds__(128) face_kernel(Params p, const double* __restrict__ Tr,
-                                                   double* __restrict__ Fs) {
+template <int DIM, int N, int D>
+__device__ __forceinline__ void face_point(const Params& p, const double* __restrict__ Tr,
+                                           double* __restrict__ Fs, long long k) {
   constexpr int Nt = Shape<DIM, N>::Nt;
-  const int d = blockIdx.y;
-  const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  const long long nf = p.nface[d];
+  const long long nf = p.nface[D];
   if (k >= nf * Nt) return;
   const long long f = k / Nt;
   const int t = (int)(k - f * Nt);
   long long eL, eR;
   if (f < p.E) {
     eR = f;
-    const long long c = elem_coord(p, f, d);
+    const long long c = elem_coord(p, f, D);
     if (c > 0)
-      eL = f - p.stride[d];
-    else if (p.bc[d][0] == 0)
-      eL = f + (p.n[d] - 1) * p.stride[d];
+      eL = f - p.stride[D];
+    else if (p.bc[D][0] == 0)
+      eL = f + (p.n[D] - 1) * p.stride[D];
     else
       eL = -1;
   } else {
     const long long j = f - p.E;
-    if (d == 0)
+    if (D == 0)
       eL = (p.n[0] - 1) + p.n[0] * j;
-    else if (d == 1)
+    else if (D == 1)
       eL = (j % p.n[0]) + p.n[0] * ((p.n[1] - 1) + p.n[1] * (j / p.n[0]));
     else
       eL = j + p.n[0] * p.n[1] * (p.n[2] - 1);
@@ -235,8 +234,8 @@ __global__ void __launch_bounds__(128) face_kernel(Params p, const double* __res
   }
   double WL[5], WR[5];
   const long long side_stride = 5 * p.E * Nt;
-  const double* trL = Tr + ((long long)d * 2 + 1) * side_stride;  // high side of the left elem
-  const double* trR = Tr + ((long long)d * 2 + 0) * side_stride;  // low side of the right elem
+  const double* trL = Tr + ((long long)D * 2 + 1) * side_stride;  // high side of the left elem
+  const double* trR = Tr + ((long long)D * 2 + 0) * side_stride;  // low side of the right elem
   if (eL >= 0) {
 #pragma unroll
     for (int v = 0; v < 5; ++v) WL[v] = trL[(v * p.E + eL) * Nt + t];
@@ -247,17 +246,26 @@ __global__ void __launch_bounds__(128) face_kernel(Params p, const double* __res
   }
   if (eL < 0) {
 #pragma unroll
-    for (int v = 0; v < 5; ++v) WL[v] = (p.bc[d][0] == 1) ? p.ghost[d][0][v] : WR[v];
+    for (int v = 0; v < 5; ++v) WL[v] = (p.bc[D][0] == 1) ? p.ghost[D][0][v] : WR[v];
   }
   if (eR < 0) {
 #pragma unroll
-    for (int v = 0; v < 5; ++v) WR[v] = (p.bc[d][1] == 1) ? p.ghost[d][1][v] : WL[v];
+    for (int v = 0; v < 5; ++v) WR[v] = (p.bc[D][1] == 1) ? p.ghost[D][1][v] : WL[v];
   }
   double F[5];
-  numerical_flux(p, WL, WR, d, F);
-  double* out = Fs + p.fs_off[d];
+  numerical_flux<D>(p, WL, WR, F);
+  double* out = Fs + p.fs_off[D];
 #pragma unroll
   for (int v = 0; v < 5; ++v) out[(v * nf + f) * Nt + t] = F[v];
+}
+
+template <int DIM, int N>
+__global__ void __launch_bounds__(128) face_kernel(Params p, const double* __restrict__ Tr,
+                                                   double* __restrict__ Fs) {
+  const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (blockIdx.y == 0) face_point<DIM, N, 0>(p, Tr, Fs, k);
+  if (DIM > 1 && blockIdx.y == 1) face_point<DIM, N, (DIM > 1 ? 1 : 0)>(p, Tr, Fs, k);
+  if (DIM > 2 && blockIdx.y == 2) face_point<DIM, N, (DIM > 2 ? 2 : 0)>(p, Tr, Fs, k);
 }
 
 // ---------------------------------------------------------------------------------------
