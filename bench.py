@@ -287,6 +287,34 @@ def ours(args, rank, world, local_rank):
         e2e = {"value": world * ndof * args.steps * stages / float(e2e_t.item()), "unit": UNIT,
                "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes}
 
+    # split-precision form on the same workload: tensor-core contractions, FP64 elsewhere
+    split = None
+    if not args.no_split:
+        ss = Solver(dict(spec, precision="split"), stream=stream, device=dev)
+        with torch.cuda.stream(stream):
+            V = U0.clone()
+        ss.step(V, dt, max(1, args.warmup))
+        ss.set_profiling(True)
+        ss.kernel_times(reset=True)
+        barrier()
+        ev0.record(stream)
+        ss.step(V, dt, args.steps)
+        ev1.record(stream)
+        torch.cuda.synchronize(dev)
+        barrier()
+        sms = ev0.elapsed_time(ev1)
+        sk = ss.kernel_times(reset=True)
+        ss.set_profiling(False)
+        with torch.cuda.stream(stream):
+            l1 = float(((V - U).abs().sum() / U.abs().sum()).item())
+        sstatus, _ = ss.stats()
+        split = {"value": world * ndof * args.steps * stages / (sms * 1e-3), "unit": UNIT,
+                 "ms_per_step": sms / args.steps, "speedup_vs_fp64": ms / sms,
+                 "l1_rel_vs_fp64": l1, "device_status": sstatus,
+                 "contractions": "3xTF32 mma.sync m16n8k8, FP32 accumulation, deviation form",
+                 "kernel_ms_per_launch": {k: round(v[0] / max(v[1], 1), 4) for k, v in sk.items() if v[1]}}
+        ss.close()
+
     # oracle on the host cores (rank 0, N = 1 only)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -326,6 +354,7 @@ def ours(args, rank, world, local_rank):
                        "l2": "inputs larger than L2 (state 168 MB + scratch)",
                        "precision": "fp64"},
             "roofline": roofline, "kernel_shares": shares,
+            "split_precision": split,
             "cpu_baseline": cpu,
             "e2e": e2e,
             "gpu_launches": launches,
@@ -347,6 +376,7 @@ def main():
                     help="con2prim solver (default: the workload's)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end timing")
+    ap.add_argument("--no-split", action="store_true", help="skip the split-precision run")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

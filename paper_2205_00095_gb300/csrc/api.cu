@@ -29,6 +29,7 @@ struct dgsrhd_ctx {
   double* Rv;   // volume term / R
   double* Tr;   // face traces
   double* Fs;   // face fluxes
+  double* Fref; // split precision: reference flux per element [dim][5][E]
   double* Ud;   // device state for dgsrhd_step_host
   double* Wv;   // VJP: nodal primitives
   double* TrB;  // VJP: trace adjoints
@@ -155,6 +156,8 @@ cudaError_t timed_launch(dgsrhd_ctx* c, int kind, F&& launch) {
 cudaError_t run_stage(dgsrhd_ctx* c, StageArgs& a) {
   a.p = &c->p;
   a.stream = c->stream;
+  a.split = c->cfg.precision == DGSRHD_PREC_SPLIT;
+  a.Fref = c->Fref;
   cudaError_t e = timed_launch(c, kernel_kind(a.op), [&]() {
     switch (c->dim) {
       case 1: return dgsrhd::dispatch_stage<1>(c->N, a);
@@ -318,6 +321,7 @@ int32_t dgsrhd_create(const dgsrhd_config* cfg, void* stream, dgsrhd_ctx** out) 
   if (e == cudaSuccess) e = alloc(&c->Rv, c->nstate);
   if (e == cudaSuccess) e = alloc(&c->Tr, ntr);
   if (e == cudaSuccess) e = alloc(&c->Fs, fs_total);
+  if (e == cudaSuccess && cfg->precision == DGSRHD_PREC_SPLIT) e = alloc(&c->Fref, 5LL * c->dim * E);
   if (e == cudaSuccess) e = alloc(&c->Ud, c->nstate);
   if (e == cudaSuccess) e = alloc(&c->stats, (size_t)dgsrhd::kStatCount * 64);
   if (e == cudaSuccess) e = cudaMemsetAsync(c->stats, 0, sizeof(unsigned long long) * dgsrhd::kStatCount * 64, c->stream);
@@ -345,6 +349,7 @@ void dgsrhd_destroy(dgsrhd_ctx* c) {
   cudaFree(c->Rv);
   cudaFree(c->Tr);
   cudaFree(c->Fs);
+  cudaFree(c->Fref);
   cudaFree(c->Ud);
   cudaFree(c->Wv);
   cudaFree(c->TrB);

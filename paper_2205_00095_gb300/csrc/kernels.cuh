@@ -272,18 +272,18 @@ __global__ void __launch_bounds__(128) face_kernel(Params p, const double* __res
 // Physicality operator on the elements of one block (Sec. 2.5).  u holds this thread's node
 // state; on return it holds the smoothed state.  Every thread of the block must call it.
 // ---------------------------------------------------------------------------------------
-template <int DIM, int N>
+template <int DIM, int N, int BLOCKSZ = Shape<DIM, N>::BLOCK>
 struct EnforceShared {
-  double a[5][Shape<DIM, N>::BLOCK];
+  double a[5][BLOCKSZ];
   double mean[Shape<DIM, N>::EPB][5];
   double s[Shape<DIM, N>::EPB];
   int flag[Shape<DIM, N>::EPB];
 };
 
-template <int DIM, int N>
+template <int DIM, int N, int BLOCKSZ>
 __device__ __forceinline__ void enforce_block(const Params& p, double u[5], bool valid, int le,
                                               int li, long long e, double* s_out,
-                                              EnforceShared<DIM, N>& sh) {
+                                              EnforceShared<DIM, N, BLOCKSZ>& sh) {
   constexpr int Nn = Shape<DIM, N>::Nn;
   const int tid = threadIdx.x;
   const bool bad = valid && !admissible(u);
@@ -422,7 +422,7 @@ __global__ void __launch_bounds__(Shape<DIM, N>::BLOCK)
     }
   }
   if (mode == 0) return;  // uniform over the grid
-  if (enforce) enforce_block<DIM, N>(p, u, valid, le, li, e, s_out, sh);
+  if (enforce) enforce_block(p, u, valid, le, li, e, s_out, sh);
   if (valid) {
 #pragma unroll
     for (int v = 0; v < 5; ++v) Uout[v * tot + g] = u[v];
@@ -446,7 +446,7 @@ __global__ void __launch_bounds__(Shape<DIM, N>::BLOCK)
   if (valid)
 #pragma unroll
     for (int v = 0; v < 5; ++v) u[v] = U[v * tot + g];
-  enforce_block<DIM, N>(p, u, valid, le, li, e, s_out, sh);
+  enforce_block(p, u, valid, le, li, e, s_out, sh);
   if (valid)
 #pragma unroll
     for (int v = 0; v < 5; ++v) U[v * tot + g] = u[v];
@@ -456,10 +456,33 @@ __global__ void __launch_bounds__(Shape<DIM, N>::BLOCK)
 // Host-side launchers
 // ---------------------------------------------------------------------------------------
 template <int DIM, int N>
+static cudaError_t launch_stage_kernels(const StageArgs& a);
+
+}  // namespace dgsrhd
+
+#include "kernels_split.cuh"
+
+namespace dgsrhd {
+
+template <int DIM, int N>
 static cudaError_t launch_stage_kernels(const StageArgs& a) {
   using S = Shape<DIM, N>;
   const Params& p = *a.p;
   const unsigned eblocks = (unsigned)((p.E + S::EPB - 1) / S::EPB);
+  if (a.split && (a.op == Op::Volume || a.op == Op::Update)) {
+    constexpr int SB = SplitShape<DIM, N>::BLOCK;
+    if (a.op == Op::Volume) {
+      const size_t smem = VolSmem<DIM, N>::TOTAL;
+      cudaFuncSetAttribute(volume_kernel_split<DIM, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      volume_kernel_split<DIM, N><<<eblocks, SB, smem, a.stream>>>(p, a.U, a.Rvol, a.Tr, a.Fref);
+    } else {
+      const size_t smem = UpdSmem<DIM, N>::TOTAL;
+      cudaFuncSetAttribute(update_kernel_split<DIM, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      update_kernel_split<DIM, N><<<eblocks, SB, smem, a.stream>>>(
+          p, a.Rvol, a.Fs, a.Fref, a.Un, a.Uk, a.Uout, a.a_n, a.b_k, a.dt, a.mode, a.enforce, a.s_out);
+    }
+    return cudaGetLastError();
+  }
   switch (a.op) {
     case Op::Volume:
       volume_kernel<DIM, N><<<eblocks, S::BLOCK, 0, a.stream>>>(p, a.U, a.Rvol, a.Tr);

@@ -17,12 +17,14 @@ struct StageArgs {
   double* Rvol;        // volume term (also R of the VJP)
   double* Tr;          // face traces
   double* Fs;          // face fluxes
+  double* Fref;        // split precision: per-element reference flux [dim][5][E]
   const double* Un;    // Update: U^n
   const double* Uk;    // Update: U^(k-1)
   double* Uout;        // Update: output; Enforce: state in place
   double a_n, b_k, dt;
   int mode;            // Update: 0 = write R, 1 = RK stage
   int enforce;
+  int split;           // Volume / Update: split-precision tensor-core contractions
   double* s_out;
   // VJP buffers
   const double* Rbar;

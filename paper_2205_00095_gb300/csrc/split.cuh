@@ -1,0 +1,94 @@
+// Split-precision basis contractions on tensor cores (3xTF32, FP32 accumulation).
+//
+// The volume term, the face-trace extrapolation and the lift are small dense contractions along
+// one axis of an element: out[i] = sum_a C[i][a] x[a] for every line of N nodes.  Gathered over
+// a block they are matrix products of shape (lines x N) * (N x N) (or N x 2 for traces, 2 x N
+// for the lift), done here with mma.sync.m16n8k8 TF32: a warp multiplies 16 lines (rows of A)
+// by the coefficient matrix (B, 8 x 8 with zero padding).  Each operand x is split as
+// x = hi + lo with hi, lo TF32 and the product formed as hi*hi + lo*hi + hi*lo in FP32.
+//
+// On this GPU FP64<->FP32 conversion instructions issue on the FP64 pipe at the DFMA rate, so
+// the splits and the conversions of FP32 results back to FP64 are done with integer
+// operations on the bit patterns (FP32-normal range; smaller magnitudes flush to zero, larger
+// saturate to infinity).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace dgsrhd {
+
+// double -> float by truncating the mantissa, via bit operations only
+__device__ __forceinline__ float f64_to_f32_bits(double x) {
+  const int hw = __double2hiint(x);
+  const unsigned lw = (unsigned)__double2loint(x);
+  const unsigned sign = (unsigned)hw & 0x80000000u;
+  const int e = (hw >> 20) & 0x7ff;
+  const unsigned mant = (((unsigned)hw & 0xfffffu) << 3) | (lw >> 29);
+  const int ef = e - 896;  // rebias 1023 -> 127
+  unsigned bits;
+  if (ef <= 0)
+    bits = sign;  // zero, subnormal or below the FP32-normal range
+  else if (ef >= 255)
+    bits = sign | 0x7f800000u | (e == 0x7ff && ((hw & 0xfffff) | lw) ? 0x400000u : 0u);
+  else
+    bits = sign | ((unsigned)ef << 23) | mant;
+  return __uint_as_float(bits);
+}
+
+// float -> double (exact for FP32-normal values), via bit operations only
+__device__ __forceinline__ double f32_to_f64_bits(float f) {
+  const unsigned b = __float_as_uint(f);
+  const unsigned sign = b & 0x80000000u;
+  const unsigned ef = (b >> 23) & 0xffu;
+  const unsigned mf = b & 0x7fffffu;
+  int hw;
+  unsigned lw;
+  if (ef == 0) {
+    hw = (int)sign;
+    lw = 0u;
+  } else if (ef == 255) {
+    hw = (int)(sign | 0x7ff00000u | (mf >> 3));
+    lw = mf << 29;
+  } else {
+    hw = (int)(sign | ((ef + 896u) << 20) | (mf >> 3));
+    lw = mf << 29;
+  }
+  return __hiloint2double(hw, (int)lw);
+}
+
+// TF32 split of a float: hi keeps the top 10 explicit mantissa bits, lo = x - hi (exact in
+// FP32), rounded to TF32 by the tensor core's truncation of its low 13 bits.
+struct Tf32Pair {
+  unsigned hi, lo;
+};
+
+__device__ __forceinline__ Tf32Pair split_tf32(float x) {
+  const unsigned h = __float_as_uint(x) & 0xffffe000u;
+  const float lo = x - __uint_as_float(h);
+  Tf32Pair p;
+  p.hi = h;
+  p.lo = __float_as_uint(lo) & 0xffffe000u;
+  return p;
+}
+
+__device__ __forceinline__ Tf32Pair split_tf32_f64(double x) { return split_tf32(f64_to_f32_bits(x)); }
+
+// D (16x8, f32) += A (16x8, tf32, row) * B (8x8, tf32, col)
+__device__ __forceinline__ void mma_tf32(float c[4], const unsigned a[4], const unsigned b[2]) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
+      "{%8,%9}, {%0,%1,%2,%3};\n"
+      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+// 3xTF32 product: c += A_lo B_hi + A_hi B_lo + A_hi B_hi (small terms first)
+__device__ __forceinline__ void mma_3xtf32(float c[4], const unsigned ahi[4], const unsigned alo[4],
+                                           const unsigned bhi[2], const unsigned blo[2]) {
+  mma_tf32(c, alo, bhi);
+  mma_tf32(c, ahi, blo);
+  mma_tf32(c, ahi, bhi);
+}
+
+}  // namespace dgsrhd
