@@ -315,6 +315,45 @@ def ours(args, rank, world, local_rank):
                  "kernel_ms_per_launch": {k: round(v[0] / max(v[1], 1), 4) for k, v in sk.items() if v[1]}}
         ss.close()
 
+    # adjoint: gradient of the transverse kinetic energy after 200 SSPRK3 steps of the 2D
+    # Kelvin-Helmholtz set-up at 128 x 256, p = 3, checkpoint every 20 steps, against the forward
+    adj = None
+    if not args.no_adjoint:
+        from paper_2205_00095_gb300 import adjoint as adjm
+        spec4 = wl.kh2d(nx=128, ny=256, degree=3)
+        sa = Solver(spec4, stream=stream, device=dev)
+        with torch.cuda.stream(stream):
+            A0 = sa.initial_state(wl.kh2d_ic(spec4, sa.node_coords()))
+            sa.enforce(A0)
+            Af = A0.clone()
+        dta = sa.cfl_dt(0.2)
+        sa.step(Af, dta, 3)  # warm-up and graph capture
+        with torch.cuda.stream(stream):
+            Af.copy_(A0)
+        barrier()
+        ev0.record(stream)
+        sa.step(Af, dta, 200)
+        ev1.record(stream)
+        torch.cuda.synchronize(dev)
+        fwd_ms = ev0.elapsed_time(ev1)
+        barrier()
+        with torch.cuda.stream(stream):
+            U0g = A0.clone().requires_grad_(True)
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        with torch.cuda.stream(stream):
+            UT = adjm.rollout(sa, U0g, dta, 200, 20)
+            Jv = adjm.transverse_kinetic_energy(sa, UT)
+            Jv.backward()
+        torch.cuda.synchronize(dev)
+        adj_ms = 1e3 * (time.perf_counter() - t0)
+        ast, ast_counts = sa.stats()
+        adj = {"workload": "kh_2d 128x256 elements p=3 TM Brent HLL SSPRK3, 200 steps, checkpoint every 20",
+               "objective": "sum rho gamma^2 v_y^2 at t_final", "forward_ms": fwd_ms,
+               "forward_plus_adjoint_ms": adj_ms, "adjoint_forward_ratio": adj_ms / fwd_ms,
+               "grad_norm": float(U0g.grad.norm()), "enforced_cells": ast_counts["enforced_cells"]}
+        sa.close()
+
     # oracle on the host cores (rank 0, N = 1 only)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -355,6 +394,7 @@ def ours(args, rank, world, local_rank):
                        "precision": "fp64"},
             "roofline": roofline, "kernel_shares": shares,
             "split_precision": split,
+            "adjoint": adj,
             "cpu_baseline": cpu,
             "e2e": e2e,
             "gpu_launches": launches,
@@ -377,6 +417,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end timing")
     ap.add_argument("--no-split", action="store_true", help="skip the split-precision run")
+    ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint/forward timing")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

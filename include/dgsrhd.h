@@ -141,14 +141,45 @@ int32_t dgsrhd_step(dgsrhd_ctx* ctx, double* U, double dt, int32_t nsteps);
  * synchronises the stream.  For pinned host memory the copies are asynchronous DMA. */
 int32_t dgsrhd_step_host(dgsrhd_ctx* ctx, double* U_host, double dt, int32_t nsteps);
 
-/* U_bar = (dR/dU)^T R_bar for R = dgsrhd_rhs(U) (vector-Jacobian product).  Non-smooth
- * choices (HLL/LLF speed selection, face guard) are frozen at their forward branch. */
+/* U_bar = (dR/dU)^T R_bar for R = dgsrhd_rhs(U) (vector-Jacobian product), in FP64 whatever
+ * the configured precision: transposed lift, reverse of the LLF/HLL flux, transposed trace
+ * extrapolation and volume term, transposed flux Jacobians and the con2prim adjoint
+ * (dU/dW)^{-T}.  Non-smooth choices (the min/max wavespeed selection, the clamps of HLL, |lambda|
+ * of LLF, the face guard) are frozen at their forward branch.  U_bar must not alias U or R_bar. */
 int32_t dgsrhd_rhs_vjp(dgsrhd_ctx* ctx, const double* U, const double* R_bar, double* U_bar);
 
 /* VJP of the physicality operator with each element's factor s frozen at its forward value
  * (s from dgsrhd_enforce): U_bar_i = s Ut_bar_i + (1 - s) w_i / sum(w) sum_j Ut_bar_j. */
 int32_t dgsrhd_enforce_vjp(dgsrhd_ctx* ctx, const double* s, const double* Ut_bar,
                            double* U_bar);
+
+/* One Shu-Osher stage `stage` (0-based) of the configured scheme:
+ * Uout = a_k Un + b_k (Uk + dt R(Uk)), followed (if enabled) by the physicality operator, whose
+ * per-element factors go to s_out (nullable, [n_elem]).  Uout may alias Un or Uk.  Composing
+ * the stages reproduces dgsrhd_step.  save (nullable, device, dgsrhd_stage_save_size doubles)
+ * receives the nodal (rho, u, P) and the face traces of R(Uk) for dgsrhd_stage_vjp; a stage
+ * with save runs the FP64 kernels whatever the configured precision. */
+int32_t dgsrhd_step_stage(dgsrhd_ctx* ctx, const double* Un, const double* Uk, double* Uout,
+                          int32_t stage, double dt, double* s_out, double* save);
+
+/* Doubles of the `save` buffer of dgsrhd_step_stage: 5 E Nn + 10 dim E Nt. */
+int32_t dgsrhd_stage_save_size(const dgsrhd_ctx* ctx, int64_t* n);
+
+/* Reverse sweep of one stage (the transpose of dgsrhd_step_stage at its input Uk, with the
+ * operator's factors s frozen; s NULL or enforcement off: no operator):
+ *   Y_bar = enforce_vjp(s, Z_bar),  Un_bar += a_k Y_bar,
+ *   Uk_bar += b_k (Y_bar + dt (dR/dU)^T Y_bar)  at U = Uk.
+ * saved (nullable): the `save` buffer of the forward stage; without it the forward quantities
+ * are recomputed.  Both outputs ACCUMULATE (zero them first); they may alias each other but
+ * not Z_bar. */
+int32_t dgsrhd_stage_vjp(dgsrhd_ctx* ctx, const double* Uk, const double* s, const double* saved,
+                         const double* Z_bar, double* Un_bar, double* Uk_bar, int32_t stage,
+                         double dt);
+
+/* Adjoint of con2prim by the implicit-function theorem (Sec. 3): W = (rho, v, P) solves
+ * U = prim2cons(W) (Eq. primitive_to_conserved), so U_bar = (dU/dW)^{-T} W_bar, one 5 x 5 solve
+ * per node at the recovered root.  W_bar is in the layout of W. */
+int32_t dgsrhd_con2prim_vjp(dgsrhd_ctx* ctx, const double* U, const double* W_bar, double* U_bar);
 
 /* Time step of the CFL rule dt = cfl / ((2p + 1) sum_d 1/dx_d) (all speeds <= c = 1). */
 int32_t dgsrhd_cfl_dt(const dgsrhd_ctx* ctx, double cfl, double* dt);

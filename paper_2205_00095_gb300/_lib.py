@@ -95,6 +95,10 @@ def load() -> ctypes.CDLL:
         "dgsrhd_kernel_times": (i32, [vp, P(d), P(i64), i32]),
         "dgsrhd_status_string": (ctypes.c_char_p, [i32]),
         "dgsrhd_rhs_noalloc": (i32, [P(dgsrhd_config), vp, vp, vp, P(dgsrhd_stats)]),
+        "dgsrhd_step_stage": (i32, [vp, vp, vp, vp, i32, d, vp, vp]),
+        "dgsrhd_stage_save_size": (i32, [vp, P(i64)]),
+        "dgsrhd_stage_vjp": (i32, [vp, vp, vp, vp, vp, vp, vp, i32, d]),
+        "dgsrhd_con2prim_vjp": (i32, [vp, vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -112,7 +116,8 @@ def exported_symbols():
         "dgsrhd_enforce", "dgsrhd_step", "dgsrhd_step_host", "dgsrhd_rhs_vjp",
         "dgsrhd_enforce_vjp", "dgsrhd_cfl_dt", "dgsrhd_get_stats", "dgsrhd_kernel_launches",
         "dgsrhd_set_profiling", "dgsrhd_kernel_times", "dgsrhd_status_string",
-        "dgsrhd_rhs_noalloc",
+        "dgsrhd_rhs_noalloc", "dgsrhd_step_stage", "dgsrhd_stage_save_size", "dgsrhd_stage_vjp",
+        "dgsrhd_con2prim_vjp",
     ]
 
 

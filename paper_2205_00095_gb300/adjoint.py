@@ -1,0 +1,173 @@
+"""Differentiation through the solver: torch.autograd functions over the library's hand-written
+vector-Jacobian products.
+
+* ``rhs(solver, U)``: R = dU/dt with ``dgsrhd_rhs_vjp`` as its backward.
+* ``rollout(solver, U0, dt, nsteps, every)``: nsteps SSP-RK steps; the backward keeps only a
+  checkpoint every ``every`` steps from the forward pass, recomputes each segment stage by stage
+  (``dgsrhd_step_stage``, which also returns the physicality operator's factors and keeps the
+  nodal primitives and face traces of each stage) and runs the stages' reverse sweeps
+  (``dgsrhd_stage_vjp``, factors frozen at their forward values).
+* ``transverse_kinetic_energy(solver, U)``: J = sum over elements and nodes of
+  (prod_d dx_d/2) w_node rho gamma^2 v_y^2, with ``dgsrhd_con2prim_vjp`` in its backward.
+
+Every step of the forward and reverse sweeps runs in the library's kernels; torch holds the
+buffers and evaluates the objective's pointwise derivative.
+"""
+from __future__ import annotations
+
+import numpy as np
+import torch
+
+from .solver import Solver
+
+
+class _OnSolverStream:
+    """Run a block on the solver's stream, ordered after the caller's stream and before it."""
+
+    def __init__(self, solver: Solver):
+        self.solver = solver
+
+    def __enter__(self):
+        self.caller = torch.cuda.current_stream(self.solver.device)
+        self.solver.stream.wait_stream(self.caller)
+        self.ctx = torch.cuda.stream(self.solver.stream)
+        self.ctx.__enter__()
+
+    def __exit__(self, *exc):
+        self.ctx.__exit__(*exc)
+        self.caller.wait_stream(self.solver.stream)
+
+
+class _RHS(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, U, solver):
+        U = U.detach().contiguous()
+        ctx.solver = solver
+        ctx.save_for_backward(U)
+        with _OnSolverStream(solver):
+            return solver.rhs(U)
+
+    @staticmethod
+    def backward(ctx, R_bar):
+        (U,) = ctx.saved_tensors
+        with _OnSolverStream(ctx.solver):
+            return ctx.solver.rhs_vjp(U, R_bar.contiguous()), None
+
+
+def rhs(solver: Solver, U: torch.Tensor) -> torch.Tensor:
+    return _RHS.apply(U, solver)
+
+
+class _Rollout(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, U0, solver, dt, nsteps, every):
+        checkpoints = []
+        with _OnSolverStream(solver):
+            U = U0.detach().clone()
+            done = 0
+            while done < nsteps:
+                n = min(every, nsteps - done)
+                checkpoints.append((done, U.clone()))
+                solver.step(U, dt, n)
+                done += n
+        ctx.solver, ctx.dt, ctx.nsteps = solver, dt, nsteps
+        ctx.checkpoints = checkpoints
+        return U
+
+    @staticmethod
+    def backward(ctx, U_bar):
+        s: Solver = ctx.solver
+        dt, nsteps = ctx.dt, ctx.nsteps
+        stages = int(s.spec.get("rk_stages", 3))
+        nsave = s.stage_save_size()
+        with _OnSolverStream(s):
+            Zb = U_bar.detach().clone().contiguous()
+            bounds = [c[0] for c in ctx.checkpoints] + [nsteps]
+            for seg in reversed(range(len(ctx.checkpoints))):
+                start, U = ctx.checkpoints[seg]
+                nseg = bounds[seg + 1] - start
+                # recompute the segment, keeping every stage input, operator factor and the
+                # forward quantities (nodal primitives, face traces) of each stage's RHS
+                X, S, SV = [], [], []
+                cur = U.clone()
+                for _ in range(nseg):
+                    xs, ss, sv = [cur], [], []
+                    for k in range(stages):
+                        out = torch.empty_like(cur)
+                        sk = torch.empty(s.n_elem, dtype=torch.float64, device=cur.device)
+                        save = torch.empty(nsave, dtype=torch.float64, device=cur.device)
+                        s.step_stage(xs[0], xs[k], out, k, dt, sk, save)
+                        ss.append(sk)
+                        sv.append(save)
+                        if k < stages - 1:
+                            xs.append(out)
+                    X.append(xs)
+                    S.append(ss)
+                    SV.append(sv)
+                    cur = out
+                # reverse sweep of the segment
+                for j in reversed(range(nseg)):
+                    Unb = torch.zeros_like(Zb)
+                    z = Zb
+                    for k in reversed(range(stages)):
+                        if k > 0:
+                            xb = torch.zeros_like(Zb)
+                            s.stage_vjp(X[j][k], S[j][k], z, Unb, xb, k, dt, SV[j][k])
+                            z = xb
+                        else:
+                            s.stage_vjp(X[j][0], S[j][0], z, Unb, Unb, 0, dt, SV[j][0])
+                    Zb = Unb
+        return Zb, None, None, None, None
+
+
+def rollout(solver: Solver, U0: torch.Tensor, dt: float, nsteps: int, every: int = 20) -> torch.Tensor:
+    return _Rollout.apply(U0, solver, float(dt), int(nsteps), int(every))
+
+
+def node_weights(solver: Solver) -> torch.Tensor:
+    """Quadrature weight of every node, (prod_d dx_d / 2) w_a w_b ..., shape (n_elem, n_node)."""
+    spec = solver.spec
+    dim, N = int(spec["dim"]), int(spec["degree"]) + 1
+    x = solver.node_coords()
+    w1 = np.polynomial.legendre.leggauss(N)[1]
+    w = w1
+    for _ in range(dim - 1):
+        w = np.multiply.outer(w1, w).ravel()
+    jac = 1.0
+    for d in range(dim):
+        jac *= (spec["hi"][d] - spec["lo"][d]) / spec["n_elem"][d] / 2.0
+    return torch.from_numpy(np.broadcast_to(w * jac, x.shape[1:]).copy()).to(solver.device)
+
+
+class _KineticY(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, U, solver, weights):
+        U = U.detach().contiguous()
+        with _OnSolverStream(solver):
+            W = solver.con2prim(U)
+            rho, v = W[0], W[1:4]
+            g2 = 1.0 / (1.0 - (v * v).sum(0))
+            J = (weights * rho * g2 * v[1] * v[1]).sum()
+        ctx.solver = solver
+        ctx.save_for_backward(U, W, weights)
+        return J
+
+    @staticmethod
+    def backward(ctx, Jb):
+        U, W, wts = ctx.saved_tensors
+        with _OnSolverStream(ctx.solver):
+            rho, v = W[0], W[1:4]
+            g2 = 1.0 / (1.0 - (v * v).sum(0))
+            Wb = torch.zeros_like(W)
+            Wb[0] = wts * g2 * v[1] * v[1]
+            # d(gamma^2)/dv_k = 2 gamma^4 v_k
+            for k in range(3):
+                Wb[1 + k] = wts * rho * 2.0 * g2 * g2 * v[k] * v[1] * v[1]
+            Wb[2] += wts * rho * g2 * 2.0 * v[1]
+            Wb *= Jb
+            Ub = ctx.solver.con2prim_vjp(U, Wb.contiguous())
+        return Ub, None, None
+
+
+def transverse_kinetic_energy(solver: Solver, U: torch.Tensor) -> torch.Tensor:
+    return _KineticY.apply(U, solver, node_weights(solver))

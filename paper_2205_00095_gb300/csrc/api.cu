@@ -31,8 +31,10 @@ struct dgsrhd_ctx {
   double* Fs;   // face fluxes
   double* Fref; // split precision: reference flux per element [dim][5][E]
   double* Ud;   // device state for dgsrhd_step_host
-  double* Wv;   // VJP: nodal primitives
+  double* Wv;   // VJP: nodal (rho, u, P)
   double* TrB;  // VJP: trace adjoints
+  double* Yb;   // stage VJP: adjoint of the stage before the operator
+  double* Vb;   // stage VJP: (dR/dU)^T Yb
   unsigned long long* stats;
   long long c2p_calls;
   long long launches;
@@ -156,7 +158,7 @@ cudaError_t timed_launch(dgsrhd_ctx* c, int kind, F&& launch) {
 cudaError_t run_stage(dgsrhd_ctx* c, StageArgs& a) {
   a.p = &c->p;
   a.stream = c->stream;
-  a.split = c->cfg.precision == DGSRHD_PREC_SPLIT;
+  a.split = c->cfg.precision == DGSRHD_PREC_SPLIT && !a.fp64_only;
   a.Fref = c->Fref;
   cudaError_t e = timed_launch(c, kernel_kind(a.op), [&]() {
     switch (c->dim) {
@@ -323,6 +325,10 @@ int32_t dgsrhd_create(const dgsrhd_config* cfg, void* stream, dgsrhd_ctx** out) 
   if (e == cudaSuccess) e = alloc(&c->Fs, fs_total);
   if (e == cudaSuccess && cfg->precision == DGSRHD_PREC_SPLIT) e = alloc(&c->Fref, 5LL * c->dim * E);
   if (e == cudaSuccess) e = alloc(&c->Ud, c->nstate);
+  if (e == cudaSuccess) e = alloc(&c->Wv, c->nstate);
+  if (e == cudaSuccess) e = alloc(&c->TrB, ntr);
+  if (e == cudaSuccess) e = alloc(&c->Yb, c->nstate);
+  if (e == cudaSuccess) e = alloc(&c->Vb, c->nstate);
   if (e == cudaSuccess) e = alloc(&c->stats, (size_t)dgsrhd::kStatCount * 64);
   if (e == cudaSuccess) e = cudaMemsetAsync(c->stats, 0, sizeof(unsigned long long) * dgsrhd::kStatCount * 64, c->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
@@ -353,6 +359,8 @@ void dgsrhd_destroy(dgsrhd_ctx* c) {
   cudaFree(c->Ud);
   cudaFree(c->Wv);
   cudaFree(c->TrB);
+  cudaFree(c->Yb);
+  cudaFree(c->Vb);
   cudaFree(c->stats);
   delete c;
 }
@@ -568,20 +576,139 @@ int32_t dgsrhd_kernel_times(dgsrhd_ctx* c, double* ms, int64_t* counts, int32_t 
   return DGSRHD_OK;
 }
 
+}  // extern "C"
+
+namespace {
+
+// Reverse sweep of the RHS.  `saved` (nullable) holds the nodal (rho, u, P) and the face traces
+// of the forward evaluation at U (written by dgsrhd_step_stage); without it the forward volume
+// kernel is re-run to provide them.
+int32_t rhs_vjp_core(dgsrhd_ctx* c, const double* U, const double* R_bar, double* U_bar,
+                     const double* saved) {
+  const double* Wst = saved;
+  const double* Tr = saved ? saved + c->nstate : nullptr;
+  if (!saved) {
+    StageArgs v{};
+    v.op = Op::Volume;
+    v.fp64_only = 1;
+    v.U = U;
+    v.Rvol = c->Rv;
+    v.Tr = c->Tr;
+    v.Wstore = c->Wv;
+    if (run_stage(c, v) != cudaSuccess) return DGSRHD_ECUDA;
+    c->c2p_calls += c->E * c->Nn;
+    Wst = c->Wv;
+    Tr = c->Tr;
+  }
+  StageArgs f{};
+  f.op = Op::VjpFace;
+  f.Tr = const_cast<double*>(Tr);
+  f.Rbar = R_bar;
+  f.TrBar = c->TrB;
+  if (run_stage(c, f) != cudaSuccess) return DGSRHD_ECUDA;
+  StageArgs n{};
+  n.op = Op::VjpNode;
+  n.U = U;
+  n.Wstore = const_cast<double*>(Wst);
+  n.Rbar = R_bar;
+  n.TrBar = c->TrB;
+  n.Ubar = U_bar;
+  return cuda_status(run_stage(c, n));
+}
+
+long long trace_doubles(const dgsrhd_ctx* c) { return 2LL * c->dim * 5 * c->E * c->p.Nt; }
+
+}  // namespace
+
+extern "C" {
+
 int32_t dgsrhd_rhs_vjp(dgsrhd_ctx* c, const double* U, const double* R_bar, double* U_bar) {
-  (void)c;
-  (void)U;
-  (void)R_bar;
-  (void)U_bar;
-  return DGSRHD_EINVAL;
+  if (!c || !U || !R_bar || !U_bar || U_bar == U || U_bar == R_bar) return DGSRHD_EINVAL;
+  return rhs_vjp_core(c, U, R_bar, U_bar, nullptr);
+}
+
+int32_t dgsrhd_stage_save_size(const dgsrhd_ctx* c, int64_t* n) {
+  if (!c || !n) return DGSRHD_EINVAL;
+  *n = c->nstate + trace_doubles(c);
+  return DGSRHD_OK;
 }
 
 int32_t dgsrhd_enforce_vjp(dgsrhd_ctx* c, const double* s, const double* Ut_bar, double* U_bar) {
-  (void)c;
-  (void)s;
-  (void)Ut_bar;
-  (void)U_bar;
-  return DGSRHD_EINVAL;
+  if (!c || !s || !Ut_bar || !U_bar) return DGSRHD_EINVAL;
+  StageArgs a{};
+  a.op = Op::EnforceVjp;
+  a.s_in = s;
+  a.Tbar = Ut_bar;
+  a.Ubar = U_bar;
+  return cuda_status(run_stage(c, a));
+}
+
+int32_t dgsrhd_step_stage(dgsrhd_ctx* c, const double* Un, const double* Uk, double* Uout,
+                          int32_t stage, double dt, double* s_out, double* save) {
+  if (!c || !Un || !Uk || !Uout || stage < 0 || stage >= c->cfg.rk_stages || !(dt >= 0.0))
+    return DGSRHD_EINVAL;
+  const int ns = c->cfg.rk_stages;
+  StageArgs v{};
+  v.op = Op::Volume;
+  v.U = Uk;
+  v.Rvol = c->Rv;
+  v.Tr = save ? save + c->nstate : c->Tr;
+  v.Wstore = save;
+  if (save) v.fp64_only = 1;  // the saved quantities feed the FP64 reverse sweep
+  if (run_stage(c, v) != cudaSuccess) return DGSRHD_ECUDA;
+  c->c2p_calls += c->E * c->Nn;
+  StageArgs f{};
+  f.op = Op::Face;
+  f.Tr = v.Tr;
+  f.Fs = c->Fs;
+  if (run_stage(c, f) != cudaSuccess) return DGSRHD_ECUDA;
+  StageArgs u{};
+  u.op = Op::Update;
+  u.fp64_only = v.fp64_only;
+  u.Rvol = c->Rv;
+  u.Fs = c->Fs;
+  u.Un = Un;
+  u.Uk = Uk;
+  u.Uout = Uout;
+  u.a_n = kAn[ns - 1][stage];
+  u.b_k = kBk[ns - 1][stage];
+  u.dt = dt;
+  u.mode = 1;
+  u.enforce = c->cfg.enforce;
+  u.s_out = s_out;
+  return cuda_status(run_stage(c, u));
+}
+
+int32_t dgsrhd_stage_vjp(dgsrhd_ctx* c, const double* Uk, const double* s, const double* saved,
+                         const double* Z_bar, double* Un_bar, double* Uk_bar, int32_t stage,
+                         double dt) {
+  if (!c || !Uk || !Z_bar || !Un_bar || !Uk_bar || stage < 0 || stage >= c->cfg.rk_stages)
+    return DGSRHD_EINVAL;
+  if (Z_bar == Un_bar || Z_bar == Uk_bar) return DGSRHD_EINVAL;
+  const int ns = c->cfg.rk_stages;
+  const double* Yb = Z_bar;
+  if (c->cfg.enforce && s) {
+    int32_t st = dgsrhd_enforce_vjp(c, s, Z_bar, c->Yb);
+    if (st != DGSRHD_OK) return st;
+    Yb = c->Yb;
+  }
+  int32_t st = rhs_vjp_core(c, Uk, Yb, c->Vb, saved);
+  if (st != DGSRHD_OK) return st;
+  const double a_n = kAn[ns - 1][stage], b_k = kBk[ns - 1][stage];
+  cudaError_t e = timed_launch(c, DGSRHD_KERNEL_VJP, [&]() {
+    return dgsrhd::launch_stage_combine(c->stream, c->nstate, Yb, c->Vb, a_n, b_k, dt, Un_bar, Uk_bar);
+  });
+  if (e == cudaSuccess) c->launches += 1;
+  return cuda_status(e);
+}
+
+int32_t dgsrhd_con2prim_vjp(dgsrhd_ctx* c, const double* U, const double* W_bar, double* U_bar) {
+  if (!c || !U || !W_bar || !U_bar) return DGSRHD_EINVAL;
+  cudaError_t e = timed_launch(c, DGSRHD_KERNEL_VJP, [&]() {
+    return dgsrhd::launch_con2prim_vjp(c->p, c->stream, c->E * c->Nn, U, W_bar, U_bar);
+  });
+  if (e == cudaSuccess) c->launches += 1;
+  return cuda_status(e);
 }
 
 const char* dgsrhd_status_string(int32_t s) {

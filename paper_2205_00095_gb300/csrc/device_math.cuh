@@ -505,4 +505,53 @@ __device__ __forceinline__ void numerical_flux(const Params& p, const double WL[
   }
 }
 
+// con2prim adjoint by the implicit-function theorem: W = (rho, v, P) inverts
+// U = prim2cons(W) (Eq. primitive_to_conserved), so U_bar = (dU/dW)^{-T} W_bar.
+// With E = tau + D the map is D = gamma rho, S = w gamma^2 v, E = w gamma^2 - P (w = rho h), and
+// (dU/dW)^T x = W_bar becomes, for y = (x_D - x_tau, x_S, x_tau) and a = v . y_S,
+//   gamma y_D + w_rho gamma^2 (a + y_E)                       = W_bar_rho
+//   rho gamma^3 v y_D + w gamma^2 y_S + 2 w gamma^4 v (a + y_E) = W_bar_v
+//   w_P gamma^2 a + (w_P gamma^2 - 1) y_E                     = W_bar_P
+// The v equation gives y_S = (W_bar_v - c v) / (w gamma^2), c = rho gamma^3 y_D + 2 w gamma^4 (a + y_E);
+// projected on v it closes a 3 x 3 system in (y_D, a, y_E), solved by Cramer's rule.
+__device__ __forceinline__ void c2p_adjoint(const Params& p, double rho, const double v[3], double P,
+                                            double lor, const double Wb[5], double Ub[5]) {
+  double w, w_r, w_P;
+  if (p.eos == 0) {
+    w = rho + p.alpha * P;
+    w_r = 1.0;
+    w_P = p.alpha;
+  } else {
+    const double sg = sqrt(P * P + (4.0 / 9.0) * rho * rho);
+    w = 2.5 * P + 1.5 * sg;
+    w_r = (2.0 / 3.0) * rho / sg;
+    w_P = 2.5 + 1.5 * P / sg;
+  }
+  const double g2 = lor * lor, g3 = g2 * lor, g4 = g2 * g2;
+  const double v2 = v[0] * v[0] + v[1] * v[1] + v[2] * v[2];
+  const double vW = v[0] * Wb[1] + v[1] * Wb[2] + v[2] * Wb[3];
+  // rows: (y_D, a, y_E) coefficients and right-hand sides
+  //  (1) gamma y_D + w_r g2 a + w_r g2 y_E = Wb_rho
+  //  (2) v2 rho g3 y_D + (w g2 + 2 w g4 v2) a + 2 w g4 v2 y_E = vW
+  //  (3) 0 y_D + w_P g2 a + (w_P g2 - 1) y_E = Wb_P
+  const double m11 = lor, m12 = w_r * g2, m13 = w_r * g2;
+  const double m21 = v2 * rho * g3, m22 = w * g2 + 2.0 * w * g4 * v2, m23 = 2.0 * w * g4 * v2;
+  const double m32 = w_P * g2, m33 = w_P * g2 - 1.0;
+  const double r1 = Wb[0], r2 = vW, r3 = Wb[4];
+  const double c11 = m22 * m33 - m23 * m32;
+  const double c12 = m21 * m33;           // minus sign applied below
+  const double c13 = m21 * m32;
+  const double det = m11 * c11 - m12 * c12 + m13 * c13;
+  const double idet = 1.0 / det;
+  const double yD = (r1 * c11 - m12 * (r2 * m33 - m23 * r3) + m13 * (r2 * m32 - m22 * r3)) * idet;
+  const double a = (m11 * (r2 * m33 - m23 * r3) - r1 * c12 + m13 * (m21 * r3)) * idet;
+  const double yE = (m11 * (m22 * r3 - r2 * m32) - m12 * (m21 * r3) + r1 * c13) * idet;
+  const double c = rho * g3 * yD + 2.0 * w * g4 * (a + yE);
+  const double iw = 1.0 / (w * g2);
+  Ub[0] = yD + yE;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) Ub[1 + k] = (Wb[1 + k] - c * v[k]) * iw;
+  Ub[4] = yE;
+}
+
 }  // namespace dgsrhd

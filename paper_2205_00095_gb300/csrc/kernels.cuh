@@ -117,7 +117,7 @@ __device__ __forceinline__ void block_stats(const Params& p, int iters, int stat
 template <int DIM, int N>
 __global__ void __launch_bounds__(Shape<DIM, N>::BLOCK)
     volume_kernel(Params p, const double* __restrict__ U, double* __restrict__ Rvol,
-                  double* __restrict__ Tr) {
+                  double* __restrict__ Tr, double* __restrict__ Wout) {
   using S = Shape<DIM, N>;
   constexpr int Nn = S::Nn, Nt = S::Nt, BLOCK = S::BLOCK;
   __shared__ double shF[DIM][5][BLOCK];
@@ -151,6 +151,10 @@ __global__ void __launch_bounds__(Shape<DIM, N>::BLOCK)
     shW[2][tid] = W.lor * W.v[1];
     shW[3][tid] = W.lor * W.v[2];
     shW[4][tid] = W.P;
+    if (Wout) {  // the interpolated primitive (rho, u, P) kept for the vector-Jacobian product
+#pragma unroll
+      for (int v = 0; v < 5; ++v) Wout[v * tot + g] = shW[v][tid];
+    }
   }
   block_stats(p, iters, status, shred);  // contains __syncthreads
 
@@ -461,6 +465,7 @@ static cudaError_t launch_stage_kernels(const StageArgs& a);
 }  // namespace dgsrhd
 
 #include "kernels_split.cuh"
+#include "kernels_vjp.cuh"
 
 namespace dgsrhd {
 
@@ -485,7 +490,7 @@ static cudaError_t launch_stage_kernels(const StageArgs& a) {
   }
   switch (a.op) {
     case Op::Volume:
-      volume_kernel<DIM, N><<<eblocks, S::BLOCK, 0, a.stream>>>(p, a.U, a.Rvol, a.Tr);
+      volume_kernel<DIM, N><<<eblocks, S::BLOCK, 0, a.stream>>>(p, a.U, a.Rvol, a.Tr, a.Wstore);
       break;
     case Op::Face: {
       long long mx = 0;
@@ -501,6 +506,20 @@ static cudaError_t launch_stage_kernels(const StageArgs& a) {
       break;
     case Op::Enforce:
       enforce_kernel<DIM, N><<<eblocks, S::BLOCK, 0, a.stream>>>(p, a.Uout, a.s_out);
+      break;
+    case Op::VjpFace: {
+      long long mx = 0;
+      for (int d = 0; d < DIM; ++d) mx = p.nface[d] > mx ? p.nface[d] : mx;
+      const long long nthreads = mx * S::Nt;
+      dim3 grid((unsigned)((nthreads + 127) / 128), DIM);
+      face_vjp_kernel<DIM, N><<<grid, 128, 0, a.stream>>>(p, a.Tr, a.Rbar, a.TrBar);
+      break;
+    }
+    case Op::VjpNode:
+      node_vjp_kernel<DIM, N><<<eblocks, S::BLOCK, 0, a.stream>>>(p, a.U, a.Wstore, a.Rbar, a.TrBar, a.Ubar);
+      break;
+    case Op::EnforceVjp:
+      enforce_vjp_kernel<DIM, N><<<eblocks, S::BLOCK, 0, a.stream>>>(p, a.s_in, a.Tbar, a.Ubar);
       break;
     default:
       return cudaErrorInvalidValue;

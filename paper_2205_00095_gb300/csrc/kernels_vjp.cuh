@@ -1,0 +1,488 @@
+// Vector-Jacobian product of the DG right-hand side, U_bar = (dR/dU)^T R_bar, and of the
+// physicality operator with frozen smoothing factors.
+//
+// The forward RHS is R = Dhat-volume(F(U, W(U))) - lift(F*(traces(W(U)))).  Its reverse sweep:
+//   face_vjp_kernel : per face point, F*_bar = (2/dx)(sum_a l-_a R_bar_right - sum_a l+_a R_bar_left)
+//                     (transposed lift), then the reverse of the LLF/HLL flux with its branch
+//                     choices (min/max of the wavespeeds, the clamps to 0, |lambda|) frozen at
+//                     their forward values, giving the adjoints of the two face traces.
+//   node_vjp_kernel : per node, the transposed volume contraction F_bar = (2/dx) Dhat^T R_bar, the
+//                     transposed trace extrapolation (face guard frozen), the transposed flux
+//                     Jacobians, and the con2prim adjoint by the implicit-function theorem: W(U)
+//                     inverts U = prim2cons(W) (Eq. primitive_to_conserved), so
+//                     U_bar = (dU/dW)^{-T} W_bar, a 5 x 5 solve at the converged root.
+// The forward volume kernel is re-run first to provide the face traces and the nodal (rho, u, P).
+#pragma once
+
+#include "kernels.cuh"
+
+namespace dgsrhd {
+
+// ---------------------------------------------------------------------------------------
+// One face state: forward with its intermediates, then its reverse.
+// ---------------------------------------------------------------------------------------
+struct FaceFwd {
+  double Wu[5];
+  double u2, q, ilor, lor, rho_hm1, A, B, sg, Z, K, H, rhoh_lor, den1;
+  double U[5], v[3];
+  double F[5];
+  double X, r, i, lm, lp;
+};
+
+template <int D>
+__device__ __forceinline__ void face_fwd(const Params& p, const double Wu[5], FaceFwd& f) {
+#pragma unroll
+  for (int k = 0; k < 5; ++k) f.Wu[k] = Wu[k];
+  const double rho = Wu[0], P = Wu[4];
+  f.u2 = Wu[1] * Wu[1] + Wu[2] * Wu[2] + Wu[3] * Wu[3];
+  f.q = 1.0 + f.u2;
+  f.ilor = rsqrt(f.q);
+  f.lor = f.q * f.ilor;
+  if (p.eos == 0) {
+    f.rho_hm1 = p.alpha * P;
+    f.A = p.gamma_ad * P;
+    f.B = f.q * (rho + f.rho_hm1 - f.A);
+    f.sg = f.Z = f.K = 0.0;
+  } else {
+    f.sg = sqrt(P * P + (4.0 / 9.0) * rho * rho);
+    f.Z = f.sg + (2.0 / 3.0) * rho;
+    f.rho_hm1 = 2.5 * P + 1.5 * P * P / f.Z;
+    f.A = P * (3.0 * P + 5.0 * f.sg);
+    f.K = 12.0 * P * (P + f.sg) + 2.0 * rho * rho - f.A;
+    f.B = f.q * f.K;
+  }
+  f.H = rho + f.rho_hm1;
+  f.rhoh_lor = f.H * f.lor;
+  f.den1 = f.lor + 1.0;
+  f.U[0] = f.lor * rho;
+  f.U[1] = f.rhoh_lor * Wu[1];
+  f.U[2] = f.rhoh_lor * Wu[2];
+  f.U[3] = f.rhoh_lor * Wu[3];
+  f.U[4] = f.U[0] * f.u2 / f.den1 + f.q * f.rho_hm1 - P;
+  f.v[0] = Wu[1] * f.ilor;
+  f.v[1] = Wu[2] * f.ilor;
+  f.v[2] = Wu[3] * f.ilor;
+  const double vd = f.v[D];
+  f.F[0] = f.U[0] * vd;
+  f.F[1] = f.U[1] * vd;
+  f.F[2] = f.U[2] * vd;
+  f.F[3] = f.U[3] * vd;
+  f.F[1 + D] += P;
+  f.F[4] = (f.U[4] + P) * vd;
+  f.X = f.A * (f.B * (1.0 - vd * vd) + f.A);
+  f.r = sqrt(f.X);
+  f.i = 1.0 / (f.A + f.B);
+  f.lm = (vd * f.B - f.r) * f.i;
+  f.lp = (vd * f.B + f.r) * f.i;
+}
+
+// Reverse of face_fwd: adjoints of its outputs (flux Fb, conserved state Ub, wavespeeds lmb,
+// lpb) -> adjoint of the face primitive (rho, u, P).
+template <int D>
+__device__ __forceinline__ void face_rev(const Params& p, const FaceFwd& f, const double Fb[5],
+                                         const double Ub[5], double lmb, double lpb, double Wb[5]) {
+  const double rho = f.Wu[0], P = f.Wu[4];
+  const double vd = f.v[D];
+  // wavespeeds
+  const double ib = lmb * (vd * f.B - f.r) + lpb * (vd * f.B + f.r);
+  double vdb = (lmb + lpb) * f.B * f.i;
+  double Bb = (lmb + lpb) * vd * f.i - ib * f.i * f.i;
+  double Ab = -ib * f.i * f.i;
+  const double rb = (lpb - lmb) * f.i;
+  const double Xb = f.r > 0.0 ? rb / (2.0 * f.r) : 0.0;
+  Ab += Xb * (f.B * (1.0 - vd * vd) + 2.0 * f.A);
+  Bb += Xb * f.A * (1.0 - vd * vd);
+  vdb += Xb * f.A * f.B * (-2.0 * vd);
+  // flux along D
+  double Db = Ub[0] + Fb[0] * vd;
+  double Sb[3] = {Ub[1] + Fb[1] * vd, Ub[2] + Fb[2] * vd, Ub[3] + Fb[3] * vd};
+  const double taub = Ub[4] + Fb[4] * vd;
+  double Pb = Fb[1 + D] + Fb[4] * vd;
+  vdb += Fb[0] * f.U[0] + Fb[1] * f.U[1] + Fb[2] * f.U[2] + Fb[3] * f.U[3] + Fb[4] * (f.U[4] + P);
+  // v_k = u_k / gamma
+  double ub[3] = {0.0, 0.0, 0.0};
+  ub[D] = vdb * f.ilor;
+  double ilorb = vdb * f.Wu[1 + D];
+  // tau = D u2/(gamma + 1) + q rho(h-1) - P
+  Db += taub * f.u2 / f.den1;
+  double u2b = taub * f.U[0] / f.den1;
+  double lorb = -taub * f.U[0] * f.u2 / (f.den1 * f.den1);
+  double qb = taub * f.rho_hm1;
+  double rhm1b = taub * f.q;
+  Pb -= taub;
+  // S_k = rho h gamma u_k
+  const double rhlb = Sb[0] * f.Wu[1] + Sb[1] * f.Wu[2] + Sb[2] * f.Wu[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) ub[k] += Sb[k] * f.rhoh_lor;
+  const double Hb = rhlb * f.lor;
+  lorb += rhlb * f.H;
+  double rhob = Hb;
+  rhm1b += Hb;
+  // D = gamma rho
+  lorb += Db * rho;
+  rhob += Db * f.lor;
+  // equation of state
+  if (p.eos == 0) {
+    const double c = rho + f.rho_hm1 - f.A;
+    qb += Bb * c;
+    rhob += Bb * f.q;
+    rhm1b += Bb * f.q;
+    Ab -= Bb * f.q;
+    Pb += Ab * p.gamma_ad + rhm1b * p.alpha;
+  } else {
+    qb += Bb * f.K;
+    const double Kb = Bb * f.q;
+    Pb += Kb * 12.0 * (2.0 * P + f.sg);
+    double sgb = Kb * 12.0 * P;
+    rhob += Kb * 4.0 * rho;
+    Ab -= Kb;
+    Pb += Ab * (6.0 * P + 5.0 * f.sg);
+    sgb += Ab * 5.0 * P;
+    Pb += rhm1b * (2.5 + 3.0 * P / f.Z);
+    const double Zb = -rhm1b * 1.5 * P * P / (f.Z * f.Z);
+    sgb += Zb;
+    rhob += Zb * (2.0 / 3.0);
+    Pb += sgb * P / f.sg;
+    rhob += sgb * (4.0 / 9.0) * rho / f.sg;
+  }
+  // gamma = q^(1/2), 1/gamma = q^(-1/2), q = 1 + u2
+  qb += lorb * 0.5 * f.ilor - ilorb * 0.5 * f.ilor / f.q;
+  u2b += qb;
+  Wb[0] = rhob;
+  Wb[1] = ub[0] + 2.0 * f.Wu[1] * u2b;
+  Wb[2] = ub[1] + 2.0 * f.Wu[2] * u2b;
+  Wb[3] = ub[2] + 2.0 * f.Wu[3] * u2b;
+  Wb[4] = Pb;
+}
+
+// Reverse of numerical_flux<D>: Fsb -> adjoints of the left and right face primitives.
+template <int D>
+__device__ __forceinline__ void numerical_flux_vjp(const Params& p, const double WL[5],
+                                                   const double WR[5], const double Fsb[5],
+                                                   double WLb[5], double WRb[5]) {
+  FaceFwd L, R;
+  face_fwd<D>(p, WL, L);
+  face_fwd<D>(p, WR, R);
+  const bool selL_from_L = L.lm <= R.lm;  // lambda_L = min(lm_L, lm_R)
+  const bool selR_from_L = L.lp >= R.lp;  // lambda_R = max(lp_L, lp_R)
+  const double lamL = selL_from_L ? L.lm : R.lm, lamR = selR_from_L ? L.lp : R.lp;
+  double FLb[5], FRb[5], ULb[5], URb[5];
+  double lamLb = 0.0, lamRb = 0.0;
+  if (p.flux == 1) {
+    const bool actL = lamL < 0.0, actR = lamR > 0.0;
+    const double sL = actL ? lamL : 0.0, sR = actR ? lamR : 0.0;
+    const double den = sR - sL;
+    if (den == 0.0) {
+#pragma unroll
+      for (int v = 0; v < 5; ++v) {
+        FLb[v] = FRb[v] = 0.5 * Fsb[v];
+        ULb[v] = URb[v] = 0.0;
+      }
+    } else {
+      const double id = 1.0 / den;
+      double sLb = 0.0, sRb = 0.0;
+#pragma unroll
+      for (int v = 0; v < 5; ++v) {
+        const double dU = R.U[v] - L.U[v];
+        const double Fs = (sR * L.F[v] - sL * R.F[v] + sL * sR * dU) * id;
+        FLb[v] = sR * id * Fsb[v];
+        FRb[v] = -sL * id * Fsb[v];
+        URb[v] = sL * sR * id * Fsb[v];
+        ULb[v] = -URb[v];
+        sRb += Fsb[v] * (L.F[v] + sL * dU - Fs) * id;
+        sLb += Fsb[v] * (-R.F[v] + sR * dU + Fs) * id;
+      }
+      lamLb = actL ? sLb : 0.0;
+      lamRb = actR ? sRb : 0.0;
+    }
+  } else {
+    const bool useL = fabs(lamL) >= fabs(lamR);  // a = max(|lambda_L|, |lambda_R|)
+    const double a = useL ? fabs(lamL) : fabs(lamR);
+    double ab = 0.0;
+#pragma unroll
+    for (int v = 0; v < 5; ++v) {
+      FLb[v] = FRb[v] = 0.5 * Fsb[v];
+      ULb[v] = 0.5 * a * Fsb[v];
+      URb[v] = -0.5 * a * Fsb[v];
+      ab -= 0.5 * Fsb[v] * (R.U[v] - L.U[v]);
+    }
+    if (useL)
+      lamLb = ab * (lamL >= 0.0 ? 1.0 : -1.0);
+    else
+      lamRb = ab * (lamR >= 0.0 ? 1.0 : -1.0);
+  }
+  const double lmLb = selL_from_L ? lamLb : 0.0, lmRb = selL_from_L ? 0.0 : lamLb;
+  const double lpLb = selR_from_L ? lamRb : 0.0, lpRb = selR_from_L ? 0.0 : lamRb;
+  face_rev<D>(p, L, FLb, ULb, lmLb, lpLb, WLb);
+  face_rev<D>(p, R, FRb, URb, lmRb, lpRb, WRb);
+}
+
+// ---------------------------------------------------------------------------------------
+// Face kernel of the VJP: adjoints of the face traces, TrB in the layout of Tr.
+// ---------------------------------------------------------------------------------------
+template <int DIM, int N, int D>
+__device__ __forceinline__ void face_vjp_point(const Params& p, const double* __restrict__ Tr,
+                                               const double* __restrict__ Rb,
+                                               double* __restrict__ TrB, long long k) {
+  constexpr int Nn = Shape<DIM, N>::Nn, Nt = Shape<DIM, N>::Nt;
+  const long long nf = p.nface[D];
+  if (k >= nf * Nt) return;
+  const long long f = k / Nt;
+  const int t = (int)(k - f * Nt);
+  long long eL, eR;
+  if (f < p.E) {
+    eR = f;
+    const long long c = elem_coord(p, f, D);
+    if (c > 0)
+      eL = f - p.stride[D];
+    else if (p.bc[D][0] == 0)
+      eL = f + (p.n[D] - 1) * p.stride[D];
+    else
+      eL = -1;
+  } else {
+    const long long j = f - p.E;
+    if (D == 0)
+      eL = (p.n[0] - 1) + p.n[0] * j;
+    else if (D == 1)
+      eL = (j % p.n[0]) + p.n[0] * ((p.n[1] - 1) + p.n[1] * (j / p.n[0]));
+    else
+      eL = j + p.n[0] * p.n[1] * (p.n[2] - 1);
+    eR = -1;
+  }
+  const long long tot = p.E * Nn;
+  const long long side_stride = 5 * p.E * Nt;
+  const double* trL = Tr + ((long long)D * 2 + 1) * side_stride;
+  const double* trR = Tr + ((long long)D * 2 + 0) * side_stride;
+  double WL[5], WR[5], Fsb[5];
+  if (eL >= 0) {
+#pragma unroll
+    for (int v = 0; v < 5; ++v) WL[v] = trL[(v * p.E + eL) * Nt + t];
+  }
+  if (eR >= 0) {
+#pragma unroll
+    for (int v = 0; v < 5; ++v) WR[v] = trR[(v * p.E + eR) * Nt + t];
+  }
+  if (eL < 0) {
+#pragma unroll
+    for (int v = 0; v < 5; ++v) WL[v] = (p.bc[D][0] == 1) ? p.ghost[D][0][v] : WR[v];
+  }
+  if (eR < 0) {
+#pragma unroll
+    for (int v = 0; v < 5; ++v) WR[v] = (p.bc[D][1] == 1) ? p.ghost[D][1][v] : WL[v];
+  }
+  // transposed lift: R_left -= s l+ F*, R_right += s l- F*
+  const double sc = p.inv_half_dx[D];
+#pragma unroll
+  for (int v = 0; v < 5; ++v) {
+    double acc = 0.0;
+#pragma unroll
+    for (int a = 0; a < N; ++a) {
+      const int node = line_node<DIM, N>(D, t, a);
+      if (eR >= 0) acc += p.lm[a] * Rb[v * tot + eR * Nn + node];
+      if (eL >= 0) acc -= p.lp[a] * Rb[v * tot + eL * Nn + node];
+    }
+    Fsb[v] = sc * acc;
+  }
+  double WLb[5], WRb[5];
+  numerical_flux_vjp<D>(p, WL, WR, Fsb, WLb, WRb);
+  // ghost states: Dirichlet ghosts are constant, outflow ghosts copy the interior trace
+  if (eL < 0 && p.bc[D][0] == 2)
+#pragma unroll
+    for (int v = 0; v < 5; ++v) WRb[v] += WLb[v];
+  if (eR < 0 && p.bc[D][1] == 2)
+#pragma unroll
+    for (int v = 0; v < 5; ++v) WLb[v] += WRb[v];
+  double* tbL = TrB + ((long long)D * 2 + 1) * side_stride;
+  double* tbR = TrB + ((long long)D * 2 + 0) * side_stride;
+  if (eL >= 0)
+#pragma unroll
+    for (int v = 0; v < 5; ++v) tbL[(v * p.E + eL) * Nt + t] = WLb[v];
+  if (eR >= 0)
+#pragma unroll
+    for (int v = 0; v < 5; ++v) tbR[(v * p.E + eR) * Nt + t] = WRb[v];
+}
+
+template <int DIM, int N>
+__global__ void __launch_bounds__(128) face_vjp_kernel(Params p, const double* __restrict__ Tr,
+                                                       const double* __restrict__ Rb,
+                                                       double* __restrict__ TrB) {
+  const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (blockIdx.y == 0) face_vjp_point<DIM, N, 0>(p, Tr, Rb, TrB, k);
+  if (DIM > 1 && blockIdx.y == 1) face_vjp_point<DIM, N, (DIM > 1 ? 1 : 0)>(p, Tr, Rb, TrB, k);
+  if (DIM > 2 && blockIdx.y == 2) face_vjp_point<DIM, N, (DIM > 2 ? 2 : 0)>(p, Tr, Rb, TrB, k);
+}
+
+// ---------------------------------------------------------------------------------------
+// Nodal adjoint: U_bar = (dF/dU|_W)^T F_bar + (dU/dW)^{-T} W_bar, W = (rho, v, P).
+// ---------------------------------------------------------------------------------------
+
+// Given the node state (U, rho, u, P), the adjoint of its nodal fluxes (Fb[d][5]) and of its
+// interpolated primitive (Wub = adjoint of (rho, u, P)), return U_bar.
+template <int DIM>
+__device__ __forceinline__ void node_adjoint(const Params& p, const double U[5], const double Wu[5],
+                                             const double Fb[DIM][5], const double Wub[5],
+                                             double Ub[5]) {
+  const double rho = Wu[0], P = Wu[4];
+  const double u2 = Wu[1] * Wu[1] + Wu[2] * Wu[2] + Wu[3] * Wu[3];
+  const double lor = sqrt(1.0 + u2);
+  const double ilor = 1.0 / lor;
+  const double v[3] = {Wu[1] * ilor, Wu[2] * ilor, Wu[3] * ilor};
+  double Wb[5] = {Wub[0], 0.0, 0.0, 0.0, Wub[4]};  // adjoint of (rho, v, P)
+  // u = gamma v: du/dv = gamma I + gamma^3 v v^T (symmetric)
+  const double vu = v[0] * Wub[1] + v[1] * Wub[2] + v[2] * Wub[3];
+  const double l3 = lor * lor * lor;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) Wb[1 + k] = lor * Wub[1 + k] + l3 * v[k] * vu;
+  // fluxes F^d = (D v_d, S v_d + P e_d, (tau + P) v_d)
+#pragma unroll
+  for (int k = 0; k < 5; ++k) Ub[k] = 0.0;
+#pragma unroll
+  for (int d = 0; d < DIM; ++d) {
+    const double vd = v[d];
+#pragma unroll
+    for (int k = 0; k < 5; ++k) Ub[k] += vd * Fb[d][k];
+    Wb[1 + d] += Fb[d][0] * U[0] + Fb[d][1] * U[1] + Fb[d][2] * U[2] + Fb[d][3] * U[3] +
+                 Fb[d][4] * (U[4] + P);
+    Wb[4] += Fb[d][1 + d] + Fb[d][4] * vd;
+  }
+  double x[5];
+  c2p_adjoint(p, rho, v, P, lor, Wb, x);
+#pragma unroll
+  for (int k = 0; k < 5; ++k) Ub[k] += x[k];
+}
+
+template <int DIM, int N>
+__global__ void __launch_bounds__(Shape<DIM, N>::BLOCK)
+    node_vjp_kernel(Params p, const double* __restrict__ U, const double* __restrict__ Wst,
+                    const double* __restrict__ Rb, const double* __restrict__ TrB,
+                    double* __restrict__ Ub) {
+  using S = Shape<DIM, N>;
+  constexpr int Nn = S::Nn, Nt = S::Nt, BLOCK = S::BLOCK;
+  __shared__ double shR[5][BLOCK];
+  __shared__ double shW[5][BLOCK];
+  __shared__ double shD[N * N];
+  const int tid = threadIdx.x;
+  if (tid < N * N) shD[tid] = p.Dhat[tid];
+  const int le = tid / Nn, li = tid - le * Nn;
+  const long long e = (long long)blockIdx.x * S::EPB + le;
+  const bool valid = e < p.E;
+  const long long tot = p.E * Nn;
+  const long long g = e * Nn + li;
+  if (valid) {
+#pragma unroll
+    for (int v = 0; v < 5; ++v) {
+      shR[v][tid] = Rb[v * tot + g];
+      shW[v][tid] = Wst[v * tot + g];
+    }
+  }
+  __syncthreads();
+  if (!valid) return;
+  int ijk[3];
+  node_ijk<DIM, N>(li, ijk);
+  // transposed volume term: F_bar^d[a] = (2/dx_d) sum_i Dhat[i][a] R_bar[i]
+  double Fb[DIM][5];
+#pragma unroll
+  for (int d = 0; d < DIM; ++d) {
+    const int ns = node_stride<N>(d);
+    const int base = tid - ijk[d] * ns;
+    const double sc = p.inv_half_dx[d];
+#pragma unroll
+    for (int v = 0; v < 5; ++v) Fb[d][v] = 0.0;
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+      const double c = sc * shD[i * N + ijk[d]];
+#pragma unroll
+      for (int v = 0; v < 5; ++v) Fb[d][v] = fma(c, shR[v][base + i * ns], Fb[d][v]);
+    }
+  }
+  // transposed trace extrapolation; the face guard is re-decided exactly as in the forward pass
+  double Wub[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+#pragma unroll
+  for (int d = 0; d < DIM; ++d) {
+    const int t = tan_index<DIM, N>(ijk, d);
+#pragma unroll
+    for (int side = 0; side < 2; ++side) {
+      double rf = 0.0, Pf = 0.0;
+#pragma unroll
+      for (int a = 0; a < N; ++a) {
+        const int node = le * Nn + line_node<DIM, N>(d, t, a);
+        const double c = side ? p.ep[a] : p.em[a];
+        rf = fma(c, shW[0][node], rf);
+        Pf = fma(c, shW[4][node], Pf);
+      }
+      const bool guarded = !(rf > 0.0) || !(Pf > 0.0);
+      const double w = guarded ? ((ijk[d] == (side ? N - 1 : 0)) ? 1.0 : 0.0)
+                               : (side ? p.ep[ijk[d]] : p.em[ijk[d]]);
+      if (w != 0.0) {
+#pragma unroll
+        for (int v = 0; v < 5; ++v)
+          Wub[v] = fma(w, TrB[((((long long)d * 2 + side) * 5 + v) * p.E + e) * Nt + t], Wub[v]);
+      }
+    }
+  }
+  double u[5], Wu[5], out[5];
+#pragma unroll
+  for (int v = 0; v < 5; ++v) {
+    u[v] = U[v * tot + g];
+    Wu[v] = shW[v][tid];
+  }
+  node_adjoint<DIM>(p, u, Wu, Fb, Wub, out);
+#pragma unroll
+  for (int v = 0; v < 5; ++v) Ub[v * tot + g] = out[v];
+}
+
+// ---------------------------------------------------------------------------------------
+// Physicality operator with frozen factors: U~_i = s U_i + (1 - s) mean(U), so
+// U_bar_i = s Ut_bar_i + (1 - s) (w_i / sum w) sum_j Ut_bar_j.
+// ---------------------------------------------------------------------------------------
+template <int DIM, int N>
+__global__ void __launch_bounds__(Shape<DIM, N>::BLOCK)
+    enforce_vjp_kernel(Params p, const double* __restrict__ s, const double* __restrict__ Tb,
+                       double* __restrict__ Ub) {
+  using S = Shape<DIM, N>;
+  constexpr int Nn = S::Nn;
+  __shared__ double sh[5][S::BLOCK];
+  __shared__ double sum[S::EPB][5];
+  const int tid = threadIdx.x;
+  const int le = tid / Nn, li = tid - le * Nn;
+  const long long e = (long long)blockIdx.x * S::EPB + le;
+  const bool valid = e < p.E;
+  const long long tot = p.E * Nn;
+  const long long g = e * Nn + li;
+  double t[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+  const double se = valid ? s[e] : 1.0;
+  if (valid)
+#pragma unroll
+    for (int v = 0; v < 5; ++v) t[v] = Tb[v * tot + g];
+  const bool any = __syncthreads_or(valid && se != 1.0);
+  if (any) {
+#pragma unroll
+    for (int v = 0; v < 5; ++v) sh[v][tid] = t[v];
+    __syncthreads();
+    if (valid && li == 0 && se != 1.0) {
+#pragma unroll
+      for (int v = 0; v < 5; ++v) {
+        double acc = 0.0;
+        for (int j = 0; j < Nn; ++j) acc += sh[v][le * Nn + j];
+        sum[le][v] = acc;
+      }
+    }
+    __syncthreads();
+  }
+  if (!valid) return;
+  if (se == 1.0) {
+#pragma unroll
+    for (int v = 0; v < 5; ++v) Ub[v * tot + g] = t[v];
+    return;
+  }
+  int ijk[3];
+  node_ijk<DIM, N>(li, ijk);
+  double wi = 1.0;
+#pragma unroll
+  for (int d = 0; d < DIM; ++d) wi *= p.w[ijk[d]];
+  const double c = (1.0 - se) * wi / p.wsum;
+#pragma unroll
+  for (int v = 0; v < 5; ++v) Ub[v * tot + g] = se * t[v] + c * sum[le][v];
+}
+
+}  // namespace dgsrhd

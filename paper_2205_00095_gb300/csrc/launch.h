@@ -7,7 +7,7 @@
 
 namespace dgsrhd {
 
-enum class Op { Volume, Face, Update, Enforce, VjpVolume, VjpFace, VjpLift };
+enum class Op { Volume, Face, Update, Enforce, VjpFace, VjpNode, EnforceVjp };
 
 struct StageArgs {
   Op op;
@@ -24,13 +24,16 @@ struct StageArgs {
   double a_n, b_k, dt;
   int mode;            // Update: 0 = write R, 1 = RK stage
   int enforce;
-  int split;           // Volume / Update: split-precision tensor-core contractions
+  int split;           // Volume / Update: split-precision tensor-core contractions (set by the host)
+  int fp64_only;       // force the FP64 kernels whatever the configured precision
   double* s_out;
   // VJP buffers
-  const double* Rbar;
-  double* Ubar;
-  double* TrBar;
-  double* Wstore;
+  const double* Rbar;  // VjpFace / VjpNode: adjoint of R
+  double* Ubar;        // VjpNode / EnforceVjp: output adjoint of U
+  double* TrBar;       // VjpFace output / VjpNode input: adjoints of the face traces
+  double* Wstore;      // Volume: optional output of the nodal (rho, u, P); VjpNode: its input
+  const double* s_in;  // EnforceVjp: smoothing factor per element
+  const double* Tbar;  // EnforceVjp: adjoint of the smoothed state
 };
 
 template <int DIM>
@@ -41,6 +44,10 @@ cudaError_t launch_prim2cons(const Params& p, cudaStream_t s, long long n, const
                              double* U);
 cudaError_t launch_con2prim(const Params& p, cudaStream_t s, long long n, const double* U,
                             double* W, int* iters);
+cudaError_t launch_stage_combine(cudaStream_t s, long long n, const double* Yb, const double* Vb,
+                                 double a_n, double b_k, double dt, double* Unb, double* Ukb);
+cudaError_t launch_con2prim_vjp(const Params& p, cudaStream_t s, long long n, const double* U,
+                                const double* Wb, double* Ub);
 
 }  // namespace dgsrhd
 

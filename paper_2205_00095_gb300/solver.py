@@ -134,6 +134,40 @@ class Solver:
             _dev_ptr(Ub, "U_bar", self.shape)))
         return Ub
 
+    def stage_save_size(self) -> int:
+        n = ctypes.c_int64()
+        check("dgsrhd_stage_save_size", self.lib.dgsrhd_stage_save_size(self.ctx, ctypes.byref(n)))
+        return n.value
+
+    def step_stage(self, Un: torch.Tensor, Uk: torch.Tensor, Uout: torch.Tensor, stage: int,
+                   dt: float, s_out: torch.Tensor | None = None,
+                   save: torch.Tensor | None = None) -> torch.Tensor:
+        if save is not None and (not save.is_cuda or save.dtype != torch.float64 or
+                                 save.numel() < self.stage_save_size()):
+            raise ValueError("save must be a float64 CUDA tensor of stage_save_size() doubles")
+        check("dgsrhd_step_stage", self.lib.dgsrhd_step_stage(
+            self.ctx, _dev_ptr(Un, "Un", self.shape), _dev_ptr(Uk, "Uk", self.shape),
+            _dev_ptr(Uout, "Uout", self.shape), int(stage), float(dt),
+            s_out.data_ptr() if s_out is not None else None,
+            save.data_ptr() if save is not None else None))
+        return Uout
+
+    def stage_vjp(self, Uk: torch.Tensor, s: torch.Tensor | None, Z_bar: torch.Tensor,
+                  Un_bar: torch.Tensor, Uk_bar: torch.Tensor, stage: int, dt: float,
+                  saved: torch.Tensor | None = None):
+        check("dgsrhd_stage_vjp", self.lib.dgsrhd_stage_vjp(
+            self.ctx, _dev_ptr(Uk, "Uk", self.shape), s.data_ptr() if s is not None else None,
+            saved.data_ptr() if saved is not None else None,
+            _dev_ptr(Z_bar, "Z_bar", self.shape), _dev_ptr(Un_bar, "Un_bar", self.shape),
+            _dev_ptr(Uk_bar, "Uk_bar", self.shape), int(stage), float(dt)))
+
+    def con2prim_vjp(self, U: torch.Tensor, W_bar: torch.Tensor, out: torch.Tensor | None = None):
+        Ub = self.empty() if out is None else out
+        check("dgsrhd_con2prim_vjp", self.lib.dgsrhd_con2prim_vjp(
+            self.ctx, _dev_ptr(U, "U", self.shape), _dev_ptr(W_bar, "W_bar", self.shape),
+            _dev_ptr(Ub, "U_bar", self.shape)))
+        return Ub
+
     def cfl_dt(self, cfl: float | None = None) -> float:
         dt = ctypes.c_double()
         check("dgsrhd_cfl_dt", self.lib.dgsrhd_cfl_dt(self.ctx, float(cfl or self.spec.get("cfl", 0.2)),

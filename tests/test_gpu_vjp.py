@@ -1,0 +1,205 @@
+"""The hand-written vector-Jacobian products (through the C ABI) against central finite
+differences of the FP64 oracle: the RHS, con2prim, the frozen-factor physicality operator, and
+the gradient of the transverse kinetic energy after a checkpointed SSPRK3 rollout of the
+Kelvin-Helmholtz set-up with respect to the perturbation amplitude and the nodal initial v_x.
+Tolerance: 1e-6 relative (central differences with h = 1e-6)."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+
+def dev(a):
+    t = torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).cuda()
+    torch.cuda.synchronize()
+    return t
+
+
+def solver(spec):
+    from paper_2205_00095_gb300 import Solver
+    return Solver(spec)  # default stream
+
+
+VJP_CASES = [
+    (1, [9], 2, "ideal", "llf", [("dirichlet", "outflow")], "iterative"),
+    (1, [7], 3, "tm", "hll", None, "analytic"),
+    (2, [5, 4], 3, "tm", "hll", None, "iterative"),
+    (2, [4, 5], 1, "ideal", "llf", [("outflow", "outflow"), ("periodic", "periodic")], "analytic"),
+    (2, [4, 3], 4, "ideal", "hll", None, "iterative"),
+    (3, [3, 3, 2], 2, "tm", "llf", None, "iterative"),
+]
+
+
+@pytest.mark.parametrize("dim,n,degree,eos,flux,bc,c2p", VJP_CASES)
+def test_rhs_vjp_against_oracle_differences(gpu_lib, dim, n, degree, eos, flux, bc, c2p):
+    spec = wl.smooth_random(dim, n, degree, eos=eos, flux=flux, c2p=c2p, seed=3, bc=bc)
+    X = oracle.node_coords(spec)
+    W = wl.smooth_random_ic(spec, X)
+    Uo = oracle.prim2cons(spec, W)
+    rng = np.random.default_rng(7)
+    V = rng.normal(size=Uo.shape) * np.abs(Uo).mean(axis=(1, 2), keepdims=True)
+    Rb = rng.normal(size=Uo.shape)
+    h = 1e-6
+    Rp, _ = oracle.rhs(spec, Uo + h * V)
+    Rm, _ = oracle.rhs(spec, Uo - h * V)
+    fd = float((Rb * (Rp - Rm) / (2 * h)).sum())
+    s = solver(spec)
+    U = s.initial_state(W)
+    Ub = s.rhs_vjp(U, dev(Rb))
+    torch.cuda.synchronize()
+    got = float((Ub.cpu().numpy() * V).sum())
+    assert abs(got - fd) <= 1e-6 * abs(fd), (got, fd)
+
+
+@pytest.mark.parametrize("eos,c2p", [("ideal", "analytic"), ("ideal", "iterative"),
+                                     ("tm", "analytic"), ("tm", "iterative")])
+def test_con2prim_vjp_against_oracle_differences(gpu_lib, eos, c2p):
+    n = 200
+    spec = dict(dim=1, degree=0, n_elem=[n], eos=eos, gamma_ad=4.0 / 3.0, c2p=c2p)
+    W = wl.random_primitive_states(n, seed=9, gamma_max=5.0, theta_range=(1e-2, 1e2),
+                                   rho_range=(0.1, 10.0))[:, :, None]
+    Uo = oracle.prim2cons(spec, W)
+    rng = np.random.default_rng(2)
+    V = rng.normal(size=Uo.shape) * np.abs(Uo)
+    Wb = rng.normal(size=Uo.shape)
+    h = 1e-6
+    # The adjoint is the derivative of the exact inverse of prim->cons, whichever solver finds
+    # it; differences of the closed-form ideal solver are dominated by its rounding (Sec. 3.3:
+    # up to 1e-10 relative), so the ideal case is differenced with the Newton solver.
+    fd_spec = dict(spec, c2p="iterative") if eos == "ideal" else spec
+    Wp, _, _ = oracle.con2prim(fd_spec, Uo + h * V)
+    Wm, _, _ = oracle.con2prim(fd_spec, Uo - h * V)
+    fd = (Wb * (Wp - Wm) / (2 * h)).sum(axis=0)[:, 0]
+    s = solver(spec)
+    Ub = s.con2prim_vjp(dev(Uo), dev(Wb)).cpu().numpy()
+    got = (Ub * V).sum(axis=0)[:, 0]
+    assert np.all(np.abs(got - fd) <= 1e-6 * np.maximum(np.abs(fd), 1e-3 * np.abs(fd).max())), \
+        np.abs(got - fd).max()
+
+
+def test_enforce_vjp_is_the_transpose_of_the_frozen_operator(gpu_lib):
+    """With each element's factor s frozen the operator is the linear map
+    V -> s V + (1 - s) mean(V) (Eq. smoothed_states); its transpose must satisfy
+    <Z, L_s V> = <L_s^T Z, V>."""
+    spec = dict(dim=2, degree=3, n_elem=[12, 10], eos="ideal", gamma_ad=5.0 / 3.0)
+    E, Nn = wl.shape(spec)
+    U = wl.random_conserved_cells(E, Nn, seed=4)
+    s = solver(spec)
+    _, sf = s.enforce(dev(U), with_s=True)
+    sf_np = sf.cpu().numpy()
+    assert np.any(sf_np < 1.0) and np.any(sf_np == 1.0)
+    rng = np.random.default_rng(5)
+    V = rng.normal(size=U.shape)
+    Z = rng.normal(size=U.shape)
+    w1 = np.polynomial.legendre.leggauss(4)[1]
+    w = np.multiply.outer(w1, w1).ravel()
+    mean = (V * w).sum(-1, keepdims=True) / w.sum()
+    LV = sf_np[None, :, None] * V + (1 - sf_np[None, :, None]) * mean
+    LTZ = s.enforce_vjp(sf, dev(Z)).cpu().numpy()
+    lhs, rhs = float((Z * LV).sum()), float((LTZ * V).sum())
+    assert abs(lhs - rhs) <= 1e-12 * abs(lhs)
+
+
+def oracle_objective(spec, A, vx_dir=None, eps=0.0, nsteps=10):
+    X = oracle.node_coords(spec)
+    W = wl.kh2d_ic(spec, X, amplitude=A)
+    if vx_dir is not None:
+        W[1] += eps * vx_dir
+    U = oracle.prim2cons(spec, W)
+    U, st = oracle.step(spec, U, spec["dt"], nsteps)
+    assert st["enforced_cells"] == 0 and st["c2p_invalid_input"] == 0
+    Wf, _, _ = oracle.con2prim(spec, U)
+    g2 = 1.0 / (1.0 - (Wf[1:4] ** 2).sum(0))
+    N = spec["degree"] + 1
+    w1 = np.polynomial.legendre.leggauss(N)[1]
+    w = np.multiply.outer(w1, w1).ravel()
+    jac = (spec["hi"][0] - spec["lo"][0]) / spec["n_elem"][0] / 2 * (spec["hi"][1] - spec["lo"][1]) / spec["n_elem"][1] / 2
+    return float((w * jac * Wf[0] * g2 * Wf[2] ** 2).sum())
+
+
+def test_checkpointed_rollout_gradient_against_oracle_differences(gpu_lib):
+    from paper_2205_00095_gb300 import adjoint
+
+    spec = wl.kh2d(nx=8, ny=16, degree=3)
+    s = solver(spec)
+    spec["dt"] = s.cfl_dt(0.2)
+    nsteps, every, A = 10, 4, 0.01
+    X = s.node_coords()
+    W0 = wl.kh2d_ic(spec, X, amplitude=A)
+    U0 = s.initial_state(W0).requires_grad_(True)
+    UT = adjoint.rollout(s, U0, spec["dt"], nsteps, every)
+    J = adjoint.transverse_kinetic_energy(s, UT)
+    J.backward()
+    torch.cuda.synchronize()
+    Ubar0 = U0.grad.cpu().numpy()
+    status, st = s.stats()
+    assert st["enforced_cells"] == 0
+
+    # forward objective agrees with the oracle
+    assert abs(float(J) - oracle_objective(spec, A, nsteps=nsteps)) <= 1e-11 * abs(float(J))
+
+    def tangent(dW):
+        h = 1e-6
+        Up = s.initial_state(W0 + h * dW).cpu().numpy()
+        Um = s.initial_state(W0 - h * dW).cpu().numpy()
+        return (Up - Um) / (2 * h)
+
+    # d J / d A: the amplitude enters through v_y only
+    dW = np.zeros_like(W0)
+    dW[2] = wl.kh2d_ic(spec, X, amplitude=1.0)[2]
+    g_adj = float((Ubar0 * tangent(dW)).sum())
+    hA = 1e-6 * A
+    g_fd = (oracle_objective(spec, A + hA, nsteps=nsteps) - oracle_objective(spec, A - hA, nsteps=nsteps)) / (2 * hA)
+    assert abs(g_adj - g_fd) <= 1e-6 * abs(g_fd), (g_adj, g_fd)
+
+    # nodal initial v_x: individual nodes and random directions
+    rng = np.random.default_rng(11)
+    E, Nn = s.n_elem, s.n_node
+    dirs = []
+    for flat in rng.choice(E * Nn, size=6, replace=False):
+        d = np.zeros((E, Nn))
+        d.flat[flat] = 1.0
+        dirs.append(d)
+    dirs += [rng.normal(size=(E, Nn)) for _ in range(2)]
+    for d in dirs:
+        dWx = np.zeros_like(W0)
+        dWx[1] = d
+        g_adj = float((Ubar0 * tangent(dWx)).sum())
+        eps = 1e-6
+        g_fd = (oracle_objective(spec, A, d, eps, nsteps) - oracle_objective(spec, A, d, -eps, nsteps)) / (2 * eps)
+        # floor: the rounding of J (a sum over ~2000 nodes) divided by 2 eps
+        floor = 1e-8 * abs(float(J))
+        assert abs(g_adj - g_fd) <= 1e-6 * abs(g_fd) + floor, (g_adj, g_fd)
+
+
+def test_stage_vjp_with_saved_forward_equals_recompute(gpu_lib):
+    """dgsrhd_stage_vjp on the quantities kept by dgsrhd_step_stage gives the same adjoint as the
+    version that re-runs the forward volume kernel, and the stages compose to dgsrhd_step."""
+    spec = wl.kh2d(nx=8, ny=8, degree=2)
+    s = solver(spec)
+    U = s.initial_state(wl.kh2d_ic(spec, s.node_coords()))
+    dt = s.cfl_dt(0.2)
+    ref = U.clone()
+    s.step(ref, dt, 1)
+    X1 = torch.empty_like(U)
+    X2 = torch.empty_like(U)
+    out = torch.empty_like(U)
+    saves = [torch.empty(s.stage_save_size(), dtype=torch.float64, device="cuda") for _ in range(3)]
+    ss = [torch.empty(s.n_elem, dtype=torch.float64, device="cuda") for _ in range(3)]
+    s.step_stage(U, U, X1, 0, dt, ss[0], saves[0])
+    s.step_stage(U, X1, X2, 1, dt, ss[1], saves[1])
+    s.step_stage(U, X2, out, 2, dt, ss[2], saves[2])
+    torch.cuda.synchronize()
+    assert torch.equal(out, ref)
+    Z = torch.from_numpy(np.random.default_rng(1).normal(size=U.shape)).cuda()
+    for k, Xk in enumerate((U, X1, X2)):
+        a_un, a_uk = torch.zeros_like(U), torch.zeros_like(U)
+        b_un, b_uk = torch.zeros_like(U), torch.zeros_like(U)
+        s.stage_vjp(Xk, ss[k], Z, a_un, a_uk, k, dt, saves[k])
+        s.stage_vjp(Xk, ss[k], Z, b_un, b_uk, k, dt, None)
+        torch.cuda.synchronize()
+        assert torch.equal(a_un, b_un) and torch.equal(a_uk, b_uk)
