@@ -3,7 +3,8 @@ vector-Jacobian products.
 
 * ``rhs(solver, U)``: R = dU/dt with ``dgsrhd_rhs_vjp`` as its backward.
 * ``rollout(solver, U0, dt, nsteps, every)``: nsteps SSP-RK steps; the backward keeps only a
-  checkpoint every ``every`` steps from the forward pass, recomputes each segment stage by stage
+  checkpoint every ``every`` steps from the forward pass (whose last segment is run stage by
+  stage and kept whole), recomputes each earlier segment stage by stage
   (``dgsrhd_step_stage``, which also returns the physicality operator's factors and keeps the
   nodal primitives and face traces of each stage) and runs the stages' reverse sweeps
   (``dgsrhd_stage_vjp``, factors frozen at their forward values).
@@ -58,20 +59,51 @@ def rhs(solver: Solver, U: torch.Tensor) -> torch.Tensor:
     return _RHS.apply(U, solver)
 
 
+def _run_segment(solver: Solver, U: torch.Tensor, dt: float, nseg: int, stages: int, nsave: int):
+    """nseg steps stage by stage from U, keeping every stage input, operator factor and the
+    forward quantities (nodal primitives, face traces) of each stage's RHS; returns the end
+    state and the kept data."""
+    X, S, SV = [], [], []
+    cur = U
+    for _ in range(nseg):
+        xs, ss, sv = [cur], [], []
+        for k in range(stages):
+            out = torch.empty_like(cur)
+            sk = torch.empty(solver.n_elem, dtype=torch.float64, device=cur.device)
+            save = torch.empty(nsave, dtype=torch.float64, device=cur.device)
+            solver.step_stage(xs[0], xs[k], out, k, dt, sk, save)
+            ss.append(sk)
+            sv.append(save)
+            if k < stages - 1:
+                xs.append(out)
+        X.append(xs)
+        S.append(ss)
+        SV.append(sv)
+        cur = out
+    return cur, (X, S, SV)
+
+
 class _Rollout(torch.autograd.Function):
     @staticmethod
     def forward(ctx, U0, solver, dt, nsteps, every):
+        stages = int(solver.spec.get("rk_stages", 3))
+        nsave = solver.stage_save_size()
         checkpoints = []
         with _OnSolverStream(solver):
             U = U0.detach().clone()
             done = 0
+            last = None
             while done < nsteps:
                 n = min(every, nsteps - done)
                 checkpoints.append((done, U.clone()))
-                solver.step(U, dt, n)
+                if done + n < nsteps:
+                    solver.step(U, dt, n)
+                else:  # the last segment keeps its stage data: no recompute needed for it
+                    U, last = _run_segment(solver, U, dt, n, stages, nsave)
                 done += n
         ctx.solver, ctx.dt, ctx.nsteps = solver, dt, nsteps
         ctx.checkpoints = checkpoints
+        ctx.last = last
         return U
 
     @staticmethod
@@ -86,25 +118,11 @@ class _Rollout(torch.autograd.Function):
             for seg in reversed(range(len(ctx.checkpoints))):
                 start, U = ctx.checkpoints[seg]
                 nseg = bounds[seg + 1] - start
-                # recompute the segment, keeping every stage input, operator factor and the
-                # forward quantities (nodal primitives, face traces) of each stage's RHS
-                X, S, SV = [], [], []
-                cur = U.clone()
-                for _ in range(nseg):
-                    xs, ss, sv = [cur], [], []
-                    for k in range(stages):
-                        out = torch.empty_like(cur)
-                        sk = torch.empty(s.n_elem, dtype=torch.float64, device=cur.device)
-                        save = torch.empty(nsave, dtype=torch.float64, device=cur.device)
-                        s.step_stage(xs[0], xs[k], out, k, dt, sk, save)
-                        ss.append(sk)
-                        sv.append(save)
-                        if k < stages - 1:
-                            xs.append(out)
-                    X.append(xs)
-                    S.append(ss)
-                    SV.append(sv)
-                    cur = out
+                if seg == len(ctx.checkpoints) - 1 and ctx.last is not None:
+                    X, S, SV = ctx.last
+                    ctx.last = None
+                else:
+                    _, (X, S, SV) = _run_segment(s, U.clone(), dt, nseg, stages, nsave)
                 # reverse sweep of the segment
                 for j in reversed(range(nseg)):
                     Unb = torch.zeros_like(Zb)

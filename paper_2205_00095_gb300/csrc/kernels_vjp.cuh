@@ -23,10 +23,10 @@ namespace dgsrhd {
 // ---------------------------------------------------------------------------------------
 struct FaceFwd {
   double Wu[5];
-  double u2, q, ilor, lor, rho_hm1, A, B, sg, Z, K, H, rhoh_lor, den1;
+  double u2, q, ilor, lor, rho_hm1, A, B, sg, isg, Z, iZ, K, H, rhoh_lor, id1;
   double U[5], v[3];
   double F[5];
-  double X, r, i, lm, lp;
+  double X, r, ir, i, lm, lp;
 };
 
 template <int D>
@@ -38,27 +38,30 @@ __device__ __forceinline__ void face_fwd(const Params& p, const double Wu[5], Fa
   f.q = 1.0 + f.u2;
   f.ilor = rsqrt(f.q);
   f.lor = f.q * f.ilor;
+  // reciprocals are formed once here and reused by the reverse sweep
   if (p.eos == 0) {
     f.rho_hm1 = p.alpha * P;
     f.A = p.gamma_ad * P;
     f.B = f.q * (rho + f.rho_hm1 - f.A);
-    f.sg = f.Z = f.K = 0.0;
+    f.sg = f.isg = f.Z = f.iZ = f.K = 0.0;
   } else {
     f.sg = sqrt(P * P + (4.0 / 9.0) * rho * rho);
+    f.isg = 1.0 / f.sg;
     f.Z = f.sg + (2.0 / 3.0) * rho;
-    f.rho_hm1 = 2.5 * P + 1.5 * P * P / f.Z;
+    f.iZ = 1.0 / f.Z;
+    f.rho_hm1 = 2.5 * P + 1.5 * P * P * f.iZ;
     f.A = P * (3.0 * P + 5.0 * f.sg);
     f.K = 12.0 * P * (P + f.sg) + 2.0 * rho * rho - f.A;
     f.B = f.q * f.K;
   }
   f.H = rho + f.rho_hm1;
   f.rhoh_lor = f.H * f.lor;
-  f.den1 = f.lor + 1.0;
+  f.id1 = 1.0 / (f.lor + 1.0);
   f.U[0] = f.lor * rho;
   f.U[1] = f.rhoh_lor * Wu[1];
   f.U[2] = f.rhoh_lor * Wu[2];
   f.U[3] = f.rhoh_lor * Wu[3];
-  f.U[4] = f.U[0] * f.u2 / f.den1 + f.q * f.rho_hm1 - P;
+  f.U[4] = f.U[0] * f.u2 * f.id1 + f.q * f.rho_hm1 - P;
   f.v[0] = Wu[1] * f.ilor;
   f.v[1] = Wu[2] * f.ilor;
   f.v[2] = Wu[3] * f.ilor;
@@ -71,6 +74,7 @@ __device__ __forceinline__ void face_fwd(const Params& p, const double Wu[5], Fa
   f.F[4] = (f.U[4] + P) * vd;
   f.X = f.A * (f.B * (1.0 - vd * vd) + f.A);
   f.r = sqrt(f.X);
+  f.ir = f.r > 0.0 ? 1.0 / f.r : 0.0;
   f.i = 1.0 / (f.A + f.B);
   f.lm = (vd * f.B - f.r) * f.i;
   f.lp = (vd * f.B + f.r) * f.i;
@@ -89,7 +93,7 @@ __device__ __forceinline__ void face_rev(const Params& p, const FaceFwd& f, cons
   double Bb = (lmb + lpb) * vd * f.i - ib * f.i * f.i;
   double Ab = -ib * f.i * f.i;
   const double rb = (lpb - lmb) * f.i;
-  const double Xb = f.r > 0.0 ? rb / (2.0 * f.r) : 0.0;
+  const double Xb = 0.5 * rb * f.ir;
   Ab += Xb * (f.B * (1.0 - vd * vd) + 2.0 * f.A);
   Bb += Xb * f.A * (1.0 - vd * vd);
   vdb += Xb * f.A * f.B * (-2.0 * vd);
@@ -104,9 +108,9 @@ __device__ __forceinline__ void face_rev(const Params& p, const FaceFwd& f, cons
   ub[D] = vdb * f.ilor;
   double ilorb = vdb * f.Wu[1 + D];
   // tau = D u2/(gamma + 1) + q rho(h-1) - P
-  Db += taub * f.u2 / f.den1;
-  double u2b = taub * f.U[0] / f.den1;
-  double lorb = -taub * f.U[0] * f.u2 / (f.den1 * f.den1);
+  Db += taub * f.u2 * f.id1;
+  double u2b = taub * f.U[0] * f.id1;
+  double lorb = -taub * f.U[0] * f.u2 * f.id1 * f.id1;
   double qb = taub * f.rho_hm1;
   double rhm1b = taub * f.q;
   Pb -= taub;
@@ -138,15 +142,15 @@ __device__ __forceinline__ void face_rev(const Params& p, const FaceFwd& f, cons
     Ab -= Kb;
     Pb += Ab * (6.0 * P + 5.0 * f.sg);
     sgb += Ab * 5.0 * P;
-    Pb += rhm1b * (2.5 + 3.0 * P / f.Z);
-    const double Zb = -rhm1b * 1.5 * P * P / (f.Z * f.Z);
+    Pb += rhm1b * (2.5 + 3.0 * P * f.iZ);
+    const double Zb = -rhm1b * 1.5 * P * P * f.iZ * f.iZ;
     sgb += Zb;
     rhob += Zb * (2.0 / 3.0);
-    Pb += sgb * P / f.sg;
-    rhob += sgb * (4.0 / 9.0) * rho / f.sg;
+    Pb += sgb * P * f.isg;
+    rhob += sgb * (4.0 / 9.0) * rho * f.isg;
   }
   // gamma = q^(1/2), 1/gamma = q^(-1/2), q = 1 + u2
-  qb += lorb * 0.5 * f.ilor - ilorb * 0.5 * f.ilor / f.q;
+  qb += 0.5 * f.ilor * (lorb - ilorb * f.ilor * f.ilor);
   u2b += qb;
   Wb[0] = rhob;
   Wb[1] = ub[0] + 2.0 * f.Wu[1] * u2b;
