@@ -115,20 +115,35 @@ class ClockSampler:
 # ----------------------------------------------------------------------------------------
 # algorithmic work (per DOF update, p = 3, 2D) used for the roofline of the volume kernel
 # ----------------------------------------------------------------------------------------
-def volume_kernel_flops_per_node(spec: dict) -> float:
-    """FP64 operations of the volume kernel per node (add/mul = 1, fma = 2, div/sqrt and each
-    transcendental call = 1), counted from the method's arithmetic:
-      con2prim (closed-form ideal quartic): xi, eta, the quartic coefficients, the resolvent,
-      Cardano's root, the two square-root factorisations and the recovery of rho, v, P;
-      nodal flux 5 products + 2 sums per direction; volume term 2 N flops per variable and
-      direction; face traces 2 N flops per variable per face point (2 dim N^(dim-1) points per
-      N^dim nodes)."""
+# Algorithmic FP64 operations per node of the volume kernel, counted from the method's arithmetic
+# as the oracle writes it (add, sub, mul, div = 1; fma = 2; sqrt, cbrt and other library calls
+# = 1 each; comparisons not counted):
+#   con2prim, closed-form ideal quartic:    12 (xi, eta, admissibility) + 87 (quartic
+#       coefficients, resolvent cubic, Cardano root, two quadratic factors) + 21 (rho, v, P)
+#   con2prim, Newton on the Riccardi quartic: 12 + 20 (series start) + 19 per iteration
+#       (Horner value and derivative, step) + 17 (rho, v, P)
+#   con2prim, Taub-Matthews cubic closed form: 12 + 25 (coefficients) + 16 (Cardano) + 24
+#   con2prim, Taub-Matthews Brent: 12 + 25 + 14 per iteration (cubic value 6, interpolation 8)
+#       + 24
+#   nodal flux 7 per axis; volume term 2 N 5 per axis (pre-scaled Dhat); face traces 2 N 5 per
+#   face point, 2 dim N^(dim-1) face points per N^dim nodes.
+C2P_FLOPS = {
+    ("ideal", "analytic"): lambda it: 120.0,
+    ("ideal", "iterative"): lambda it: 12.0 + 20.0 + 19.0 * it + 17.0,
+    ("tm", "analytic"): lambda it: 12.0 + 25.0 + 16.0 + 24.0,
+    ("tm", "iterative"): lambda it: 12.0 + 25.0 + 14.0 * it + 24.0,
+}
+
+
+def volume_kernel_flops_per_node(spec: dict, mean_iters: float = 0.0) -> float:
     d, N = spec["dim"], spec["degree"] + 1
-    c2p = {"analytic": 95.0, "iterative": 60.0 + 6 * 18.0}[spec["c2p"] if spec["c2p"] != "default" else "analytic"]
+    c2p = spec["c2p"]
+    if c2p == "default":
+        c2p = "analytic" if spec["eos"] == "ideal" else "iterative"
     flux = 7.0 * d
-    volume = 2.0 * N * 5 * d + 5 * d
-    traces = (2 * d * N ** (d - 1) / N ** d) * 5 * 2.0 * N
-    return c2p + flux + volume + traces
+    volume = 2.0 * N * 5 * d
+    traces = (2.0 * d * N ** (d - 1) / N ** d) * 5 * 2.0 * N
+    return C2P_FLOPS[(spec["eos"], c2p)](mean_iters) + flux + volume + traces
 
 
 def measured_traffic(kernel: str, workload_name: str):
@@ -369,13 +384,15 @@ def ours(args, rank, world, local_rank):
     avg_s = dom_ms / max(dom_n, 1) * 1e-3
     roofline = None
     if dom == "volume":
-        flops = volume_kernel_flops_per_node(spec) * ndof
+        mean_it = st["c2p_iters_total"] / max(st["c2p_calls"], 1)
+        fpn = volume_kernel_flops_per_node(spec, mean_it)
+        flops = fpn * ndof
         achieved = flops / avg_s / 1e12
         roofline = {"kernel": "volume_kernel", "bound": "alu", "achieved": achieved,
                     "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
                     "traffic": measured_traffic("volume_kernel", args.workload),
                     "peak_source": "GB300 nominal dense FP64 1.25 TFLOP/s (DFMA probe measured 1.256)",
-                    "algorithmic_flops_per_node": volume_kernel_flops_per_node(spec),
+                    "algorithmic_flops_per_node": fpn,
                     "avg_launch_ms": avg_s * 1e3}
     else:
         roofline = {"kernel": dom, "bound": "alu", "achieved": None, "peak": FP64_PEAK_TFLOPS,

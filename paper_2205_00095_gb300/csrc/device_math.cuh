@@ -67,21 +67,6 @@ __device__ __forceinline__ bool admissible(const double U[5]) {
   return admissible_parts(U[0], U[1] * U[1] + U[2] * U[2] + U[3] * U[3], U[4]);
 }
 
-// Cube root: FP32 reciprocal cube root as the seed, two division-free Newton steps in FP64 on
-// r = a^(-1/3) (r <- r + r (1 - a r^3) / 3, quadratic convergence from ~1e-7), then a r^2.
-// Arguments outside the FP32-normal range use the library cube root.
-__device__ __forceinline__ double cbrt_newton(double a) {
-  const double aa = fabs(a);
-  if (!(aa > 1e-30 && aa < 1e30)) return cbrt(a);
-  double r = (double)rcbrtf((float)aa);
-#pragma unroll
-  for (int k = 0; k < 2; ++k) {
-    const double e = fma(-aa * r, r * r, 1.0);
-    r = fma(r * (1.0 / 3.0), e, r);
-  }
-  return copysign(aa * r * r, a);
-}
-
 // ---------------------------------------------------------------------------------------
 // Conserved -> primitive (Sec. 3).  xi = |S|/D, eta = E/D.
 // ---------------------------------------------------------------------------------------
@@ -107,7 +92,7 @@ __device__ __forceinline__ double beta_ideal_closed_form(double G, double xi, do
     x = 2.0 * pow(R * R - T, 1.0 / 6.0) * cos(atan2(sqrt(-T), R) * (1.0 / 3.0)) - i1 * (1.0 / 3.0);
   } else {
     const double sT = sqrt(T);
-    x = cbrt_newton(R + sT) + cbrt_newton(R - sT) - i1 * (1.0 / 3.0);
+    x = cbrt(R + sT) + cbrt(R - sT) - i1 * (1.0 / 3.0);
   }
   const double B = 0.5 * (a3 + sqrt(a3 * a3 - 4.0 * a2 + 4.0 * x));
   const double C = 0.5 * (x - sqrt(x * x - 4.0 * a0));
@@ -199,7 +184,7 @@ __device__ __forceinline__ double W_tm_closed_form(double xi, double eta) {
     W = 2.0 * sqrt(-Q) * cos(iota * (1.0 / 3.0)) - c.c1 * (1.0 / 3.0);
   } else {
     const double sd = sqrt(d);
-    W = -c.c1 * (1.0 / 3.0) + cbrt_newton(R + sd) + cbrt_newton(R - sd);
+    W = -c.c1 * (1.0 / 3.0) + cbrt(R + sd) + cbrt(R - sd);
   }
   return fmax(W, 0.0);
 }

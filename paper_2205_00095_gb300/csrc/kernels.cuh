@@ -122,10 +122,10 @@ __global__ void __launch_bounds__(Shape<DIM, N>::BLOCK)
   constexpr int Nn = S::Nn, Nt = S::Nt, BLOCK = S::BLOCK;
   __shared__ double shF[DIM][5][BLOCK];
   __shared__ double shW[5][BLOCK];
-  __shared__ double shD[N * N];
+  __shared__ double shD[DIM][N * N];  // (2/dx_d) Dhat per axis
   __shared__ int shred[4 * 32];
   const int tid = threadIdx.x;
-  if (tid < N * N) shD[tid] = p.Dhat[tid];
+  if (tid < DIM * N * N) shD[tid / (N * N)][tid % (N * N)] = p.inv_half_dx[tid / (N * N)] * p.Dhat[tid % (N * N)];
   const int le = tid / Nn, li = tid - le * Nn;
   const long long e = (long long)blockIdx.x * S::EPB + le;
   const bool valid = e < p.E;
@@ -166,10 +166,9 @@ __global__ void __launch_bounds__(Shape<DIM, N>::BLOCK)
     for (int d = 0; d < DIM; ++d) {
       const int ns = node_stride<N>(d);
       const int base = tid - ijk[d] * ns;
-      const double sc = p.inv_half_dx[d];
 #pragma unroll
       for (int a = 0; a < N; ++a) {
-        const double c = sc * shD[ijk[d] * N + a];
+        const double c = shD[d][ijk[d] * N + a];
 #pragma unroll
         for (int v = 0; v < 5; ++v) acc[v] = fma(c, shF[d][v][base + a * ns], acc[v]);
       }
@@ -380,11 +379,12 @@ __global__ void __launch_bounds__(Shape<DIM, N>::BLOCK)
   using S = Shape<DIM, N>;
   constexpr int Nn = S::Nn;
   __shared__ EnforceShared<DIM, N> sh;
-  __shared__ double shl[2][N];
+  __shared__ double shl[DIM][2][N];  // (2/dx_d) phi_i(-+1)/w_i per axis
   const int tid = threadIdx.x;
-  if (tid < N) {
-    shl[0][tid] = p.lm[tid];
-    shl[1][tid] = p.lp[tid];
+  if (tid < DIM * N) {
+    const int d = tid / N, i = tid % N;
+    shl[d][0][i] = p.inv_half_dx[d] * p.lm[i];
+    shl[d][1][i] = p.inv_half_dx[d] * p.lp[i];
   }
   __syncthreads();
   const int le = tid / Nn, li = tid - le * Nn;
@@ -405,8 +405,8 @@ __global__ void __launch_bounds__(Shape<DIM, N>::BLOCK)
       const long long nf = p.nface[d];
       const double* fs = Fs + p.fs_off[d];
       const long long flo = e, fhi = high_face(p, e, d);
-      const double cp = p.inv_half_dx[d] * shl[1][ijk[d]];
-      const double cm = p.inv_half_dx[d] * shl[0][ijk[d]];
+      const double cp = shl[d][1][ijk[d]];
+      const double cm = shl[d][0][ijk[d]];
 #pragma unroll
       for (int v = 0; v < 5; ++v) {
         const double Fhi = fs[(v * nf + fhi) * S::Nt + t];
@@ -421,7 +421,7 @@ __global__ void __launch_bounds__(Shape<DIM, N>::BLOCK)
 #pragma unroll
       for (int v = 0; v < 5; ++v) {
         const double x = fma(dt, R[v], Uk[v * tot + g]);
-        u[v] = (a_n != 0.0) ? fma(a_n, Un[v * tot + g], b_k * x) : b_k * x;
+        u[v] = (a_n != 0.0) ? fma(a_n, Un[v * tot + g], b_k * x) : (b_k == 1.0 ? x : b_k * x);
       }
     }
   }
