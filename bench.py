@@ -188,7 +188,8 @@ def oracle_sample_spec(spec: dict, target_s: float = 1.0):
     oracle.step(s, U, oracle.cfl_dt(s, 0.2), 1)
     t = time.perf_counter() - t0
     scale = max(1.0, (target_s / max(t, 1e-6)) ** (1.0 / d))
-    s["n_elem"] = [max(2, int(v * scale)) for v in s["n_elem"]]
+    # never larger than the workload itself
+    s["n_elem"] = [min(int(full), max(2, int(v * scale))) for v, full in zip(s["n_elem"], spec["n_elem"])]
     return s
 
 

@@ -237,7 +237,8 @@ struct UpdSmem {
   static constexpr size_t E = 0;                                         // Enf
   static constexpr size_t BL = (sizeof(Enf) + 15) / 16 * 16;             // uint2 [DIM][8][8]
   static constexpr size_t OL = BL + sizeof(uint2) * DIM * 64;            // float [DIM][5][BLOCK]
-  static constexpr size_t TOTAL = OL + sizeof(float) * DIM * 5 * BLOCK;
+  static constexpr size_t FS = OL + sizeof(float) * DIM * 5 * BLOCK;     // uint2 [DIM][2][5][LINES]
+  static constexpr size_t TOTAL = FS + sizeof(uint2) * DIM * 2 * 5 * Q::LINES;
 };
 
 template <int DIM, int N>
@@ -254,6 +255,7 @@ __global__ void __launch_bounds__(SplitShape<DIM, N>::BLOCK)
   typename L::Enf& sh = *reinterpret_cast<typename L::Enf*>(smem + L::E);
   uint2* shBL = reinterpret_cast<uint2*>(smem + L::BL);
   float* outL = reinterpret_cast<float*>(smem + L::OL);
+  uint2* shFs = reinterpret_cast<uint2*>(smem + L::FS);
   const int tid = threadIdx.x;
   // lift coefficients B[k][n]: k = 0 low-face flux (+ (2/dx) phi_n(-1)/w_n),
   // k = 1 high-face flux (- (2/dx) phi_n(+1)/w_n)
@@ -266,27 +268,40 @@ __global__ void __launch_bounds__(SplitShape<DIM, N>::BLOCK)
   }
   __syncthreads();
 
+  // stage the block's face fluxes minus the reference flux, TF32-split, in shared memory:
+  // shFs[d][side][v][line], side 0 = low face, 1 = high face; lines run fastest so that
+  // consecutive threads read consecutive face points
+  for (int j = tid; j < DIM * 2 * 5 * LINES; j += BLOCK) {
+    const int r = j % LINES;
+    const int v = (j / LINES) % 5;
+    const int side = (j / (5 * LINES)) % 2;
+    const int d = j / (10 * LINES);
+    const int lr = r / Nt, t = r - lr * Nt;
+    const long long e = (long long)blockIdx.x * S::EPB + lr;
+    uint2 val = make_uint2(0u, 0u);
+    if (e < p.E) {
+      const long long f = side == 0 ? e : high_face(p, e, d);
+      const double x = Fs[p.fs_off[d] + (v * p.nface[d] + f) * Nt + t] - Fref[((long long)d * 5 + v) * p.E + e];
+      val = as_u2(split_tf32_f64(x));
+    }
+    shFs[j] = val;
+  }
+  __syncthreads();
+
   // lift on tensor cores: rows are the block's lines, k selects the low / high face flux
   const int warp = tid >> 5, lane = tid & 31, gq = lane >> 2, tig = lane & 3;
   constexpr int TASKS = DIM * 5 * Q::TILES;
   for (int task = warp; task < TASKS; task += Q::WARPS) {
     const int d = task / (5 * Q::TILES), v = (task / Q::TILES) % 5, tile = task % Q::TILES;
-    const long long nf = p.nface[d];
-    const double* fs = Fs + p.fs_off[d];
     unsigned ahi[4] = {0u, 0u, 0u, 0u}, alo[4] = {0u, 0u, 0u, 0u};
     if (tig < 2) {  // k = tig in {0, 1}; k = tig + 4 is padding
 #pragma unroll
       for (int rr = 0; rr < 2; ++rr) {
         const int r = tile * 16 + gq + 8 * rr;
         if (r < LINES) {
-          const int lr = r / Nt, t = r - lr * Nt;
-          const long long e = (long long)blockIdx.x * S::EPB + lr;
-          if (e < p.E) {
-            const long long f = tig == 0 ? e : high_face(p, e, d);
-            const Tf32Pair q = split_tf32_f64(fs[(v * nf + f) * Nt + t] - Fref[((long long)d * 5 + v) * p.E + e]);
-            ahi[rr] = q.hi;
-            alo[rr] = q.lo;
-          }
+          const uint2 q = shFs[((d * 2 + tig) * 5 + v) * LINES + r];
+          ahi[rr] = q.x;
+          alo[rr] = q.y;
         }
       }
     }

@@ -305,3 +305,89 @@ def test_full_size_sampled_elements(lib):
         got = Ug[:, ex + 512 * ey, :]
         want = Up1[:, 3 + 7 * 3, :]
         assert np.abs(got - want).max() < 1e-11 * np.abs(want).max()
+
+
+def _sampled_patch_parity(s, spec, U_after, samples, dt, tol=1e-11):
+    """Each sampled element after one SSPRK3 step against the oracle run on the (2 r + 1)^d
+    element patch around it (three stages reach three elements), built from the same workload
+    field with outflow sides."""
+    dim = spec["dim"]
+    n = spec["n_elem"][:dim]
+    h = [(spec["hi"][d] - spec["lo"][d]) / n[d] for d in range(dim)]
+    Ug = U_after
+    for ec in samples:
+        patch = dict(spec, n_elem=[7] * dim,
+                     lo=[spec["lo"][d] + (ec[d] - 3) * h[d] for d in range(dim)],
+                     hi=[spec["lo"][d] + (ec[d] + 4) * h[d] for d in range(dim)],
+                     bc=[("outflow", "outflow")] * dim)
+        Xp = oracle.node_coords(patch)
+        Up = oracle.prim2cons(patch, wl.initial_primitive(spec, Xp))
+        Up1, _ = oracle.step(patch, Up, dt, 1)
+        e = ec[0] + n[0] * (ec[1] + (n[1] * ec[2] if dim > 2 else 0))
+        centre = 3 + 7 * 3 + (49 * 3 if dim > 2 else 0)
+        got, want = Ug[:, e, :], Up1[:, centre, :]
+        assert np.abs(got - want).max() < tol * np.abs(want).max(), (ec, np.abs(got - want).max())
+
+
+def test_full_size_kh2d_sampled_elements(lib):
+    """The 2D Taub-Matthews Kelvin-Helmholtz workload at full size (256 x 512, p = 3, Brent,
+    HLL): one SSPRK3 step, sampled elements against the oracle."""
+    spec = wl.kh2d(nx=256, ny=512, degree=3)
+    s = solver(spec, stream=torch.cuda.Stream())
+    U = gpu_state(s, spec)
+    dt = s.cfl_dt(0.2)
+    s.step(U, dt, 1)
+    s.synchronize()
+    rng = np.random.default_rng(21)
+    samples = [(0, 0), (255, 511), (128, 256), (3, 255)] + [tuple(int(x) for x in rng.integers(0, [256, 512])) for _ in range(4)]
+    _sampled_patch_parity(s, spec, U.cpu().numpy(), samples, dt)
+
+
+def test_full_size_kh3d_sampled_elements(lib):
+    """The 3D high-Lorentz-factor Kelvin-Helmholtz workload at full size (128^3 elements,
+    p = 3, 134M nodes, Brent, HLL): one SSPRK3 step, sampled elements against the oracle."""
+    spec = wl.kh3d(n=128, degree=3)
+    s = solver(spec, stream=torch.cuda.Stream())
+    U = gpu_state(s, spec)
+    dt = s.cfl_dt(0.2)
+    s.step(U, dt, 1)
+    s.synchronize()
+    status, st = s.stats()
+    assert status == 0 and st["c2p_nonconverged"] == 0
+    rng = np.random.default_rng(23)
+    samples = [(0, 32, 0), (127, 96, 127)] + [tuple(int(x) for x in rng.integers(0, 128, 3)) for _ in range(2)]
+    Uc = U.cpu().numpy()
+    del U
+    _sampled_patch_parity(s, spec, Uc, samples, dt)
+
+
+@pytest.mark.parametrize("dim,n,degree", [(1, [1], 3), (2, [1, 6], 2), (2, [5, 1], 4), (3, [1, 2, 1], 2)])
+def test_single_element_periodic_axes(lib, dim, n, degree):
+    """An axis with one element is periodic onto itself: the element is its own neighbour."""
+    spec = wl.smooth_random(dim, n, degree, eos="tm", flux="hll", seed=31)
+    s = solver(spec)
+    R = s.rhs(gpu_state(s, spec)).cpu().numpy()
+    Ro, _ = oracle.rhs(spec, oracle_state(spec))
+    assert rel_inf(R, Ro) < 1e-11
+
+
+@pytest.mark.parametrize("eos,c2p", [("ideal", "analytic"), ("ideal", "iterative"),
+                                     ("tm", "analytic"), ("tm", "iterative")])
+def test_con2prim_zero_and_tiny_momentum(lib, eos, c2p):
+    n = 6
+    W = np.array([[1.0, 2.0, 0.5, 1.0, 1.0, 3.0],
+                  [0.0, 0.0, 0.0, 1e-9, 0.0, 3e-7],
+                  [0.0, 0.0, 0.0, 0.0, -2e-8, 0.0],
+                  [0.0, 0.0, 0.0, 0.0, 0.0, 0.0],
+                  [1.0, 1e-6, 10.0, 1.0, 0.3, 0.2]])[:, :, None]
+    spec = dict(dim=1, degree=0, n_elem=[n], eos=eos, gamma_ad=5.0 / 3.0, c2p=c2p)
+    Uo = oracle.prim2cons(spec, W)
+    s = solver(spec)
+    Wg = s.con2prim(to_dev(Uo)).cpu().numpy()
+    Wo, _, sto = oracle.con2prim(spec, Uo)
+    assert np.all(Wg[1:4, :3] == 0.0)
+    if (eos, c2p) == ("ideal", "analytic"):
+        # the closed form loses its digits as xi -> 0 (finite, but inaccurate); compare rho, P
+        assert np.allclose(Wg[[0, 4], :3], Wo[[0, 4], :3], rtol=1e-14)
+    else:
+        assert np.allclose(Wg, Wo, rtol=1e-12, atol=1e-20)
