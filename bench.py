@@ -240,9 +240,8 @@ def ours(args, rank, world, local_rank):
     spec = make_spec(args.workload, args.c2p)
     stream = torch.cuda.Stream(device=dev)
     s = Solver(spec, stream=stream, device=dev)
-    X = s.node_coords()
     with torch.cuda.stream(stream):
-        U0 = s.initial_state(wl.initial_primitive(spec, X))
+        U0 = s.initial_state(wl.initial_primitive(spec, s.node_coords_device()))
         s.enforce(U0)
         U = U0.clone()
     dt = s.cfl_dt(0.2)
@@ -339,7 +338,7 @@ def ours(args, rank, world, local_rank):
         spec4 = wl.kh2d(nx=128, ny=256, degree=3)
         sa = Solver(spec4, stream=stream, device=dev)
         with torch.cuda.stream(stream):
-            A0 = sa.initial_state(wl.kh2d_ic(spec4, sa.node_coords()))
+            A0 = sa.initial_state(wl.kh2d_ic(spec4, sa.node_coords_device()))
             sa.enforce(A0)
             Af = A0.clone()
         dta = sa.cfl_dt(0.2)

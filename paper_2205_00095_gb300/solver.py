@@ -197,10 +197,19 @@ class Solver:
         return {k: (ms[i], int(cnt[i])) for i, k in enumerate(_lib.KERNEL_KINDS)}
 
     # -- convenience -------------------------------------------------------------------
-    def initial_state(self, W_host: np.ndarray) -> torch.Tensor:
-        """Upload a primitive field (5, n_elem, n_node) and convert it on the device."""
+    def node_coords_device(self) -> torch.Tensor:
+        """Node coordinates as a float64 tensor on the solver's device, shape (dim, E, Nn)."""
         with torch.cuda.stream(self.stream):
-            W = torch.from_numpy(np.ascontiguousarray(W_host, dtype=np.float64)).to(self.device)
+            return torch.from_numpy(self.node_coords()).to(self.device)
+
+    def initial_state(self, W) -> torch.Tensor:
+        """Conserved state from a primitive field (5, n_elem, n_node): a host array is uploaded,
+        a device tensor used in place; prim -> cons runs on the device."""
+        with torch.cuda.stream(self.stream):
+            if isinstance(W, torch.Tensor):
+                W = W.to(self.device, torch.float64).contiguous()
+            else:
+                W = torch.from_numpy(np.ascontiguousarray(W, dtype=np.float64)).to(self.device)
         return self.prim2cons(W)
 
     def synchronize(self):

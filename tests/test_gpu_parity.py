@@ -34,8 +34,8 @@ def rel_inf(got, want):
 
 
 def gpu_state(s, spec):
-    X = s.node_coords()
-    U = s.initial_state(wl.initial_primitive(spec, X))
+    with torch.cuda.stream(s.stream):
+        U = s.initial_state(wl.initial_primitive(spec, s.node_coords_device()))
     s.synchronize()
     return U
 
@@ -386,8 +386,10 @@ def test_con2prim_zero_and_tiny_momentum(lib, eos, c2p):
     Wg = s.con2prim(to_dev(Uo)).cpu().numpy()
     Wo, _, sto = oracle.con2prim(spec, Uo)
     assert np.all(Wg[1:4, :3] == 0.0)
-    if (eos, c2p) == ("ideal", "analytic"):
-        # the closed form loses its digits as xi -> 0 (finite, but inaccurate); compare rho, P
-        assert np.allclose(Wg[[0, 4], :3], Wo[[0, 4], :3], rtol=1e-14)
+    if c2p == "analytic":
+        # the closed forms lose their digits as xi -> 0 (they stay finite); rho and P agree,
+        # the velocity to an absolute 1e-6
+        assert np.allclose(Wg[[0, 4]], Wo[[0, 4]], rtol=1e-12)
+        assert np.allclose(Wg[1:4], Wo[1:4], rtol=0, atol=1e-6)
     else:
         assert np.allclose(Wg, Wo, rtol=1e-12, atol=1e-20)

@@ -18,7 +18,8 @@ def solver(spec, **kw):
 
 
 def gpu_state(s, spec):
-    U = s.initial_state(wl.initial_primitive(spec, s.node_coords()))
+    with torch.cuda.stream(s.stream):
+        U = s.initial_state(wl.initial_primitive(spec, s.node_coords_device()))
     s.synchronize()
     return U
 

@@ -75,49 +75,55 @@ def shape(spec: dict):
 
 
 # --------------------------------------------------------------------------
-# Initial primitive fields W = (rho, vx, vy, vz, P) at given coordinates
+# Initial primitive fields W = (rho, vx, vy, vz, P) at given coordinates.
+# X is a numpy array or a torch tensor (then the field is evaluated where X lives, e.g. on
+# the GPU); the result has the same type, shape (5,) + X.shape[1:].
 # --------------------------------------------------------------------------
 
-def blast_wave_ic(spec: dict, X: np.ndarray) -> np.ndarray:
+def _xp(X):
+    """numpy or torch, whichever holds X (only functions both provide are used)."""
+    if isinstance(X, np.ndarray):
+        return np
+    import torch
+    if isinstance(X, torch.Tensor):
+        return torch
+    raise TypeError(f"coordinates must be a numpy array or a torch tensor, not {type(X)}")
+
+
+def _const(x, c):
+    return x * 0.0 + c
+
+
+def blast_wave_ic(spec: dict, X) -> np.ndarray:
+    xp = _xp(X)
     x = X[0]
-    W = np.empty((5,) + x.shape)
     left, right = spec["left"], spec["right"]
-    for v in range(5):
-        W[v] = np.where(x < 0.5, left[v], right[v])
-    return W
+    return xp.stack([xp.where(x < 0.5, _const(x, left[v]), _const(x, right[v])) for v in range(5)])
 
 
-def advected_wave_ic(spec: dict, X: np.ndarray, t: float = 0.0) -> np.ndarray:
+def advected_wave_ic(spec: dict, X, t: float = 0.0):
     """rho = 1 + 0.5 sin(2 pi (x + y - (vx + vy) t)), v = (0.5, 0.5)/sqrt(2), P = 1."""
+    xp = _xp(X)
     x, y = X[0], X[1]
     vx = vy = 0.5 / math.sqrt(2.0)
-    W = np.empty((5,) + x.shape)
-    W[0] = 1.0 + 0.5 * np.sin(2.0 * np.pi * (x + y - (vx + vy) * t))
-    W[1] = vx
-    W[2] = vy
-    W[3] = 0.0
-    W[4] = 1.0
-    return W
+    rho = 1.0 + 0.5 * xp.sin(2.0 * np.pi * (x + y - (vx + vy) * t))
+    return xp.stack([rho, _const(x, vx), _const(x, vy), _const(x, 0.0), _const(x, 1.0)])
 
 
-def _double_layer(y, a=0.01):
+def _double_layer(xp, y, a=0.01):
     """+1 inside 0 < y < 1, -1 inside -1 < y < 0 (period 2), tanh layers of width a."""
-    return np.tanh(y / a) - np.tanh((y - 1.0) / a) - np.tanh((y + 1.0) / a)
+    return xp.tanh(y / a) - xp.tanh((y - 1.0) / a) - xp.tanh((y + 1.0) / a)
 
 
-def kh2d_ic(spec: dict, X: np.ndarray, amplitude: float | None = None) -> np.ndarray:
+def kh2d_ic(spec: dict, X, amplitude: float | None = None):
     """v_x = 0.5 f(y), rho = 0.55 + 0.45 f(y) (1 and 0.1), P = 1,
     v_y = A sin(2 pi x) exp(-y^2 / 0.01)."""
+    xp = _xp(X)
     A = spec.get("amplitude", 0.01) if amplitude is None else amplitude
     x, y = X[0], X[1]
-    f = _double_layer(y)
-    W = np.empty((5,) + x.shape)
-    W[0] = 0.55 + 0.45 * f
-    W[1] = 0.5 * f
-    W[2] = A * np.sin(2.0 * np.pi * x) * np.exp(-y * y / 0.01)
-    W[3] = 0.0
-    W[4] = 1.0
-    return W
+    f = _double_layer(xp, y)
+    return xp.stack([0.55 + 0.45 * f, 0.5 * f, A * xp.sin(2.0 * np.pi * x) * xp.exp(-y * y / 0.01),
+                     _const(x, 0.0), _const(x, 1.0)])
 
 
 def _modes(rng, kmax2):
@@ -127,14 +133,23 @@ def _modes(rng, kmax2):
     return np.array(ks, dtype=np.float64), phases
 
 
-def _mode_sum(ks, phases, x, y, z):
-    s = np.zeros_like(x)
+def _mode_sum(xp, ks, phases, x, y, z):
+    s = x * 0.0
     for (kx, ky, kz), ph in zip(ks, phases):
-        s += np.sin(2.0 * np.pi * (kx * x + ky * y + kz * z) + ph)
+        s = s + xp.sin(2.0 * np.pi * (kx * x + ky * y + kz * z) + ph)
     return s / len(ks)
 
 
-def kh3d_ic(spec: dict, X: np.ndarray) -> np.ndarray:
+def _kh3d_fields(xp, kp, php, kq, phq, kb, phb, x, y, z):
+    f = xp.tanh((y - 0.25) / 0.01) - xp.tanh((y - 0.75) / 0.01) - 1.0
+    ux = 0.9 / math.sqrt(1.0 - 0.81) * f
+    uy = 1e-3 * _mode_sum(xp, kp, php, x, y, z)
+    uz0 = 1e-3 * _mode_sum(xp, kq, phq, x, y, z)
+    g = _mode_sum(xp, kb, phb, x, y, z)
+    return f, ux, uy, uz0, g
+
+
+def kh3d_ic(spec: dict, X):
     """Shear v_x = +-0.9 between layers at y = 0.25 and 0.75, a seeded perturbation of
     amplitude 1e-3 in (v_y, v_z), and a seeded smooth bulk boost in the 4-velocity u_z
     scaled so that the largest Lorentz factor on a fixed 64^3 sample grid is 10.
@@ -143,20 +158,14 @@ def kh3d_ic(spec: dict, X: np.ndarray) -> np.ndarray:
     kp, php = _modes(rng, 4)
     kq, phq = _modes(rng, 4)
     kb, phb = _modes(rng, 2)
-
-    def fields(x, y, z, boost):
-        f = np.tanh((y - 0.25) / 0.01) - np.tanh((y - 0.75) / 0.01) - 1.0
-        ux = 0.9 / math.sqrt(1.0 - 0.81) * f
-        uy = 1e-3 * _mode_sum(kp, php, x, y, z)
-        uz = 1e-3 * _mode_sum(kq, phq, x, y, z) + boost * _mode_sum(kb, phb, x, y, z)
-        return f, ux, uy, uz
-
-    g = (np.arange(64) + 0.5) / 64.0
-    gx, gy, gz = np.meshgrid(g, g, g, indexing="ij")
+    g1 = (np.arange(64) + 0.5) / 64.0
+    gx, gy, gz = np.meshgrid(g1, g1, g1, indexing="ij")
+    _, ux_s, uy_s, uz0_s, g_s = _kh3d_fields(np, kp, php, kq, phq, kb, phb, gx, gy, gz)
+    base = 1.0 + ux_s * ux_s + uy_s * uy_s
 
     def max_gamma(boost):
-        _, ux, uy, uz = fields(gx, gy, gz, boost)
-        return float(np.sqrt(1.0 + ux * ux + uy * uy + uz * uz).max())
+        uz = uz0_s + boost * g_s
+        return float(np.sqrt(base + uz * uz).max())
 
     lo, hi = 0.0, 100.0
     for _ in range(200):
@@ -166,18 +175,14 @@ def kh3d_ic(spec: dict, X: np.ndarray) -> np.ndarray:
         else:
             hi = mid
     boost = 0.5 * (lo + hi)
-    f, ux, uy, uz = fields(X[0], X[1], X[2], boost)
-    lor = np.sqrt(1.0 + ux * ux + uy * uy + uz * uz)
-    W = np.empty((5,) + X[0].shape)
-    W[0] = 0.55 + 0.45 * f
-    W[1] = ux / lor
-    W[2] = uy / lor
-    W[3] = uz / lor
-    W[4] = 1.0
-    return W
+    xp = _xp(X)
+    f, ux, uy, uz0, g = _kh3d_fields(xp, kp, php, kq, phq, kb, phb, X[0], X[1], X[2])
+    uz = uz0 + boost * g
+    lor = xp.sqrt(1.0 + ux * ux + uy * uy + uz * uz)
+    return xp.stack([0.55 + 0.45 * f, ux / lor, uy / lor, uz / lor, _const(f, 1.0)])
 
 
-def initial_primitive(spec: dict, X: np.ndarray) -> np.ndarray:
+def initial_primitive(spec: dict, X):
     name = spec["name"]
     if name == "blast_wave_1d":
         return blast_wave_ic(spec, X)
@@ -208,30 +213,29 @@ def smooth_random(dim: int, n_elem, degree: int, eos: str = "ideal", seed: int =
                 vmax=vmax, bc_state=[[(1.0, 0.1, 0.0, 0.0, 1.0), (0.5, -0.1, 0.0, 0.0, 0.5)]] * dim)
 
 
-def smooth_random_ic(spec: dict, X: np.ndarray) -> np.ndarray:
+def smooth_random_ic(spec: dict, X):
+    xp = _xp(X)
     rng = np.random.default_rng(spec.get("seed", 0))
     dim = X.shape[0]
     coords = [X[d] for d in range(dim)]
-    out = np.empty((5,) + X[0].shape)
 
     def field():
-        s = np.zeros_like(coords[0])
+        s = coords[0] * 0.0
         for _ in range(3):
             k = rng.integers(-2, 3, size=dim)
             if not np.any(k):
                 k[0] = 1
             ph = rng.uniform(0, 2 * np.pi)
             amp = rng.uniform(0.3, 1.0)
-            s += amp * np.sin(2 * np.pi * sum(k[d] * coords[d] for d in range(dim)) + ph)
+            s = s + amp * xp.sin(2 * np.pi * sum(float(k[d]) * coords[d] for d in range(dim)) + ph)
         return s / 3.0
 
-    out[0] = 1.0 + 0.7 * field()
+    rho = 1.0 + 0.7 * field()
     vx, vy, vz = field(), field(), field()
-    vmag = np.sqrt(vx * vx + vy * vy + vz * vz)
+    vmag = xp.sqrt(vx * vx + vy * vy + vz * vz)
     scale = spec.get("vmax", 0.6) / max(float(vmag.max()), 1e-30)
-    out[1], out[2], out[3] = vx * scale, vy * scale, vz * scale
-    out[4] = 1.0 + 0.8 * field()
-    return out
+    P = 1.0 + 0.8 * field()
+    return xp.stack([rho, vx * scale, vy * scale, vz * scale, P])
 
 
 def random_primitive_states(n: int, seed: int = 0, gamma_max: float = 10.0,
