@@ -254,49 +254,89 @@ __device__ __forceinline__ T brent_cubic(T c1, T c2, T c3, T a, T b, T fa, T fb,
 }
 
 // Taub-Matthews iterative (Sec. 3.2): Brent on the cubic, bracketed by gamma in [1, 200]
-// with the upper end multiplied by 4 (at most 10 times) until the sign changes.  The solve
-// runs in FP32 first; FP64 Brent then starts from the bracket W32 (1 -+ 1e-4) when the
-// cubic changes sign across it, and from the full bracket otherwise.  `iters` counts both
-// phases and max_iter caps their sum.
+// with the upper end multiplied by 4 (at most 10 times) until the sign changes.  Brent runs in
+// FP32 (FP32 issues 58x faster than FP64 on this GPU); the FP32 root W32 is then polished in
+// FP64 by Newton's method on the cubic, safeguarded inside the bracket W32 (1 -+ 1e-5): a step
+// that leaves the bracket is replaced by bisection, and the bracket shrinks with the sign of
+// the cubic.  The bracket holds the unique non-negative root, so the polish cannot stray to
+// another root (the reason Sec. 3.2 gives for a bracketed solver).  When the cubic does not
+// change sign across that bracket, FP64 Brent runs on the paper's bracket instead.  Stop rule
+// |dW| <= 2 eps |W| + 1e-300 (Brent's tolerance); `iters` counts all iterations and
+// max_iter caps their sum.
 static __device__ __noinline__ double W_tm_brent(double xi, double eta, int max_iter, int& iters,
                                                  bool& conv) {
   const Cubic cc = tm_cubic(xi, eta);
   iters = 0;
   conv = false;
-  const double f0 = cubic_at(cc, 0.0);
+  const double f0 = cc.c3;  // the cubic at W = 0
   if (f0 == 0.0) {
     conv = true;
     return 0.0;
   }
+  // FP32 phase.  Its bracket: |v| < |S|/E, so W = u^2 < xi^2 / ((eta - xi)(eta + xi)) for an
+  // admissible state; eta - xi is formed in FP64 (it cancels at large Lorentz factors) and the
+  // bound is widened by 1e-3 relative and capped at the paper's 200^2 - 1.  Any state whose
+  // bound fails the sign check takes FP64 Brent on the paper's bracket below.
+  const float g1 = (float)cc.c1, g2 = (float)cc.c2, g3 = (float)cc.c3;
+  auto ff = [&](float W) { return ((W + g1) * W + g2) * W + g3; };
+  int it32 = 0;
+  bool conv32 = false;
+  float W32 = 0.0f;
+  const float x = (float)xi, exm = (float)(eta - xi);
+  if (exm > 0.0f && g3 < 0.0f) {
+    const float hi32 = fminf(x * x / (exm * ((float)eta + x)) * 1.001f + 1e-30f, 39999.0f);
+    const float fh32 = ff(hi32);
+    if (fh32 > 0.0f) {
+      const int max32 = max_iter > 2 ? max_iter - 2 : 1;  // the FP64 phase keeps the rest
+      W32 = brent_cubic<float>(g1, g2, g3, 0.0f, hi32, g3, fh32, max32, 1.1920929e-07f, 1e-37f,
+                               it32, conv32);
+    }
+  }
+  // FP64 phase: safeguarded Newton inside a tight bracket around the FP32 root
+  if (conv32 && W32 > 0.0f) {
+    double a = (double)W32 * (1.0 - 1e-5), b = (double)W32 * (1.0 + 1e-5);
+    const double fa = cubic_at(cc, a), fb = cubic_at(cc, b);
+    if (fa * fb <= 0.0) {
+      const bool rising = fa < 0.0;  // the cubic runs from fa to fb across [a, b]
+      double W = (double)W32;
+      int it = it32;
+      while (it < max_iter) {
+        ++it;
+        const double f = cubic_at(cc, W);
+        if (f == 0.0) {
+          conv = true;
+          break;
+        }
+        if ((f < 0.0) == rising)
+          a = W;
+        else
+          b = W;
+        const double df = fma(fma(3.0, W, 2.0 * cc.c1), W, cc.c2);
+        const double Wn = W - f / df;
+        // stop on a Newton step at rounding level before the bracket test: once W sits on
+        // the root, rounding noise in f can move a bracket end onto W itself
+        if (fabs(Wn - W) <= 2.0 * 2.220446049250313e-16 * fabs(W) + 1e-300) {
+          W = Wn;
+          conv = true;
+          break;
+        }
+        W = (Wn > a && Wn < b) ? Wn : 0.5 * (a + b);
+      }
+      iters = it;
+      return W;
+    }
+  }
+  // FP64 Brent on the paper's bracket [0, 200^2 - 1], upper end x4 until the sign changes
   double hi = 200.0 * 200.0 - 1.0, fhi = cubic_at(cc, hi);
   for (int k = 0; k < 10 && f0 * fhi > 0.0; ++k) {
     hi *= 4.0;
     fhi = cubic_at(cc, hi);
   }
+  iters = it32;
   if (f0 * fhi > 0.0) return __longlong_as_double(0x7ff8000000000000LL);
-  // FP32 phase on the paper's bracket
-  const float g1 = (float)cc.c1, g2 = (float)cc.c2, g3 = (float)cc.c3;
-  auto ff = [&](float W) { return ((W + g1) * W + g2) * W + g3; };
-  int it32 = 0;
-  bool conv32 = false;
-  const int max32 = max_iter > 2 ? max_iter - 2 : 1;  // the FP64 phase keeps the rest
-  const float W32 = brent_cubic<float>(g1, g2, g3, 0.0f, (float)hi, ff(0.0f), ff((float)hi), max32,
-                                       1.1920929e-07f, 1e-37f, it32, conv32);
-  // FP64 phase
-  double a = 0.0, b = hi, fa = f0, fb = fhi;
-  if (conv32 && W32 > 0.0f) {
-    const double lo2 = (double)W32 * (1.0 - 1e-4), hi2 = (double)W32 * (1.0 + 1e-4);
-    const double flo = cubic_at(cc, lo2), fhi2 = cubic_at(cc, hi2);
-    if (flo * fhi2 <= 0.0) {
-      a = lo2;
-      b = hi2;
-      fa = flo;
-      fb = fhi2;
-    }
-  }
   int it64 = 0;
-  const double W = brent_cubic<double>(cc.c1, cc.c2, cc.c3, a, b, fa, fb, max_iter - it32,
-                                       2.220446049250313e-16, 1e-300, it64, conv);
+  const double W = brent_cubic<double>(cc.c1, cc.c2, cc.c3, 0.0, hi, f0, fhi,
+                                       max_iter - it32, 2.220446049250313e-16, 1e-300, it64, conv);
   iters = it32 + it64;
   return W;
 }

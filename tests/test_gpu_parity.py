@@ -89,7 +89,12 @@ def test_con2prim(lib, eos, c2p):
     assert (np.abs(Wg[4] - Wo[4]) / Wo[4] / kappa).max() < tol
     if c2p == "iterative":
         # the GPU counts its FP32 and FP64 iterations together
-        assert 0.5 * float(ito.mean()) <= float(it.float().mean()) <= 1.6 * float(ito.mean()) + 1.0
+        if eos == "ideal":
+            assert 0.5 * float(ito.mean()) <= float(it.float().mean()) <= 1.6 * float(ito.mean()) + 1.0
+        else:
+            # Brent's FP32 phase starts from the bound W < xi^2/(eta^2 - xi^2) instead of the
+            # paper's [0, 200^2 - 1]: fewer iterations than the oracle, never more
+            assert 1.0 <= float(it.float().mean()) <= float(ito.mean())
         assert st["c2p_iters_total"] == int(it.sum())
 
 
