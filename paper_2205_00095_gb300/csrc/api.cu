@@ -34,7 +34,8 @@ struct dgsrhd_ctx {
   double* Wv;   // VJP: nodal (rho, u, P)
   double* TrB;  // VJP: trace adjoints
   double* Yb;   // stage VJP: adjoint of the stage before the operator
-  double* Vb;   // stage VJP: (dR/dU)^T Yb
+  unsigned char* Gd;  // VJP: face-guard flag per face point [E][2 dim Nt]
+  long long fs_total;  // doubles of the face-flux buffer
   unsigned long long* stats;
   long long c2p_calls;
   long long launches;
@@ -303,6 +304,7 @@ int32_t dgsrhd_create(const dgsrhd_config* cfg, void* stream, dgsrhd_ctx** out) 
     }
   }
   const long long fs_total = off;
+  c->fs_total = fs_total;
   p.eos = cfg->eos;
   p.gamma_ad = cfg->gamma_ad;
   p.alpha = cfg->eos == DGSRHD_EOS_IDEAL ? cfg->gamma_ad / (cfg->gamma_ad - 1.0) : 0.0;
@@ -328,7 +330,7 @@ int32_t dgsrhd_create(const dgsrhd_config* cfg, void* stream, dgsrhd_ctx** out) 
   if (e == cudaSuccess) e = alloc(&c->Wv, c->nstate);
   if (e == cudaSuccess) e = alloc(&c->TrB, ntr);
   if (e == cudaSuccess) e = alloc(&c->Yb, c->nstate);
-  if (e == cudaSuccess) e = alloc(&c->Vb, c->nstate);
+  if (e == cudaSuccess) e = alloc(&c->Gd, 2LL * c->dim * E * p.Nt);
   if (e == cudaSuccess) e = alloc(&c->stats, (size_t)dgsrhd::kStatCount * 64);
   if (e == cudaSuccess) e = cudaMemsetAsync(c->stats, 0, sizeof(unsigned long long) * dgsrhd::kStatCount * 64, c->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
@@ -360,7 +362,7 @@ void dgsrhd_destroy(dgsrhd_ctx* c) {
   cudaFree(c->Wv);
   cudaFree(c->TrB);
   cudaFree(c->Yb);
-  cudaFree(c->Vb);
+  cudaFree(c->Gd);
   cudaFree(c->stats);
   delete c;
 }
@@ -583,10 +585,36 @@ namespace {
 // Reverse sweep of the RHS.  `saved` (nullable) holds the nodal (rho, u, P) and the face traces
 // of the forward evaluation at U (written by dgsrhd_step_stage); without it the forward volume
 // kernel is re-run to provide them.
+long long trace_doubles(const dgsrhd_ctx* c) { return 2LL * c->dim * 5 * c->E * c->p.Nt; }
+// face-state tape: 2 kFaceTape doubles per face point, face points = fs_total / 5
+long long tape_doubles(const dgsrhd_ctx* c) { return (c->fs_total / 5) * 2 * dgsrhd::kFaceTape; }
+// face-guard flags: one byte per face point of every element, rounded up to whole doubles
+long long guard_doubles(const dgsrhd_ctx* c) { return (2LL * c->dim * c->E * c->p.Nt + 7) / 8; }
+
+// Sections of a stage's saved forward quantities: nodal (rho, u, P), face traces, face-state
+// tape, face-guard flags.
+struct Saved {
+  double* W;
+  double* Tr;
+  double* tape;
+  unsigned char* guard;
+};
+Saved saved_sections(const dgsrhd_ctx* c, double* save) {
+  Saved v{};
+  if (!save) return v;
+  v.W = save;
+  v.Tr = save + c->nstate;
+  v.tape = v.Tr + trace_doubles(c);
+  v.guard = reinterpret_cast<unsigned char*>(v.tape + tape_doubles(c));
+  return v;
+}
+
+// (dR/dU)^T R_bar -> U_bar; with Ukb set, the stage combination Unb += a_n R_bar,
+// Ukb += b_k (R_bar + dt U_bar) replaces the write of U_bar.
 int32_t rhs_vjp_core(dgsrhd_ctx* c, const double* U, const double* R_bar, double* U_bar,
-                     const double* saved) {
-  const double* Wst = saved;
-  const double* Tr = saved ? saved + c->nstate : nullptr;
+                     const double* saved, double* Unb = nullptr, double* Ukb = nullptr,
+                     double a_n = 0.0, double b_k = 0.0, double dt = 0.0) {
+  Saved sv = saved_sections(c, const_cast<double*>(saved));
   if (!saved) {
     StageArgs v{};
     v.op = Op::Volume;
@@ -595,28 +623,37 @@ int32_t rhs_vjp_core(dgsrhd_ctx* c, const double* U, const double* R_bar, double
     v.Rvol = c->Rv;
     v.Tr = c->Tr;
     v.Wstore = c->Wv;
+    v.guard = c->Gd;
     if (run_stage(c, v) != cudaSuccess) return DGSRHD_ECUDA;
     c->c2p_calls += c->E * c->Nn;
-    Wst = c->Wv;
-    Tr = c->Tr;
+    sv.W = c->Wv;
+    sv.Tr = c->Tr;
+    sv.tape = nullptr;  // the face reverse sweep evaluates its roots and reciprocals itself
+    sv.guard = c->Gd;
   }
   StageArgs f{};
   f.op = Op::VjpFace;
-  f.Tr = const_cast<double*>(Tr);
+  f.Tr = sv.Tr;
+  f.tape = sv.tape;
   f.Rbar = R_bar;
   f.TrBar = c->TrB;
   if (run_stage(c, f) != cudaSuccess) return DGSRHD_ECUDA;
   StageArgs n{};
   n.op = Op::VjpNode;
   n.U = U;
-  n.Wstore = const_cast<double*>(Wst);
+  n.Wstore = sv.W;
+  n.guard = sv.guard;
   n.Rbar = R_bar;
   n.TrBar = c->TrB;
   n.Ubar = U_bar;
+  n.Unb = Unb;
+  n.Ukb = Ukb;
+  n.a_n = a_n;
+  n.b_k = b_k;
+  n.dt = dt;
   return cuda_status(run_stage(c, n));
 }
 
-long long trace_doubles(const dgsrhd_ctx* c) { return 2LL * c->dim * 5 * c->E * c->p.Nt; }
 
 }  // namespace
 
@@ -629,7 +666,7 @@ int32_t dgsrhd_rhs_vjp(dgsrhd_ctx* c, const double* U, const double* R_bar, doub
 
 int32_t dgsrhd_stage_save_size(const dgsrhd_ctx* c, int64_t* n) {
   if (!c || !n) return DGSRHD_EINVAL;
-  *n = c->nstate + trace_doubles(c);
+  *n = c->nstate + trace_doubles(c) + tape_doubles(c) + guard_doubles(c);
   return DGSRHD_OK;
 }
 
@@ -648,12 +685,14 @@ int32_t dgsrhd_step_stage(dgsrhd_ctx* c, const double* Un, const double* Uk, dou
   if (!c || !Un || !Uk || !Uout || stage < 0 || stage >= c->cfg.rk_stages || !(dt >= 0.0))
     return DGSRHD_EINVAL;
   const int ns = c->cfg.rk_stages;
+  const Saved sv = saved_sections(c, save);
   StageArgs v{};
   v.op = Op::Volume;
   v.U = Uk;
   v.Rvol = c->Rv;
-  v.Tr = save ? save + c->nstate : c->Tr;
-  v.Wstore = save;
+  v.Tr = save ? sv.Tr : c->Tr;
+  v.Wstore = sv.W;
+  v.guard = sv.guard;
   if (save) v.fp64_only = 1;  // the saved quantities feed the FP64 reverse sweep
   if (run_stage(c, v) != cudaSuccess) return DGSRHD_ECUDA;
   c->c2p_calls += c->E * c->Nn;
@@ -661,6 +700,7 @@ int32_t dgsrhd_step_stage(dgsrhd_ctx* c, const double* Un, const double* Uk, dou
   f.op = Op::Face;
   f.Tr = v.Tr;
   f.Fs = c->Fs;
+  f.tape = sv.tape;
   if (run_stage(c, f) != cudaSuccess) return DGSRHD_ECUDA;
   StageArgs u{};
   u.op = Op::Update;
@@ -692,14 +732,9 @@ int32_t dgsrhd_stage_vjp(dgsrhd_ctx* c, const double* Uk, const double* s, const
     if (st != DGSRHD_OK) return st;
     Yb = c->Yb;
   }
-  int32_t st = rhs_vjp_core(c, Uk, Yb, c->Vb, saved);
-  if (st != DGSRHD_OK) return st;
+  // the node reverse sweep adds a_n Yb to Un_bar and b_k (Yb + dt (dR/dU)^T Yb) to Uk_bar
   const double a_n = kAn[ns - 1][stage], b_k = kBk[ns - 1][stage];
-  cudaError_t e = timed_launch(c, DGSRHD_KERNEL_VJP, [&]() {
-    return dgsrhd::launch_stage_combine(c->stream, c->nstate, Yb, c->Vb, a_n, b_k, dt, Un_bar, Uk_bar);
-  });
-  if (e == cudaSuccess) c->launches += 1;
-  return cuda_status(e);
+  return rhs_vjp_core(c, Uk, Yb, nullptr, saved, Un_bar, Uk_bar, a_n, b_k, dt);
 }
 
 int32_t dgsrhd_con2prim_vjp(dgsrhd_ctx* c, const double* U, const double* W_bar, double* U_bar) {

@@ -437,50 +437,85 @@ __device__ __forceinline__ void phys_flux(const double U[5], const double v[3], 
 struct FaceState {
   double U[5];
   double v[3];
-  double P;
-  double A, B;
+  double P, A, B;
+  // intermediates, kept for the reverse sweep
+  double u2, q, ilor, lor, rho_hm1, sg, isg, Z, iZ, K, id1, i;
 };
 
-__device__ __forceinline__ void face_state(const Params& p, const double Wu[5], FaceState& c) {
+// Face state from (rho, u, P).  The three reciprocals 1/Z, 1/(gamma + 1) and 1/(A + B) come
+// from one division of their product, and the roots from rsqrt (the root itself is x rsqrt(x)).
+// With `rec` given, the roots and reciprocals are read from it instead (values saved by an
+// earlier evaluation on the same state), and no root or division is evaluated.
+__device__ __forceinline__ void face_state_core(const Params& p, const double Wu[5], FaceState& c,
+                                                const double* rec) {
+  // Sums that take a product are written with __dadd_rn / __dsub_rn, which the compiler never
+  // fuses into an FMA: the roots and reciprocals must come out bit-identical in every kernel
+  // that evaluates them, whether they are saved by one and read by another or recomputed.
   const double rho = Wu[0], P = Wu[4];
-  const double u2 = Wu[1] * Wu[1] + Wu[2] * Wu[2] + Wu[3] * Wu[3];
-  const double q = 1.0 + u2;
-  const double ilor = rsqrt(q);
-  const double lor = q * ilor;
-  const double lor2 = q;  // gamma^2 = 1 + u^2
-  double rho_hm1;         // rho (h - 1)
+  c.u2 = fma(Wu[1], Wu[1], fma(Wu[2], Wu[2], Wu[3] * Wu[3]));
+  c.q = __dadd_rn(1.0, c.u2);  // gamma^2
+  c.ilor = rec ? rec[0] : rsqrt(c.q);
+  c.lor = c.q * c.ilor;
+  c.P = P;
   if (p.eos == 0) {
-    rho_hm1 = p.alpha * P;
     c.A = p.gamma_ad * P;
-    c.B = lor2 * (rho + rho_hm1 - c.A);
+    c.K = __dsub_rn(fma(p.alpha, P, rho), c.A);
+    c.sg = c.isg = c.Z = c.iZ = 0.0;
   } else {
-    const double sg = sqrt(fma(P, P, (4.0 / 9.0) * rho * rho));
-    rho_hm1 = 2.5 * P + 1.5 * P * P / (sg + (2.0 / 3.0) * rho);
-    c.A = P * fma(3.0, P, 5.0 * sg);
-    c.B = lor2 * (fma(12.0 * P, P + sg, 2.0 * rho * rho) - c.A);
+    const double x2 = fma(P, P, (4.0 / 9.0) * rho * rho);
+    c.isg = rec ? rec[1] : rsqrt(x2);
+    c.sg = x2 * c.isg;
+    c.Z = fma(2.0 / 3.0, rho, c.sg);
+    c.A = P * fma(3.0, P, 5.0 * c.sg);
+    c.K = __dsub_rn(fma(12.0 * P, __dadd_rn(P, c.sg), 2.0 * rho * rho), c.A);
   }
-  const double D = lor * rho;
-  const double rhoh_lor = (rho + rho_hm1) * lor;  // S = rho h gamma u
+  c.B = c.q * c.K;
+  const double L1 = __dadd_rn(c.lor, 1.0), AB = __dadd_rn(c.A, c.B);
+  if (rec) {
+    c.iZ = rec[2];
+    c.id1 = rec[3];
+    c.i = rec[4];
+  } else if (p.eos == 0) {
+    const double t = 1.0 / (L1 * AB);
+    c.id1 = t * AB;
+    c.i = t * L1;
+  } else {
+    const double ZL = c.Z * L1;
+    const double t = 1.0 / (ZL * AB);
+    c.iZ = t * L1 * AB;
+    c.id1 = t * c.Z * AB;
+    c.i = t * ZL;
+  }
+  c.rho_hm1 = p.eos == 0 ? p.alpha * P : fma(1.5 * P * P, c.iZ, 2.5 * P);
+  const double D = c.lor * rho;
+  const double rhoh_lor = __dadd_rn(rho, c.rho_hm1) * c.lor;  // S = rho h gamma u
   c.U[0] = D;
   c.U[1] = rhoh_lor * Wu[1];
   c.U[2] = rhoh_lor * Wu[2];
   c.U[3] = rhoh_lor * Wu[3];
-  c.U[4] = D * u2 / (lor + 1.0) + lor2 * rho_hm1 - P;
-  c.v[0] = Wu[1] * ilor;
-  c.v[1] = Wu[2] * ilor;
-  c.v[2] = Wu[3] * ilor;
-  c.P = P;
+  c.U[4] = fma(D * c.u2, c.id1, fma(c.q, c.rho_hm1, -P));
+  c.v[0] = Wu[1] * c.ilor;
+  c.v[1] = Wu[2] * c.ilor;
+  c.v[2] = Wu[3] * c.ilor;
+}
+
+__device__ __forceinline__ void face_state(const Params& p, const double Wu[5], FaceState& c) {
+  face_state_core(p, Wu, c, nullptr);
 }
 
 // lambda_pm = (v_d +- sqrt(sig (1 - v_d^2 + sig))) / (1 + sig) with sig = A / B, evaluated as
-// (v_d B +- sqrt(A (B (1 - v_d^2) + A))) / (A + B): one root and one division for both.
+// (v_d B +- r) i with r = sqrt(X), X = A (B (1 - v_d^2) + A), and i = 1/(A + B) from the face
+// state.  Also returns X, r and 1/r (0 where r = 0); 1/r is read from `ir_saved` when given.
 template <int D>
-__device__ __forceinline__ void wavespeeds_ab(const FaceState& c, double& lm, double& lp) {
+__device__ __forceinline__ void wavespeeds_full(const FaceState& c, double& lm, double& lp,
+                                                double& X, double& r, double& ir,
+                                                const double* ir_saved) {
   const double vd = c.v[D];
-  const double r = sqrt(c.A * fma(c.B, fma(-vd, vd, 1.0), c.A));
-  const double i = 1.0 / (c.A + c.B);
-  lm = (vd * c.B - r) * i;
-  lp = (vd * c.B + r) * i;
+  X = c.A * fma(c.B, fma(-vd, vd, 1.0), c.A);
+  ir = ir_saved ? *ir_saved : (X > 0.0 ? rsqrt(X) : 0.0);
+  r = X * ir;
+  lm = fma(vd, c.B, -r) * c.i;
+  lp = fma(vd, c.B, r) * c.i;
 }
 
 template <int D>
@@ -495,22 +530,36 @@ __device__ __forceinline__ void phys_flux_dir(const double U[5], const double v[
   F[4] = (U[4] + P) * vd;
 }
 
+// The kFaceTape values of one face state, in the order documented with kFaceTape.
+__device__ __forceinline__ void face_tape(const FaceState& c, double r, double ir, double lm,
+                                          double lp, double t[kFaceTape]) {
+  t[0] = c.ilor, t[1] = c.isg, t[2] = c.iZ, t[3] = c.id1, t[4] = c.i, t[5] = ir;
+  t[6] = c.u2, t[7] = c.lor, t[8] = c.sg, t[9] = c.A, t[10] = c.B, t[11] = c.K;
+  t[12] = c.rho_hm1;
+#pragma unroll
+  for (int k = 0; k < 5; ++k) t[13 + k] = c.U[k];
+  t[18] = r, t[19] = lm, t[20] = lp;
+}
+
 // Numerical flux along axis D between face states given as (rho, u, P).  HLL: S_L =
 // min(lambda_L, 0), S_R = max(lambda_R, 0), (S_R F_L - S_L F_R + S_L S_R (U_R - U_L)) /
 // (S_R - S_L) (the average when both vanish); LLF: (F_L + F_R)/2 - a (U_R - U_L)/2 with
 // a = max |lambda|.
 template <int D>
 __device__ __forceinline__ void numerical_flux(const Params& p, const double WL[5],
-                                               const double WR[5], double Fs[5]) {
+                                               const double WR[5], double Fs[5],
+                                               double recL[kFaceTape], double recR[kFaceTape]) {
   FaceState L, R;
   face_state(p, WL, L);
   face_state(p, WR, R);
   double FL[5], FR[5];
   phys_flux_dir<D>(L.U, L.v, L.P, FL);
   phys_flux_dir<D>(R.U, R.v, R.P, FR);
-  double lmL, lpL, lmR, lpR;
-  wavespeeds_ab<D>(L, lmL, lpL);
-  wavespeeds_ab<D>(R, lmR, lpR);
+  double lmL, lpL, lmR, lpR, XL, rL, irL, XR, rR, irR;
+  wavespeeds_full<D>(L, lmL, lpL, XL, rL, irL, nullptr);
+  wavespeeds_full<D>(R, lmR, lpR, XR, rR, irR, nullptr);
+  face_tape(L, rL, irL, lmL, lpL, recL);
+  face_tape(R, rR, irR, lmR, lpR, recR);
   const double lamL = fmin(lmL, lmR), lamR = fmax(lpL, lpR);
   if (p.flux == 1) {
     const double sL = fmin(lamL, 0.0), sR = fmax(lamR, 0.0);
@@ -547,10 +596,12 @@ __device__ __forceinline__ void c2p_adjoint(const Params& p, double rho, const d
     w_r = 1.0;
     w_P = p.alpha;
   } else {
-    const double sg = sqrt(P * P + (4.0 / 9.0) * rho * rho);
-    w = 2.5 * P + 1.5 * sg;
-    w_r = (2.0 / 3.0) * rho / sg;
-    w_P = 2.5 + 1.5 * P / sg;
+    const double x2 = fma(P, P, (4.0 / 9.0) * rho * rho);
+    const double isg = rsqrt(x2);
+    const double sg = x2 * isg;
+    w = fma(2.5, P, 1.5 * sg);
+    w_r = (2.0 / 3.0) * rho * isg;
+    w_P = fma(1.5 * P, isg, 2.5);
   }
   const double g2 = lor * lor, g3 = g2 * lor, g4 = g2 * g2;
   const double v2 = v[0] * v[0] + v[1] * v[1] + v[2] * v[2];
@@ -567,12 +618,14 @@ __device__ __forceinline__ void c2p_adjoint(const Params& p, double rho, const d
   const double c12 = m21 * m33;           // minus sign applied below
   const double c13 = m21 * m32;
   const double det = m11 * c11 - m12 * c12 + m13 * c13;
-  const double idet = 1.0 / det;
+  // 1/det and 1/(w gamma^2) from one division
+  const double wg2 = w * g2;
+  const double t = 1.0 / (det * wg2);
+  const double idet = t * wg2, iw = t * det;
   const double yD = (r1 * c11 - m12 * (r2 * m33 - m23 * r3) + m13 * (r2 * m32 - m22 * r3)) * idet;
   const double a = (m11 * (r2 * m33 - m23 * r3) - r1 * c12 + m13 * (m21 * r3)) * idet;
   const double yE = (m11 * (m22 * r3 - r2 * m32) - m12 * (m21 * r3) + r1 * c13) * idet;
   const double c = rho * g3 * yD + 2.0 * w * g4 * (a + yE);
-  const double iw = 1.0 / (w * g2);
   Ub[0] = yD + yE;
 #pragma unroll
   for (int k = 0; k < 3; ++k) Ub[1 + k] = (Wb[1 + k] - c * v[k]) * iw;

@@ -117,7 +117,8 @@ __device__ __forceinline__ void block_stats(const Params& p, int iters, int stat
 template <int DIM, int N>
 __global__ void __launch_bounds__(Shape<DIM, N>::BLOCK)
     volume_kernel(Params p, const double* __restrict__ U, double* __restrict__ Rvol,
-                  double* __restrict__ Tr, double* __restrict__ Wout) {
+                  double* __restrict__ Tr, double* __restrict__ Wout,
+                  unsigned char* __restrict__ guard_out) {
   using S = Shape<DIM, N>;
   constexpr int Nn = S::Nn, Nt = S::Nt, BLOCK = S::BLOCK;
   __shared__ double shF[DIM][5][BLOCK];
@@ -190,12 +191,15 @@ __global__ void __launch_bounds__(Shape<DIM, N>::BLOCK)
 #pragma unroll
         for (int v = 0; v < 5; ++v) out[v] = fma(c, shW[v][node], out[v]);
       }
-      if (!(out[0] > 0.0) || !(out[4] > 0.0)) {
+      const bool guarded = !(out[0] > 0.0) || !(out[4] > 0.0);
+      if (guarded) {
         const int node = le * Nn + line_node<DIM, N>(d, t, side ? N - 1 : 0);
 #pragma unroll
         for (int v = 0; v < 5; ++v) out[v] = shW[v][node];
         ++guard;
       }
+      // the guard decision per face point, kept with the primitives for the reverse sweep
+      if (guard_out) guard_out[e * S::NFP + fp] = guarded ? 1 : 0;
 #pragma unroll
       for (int v = 0; v < 5; ++v) Tr[((((long long)d * 2 + side) * 5 + v) * p.E + e) * Nt + t] = out[v];
     }
@@ -207,9 +211,16 @@ __global__ void __launch_bounds__(Shape<DIM, N>::BLOCK)
 // Face kernel: blockIdx.y = axis; each axis runs its own instantiation of the face point so
 // that every index into the state is known at compile time.
 // ---------------------------------------------------------------------------------------
-template <int DIM, int N, int D>
+// Face-state tape: kFaceTape values per side (left, then right) per face point, plane j of axis
+// D at (fs_off[D] / 5) * 2 kFaceTape + j nface[D] Nt.
+__device__ __forceinline__ long long tape_base(const Params& p, int D) {
+  return (p.fs_off[D] / 5) * (2 * kFaceTape);
+}
+
+template <int DIM, int N, int D, bool SAVE>
 __device__ __forceinline__ void face_point(const Params& p, const double* __restrict__ Tr,
-                                           double* __restrict__ Fs, long long k) {
+                                           double* __restrict__ Fs, double* __restrict__ tape,
+                                           long long k) {
   constexpr int Nt = Shape<DIM, N>::Nt;
   const long long nf = p.nface[D];
   if (k >= nf * Nt) return;
@@ -255,20 +266,27 @@ __device__ __forceinline__ void face_point(const Params& p, const double* __rest
 #pragma unroll
     for (int v = 0; v < 5; ++v) WR[v] = (p.bc[D][1] == 1) ? p.ghost[D][1][v] : WL[v];
   }
-  double F[5];
-  numerical_flux<D>(p, WL, WR, F);
+  double F[5], rec[2][kFaceTape];
+  numerical_flux<D>(p, WL, WR, F, rec[0], rec[1]);
   double* out = Fs + p.fs_off[D];
 #pragma unroll
   for (int v = 0; v < 5; ++v) out[(v * nf + f) * Nt + t] = F[v];
+  if (SAVE) {
+    double* tp = tape + tape_base(p, D);
+#pragma unroll
+    for (int j = 0; j < 2 * kFaceTape; ++j) tp[j * nf * Nt + k] = rec[j / kFaceTape][j % kFaceTape];
+  }
 }
 
-template <int DIM, int N>
+// SAVE: also write the face-state tape for the reverse sweep.
+template <int DIM, int N, bool SAVE>
 __global__ void __launch_bounds__(128) face_kernel(Params p, const double* __restrict__ Tr,
-                                                   double* __restrict__ Fs) {
+                                                   double* __restrict__ Fs,
+                                                   double* __restrict__ tape) {
   const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (blockIdx.y == 0) face_point<DIM, N, 0>(p, Tr, Fs, k);
-  if (DIM > 1 && blockIdx.y == 1) face_point<DIM, N, (DIM > 1 ? 1 : 0)>(p, Tr, Fs, k);
-  if (DIM > 2 && blockIdx.y == 2) face_point<DIM, N, (DIM > 2 ? 2 : 0)>(p, Tr, Fs, k);
+  if (blockIdx.y == 0) face_point<DIM, N, 0, SAVE>(p, Tr, Fs, tape, k);
+  if (DIM > 1 && blockIdx.y == 1) face_point<DIM, N, (DIM > 1 ? 1 : 0), SAVE>(p, Tr, Fs, tape, k);
+  if (DIM > 2 && blockIdx.y == 2) face_point<DIM, N, (DIM > 2 ? 2 : 0), SAVE>(p, Tr, Fs, tape, k);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -490,14 +508,18 @@ static cudaError_t launch_stage_kernels(const StageArgs& a) {
   }
   switch (a.op) {
     case Op::Volume:
-      volume_kernel<DIM, N><<<eblocks, S::BLOCK, 0, a.stream>>>(p, a.U, a.Rvol, a.Tr, a.Wstore);
+      volume_kernel<DIM, N><<<eblocks, S::BLOCK, 0, a.stream>>>(p, a.U, a.Rvol, a.Tr, a.Wstore,
+                                                                 a.guard);
       break;
     case Op::Face: {
       long long mx = 0;
       for (int d = 0; d < DIM; ++d) mx = p.nface[d] > mx ? p.nface[d] : mx;
       const long long nthreads = mx * S::Nt;
       dim3 grid((unsigned)((nthreads + 127) / 128), DIM);
-      face_kernel<DIM, N><<<grid, 128, 0, a.stream>>>(p, a.Tr, a.Fs);
+      if (a.tape)
+        face_kernel<DIM, N, true><<<grid, 128, 0, a.stream>>>(p, a.Tr, a.Fs, a.tape);
+      else
+        face_kernel<DIM, N, false><<<grid, 128, 0, a.stream>>>(p, a.Tr, a.Fs, nullptr);
       break;
     }
     case Op::Update:
@@ -512,11 +534,13 @@ static cudaError_t launch_stage_kernels(const StageArgs& a) {
       for (int d = 0; d < DIM; ++d) mx = p.nface[d] > mx ? p.nface[d] : mx;
       const long long nthreads = mx * S::Nt;
       dim3 grid((unsigned)((nthreads + 127) / 128), DIM);
-      face_vjp_kernel<DIM, N><<<grid, 128, 0, a.stream>>>(p, a.Tr, a.Rbar, a.TrBar);
+      face_vjp_kernel<DIM, N><<<grid, 128, 0, a.stream>>>(p, a.Tr, a.tape, a.Rbar, a.TrBar);
       break;
     }
     case Op::VjpNode:
-      node_vjp_kernel<DIM, N><<<eblocks, S::BLOCK, 0, a.stream>>>(p, a.U, a.Wstore, a.Rbar, a.TrBar, a.Ubar);
+      if (!a.guard) return cudaErrorInvalidValue;
+      node_vjp_kernel<DIM, N><<<eblocks, S::BLOCK, 0, a.stream>>>(
+          p, a.U, a.Wstore, a.guard, a.Rbar, a.TrBar, a.Ubar, a.Unb, a.Ukb, a.a_n, a.b_k, a.dt);
       break;
     case Op::EnforceVjp:
       enforce_vjp_kernel<DIM, N><<<eblocks, S::BLOCK, 0, a.stream>>>(p, a.s_in, a.Tbar, a.Ubar);

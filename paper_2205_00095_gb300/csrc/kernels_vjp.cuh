@@ -7,11 +7,15 @@
 //                     choices (min/max of the wavespeeds, the clamps to 0, |lambda|) frozen at
 //                     their forward values, giving the adjoints of the two face traces.
 //   node_vjp_kernel : per node, the transposed volume contraction F_bar = (2/dx) Dhat^T R_bar, the
-//                     transposed trace extrapolation (face guard frozen), the transposed flux
-//                     Jacobians, and the con2prim adjoint by the implicit-function theorem: W(U)
-//                     inverts U = prim2cons(W) (Eq. primitive_to_conserved), so
-//                     U_bar = (dU/dW)^{-T} W_bar, a 5 x 5 solve at the converged root.
-// The forward volume kernel is re-run first to provide the face traces and the nodal (rho, u, P).
+//                     transposed trace extrapolation (face guard as decided in the forward pass),
+//                     the transposed flux Jacobians, and the con2prim adjoint by the
+//                     implicit-function theorem: W(U) inverts U = prim2cons(W) (Eq.
+//                     primitive_to_conserved), so U_bar = (dU/dW)^{-T} W_bar, a 5 x 5 solve at the
+//                     converged root.
+// Inputs kept from the forward pass: the nodal (rho, u, P), the face traces, the face-guard
+// flags and, when the forward face kernel was asked for it, the face-state tape (the roots and
+// reciprocals of every face state), which leaves the face reverse sweep without a root or a
+// division.
 #pragma once
 
 #include "kernels.cuh"
@@ -21,63 +25,41 @@ namespace dgsrhd {
 // ---------------------------------------------------------------------------------------
 // One face state: forward with its intermediates, then its reverse.
 // ---------------------------------------------------------------------------------------
-struct FaceFwd {
+struct FaceFwd : FaceState {
   double Wu[5];
-  double u2, q, ilor, lor, rho_hm1, A, B, sg, isg, Z, iZ, K, H, rhoh_lor, id1;
-  double U[5], v[3];
+  double H, rhoh_lor;
   double F[5];
-  double X, r, ir, i, lm, lp;
+  double X, r, ir, lm, lp;
 };
 
+// The forward face state with the intermediates of its reverse.  `t` (kFaceTape values at
+// stride ts, or null) is the tape the forward face kernel wrote for this face state: with it only the flux
+// and two sums are formed here; without it the state is evaluated in full.  Both give the same
+// bits, since the tape holds what the same functions compute.
 template <int D>
-__device__ __forceinline__ void face_fwd(const Params& p, const double Wu[5], FaceFwd& f) {
+__device__ __forceinline__ void face_fwd(const Params& p, const double Wu[5],
+                                         const double* __restrict__ t, long long ts, FaceFwd& f) {
 #pragma unroll
   for (int k = 0; k < 5; ++k) f.Wu[k] = Wu[k];
-  const double rho = Wu[0], P = Wu[4];
-  f.u2 = Wu[1] * Wu[1] + Wu[2] * Wu[2] + Wu[3] * Wu[3];
-  f.q = 1.0 + f.u2;
-  f.ilor = rsqrt(f.q);
-  f.lor = f.q * f.ilor;
-  // reciprocals are formed once here and reused by the reverse sweep
-  if (p.eos == 0) {
-    f.rho_hm1 = p.alpha * P;
-    f.A = p.gamma_ad * P;
-    f.B = f.q * (rho + f.rho_hm1 - f.A);
-    f.sg = f.isg = f.Z = f.iZ = f.K = 0.0;
+  if (t) {
+    f.ilor = t[0], f.isg = t[ts], f.iZ = t[2 * ts], f.id1 = t[3 * ts], f.i = t[4 * ts];
+    f.ir = t[5 * ts], f.u2 = t[6 * ts], f.lor = t[7 * ts], f.sg = t[8 * ts], f.A = t[9 * ts];
+    f.B = t[10 * ts], f.K = t[11 * ts], f.rho_hm1 = t[12 * ts];
+#pragma unroll
+    for (int k = 0; k < 5; ++k) f.U[k] = t[(13 + k) * ts];
+    f.r = t[18 * ts], f.lm = t[19 * ts], f.lp = t[20 * ts];
+    f.q = __dadd_rn(1.0, f.u2);
+    f.P = Wu[4];
+    f.v[0] = Wu[1] * f.ilor;
+    f.v[1] = Wu[2] * f.ilor;
+    f.v[2] = Wu[3] * f.ilor;
   } else {
-    f.sg = sqrt(P * P + (4.0 / 9.0) * rho * rho);
-    f.isg = 1.0 / f.sg;
-    f.Z = f.sg + (2.0 / 3.0) * rho;
-    f.iZ = 1.0 / f.Z;
-    f.rho_hm1 = 2.5 * P + 1.5 * P * P * f.iZ;
-    f.A = P * (3.0 * P + 5.0 * f.sg);
-    f.K = 12.0 * P * (P + f.sg) + 2.0 * rho * rho - f.A;
-    f.B = f.q * f.K;
+    face_state_core(p, Wu, f, nullptr);
+    wavespeeds_full<D>(f, f.lm, f.lp, f.X, f.r, f.ir, nullptr);
   }
-  f.H = rho + f.rho_hm1;
+  f.H = __dadd_rn(Wu[0], f.rho_hm1);
   f.rhoh_lor = f.H * f.lor;
-  f.id1 = 1.0 / (f.lor + 1.0);
-  f.U[0] = f.lor * rho;
-  f.U[1] = f.rhoh_lor * Wu[1];
-  f.U[2] = f.rhoh_lor * Wu[2];
-  f.U[3] = f.rhoh_lor * Wu[3];
-  f.U[4] = f.U[0] * f.u2 * f.id1 + f.q * f.rho_hm1 - P;
-  f.v[0] = Wu[1] * f.ilor;
-  f.v[1] = Wu[2] * f.ilor;
-  f.v[2] = Wu[3] * f.ilor;
-  const double vd = f.v[D];
-  f.F[0] = f.U[0] * vd;
-  f.F[1] = f.U[1] * vd;
-  f.F[2] = f.U[2] * vd;
-  f.F[3] = f.U[3] * vd;
-  f.F[1 + D] += P;
-  f.F[4] = (f.U[4] + P) * vd;
-  f.X = f.A * (f.B * (1.0 - vd * vd) + f.A);
-  f.r = sqrt(f.X);
-  f.ir = f.r > 0.0 ? 1.0 / f.r : 0.0;
-  f.i = 1.0 / (f.A + f.B);
-  f.lm = (vd * f.B - f.r) * f.i;
-  f.lp = (vd * f.B + f.r) * f.i;
+  phys_flux_dir<D>(f.U, f.v, f.P, f.F);
 }
 
 // Reverse of face_fwd: adjoints of its outputs (flux Fb, conserved state Ub, wavespeeds lmb,
@@ -162,11 +144,13 @@ __device__ __forceinline__ void face_rev(const Params& p, const FaceFwd& f, cons
 // Reverse of numerical_flux<D>: Fsb -> adjoints of the left and right face primitives.
 template <int D>
 __device__ __forceinline__ void numerical_flux_vjp(const Params& p, const double WL[5],
-                                                   const double WR[5], const double Fsb[5],
-                                                   double WLb[5], double WRb[5]) {
+                                                   const double WR[5], const double* tL,
+                                                   const double* tR, long long ts,
+                                                   const double Fsb[5], double WLb[5],
+                                                   double WRb[5]) {
   FaceFwd L, R;
-  face_fwd<D>(p, WL, L);
-  face_fwd<D>(p, WR, R);
+  face_fwd<D>(p, WL, tL, ts, L);
+  face_fwd<D>(p, WR, tR, ts, R);
   const bool selL_from_L = L.lm <= R.lm;  // lambda_L = min(lm_L, lm_R)
   const bool selR_from_L = L.lp >= R.lp;  // lambda_R = max(lp_L, lp_R)
   const double lamL = selL_from_L ? L.lm : R.lm, lamR = selR_from_L ? L.lp : R.lp;
@@ -183,19 +167,25 @@ __device__ __forceinline__ void numerical_flux_vjp(const Params& p, const double
         ULb[v] = URb[v] = 0.0;
       }
     } else {
+      // F* = (sR F_L - sL F_R + sL sR dU) / den, den = sR - sL, so
+      // dF*/dsR = sL (dF - sL dU) / den^2 and dF*/dsL = -sR (dF - sR dU) / den^2
+      // (dU = U_R - U_L, dF = F_R - F_L; differences unfused so that they round alike however
+      // their operands were formed)
       const double id = 1.0 / den;
-      double sLb = 0.0, sRb = 0.0;
+      const double sRid = sR * id, sLid = sL * id, sLsRid = sL * sRid;
+      double SA = 0.0, SB = 0.0;
 #pragma unroll
       for (int v = 0; v < 5; ++v) {
-        const double dU = R.U[v] - L.U[v];
-        const double Fs = (sR * L.F[v] - sL * R.F[v] + sL * sR * dU) * id;
-        FLb[v] = sR * id * Fsb[v];
-        FRb[v] = -sL * id * Fsb[v];
-        URb[v] = sL * sR * id * Fsb[v];
+        const double dU = __dsub_rn(R.U[v], L.U[v]);
+        const double dF = __dsub_rn(R.F[v], L.F[v]);
+        SA = fma(Fsb[v], fma(-sL, dU, dF), SA);
+        SB = fma(Fsb[v], fma(-sR, dU, dF), SB);
+        FLb[v] = sRid * Fsb[v];
+        FRb[v] = -sLid * Fsb[v];
+        URb[v] = sLsRid * Fsb[v];
         ULb[v] = -URb[v];
-        sRb += Fsb[v] * (L.F[v] + sL * dU - Fs) * id;
-        sLb += Fsb[v] * (-R.F[v] + sR * dU + Fs) * id;
       }
+      const double sRb = sLid * id * SA, sLb = -sRid * id * SB;
       lamLb = actL ? sLb : 0.0;
       lamRb = actR ? sRb : 0.0;
     }
@@ -208,7 +198,7 @@ __device__ __forceinline__ void numerical_flux_vjp(const Params& p, const double
       FLb[v] = FRb[v] = 0.5 * Fsb[v];
       ULb[v] = 0.5 * a * Fsb[v];
       URb[v] = -0.5 * a * Fsb[v];
-      ab -= 0.5 * Fsb[v] * (R.U[v] - L.U[v]);
+      ab -= 0.5 * Fsb[v] * __dsub_rn(R.U[v], L.U[v]);
     }
     if (useL)
       lamLb = ab * (lamL >= 0.0 ? 1.0 : -1.0);
@@ -226,6 +216,7 @@ __device__ __forceinline__ void numerical_flux_vjp(const Params& p, const double
 // ---------------------------------------------------------------------------------------
 template <int DIM, int N, int D>
 __device__ __forceinline__ void face_vjp_point(const Params& p, const double* __restrict__ Tr,
+                                               const double* __restrict__ tape,
                                                const double* __restrict__ Rb,
                                                double* __restrict__ TrB, long long k) {
   constexpr int Nn = Shape<DIM, N>::Nn, Nt = Shape<DIM, N>::Nt;
@@ -288,7 +279,13 @@ __device__ __forceinline__ void face_vjp_point(const Params& p, const double* __
     Fsb[v] = sc * acc;
   }
   double WLb[5], WRb[5];
-  numerical_flux_vjp<D>(p, WL, WR, Fsb, WLb, WRb);
+  if (tape) {
+    const long long ts = nf * Nt;
+    const double* tp = tape + tape_base(p, D) + k;
+    numerical_flux_vjp<D>(p, WL, WR, tp, tp + kFaceTape * ts, ts, Fsb, WLb, WRb);
+  } else {
+    numerical_flux_vjp<D>(p, WL, WR, nullptr, nullptr, 0, Fsb, WLb, WRb);
+  }
   // ghost states: Dirichlet ghosts are constant, outflow ghosts copy the interior trace
   if (eL < 0 && p.bc[D][0] == 2)
 #pragma unroll
@@ -308,12 +305,13 @@ __device__ __forceinline__ void face_vjp_point(const Params& p, const double* __
 
 template <int DIM, int N>
 __global__ void __launch_bounds__(128) face_vjp_kernel(Params p, const double* __restrict__ Tr,
+                                                       const double* __restrict__ tape,
                                                        const double* __restrict__ Rb,
                                                        double* __restrict__ TrB) {
   const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (blockIdx.y == 0) face_vjp_point<DIM, N, 0>(p, Tr, Rb, TrB, k);
-  if (DIM > 1 && blockIdx.y == 1) face_vjp_point<DIM, N, (DIM > 1 ? 1 : 0)>(p, Tr, Rb, TrB, k);
-  if (DIM > 2 && blockIdx.y == 2) face_vjp_point<DIM, N, (DIM > 2 ? 2 : 0)>(p, Tr, Rb, TrB, k);
+  if (blockIdx.y == 0) face_vjp_point<DIM, N, 0>(p, Tr, tape, Rb, TrB, k);
+  if (DIM > 1 && blockIdx.y == 1) face_vjp_point<DIM, N, (DIM > 1 ? 1 : 0)>(p, Tr, tape, Rb, TrB, k);
+  if (DIM > 2 && blockIdx.y == 2) face_vjp_point<DIM, N, (DIM > 2 ? 2 : 0)>(p, Tr, tape, Rb, TrB, k);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -327,16 +325,17 @@ __device__ __forceinline__ void node_adjoint(const Params& p, const double U[5],
                                              const double Fb[DIM][5], const double Wub[5],
                                              double Ub[5]) {
   const double rho = Wu[0], P = Wu[4];
-  const double u2 = Wu[1] * Wu[1] + Wu[2] * Wu[2] + Wu[3] * Wu[3];
-  const double lor = sqrt(1.0 + u2);
-  const double ilor = 1.0 / lor;
+  const double u2 = fma(Wu[1], Wu[1], fma(Wu[2], Wu[2], Wu[3] * Wu[3]));
+  const double q = 1.0 + u2;
+  const double ilor = rsqrt(q);
+  const double lor = q * ilor;
   const double v[3] = {Wu[1] * ilor, Wu[2] * ilor, Wu[3] * ilor};
   double Wb[5] = {Wub[0], 0.0, 0.0, 0.0, Wub[4]};  // adjoint of (rho, v, P)
   // u = gamma v: du/dv = gamma I + gamma^3 v v^T (symmetric)
   const double vu = v[0] * Wub[1] + v[1] * Wub[2] + v[2] * Wub[3];
-  const double l3 = lor * lor * lor;
+  const double l3vu = lor * q * vu;
 #pragma unroll
-  for (int k = 0; k < 3; ++k) Wb[1 + k] = lor * Wub[1 + k] + l3 * v[k] * vu;
+  for (int k = 0; k < 3; ++k) Wb[1 + k] = fma(lor, Wub[1 + k], l3vu * v[k]);
   // fluxes F^d = (D v_d, S v_d + P e_d, (tau + P) v_d)
 #pragma unroll
   for (int k = 0; k < 5; ++k) Ub[k] = 0.0;
@@ -344,10 +343,10 @@ __device__ __forceinline__ void node_adjoint(const Params& p, const double U[5],
   for (int d = 0; d < DIM; ++d) {
     const double vd = v[d];
 #pragma unroll
-    for (int k = 0; k < 5; ++k) Ub[k] += vd * Fb[d][k];
+    for (int k = 0; k < 5; ++k) Ub[k] = fma(vd, Fb[d][k], Ub[k]);
     Wb[1 + d] += Fb[d][0] * U[0] + Fb[d][1] * U[1] + Fb[d][2] * U[2] + Fb[d][3] * U[3] +
                  Fb[d][4] * (U[4] + P);
-    Wb[4] += Fb[d][1 + d] + Fb[d][4] * vd;
+    Wb[4] += fma(Fb[d][4], vd, Fb[d][1 + d]);
   }
   double x[5];
   c2p_adjoint(p, rho, v, P, lor, Wb, x);
@@ -355,18 +354,20 @@ __device__ __forceinline__ void node_adjoint(const Params& p, const double U[5],
   for (int k = 0; k < 5; ++k) Ub[k] += x[k];
 }
 
+// With Ukb null: Ub = U_bar.  Otherwise the stage combination of the SSP-RK reverse sweep is
+// fused in: Unb += a_n R_bar and Ukb += b_k (R_bar + dt U_bar) (Unb and Ukb may be the same).
 template <int DIM, int N>
 __global__ void __launch_bounds__(Shape<DIM, N>::BLOCK)
     node_vjp_kernel(Params p, const double* __restrict__ U, const double* __restrict__ Wst,
-                    const double* __restrict__ Rb, const double* __restrict__ TrB,
-                    double* __restrict__ Ub) {
+                    const unsigned char* __restrict__ guard, const double* __restrict__ Rb,
+                    const double* __restrict__ TrB, double* __restrict__ Ub, double* Unb,
+                    double* Ukb, double a_n, double b_k, double dt) {
   using S = Shape<DIM, N>;
   constexpr int Nn = S::Nn, Nt = S::Nt, BLOCK = S::BLOCK;
   __shared__ double shR[5][BLOCK];
-  __shared__ double shW[5][BLOCK];
-  __shared__ double shD[N * N];
+  __shared__ double shD[DIM][N * N];  // (2/dx_d) Dhat per axis
   const int tid = threadIdx.x;
-  if (tid < N * N) shD[tid] = p.Dhat[tid];
+  if (tid < DIM * N * N) shD[tid / (N * N)][tid % (N * N)] = p.inv_half_dx[tid / (N * N)] * p.Dhat[tid % (N * N)];
   const int le = tid / Nn, li = tid - le * Nn;
   const long long e = (long long)blockIdx.x * S::EPB + le;
   const bool valid = e < p.E;
@@ -374,10 +375,7 @@ __global__ void __launch_bounds__(Shape<DIM, N>::BLOCK)
   const long long g = e * Nn + li;
   if (valid) {
 #pragma unroll
-    for (int v = 0; v < 5; ++v) {
-      shR[v][tid] = Rb[v * tot + g];
-      shW[v][tid] = Wst[v * tot + g];
-    }
+    for (int v = 0; v < 5; ++v) shR[v][tid] = Rb[v * tot + g];
   }
   __syncthreads();
   if (!valid) return;
@@ -389,32 +387,23 @@ __global__ void __launch_bounds__(Shape<DIM, N>::BLOCK)
   for (int d = 0; d < DIM; ++d) {
     const int ns = node_stride<N>(d);
     const int base = tid - ijk[d] * ns;
-    const double sc = p.inv_half_dx[d];
 #pragma unroll
     for (int v = 0; v < 5; ++v) Fb[d][v] = 0.0;
 #pragma unroll
     for (int i = 0; i < N; ++i) {
-      const double c = sc * shD[i * N + ijk[d]];
+      const double c = shD[d][i * N + ijk[d]];
 #pragma unroll
       for (int v = 0; v < 5; ++v) Fb[d][v] = fma(c, shR[v][base + i * ns], Fb[d][v]);
     }
   }
-  // transposed trace extrapolation; the face guard is re-decided exactly as in the forward pass
+  // transposed trace extrapolation; a guarded face point took the end node's primitive
   double Wub[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
 #pragma unroll
   for (int d = 0; d < DIM; ++d) {
     const int t = tan_index<DIM, N>(ijk, d);
 #pragma unroll
     for (int side = 0; side < 2; ++side) {
-      double rf = 0.0, Pf = 0.0;
-#pragma unroll
-      for (int a = 0; a < N; ++a) {
-        const int node = le * Nn + line_node<DIM, N>(d, t, a);
-        const double c = side ? p.ep[a] : p.em[a];
-        rf = fma(c, shW[0][node], rf);
-        Pf = fma(c, shW[4][node], Pf);
-      }
-      const bool guarded = !(rf > 0.0) || !(Pf > 0.0);
+      const bool guarded = guard[e * S::NFP + (d * 2 + side) * Nt + t] != 0;
       const double w = guarded ? ((ijk[d] == (side ? N - 1 : 0)) ? 1.0 : 0.0)
                                : (side ? p.ep[ijk[d]] : p.em[ijk[d]]);
       if (w != 0.0) {
@@ -428,11 +417,20 @@ __global__ void __launch_bounds__(Shape<DIM, N>::BLOCK)
 #pragma unroll
   for (int v = 0; v < 5; ++v) {
     u[v] = U[v * tot + g];
-    Wu[v] = shW[v][tid];
+    Wu[v] = Wst[v * tot + g];
   }
   node_adjoint<DIM>(p, u, Wu, Fb, Wub, out);
+  if (!Ukb) {
 #pragma unroll
-  for (int v = 0; v < 5; ++v) Ub[v * tot + g] = out[v];
+    for (int v = 0; v < 5; ++v) Ub[v * tot + g] = out[v];
+  } else {
+#pragma unroll
+    for (int v = 0; v < 5; ++v) {
+      const double y = shR[v][tid];
+      if (a_n != 0.0) Unb[v * tot + g] += a_n * y;
+      Ukb[v * tot + g] += b_k * fma(dt, out[v], y);  // re-read: Ukb may be Unb
+    }
+  }
 }
 
 // ---------------------------------------------------------------------------------------

@@ -32,6 +32,11 @@ struct StageArgs {
   double* Ubar;        // VjpNode / EnforceVjp: output adjoint of U
   double* TrBar;       // VjpFace output / VjpNode input: adjoints of the face traces
   double* Wstore;      // Volume: optional output of the nodal (rho, u, P); VjpNode: its input
+  unsigned char* guard;  // Volume: optional face-guard flag per face point [E][NFP]; VjpNode: input
+  double* tape;        // Face: optional face-state tape (roots and reciprocals); VjpFace: input
+  // VjpNode with Ukb set: fused stage combination Unb += a_n Rbar, Ukb += b_k (Rbar + dt Ubar)
+  double* Unb;
+  double* Ukb;
   const double* s_in;  // EnforceVjp: smoothing factor per element
   const double* Tbar;  // EnforceVjp: adjoint of the smoothed state
 };
@@ -44,8 +49,6 @@ cudaError_t launch_prim2cons(const Params& p, cudaStream_t s, long long n, const
                              double* U);
 cudaError_t launch_con2prim(const Params& p, cudaStream_t s, long long n, const double* U,
                             double* W, int* iters);
-cudaError_t launch_stage_combine(cudaStream_t s, long long n, const double* Yb, const double* Vb,
-                                 double a_n, double b_k, double dt, double* Unb, double* Ukb);
 cudaError_t launch_con2prim_vjp(const Params& p, cudaStream_t s, long long n, const double* U,
                                 const double* Wb, double* Ub);
 

@@ -6,6 +6,11 @@
 namespace dgsrhd {
 
 constexpr int kMaxN = 5;  // degree <= 4
+// Values per face state that the forward sweep can save for the reverse one: the roots and
+// reciprocals 1/gamma, 1/sigma, 1/Z, 1/(gamma + 1), 1/(A + B), 1/r (the first six), then u^2,
+// gamma, sigma, A, B, K, rho (h - 1), the conserved state U[5], r and the wavespeeds lambda-+.
+constexpr int kFaceTape = 21;
+constexpr int kFaceTapeRecips = 6;
 
 // Indices into the device counter array (unsigned long long).
 enum StatSlot {

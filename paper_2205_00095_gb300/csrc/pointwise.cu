@@ -59,20 +59,6 @@ __global__ void __launch_bounds__(256) con2prim_kernel(Params p, long long n,
   }
 }
 
-// Reverse sweep of one RK stage, elementwise: Unb += a_n Yb (when a_n != 0) and
-// Ukb += b_k (Yb + dt Vb), with Vb = (dR/dU)^T Yb at the stage input.
-__global__ void __launch_bounds__(256) stage_combine_kernel(long long n, const double* __restrict__ Yb,
-                                                            const double* __restrict__ Vb, double a_n,
-                                                            double b_k, double dt, double* Unb,
-                                                            double* Ukb) {
-  for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < n;
-       k += (long long)gridDim.x * blockDim.x) {
-    const double y = Yb[k];
-    if (a_n != 0.0) Unb[k] += a_n * y;
-    Ukb[k] += b_k * fma(dt, Vb[k], y);
-  }
-}
-
 // U_bar = (dW/dU)^T W_bar for W = con2prim(U), W = (rho, v, P): con2prim at the node, then the
 // implicit-function-theorem solve (dU/dW)^T U_bar = W_bar.
 __global__ void __launch_bounds__(256) con2prim_vjp_kernel(Params p, long long n,
@@ -111,12 +97,6 @@ cudaError_t launch_prim2cons(const Params& p, cudaStream_t s, long long n, const
 cudaError_t launch_con2prim(const Params& p, cudaStream_t s, long long n, const double* U,
                             double* W, int* iters) {
   con2prim_kernel<<<grid_for(n), 256, 0, s>>>(p, n, U, W, iters);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_stage_combine(cudaStream_t s, long long n, const double* Yb, const double* Vb,
-                                 double a_n, double b_k, double dt, double* Unb, double* Ukb) {
-  stage_combine_kernel<<<grid_for(n), 256, 0, s>>>(n, Yb, Vb, a_n, b_k, dt, Unb, Ukb);
   return cudaGetLastError();
 }
 
