@@ -59,8 +59,22 @@ __device__ __forceinline__ void prim_v_to_cons(const Params& p, const double W[5
 // and D > 0 this holds exactly when tau > 0 and tau (tau + 2 D) > |S|^2: no root, no division,
 // no cancellation of D for cold states.
 // ---------------------------------------------------------------------------------------
+// Sign and order tests read from the bit pattern (integer pipe instead of FP64 compares).  A
+// double that is not NaN is > 0 exactly when its pattern, as a signed 64-bit integer, lies in
+// (0, +inf], and two non-negative doubles order as their patterns do.
+__device__ __forceinline__ long long dbits(double x) { return __double_as_longlong(x); }
+constexpr long long kInfBits = 0x7ff0000000000000LL;
+__device__ __forceinline__ bool pos_bits(double x) {  // x > 0 (false for NaN)
+  const long long b = dbits(x);
+  return b > 0 && b <= kInfBits;
+}
+__device__ __forceinline__ bool finite_bits(double x) { return (dbits(x) & kInfBits) != kInfBits; }
+
+// D > 0, tau > 0 and tau (tau + 2D) > S^2 (S2 >= 0 or NaN; a NaN makes it false)
 __device__ __forceinline__ bool admissible_parts(double D, double S2, double tau) {
-  return D > 0.0 && tau > 0.0 && tau * (tau + 2.0 * D) > S2;
+  const long long s2 = dbits(S2);
+  return pos_bits(D) && pos_bits(tau) && s2 >= 0 && s2 <= kInfBits &&
+         dbits(tau * (tau + 2.0 * D)) > s2;
 }
 
 __device__ __forceinline__ bool admissible(const double U[5]) {
@@ -74,12 +88,13 @@ __device__ __forceinline__ bool admissible(const double U[5]) {
 // Ideal EOS, closed form: monic quartic beta^4 + a3 beta^3 + a2 beta^2 + a1 beta + a0 with
 // the coefficients of Sec. 3.1, its resolvent cubic (i1, i2, i3), Cardano's root x of the
 // resolvent (trigonometric form when T < 0), the quadratic factor beta^2 + B beta + C.
-__device__ __forceinline__ double beta_ideal_closed_form(double G, double xi, double eta) {
+__device__ __forceinline__ double beta_ideal_closed_form(double G, double xi, double eta,
+                                                         double inv) {
+  // inv = 1 / ((G - 1)^2 (1 + xi^2)) is passed in (formed with 1/D from one division)
   const double gm1 = G - 1.0;
-  const double inv = 1.0 / (gm1 * gm1 * fma(xi, xi, 1.0));
-  const double a3 = -2.0 * G * gm1 * xi * eta * inv;
-  const double a2 = (G * G * eta * eta + 2.0 * gm1 * xi * xi - gm1 * gm1) * inv;
   const double a1 = -2.0 * G * xi * eta * inv;
+  const double a3 = gm1 * a1;
+  const double a2 = (G * G * eta * eta + 2.0 * gm1 * xi * xi - gm1 * gm1) * inv;
   const double a0 = xi * xi * inv;
   const double i1 = -a2;
   const double i2 = a3 * a1 - 4.0 * a0;
@@ -88,11 +103,19 @@ __device__ __forceinline__ double beta_ideal_closed_form(double G, double xi, do
   const double S = (3.0 * i2 - i1 * i1) * (1.0 / 9.0);
   const double T = R * R + S * S * S;
   double x;
-  if (T < 0.0) {
+  if (dbits(T) < 0 && dbits(T) != (long long)0x8000000000000000ULL) {  // T < 0
     x = 2.0 * pow(R * R - T, 1.0 / 6.0) * cos(atan2(sqrt(-T), R) * (1.0 / 3.0)) - i1 * (1.0 / 3.0);
   } else {
-    const double sT = sqrt(T);
-    x = cbrt(R + sT) + cbrt(R - sT) - i1 * (1.0 / 3.0);
+    // Cardano's pair cbrt(R + sqrt(T)) + cbrt(R - sqrt(T)): their product is -S, so with
+    // y = R + sign(R) sqrt(T) (no cancellation) the pair is y^(1/3) - S y^(-1/3), both from
+    // one reciprocal cube root r = y^(-1/3): y^(1/3) = y r^2.
+    const double y = R + copysign(sqrt(T), R);
+    if (y == 0.0) {
+      x = -i1 * (1.0 / 3.0);
+    } else {
+      const double r = rcbrt(y);
+      x = fma(y * r, r, -S * r) - i1 * (1.0 / 3.0);
+    }
   }
   const double B = 0.5 * (a3 + sqrt(a3 * a3 - 4.0 * a2 + 4.0 * x));
   const double C = 0.5 * (x - sqrt(x * x - 4.0 * a0));
@@ -353,43 +376,63 @@ __device__ __forceinline__ int con2prim(const Params& p, const double U[5], Prim
   const double S2 = U[1] * U[1] + U[2] * U[2] + U[3] * U[3];
   iters = 0;
   const double nanv = __longlong_as_double(0x7ff8000000000000LL);
-  if (!admissible_parts(D, S2, tau) || !isfinite(S2) || !isfinite(tau)) {
+  if (!admissible_parts(D, S2, tau) || !finite_bits(S2) || !finite_bits(tau)) {
     W.rho = W.v[0] = W.v[1] = W.v[2] = W.P = W.lor = nanv;
     return 1;
   }
-  const double iD = 1.0 / D;
-  const double rS = (S2 > 0.0) ? rsqrt(S2) : 0.0;  // 1/|S|
+  const bool moving = dbits(S2) != 0;  // S2 > 0 (S2 is finite and >= 0 here)
+  const double rS = moving ? rsqrt(S2) : 0.0;  // 1/|S|
   const double S = S2 * rS;
+  const bool closed_ideal = p.eos == 0 && p.c2p == 0;
+  double iD, inv = 0.0;
+  if (closed_ideal) {
+    // 1/D and the quartic's 1/((G - 1)^2 (1 + xi^2)) = D^2/((G - 1)^2 (D^2 + S^2)) from one
+    // division: t = 1/(D (G - 1)^2 (D^2 + S^2))
+    const double gm1 = p.gamma_ad - 1.0;
+    const double q = gm1 * gm1 * fma(D, D, S2);
+    const double t = 1.0 / (D * q);
+    iD = t * q;
+    inv = t * D * D * D;
+  } else {
+    iD = 1.0 / D;
+  }
   const double xi = S * iD;
   const double eta = fma(tau, iD, 1.0);
   // beta = |v|, ginv = 1/gamma, omg = 1 - 1/gamma (cancellation-free per method)
-  double beta, ginv, omg;
+  double beta, ginv, lor, omg = 0.0, Wl = 0.0;
   bool conv = true;
-  if (S2 == 0.0) {
+  if (!moving) {
     beta = 0.0;
     ginv = 1.0;
-    omg = 0.0;
-  } else if (p.eos == 0 && p.c2p == 0) {
-    beta = beta_ideal_closed_form(p.gamma_ad, xi, eta);
-    conv = (beta >= 0.0 && beta < 1.0);
-    ginv = sqrt(1.0 - beta * beta);
-    omg = beta * beta / (1.0 + ginv);
+    lor = 1.0;
+  } else if (closed_ideal) {
+    beta = beta_ideal_closed_form(p.gamma_ad, xi, eta, inv);
+    conv = dbits(beta) >= 0 && dbits(beta) < dbits(1.0);  // 0 <= beta < 1
+    // gamma = (1 - beta^2)^(-1/2) from rsqrt; 1 - 1/gamma = beta^2 gamma / (gamma + 1)
+    const double b2 = beta * beta;
+    const double om = 1.0 - b2;
+    lor = rsqrt(om);
+    ginv = om * lor;
+    omg = b2 * lor / (lor + 1.0);
   } else if (p.eos == 0) {
     const double w = w_ideal_newton(p.alpha, xi, eta, p.max_iter, iters, conv);
     const double w2 = w * w;
-    const double i1w2 = 1.0 / (1.0 + w2);
+    // beta = 2w/(1 + w^2), 1/gamma = (1 - w^2)/(1 + w^2), gamma from the same division
+    const double ap = 1.0 + w2, am = 1.0 - w2;
+    const double t = 1.0 / (ap * am);
+    const double i1w2 = t * am;
     beta = 2.0 * w * i1w2;
-    ginv = (1.0 - w2) * i1w2;
+    ginv = am * i1w2;
     omg = 2.0 * w2 * i1w2;
-    conv = conv && (w > 0.0 && w < 1.0);
+    lor = t * ap * ap;
+    conv = conv && dbits(w) > 0 && dbits(w) < dbits(1.0);  // 0 < w < 1
   } else {
-    const double Wl = (p.c2p == 0) ? W_tm_closed_form(xi, eta)
-                                   : W_tm_brent(xi, eta, p.max_iter, iters, conv);
-    conv = conv && (Wl >= 0.0) && isfinite(Wl);
-    const double lor = sqrt(Wl + 1.0);
-    ginv = 1.0 / lor;
+    Wl = (p.c2p == 0) ? W_tm_closed_form(xi, eta) : W_tm_brent(xi, eta, p.max_iter, iters, conv);
+    conv = conv && dbits(Wl) >= 0 && finite_bits(Wl);  // Wl >= 0 and finite
+    const double q = Wl + 1.0;  // gamma^2
+    ginv = rsqrt(q);
+    lor = q * ginv;
     beta = sqrt(Wl) * ginv;
-    omg = Wl * ginv / (lor + 1.0);
   }
   const double rho = D * ginv;
   const double vs = beta * rS;  // v = beta S / |S|
@@ -397,17 +440,23 @@ __device__ __forceinline__ int con2prim(const Params& p, const double U[5], Prim
   W.v[1] = vs * U[2];
   W.v[2] = vs * U[3];
   const double Sv = beta * S;  // S.v
-  const double e_m_rho = tau - Sv + D * omg;  // E - S.v - rho
   double P;
   if (p.eos == 0) {
+    const double e_m_rho = tau - Sv + D * omg;  // E - S.v - rho
     P = (p.gamma_ad - 1.0) * e_m_rho;
   } else {
+    // 1 - 1/gamma = W/(gamma (gamma + 1)) and P = (E - S.v - rho)(E - S.v + rho)/(3(E - S.v)):
+    // 1/(gamma + 1) and 1/(3(E - S.v)) from one division
     const double Ev = tau + D - Sv;  // E - S.v
-    P = e_m_rho * (Ev + rho) / (3.0 * Ev);
+    const double L1 = lor + 1.0, E3 = 3.0 * Ev;
+    const double t = 1.0 / (L1 * E3);
+    omg = Wl * ginv * E3 * t;
+    const double e_m_rho = tau - Sv + D * omg;
+    P = e_m_rho * (Ev + rho) * L1 * t;
   }
   W.rho = rho;
   W.P = P;
-  W.lor = 1.0 / ginv;
+  W.lor = lor;
   return conv ? 0 : 2;
 }
 

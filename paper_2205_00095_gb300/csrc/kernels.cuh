@@ -191,7 +191,7 @@ __global__ void __launch_bounds__(Shape<DIM, N>::BLOCK)
 #pragma unroll
         for (int v = 0; v < 5; ++v) out[v] = fma(c, shW[v][node], out[v]);
       }
-      const bool guarded = !(out[0] > 0.0) || !(out[4] > 0.0);
+      const bool guarded = !pos_bits(out[0]) || !pos_bits(out[4]);
       if (guarded) {
         const int node = le * Nn + line_node<DIM, N>(d, t, side ? N - 1 : 0);
 #pragma unroll
