@@ -635,13 +635,19 @@ __device__ __forceinline__ void numerical_flux(const Params& p, const double WL[
 //   gamma y_D + w_rho gamma^2 (a + y_E)                       = W_bar_rho
 //   rho gamma^3 v y_D + w gamma^2 y_S + 2 w gamma^4 v (a + y_E) = W_bar_v
 //   w_P gamma^2 a + (w_P gamma^2 - 1) y_E                     = W_bar_P
-// The v equation gives y_S = (W_bar_v - c v) / (w gamma^2), c = rho gamma^3 y_D + 2 w gamma^4 (a + y_E);
-// projected on v it closes a 3 x 3 system in (y_D, a, y_E), solved by Cramer's rule.
+// The v equation gives y_S = (W_bar_v - c v) / (w gamma^2), c = rho gamma^3 y_D + 2 w gamma^4 s
+// with s = a + y_E; projected on v it closes a 3 x 3 system in (y_D, a, y_E).  Its first and
+// third rows give y_D = W_bar_rho / gamma - w_rho gamma s and y_E = w_P gamma^2 s - W_bar_P, and
+// the projected second row then leaves one equation for s:
+//   gamma^2 [w (1 - w_P gamma^2) + u^2 (2w - rho w_rho)] s
+//       = v . W_bar_v - w gamma^2 W_bar_P - rho u^2 W_bar_rho        (u^2 = gamma^2 v^2).
+// lor = gamma, ilor = 1/gamma, g2 = gamma^2, u2 = gamma^2 v^2 are passed in.
 __device__ __forceinline__ void c2p_adjoint(const Params& p, double rho, const double v[3], double P,
-                                            double lor, const double Wb[5], double Ub[5]) {
+                                            double lor, double ilor, double g2, double u2,
+                                            const double Wb[5], double Ub[5]) {
   double w, w_r, w_P;
   if (p.eos == 0) {
-    w = rho + p.alpha * P;
+    w = fma(p.alpha, P, rho);
     w_r = 1.0;
     w_P = p.alpha;
   } else {
@@ -652,32 +658,21 @@ __device__ __forceinline__ void c2p_adjoint(const Params& p, double rho, const d
     w_r = (2.0 / 3.0) * rho * isg;
     w_P = fma(1.5 * P, isg, 2.5);
   }
-  const double g2 = lor * lor, g3 = g2 * lor, g4 = g2 * g2;
-  const double v2 = v[0] * v[0] + v[1] * v[1] + v[2] * v[2];
-  const double vW = v[0] * Wb[1] + v[1] * Wb[2] + v[2] * Wb[3];
-  // rows: (y_D, a, y_E) coefficients and right-hand sides
-  //  (1) gamma y_D + w_r g2 a + w_r g2 y_E = Wb_rho
-  //  (2) v2 rho g3 y_D + (w g2 + 2 w g4 v2) a + 2 w g4 v2 y_E = vW
-  //  (3) 0 y_D + w_P g2 a + (w_P g2 - 1) y_E = Wb_P
-  const double m11 = lor, m12 = w_r * g2, m13 = w_r * g2;
-  const double m21 = v2 * rho * g3, m22 = w * g2 + 2.0 * w * g4 * v2, m23 = 2.0 * w * g4 * v2;
-  const double m32 = w_P * g2, m33 = w_P * g2 - 1.0;
-  const double r1 = Wb[0], r2 = vW, r3 = Wb[4];
-  const double c11 = m22 * m33 - m23 * m32;
-  const double c12 = m21 * m33;           // minus sign applied below
-  const double c13 = m21 * m32;
-  const double det = m11 * c11 - m12 * c12 + m13 * c13;
-  // 1/det and 1/(w gamma^2) from one division
-  const double wg2 = w * g2;
-  const double t = 1.0 / (det * wg2);
-  const double idet = t * wg2, iw = t * det;
-  const double yD = (r1 * c11 - m12 * (r2 * m33 - m23 * r3) + m13 * (r2 * m32 - m22 * r3)) * idet;
-  const double a = (m11 * (r2 * m33 - m23 * r3) - r1 * c12 + m13 * (m21 * r3)) * idet;
-  const double yE = (m11 * (m22 * r3 - r2 * m32) - m12 * (m21 * r3) + r1 * c13) * idet;
-  const double c = rho * g3 * yD + 2.0 * w * g4 * (a + yE);
+  const double vW = fma(v[0], Wb[1], fma(v[1], Wb[2], v[2] * Wb[3]));
+  const double wg2 = w * g2, wPg2 = w_P * g2;
+  const double Kp = fma(u2, fma(-rho, w_r, 2.0 * w), w * (1.0 - wPg2));
+  const double num = fma(-rho * u2, Wb[0], fma(-wg2, Wb[4], vW));
+  // 1/(gamma^2 K') and 1/(w gamma^2) from one division
+  const double gK = g2 * Kp;
+  const double t = 1.0 / (gK * wg2);
+  const double s = num * (t * wg2);
+  const double iw = t * gK;
+  const double yD = fma(-w_r * lor, s, Wb[0] * ilor);
+  const double yE = fma(wPg2, s, -Wb[4]);
+  const double c = fma(rho * g2 * lor, yD, 2.0 * wg2 * g2 * s);
   Ub[0] = yD + yE;
 #pragma unroll
-  for (int k = 0; k < 3; ++k) Ub[1 + k] = (Wb[1 + k] - c * v[k]) * iw;
+  for (int k = 0; k < 3; ++k) Ub[1 + k] = fma(-c, v[k], Wb[1 + k]) * iw;
   Ub[4] = yE;
 }
 

@@ -349,7 +349,7 @@ __device__ __forceinline__ void node_adjoint(const Params& p, const double U[5],
     Wb[4] += fma(Fb[d][4], vd, Fb[d][1 + d]);
   }
   double x[5];
-  c2p_adjoint(p, rho, v, P, lor, Wb, x);
+  c2p_adjoint(p, rho, v, P, lor, ilor, q, u2, Wb, x);
 #pragma unroll
   for (int k = 0; k < 5; ++k) Ub[k] += x[k];
 }

@@ -76,7 +76,9 @@ __global__ void __launch_bounds__(256) con2prim_vjp_kernel(Params p, long long n
     Prim w;
     int it;
     con2prim(p, u, w, it);
-    c2p_adjoint(p, w.rho, w.v, w.P, w.lor, wb, out);
+    const double g2 = w.lor * w.lor;
+    const double v2 = w.v[0] * w.v[0] + w.v[1] * w.v[1] + w.v[2] * w.v[2];
+    c2p_adjoint(p, w.rho, w.v, w.P, w.lor, 1.0 / w.lor, g2, g2 * v2, wb, out);
 #pragma unroll
     for (int v = 0; v < 5; ++v) Ub[v * n + k] = out[v];
   }
