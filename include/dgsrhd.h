@@ -236,6 +236,15 @@ int32_t dgsrhd_kernel_times(dgsrhd_ctx* ctx, double* ms, int64_t* counts, int32_
 int32_t dgsrhd_rhs_noalloc(const dgsrhd_config* cfg, void* stream, const double* U, double* R,
                            dgsrhd_stats* stats_out);
 
+/* Diagnostic (no paper counterpart): the library's FP64 reciprocal and square root primitives
+ * next to CUDA's own, for checking the former against the latter.
+ * x:   DEVICE, n doubles.  out: DEVICE, 4 n doubles, written as four blocks of n:
+ *      [ reciprocal 1/x by Newton-Raphson refinement of an FP32 seed | 1.0 / x (division) |
+ *        sqrt(x) as x rsqrt(x) | sqrt(x) ].
+ * stream: cudaStream_t or NULL for the default stream; the call only queues the kernel.
+ * Returns DGSRHD_EINVAL for null pointers or n < 0, DGSRHD_ECUDA on a launch failure. */
+int32_t dgsrhd_math_check(const double* x, int64_t n, double* out, void* stream);
+
 /* Human-readable name of a status code. */
 const char* dgsrhd_status_string(int32_t status);
 

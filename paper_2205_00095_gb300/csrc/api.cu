@@ -746,6 +746,11 @@ int32_t dgsrhd_con2prim_vjp(dgsrhd_ctx* c, const double* U, const double* W_bar,
   return cuda_status(e);
 }
 
+int32_t dgsrhd_math_check(const double* x, int64_t n, double* out, void* stream) {
+  if (!x || !out || n < 0) return DGSRHD_EINVAL;
+  return cuda_status(dgsrhd::launch_math_check((cudaStream_t)stream, n, x, out));
+}
+
 const char* dgsrhd_status_string(int32_t s) {
   switch (s) {
     case DGSRHD_OK: return "ok";

@@ -10,6 +10,7 @@
 #include <math.h>
 #include <stdint.h>
 
+#include "bits.cuh"
 #include "params.h"
 
 namespace dgsrhd {
@@ -109,7 +110,7 @@ __device__ __forceinline__ double beta_ideal_closed_form(double G, double xi, do
     // Cardano's pair cbrt(R + sqrt(T)) + cbrt(R - sqrt(T)): their product is -S, so with
     // y = R + sign(R) sqrt(T) (no cancellation) the pair is y^(1/3) - S y^(-1/3), both from
     // one reciprocal cube root r = y^(-1/3): y^(1/3) = y r^2.
-    const double y = R + copysign(sqrt(T), R);
+    const double y = R + copysign(sqrt_rs(T), R);
     if (y == 0.0) {
       x = -i1 * (1.0 / 3.0);
     } else {
@@ -117,9 +118,12 @@ __device__ __forceinline__ double beta_ideal_closed_form(double G, double xi, do
       x = fma(y * r, r, -S * r) - i1 * (1.0 / 3.0);
     }
   }
-  const double B = 0.5 * (a3 + sqrt(a3 * a3 - 4.0 * a2 + 4.0 * x));
-  const double C = 0.5 * (x - sqrt(x * x - 4.0 * a0));
-  return 0.5 * (-B + sqrt(B * B - 4.0 * C));
+  // The three radicands are non-negative for an admissible state; as xi -> 0 they shrink to
+  // rounding level and can round below zero, so a negative one is taken as zero.
+  auto root0 = [](double r) { return sqrt_rs(dbits(r) < 0 ? 0.0 : r); };
+  const double B = 0.5 * (a3 + root0(a3 * a3 - 4.0 * a2 + 4.0 * x));
+  const double C = 0.5 * (x - root0(x * x - 4.0 * a0));
+  return 0.5 * (-B + root0(B * B - 4.0 * C));
 }
 
 // Ideal EOS, Newton-Raphson on the Riccardi quartic in w, beta = 2w/(1 + w^2)
@@ -131,7 +135,7 @@ __device__ __forceinline__ double beta_ideal_closed_form(double G, double xi, do
 __device__ __forceinline__ double w_ideal_newton(double al, double xi, double eta, int max_iter,
                                                  int& iters, bool& conv) {
   const double k1 = al * eta - 1.0;
-  const double ik1 = 1.0 / k1;
+  const double ik1 = recip_nr(k1);
   const double ik1sq = ik1 * ik1;
   const double series = (al - 1.0) * 0.5 * ik1 * xi +
                         (al - 1.0) * (al - 1.0) * 0.125 * ik1sq * ik1sq *
@@ -142,8 +146,10 @@ __device__ __forceinline__ double w_ideal_newton(double al, double xi, double et
   const double c4 = (al - 1.0) * xi, c3 = -2.0 * (al * eta + 1.0), c2 = 2.0 * (al + 1.0) * xi,
                c1 = -2.0 * k1, c0 = c4;
   // FP32 phase
-  const float f4 = (float)c4, f3 = (float)c3, f2 = (float)c2, f1 = (float)c1, f0 = (float)c0;
-  float wf = fminf(fmaxf((float)series, 1e-30f), 1.0f - 6e-8f);
+  // conversions on the bit patterns (a cast would issue on the FP64 pipe)
+  const float f4 = f64_to_f32_bits(c4), f3 = f64_to_f32_bits(c3), f2 = f64_to_f32_bits(c2),
+              f1 = f64_to_f32_bits(c1), f0 = f64_to_f32_bits(c0);
+  float wf = fminf(fmaxf(f64_to_f32_bits(series), 1e-30f), 1.0f - 6e-8f);
   int it = 0;
   const int max32 = max_iter - 2;  // the FP64 phase keeps at least two iterations
   while (it < max32) {
@@ -154,13 +160,13 @@ __device__ __forceinline__ double w_ideal_newton(double al, double xi, double et
     ++it;
     if (!(fabsf(dw) > 1e-6f * wf)) break;  // also leaves on NaN
   }
-  double w = (wf > 0.0f && wf < 1.0f) ? (double)wf : fmin(fmax(series, 1e-300), 1.0 - 1e-15);
+  double w = (wf > 0.0f && wf < 1.0f) ? f32_to_f64_bits(wf) : fmin(fmax(series, 1e-300), 1.0 - 1e-15);
   // FP64 phase
   conv = false;
   while (it < max_iter) {
     const double Pw = fma(fma(fma(fma(c4, w, c3), w, c2), w, c1), w, c0);
     const double dP = fma(fma(fma(4.0 * c4, w, 3.0 * c3), w, 2.0 * c2), w, c1);
-    const double dw = Pw / dP;
+    const double dw = Pw * recip_nr(dP);
     w -= dw;
     ++it;
     if (fabs(dw) <= 1e-14 * w) {
@@ -181,7 +187,7 @@ __device__ __forceinline__ Cubic tm_cubic(double xi, double eta) {
   const double e2 = eta * eta, x2 = xi * xi;
   const double s = e2 + x2;
   const double dm = e2 - x2;
-  const double idm2 = 1.0 / (dm * dm);
+  const double idm2 = recip_nr(dm * dm);
   const double k = 4.0 * s - (x2 + 1.0);
   Cubic c;
   c.c1 = (s * k - 14.0 * x2 * e2) * 0.5 * idm2;
@@ -300,14 +306,15 @@ static __device__ __noinline__ double W_tm_brent(double xi, double eta, int max_
   // admissible state; eta - xi is formed in FP64 (it cancels at large Lorentz factors) and the
   // bound is widened by 1e-3 relative and capped at the paper's 200^2 - 1.  Any state whose
   // bound fails the sign check takes FP64 Brent on the paper's bracket below.
-  const float g1 = (float)cc.c1, g2 = (float)cc.c2, g3 = (float)cc.c3;
+  // conversions on the bit patterns (a cast would issue on the FP64 pipe)
+  const float g1 = f64_to_f32_bits(cc.c1), g2 = f64_to_f32_bits(cc.c2), g3 = f64_to_f32_bits(cc.c3);
   auto ff = [&](float W) { return ((W + g1) * W + g2) * W + g3; };
   int it32 = 0;
   bool conv32 = false;
   float W32 = 0.0f;
-  const float x = (float)xi, exm = (float)(eta - xi);
+  const float x = f64_to_f32_bits(xi), exm = f64_to_f32_bits(eta - xi);
   if (exm > 0.0f && g3 < 0.0f) {
-    const float hi32 = fminf(x * x / (exm * ((float)eta + x)) * 1.001f + 1e-30f, 39999.0f);
+    const float hi32 = fminf(x * x / (exm * (f64_to_f32_bits(eta) + x)) * 1.001f + 1e-30f, 39999.0f);
     const float fh32 = ff(hi32);
     if (fh32 > 0.0f) {
       const int max32 = max_iter > 2 ? max_iter - 2 : 1;  // the FP64 phase keeps the rest
@@ -317,11 +324,12 @@ static __device__ __noinline__ double W_tm_brent(double xi, double eta, int max_
   }
   // FP64 phase: safeguarded Newton inside a tight bracket around the FP32 root
   if (conv32 && W32 > 0.0f) {
-    double a = (double)W32 * (1.0 - 1e-5), b = (double)W32 * (1.0 + 1e-5);
+    const double W32d = f32_to_f64_bits(W32);
+    double a = W32d * (1.0 - 1e-5), b = W32d * (1.0 + 1e-5);
     const double fa = cubic_at(cc, a), fb = cubic_at(cc, b);
     if (fa * fb <= 0.0) {
       const bool rising = fa < 0.0;  // the cubic runs from fa to fb across [a, b]
-      double W = (double)W32;
+      double W = W32d;
       int it = it32;
       while (it < max_iter) {
         ++it;
@@ -335,7 +343,7 @@ static __device__ __noinline__ double W_tm_brent(double xi, double eta, int max_
         else
           b = W;
         const double df = fma(fma(3.0, W, 2.0 * cc.c1), W, cc.c2);
-        const double Wn = W - f / df;
+        const double Wn = W - f * recip_nr(df);
         // stop on a Newton step at rounding level before the bracket test: once W sits on
         // the root, rounding noise in f can move a bracket end onto W itself
         if (fabs(Wn - W) <= 2.0 * 2.220446049250313e-16 * fabs(W) + 1e-300) {
@@ -390,11 +398,11 @@ __device__ __forceinline__ int con2prim(const Params& p, const double U[5], Prim
     // division: t = 1/(D (G - 1)^2 (D^2 + S^2))
     const double gm1 = p.gamma_ad - 1.0;
     const double q = gm1 * gm1 * fma(D, D, S2);
-    const double t = 1.0 / (D * q);
+    const double t = recip_nr(D * q);
     iD = t * q;
     inv = t * D * D * D;
   } else {
-    iD = 1.0 / D;
+    iD = recip_nr(D);
   }
   const double xi = S * iD;
   const double eta = fma(tau, iD, 1.0);
@@ -413,13 +421,13 @@ __device__ __forceinline__ int con2prim(const Params& p, const double U[5], Prim
     const double om = 1.0 - b2;
     lor = rsqrt(om);
     ginv = om * lor;
-    omg = b2 * lor / (lor + 1.0);
+    omg = b2 * recip_nr(1.0 + ginv);  // = b2 gamma / (gamma + 1)
   } else if (p.eos == 0) {
     const double w = w_ideal_newton(p.alpha, xi, eta, p.max_iter, iters, conv);
     const double w2 = w * w;
     // beta = 2w/(1 + w^2), 1/gamma = (1 - w^2)/(1 + w^2), gamma from the same division
     const double ap = 1.0 + w2, am = 1.0 - w2;
-    const double t = 1.0 / (ap * am);
+    const double t = recip_nr(ap * am);
     const double i1w2 = t * am;
     beta = 2.0 * w * i1w2;
     ginv = am * i1w2;
@@ -432,7 +440,7 @@ __device__ __forceinline__ int con2prim(const Params& p, const double U[5], Prim
     const double q = Wl + 1.0;  // gamma^2
     ginv = rsqrt(q);
     lor = q * ginv;
-    beta = sqrt(Wl) * ginv;
+    beta = sqrt_rs(Wl) * ginv;
   }
   const double rho = D * ginv;
   const double vs = beta * rS;  // v = beta S / |S|
@@ -449,7 +457,7 @@ __device__ __forceinline__ int con2prim(const Params& p, const double U[5], Prim
     // 1/(gamma + 1) and 1/(3(E - S.v)) from one division
     const double Ev = tau + D - Sv;  // E - S.v
     const double L1 = lor + 1.0, E3 = 3.0 * Ev;
-    const double t = 1.0 / (L1 * E3);
+    const double t = recip_nr(L1 * E3);
     omg = Wl * ginv * E3 * t;
     const double e_m_rho = tau - Sv + D * omg;
     P = e_m_rho * (Ev + rho) * L1 * t;
@@ -525,12 +533,12 @@ __device__ __forceinline__ void face_state_core(const Params& p, const double Wu
     c.id1 = rec[3];
     c.i = rec[4];
   } else if (p.eos == 0) {
-    const double t = 1.0 / (L1 * AB);
+    const double t = recip_nr(L1 * AB);
     c.id1 = t * AB;
     c.i = t * L1;
   } else {
     const double ZL = c.Z * L1;
-    const double t = 1.0 / (ZL * AB);
+    const double t = recip_nr(ZL * AB);
     c.iZ = t * L1 * AB;
     c.id1 = t * c.Z * AB;
     c.i = t * ZL;
@@ -617,7 +625,7 @@ __device__ __forceinline__ void numerical_flux(const Params& p, const double WL[
 #pragma unroll
       for (int v = 0; v < 5; ++v) Fs[v] = 0.5 * (FL[v] + FR[v]);
     } else {
-      const double id = 1.0 / den;
+      const double id = recip_nr(den);
 #pragma unroll
       for (int v = 0; v < 5; ++v) Fs[v] = (sR * FL[v] - sL * FR[v] + sL * sR * (R.U[v] - L.U[v])) * id;
     }
@@ -664,7 +672,7 @@ __device__ __forceinline__ void c2p_adjoint(const Params& p, double rho, const d
   const double num = fma(-rho * u2, Wb[0], fma(-wg2, Wb[4], vW));
   // 1/(gamma^2 K') and 1/(w gamma^2) from one division
   const double gK = g2 * Kp;
-  const double t = 1.0 / (gK * wg2);
+  const double t = recip_nr(gK * wg2);
   const double s = num * (t * wg2);
   const double iw = t * gK;
   const double yD = fma(-w_r * lor, s, Wb[0] * ilor);

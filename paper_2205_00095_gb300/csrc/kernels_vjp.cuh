@@ -171,7 +171,7 @@ __device__ __forceinline__ void numerical_flux_vjp(const Params& p, const double
       // dF*/dsR = sL (dF - sL dU) / den^2 and dF*/dsL = -sR (dF - sR dU) / den^2
       // (dU = U_R - U_L, dF = F_R - F_L; differences unfused so that they round alike however
       // their operands were formed)
-      const double id = 1.0 / den;
+      const double id = recip_nr(den);
       const double sRid = sR * id, sLid = sL * id, sLsRid = sL * sRid;
       double SA = 0.0, SB = 0.0;
 #pragma unroll

@@ -49,6 +49,7 @@ cudaError_t launch_prim2cons(const Params& p, cudaStream_t s, long long n, const
                              double* U);
 cudaError_t launch_con2prim(const Params& p, cudaStream_t s, long long n, const double* U,
                             double* W, int* iters);
+cudaError_t launch_math_check(cudaStream_t s, long long n, const double* x, double* out);
 cudaError_t launch_con2prim_vjp(const Params& p, cudaStream_t s, long long n, const double* U,
                                 const double* Wb, double* Ub);
 

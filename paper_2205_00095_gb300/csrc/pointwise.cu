@@ -84,6 +84,19 @@ __global__ void __launch_bounds__(256) con2prim_vjp_kernel(Params p, long long n
   }
 }
 
+// The library's reciprocal and square root next to CUDA's, for the diagnostic entry point.
+__global__ void __launch_bounds__(256) math_check_kernel(long long n, const double* __restrict__ x,
+                                                         double* __restrict__ out) {
+  for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < n;
+       k += (long long)gridDim.x * blockDim.x) {
+    const double v = x[k];
+    out[k] = recip_nr(v);
+    out[n + k] = 1.0 / v;
+    out[2 * n + k] = sqrt_rs(v);
+    out[3 * n + k] = sqrt(v);
+  }
+}
+
 static unsigned grid_for(long long n) {
   long long b = (n + 255) / 256;
   const long long cap = 152LL * 16;  // enough resident blocks to fill the GPU
@@ -99,6 +112,12 @@ cudaError_t launch_prim2cons(const Params& p, cudaStream_t s, long long n, const
 cudaError_t launch_con2prim(const Params& p, cudaStream_t s, long long n, const double* U,
                             double* W, int* iters) {
   con2prim_kernel<<<grid_for(n), 256, 0, s>>>(p, n, U, W, iters);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_math_check(cudaStream_t s, long long n, const double* x, double* out) {
+  if (n == 0) return cudaSuccess;
+  math_check_kernel<<<grid_for(n), 256, 0, s>>>(n, x, out);
   return cudaGetLastError();
 }
 

@@ -7,55 +7,16 @@
 // by the coefficient matrix (B, 8 x 8 with zero padding).  Each operand x is split as
 // x = hi + lo with hi, lo TF32 and the product formed as hi*hi + lo*hi + hi*lo in FP32.
 //
-// On this GPU FP64<->FP32 conversion instructions issue on the FP64 pipe at the DFMA rate, so
-// the splits and the conversions of FP32 results back to FP64 are done with integer
-// operations on the bit patterns (FP32-normal range; smaller magnitudes flush to zero, larger
-// saturate to infinity).
+// The splits and the conversions of FP32 results back to FP64 use the integer bit-pattern
+// conversions of bits.cuh.
 #pragma once
 
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "bits.cuh"
+
 namespace dgsrhd {
-
-// double -> float by truncating the mantissa, via bit operations only
-__device__ __forceinline__ float f64_to_f32_bits(double x) {
-  const int hw = __double2hiint(x);
-  const unsigned lw = (unsigned)__double2loint(x);
-  const unsigned sign = (unsigned)hw & 0x80000000u;
-  const int e = (hw >> 20) & 0x7ff;
-  const unsigned mant = (((unsigned)hw & 0xfffffu) << 3) | (lw >> 29);
-  const int ef = e - 896;  // rebias 1023 -> 127
-  unsigned bits;
-  if (ef <= 0)
-    bits = sign;  // zero, subnormal or below the FP32-normal range
-  else if (ef >= 255)
-    bits = sign | 0x7f800000u | (e == 0x7ff && ((hw & 0xfffff) | lw) ? 0x400000u : 0u);
-  else
-    bits = sign | ((unsigned)ef << 23) | mant;
-  return __uint_as_float(bits);
-}
-
-// float -> double (exact for FP32-normal values), via bit operations only
-__device__ __forceinline__ double f32_to_f64_bits(float f) {
-  const unsigned b = __float_as_uint(f);
-  const unsigned sign = b & 0x80000000u;
-  const unsigned ef = (b >> 23) & 0xffu;
-  const unsigned mf = b & 0x7fffffu;
-  int hw;
-  unsigned lw;
-  if (ef == 0) {
-    hw = (int)sign;
-    lw = 0u;
-  } else if (ef == 255) {
-    hw = (int)(sign | 0x7ff00000u | (mf >> 3));
-    lw = mf << 29;
-  } else {
-    hw = (int)(sign | ((ef + 896u) << 20) | (mf >> 3));
-    lw = mf << 29;
-  }
-  return __hiloint2double(hw, (int)lw);
-}
 
 // TF32 split of a float: hi keeps the top 10 explicit mantissa bits, lo = x - hi (exact in
 // FP32), rounded to TF32 by the tensor core's truncation of its low 13 bits.

@@ -398,3 +398,36 @@ def test_con2prim_zero_and_tiny_momentum(lib, eos, c2p):
         assert np.allclose(Wg[1:4], Wo[1:4], rtol=0, atol=1e-6)
     else:
         assert np.allclose(Wg, Wo, rtol=1e-12, atol=1e-20)
+
+
+# ---------------------------------------------------------------------------------------
+# the library's FP64 reciprocal (Newton-Raphson from an FP32 seed) and x rsqrt(x) square root
+# against CUDA's division and sqrt
+# ---------------------------------------------------------------------------------------
+def test_reciprocal_and_sqrt_primitives_against_cuda(lib):
+    from paper_2205_00095_gb300 import _lib
+    rng = np.random.default_rng(12)
+    mags = np.ldexp(1.0 + rng.random(200000), rng.integers(-120, 121, size=200000))
+    edge = np.array([1.0, 2.0, 0.5, np.nextafter(2.0, 0), np.ldexp(1.0, -100), np.ldexp(1.0, 100),
+                     np.ldexp(1.5, -101), np.ldexp(1.5, 101), 5e-324, 2.2e-308, 1.7e308])
+    x = np.concatenate([mags, -mags[:1000], edge, -edge, [0.0, -0.0, np.inf, -np.inf, np.nan]])
+    xd = to_dev(x)
+    out = torch.empty(4 * x.size, dtype=torch.float64, device="cuda")
+    assert lib.dgsrhd_math_check(xd.data_ptr(), x.size, out.data_ptr(), None) == 0
+    torch.cuda.synchronize()
+    o = out.cpu().numpy().reshape(4, x.size)
+
+    def ulps(a, b):
+        ia, ib = a.view(np.int64), b.view(np.int64)
+        return np.abs(ia - ib)
+
+    fin = np.isfinite(o[1]) & (o[1] != 0.0)
+    assert ulps(o[0][fin], o[1][fin]).max() <= 1
+    assert np.array_equal(np.isnan(o[0]), np.isnan(o[1]))
+    assert np.array_equal(o[0][~fin & ~np.isnan(o[1])], o[1][~fin & ~np.isnan(o[1])])
+    pos = (x > 0) & np.isfinite(x)
+    assert ulps(o[2][pos], o[3][pos]).max() <= 2
+    assert np.all(np.isnan(o[2][x < 0])) and np.all(o[2][x == 0] == 0.0)
+    assert np.isnan(o[2][np.isnan(x)]).all()
+    assert lib.dgsrhd_math_check(None, 1, out.data_ptr(), None) == _lib.DGSRHD_EINVAL
+    assert lib.dgsrhd_math_check(xd.data_ptr(), -1, out.data_ptr(), None) == _lib.DGSRHD_EINVAL
