@@ -236,6 +236,16 @@ int32_t dgsrhd_kernel_times(dgsrhd_ctx* ctx, double* ms, int64_t* counts, int32_
 int32_t dgsrhd_rhs_noalloc(const dgsrhd_config* cfg, void* stream, const double* U, double* R,
                            dgsrhd_stats* stats_out);
 
+/* Spatial mean of a squared velocity component, <v_a^2> = (1/|Omega|) int v_a^2 dV, the
+ * diagnostic of the Kelvin-Helmholtz study (Sec. 4.4, the mean of v_y^2 whose growth rate the
+ * paper fits), by the nodal quadrature of the basis with con2prim at every node.
+ * U: DEVICE state [5][E][Nn]; axis: 0, 1 or 2 (v_x, v_y, v_z); out: HOST double.
+ * Synchronises the context's stream (the per-block partial sums are added on the host in a
+ * fixed order, so the result is reproducible).  Uses the context's R scratch buffer: do not
+ * overlap with another call on the same context.  DGSRHD_EINVAL for null pointers or a bad
+ * axis, DGSRHD_ECUDA on a CUDA error; a state con2prim cannot invert gives NaN. */
+int32_t dgsrhd_mean_square_velocity(dgsrhd_ctx* ctx, const double* U, int32_t axis, double* out);
+
 /* Diagnostic (no paper counterpart): the library's FP64 reciprocal and square root primitives
  * next to CUDA's own, for checking the former against the latter.
  * x:   DEVICE, n doubles.  out: DEVICE, 4 n doubles, written as four blocks of n:

@@ -141,6 +141,8 @@ def _load():
             lib.or_enthalpy.restype = d
             lib.or_cs2.argtypes = [cfg, d, d]
             lib.or_cs2.restype = d
+            lib.or_mean_square_velocity.argtypes = [cfg, dp, ctypes.c_int]
+            lib.or_mean_square_velocity.restype = d
             _lib = lib
     return _lib
 
@@ -243,6 +245,12 @@ def step(spec: dict, U: np.ndarray, dt: float, nsteps: int = 1):
 
 def cfl_dt(spec: dict, cfl: float) -> float:
     return float(_load().or_cfl_dt(ctypes.byref(make_config(spec)), float(cfl)))
+
+
+def mean_square_velocity(spec: dict, U: np.ndarray, axis: int = 1) -> float:
+    """<v_axis^2> = (1/|Omega|) int v_axis^2 dV by the nodal quadrature (Sec. 4.4)."""
+    U = _f64(U)
+    return float(_load().or_mean_square_velocity(ctypes.byref(make_config(spec)), _ptr(U), int(axis)))
 
 
 def wavespeeds(spec: dict, Wv, d: int):

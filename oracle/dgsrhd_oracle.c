@@ -957,5 +957,37 @@ int or_phys_flux(const or_config *c, const double *Wv, int d, double *F) {
   return 0;
 }
 
+/* ------------------------------------------------------------------------ */
+/* Diagnostic of the Kelvin-Helmholtz study (Sec. 4.4): the spatial mean of  */
+/* the squared velocity component `axis`, <v_a^2> = (1/|Omega|) int v_a^2 dV, */
+/* by the nodal quadrature of the basis: sum over elements and nodes of      */
+/* (prod_d dx_d / 2) w_node v_a^2 with v from con2prim at the node.          */
+/* ------------------------------------------------------------------------ */
+double or_mean_square_velocity(const or_config *c, const double *U, int axis) {
+  mesh m;
+  if (mesh_init(c, &m) || axis < 0 || axis > 2) return NAN;
+  const int64_t n = m.E * m.Nn;
+  double *W = (double *)malloc(sizeof(double) * 5 * (size_t)n);
+  int32_t *it = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
+  if (!W || !it) { free(W); free(it); return NAN; }
+  or_stats st;
+  memset(&st, 0, sizeof st);
+  or_con2prim(c, n, U, W, it, &st);
+  double jac = 1.0, vol = 1.0;
+  for (int d = 0; d < m.dim; ++d) {
+    jac *= 0.5 * m.dx[d];
+    vol *= c->hi[d] - c->lo[d];
+  }
+  double sum = 0.0;
+  for (int64_t e = 0; e < m.E; ++e)
+    for (int i = 0; i < m.Nn; ++i) {
+      const double v = W[(int64_t)(1 + axis) * n + e * m.Nn + i];
+      sum += jac * node_weight(&m, i) * v * v;
+    }
+  free(W);
+  free(it);
+  return sum / vol;
+}
+
 double or_enthalpy(const or_config *c, double rho, double P) { return eos_enthalpy(c, rho, P); }
 double or_cs2(const or_config *c, double rho, double P) { return eos_cs2(c, rho, P); }

@@ -100,6 +100,7 @@ def load() -> ctypes.CDLL:
         "dgsrhd_stage_vjp": (i32, [vp, vp, vp, vp, vp, vp, vp, i32, d]),
         "dgsrhd_con2prim_vjp": (i32, [vp, vp, vp, vp]),
         "dgsrhd_math_check": (i32, [vp, i64, vp, vp]),
+        "dgsrhd_mean_square_velocity": (i32, [vp, vp, i32, P(d)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -118,7 +119,7 @@ def exported_symbols():
         "dgsrhd_enforce_vjp", "dgsrhd_cfl_dt", "dgsrhd_get_stats", "dgsrhd_kernel_launches",
         "dgsrhd_set_profiling", "dgsrhd_kernel_times", "dgsrhd_status_string",
         "dgsrhd_rhs_noalloc", "dgsrhd_step_stage", "dgsrhd_stage_save_size", "dgsrhd_stage_vjp",
-        "dgsrhd_con2prim_vjp", "dgsrhd_math_check",
+        "dgsrhd_con2prim_vjp", "dgsrhd_math_check", "dgsrhd_mean_square_velocity",
     ]
 
 

@@ -5,6 +5,7 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <algorithm>
 #include <new>
 #include <vector>
 
@@ -744,6 +745,30 @@ int32_t dgsrhd_con2prim_vjp(dgsrhd_ctx* c, const double* U, const double* W_bar,
   });
   if (e == cudaSuccess) c->launches += 1;
   return cuda_status(e);
+}
+
+int32_t dgsrhd_mean_square_velocity(dgsrhd_ctx* c, const double* U, int32_t axis, double* out) {
+  if (!c || !U || !out || axis < 0 || axis > 2) return DGSRHD_EINVAL;
+  const long long n = c->E * c->Nn;
+  const int blocks = (int)std::min<long long>(1024, (n + 255) / 256);
+  cudaError_t e = timed_launch(c, DGSRHD_KERNEL_POINTWISE, [&]() {
+    return dgsrhd::launch_velocity_square(c->p, c->stream, n, (int)c->Nn, U, axis, c->Rv, blocks);
+  });
+  if (e != cudaSuccess) return DGSRHD_ECUDA;
+  c->launches += 1;
+  std::vector<double> part((size_t)blocks);
+  e = cudaMemcpyAsync(part.data(), c->Rv, sizeof(double) * blocks, cudaMemcpyDeviceToHost,
+                      c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return DGSRHD_ECUDA;
+  double sum = 0.0, jac = 1.0, vol = 1.0;
+  for (int b = 0; b < blocks; ++b) sum += part[(size_t)b];
+  for (int d = 0; d < c->dim; ++d) {
+    jac *= 0.5 * c->dx[d];
+    vol *= c->cfg.hi[d] - c->cfg.lo[d];
+  }
+  *out = sum * jac / vol;
+  return DGSRHD_OK;
 }
 
 int32_t dgsrhd_math_check(const double* x, int64_t n, double* out, void* stream) {

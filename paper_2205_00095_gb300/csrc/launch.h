@@ -49,6 +49,8 @@ cudaError_t launch_prim2cons(const Params& p, cudaStream_t s, long long n, const
                              double* U);
 cudaError_t launch_con2prim(const Params& p, cudaStream_t s, long long n, const double* U,
                             double* W, int* iters);
+cudaError_t launch_velocity_square(const Params& p, cudaStream_t s, long long n, int Nn,
+                                   const double* U, int axis, double* partial, int blocks);
 cudaError_t launch_math_check(cudaStream_t s, long long n, const double* x, double* out);
 cudaError_t launch_con2prim_vjp(const Params& p, cudaStream_t s, long long n, const double* U,
                                 const double* Wb, double* Ub);

@@ -84,6 +84,40 @@ __global__ void __launch_bounds__(256) con2prim_vjp_kernel(Params p, long long n
   }
 }
 
+// Partial sums of the quadrature of v_axis^2 (the Kelvin-Helmholtz diagnostic of Sec. 4.4):
+// con2prim at every node, weight prod_d w[node index along d]; one partial per block (fixed
+// assignment of nodes to threads and fixed reduction tree, so the sums are reproducible).
+__global__ void __launch_bounds__(256) velocity_square_kernel(Params p, long long n, int Nn,
+                                                              const double* __restrict__ U,
+                                                              int axis,
+                                                              double* __restrict__ partial) {
+  __shared__ double sh[256];
+  double acc = 0.0;
+  for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < n;
+       k += (long long)gridDim.x * blockDim.x) {
+    double u[5];
+#pragma unroll
+    for (int v = 0; v < 5; ++v) u[v] = U[v * n + k];
+    Prim w;
+    int it;
+    con2prim(p, u, w, it);
+    int node = (int)(k % Nn);
+    double wq = 1.0;
+    for (int d = 0; d < p.dim; ++d) {
+      wq *= p.w[node % p.N];
+      node /= p.N;
+    }
+    acc = fma(wq * w.v[axis], w.v[axis], acc);
+  }
+  sh[threadIdx.x] = acc;
+  __syncthreads();
+  for (int h = 128; h > 0; h >>= 1) {
+    if ((int)threadIdx.x < h) sh[threadIdx.x] += sh[threadIdx.x + h];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) partial[blockIdx.x] = sh[0];
+}
+
 // The library's reciprocal and square root next to CUDA's, for the diagnostic entry point.
 __global__ void __launch_bounds__(256) math_check_kernel(long long n, const double* __restrict__ x,
                                                          double* __restrict__ out) {
@@ -112,6 +146,12 @@ cudaError_t launch_prim2cons(const Params& p, cudaStream_t s, long long n, const
 cudaError_t launch_con2prim(const Params& p, cudaStream_t s, long long n, const double* U,
                             double* W, int* iters) {
   con2prim_kernel<<<grid_for(n), 256, 0, s>>>(p, n, U, W, iters);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_velocity_square(const Params& p, cudaStream_t s, long long n, int Nn,
+                                   const double* U, int axis, double* partial, int blocks) {
+  velocity_square_kernel<<<blocks, 256, 0, s>>>(p, n, Nn, U, axis, partial);
   return cudaGetLastError();
 }
 

@@ -168,6 +168,14 @@ class Solver:
             _dev_ptr(Ub, "U_bar", self.shape)))
         return Ub
 
+    def mean_square_velocity(self, U: torch.Tensor, axis: int = 1) -> float:
+        """<v_axis^2> = (1/|Omega|) int v_axis^2 dV (the Kelvin-Helmholtz diagnostic of Sec. 4.4),
+        evaluated by the library; synchronises the solver's stream."""
+        out = ctypes.c_double()
+        check("dgsrhd_mean_square_velocity", self.lib.dgsrhd_mean_square_velocity(
+            self.ctx, _dev_ptr(U, "U", self.shape), int(axis), ctypes.byref(out)))
+        return out.value
+
     def cfl_dt(self, cfl: float | None = None) -> float:
         dt = ctypes.c_double()
         check("dgsrhd_cfl_dt", self.lib.dgsrhd_cfl_dt(self.ctx, float(cfl or self.spec.get("cfl", 0.2)),

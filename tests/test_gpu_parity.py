@@ -189,6 +189,8 @@ def test_enforce(lib, dim, degree, n):
     (lambda c2p: wl.kh2d(nx=12, ny=24, degree=3, c2p=c2p), "iterative"),
     (lambda c2p: wl.kh2d(nx=12, ny=24, degree=3, c2p=c2p), "analytic"),
     (lambda c2p: wl.smooth_random(3, [5, 6, 4], 2, eos="tm", flux="hll", c2p=c2p, seed=8), "iterative"),
+    (lambda c2p: wl.kh_single(nx=12, ny=24, degree=1, c2p=c2p), "iterative"),
+    (lambda c2p: wl.kh_single(nx=10, ny=20, degree=2, c2p=c2p), "iterative"),
 ])
 def test_step_one_and_hundred(lib, spec_fn, c2p):
     spec = spec_fn(c2p)

@@ -90,3 +90,26 @@ def test_split_matches_fp64_at_benchmark_size(gpu_lib):
     st.synchronize()
     err = float((U - V).abs().sum() / U.abs().sum())
     assert err < 1e-6, err
+
+
+def test_split_error_against_the_exact_wave_equals_fp64(gpu_lib):
+    """Advected wave 64^2, p = 3, 100 SSPRK3 steps: the relative L1 errors of the FP64 and the
+    split-precision states against the exact translated wave agree to 1e-6."""
+    from paper_2205_00095_gb300 import Solver
+    spec = wl.advected_wave(n=64, degree=3, c2p="analytic")
+    st = torch.cuda.Stream()
+    a = Solver(spec, stream=st)
+    b = Solver(dict(spec, precision="split"), stream=st)
+    U = gpu_state(a, spec)
+    V = U.clone()
+    dt = a.cfl_dt(0.2)
+    a.step(U, dt, 100)
+    b.step(V, dt, 100)
+    with torch.cuda.stream(st):
+        Ue = a.initial_state(wl.advected_wave_ic(spec, a.node_coords_device(), 100 * dt))
+    st.synchronize()
+    nrm = float(Ue.abs().sum())
+    e64 = float((U - Ue).abs().sum()) / nrm
+    esp = float((V - Ue).abs().sum()) / nrm
+    assert e64 < 1e-6  # the wave is resolved
+    assert abs(esp - e64) <= 1e-6, (esp, e64)

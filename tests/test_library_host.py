@@ -4,6 +4,7 @@ import ctypes
 import os
 import re
 
+import numpy as np
 import pytest
 
 from paper_2205_00095_gb300 import _lib, build
@@ -68,3 +69,11 @@ def test_null_arguments_rejected(lib):
     assert lib.dgsrhd_rhs(None, None, None) == _lib.DGSRHD_EINVAL
     assert lib.dgsrhd_step(None, None, 0.1, 1) == _lib.DGSRHD_EINVAL
     lib.dgsrhd_destroy(None)
+
+
+def test_fit_growth_recovers_a_known_rate():
+    """Host-side fit: exp(0.7 + 2.5 t) sampled on [0, 4] gives rate 2.5, intercept 0.7."""
+    from paper_2205_00095_gb300 import kh_growth
+    t = np.linspace(0.0, 4.0, 81)
+    r, a, r2 = kh_growth.fit_growth(t, np.exp(0.7 + 2.5 * t))
+    assert abs(r - 2.5) < 1e-12 and abs(a - 0.7) < 1e-12 and r2 > 1.0 - 1e-12

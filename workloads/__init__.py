@@ -19,6 +19,8 @@ The workloads follow the problems of the paper:
   kh2d            -- 2D relativistic Kelvin-Helmholtz, double shear layer (Sec. 4.4 set-up
                      recast as periodic with two layers), Taub-Matthews EOS
   kh3d            -- 3D high-Lorentz-factor Kelvin-Helmholtz, Taub-Matthews EOS
+  kh_single       -- the paper's own Kelvin-Helmholtz set-up (Sec. 4.4): one shear layer,
+                     ideal EOS, outflow in y
   e2_grid         -- the 25 x 25 (gamma, P) grid of the con2prim accuracy study (Sec. 3.3)
 """
 from __future__ import annotations
@@ -59,6 +61,19 @@ def kh2d(nx: int = 256, ny: int = 512, degree: int = 3, flux: str = "hll",
     return dict(name="kh_2d", dim=2, degree=degree, n_elem=[nx, ny], lo=[-0.5, -1.0],
                 hi=[0.5, 1.0], eos="tm", gamma_ad=4.0 / 3.0, c2p=c2p, flux=flux, rk_stages=3,
                 bc=[("periodic", "periodic")] * 2, enforce=True, cfl=0.2, amplitude=0.01)
+
+
+def kh_single(nx: int = 256, ny: int = 512, degree: int = 1, flux: str = "hll",
+              c2p: str = "iterative") -> dict:
+    """The paper's Kelvin-Helmholtz set-up (Sec. 4.4): [-0.5,0.5] x [-1,1], one shear layer at
+    y = 0 of thickness a = 0.01 with shear velocity 0.25 (c = 1), rho0 = 1, P0 = 1, ideal EOS
+    Gamma = 4/3 with the iterative con2prim, perturbation amplitude A = 0.05 at k = 2 pi;
+    periodic in x, outflow in y; SSP-RK with p + 1 stages (at most 3)."""
+    return dict(name="kh_single", dim=2, degree=degree, n_elem=[nx, ny], lo=[-0.5, -1.0],
+                hi=[0.5, 1.0], eos="ideal", gamma_ad=4.0 / 3.0, c2p=c2p, flux=flux,
+                rk_stages=min(degree + 1, 3),
+                bc=[("periodic", "periodic"), ("outflow", "outflow")], enforce=True, cfl=0.2,
+                shear=0.25, amplitude=0.05, layer=0.01, sigma=0.1)
 
 
 def kh3d(n: int = 128, degree: int = 3, flux: str = "hll", c2p: str = "default") -> dict:
@@ -113,6 +128,15 @@ def advected_wave_ic(spec: dict, X, t: float = 0.0):
 def _double_layer(xp, y, a=0.01):
     """+1 inside 0 < y < 1, -1 inside -1 < y < 0 (period 2), tanh layers of width a."""
     return xp.tanh(y / a) - xp.tanh((y - 1.0) / a) - xp.tanh((y + 1.0) / a)
+
+
+def kh_single_ic(spec: dict, X):
+    """v_x = v0 tanh(y / a), v_y = A sin(2 pi x) exp(-y^2 / sigma^2), rho = 1, P = 1."""
+    xp = _xp(X)
+    x, y = X[0], X[1]
+    vx = spec["shear"] * xp.tanh(y / spec["layer"])
+    vy = spec["amplitude"] * xp.sin(2.0 * np.pi * x) * xp.exp(-(y * y) / spec["sigma"] ** 2)
+    return xp.stack([_const(x, 1.0), vx, vy, _const(x, 0.0), _const(x, 1.0)])
 
 
 def kh2d_ic(spec: dict, X, amplitude: float | None = None):
@@ -192,6 +216,8 @@ def initial_primitive(spec: dict, X):
         return kh2d_ic(spec, X)
     if name == "kh_3d":
         return kh3d_ic(spec, X)
+    if name == "kh_single":
+        return kh_single_ic(spec, X)
     if name == "smooth_random":
         return smooth_random_ic(spec, X)
     raise KeyError(name)
