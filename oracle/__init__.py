@@ -74,8 +74,8 @@ class Stats(ctypes.Structure):
 
 _EOS = {"ideal": 0, "tm": 1, "taub_matthews": 1}
 _C2P = {"analytic": 0, "iterative": 1, "default": 2}
-_FLUX = {"llf": 0, "hll": 1}
-_BC = {"periodic": 0, "dirichlet": 1, "outflow": 2}
+_FLUX = {"llf": 0, "hll": 1, "hllc": 2}
+_BC = {"periodic": 0, "dirichlet": 1, "outflow": 2, "reflect": 3}
 
 
 def _enum(table, v):

@@ -38,9 +38,9 @@ typedef struct {
   double gamma_ad;        /* Gamma of the ideal EOS */
   int32_t c2p;            /* 0 analytic, 1 iterative, 2 default (ideal->analytic, TM->iterative) */
   int32_t c2p_max_iter;   /* <=0 : default (30 Newton, 100 Brent) */
-  int32_t flux;           /* 0 LLF, 1 HLL */
+  int32_t flux;           /* 0 LLF, 1 HLL, 2 HLLC */
   int32_t rk_stages;      /* 1, 2, 3 */
-  int32_t bc[3][2];       /* 0 periodic, 1 Dirichlet, 2 outflow */
+  int32_t bc[3][2];       /* 0 periodic, 1 Dirichlet, 2 outflow, 3 reflecting wall */
   double bc_state[3][2][5]; /* Dirichlet primitive (rho, vx, vy, vz, P) */
   int32_t enforce;        /* physicality operator after every stage */
 } or_config;
@@ -259,6 +259,11 @@ static double c2p_ideal_iterative_w(double G, double xi, double eta, int max_ite
   if (w > 1.0 - 1e-15) w = 1.0 - 1e-15;
   double c4 = (al - 1.0) * xi, c3 = -2.0 * (al * eta + 1.0), c2 = 2.0 * (al + 1.0) * xi,
          c1 = -2.0 * (al * eta - 1.0), c0 = (al - 1.0) * xi;
+  /* Stop at |dw| <= 1e-14 w, or once the residual before the step is at the rounding level of
+   * evaluating the quartic on (0, 1), |P(w)| <= 8 eps sum |c_k|: for xi ~ 1e3 that level keeps
+   * the step near 1e-14 w and the first test alone would never end (reading R10). */
+  const double pres = 8.0 * 2.220446049250313e-16 *
+                      (fabs(c4) + fabs(c3) + fabs(c2) + fabs(c1) + fabs(c0));
   *conv = 0;
   for (int it = 1; it <= max_iter; ++it) {
     double P = (((c4 * w + c3) * w + c2) * w + c1) * w + c0;
@@ -266,7 +271,7 @@ static double c2p_ideal_iterative_w(double G, double xi, double eta, int max_ite
     double dw = P / dP;
     w -= dw;
     *iters = it;
-    if (fabs(dw) <= 1e-14 * w) { *conv = 1; break; }
+    if (fabs(dw) <= 1e-14 * w || fabs(P) <= pres) { *conv = 1; break; }
   }
   return w;
 }
@@ -487,6 +492,54 @@ static void wavespeeds(const or_config *c, const double W[5], double gam, int d,
   *lp = (vd + r) / (1.0 + sig);
 }
 
+/* HLLC flux (the paper names the solver but prints no formula; this is the relativistic HLLC
+ * construction of the literature it cites, restated in the variables (D, S, tau)).  With the
+ * outer wavespeeds lamL < 0 < lamR, the HLL averages
+ *   U_hll = (lamR U_R - lamL U_L - F_R + F_L) / (lamR - lamL),
+ *   F_hll = (lamR F_L - lamL F_R + lamR lamL (U_R - U_L)) / (lamR - lamL)
+ * give, with E = tau + D, its flux F_E = F_tau + F_D (= S_d) and m = S_d, the contact speed as
+ * the root of F_E,hll x^2 - (E_hll + F_m,hll) x + m_hll = 0 that equals v_d for two equal
+ * states, written without cancellation as x = 2 m / (b + sqrt(b^2 - 4 F_E m)), b = E + F_m;
+ * the contact pressure p* = F_m,hll - x F_E,hll.  On the side K the contact faces (left when
+ * x >= 0) the star state is
+ *   D* = D (lam - v) / (lam - x),
+ *   S*_d = (S_d (lam - v) + p* - p) / (lam - x),   S*_t = S_t (lam - v) / (lam - x),
+ *   tau* = (tau (lam - v) + p* x - p v) / (lam - x)   (E* - D*, no cancellation),
+ * with v = v_d, p the pressure and lam the outer speed of K, and F* = F_K + lam (U*_K - U_K).
+ * lamL >= 0 gives F_L and lamR <= 0 gives F_R. */
+static void hllc_flux(const double UL[5], const double UR[5], const double FL[5],
+                      const double FR[5], const double WL[5], const double WR[5], double lamL,
+                      double lamR, int d, double Fs[5]) {
+  if (lamL >= 0.0) {
+    for (int v = 0; v < 5; ++v) Fs[v] = FL[v];
+    return;
+  }
+  if (lamR <= 0.0) {
+    for (int v = 0; v < 5; ++v) Fs[v] = FR[v];
+    return;
+  }
+  double Uh[5], Fh[5];
+  for (int v = 0; v < 5; ++v) {
+    Uh[v] = (lamR * UR[v] - lamL * UL[v] - FR[v] + FL[v]) / (lamR - lamL);
+    Fh[v] = (lamR * FL[v] - lamL * FR[v] + lamR * lamL * (UR[v] - UL[v])) / (lamR - lamL);
+  }
+  const double Eh = Uh[4] + Uh[0], FEh = Fh[4] + Fh[0], mh = Uh[1 + d], Fmh = Fh[1 + d];
+  const double b = Eh + Fmh;
+  const double xs = 2.0 * mh / (b + sqrt(b * b - 4.0 * FEh * mh));
+  const double ps = Fmh - xs * FEh;
+  const int left = xs >= 0.0;
+  const double *U = left ? UL : UR, *F = left ? FL : FR, *W = left ? WL : WR;
+  const double lam = left ? lamL : lamR;
+  const double v = W[1 + d], p = W[4];
+  const double den = lam - xs;
+  double Us[5];
+  Us[0] = U[0] * (lam - v) / den;
+  for (int k = 0; k < 3; ++k)
+    Us[1 + k] = (k == d) ? (U[1 + d] * (lam - v) + ps - p) / den : U[1 + k] * (lam - v) / den;
+  Us[4] = (U[4] * (lam - v) + ps * xs - p * v) / den;
+  for (int k = 0; k < 5; ++k) Fs[k] = F[k] + lam * (Us[k] - U[k]);
+}
+
 /* Numerical flux between a left and right face state given as the
  * interpolated primitive (rho, u, P).
  * Reading (formulas not printed): HLL with S_L = min(lambda_L, 0),
@@ -515,6 +568,8 @@ static void numerical_flux(const or_config *c, const double WuL[5], const double
       for (int v = 0; v < 5; ++v)
         Fs[v] = (sR * FL[v] - sL * FR[v] + sL * sR * (UR[v] - UL[v])) / (sR - sL);
     }
+  } else if (c->flux == 2) {
+    hllc_flux(UL, UR, FL, FR, WL, WR, lamL, lamR, d, Fs);
   } else {
     double a = fmax(fabs(lamL), fabs(lamR));
     for (int v = 0; v < 5; ++v) Fs[v] = 0.5 * (FL[v] + FR[v]) - 0.5 * a * (UR[v] - UL[v]);
@@ -747,13 +802,17 @@ int or_rhs(const or_config *c, const double *U, double *R, or_stats *st) {
         double WL[5] = {0, 0, 0, 0, 0}, WR[5] = {0, 0, 0, 0, 0};
         if (eL >= 0) face_trace(&m, np.Wu, eL, d, 1, tan_ijk, WL, &guard);
         if (eR >= 0) face_trace(&m, np.Wu, eR, d, 0, tan_ijk, WR, &guard);
+        /* ghosts: Dirichlet = fixed outer state; outflow = the interior trace; reflecting wall =
+           the interior trace with its normal velocity reversed */
         if (eL < 0) {
           if (c->bc[d][0] == 1) dirichlet_ghost(c, d, 0, WL);
           else for (int v = 0; v < 5; ++v) WL[v] = WR[v];
+          if (c->bc[d][0] == 3) WL[1 + d] = -WL[1 + d];
         }
         if (eR < 0) {
           if (c->bc[d][1] == 1) dirichlet_ghost(c, d, 1, WR);
           else for (int v = 0; v < 5; ++v) WR[v] = WL[v];
+          if (c->bc[d][1] == 3) WR[1 + d] = -WR[1 + d];
         }
         double Fs[5];
         numerical_flux(c, WL, WR, d, Fs);

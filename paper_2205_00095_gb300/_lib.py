@@ -22,8 +22,8 @@ DGSRHD_EBADSTATE = 6
 
 EOS = {"ideal": 0, "tm": 1, "taub_matthews": 1}
 C2P = {"analytic": 0, "iterative": 1, "default": 2}
-FLUX = {"llf": 0, "hll": 1}
-BC = {"periodic": 0, "dirichlet": 1, "outflow": 2}
+FLUX = {"llf": 0, "hll": 1, "hllc": 2}
+BC = {"periodic": 0, "dirichlet": 1, "outflow": 2, "reflect": 3}
 PRECISION = {"fp64": 0, "split": 1}
 KERNEL_KINDS = ("volume", "face", "update", "enforce", "pointwise", "vjp")
 

@@ -227,7 +227,7 @@ bool valid_config(const dgsrhd_config* c) {
     if (c->n_elem[d] < 1) return false;
     if (!(c->hi[d] > c->lo[d])) return false;
     for (int s = 0; s < 2; ++s)
-      if (c->bc[d][s] < 0 || c->bc[d][s] > 2) return false;
+      if (c->bc[d][s] < 0 || c->bc[d][s] > DGSRHD_BC_REFLECT) return false;
     if ((c->bc[d][0] == DGSRHD_BC_PERIODIC) != (c->bc[d][1] == DGSRHD_BC_PERIODIC)) return false;
     for (int s = 0; s < 2; ++s)
       if (c->bc[d][s] == DGSRHD_BC_DIRICHLET) {
@@ -239,7 +239,8 @@ bool valid_config(const dgsrhd_config* c) {
   if (c->eos != DGSRHD_EOS_IDEAL && c->eos != DGSRHD_EOS_TAUB_MATTHEWS) return false;
   if (c->eos == DGSRHD_EOS_IDEAL && !(c->gamma_ad > 1.0)) return false;
   if (c->c2p < 0 || c->c2p > 2) return false;
-  if (c->flux != DGSRHD_FLUX_LLF && c->flux != DGSRHD_FLUX_HLL) return false;
+  if (c->flux != DGSRHD_FLUX_LLF && c->flux != DGSRHD_FLUX_HLL && c->flux != DGSRHD_FLUX_HLLC)
+    return false;
   if (c->rk_stages < 1 || c->rk_stages > 3) return false;
   if (c->precision != DGSRHD_PREC_FP64 && c->precision != DGSRHD_PREC_SPLIT) return false;
   return true;
@@ -615,6 +616,7 @@ Saved saved_sections(const dgsrhd_ctx* c, double* save) {
 int32_t rhs_vjp_core(dgsrhd_ctx* c, const double* U, const double* R_bar, double* U_bar,
                      const double* saved, double* Unb = nullptr, double* Ukb = nullptr,
                      double a_n = 0.0, double b_k = 0.0, double dt = 0.0) {
+  if (c->cfg.flux == DGSRHD_FLUX_HLLC) return DGSRHD_EINVAL;  // no reverse sweep of HLLC
   Saved sv = saved_sections(c, const_cast<double*>(saved));
   if (!saved) {
     StageArgs v{};

@@ -161,7 +161,11 @@ __device__ __forceinline__ double w_ideal_newton(double al, double xi, double et
     if (!(fabsf(dw) > 1e-6f * wf)) break;  // also leaves on NaN
   }
   double w = (wf > 0.0f && wf < 1.0f) ? f32_to_f64_bits(wf) : fmin(fmax(series, 1e-300), 1.0 - 1e-15);
-  // FP64 phase
+  // FP64 phase; besides |dw| <= 1e-14 w it stops once the residual before the step is at the
+  // rounding level of the quartic on (0, 1), |P(w)| <= 8 eps sum |c_k| (for xi ~ 1e3 that level
+  // keeps the step near 1e-14 w)
+  const double pres = 8.0 * 2.220446049250313e-16 *
+                      (fabs(c4) + fabs(c3) + fabs(c2) + fabs(c1) + fabs(c0));
   conv = false;
   while (it < max_iter) {
     const double Pw = fma(fma(fma(fma(c4, w, c3), w, c2), w, c1), w, c0);
@@ -169,7 +173,7 @@ __device__ __forceinline__ double w_ideal_newton(double al, double xi, double et
     const double dw = Pw * recip_nr(dP);
     w -= dw;
     ++it;
-    if (fabs(dw) <= 1e-14 * w) {
+    if (fabs(dw) <= 1e-14 * w || fabs(Pw) <= pres) {
       conv = true;
       break;
     }
@@ -598,6 +602,51 @@ __device__ __forceinline__ void face_tape(const FaceState& c, double r, double i
   t[18] = r, t[19] = lm, t[20] = lp;
 }
 
+// HLLC along axis D (the paper names the solver but prints no formula; this is the relativistic
+// HLLC construction of the literature it cites, in the variables (D, S, tau)).  With the outer
+// speeds lamL < 0 < lamR and the HLL averages U_hll = (lamR U_R - lamL U_L - F_R + F_L)/(lamR -
+// lamL), F_hll = (lamR F_L - lamL F_R + lamR lamL (U_R - U_L))/(lamR - lamL): with E = tau + D,
+// F_E = F_tau + F_D and m = S_D, the contact speed is the root of F_E x^2 - (E + F_m) x + m = 0
+// that equals v_D for equal states, x = 2m/(b + sqrt(b^2 - 4 F_E m)), b = E + F_m, and the
+// contact pressure p* = F_m - x F_E.  On the side K the contact faces (left when x >= 0), with
+// v = v_D, P and lam of that side: D* = D (lam - v)/(lam - x), S*_D = (S_D (lam - v) + p* - P)/
+// (lam - x), S*_t = S_t (lam - v)/(lam - x), tau* = (tau (lam - v) + p* x - P v)/(lam - x), and
+// F* = F_K + lam (U* - U_K).  lamL >= 0 gives F_L, lamR <= 0 gives F_R.
+template <int D>
+__device__ __forceinline__ void hllc_flux(const FaceState& L, const FaceState& R,
+                                          const double FL[5], const double FR[5], double lamL,
+                                          double lamR, double Fs[5]) {
+  if (lamL >= 0.0 || lamR <= 0.0) {
+    const bool useL = lamL >= 0.0;
+#pragma unroll
+    for (int v = 0; v < 5; ++v) Fs[v] = useL ? FL[v] : FR[v];
+    return;
+  }
+  const double idl = recip_nr(lamR - lamL), lrl = lamR * lamL;
+  auto Uh = [&](int v) { return (lamR * R.U[v] - lamL * L.U[v] - FR[v] + FL[v]) * idl; };
+  auto Fh = [&](int v) { return (lamR * FL[v] - lamL * FR[v] + lrl * (R.U[v] - L.U[v])) * idl; };
+  const double Eh = Uh(4) + Uh(0), FEh = Fh(4) + Fh(0), mh = Uh(1 + D), Fmh = Fh(1 + D);
+  const double b = Eh + Fmh;
+  const double xs = 2.0 * mh * recip_nr(b + sqrt(fma(b, b, -4.0 * FEh * mh)));
+  const double ps = fma(-xs, FEh, Fmh);
+  const bool left = xs >= 0.0;
+  const double lam = left ? lamL : lamR, v = left ? L.v[D] : R.v[D], P = left ? L.P : R.P;
+  const double lv = lam - v, di = recip_nr(lam - xs);
+  double UK[5], FK[5];
+#pragma unroll
+  for (int k = 0; k < 5; ++k) {
+    UK[k] = left ? L.U[k] : R.U[k];
+    FK[k] = left ? FL[k] : FR[k];
+  }
+  double Us[5];
+  Us[0] = UK[0] * lv * di;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) Us[1 + k] = (k == D) ? (UK[1 + D] * lv + ps - P) * di : UK[1 + k] * lv * di;
+  Us[4] = (UK[4] * lv + ps * xs - P * v) * di;
+#pragma unroll
+  for (int k = 0; k < 5; ++k) Fs[k] = fma(lam, Us[k] - UK[k], FK[k]);
+}
+
 // Numerical flux along axis D between face states given as (rho, u, P).  HLL: S_L =
 // min(lambda_L, 0), S_R = max(lambda_R, 0), (S_R F_L - S_L F_R + S_L S_R (U_R - U_L)) /
 // (S_R - S_L) (the average when both vanish); LLF: (F_L + F_R)/2 - a (U_R - U_L)/2 with
@@ -629,6 +678,8 @@ __device__ __forceinline__ void numerical_flux(const Params& p, const double WL[
 #pragma unroll
       for (int v = 0; v < 5; ++v) Fs[v] = (sR * FL[v] - sL * FR[v] + sL * sR * (R.U[v] - L.U[v])) * id;
     }
+  } else if (p.flux == 2) {
+    hllc_flux<D>(L, R, FL, FR, lamL, lamR, Fs);
   } else {
     const double a = fmax(fabs(lamL), fabs(lamR));
 #pragma unroll

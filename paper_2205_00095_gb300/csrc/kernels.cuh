@@ -258,13 +258,17 @@ __device__ __forceinline__ void face_point(const Params& p, const double* __rest
 #pragma unroll
     for (int v = 0; v < 5; ++v) WR[v] = trR[(v * p.E + eR) * Nt + t];
   }
+  // ghosts: Dirichlet = fixed outer state; outflow = the interior trace; reflecting wall =
+  // the interior trace with its normal velocity reversed
   if (eL < 0) {
 #pragma unroll
     for (int v = 0; v < 5; ++v) WL[v] = (p.bc[D][0] == 1) ? p.ghost[D][0][v] : WR[v];
+    if (p.bc[D][0] == 3) WL[1 + D] = -WL[1 + D];
   }
   if (eR < 0) {
 #pragma unroll
     for (int v = 0; v < 5; ++v) WR[v] = (p.bc[D][1] == 1) ? p.ghost[D][1][v] : WL[v];
+    if (p.bc[D][1] == 3) WR[1 + D] = -WR[1 + D];
   }
   double F[5], rec[2][kFaceTape];
   numerical_flux<D>(p, WL, WR, F, rec[0], rec[1]);

@@ -257,13 +257,17 @@ __device__ __forceinline__ void face_vjp_point(const Params& p, const double* __
 #pragma unroll
     for (int v = 0; v < 5; ++v) WR[v] = trR[(v * p.E + eR) * Nt + t];
   }
+  // ghosts: Dirichlet = fixed outer state; outflow = the interior trace; reflecting wall =
+  // the interior trace with its normal velocity reversed
   if (eL < 0) {
 #pragma unroll
     for (int v = 0; v < 5; ++v) WL[v] = (p.bc[D][0] == 1) ? p.ghost[D][0][v] : WR[v];
+    if (p.bc[D][0] == 3) WL[1 + D] = -WL[1 + D];
   }
   if (eR < 0) {
 #pragma unroll
     for (int v = 0; v < 5; ++v) WR[v] = (p.bc[D][1] == 1) ? p.ghost[D][1][v] : WL[v];
+    if (p.bc[D][1] == 3) WR[1 + D] = -WR[1 + D];
   }
   // transposed lift: R_left -= s l+ F*, R_right += s l- F*
   const double sc = p.inv_half_dx[D];
@@ -286,13 +290,18 @@ __device__ __forceinline__ void face_vjp_point(const Params& p, const double* __
   } else {
     numerical_flux_vjp<D>(p, WL, WR, nullptr, nullptr, 0, Fsb, WLb, WRb);
   }
-  // ghost states: Dirichlet ghosts are constant, outflow ghosts copy the interior trace
-  if (eL < 0 && p.bc[D][0] == 2)
+  // ghost states: Dirichlet ghosts are constant, outflow ghosts copy the interior trace,
+  // reflecting ghosts copy it with the normal velocity reversed
+  if (eL < 0 && p.bc[D][0] >= 2) {
+    if (p.bc[D][0] == 3) WLb[1 + D] = -WLb[1 + D];
 #pragma unroll
     for (int v = 0; v < 5; ++v) WRb[v] += WLb[v];
-  if (eR < 0 && p.bc[D][1] == 2)
+  }
+  if (eR < 0 && p.bc[D][1] >= 2) {
+    if (p.bc[D][1] == 3) WRb[1 + D] = -WRb[1 + D];
 #pragma unroll
     for (int v = 0; v < 5; ++v) WLb[v] += WRb[v];
+  }
   double* tbL = TrB + ((long long)D * 2 + 1) * side_stride;
   double* tbR = TrB + ((long long)D * 2 + 0) * side_stride;
   if (eL >= 0)

@@ -140,6 +140,13 @@ RHS_CASES = [
     (3, [5, 6, 7], 2, "tm", "llf", [("periodic", "periodic"), ("outflow", "outflow"), ("periodic", "periodic")]),
     (3, [6, 5, 7], 3, "tm", "hll", None),
     (3, [4, 3, 5], 4, "ideal", "llf", None),
+    # HLLC and reflecting walls
+    (1, [129], 2, "ideal", "hllc", [("reflect", "dirichlet")]),
+    (2, [17, 15], 1, "tm", "hllc", [("reflect", "reflect"), ("periodic", "periodic")]),
+    (2, [13, 11], 3, "ideal", "hllc", [("outflow", "reflect"), ("reflect", "outflow")]),
+    (2, [12, 10], 2, "ideal", "hll", [("reflect", "reflect"), ("reflect", "reflect")]),
+    (3, [5, 4, 6], 2, "ideal", "hllc", [("reflect", "reflect"), ("periodic", "periodic"),
+                                        ("outflow", "reflect")]),
 ]
 
 
@@ -191,6 +198,8 @@ def test_enforce(lib, dim, degree, n):
     (lambda c2p: wl.smooth_random(3, [5, 6, 4], 2, eos="tm", flux="hll", c2p=c2p, seed=8), "iterative"),
     (lambda c2p: wl.kh_single(nx=12, ny=24, degree=1, c2p=c2p), "iterative"),
     (lambda c2p: wl.kh_single(nx=10, ny=20, degree=2, c2p=c2p), "iterative"),
+    (lambda c2p: wl.riemann_1d(4, n=96, degree=1), "iterative"),
+    (lambda c2p: wl.riemann_1d(5, n=64, degree=0), "iterative"),
 ])
 def test_step_one_and_hundred(lib, spec_fn, c2p):
     spec = spec_fn(c2p)
@@ -433,3 +442,25 @@ def test_reciprocal_and_sqrt_primitives_against_cuda(lib):
     assert np.isnan(o[2][np.isnan(x)]).all()
     assert lib.dgsrhd_math_check(None, 1, out.data_ptr(), None) == _lib.DGSRHD_EINVAL
     assert lib.dgsrhd_math_check(xd.data_ptr(), -1, out.data_ptr(), None) == _lib.DGSRHD_EINVAL
+
+
+# ---------------------------------------------------------------------------------------
+# reflecting walls: no mass or energy crosses them (every flux)
+# ---------------------------------------------------------------------------------------
+@pytest.mark.parametrize("flux", ["llf", "hll", "hllc"])
+def test_reflecting_box_conserves_mass_and_energy(lib, flux):
+    spec = wl.smooth_random(2, [14, 11], 2, flux=flux, seed=6,
+                            bc=[("reflect", "reflect"), ("reflect", "reflect")])
+    s = solver(spec, stream=torch.cuda.Stream())
+    U = gpu_state(s, spec)
+    w1 = np.polynomial.legendre.leggauss(3)[1]
+    w = torch.from_numpy(np.multiply.outer(w1, w1).ravel()).cuda()
+    m0, e0 = float((U[0] * w).sum()), float((U[4] * w).sum())
+    S0 = U[1].clone()
+    s.step(U, s.cfl_dt(0.2), 50)
+    s.synchronize()
+    m1, e1 = float((U[0] * w).sum()), float((U[4] * w).sum())
+    assert abs(m1 - m0) <= 1e-12 * m0 and abs(e1 - e0) <= 1e-12 * e0
+    assert float((U[1] - S0).abs().max()) > 1e-3
+    status, _ = s.stats()
+    assert status == 0

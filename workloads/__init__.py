@@ -9,12 +9,13 @@ here.
 
 A problem description is a plain dict:
   dim, degree, n_elem, lo, hi, eos ('ideal' | 'tm'), gamma_ad,
-  c2p ('analytic' | 'iterative' | 'default'), c2p_max_iter, flux ('llf' | 'hll'),
-  rk_stages, bc [(lo, hi) per dim: 'periodic' | 'dirichlet' | 'outflow'],
+  c2p ('analytic' | 'iterative' | 'default'), c2p_max_iter, flux ('llf' | 'hll' | 'hllc'),
+  rk_stages, bc [(lo, hi) per dim: 'periodic' | 'dirichlet' | 'outflow' | 'reflect'],
   bc_state [[(rho, vx, vy, vz, P) low, high] per dim], enforce, cfl.
 
 The workloads follow the problems of the paper:
   blast_wave      -- 1D relativistic blast wave (Sec. 4.2, problem 1)
+  riemann_1d      -- 1D Riemann problems 2-5 of Sec. 4.2 (problem 5: a reflecting wall)
   advected_wave   -- 2D smooth density wave, periodic (smooth convergence case)
   kh2d            -- 2D relativistic Kelvin-Helmholtz, double shear layer (Sec. 4.4 set-up
                      recast as periodic with two layers), Taub-Matthews EOS
@@ -46,6 +47,34 @@ def blast_wave(n: int = 128, degree: int = 1, p_left: float = 13.33, p_right: fl
                 eos="ideal", gamma_ad=5.0 / 3.0, c2p="iterative", flux=flux, rk_stages=2,
                 bc=[("dirichlet", "dirichlet")], bc_state=[[left, right]], enforce=True,
                 cfl=0.2, t_final=0.4, left=left, right=right)
+
+
+# The paper's 1D Riemann problems 2-5 (Sec. 4.2): primitive (rho, vx, vy, vz, P) left and
+# right of x = 0.5, adiabatic index, final time, right-hand boundary.  Problem 5 is a uniform
+# flow into a reflecting wall at x = 1.  (Problem 1 is `blast_wave`.)
+RIEMANN_1D = {
+    2: dict(left=(1.0, 0.0, 0.0, 0.0, 1e3), right=(1.0, 0.0, 0.0, 0.0, 1e-2), gamma_ad=5.0 / 3.0,
+            t_final=0.4, right_bc="dirichlet"),
+    3: dict(left=(1.0, 0.0, 0.0, 0.0, 1e3), right=(1.0, 0.0, 0.99, 0.0, 1e-2), gamma_ad=5.0 / 3.0,
+            t_final=0.4, right_bc="dirichlet"),
+    4: dict(left=(1.0, 0.01, 0.0, 0.0, 1.0), right=(0.125, 0.01, 0.0, 0.0, 0.1), gamma_ad=4.0 / 3.0,
+            t_final=0.4, right_bc="dirichlet"),
+    5: dict(left=(1.0, 0.99999, 0.0, 0.0, 0.01), right=(1.0, 0.99999, 0.0, 0.0, 0.01),
+            gamma_ad=4.0 / 3.0, t_final=1.5, right_bc="reflect"),
+}
+
+
+def riemann_1d(problem: int, n: int = 128, degree: int = 1, flux: str = "hllc") -> dict:
+    """1D Riemann problem `problem` (2-5) of Sec. 4.2 on [0, 1]: ideal EOS with the iterative
+    con2prim, Dirichlet ends (problem 5: a reflecting wall at x = 1), SSP-RK with p + 1 stages
+    (at most 3), CFL 0.2."""
+    P = RIEMANN_1D[problem]
+    left, right = P["left"], P["right"]
+    return dict(name="riemann_1d", problem=problem, dim=1, degree=degree, n_elem=[n], lo=[0.0],
+                hi=[1.0], eos="ideal", gamma_ad=P["gamma_ad"], c2p="iterative", flux=flux,
+                rk_stages=min(degree + 1, 3), bc=[("dirichlet", P["right_bc"])],
+                bc_state=[[left, right]], enforce=True, cfl=0.2, t_final=P["t_final"],
+                left=left, right=right)
 
 
 def advected_wave(n: int = 512, degree: int = 3, flux: str = "llf", c2p: str = "default") -> dict:
@@ -208,7 +237,7 @@ def kh3d_ic(spec: dict, X):
 
 def initial_primitive(spec: dict, X):
     name = spec["name"]
-    if name == "blast_wave_1d":
+    if name in ("blast_wave_1d", "riemann_1d"):
         return blast_wave_ic(spec, X)
     if name == "advected_wave_2d":
         return advected_wave_ic(spec, X)
