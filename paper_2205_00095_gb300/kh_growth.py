@@ -78,7 +78,7 @@ def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--nx", type=int, default=256)
     ap.add_argument("--degree", type=int, default=1)
-    ap.add_argument("--flux", default="hll", choices=["hll", "llf"])
+    ap.add_argument("--flux", default="hll", choices=["hll", "hllc", "llf"])
     ap.add_argument("--t-end", type=float, default=3.0)
     args = ap.parse_args()
     from . import build

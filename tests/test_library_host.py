@@ -77,3 +77,11 @@ def test_fit_growth_recovers_a_known_rate():
     t = np.linspace(0.0, 4.0, 81)
     r, a, r2 = kh_growth.fit_growth(t, np.exp(0.7 + 2.5 * t))
     assert abs(r - 2.5) < 1e-12 and abs(a - 0.7) < 1e-12 and r2 > 1.0 - 1e-12
+
+
+def test_linear_wave_order_fit_recovers_a_known_order():
+    """L1(dx) = 3e-9 + 2 dx^3 sampled at four resolutions: the fitted p2 is 3."""
+    from paper_2205_00095_gb300 import linear_waves
+    dx = np.array([0.2, 0.1, 0.05, 0.025])
+    p2, slope = linear_waves.fit_order(dx, 3e-9 + 2.0 * dx ** 3)
+    assert abs(p2 - 3.0) < 1e-3 and slope > 2.8

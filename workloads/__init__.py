@@ -22,6 +22,7 @@ The workloads follow the problems of the paper:
   kh3d            -- 3D high-Lorentz-factor Kelvin-Helmholtz, Taub-Matthews EOS
   kh_single       -- the paper's own Kelvin-Helmholtz set-up (Sec. 4.4): one shear layer,
                      ideal EOS, outflow in y
+  linear_wave     -- linear waves of Sec. 4.1 in grid-aligned and oblique periodic boxes
   e2_grid         -- the 25 x 25 (gamma, P) grid of the con2prim accuracy study (Sec. 3.3)
 """
 from __future__ import annotations
@@ -105,6 +106,46 @@ def kh_single(nx: int = 256, ny: int = 512, degree: int = 1, flux: str = "hll",
                 shear=0.25, amplitude=0.05, layer=0.01, sigma=0.1)
 
 
+# Linear waves (Sec. 4.1): wave frames.  Table 1 of that section gives (N wavelengths, n-th
+# acceptable angle) per test type; tan(theta) = sqrt(N / (N - n) - 1).  The 3D rotation is
+# about a = (0, -1, 1)/sqrt(2); in 2D the wave vector is turned by theta within the x-y plane.
+LINEAR_WAVE_FRAMES = {
+    "1d": (1, 1, 0), "2d": (2, 1, 0), "2d_oblique": (2, 2, 1), "3d": (3, 1, 0), "3d_oblique": (3, 3, 2),
+}
+
+
+def _rotation(axis, theta):
+    a = np.asarray(axis, dtype=np.float64)
+    a = a / np.linalg.norm(a)
+    K = np.array([[0.0, -a[2], a[1]], [a[2], 0.0, -a[0]], [-a[1], a[0], 0.0]])
+    return math.cos(theta) * np.eye(3) + (1.0 - math.cos(theta)) * np.outer(a, a) + math.sin(theta) * K
+
+
+def linear_wave(frame: str, degree: int, n_base: int, refine: int, eigvec, eigval: float,
+                rho0: float = 1.0, P0: float = 1.0, gamma_ad: float = 5.0 / 3.0,
+                amplitude: float = 1e-6, t_final: float = 0.5, flux: str = "llf") -> dict:
+    """A linear wave of unit wavelength (Sec. 4.1) on a periodic box aligned with its wave frame
+    (`frame` in LINEAR_WAVE_FRAMES), base state (rho0, v = 0, P0), ideal EOS.  eigvec is the
+    right eigenvector (rho, v_par, v_perp1, v_perp2, P) in the wave frame and eigval its
+    eigenvalue (the caller computes both: they need the sound speed).  Elements per axis:
+    n_base 2^refine times the box length; SSP-RK with p + 1 stages (RK1, SSPRK2, SSPRK3)."""
+    dim, N, n = LINEAR_WAVE_FRAMES[frame]
+    theta = math.atan(math.sqrt(N / (N - n) - 1.0)) if n else 0.0
+    R = _rotation((0.0, -1.0, 1.0) if dim == 3 else (0.0, 0.0, 1.0), theta)
+    khat = R[:, 0]
+    # box: N khat per axis (N |khat_d| is a whole number of wave periods along axis d); one
+    # unit along the axes the wave does not vary on
+    L = [float(N * abs(khat[d])) if abs(khat[d]) > 1e-12 else 1.0 for d in range(dim)]
+    ne = [max(1, int(round(n_base * 2 ** refine * L[d]))) for d in range(dim)]
+    return dict(name="linear_wave", frame=frame, dim=dim, degree=degree, n_elem=ne,
+                lo=[0.0] * dim, hi=L, eos="ideal", gamma_ad=gamma_ad, c2p="iterative",
+                flux=flux, rk_stages=min(degree + 1, 3), bc=[("periodic", "periodic")] * dim,
+                enforce=True, cfl=0.2, t_final=t_final, rho0=rho0, P0=P0, amplitude=amplitude,
+                eigvec=tuple(float(v) for v in eigvec), eigval=float(eigval),
+                khat=tuple(float(v) for v in khat), e1=tuple(float(v) for v in R[:, 1]),
+                e2=tuple(float(v) for v in R[:, 2]))
+
+
 def kh3d(n: int = 128, degree: int = 3, flux: str = "hll", c2p: str = "default") -> dict:
     """3D high-Lorentz-factor Kelvin-Helmholtz on the periodic unit cube, Taub-Matthews EOS."""
     return dict(name="kh_3d", dim=3, degree=degree, n_elem=[n, n, n], lo=[0.0] * 3,
@@ -157,6 +198,22 @@ def advected_wave_ic(spec: dict, X, t: float = 0.0):
 def _double_layer(xp, y, a=0.01):
     """+1 inside 0 < y < 1, -1 inside -1 < y < 0 (period 2), tanh layers of width a."""
     return xp.tanh(y / a) - xp.tanh((y - 1.0) / a) - xp.tanh((y + 1.0) / a)
+
+
+def linear_wave_ic(spec: dict, X, t: float = 0.0):
+    """W = W0 + A r sin(2 pi (khat . x) - omega t), omega = 2 pi eigval, with the velocity
+    part of r turned from the wave frame: v = r_par khat + r_perp1 e1 + r_perp2 e2."""
+    xp = _xp(X)
+    dim = int(spec["dim"])
+    x = X[0]
+    phase = _const(x, 0.0)
+    for d in range(dim):
+        phase = phase + spec["khat"][d] * X[d]
+    s = xp.sin(2.0 * np.pi * (phase - spec["eigval"] * t))
+    A, r = spec["amplitude"], spec["eigvec"]
+    v = [A * (r[1] * spec["khat"][c] + r[2] * spec["e1"][c] + r[3] * spec["e2"][c]) * s
+         for c in range(3)]
+    return xp.stack([spec["rho0"] + A * r[0] * s, v[0], v[1], v[2], spec["P0"] + A * r[4] * s])
 
 
 def kh_single_ic(spec: dict, X):
@@ -247,6 +304,8 @@ def initial_primitive(spec: dict, X):
         return kh3d_ic(spec, X)
     if name == "kh_single":
         return kh_single_ic(spec, X)
+    if name == "linear_wave":
+        return linear_wave_ic(spec, X)
     if name == "smooth_random":
         return smooth_random_ic(spec, X)
     raise KeyError(name)
