@@ -207,6 +207,23 @@ def run_oracle(spec: dict, steps: int, warmup: int):
     return dof(spec) * steps * spec["rk_stages"] / t, t
 
 
+def reduce_max_over_ranks(x: float, world: int, device) -> float:
+    """The largest x over the ranks (the slowest replica's time); x itself on one rank."""
+    if world == 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(world: int, ndof: int, steps: int, stages: int, t_ms: float) -> float:
+    """Whole-job DOF-updates/s: every replica advances ndof nodes through steps x stages stage
+    updates; the job takes the slowest replica's t_ms."""
+    return world * ndof * steps * stages / (t_ms * 1e-3)
+
+
 def reference_arm(args, rank, world):
     if rank != 0:
         return
@@ -276,12 +293,8 @@ def ours(args, rank, world, local_rank):
     ktimes = s.kernel_times(reset=True)
     s.set_profiling(False)
     status, st = s.stats()
-    t_max = ms
-    if world > 1:
-        tt = torch.tensor([ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_max = float(tt.item())
-    value = world * ndof * args.steps * stages / (t_max * 1e-3)
+    t_max = reduce_max_over_ranks(ms, world, dev)
+    value = job_throughput(world, ndof, args.steps, stages, t_max)
 
     # end to end through the C ABI with a pinned host state: per step H2D, one step (graph), D2H
     e2e = None
@@ -296,10 +309,8 @@ def ours(args, rank, world, local_rank):
             s.step_host(Uh, dt, 1)
         barrier()
         e2e_s = time.perf_counter() - t0
-        e2e_t = torch.tensor([e2e_s], device=dev, dtype=torch.float64)
-        if world > 1:
-            dist.all_reduce(e2e_t, op=dist.ReduceOp.MAX)
-        e2e = {"value": world * ndof * args.steps * stages / float(e2e_t.item()), "unit": UNIT,
+        e2e_max = reduce_max_over_ranks(e2e_s, world, dev)
+        e2e = {"value": job_throughput(world, ndof, args.steps, stages, 1e3 * e2e_max), "unit": UNIT,
                "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes}
 
     # split-precision form on the same workload: tensor-core contractions, FP64 elsewhere
