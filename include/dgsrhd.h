@@ -66,13 +66,20 @@ extern "C" {
 #define DGSRHD_BC_REFLECT 3      /* reflecting wall: the interior trace with its normal velocity
                                     reversed */
 
+/* node family of the collocated nodal basis (the paper's node set is unnamed: Gauss-Legendre
+ * is the default; Gauss-Lobatto-Legendre puts nodes on the faces, so the face traces are nodal
+ * values that the physicality operator covers, at the price of an inexact (degree 2N - 3)
+ * collocated quadrature) */
+#define DGSRHD_NODES_GL 0
+#define DGSRHD_NODES_GLL 1
+
 /* arithmetic of the basis contractions */
 #define DGSRHD_PREC_FP64 0
 #define DGSRHD_PREC_SPLIT 1      /* split-precision tensor-core contractions, FP64 elsewhere */
 
 typedef struct dgsrhd_config {
   int32_t dim;                 /* 1, 2 or 3 */
-  int32_t degree;              /* p in 0..4; N = p + 1 Gauss-Legendre nodes per axis */
+  int32_t degree;              /* p in 0..4 (1..4 for Gauss-Lobatto); N = p + 1 nodes per axis */
   int64_t n_elem[3];           /* elements per axis (unused axes: 1) */
   double lo[3], hi[3];         /* domain box */
   int32_t eos;                 /* DGSRHD_EOS_* */
@@ -85,6 +92,7 @@ typedef struct dgsrhd_config {
   double bc_state[3][2][5];    /* Dirichlet primitive (rho, vx, vy, vz, P) per side */
   int32_t enforce;             /* 1: physicality operator after every RK stage */
   int32_t precision;           /* DGSRHD_PREC_* */
+  int32_t nodes;               /* DGSRHD_NODES_*: node family of the collocated basis */
 } dgsrhd_config;
 
 typedef struct dgsrhd_stats {

@@ -60,6 +60,7 @@ class Config(ctypes.Structure):
         ("bc", (ctypes.c_int32 * 2) * 3),
         ("bc_state", ((ctypes.c_double * 5) * 2) * 3),
         ("enforce", ctypes.c_int32),
+        ("nodes", ctypes.c_int32),
     ]
 
 
@@ -74,6 +75,7 @@ class Stats(ctypes.Structure):
 
 _EOS = {"ideal": 0, "tm": 1, "taub_matthews": 1}
 _C2P = {"analytic": 0, "iterative": 1, "default": 2}
+_NODES = {"gl": 0, "gll": 1}
 _FLUX = {"llf": 0, "hll": 1, "hllc": 2}
 _BC = {"periodic": 0, "dirichlet": 1, "outflow": 2, "reflect": 3}
 
@@ -111,6 +113,7 @@ def make_config(spec: dict) -> Config:
                 for v in range(5):
                     c.bc_state[d][s][v] = float(bcs[d][s][v])
     c.enforce = int(bool(spec.get("enforce", True)))
+    c.nodes = _enum(_NODES, spec.get("nodes", "gl"))
     return c
 
 
@@ -126,6 +129,7 @@ def _load():
             dp = P(d)
             lib.or_gauss_legendre.argtypes = [ctypes.c_int, dp, dp]
             lib.or_basis.argtypes = [ctypes.c_int, dp, dp, dp, dp, dp]
+            lib.or_basis_family.argtypes = [ctypes.c_int, ctypes.c_int, dp, dp, dp, dp, dp]
             lib.or_prim2cons.argtypes = [cfg, ctypes.c_int64, dp, dp]
             lib.or_con2prim.argtypes = [cfg, ctypes.c_int64, dp, dp, P(ctypes.c_int32), st]
             lib.or_rhs.argtypes = [cfg, dp, dp, st]
@@ -171,10 +175,12 @@ def gauss_legendre(N: int):
     return x, w
 
 
-def basis(N: int) -> dict:
+def basis(N: int, nodes: str = "gl") -> dict:
+    """Nodes, weights and the tables of the collocated scheme for N Gauss-Legendre ('gl') or
+    Gauss-Lobatto-Legendre ('gll', N >= 2) nodes."""
     x, w, em, ep = (np.zeros(N) for _ in range(4))
     Dhat = np.zeros(N * N)
-    if _load().or_basis(N, _ptr(x), _ptr(w), _ptr(Dhat), _ptr(em), _ptr(ep)):
+    if _load().or_basis_family(N, _NODES[nodes], _ptr(x), _ptr(w), _ptr(Dhat), _ptr(em), _ptr(ep)):
         raise ValueError("bad N")
     return {"x": x, "w": w, "Dhat": Dhat.reshape(N, N), "em": em, "ep": ep}
 

@@ -43,6 +43,7 @@ typedef struct {
   int32_t bc[3][2];       /* 0 periodic, 1 Dirichlet, 2 outflow, 3 reflecting wall */
   double bc_state[3][2][5]; /* Dirichlet primitive (rho, vx, vy, vz, P) */
   int32_t enforce;        /* physicality operator after every stage */
+  int32_t nodes;          /* 0 Gauss-Legendre, 1 Gauss-Lobatto-Legendre (degree >= 1) */
 } or_config;
 
 typedef struct {
@@ -94,6 +95,38 @@ int or_gauss_legendre(int N, double *x, double *w) {
   return 0;
 }
 
+/* N >= 2 Gauss-Lobatto-Legendre nodes (ascending) and weights on [-1, 1]: the end points and
+ * the N - 2 roots of P'_{N-1}, found by Newton's method with
+ * P''_n = (2 x P'_n - n (n + 1) P_n) / (1 - x^2) from the Chebyshev-Lobatto guesses;
+ * weights 2 / (N (N - 1) P_{N-1}(x_i)^2). */
+int or_gauss_lobatto(int N, double *x, double *w) {
+  if (N < 2 || N > MAXN) return 1;
+  const int n = N - 1;
+  for (int i = 0; i < N; ++i) {
+    double xi = -cos(M_PI * i / (double)n);
+    if (i > 0 && i < n) {
+      for (int it = 0; it < 100; ++it) {
+        double pn, dpn;
+        legendre(n, xi, &pn, &dpn);
+        double d2 = (2.0 * xi * dpn - n * (n + 1.0) * pn) / (1.0 - xi * xi);
+        double dx = dpn / d2;
+        xi -= dx;
+        if (fabs(dx) < 1e-16) break;
+      }
+    }
+    double pn, dpn;
+    if (i == 0) xi = -1.0;
+    if (i == n) xi = 1.0;
+    legendre(n, xi, &pn, &dpn);
+    /* P_n(+-1) = (+-1)^n; the derivative formula is not needed at the end points */
+    if (i == 0) pn = (n % 2) ? -1.0 : 1.0;
+    if (i == n) pn = 1.0;
+    x[i] = xi;
+    w[i] = 2.0 / (N * (N - 1.0) * pn * pn);
+  }
+  return 0;
+}
+
 /* Lagrange polynomial phi_i(t) through nodes x[0..N-1]. */
 static double lagrange(int N, const double *x, int i, double t) {
   double v = 1.0;
@@ -121,8 +154,9 @@ static double lagrange_deriv(int N, const double *x, int i, double t) {
  *   Dhat[i*N + a] = w_a phi_i'(x_a) / w_i   (volume term)
  *   em[i] = phi_i(-1), ep[i] = phi_i(+1)   (trace extrapolation)
  * The lifting coefficients are ep[i]/w_i and em[i]/w_i. */
-int or_basis(int N, double *x, double *w, double *Dhat, double *em, double *ep) {
-  if (or_gauss_legendre(N, x, w)) return 1;
+int or_basis_family(int N, int family, double *x, double *w, double *Dhat, double *em,
+                    double *ep) {
+  if (family == 1 ? or_gauss_lobatto(N, x, w) : or_gauss_legendre(N, x, w)) return 1;
   for (int i = 0; i < N; ++i) {
     for (int a = 0; a < N; ++a)
       Dhat[i * N + a] = (N == 1) ? 0.0 : w[a] * lagrange_deriv(N, x, i, x[a]) / w[i];
@@ -130,6 +164,10 @@ int or_basis(int N, double *x, double *w, double *Dhat, double *em, double *ep) 
     ep[i] = lagrange(N, x, i, +1.0);
   }
   return 0;
+}
+
+int or_basis(int N, double *x, double *w, double *Dhat, double *em, double *ep) {
+  return or_basis_family(N, 0, x, w, Dhat, em, ep);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -599,7 +637,8 @@ static int mesh_init(const or_config *c, mesh *m) {
     m->E *= m->n[d];
     if (d < c->dim) m->Nn *= m->N;
   }
-  return or_basis(m->N, m->x, m->w, m->Dhat, m->em, m->ep);
+  if (c->nodes == 1 && m->N < 2) return 1;
+  return or_basis_family(m->N, c->nodes, m->x, m->w, m->Dhat, m->em, m->ep);
 }
 
 static void node_ijk(const mesh *m, int node, int ijk[3]) {

@@ -25,6 +25,7 @@ C2P = {"analytic": 0, "iterative": 1, "default": 2}
 FLUX = {"llf": 0, "hll": 1, "hllc": 2}
 BC = {"periodic": 0, "dirichlet": 1, "outflow": 2, "reflect": 3}
 PRECISION = {"fp64": 0, "split": 1}
+NODES = {"gl": 0, "gll": 1}
 KERNEL_KINDS = ("volume", "face", "update", "enforce", "pointwise", "vjp")
 
 
@@ -45,6 +46,7 @@ class dgsrhd_config(ctypes.Structure):
         ("bc_state", ((ctypes.c_double * 5) * 2) * 3),
         ("enforce", ctypes.c_int32),
         ("precision", ctypes.c_int32),
+        ("nodes", ctypes.c_int32),
     ]
 
 
@@ -157,6 +159,7 @@ def make_config(spec: dict) -> dgsrhd_config:
                     c.bc_state[k][s][v] = float(bcs[k][s][v])
     c.enforce = int(bool(spec.get("enforce", True)))
     c.precision = _enum(PRECISION, spec.get("precision", "fp64"))
+    c.nodes = _enum(NODES, spec.get("nodes", "gl"))
     return c
 
 

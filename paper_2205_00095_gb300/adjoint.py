@@ -144,13 +144,11 @@ def rollout(solver: Solver, U0: torch.Tensor, dt: float, nsteps: int, every: int
 
 def node_weights(solver: Solver) -> torch.Tensor:
     """Quadrature weight of every node, (prod_d dx_d / 2) w_a w_b ..., shape (n_elem, n_node)."""
+    from .solver import node_weights_nd
     spec = solver.spec
-    dim, N = int(spec["dim"]), int(spec["degree"]) + 1
+    dim = int(spec["dim"])
     x = solver.node_coords()
-    w1 = np.polynomial.legendre.leggauss(N)[1]
-    w = w1
-    for _ in range(dim - 1):
-        w = np.multiply.outer(w1, w).ravel()
+    w = node_weights_nd(spec)
     jac = 1.0
     for d in range(dim):
         jac *= (spec["hi"][d] - spec["lo"][d]) / spec["n_elem"][d] / 2.0

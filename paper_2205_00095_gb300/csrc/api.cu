@@ -92,6 +92,29 @@ void gauss_legendre(int N, double* x, double* w) {
   }
 }
 
+// N >= 2 Gauss-Lobatto-Legendre nodes (ascending) and weights: the end points and the roots of
+// P'_{N-1} (Newton, with P''_n (1 - x^2) = 2 x P'_n - n (n + 1) P_n), weights
+// 2 / (N (N - 1) P_{N-1}(x)^2).
+void gauss_lobatto(int N, double* x, double* w) {
+  const int n = N - 1;
+  for (int i = 0; i < N; ++i) {
+    double t = -cos(M_PI * i / n);
+    if (i == 0) t = -1.0;
+    if (i == n) t = 1.0;
+    for (int k = 0; k < 60 && i > 0 && i < n; ++k) {
+      double p, dp;
+      legendre_pair(n, t, &p, &dp);
+      const double step = dp * (1.0 - t * t) / (2.0 * t * dp - n * (n + 1.0) * p);
+      t -= step;
+      if (fabs(step) <= 1e-17) break;
+    }
+    double p = (i == 0) ? ((n % 2) ? -1.0 : 1.0) : 1.0, dp;
+    if (i > 0 && i < n) legendre_pair(n, t, &p, &dp);
+    x[i] = t;
+    w[i] = 2.0 / (N * (N - 1.0) * p * p);
+  }
+}
+
 // Tables of the collocated scheme: Dhat[i][a] = w_a phi_i'(x_a)/w_i, e-+_i = phi_i(-+1).
 void basis_tables(int N, const double* x, const double* w, double* Dhat, double* em, double* ep) {
   double lam[dgsrhd::kMaxN];
@@ -116,9 +139,17 @@ void basis_tables(int N, const double* x, const double* w, double* Dhat, double*
     for (int a = 0; a < N; ++a) Dhat[i * N + a] = (N == 1) ? 0.0 : w[a] * Dm[a][i] / w[i];
   for (int s = 0; s < 2; ++s) {
     const double xe = s ? 1.0 : -1.0;
+    double* e = s ? ep : em;
+    int hit = -1;  // a node on the end point (Gauss-Lobatto): the trace is that node's value
+    for (int j = 0; j < N; ++j)
+      if (x[j] == xe) hit = j;
+    if (hit >= 0) {
+      for (int i = 0; i < N; ++i) e[i] = (i == hit) ? 1.0 : 0.0;
+      continue;
+    }
     double den = 0.0;
     for (int j = 0; j < N; ++j) den += lam[j] / (xe - x[j]);
-    for (int i = 0; i < N; ++i) (s ? ep : em)[i] = (lam[i] / (xe - x[i])) / den;
+    for (int i = 0; i < N; ++i) e[i] = (lam[i] / (xe - x[i])) / den;
   }
 }
 
@@ -243,6 +274,8 @@ bool valid_config(const dgsrhd_config* c) {
     return false;
   if (c->rk_stages < 1 || c->rk_stages > 3) return false;
   if (c->precision != DGSRHD_PREC_FP64 && c->precision != DGSRHD_PREC_SPLIT) return false;
+  if (c->nodes != DGSRHD_NODES_GL && c->nodes != DGSRHD_NODES_GLL) return false;
+  if (c->nodes == DGSRHD_NODES_GLL && c->degree < 1) return false;
   return true;
 }
 
@@ -313,7 +346,10 @@ int32_t dgsrhd_create(const dgsrhd_config* cfg, void* stream, dgsrhd_ctx** out) 
   p.c2p = cfg->c2p == DGSRHD_C2P_DEFAULT ? (cfg->eos == DGSRHD_EOS_IDEAL ? 0 : 1) : cfg->c2p;
   p.max_iter = cfg->c2p_max_iter > 0 ? cfg->c2p_max_iter : (cfg->eos == DGSRHD_EOS_IDEAL ? 30 : 100);
   p.flux = cfg->flux;
-  gauss_legendre(N, c->x, p.w);
+  if (cfg->nodes == DGSRHD_NODES_GLL)
+    gauss_lobatto(N, c->x, p.w);
+  else
+    gauss_legendre(N, c->x, p.w);
   basis_tables(N, c->x, p.w, p.Dhat, p.em, p.ep);
   for (int i = 0; i < N; ++i) {
     p.lm[i] = p.em[i] / p.w[i];
@@ -844,7 +880,10 @@ bool params_from_config(const dgsrhd_config* cfg, Params* out, long long* n_trac
   p.max_iter = cfg->c2p_max_iter > 0 ? cfg->c2p_max_iter : (cfg->eos == DGSRHD_EOS_IDEAL ? 30 : 100);
   p.flux = cfg->flux;
   double x[kMaxN];
-  gauss_legendre(N, x, p.w);
+  if (cfg->nodes == DGSRHD_NODES_GLL)
+    gauss_lobatto(N, x, p.w);
+  else
+    gauss_legendre(N, x, p.w);
   basis_tables(N, x, p.w, p.Dhat, p.em, p.ep);
   for (int i = 0; i < N; ++i) {
     p.lm[i] = p.em[i] / p.w[i];

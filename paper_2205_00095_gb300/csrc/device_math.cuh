@@ -213,11 +213,21 @@ __device__ __forceinline__ double W_tm_closed_form(double xi, double eta) {
   const double d = Q * Q * Q + R * R;
   double W;
   if (d < 0.0) {
-    const double iota = acos(R / sqrt(-Q * Q * Q));
-    W = 2.0 * sqrt(-Q) * cos(iota * (1.0 / 3.0)) - c.c1 * (1.0 / 3.0);
+    // (d < 0 implies Q < 0) sqrt(-Q^3) and sqrt(-Q) from one rsqrt(-Q)
+    const double rq = rsqrt(-Q);
+    const double iota = acos(R * rq * rq * rq);
+    W = 2.0 * (-Q) * rq * cos(iota * (1.0 / 3.0)) - c.c1 * (1.0 / 3.0);
   } else {
-    const double sd = sqrt(d);
-    W = -c.c1 * (1.0 / 3.0) + cbrt(R + sd) + cbrt(R - sd);
+    // Cardano's pair cbrt(R + sqrt(d)) + cbrt(R - sqrt(d)): the product of the two is -Q, so
+    // with y = R + sign(R) sqrt(d) (no cancellation) the pair is y^(1/3) - Q y^(-1/3), from one
+    // reciprocal cube root
+    const double y = R + copysign(sqrt_rs(d), R);
+    if (y == 0.0) {
+      W = -c.c1 * (1.0 / 3.0);
+    } else {
+      const double r = rcbrt(y);
+      W = fma(y * r, r, -Q * r) - c.c1 * (1.0 / 3.0);
+    }
   }
   return fmax(W, 0.0);
 }

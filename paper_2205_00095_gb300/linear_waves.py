@@ -67,12 +67,9 @@ def errors(s: Solver, spec: dict, U: torch.Tensor, t: float, wl):
     We = wl.linear_wave_ic(spec, X, t)
     Ue = s.initial_state(We)
     W = s.con2prim(U)
-    dim, N = int(spec["dim"]), int(spec["degree"]) + 1
-    w1 = np.polynomial.legendre.leggauss(N)[1]
-    w = w1
-    for _ in range(dim - 1):
-        w = np.multiply.outer(w1, w).ravel()
-    wq = torch.from_numpy(w).to(U.device)
+    from .solver import node_weights_nd
+    dim = int(spec["dim"])
+    wq = torch.from_numpy(node_weights_nd(spec)).to(U.device)
     jac = np.prod([(spec["hi"][d] - spec["lo"][d]) / spec["n_elem"][d] / 2.0 for d in range(dim)])
     vol = np.prod([spec["hi"][d] - spec["lo"][d] for d in range(dim)])
     E = U[4] + U[0]

@@ -33,6 +33,28 @@ def _dev_ptr(t: torch.Tensor, name: str, shape=None) -> int:
     return t.data_ptr()
 
 
+def quadrature_weights_1d(N: int, nodes: str = "gl") -> np.ndarray:
+    """The N one-dimensional quadrature weights of the collocated basis on [-1, 1]:
+    Gauss-Legendre ('gl'), or Gauss-Lobatto-Legendre ('gll', N >= 2: the end points and the
+    roots of P'_{N-1}, weights 2 / (N (N - 1) P_{N-1}(x)^2))."""
+    if nodes == "gl":
+        return np.polynomial.legendre.leggauss(N)[1]
+    P = np.polynomial.legendre.Legendre.basis(N - 1)
+    x = np.concatenate([[-1.0], np.sort(P.deriv().roots().real), [1.0]]) if N > 2 else np.array([-1.0, 1.0])
+    return 2.0 / (N * (N - 1) * P(x) ** 2)
+
+
+def node_weights_nd(spec: dict) -> np.ndarray:
+    """Tensor-product quadrature weight of every node of an element (x fastest), without the
+    (dx/2) Jacobians."""
+    dim, N = int(spec["dim"]), int(spec["degree"]) + 1
+    w1 = quadrature_weights_1d(N, spec.get("nodes", "gl"))
+    w = w1
+    for _ in range(dim - 1):
+        w = np.multiply.outer(w1, w).ravel()
+    return w
+
+
 class Solver:
     """One mesh and method choice (a dgsrhd context) bound to a CUDA stream."""
 

@@ -464,3 +464,48 @@ def test_reflecting_box_conserves_mass_and_energy(lib, flux):
     assert float((U[1] - S0).abs().max()) > 1e-3
     status, _ = s.stats()
     assert status == 0
+
+
+# ---------------------------------------------------------------------------------------
+# Gauss-Lobatto-Legendre nodes: the same method on the other node family
+# ---------------------------------------------------------------------------------------
+GLL_CASES = [
+    (1, [53], 1, "ideal", "llf", None),
+    (2, [13, 11], 2, "tm", "hll", [("outflow", "reflect"), ("periodic", "periodic")]),
+    (2, [9, 10], 3, "ideal", "hllc", None),
+    (3, [4, 5, 3], 4, "tm", "llf", None),
+]
+
+
+@pytest.mark.parametrize("dim,n,degree,eos,flux,bc", GLL_CASES)
+def test_rhs_gll(lib, dim, n, degree, eos, flux, bc):
+    spec = dict(wl.smooth_random(dim, n, degree, eos=eos, flux=flux, seed=dim + 7 * degree, bc=bc),
+                nodes="gll")
+    s = solver(spec)
+    U = gpu_state(s, spec)
+    R = s.rhs(U).cpu().numpy()
+    Ro, sto = oracle.rhs(spec, oracle_state(spec))
+    assert rel_inf(R, Ro) < 1e-11
+    X = s.node_coords()
+    assert np.isclose(X[0].min(), spec["lo"][0]) and np.isclose(X[0].max(), spec["hi"][0])
+
+
+def test_gll_blast_wave_needs_no_face_guard(lib):
+    """Problem 1 at p = 1 on Gauss-Lobatto nodes: the face traces are node values, which the
+    physicality operator keeps admissible, so the face guard never fires; GPU and oracle agree
+    after 100 steps."""
+    spec = dict(wl.blast_wave(n=64, degree=1), nodes="gll")
+    s = solver(spec, stream=torch.cuda.Stream())
+    dt = s.cfl_dt(0.2)
+    with torch.cuda.stream(s.stream):
+        U = s.initial_state(wl.initial_primitive(spec, s.node_coords_device()))
+        s.enforce(U)
+    Uo = oracle.prim2cons(spec, wl.initial_primitive(spec, oracle.node_coords(spec)))
+    Uo, _, _ = oracle.enforce(spec, Uo)
+    s.step(U, dt, 100)
+    s.synchronize()
+    Uo, sto = oracle.step(spec, Uo, dt, 100)
+    status, st = s.stats()
+    assert st["face_guard_hits"] == 0 and sto["face_guard_hits"] == 0
+    assert st["enforced_cells"] == sto["enforced_cells"] > 0
+    assert rel_inf(U.cpu().numpy(), Uo) < 1e-9

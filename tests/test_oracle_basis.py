@@ -56,3 +56,37 @@ def test_node_coordinates_2d():
             a, b = n % 3, n // 3
             assert abs(X[0, e, n] - (-1.0 + (ex + 0.5 * (1 + x[a])) * 1.0)) < 1e-14
             assert abs(X[1, e, n] - (0.5 + (ey + 0.5 * (1 + x[b])) * 0.5)) < 1e-14
+
+
+# ---------------------------------------------------------------------------------------
+# Gauss-Lobatto-Legendre variant (the node family the paper leaves open)
+# ---------------------------------------------------------------------------------------
+GLL_TABLE = {
+    2: ([-1.0, 1.0], [1.0, 1.0]),
+    3: ([-1.0, 0.0, 1.0], [1 / 3, 4 / 3, 1 / 3]),
+    4: ([-1.0, -1 / np.sqrt(5), 1 / np.sqrt(5), 1.0], [1 / 6, 5 / 6, 5 / 6, 1 / 6]),
+    5: ([-1.0, -np.sqrt(3 / 7), 0.0, np.sqrt(3 / 7), 1.0], [1 / 10, 49 / 90, 32 / 45, 49 / 90, 1 / 10]),
+}
+
+
+@pytest.mark.parametrize("N", [2, 3, 4, 5])
+def test_gll_nodes_and_weights_match_the_closed_forms(N):
+    b = oracle.basis(N, "gll")
+    x, w = GLL_TABLE[N]
+    assert np.allclose(b["x"], x, rtol=0, atol=1e-15) and np.allclose(b["w"], w, rtol=0, atol=1e-15)
+
+
+@pytest.mark.parametrize("N", [2, 3, 4, 5])
+def test_gll_quadrature_degree_and_summation_by_parts(N):
+    """Exact for degree 2N - 3; end-point traces are the end nodes; the collocated
+    differentiation satisfies W D + (W D)^T = diag(-1, 0, ..., 0, 1) (summation by parts)."""
+    b = oracle.basis(N, "gll")
+    x, w = b["x"], b["w"]
+    for k in range(2 * N - 2):
+        assert abs((w * x ** k).sum() - (2.0 / (k + 1) if k % 2 == 0 else 0.0)) < 1e-14
+    assert np.allclose(b["em"], np.eye(N)[0]) and np.allclose(b["ep"], np.eye(N)[-1])
+    # Dhat[i][a] = w_a phi_i'(x_a) / w_i, so w_i Dhat[i][a] = w_a phi_i'(x_a) = (W D)[a][i]
+    WD = (w[:, None] * b["Dhat"]).T
+    B = np.zeros((N, N))
+    B[0, 0], B[-1, -1] = -1.0, 1.0
+    assert np.allclose(WD + WD.T, B, atol=1e-13)

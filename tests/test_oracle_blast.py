@@ -60,3 +60,25 @@ def test_higher_degree_is_more_accurate():
     l2, st = run(128, 2)
     assert l1[0] < 0.3 * l0[0] and l2[0] < l1[0]
     assert st["c2p_invalid_input"] == 0
+
+
+def test_gll_nodes_converge_without_the_face_guard():
+    """The same blast wave on Gauss-Lobatto nodes (p = 1): no face guard hits, and the L1
+    error still falls with resolution."""
+    errs = []
+    for n in (64, 128):
+        spec = dict(wl.blast_wave(n=n, degree=1), nodes="gll")
+        X = oracle.node_coords(spec)
+        U = oracle.prim2cons(spec, wl.blast_wave_ic(spec, X))
+        U, _, _ = oracle.enforce(spec, U)
+        T = spec["t_final"]
+        nsteps = int(round(T / oracle.cfl_dt(spec, spec["cfl"])))
+        U, st = oracle.step(spec, U, T / nsteps, nsteps)
+        assert st["face_guard_hits"] == 0 and st["mean_inadmissible_cells"] == 0
+        g = json.load(open(GOLDEN))
+        ex = ExactRiemann((g["left"]["rho"], 0.0, g["left"]["P_workload"]),
+                          (g["right"]["rho"], 0.0, g["right"]["P_workload"]), g["gamma_ad"],
+                          g["interface"])
+        Uex = oracle.prim2cons(spec, ex.sample(X[0], T))
+        errs.append(np.abs(U[0] - Uex[0]).mean())
+    assert errs[1] < 0.8 * errs[0], errs
