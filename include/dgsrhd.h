@@ -93,6 +93,8 @@ typedef struct dgsrhd_config {
   int32_t enforce;             /* 1: physicality operator after every RK stage */
   int32_t precision;           /* DGSRHD_PREC_* */
   int32_t nodes;               /* DGSRHD_NODES_*: node family of the collocated basis */
+  int32_t limiter;             /* 1: scaling limiter after every RK stage, before the operator */
+  double limiter_alpha;        /* limiter bound relaxation: alpha = limiter_alpha h^(3/2) */
 } dgsrhd_config;
 
 typedef struct dgsrhd_stats {
@@ -104,6 +106,7 @@ typedef struct dgsrhd_stats {
   int64_t face_guard_hits;         /* face traces with rho <= 0 or P <= 0 replaced */
   int64_t enforced_cells;          /* elements smoothed by the physicality operator */
   int64_t mean_inadmissible_cells; /* flagged elements whose mean was inadmissible */
+  int64_t limited_cells;           /* elements scaled towards their mean by the limiter */
 } dgsrhd_stats;
 
 typedef struct dgsrhd_ctx dgsrhd_ctx;

@@ -61,13 +61,16 @@ class Config(ctypes.Structure):
         ("bc_state", ((ctypes.c_double * 5) * 2) * 3),
         ("enforce", ctypes.c_int32),
         ("nodes", ctypes.c_int32),
+        ("limiter", ctypes.c_int32),
+        ("limiter_alpha", ctypes.c_double),
     ]
 
 
 class Stats(ctypes.Structure):
     _fields_ = [(n, ctypes.c_int64) for n in (
         "c2p_calls", "c2p_iters_total", "c2p_iters_max", "c2p_nonconverged",
-        "c2p_invalid_input", "face_guard_hits", "enforced_cells", "mean_inadmissible_cells")]
+        "c2p_invalid_input", "face_guard_hits", "enforced_cells", "mean_inadmissible_cells",
+        "limited_cells")]
 
     def as_dict(self):
         return {n: int(getattr(self, n)) for n, _ in self._fields_}
@@ -114,6 +117,8 @@ def make_config(spec: dict) -> Config:
                     c.bc_state[d][s][v] = float(bcs[d][s][v])
     c.enforce = int(bool(spec.get("enforce", True)))
     c.nodes = _enum(_NODES, spec.get("nodes", "gl"))
+    c.limiter = int(bool(spec.get("limiter", False)))
+    c.limiter_alpha = float(spec.get("limiter_alpha", 50.0))
     return c
 
 

@@ -44,6 +44,8 @@ typedef struct {
   double bc_state[3][2][5]; /* Dirichlet primitive (rho, vx, vy, vz, P) */
   int32_t enforce;        /* physicality operator after every stage */
   int32_t nodes;          /* 0 Gauss-Legendre, 1 Gauss-Lobatto-Legendre (degree >= 1) */
+  int32_t limiter;        /* 1: scaling limiter after every stage, before the operator */
+  double limiter_alpha;   /* bound relaxation alpha = limiter_alpha h^(3/2) */
 } or_config;
 
 typedef struct {
@@ -55,6 +57,7 @@ typedef struct {
   int64_t face_guard_hits;
   int64_t enforced_cells;
   int64_t mean_inadmissible_cells;
+  int64_t limited_cells;
 } or_stats;
 
 /* ------------------------------------------------------------------------ */
@@ -993,6 +996,96 @@ int or_enforce(const or_config *c, double *U, double *s_out, or_stats *st) {
 /*           U^{n+1} = 1/3 U + 2/3 (U2 + dt R(U2))                           */
 /* with the physicality operator after every stage.                         */
 /* ------------------------------------------------------------------------ */
+/* ------------------------------------------------------------------------ */
+/* Slope limiter (reading: the paper adds the limiter of Moe et al. for p >= 1 */
+/* but prints no formula; this is a scaling limiter of that kind).            */
+/* For every element e with quadrature mean Ub_e and every conserved q: the   */
+/* bounds M = max(Ub over e and its face neighbours) + alpha and              */
+/* m = min(...) - alpha, alpha = limiter_alpha h^(3/2) (h the smallest dx);   */
+/* the element's extremes M*, m* over its nodes and its face traces;          */
+/* theta_q = min(1, (M - Ub)/(M* - Ub) if M* > M, (Ub - m)/(Ub - m*) if       */
+/* m* < m); theta = min over q; U_i <- Ub + theta (U_i - Ub) (the mean is     */
+/* kept and the state stays a convex combination of itself and its mean).    */
+/* Non-periodic boundaries contribute no neighbour.                          */
+/* ------------------------------------------------------------------------ */
+static void limit_all(const or_config *c, const mesh *m, double *U, or_stats *st) {
+  const int64_t tot = m->E * m->Nn;
+  double wsum = 0.0, h = 1e300;
+  for (int i = 0; i < m->Nn; ++i) wsum += node_weight(m, i);
+  for (int d = 0; d < m->dim; ++d) h = fmin(h, m->dx[d]);
+  const double alpha = c->limiter_alpha * pow(h, 1.5);
+  double *mean = (double *)malloc(sizeof(double) * 5 * (size_t)m->E);
+  if (!mean) return;
+  for (int64_t e = 0; e < m->E; ++e)
+    for (int v = 0; v < 5; ++v) {
+      double acc = 0.0;
+      for (int i = 0; i < m->Nn; ++i) acc += node_weight(m, i) * U[v * tot + e * m->Nn + i];
+      mean[v * m->E + e] = acc / wsum;
+    }
+  int Nt = 1;
+  for (int d = 0; d < m->dim - 1; ++d) Nt *= m->N;
+  for (int64_t e = 0; e < m->E; ++e) {
+    int64_t ec[3];
+    elem_coords(m, e, ec);
+    double theta = 1.0;
+    for (int v = 0; v < 5; ++v) {
+      const double ub = mean[v * m->E + e];
+      double M = ub, mn = ub;
+      for (int d = 0; d < m->dim; ++d)
+        for (int side = 0; side < 2; ++side) {
+          int64_t nc[3] = {ec[0], ec[1], ec[2]};
+          nc[d] += side ? 1 : -1;
+          if (nc[d] < 0 || nc[d] >= m->n[d]) {
+            if (c->bc[d][side] != 0) continue;
+            nc[d] = (nc[d] + m->n[d]) % m->n[d];
+          }
+          const double un = mean[v * m->E + elem_index(m, nc)];
+          M = fmax(M, un);
+          mn = fmin(mn, un);
+        }
+      M += alpha;
+      mn -= alpha;
+      /* extremes over the nodes and the face traces */
+      double hi = -1e300, lo = 1e300;
+      for (int i = 0; i < m->Nn; ++i) {
+        const double q = U[v * tot + e * m->Nn + i];
+        hi = fmax(hi, q);
+        lo = fmin(lo, q);
+      }
+      for (int d = 0; d < m->dim; ++d)
+        for (int side = 0; side < 2; ++side)
+          for (int t = 0; t < Nt; ++t) {
+            int ijk[3] = {0, 0, 0}, rem = t;
+            for (int dd = 0; dd < m->dim; ++dd) {
+              if (dd == d) continue;
+              ijk[dd] = rem % m->N;
+              rem /= m->N;
+            }
+            double q = 0.0;
+            for (int a = 0; a < m->N; ++a) {
+              ijk[d] = a;
+              q += (side ? m->ep[a] : m->em[a]) * U[v * tot + e * m->Nn + node_index(m, ijk)];
+            }
+            hi = fmax(hi, q);
+            lo = fmin(lo, q);
+          }
+      if (hi > M) theta = fmin(theta, (M - ub) / (hi - ub));
+      if (lo < mn) theta = fmin(theta, (ub - mn) / (ub - lo));
+    }
+    if (theta < 1.0) {
+      if (st) st->limited_cells += 1;
+      for (int v = 0; v < 5; ++v) {
+        const double ub = mean[v * m->E + e];
+        for (int i = 0; i < m->Nn; ++i) {
+          double *q = &U[v * tot + e * m->Nn + i];
+          *q = ub + theta * (*q - ub);
+        }
+      }
+    }
+  }
+  free(mean);
+}
+
 int or_step(const or_config *c, double *U, double dt, int nsteps, or_stats *st) {
   mesh m;
   if (mesh_init(c, &m)) return 1;
@@ -1013,6 +1106,7 @@ int or_step(const or_config *c, double *U, double dt, int nsteps, or_stats *st) 
       if (rc) { free(U0); free(Uk); free(R); return rc; }
       double a = a_n[ns - 1][k], b = b_k[ns - 1][k];
       for (int64_t j = 0; j < n; ++j) Uk[j] = a * U0[j] + b * (Uk[j] + dt * R[j]);
+      if (c->limiter) limit_all(c, &m, Uk, st);
       if (c->enforce) or_enforce(c, Uk, NULL, st);
     }
     memcpy(U, Uk, sizeof(double) * n);

@@ -47,11 +47,14 @@ class dgsrhd_config(ctypes.Structure):
         ("enforce", ctypes.c_int32),
         ("precision", ctypes.c_int32),
         ("nodes", ctypes.c_int32),
+        ("limiter", ctypes.c_int32),
+        ("limiter_alpha", ctypes.c_double),
     ]
 
 
 STAT_FIELDS = ("c2p_calls", "c2p_iters_total", "c2p_iters_max", "c2p_nonconverged",
-               "c2p_invalid_input", "face_guard_hits", "enforced_cells", "mean_inadmissible_cells")
+               "c2p_invalid_input", "face_guard_hits", "enforced_cells", "mean_inadmissible_cells",
+               "limited_cells")
 
 
 class dgsrhd_stats(ctypes.Structure):
@@ -160,6 +163,8 @@ def make_config(spec: dict) -> dgsrhd_config:
     c.enforce = int(bool(spec.get("enforce", True)))
     c.precision = _enum(PRECISION, spec.get("precision", "fp64"))
     c.nodes = _enum(NODES, spec.get("nodes", "gl"))
+    c.limiter = int(bool(spec.get("limiter", False)))
+    c.limiter_alpha = float(spec.get("limiter_alpha", 50.0))
     return c
 
 

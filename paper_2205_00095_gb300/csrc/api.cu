@@ -36,6 +36,7 @@ struct dgsrhd_ctx {
   double* TrB;  // VJP: trace adjoints
   double* Yb;   // stage VJP: adjoint of the stage before the operator
   unsigned char* Gd;  // VJP: face-guard flag per face point [E][2 dim Nt]
+  double* Mn;   // limiter: element means [5][E]
   long long fs_total;  // doubles of the face-flux buffer
   unsigned long long* stats;
   long long c2p_calls;
@@ -160,7 +161,9 @@ int kernel_kind(Op op) {
     case Op::Volume: return DGSRHD_KERNEL_VOLUME;
     case Op::Face: return DGSRHD_KERNEL_FACE;
     case Op::Update: return DGSRHD_KERNEL_UPDATE;
-    case Op::Enforce: return DGSRHD_KERNEL_ENFORCE;
+    case Op::Enforce:
+    case Op::Means:
+    case Op::Limit: return DGSRHD_KERNEL_ENFORCE;
     default: return DGSRHD_KERNEL_VJP;
   }
 }
@@ -221,6 +224,24 @@ cudaError_t volume_and_faces(dgsrhd_ctx* c, const double* U) {
   return run_stage(c, f);
 }
 
+// The limiter after a stage: element means, then the limit kernel (which also applies the
+// physicality operator when it is enabled).
+cudaError_t limit_stage(dgsrhd_ctx* c, double* U, double* s_out) {
+  StageArgs m{};
+  m.op = Op::Means;
+  m.Uout = U;
+  m.means = c->Mn;
+  cudaError_t e = run_stage(c, m);
+  if (e != cudaSuccess) return e;
+  StageArgs l{};
+  l.op = Op::Limit;
+  l.Uout = U;
+  l.means = c->Mn;
+  l.enforce = c->cfg.enforce;
+  l.s_out = s_out;
+  return run_stage(c, l);
+}
+
 // Shu-Osher coefficients U^(k) = a_n U^n + b_k (U^(k-1) + dt R(U^(k-1)))
 const double kAn[3][3] = {{0.0, 0.0, 0.0}, {0.0, 0.5, 0.0}, {0.0, 0.75, 1.0 / 3.0}};
 const double kBk[3][3] = {{1.0, 0.0, 0.0}, {1.0, 0.5, 0.0}, {1.0, 0.25, 2.0 / 3.0}};
@@ -243,9 +264,13 @@ cudaError_t one_step(dgsrhd_ctx* c, double* U, double dt) {
     u.b_k = kBk[ns - 1][k];
     u.dt = dt;
     u.mode = 1;
-    u.enforce = c->cfg.enforce;
+    u.enforce = c->cfg.enforce && !c->cfg.limiter;
     e = run_stage(c, u);
     if (e != cudaSuccess) return e;
+    if (c->cfg.limiter) {
+      e = limit_stage(c, Uout, nullptr);
+      if (e != cudaSuccess) return e;
+    }
   }
   return cudaSuccess;
 }
@@ -276,6 +301,8 @@ bool valid_config(const dgsrhd_config* c) {
   if (c->precision != DGSRHD_PREC_FP64 && c->precision != DGSRHD_PREC_SPLIT) return false;
   if (c->nodes != DGSRHD_NODES_GL && c->nodes != DGSRHD_NODES_GLL) return false;
   if (c->nodes == DGSRHD_NODES_GLL && c->degree < 1) return false;
+  if (c->limiter != 0 && c->limiter != 1) return false;
+  if (c->limiter && !(c->limiter_alpha >= 0.0)) return false;
   return true;
 }
 
@@ -346,6 +373,12 @@ int32_t dgsrhd_create(const dgsrhd_config* cfg, void* stream, dgsrhd_ctx** out) 
   p.c2p = cfg->c2p == DGSRHD_C2P_DEFAULT ? (cfg->eos == DGSRHD_EOS_IDEAL ? 0 : 1) : cfg->c2p;
   p.max_iter = cfg->c2p_max_iter > 0 ? cfg->c2p_max_iter : (cfg->eos == DGSRHD_EOS_IDEAL ? 30 : 100);
   p.flux = cfg->flux;
+  {
+    double h = 1e300;
+    for (int d = 0; d < cfg->dim; ++d) h = fmin(h, (cfg->hi[d] - cfg->lo[d]) / (double)cfg->n_elem[d]);
+    p.limiter = cfg->limiter;
+    p.lim_alpha = cfg->limiter ? cfg->limiter_alpha * pow(h, 1.5) : 0.0;
+  }
   if (cfg->nodes == DGSRHD_NODES_GLL)
     gauss_lobatto(N, c->x, p.w);
   else
@@ -369,6 +402,7 @@ int32_t dgsrhd_create(const dgsrhd_config* cfg, void* stream, dgsrhd_ctx** out) 
   if (e == cudaSuccess) e = alloc(&c->TrB, ntr);
   if (e == cudaSuccess) e = alloc(&c->Yb, c->nstate);
   if (e == cudaSuccess) e = alloc(&c->Gd, 2LL * c->dim * E * p.Nt);
+  if (e == cudaSuccess && cfg->limiter) e = alloc(&c->Mn, 5LL * E);
   if (e == cudaSuccess) e = alloc(&c->stats, (size_t)dgsrhd::kStatCount * 64);
   if (e == cudaSuccess) e = cudaMemsetAsync(c->stats, 0, sizeof(unsigned long long) * dgsrhd::kStatCount * 64, c->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
@@ -401,6 +435,7 @@ void dgsrhd_destroy(dgsrhd_ctx* c) {
   cudaFree(c->TrB);
   cudaFree(c->Yb);
   cudaFree(c->Gd);
+  cudaFree(c->Mn);
   cudaFree(c->stats);
   delete c;
 }
@@ -485,7 +520,7 @@ int32_t dgsrhd_enforce(dgsrhd_ctx* c, double* U, double* s_out) {
 int32_t dgsrhd_step(dgsrhd_ctx* c, double* U, double dt, int32_t nsteps) {
   if (!c || !U || nsteps < 0 || !(dt >= 0.0)) return DGSRHD_EINVAL;
   if (nsteps == 0) return DGSRHD_OK;
-  const long long per_step = 3LL * c->cfg.rk_stages;
+  const long long per_step = (c->cfg.limiter ? 5LL : 3LL) * c->cfg.rk_stages;
   if (c->stream == nullptr || c->profiling) {
     // the legacy stream cannot be captured, and timed kernels are launched one by one
     for (int s = 0; s < nsteps; ++s) {
@@ -574,6 +609,7 @@ int32_t dgsrhd_get_stats(dgsrhd_ctx* c, dgsrhd_stats* out, int32_t reset) {
   out->face_guard_hits = (int64_t)v[dgsrhd::kStatFaceGuard];
   out->enforced_cells = (int64_t)v[dgsrhd::kStatEnforced];
   out->mean_inadmissible_cells = (int64_t)v[dgsrhd::kStatMeanBad];
+  out->limited_cells = (int64_t)v[dgsrhd::kStatLimited];
   if (reset) {
     if (cudaMemsetAsync(c->stats, 0, bytes, c->stream) != cudaSuccess) return DGSRHD_ECUDA;
     if (cudaStreamSynchronize(c->stream) != cudaSuccess) return DGSRHD_ECUDA;
@@ -753,9 +789,11 @@ int32_t dgsrhd_step_stage(dgsrhd_ctx* c, const double* Un, const double* Uk, dou
   u.b_k = kBk[ns - 1][stage];
   u.dt = dt;
   u.mode = 1;
-  u.enforce = c->cfg.enforce;
+  u.enforce = c->cfg.enforce && !c->cfg.limiter;
   u.s_out = s_out;
-  return cuda_status(run_stage(c, u));
+  if (run_stage(c, u) != cudaSuccess) return DGSRHD_ECUDA;
+  if (c->cfg.limiter) return cuda_status(limit_stage(c, Uout, s_out));
+  return DGSRHD_OK;
 }
 
 int32_t dgsrhd_stage_vjp(dgsrhd_ctx* c, const double* Uk, const double* s, const double* saved,
@@ -764,6 +802,7 @@ int32_t dgsrhd_stage_vjp(dgsrhd_ctx* c, const double* Uk, const double* s, const
   if (!c || !Uk || !Z_bar || !Un_bar || !Uk_bar || stage < 0 || stage >= c->cfg.rk_stages)
     return DGSRHD_EINVAL;
   if (Z_bar == Un_bar || Z_bar == Uk_bar) return DGSRHD_EINVAL;
+  if (c->cfg.limiter) return DGSRHD_EINVAL;  // no reverse sweep of the limiter
   const int ns = c->cfg.rk_stages;
   const double* Yb = Z_bar;
   if (c->cfg.enforce && s) {
@@ -879,6 +918,12 @@ bool params_from_config(const dgsrhd_config* cfg, Params* out, long long* n_trac
   p.c2p = cfg->c2p == DGSRHD_C2P_DEFAULT ? (cfg->eos == DGSRHD_EOS_IDEAL ? 0 : 1) : cfg->c2p;
   p.max_iter = cfg->c2p_max_iter > 0 ? cfg->c2p_max_iter : (cfg->eos == DGSRHD_EOS_IDEAL ? 30 : 100);
   p.flux = cfg->flux;
+  {
+    double h = 1e300;
+    for (int d = 0; d < cfg->dim; ++d) h = fmin(h, (cfg->hi[d] - cfg->lo[d]) / (double)cfg->n_elem[d]);
+    p.limiter = cfg->limiter;
+    p.lim_alpha = cfg->limiter ? cfg->limiter_alpha * pow(h, 1.5) : 0.0;
+  }
   double x[kMaxN];
   if (cfg->nodes == DGSRHD_NODES_GLL)
     gauss_lobatto(N, x, p.w);

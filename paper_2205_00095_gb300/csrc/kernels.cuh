@@ -479,6 +479,136 @@ __global__ void __launch_bounds__(Shape<DIM, N>::BLOCK)
 }
 
 // ---------------------------------------------------------------------------------------
+// Slope limiter (reading: a scaling limiter of the kind the paper takes from Moe et al. for
+// p >= 1, formula not printed).  means_kernel: the quadrature mean of every element.
+// limit_kernel: per element, bounds M = max(own and face-neighbour means) + alpha and
+// m = min(...) - alpha per conserved variable (non-periodic boundaries add no neighbour); the
+// element's extremes over its nodes and its face traces; one factor theta = min over the
+// variables of (M - mean)/(max - mean) and (mean - m)/(mean - min) (where exceeded), and
+// U_i <- mean + theta (U_i - mean); then the physicality operator when enabled.
+// ---------------------------------------------------------------------------------------
+template <int DIM, int N>
+__global__ void __launch_bounds__(Shape<DIM, N>::BLOCK)
+    means_kernel(Params p, const double* __restrict__ U, double* __restrict__ means) {
+  using S = Shape<DIM, N>;
+  constexpr int Nn = S::Nn;
+  __shared__ double sh[5][S::BLOCK];
+  const int tid = threadIdx.x;
+  const int le = tid / Nn, li = tid - le * Nn;
+  const long long e = (long long)blockIdx.x * S::EPB + le;
+  const bool valid = e < p.E;
+  const long long tot = p.E * Nn;
+  if (valid) {
+    int ijk[3];
+    node_ijk<DIM, N>(li, ijk);
+    double wi = 1.0;
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) wi *= p.w[ijk[d]];
+#pragma unroll
+    for (int v = 0; v < 5; ++v) sh[v][tid] = wi * U[v * tot + e * Nn + li];
+  }
+  __syncthreads();
+  if (valid) {
+    for (int v = li; v < 5; v += Nn) {  // elements of fewer than 5 nodes take several rounds
+      double acc = 0.0;
+      for (int j = 0; j < Nn; ++j) acc += sh[v][le * Nn + j];
+      means[v * p.E + e] = acc / p.wsum;
+    }
+  }
+}
+
+template <int DIM, int N>
+__global__ void __launch_bounds__(Shape<DIM, N>::BLOCK)
+    limit_kernel(Params p, double* U, const double* __restrict__ means, int enforce,
+                 double* __restrict__ s_out) {
+  using S = Shape<DIM, N>;
+  constexpr int Nn = S::Nn, Nt = S::Nt, NFP = S::NFP, EPB = S::EPB;
+  __shared__ EnforceShared<DIM, N> sh;  // sh.a holds the nodal state first
+  __shared__ double tr[EPB][NFP][5];     // face traces of the conserved variables
+  __shared__ double th[EPB];
+  const int tid = threadIdx.x;
+  const int le = tid / Nn, li = tid - le * Nn;
+  const long long e = (long long)blockIdx.x * EPB + le;
+  const bool valid = e < p.E;
+  const long long tot = p.E * Nn;
+  const long long g = e * Nn + li;
+  double u[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+  if (valid) {
+#pragma unroll
+    for (int v = 0; v < 5; ++v) {
+      u[v] = U[v * tot + g];
+      sh.a[v][tid] = u[v];
+    }
+  }
+  __syncthreads();
+  if (valid) {
+    for (int fp = li; fp < NFP; fp += Nn) {
+      const int d = fp / (2 * Nt), side = (fp / Nt) & 1, t = fp % Nt;
+#pragma unroll
+      for (int v = 0; v < 5; ++v) {
+        double q = 0.0;
+#pragma unroll
+        for (int a = 0; a < N; ++a)
+          q = fma(side ? p.ep[a] : p.em[a], sh.a[v][le * Nn + line_node<DIM, N>(d, t, a)], q);
+        tr[le][fp][v] = q;
+      }
+    }
+  }
+  __syncthreads();
+  if (valid && li == 0) {
+    double theta = 1.0;
+    for (int v = 0; v < 5; ++v) {
+      const double ub = means[v * p.E + e];
+      double M = ub, m = ub;
+#pragma unroll
+      for (int d = 0; d < DIM; ++d) {
+        const long long c = elem_coord(p, e, d);
+#pragma unroll
+        for (int side = 0; side < 2; ++side) {
+          long long ne;
+          if (side == 0)
+            ne = (c > 0) ? e - p.stride[d] : (p.bc[d][0] == 0 ? e + (p.n[d] - 1) * p.stride[d] : -1);
+          else
+            ne = (c < p.n[d] - 1) ? e + p.stride[d] : (p.bc[d][1] == 0 ? e - (p.n[d] - 1) * p.stride[d] : -1);
+          if (ne < 0) continue;
+          const double un = means[v * p.E + ne];
+          M = fmax(M, un);
+          m = fmin(m, un);
+        }
+      }
+      M += p.lim_alpha;
+      m -= p.lim_alpha;
+      double hi = -1e300, lo = 1e300;
+      for (int i = 0; i < Nn; ++i) {
+        hi = fmax(hi, sh.a[v][le * Nn + i]);
+        lo = fmin(lo, sh.a[v][le * Nn + i]);
+      }
+      for (int fp = 0; fp < NFP; ++fp) {
+        hi = fmax(hi, tr[le][fp][v]);
+        lo = fmin(lo, tr[le][fp][v]);
+      }
+      if (hi > M) theta = fmin(theta, (M - ub) / (hi - ub));
+      if (lo < m) theta = fmin(theta, (ub - m) / (ub - lo));
+    }
+    th[le] = theta;
+    if (theta < 1.0) atomicAdd(&p.stats[kStatLimited * 64 + (blockIdx.x & 63)], 1ULL);
+  }
+  __syncthreads();
+  if (valid && th[le] < 1.0) {
+    const double t = th[le];
+#pragma unroll
+    for (int v = 0; v < 5; ++v) {
+      const double ub = means[v * p.E + e];
+      u[v] = fma(t, u[v] - ub, ub);
+    }
+  }
+  if (enforce) enforce_block(p, u, valid, le, li, e, s_out, sh);
+  if (valid)
+#pragma unroll
+    for (int v = 0; v < 5; ++v) U[v * tot + g] = u[v];
+}
+
+// ---------------------------------------------------------------------------------------
 // Host-side launchers
 // ---------------------------------------------------------------------------------------
 template <int DIM, int N>
@@ -548,6 +678,12 @@ static cudaError_t launch_stage_kernels(const StageArgs& a) {
       break;
     case Op::EnforceVjp:
       enforce_vjp_kernel<DIM, N><<<eblocks, S::BLOCK, 0, a.stream>>>(p, a.s_in, a.Tbar, a.Ubar);
+      break;
+    case Op::Means:
+      means_kernel<DIM, N><<<eblocks, S::BLOCK, 0, a.stream>>>(p, a.Uout, a.means);
+      break;
+    case Op::Limit:
+      limit_kernel<DIM, N><<<eblocks, S::BLOCK, 0, a.stream>>>(p, a.Uout, a.means, a.enforce, a.s_out);
       break;
     default:
       return cudaErrorInvalidValue;

@@ -7,7 +7,7 @@
 
 namespace dgsrhd {
 
-enum class Op { Volume, Face, Update, Enforce, VjpFace, VjpNode, EnforceVjp };
+enum class Op { Volume, Face, Update, Enforce, VjpFace, VjpNode, EnforceVjp, Means, Limit };
 
 struct StageArgs {
   Op op;
@@ -34,6 +34,7 @@ struct StageArgs {
   double* Wstore;      // Volume: optional output of the nodal (rho, u, P); VjpNode: its input
   unsigned char* guard;  // Volume: optional face-guard flag per face point [E][NFP]; VjpNode: input
   double* tape;        // Face: optional face-state tape (roots and reciprocals); VjpFace: input
+  double* means;       // Means: output, Limit: input; element means [5][E]
   // VjpNode with Ukb set: fused stage combination Unb += a_n Rbar, Ukb += b_k (Rbar + dt Ubar)
   double* Unb;
   double* Ukb;

@@ -113,6 +113,7 @@ extern "C" int32_t dgsrhd_rhs_noalloc(const dgsrhd_config* cfg, void* stream, co
   stats_out->face_guard_hits = (int64_t)v[kStatFaceGuard];
   stats_out->enforced_cells = 0;
   stats_out->mean_inadmissible_cells = 0;
+  stats_out->limited_cells = 0;
   if (stats_out->c2p_invalid_input) return DGSRHD_EBADSTATE;
   if (stats_out->c2p_nonconverged) return DGSRHD_EC2P_NOCONV;
   return DGSRHD_OK;

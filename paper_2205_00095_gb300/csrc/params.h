@@ -22,6 +22,7 @@ enum StatSlot {
   kStatFaceGuard,
   kStatEnforced,
   kStatMeanBad,
+  kStatLimited,
   kStatCount
 };
 
@@ -47,6 +48,8 @@ struct Params {
   double lm[kMaxN], lp[kMaxN];   // phi_i(-1)/w_i, phi_i(+1)/w_i
   double wsum;               // sum of tensor weights = 2^dim
   unsigned long long* stats; // device counters [kStatCount]
+  int limiter;               // 1: scaling limiter after every stage
+  double lim_alpha;          // its bound relaxation (already times h^(3/2))
 };
 
 }  // namespace dgsrhd

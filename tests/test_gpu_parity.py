@@ -200,6 +200,10 @@ def test_enforce(lib, dim, degree, n):
     (lambda c2p: wl.kh_single(nx=10, ny=20, degree=2, c2p=c2p), "iterative"),
     (lambda c2p: wl.riemann_1d(4, n=96, degree=1), "iterative"),
     (lambda c2p: wl.riemann_1d(5, n=64, degree=0), "iterative"),
+    # the scaling limiter
+    (lambda c2p: dict(wl.riemann_1d(2, n=96, degree=1), limiter=True), "iterative"),
+    (lambda c2p: dict(wl.riemann_1d(5, n=64, degree=1), limiter=True), "iterative"),
+    (lambda c2p: dict(wl.kh_single(nx=12, ny=24, degree=2), limiter=True), "iterative"),
 ])
 def test_step_one_and_hundred(lib, spec_fn, c2p):
     spec = spec_fn(c2p)
@@ -208,7 +212,7 @@ def test_step_one_and_hundred(lib, spec_fn, c2p):
     U = gpu_state(s, spec)
     Uo = oracle_state(spec)
     s.step(U, dt, 1)
-    Uo1, _ = oracle.step(spec, Uo, dt, 1)
+    Uo1, st1 = oracle.step(spec, Uo, dt, 1)
     torch.cuda.synchronize()
     assert rel_inf(U.cpu().numpy(), Uo1) < 1e-11
     s.step(U, dt, 99)
@@ -216,7 +220,12 @@ def test_step_one_and_hundred(lib, spec_fn, c2p):
     torch.cuda.synchronize()
     assert rel_inf(U.cpu().numpy(), Uo100) < 1e-9
     status, st = s.stats()
-    assert status == 0 and st["enforced_cells"] == sto["enforced_cells"]
+    assert status == 0
+    # the device counters cover all 100 steps: the oracle's two calls together
+    assert st["enforced_cells"] == st1["enforced_cells"] + sto["enforced_cells"]
+    assert st["limited_cells"] == st1["limited_cells"] + sto["limited_cells"]
+    if spec.get("limiter") and spec["name"] == "riemann_1d":
+        assert st["limited_cells"] > 0
 
 
 def test_kh3d_one_step(lib):

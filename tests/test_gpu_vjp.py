@@ -217,3 +217,17 @@ def test_vjp_of_hllc_is_refused(gpu_lib):
     Ub = torch.zeros_like(U)
     torch.cuda.synchronize()
     assert s.lib.dgsrhd_rhs_vjp(s.ctx, U.data_ptr(), Rb.data_ptr(), Ub.data_ptr()) == _lib.DGSRHD_EINVAL
+
+
+def test_stage_vjp_with_the_limiter_is_refused(gpu_lib):
+    """The limiter has no reverse sweep: dgsrhd_stage_vjp returns DGSRHD_EINVAL for it."""
+    from paper_2205_00095_gb300 import _lib
+    spec = dict(wl.kh2d(nx=4, ny=8, degree=2), limiter=True)
+    s = solver(spec)
+    U = s.initial_state(wl.kh2d_ic(spec, s.node_coords()))
+    Z = torch.zeros_like(U)
+    a, b = torch.zeros_like(U), torch.zeros_like(U)
+    torch.cuda.synchronize()
+    st = s.lib.dgsrhd_stage_vjp(s.ctx, U.data_ptr(), None, None, Z.data_ptr(), a.data_ptr(),
+                                b.data_ptr(), 0, 1e-3)
+    assert st == _lib.DGSRHD_EINVAL

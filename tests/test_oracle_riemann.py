@@ -23,8 +23,8 @@ def exact(spec):
     return ExactRiemann((L[0], L[1], L[4]), (R[0], R[1], R[4]), G, 0.5)
 
 
-def run(problem, n, degree, flux="hllc"):
-    spec = wl.riemann_1d(problem, n=n, degree=degree, flux=flux)
+def run(problem, n, degree, flux="hllc", limiter=False):
+    spec = dict(wl.riemann_1d(problem, n=n, degree=degree, flux=flux), limiter=limiter)
     X = oracle.node_coords(spec)
     U = oracle.prim2cons(spec, wl.initial_primitive(spec, X))
     U, _, _ = oracle.enforce(spec, U)
@@ -68,3 +68,16 @@ def test_hllc_resolves_the_sod_contact_better_than_hll():
     l1c, _ = run(4, 128, 1, flux="hllc")
     l1h, _ = run(4, 128, 1, flux="hll")
     assert l1c[0] < l1h[0], (l1c[0], l1h[0])
+
+
+@pytest.mark.parametrize("problem", [2, 4, 5])
+def test_riemann_problem_with_the_limiter_at_p1(problem):
+    """With the scaling limiter (reading for the paper's Moe limiter) the blasts run at p = 1:
+    admissible means throughout and errors falling with resolution."""
+    l1a, st = run(problem, 64, 1, limiter=True)
+    l1b, _ = run(problem, 128, 1, limiter=True)
+    l1c, _ = run(problem, 256, 1, limiter=True)
+    assert st["mean_inadmissible_cells"] == 0 and st["c2p_invalid_input"] == 0
+    assert st["limited_cells"] > 0
+    k = [0, 1, 4]
+    assert np.all(l1b[k] < 0.9 * l1a[k]) and np.all(l1c[k] < 0.9 * l1b[k]), (l1a, l1b, l1c)
