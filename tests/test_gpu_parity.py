@@ -518,3 +518,29 @@ def test_gll_blast_wave_needs_no_face_guard(lib):
     assert st["face_guard_hits"] == 0 and sto["face_guard_hits"] == 0
     assert st["enforced_cells"] == sto["enforced_cells"] > 0
     assert rel_inf(U.cpu().numpy(), Uo) < 1e-9
+
+
+# ---------------------------------------------------------------------------------------
+# the paper's 2D Riemann problems (HLLC with the limiter)
+# ---------------------------------------------------------------------------------------
+# Test 1's colliding shocks amplify rounding-level differences quickly (the oracle alone breaks
+# its mirror symmetry by 6e-6 at p = 1, t = 0.8): one step at 1e-11, forty steps at 1e-4.
+@pytest.mark.parametrize("test,degree,steps,tol", [(1, 1, 1, 1e-11), (1, 1, 40, 1e-4),
+                                                   (2, 1, 40, 1e-9), (3, 2, 40, 1e-9)])
+def test_riemann_2d_against_oracle(lib, test, degree, steps, tol):
+    spec = wl.riemann_2d(test, n=20, degree=degree)
+    s = solver(spec, stream=torch.cuda.Stream())
+    dt = s.cfl_dt(0.2)
+    with torch.cuda.stream(s.stream):
+        U = s.initial_state(wl.initial_primitive(spec, s.node_coords_device()))
+        s.enforce(U)
+    Uo = oracle.prim2cons(spec, wl.initial_primitive(spec, oracle.node_coords(spec)))
+    Uo, _, st0 = oracle.enforce(spec, Uo)
+    s.step(U, dt, steps)
+    s.synchronize()
+    Uo, sto = oracle.step(spec, Uo, dt, steps)
+    assert rel_inf(U.cpu().numpy(), Uo) < tol
+    status, st = s.stats()
+    assert status == 0
+    if tol < 1e-8:
+        assert st["limited_cells"] == sto["limited_cells"]

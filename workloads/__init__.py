@@ -16,6 +16,7 @@ A problem description is a plain dict:
 The workloads follow the problems of the paper:
   blast_wave      -- 1D relativistic blast wave (Sec. 4.2, problem 1)
   riemann_1d      -- 1D Riemann problems 2-5 of Sec. 4.2 (problem 5: a reflecting wall)
+  riemann_2d      -- the three 2D Riemann problems of Sec. 4.3 (four quadrants)
   advected_wave   -- 2D smooth density wave, periodic (smooth convergence case)
   kh2d            -- 2D relativistic Kelvin-Helmholtz, double shear layer (Sec. 4.4 set-up
                      recast as periodic with two layers), Taub-Matthews EOS
@@ -63,6 +64,41 @@ RIEMANN_1D = {
     5: dict(left=(1.0, 0.99999, 0.0, 0.0, 0.01), right=(1.0, 0.99999, 0.0, 0.0, 0.01),
             gamma_ad=4.0 / 3.0, t_final=1.5, right_bc="reflect"),
 }
+
+
+# The paper's 2D Riemann problems (Sec. 4.3): primitive (rho, vx, vy, P) in the quadrants
+# Q1 = [0,1]x[0,1], Q2 = [-1,0]x[0,1], Q3 = [-1,0]x[-1,0], Q4 = [0,1]x[-1,0].
+RIEMANN_2D = {
+    1: [(0.035145216124503, 0.0, 0.0, 0.162931056509027), (0.1, 0.7, 0.0, 1.0),
+        (0.5, 0.0, 0.0, 1.0), (0.1, 0.0, 0.7, 1.0)],
+    2: [(0.5, 0.5, -0.5, 5.0), (1.0, 0.5, 0.5, 5.0), (3.0, -0.5, 0.5, 5.0), (1.5, -0.5, -0.5, 5.0)],
+    3: [(1.0, 0.0, 0.0, 1.0), (0.5771, -0.3529, 0.0, 0.4), (1.0, -0.3529, -0.3529, 1.0),
+        (0.5771, 0.0, -0.3529, 0.4)],
+}
+
+
+def riemann_2d(test: int, n: int = 128, degree: int = 1, flux: str = "hllc",
+               limiter: bool = True) -> dict:
+    """2D Riemann problem `test` (1-3) of Sec. 4.3 on [-1,1]^2: ideal EOS Gamma = 5/3 with the
+    iterative con2prim, transmissive (outflow) boundaries, HLLC and the limiter, to t = 0.8."""
+    return dict(name="riemann_2d", test=test, dim=2, degree=degree, n_elem=[n, n],
+                lo=[-1.0, -1.0], hi=[1.0, 1.0], eos="ideal", gamma_ad=5.0 / 3.0, c2p="iterative",
+                flux=flux, rk_stages=min(degree + 1, 3), bc=[("outflow", "outflow")] * 2,
+                enforce=True, limiter=limiter, cfl=0.2, t_final=0.8,
+                quadrants=RIEMANN_2D[test])
+
+
+def riemann_2d_ic(spec: dict, X):
+    xp = _xp(X)
+    x, y = X[0], X[1]
+    Q = spec["quadrants"]
+    right, top = x >= 0.0, y >= 0.0
+    out = []
+    for v in range(4):
+        q1, q2, q3, q4 = (_const(x, Q[k][v]) for k in range(4))
+        out.append(xp.where(top, xp.where(right, q1, q2), xp.where(right, q4, q3)))
+    rho, vx, vy, P = out
+    return xp.stack([rho, vx, vy, _const(x, 0.0), P])
 
 
 def riemann_1d(problem: int, n: int = 128, degree: int = 1, flux: str = "hllc") -> dict:
@@ -306,6 +342,8 @@ def initial_primitive(spec: dict, X):
         return kh_single_ic(spec, X)
     if name == "linear_wave":
         return linear_wave_ic(spec, X)
+    if name == "riemann_2d":
+        return riemann_2d_ic(spec, X)
     if name == "smooth_random":
         return smooth_random_ic(spec, X)
     raise KeyError(name)
