@@ -56,8 +56,7 @@ extern "C" {
 #define DGSRHD_FLUX_LLF 0
 #define DGSRHD_FLUX_HLL 1
 #define DGSRHD_FLUX_HLLC 2       /* HLL with the contact restored (the relativistic HLLC of the
-                                    literature the paper cites; no reverse sweep: the VJP calls
-                                    return DGSRHD_EINVAL for it) */
+                                    literature the paper cites) */
 
 /* boundary condition per side */
 #define DGSRHD_BC_PERIODIC 0     /* both sides of an axis must be periodic together */
@@ -162,8 +161,8 @@ int32_t dgsrhd_step_host(dgsrhd_ctx* ctx, double* U_host, double dt, int32_t nst
  * extrapolation and volume term, transposed flux Jacobians and the con2prim adjoint
  * (dU/dW)^{-T}.  Non-smooth choices (the min/max wavespeed selection, the clamps of HLL, |lambda|
  * of LLF, the face guard) are frozen at their forward branch.  U_bar must not alias U or R_bar.
- * A reflecting wall contributes the mirrored adjoint of its ghost trace.  DGSRHD_EINVAL for a
- * context configured with DGSRHD_FLUX_HLLC (as for dgsrhd_stage_vjp). */
+ * A reflecting wall contributes the mirrored adjoint of its ghost trace; HLLC keeps the side of
+ * its contact and its supersonic cases at their forward choice. */
 int32_t dgsrhd_rhs_vjp(dgsrhd_ctx* ctx, const double* U, const double* R_bar, double* U_bar);
 
 /* VJP of the physicality operator with each element's factor s frozen at its forward value

@@ -688,7 +688,6 @@ Saved saved_sections(const dgsrhd_ctx* c, double* save) {
 int32_t rhs_vjp_core(dgsrhd_ctx* c, const double* U, const double* R_bar, double* U_bar,
                      const double* saved, double* Unb = nullptr, double* Ukb = nullptr,
                      double a_n = 0.0, double b_k = 0.0, double dt = 0.0) {
-  if (c->cfg.flux == DGSRHD_FLUX_HLLC) return DGSRHD_EINVAL;  // no reverse sweep of HLLC
   Saved sv = saved_sections(c, const_cast<double*>(saved));
   if (!saved) {
     StageArgs v{};

@@ -66,12 +66,13 @@ __device__ __forceinline__ void face_fwd(const Params& p, const double Wu[5],
 // lpb) -> adjoint of the face primitive (rho, u, P).
 template <int D>
 __device__ __forceinline__ void face_rev(const Params& p, const FaceFwd& f, const double Fb[5],
-                                         const double Ub[5], double lmb, double lpb, double Wb[5]) {
+                                         const double Ub[5], double lmb, double lpb, double Wb[5],
+                                         double vdb_in = 0.0, double Pb_in = 0.0) {
   const double rho = f.Wu[0], P = f.Wu[4];
   const double vd = f.v[D];
   // wavespeeds
   const double ib = lmb * (vd * f.B - f.r) + lpb * (vd * f.B + f.r);
-  double vdb = (lmb + lpb) * f.B * f.i;
+  double vdb = fma((lmb + lpb) * f.B, f.i, vdb_in);  // vdb_in, Pb_in: direct uses (HLLC)
   double Bb = (lmb + lpb) * vd * f.i - ib * f.i * f.i;
   double Ab = -ib * f.i * f.i;
   const double rb = (lpb - lmb) * f.i;
@@ -83,7 +84,7 @@ __device__ __forceinline__ void face_rev(const Params& p, const FaceFwd& f, cons
   double Db = Ub[0] + Fb[0] * vd;
   double Sb[3] = {Ub[1] + Fb[1] * vd, Ub[2] + Fb[2] * vd, Ub[3] + Fb[3] * vd};
   const double taub = Ub[4] + Fb[4] * vd;
-  double Pb = Fb[1 + D] + Fb[4] * vd;
+  double Pb = Fb[1 + D] + fma(Fb[4], vd, Pb_in);
   vdb += Fb[0] * f.U[0] + Fb[1] * f.U[1] + Fb[2] * f.U[2] + Fb[3] * f.U[3] + Fb[4] * (f.U[4] + P);
   // v_k = u_k / gamma
   double ub[3] = {0.0, 0.0, 0.0};
@@ -141,6 +142,125 @@ __device__ __forceinline__ void face_rev(const Params& p, const FaceFwd& f, cons
   Wb[4] = Pb;
 }
 
+// Reverse of hllc_flux<D> (the forward is re-evaluated here with the same formulas), with the
+// choice of the contact's side and of the supersonic cases frozen.  Outputs: adjoints of the two
+// face states' U and F, of lamL and lamR, and of the normal velocity and pressure of the side K
+// the star state is built from (vKb, PKb, left = K is the left state).
+template <int D>
+__device__ __forceinline__ void hllc_flux_vjp(const FaceFwd& L, const FaceFwd& R, double lamL,
+                                              double lamR, const double Fsb[5], double FLb[5],
+                                              double FRb[5], double ULb[5], double URb[5],
+                                              double& lamLb, double& lamRb, double& vKb,
+                                              double& PKb, bool& left) {
+#pragma unroll
+  for (int k = 0; k < 5; ++k) FLb[k] = FRb[k] = ULb[k] = URb[k] = 0.0;
+  lamLb = lamRb = vKb = PKb = 0.0;
+  left = true;
+  if (lamL >= 0.0 || lamR <= 0.0) {  // supersonic: the upwind physical flux
+    const bool useL = lamL >= 0.0;
+    left = useL;
+#pragma unroll
+    for (int k = 0; k < 5; ++k) (useL ? FLb : FRb)[k] = Fsb[k];
+    return;
+  }
+  constexpr int m = 1 + D;
+  const double idl = recip_nr(lamR - lamL), lrl = lamR * lamL;
+  auto NU = [&](int c) { return lamR * R.U[c] - lamL * L.U[c] - R.F[c] + L.F[c]; };
+  auto NF = [&](int c) { return lamR * L.F[c] - lamL * R.F[c] + lrl * (R.U[c] - L.U[c]); };
+  const double Uh0 = NU(0) * idl, Uh4 = NU(4) * idl, Uhm = NU(m) * idl;
+  const double Fh0 = NF(0) * idl, Fh4 = NF(4) * idl, Fhm = NF(m) * idl;
+  const double Eh = Uh4 + Uh0, FEh = Fh4 + Fh0, mh = Uhm, Fmh = Fhm;
+  const double b = Eh + Fmh;
+  const double sq = sqrt(fma(b, b, -4.0 * FEh * mh));
+  const double id1 = recip_nr(b + sq);
+  const double xs = 2.0 * mh * id1;
+  const double ps = fma(-xs, FEh, Fmh);
+  left = xs >= 0.0;
+  const FaceFwd& K = left ? L : R;
+  const double lam = left ? lamL : lamR, v = K.v[D], P = K.P;
+  const double lv = lam - v, di = recip_nr(lam - xs);
+  double Num[5];
+  Num[0] = K.U[0] * lv;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) Num[1 + k] = (k == D) ? K.U[m] * lv + ps - P : K.U[1 + k] * lv;
+  Num[4] = K.U[4] * lv + ps * xs - P * v;
+  // F* = F_K + lam (Num di - U_K)
+  double lamb = 0.0, dib = 0.0, lvb = 0.0, psb = 0.0, xsb = 0.0;
+  double* UKb = left ? ULb : URb;
+  double* FKb = left ? FLb : FRb;
+#pragma unroll
+  for (int k = 0; k < 5; ++k) {
+    FKb[k] += Fsb[k];
+    lamb = fma(Fsb[k], Num[k] * di - K.U[k], lamb);
+    const double Usb = lam * Fsb[k];
+    UKb[k] -= Usb;
+    dib = fma(Usb, Num[k], dib);
+    const double Nb = Usb * di;
+    UKb[k] = fma(Nb, lv, UKb[k]);
+    lvb = fma(Nb, K.U[k], lvb);
+    if (k == m) {
+      psb += Nb;
+      PKb -= Nb;
+    }
+    if (k == 4) {
+      psb = fma(Nb, xs, psb);
+      xsb = fma(Nb, ps, xsb);
+      PKb = fma(-Nb, v, PKb);
+      vKb = fma(-Nb, P, vKb);
+    }
+  }
+  // di = 1/(lam - xs)
+  lamb = fma(-dib * di, di, lamb);
+  xsb = fma(dib * di, di, xsb);
+  lamb += lvb;
+  vKb -= lvb;
+  // ps = Fmh - xs FEh
+  double Fmhb = psb, FEhb = -psb * xs;
+  xsb = fma(-psb, FEh, xsb);
+  // xs = 2 mh / (b + sq), sq = sqrt(b^2 - 4 FEh mh)
+  double mhb = 2.0 * xsb * id1;
+  const double d1b = -xsb * xs * id1;
+  double bb = d1b;
+  const double discb = 0.5 * d1b / sq;
+  bb = fma(2.0 * b, discb, bb);
+  FEhb = fma(-4.0 * mh, discb, FEhb);
+  mhb = fma(-4.0 * FEh, discb, mhb);
+  const double Ehb = bb;
+  Fmhb += bb;
+  // the HLL averages of components 0, m, 4
+  double Uhb[5] = {0.0, 0.0, 0.0, 0.0, 0.0}, Fhb[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+  Uhb[0] = Ehb;
+  Uhb[4] = Ehb;
+  Uhb[m] += mhb;
+  Fhb[0] = FEhb;
+  Fhb[4] = FEhb;
+  Fhb[m] += Fmhb;
+  double idlb = 0.0;
+#pragma unroll
+  for (int c = 0; c < 5; ++c) {
+    if (c != 0 && c != 4 && c != m) continue;
+    const double gu = Uhb[c] * idl, gf = Fhb[c] * idl;
+    URb[c] = fma(gu, lamR, URb[c]);
+    ULb[c] = fma(-gu, lamL, ULb[c]);
+    FRb[c] -= gu;
+    FLb[c] += gu;
+    lamRb = fma(gu, R.U[c], lamRb);
+    lamLb = fma(-gu, L.U[c], lamLb);
+    const double dU = R.U[c] - L.U[c];
+    FLb[c] = fma(gf, lamR, FLb[c]);
+    FRb[c] = fma(-gf, lamL, FRb[c]);
+    URb[c] = fma(gf, lrl, URb[c]);
+    ULb[c] = fma(-gf, lrl, ULb[c]);
+    lamRb = fma(gf, fma(lamL, dU, L.F[c]), lamRb);
+    lamLb = fma(gf, fma(lamR, dU, -R.F[c]), lamLb);
+    idlb = fma(Uhb[c], NU(c), fma(Fhb[c], NF(c), idlb));
+  }
+  // idl = 1/(lamR - lamL)
+  lamRb = fma(-idlb * idl, idl, lamRb);
+  lamLb = fma(idlb * idl, idl, lamLb);
+  (left ? lamLb : lamRb) += lamb;
+}
+
 // Reverse of numerical_flux<D>: Fsb -> adjoints of the left and right face primitives.
 template <int D>
 __device__ __forceinline__ void numerical_flux_vjp(const Params& p, const double WL[5],
@@ -156,7 +276,14 @@ __device__ __forceinline__ void numerical_flux_vjp(const Params& p, const double
   const double lamL = selL_from_L ? L.lm : R.lm, lamR = selR_from_L ? L.lp : R.lp;
   double FLb[5], FRb[5], ULb[5], URb[5];
   double lamLb = 0.0, lamRb = 0.0;
-  if (p.flux == 1) {
+  double vLb = 0.0, PLb = 0.0, vRb = 0.0, PRb = 0.0;  // direct uses of v_D and P (HLLC)
+  if (p.flux == 2) {
+    double vKb, PKb;
+    bool left;
+    hllc_flux_vjp<D>(L, R, lamL, lamR, Fsb, FLb, FRb, ULb, URb, lamLb, lamRb, vKb, PKb, left);
+    (left ? vLb : vRb) = vKb;
+    (left ? PLb : PRb) = PKb;
+  } else if (p.flux == 1) {
     const bool actL = lamL < 0.0, actR = lamR > 0.0;
     const double sL = actL ? lamL : 0.0, sR = actR ? lamR : 0.0;
     const double den = sR - sL;
@@ -207,8 +334,8 @@ __device__ __forceinline__ void numerical_flux_vjp(const Params& p, const double
   }
   const double lmLb = selL_from_L ? lamLb : 0.0, lmRb = selL_from_L ? 0.0 : lamLb;
   const double lpLb = selR_from_L ? lamRb : 0.0, lpRb = selR_from_L ? 0.0 : lamRb;
-  face_rev<D>(p, L, FLb, ULb, lmLb, lpLb, WLb);
-  face_rev<D>(p, R, FRb, URb, lmRb, lpRb, WRb);
+  face_rev<D>(p, L, FLb, ULb, lmLb, lpLb, WLb, vLb, PLb);
+  face_rev<D>(p, R, FRb, URb, lmRb, lpRb, WRb, vRb, PRb);
 }
 
 // ---------------------------------------------------------------------------------------

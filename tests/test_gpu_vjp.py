@@ -33,6 +33,9 @@ VJP_CASES = [
     (3, [3, 3, 2], 2, "tm", "llf", None, "iterative"),
     (2, [5, 4], 2, "ideal", "hll", [("reflect", "outflow"), ("periodic", "periodic")], "iterative"),
     (1, [8], 3, "tm", "llf", [("reflect", "reflect")], "iterative"),
+    (1, [9], 2, "ideal", "hllc", [("dirichlet", "reflect")], "iterative"),
+    (2, [5, 4], 3, "tm", "hllc", None, "iterative"),
+    (3, [3, 2, 3], 2, "ideal", "hllc", None, "iterative"),
 ]
 
 
@@ -205,18 +208,6 @@ def test_stage_vjp_with_saved_forward_equals_recompute(gpu_lib):
         s.stage_vjp(Xk, ss[k], Z, b_un, b_uk, k, dt, None)
         torch.cuda.synchronize()
         assert torch.equal(a_un, b_un) and torch.equal(a_uk, b_uk)
-
-
-def test_vjp_of_hllc_is_refused(gpu_lib):
-    """HLLC has no reverse sweep: the VJP entry points return DGSRHD_EINVAL for it."""
-    from paper_2205_00095_gb300 import _lib
-    spec = wl.smooth_random(2, [4, 4], 2, flux="hllc", seed=1)
-    s = solver(spec)
-    U = s.initial_state(wl.smooth_random_ic(spec, oracle.node_coords(spec)))
-    Rb = torch.zeros_like(U)
-    Ub = torch.zeros_like(U)
-    torch.cuda.synchronize()
-    assert s.lib.dgsrhd_rhs_vjp(s.ctx, U.data_ptr(), Rb.data_ptr(), Ub.data_ptr()) == _lib.DGSRHD_EINVAL
 
 
 def test_stage_vjp_with_the_limiter_is_refused(gpu_lib):
