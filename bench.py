@@ -311,7 +311,10 @@ def ours(args, rank, world, local_rank):
         e2e_s = time.perf_counter() - t0
         e2e_max = reduce_max_over_ranks(e2e_s, world, dev)
         e2e = {"value": job_throughput(world, ndof, args.steps, stages, 1e3 * e2e_max), "unit": UNIT,
-               "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes}
+               "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes,
+               "transfer": "dgsrhd_step_host on a pinned host state: the first kernel of each step "
+                           "reads it over the host link and the last writes it back, overlapped "
+                           "with compute"}
 
     # split-precision form on the same workload: tensor-core contractions, FP64 elsewhere
     split = None

@@ -152,8 +152,11 @@ int32_t dgsrhd_enforce(dgsrhd_ctx* ctx, double* U, double* s_out);
  * graph; later calls replay it. */
 int32_t dgsrhd_step(dgsrhd_ctx* ctx, double* U, double dt, int32_t nsteps);
 
-/* The same with a HOST state: copies U_host to the device, steps, copies back, and
- * synchronises the stream.  For pinned host memory the copies are asynchronous DMA. */
+/* The same with a HOST state, synchronising the stream at the end.  Pinned host memory that the
+ * GPU can address (an FP64 context without the limiter): the first kernel of every step reads
+ * the state from it over the host link, overlapped with its FP64 work, and keeps a device copy,
+ * and the last kernel writes the new state back; the results are those of dgsrhd_step.  Other
+ * host memory: copied to the device, stepped, copied back. */
 int32_t dgsrhd_step_host(dgsrhd_ctx* ctx, double* U_host, double dt, int32_t nsteps);
 
 /* U_bar = (dR/dU)^T R_bar for R = dgsrhd_rhs(U) (vector-Jacobian product), in FP64 whatever
@@ -174,12 +177,16 @@ int32_t dgsrhd_enforce_vjp(dgsrhd_ctx* ctx, const double* s, const double* Ut_ba
  * Uout = a_k Un + b_k (Uk + dt R(Uk)), followed (if enabled) by the physicality operator, whose
  * per-element factors go to s_out (nullable, [n_elem]).  Uout may alias Un or Uk.  Composing
  * the stages reproduces dgsrhd_step.  save (nullable, device, dgsrhd_stage_save_size doubles)
- * receives the nodal (rho, u, P) and the face traces of R(Uk) for dgsrhd_stage_vjp; a stage
+ * receives what dgsrhd_stage_vjp needs from the forward stage: the nodal (rho, u, P, gamma,
+ * 1/gamma), the face traces, the face-state tape (per face state its roots and reciprocals, A,
+ * B, K, rho (h - 1), U, r, the wavespeeds and the normal flux) and the face-guard flags; a stage
  * with save runs the FP64 kernels whatever the configured precision. */
 int32_t dgsrhd_step_stage(dgsrhd_ctx* ctx, const double* Un, const double* Uk, double* Uout,
                           int32_t stage, double dt, double* s_out, double* save);
 
-/* Doubles of the `save` buffer of dgsrhd_step_stage: 5 E Nn + 10 dim E Nt. */
+/* Doubles of the `save` buffer of dgsrhd_step_stage: 7 E Nn (nodal primitives) + 10 dim E Nt
+ * (traces) + 52 (face points) (tape) + one byte per face point of every element (guard flags),
+ * rounded up to whole doubles. */
 int32_t dgsrhd_stage_save_size(const dgsrhd_ctx* ctx, int64_t* n);
 
 /* Reverse sweep of one stage (the transpose of dgsrhd_step_stage at its input Uk, with the

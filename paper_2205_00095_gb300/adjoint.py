@@ -6,8 +6,10 @@ vector-Jacobian products.
   checkpoint every ``every`` steps from the forward pass (whose last segment is run stage by
   stage and kept whole), recomputes each earlier segment stage by stage
   (``dgsrhd_step_stage``, which also returns the physicality operator's factors and keeps the
-  nodal primitives and face traces of each stage) and runs the stages' reverse sweeps
-  (``dgsrhd_stage_vjp``, factors frozen at their forward values).
+  quantities each stage's reverse sweep needs) and runs the stages' reverse sweeps
+  (``dgsrhd_stage_vjp``, factors frozen at their forward values).  The recompute of the next
+  segment runs on a second library context and stream while the current segment's reverse
+  sweep runs on the solver's: both are FP64-bound, and blocks of the two share the SMs.
 * ``transverse_kinetic_energy(solver, U)``: J = sum over elements and nodes of
   (prod_d dx_d/2) w_node rho gamma^2 v_y^2, with ``dgsrhd_con2prim_vjp`` in its backward.
 
@@ -57,6 +59,16 @@ class _RHS(torch.autograd.Function):
 
 def rhs(solver: Solver, U: torch.Tensor) -> torch.Tensor:
     return _RHS.apply(U, solver)
+
+
+def _recompute_solver(solver: Solver) -> Solver:
+    """A second context for the same problem on its own stream (created once per solver)."""
+    aux = getattr(solver, "_recompute_aux", None)
+    if aux is None:
+        aux = Solver(solver.spec, stream=torch.cuda.Stream(device=solver.device),
+                     device=solver.device)
+        solver._recompute_aux = aux
+    return aux
 
 
 def _run_segment(solver: Solver, U: torch.Tensor, dt: float, nseg: int, stages: int, nsave: int):
@@ -112,17 +124,42 @@ class _Rollout(torch.autograd.Function):
         dt, nsteps = ctx.dt, ctx.nsteps
         stages = int(s.spec.get("rk_stages", 3))
         nsave = s.stage_save_size()
+        aux = _recompute_solver(s)
+        main = s.stream
         with _OnSolverStream(s):
             Zb = U_bar.detach().clone().contiguous()
             bounds = [c[0] for c in ctx.checkpoints] + [nsteps]
-            for seg in reversed(range(len(ctx.checkpoints))):
+            nsegs = len(ctx.checkpoints)
+
+            def recompute(seg):
+                """Queue segment seg's forward stages on the second context's stream; returns
+                its kept data and an event the main stream waits on before using it."""
                 start, U = ctx.checkpoints[seg]
-                nseg = bounds[seg + 1] - start
-                if seg == len(ctx.checkpoints) - 1 and ctx.last is not None:
+                with torch.cuda.stream(aux.stream):
+                    _, data = _run_segment(aux, U.clone(), dt, bounds[seg + 1] - start, stages,
+                                           nsave)
+                    done = torch.cuda.Event()
+                    done.record(aux.stream)
+                for lst in data:  # the main stream reads these: keep them from early reuse
+                    for row in lst:
+                        for t in row:
+                            t.record_stream(main)
+                return data, done
+
+            aux.stream.wait_stream(main)  # the checkpoints were written on the main stream
+            pending = None
+            for seg in reversed(range(nsegs)):
+                if seg == nsegs - 1 and ctx.last is not None:
                     X, S, SV = ctx.last
                     ctx.last = None
                 else:
-                    _, (X, S, SV) = _run_segment(s, U.clone(), dt, nseg, stages, nsave)
+                    if pending is None:
+                        pending = recompute(seg)
+                    (X, S, SV), done = pending
+                    main.wait_event(done)
+                # the next segment's recompute overlaps this segment's reverse sweep
+                pending = recompute(seg - 1) if seg > 0 else None
+                nseg = bounds[seg + 1] - ctx.checkpoints[seg][0]
                 # reverse sweep of the segment
                 for j in reversed(range(nseg)):
                     Unb = torch.zeros_like(Zb)

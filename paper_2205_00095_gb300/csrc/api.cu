@@ -42,9 +42,15 @@ struct dgsrhd_ctx {
   long long c2p_calls;
   long long launches;
   // captured step
-  cudaGraphExec_t gexec;
-  double g_dt;
-  double* g_U;
+  // captured steps, one per (state pointer, dt), least recently used evicted
+  struct StepGraph {
+    cudaGraphExec_t exec;
+    double dt;
+    double* U;
+    unsigned long long used;
+  };
+  std::vector<StepGraph> graphs;
+  unsigned long long graph_clock;
   // kernel timing
   bool profiling;
   struct TimedLaunch {
@@ -275,6 +281,42 @@ cudaError_t one_step(dgsrhd_ctx* c, double* U, double dt) {
   return cudaSuccess;
 }
 
+// One step of a state in device-addressable host memory Uh: the stage-1 volume kernel reads it
+// and copies it to Ud, every later read of U^n uses Ud, and the last update writes Uh.
+cudaError_t one_step_host(dgsrhd_ctx* c, double* Uh, double dt) {
+  const int ns = c->cfg.rk_stages;
+  for (int k = 0; k < ns; ++k) {
+    StageArgs a{};
+    a.op = Op::Volume;
+    a.U = (k == 0) ? Uh : c->A;
+    a.Rvol = c->Rv;
+    a.Tr = c->Tr;
+    a.Ucopy = (k == 0) ? c->Ud : nullptr;
+    cudaError_t e = run_stage(c, a);
+    if (e != cudaSuccess) return e;
+    c->c2p_calls += c->E * c->Nn;
+    StageArgs f{};
+    f.op = Op::Face;
+    f.Tr = c->Tr;
+    f.Fs = c->Fs;
+    if ((e = run_stage(c, f)) != cudaSuccess) return e;
+    StageArgs u{};
+    u.op = Op::Update;
+    u.Rvol = c->Rv;
+    u.Fs = c->Fs;
+    u.Un = c->Ud;
+    u.Uk = (k == 0) ? c->Ud : c->A;
+    u.Uout = (k == ns - 1) ? Uh : c->A;
+    u.a_n = kAn[ns - 1][k];
+    u.b_k = kBk[ns - 1][k];
+    u.dt = dt;
+    u.mode = 1;
+    u.enforce = c->cfg.enforce;
+    if ((e = run_stage(c, u)) != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
 bool valid_config(const dgsrhd_config* c) {
   if (!c) return false;
   if (c->dim < 1 || c->dim > 3) return false;
@@ -398,7 +440,7 @@ int32_t dgsrhd_create(const dgsrhd_config* cfg, void* stream, dgsrhd_ctx** out) 
   if (e == cudaSuccess) e = alloc(&c->Fs, fs_total);
   if (e == cudaSuccess && cfg->precision == DGSRHD_PREC_SPLIT) e = alloc(&c->Fref, 5LL * c->dim * E);
   if (e == cudaSuccess) e = alloc(&c->Ud, c->nstate);
-  if (e == cudaSuccess) e = alloc(&c->Wv, c->nstate);
+  if (e == cudaSuccess) e = alloc(&c->Wv, (long long)dgsrhd::kNodePrim * E * p.Nn);
   if (e == cudaSuccess) e = alloc(&c->TrB, ntr);
   if (e == cudaSuccess) e = alloc(&c->Yb, c->nstate);
   if (e == cudaSuccess) e = alloc(&c->Gd, 2LL * c->dim * E * p.Nt);
@@ -419,7 +461,7 @@ int32_t dgsrhd_create(const dgsrhd_config* cfg, void* stream, dgsrhd_ctx** out) 
 void dgsrhd_destroy(dgsrhd_ctx* c) {
   if (!c) return;
   cudaStreamSynchronize(c->stream);
-  if (c->gexec) cudaGraphExecDestroy(c->gexec);
+  for (auto& g : c->graphs) cudaGraphExecDestroy(g.exec);
   for (auto& t : c->timed) {
     cudaEventDestroy(t.start);
     cudaEventDestroy(t.stop);
@@ -442,9 +484,9 @@ void dgsrhd_destroy(dgsrhd_ctx* c) {
 
 int32_t dgsrhd_set_stream(dgsrhd_ctx* c, void* stream) {
   if (!c) return DGSRHD_EINVAL;
-  if ((cudaStream_t)stream != c->stream && c->gexec) {
-    cudaGraphExecDestroy(c->gexec);
-    c->gexec = nullptr;
+  if ((cudaStream_t)stream != c->stream) {
+    for (auto& g : c->graphs) cudaGraphExecDestroy(g.exec);
+    c->graphs.clear();
   }
   c->stream = (cudaStream_t)stream;
   return DGSRHD_OK;
@@ -529,10 +571,17 @@ int32_t dgsrhd_step(dgsrhd_ctx* c, double* U, double dt, int32_t nsteps) {
     }
     return DGSRHD_OK;
   }
-  if (!c->gexec || c->g_dt != dt || c->g_U != U) {
-    if (c->gexec) {
-      cudaGraphExecDestroy(c->gexec);
-      c->gexec = nullptr;
+  dgsrhd_ctx::StepGraph* hit = nullptr;
+  for (auto& g : c->graphs)
+    if (g.U == U && g.dt == dt) hit = &g;
+  if (!hit) {
+    constexpr size_t kMaxGraphs = 4;
+    if (c->graphs.size() == kMaxGraphs) {
+      size_t lru = 0;
+      for (size_t i = 1; i < c->graphs.size(); ++i)
+        if (c->graphs[i].used < c->graphs[lru].used) lru = i;
+      cudaGraphExecDestroy(c->graphs[lru].exec);
+      c->graphs.erase(c->graphs.begin() + lru);
     }
     cudaGraph_t g = nullptr;
     cudaError_t e = cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal);
@@ -547,17 +596,16 @@ int32_t dgsrhd_step(dgsrhd_ctx* c, double* U, double dt, int32_t nsteps) {
       cudaGetLastError();
       return DGSRHD_ECUDA;
     }
-    e = cudaGraphInstantiate(&c->gexec, g, 0);
+    cudaGraphExec_t exec = nullptr;
+    e = cudaGraphInstantiate(&exec, g, 0);
     cudaGraphDestroy(g);
-    if (e != cudaSuccess) {
-      c->gexec = nullptr;
-      return DGSRHD_ECUDA;
-    }
-    c->g_dt = dt;
-    c->g_U = U;
+    if (e != cudaSuccess) return DGSRHD_ECUDA;
+    c->graphs.push_back({exec, dt, U, 0});
+    hit = &c->graphs.back();
   }
+  hit->used = ++c->graph_clock;
   for (int s = 0; s < nsteps; ++s) {
-    cudaError_t e = cudaGraphLaunch(c->gexec, c->stream);
+    cudaError_t e = cudaGraphLaunch(hit->exec, c->stream);
     if (e != cudaSuccess) return DGSRHD_ECUDA;
   }
   c->launches += per_step * nsteps;
@@ -567,6 +615,20 @@ int32_t dgsrhd_step(dgsrhd_ctx* c, double* U, double dt, int32_t nsteps) {
 
 int32_t dgsrhd_step_host(dgsrhd_ctx* c, double* U_host, double dt, int32_t nsteps) {
   if (!c || !U_host) return DGSRHD_EINVAL;
+  // Pinned host memory that the GPU can address: the first kernel of every step reads the state
+  // from it (over the host link, overlapped with the kernel's FP64 work) and keeps a device
+  // copy; the last kernel writes the new state back to it.
+  cudaPointerAttributes at;
+  double* Uh_dev = nullptr;
+  if (cudaPointerGetAttributes(&at, U_host) == cudaSuccess && at.type == cudaMemoryTypeHost &&
+      at.devicePointer && c->cfg.precision == DGSRHD_PREC_FP64 && !c->cfg.limiter)
+    Uh_dev = static_cast<double*>(at.devicePointer);
+  cudaGetLastError();  // clears the error an unregistered pointer leaves
+  if (Uh_dev) {
+    for (int s = 0; s < nsteps; ++s)
+      if (one_step_host(c, Uh_dev, dt) != cudaSuccess) return DGSRHD_ECUDA;
+    return cuda_status(cudaStreamSynchronize(c->stream));
+  }
   const size_t bytes = sizeof(double) * c->nstate;
   if (cudaMemcpyAsync(c->Ud, U_host, bytes, cudaMemcpyHostToDevice, c->stream) != cudaSuccess)
     return DGSRHD_ECUDA;
@@ -677,7 +739,7 @@ Saved saved_sections(const dgsrhd_ctx* c, double* save) {
   Saved v{};
   if (!save) return v;
   v.W = save;
-  v.Tr = save + c->nstate;
+  v.Tr = save + (long long)dgsrhd::kNodePrim * c->E * c->Nn;
   v.tape = v.Tr + trace_doubles(c);
   v.guard = reinterpret_cast<unsigned char*>(v.tape + tape_doubles(c));
   return v;
@@ -740,7 +802,8 @@ int32_t dgsrhd_rhs_vjp(dgsrhd_ctx* c, const double* U, const double* R_bar, doub
 
 int32_t dgsrhd_stage_save_size(const dgsrhd_ctx* c, int64_t* n) {
   if (!c || !n) return DGSRHD_EINVAL;
-  *n = c->nstate + trace_doubles(c) + tape_doubles(c) + guard_doubles(c);
+  *n = (long long)dgsrhd::kNodePrim * c->E * c->Nn + trace_doubles(c) + tape_doubles(c) +
+       guard_doubles(c);
   return DGSRHD_OK;
 }
 

@@ -389,7 +389,8 @@ static __device__ __noinline__ double W_tm_brent(double xi, double eta, int max_
 // Result of one recovery.
 struct Prim {
   double rho, v[3], P;
-  double lor;  // Lorentz factor
+  double lor;   // Lorentz factor
+  double ginv;  // 1 / Lorentz factor
 };
 
 // status: 0 ok, 1 invalid input, 2 not converged / closed form failed.
@@ -479,6 +480,7 @@ __device__ __forceinline__ int con2prim(const Params& p, const double U[5], Prim
   W.rho = rho;
   W.P = P;
   W.lor = lor;
+  W.ginv = ginv;
   return conv ? 0 : 2;
 }
 
@@ -597,19 +599,21 @@ __device__ __forceinline__ void phys_flux_dir(const double U[5], const double v[
   F[1] = U[1] * vd;
   F[2] = U[2] * vd;
   F[3] = U[3] * vd;
-  F[1 + D] += P;
+  F[1 + D] = fma(U[1 + D], vd, P);  // one rounding, the same in every kernel
   F[4] = (U[4] + P) * vd;
 }
 
 // The kFaceTape values of one face state, in the order documented with kFaceTape.
-__device__ __forceinline__ void face_tape(const FaceState& c, double r, double ir, double lm,
-                                          double lp, double t[kFaceTape]) {
+__device__ __forceinline__ void face_tape(const FaceState& c, const double F[5], double r,
+                                          double ir, double lm, double lp, double t[kFaceTape]) {
   t[0] = c.ilor, t[1] = c.isg, t[2] = c.iZ, t[3] = c.id1, t[4] = c.i, t[5] = ir;
   t[6] = c.u2, t[7] = c.lor, t[8] = c.sg, t[9] = c.A, t[10] = c.B, t[11] = c.K;
   t[12] = c.rho_hm1;
 #pragma unroll
   for (int k = 0; k < 5; ++k) t[13 + k] = c.U[k];
   t[18] = r, t[19] = lm, t[20] = lp;
+#pragma unroll
+  for (int k = 0; k < 5; ++k) t[21 + k] = F[k];
 }
 
 // HLLC along axis D (the paper names the solver but prints no formula; this is the relativistic
@@ -674,8 +678,8 @@ __device__ __forceinline__ void numerical_flux(const Params& p, const double WL[
   double lmL, lpL, lmR, lpR, XL, rL, irL, XR, rR, irR;
   wavespeeds_full<D>(L, lmL, lpL, XL, rL, irL, nullptr);
   wavespeeds_full<D>(R, lmR, lpR, XR, rR, irR, nullptr);
-  face_tape(L, rL, irL, lmL, lpL, recL);
-  face_tape(R, rR, irR, lmR, lpR, recR);
+  face_tape(L, FL, rL, irL, lmL, lpL, recL);
+  face_tape(R, FR, rR, irR, lmR, lpR, recR);
   const double lamL = fmin(lmL, lmR), lamR = fmax(lpL, lpR);
   if (p.flux == 1) {
     const double sL = fmin(lamL, 0.0), sR = fmax(lamR, 0.0);

@@ -118,7 +118,7 @@ template <int DIM, int N>
 __global__ void __launch_bounds__(Shape<DIM, N>::BLOCK)
     volume_kernel(Params p, const double* __restrict__ U, double* __restrict__ Rvol,
                   double* __restrict__ Tr, double* __restrict__ Wout,
-                  unsigned char* __restrict__ guard_out) {
+                  unsigned char* __restrict__ guard_out, double* __restrict__ Ucopy) {
   using S = Shape<DIM, N>;
   constexpr int Nn = S::Nn, Nt = S::Nt, BLOCK = S::BLOCK;
   __shared__ double shF[DIM][5][BLOCK];
@@ -138,6 +138,10 @@ __global__ void __launch_bounds__(Shape<DIM, N>::BLOCK)
     double u[5];
 #pragma unroll
     for (int v = 0; v < 5; ++v) u[v] = U[v * tot + g];
+    if (Ucopy) {  // the input state, kept on the device (it may have been read from the host)
+#pragma unroll
+      for (int v = 0; v < 5; ++v) Ucopy[v * tot + g] = u[v];
+    }
     Prim W;
     status = con2prim(p, u, W, iters);
 #pragma unroll
@@ -152,9 +156,11 @@ __global__ void __launch_bounds__(Shape<DIM, N>::BLOCK)
     shW[2][tid] = W.lor * W.v[1];
     shW[3][tid] = W.lor * W.v[2];
     shW[4][tid] = W.P;
-    if (Wout) {  // the interpolated primitive (rho, u, P) kept for the vector-Jacobian product
+    if (Wout) {  // (rho, u, P, gamma, 1/gamma) kept for the vector-Jacobian product
 #pragma unroll
       for (int v = 0; v < 5; ++v) Wout[v * tot + g] = shW[v][tid];
+      Wout[5 * tot + g] = W.lor;
+      Wout[6 * tot + g] = W.ginv;
     }
   }
   block_stats(p, iters, status, shred);  // contains __syncthreads
@@ -643,7 +649,7 @@ static cudaError_t launch_stage_kernels(const StageArgs& a) {
   switch (a.op) {
     case Op::Volume:
       volume_kernel<DIM, N><<<eblocks, S::BLOCK, 0, a.stream>>>(p, a.U, a.Rvol, a.Tr, a.Wstore,
-                                                                 a.guard);
+                                                                 a.guard, a.Ucopy);
       break;
     case Op::Face: {
       long long mx = 0;

@@ -48,6 +48,8 @@ __device__ __forceinline__ void face_fwd(const Params& p, const double Wu[5],
 #pragma unroll
     for (int k = 0; k < 5; ++k) f.U[k] = t[(13 + k) * ts];
     f.r = t[18 * ts], f.lm = t[19 * ts], f.lp = t[20 * ts];
+#pragma unroll
+    for (int k = 0; k < 5; ++k) f.F[k] = t[(21 + k) * ts];
     f.q = __dadd_rn(1.0, f.u2);
     f.P = Wu[4];
     f.v[0] = Wu[1] * f.ilor;
@@ -56,10 +58,10 @@ __device__ __forceinline__ void face_fwd(const Params& p, const double Wu[5],
   } else {
     face_state_core(p, Wu, f, nullptr);
     wavespeeds_full<D>(f, f.lm, f.lp, f.X, f.r, f.ir, nullptr);
+    phys_flux_dir<D>(f.U, f.v, f.P, f.F);
   }
   f.H = __dadd_rn(Wu[0], f.rho_hm1);
   f.rhoh_lor = f.H * f.lor;
-  phys_flux_dir<D>(f.U, f.v, f.P, f.F);
 }
 
 // Reverse of face_fwd: adjoints of its outputs (flux Fb, conserved state Ub, wavespeeds lmb,
@@ -458,13 +460,11 @@ __global__ void __launch_bounds__(128) face_vjp_kernel(Params p, const double* _
 // interpolated primitive (Wub = adjoint of (rho, u, P)), return U_bar.
 template <int DIM>
 __device__ __forceinline__ void node_adjoint(const Params& p, const double U[5], const double Wu[5],
-                                             const double Fb[DIM][5], const double Wub[5],
-                                             double Ub[5]) {
+                                             double lor, double ilor, const double Fb[DIM][5],
+                                             const double Wub[5], double Ub[5]) {
   const double rho = Wu[0], P = Wu[4];
   const double u2 = fma(Wu[1], Wu[1], fma(Wu[2], Wu[2], Wu[3] * Wu[3]));
   const double q = 1.0 + u2;
-  const double ilor = rsqrt(q);
-  const double lor = q * ilor;
   const double v[3] = {Wu[1] * ilor, Wu[2] * ilor, Wu[3] * ilor};
   double Wb[5] = {Wub[0], 0.0, 0.0, 0.0, Wub[4]};  // adjoint of (rho, v, P)
   // u = gamma v: du/dv = gamma I + gamma^3 v v^T (symmetric)
@@ -555,7 +555,8 @@ __global__ void __launch_bounds__(Shape<DIM, N>::BLOCK)
     u[v] = U[v * tot + g];
     Wu[v] = Wst[v * tot + g];
   }
-  node_adjoint<DIM>(p, u, Wu, Fb, Wub, out);
+  // gamma and 1/gamma as the forward con2prim found them
+  node_adjoint<DIM>(p, u, Wu, Wst[5 * tot + g], Wst[6 * tot + g], Fb, Wub, out);
   if (!Ukb) {
 #pragma unroll
     for (int v = 0; v < 5; ++v) Ub[v * tot + g] = out[v];

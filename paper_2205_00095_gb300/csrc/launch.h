@@ -35,6 +35,7 @@ struct StageArgs {
   unsigned char* guard;  // Volume: optional face-guard flag per face point [E][NFP]; VjpNode: input
   double* tape;        // Face: optional face-state tape (roots and reciprocals); VjpFace: input
   double* means;       // Means: output, Limit: input; element means [5][E]
+  double* Ucopy;       // Volume: optional copy of the input state
   // VjpNode with Ukb set: fused stage combination Unb += a_n Rbar, Ukb += b_k (Rbar + dt Ubar)
   double* Unb;
   double* Ukb;

@@ -8,8 +8,11 @@ namespace dgsrhd {
 constexpr int kMaxN = 5;  // degree <= 4
 // Values per face state that the forward sweep can save for the reverse one: the roots and
 // reciprocals 1/gamma, 1/sigma, 1/Z, 1/(gamma + 1), 1/(A + B), 1/r (the first six), then u^2,
-// gamma, sigma, A, B, K, rho (h - 1), the conserved state U[5], r and the wavespeeds lambda-+.
-constexpr int kFaceTape = 21;
+// gamma, sigma, A, B, K, rho (h - 1), the conserved state U[5], r, the wavespeeds lambda-+ and
+// the physical flux F[5] along the face normal.
+constexpr int kFaceTape = 26;
+// Planes of the saved nodal primitive: (rho, u_x, u_y, u_z, P, gamma, 1/gamma).
+constexpr int kNodePrim = 7;
 constexpr int kFaceTapeRecips = 6;
 
 // Indices into the device counter array (unsigned long long).

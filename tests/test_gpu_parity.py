@@ -544,3 +544,25 @@ def test_riemann_2d_against_oracle(lib, test, degree, steps, tol):
     assert status == 0
     if tol < 1e-8:
         assert st["limited_cells"] == sto["limited_cells"]
+
+
+# ---------------------------------------------------------------------------------------
+# host-state stepping: pinned memory (read and written by the kernels) and pageable memory
+# (copied) give the bits of stepping the state on the device
+# ---------------------------------------------------------------------------------------
+@pytest.mark.parametrize("spec_fn", [lambda: wl.advected_wave(n=24, degree=3),
+                                     lambda: wl.kh2d(nx=8, ny=16, degree=2),
+                                     lambda: dict(wl.smooth_random(1, [33], 1, seed=2), rk_stages=1)])
+def test_step_host_paths_match_the_device_step(lib, spec_fn):
+    spec = spec_fn()
+    s = solver(spec, stream=torch.cuda.Stream())
+    U = gpu_state(s, spec)
+    dt = s.cfl_dt(0.2)
+    pinned = U.cpu().pin_memory()
+    pageable = U.cpu().clone()
+    s.step(U, dt, 3)
+    s.step_host(pinned, dt, 3)
+    s.step_host(pageable, dt, 3)
+    s.synchronize()
+    Ud = U.cpu()
+    assert torch.equal(pinned, Ud) and torch.equal(pageable, Ud)
