@@ -293,3 +293,12 @@ def enthalpy(spec: dict, rho: float, P: float) -> float:
 
 def cs2(spec: dict, rho: float, P: float) -> float:
     return float(_load().or_cs2(ctypes.byref(make_config(spec)), rho, P))
+
+
+def gamma_eq(spec: dict, rho, P):
+    """Equivalent adiabatic index Gamma_eq = (h - 1) / (h - 1 - Theta), Theta = P / rho, c = 1
+    (Sec. 2.2 and the Taub-Matthews test of Sec. 4.2, Fig. 9): Gamma for the ideal EOS; between
+    4/3 (hot) and 5/3 (cold) for Taub-Matthews.  A diagnostic; rho and P may be arrays."""
+    rho, P = np.broadcast_arrays(np.asarray(rho, dtype=np.float64), np.asarray(P, dtype=np.float64))
+    hm1 = np.vectorize(lambda r, p: enthalpy(spec, r, p) - 1.0)(rho, P)
+    return hm1 / (hm1 - P / rho)

@@ -130,8 +130,8 @@ __device__ __forceinline__ double beta_ideal_closed_form(double G, double xi, do
 // (Eqs. iterative_quartic_unknown, iterative_quartic), started from the small-xi series of
 // Eq. iterative_cubic_approximation; stop at |dw| <= 1e-14 w; for xi < 1e-4 the series.
 // The iterations run first in FP32 (FP32 issues 58x faster than FP64 on this GPU) until the
-// step is below 1e-6 w, then continue in FP64 from that iterate to the FP64 stop rule;
-// `iters` counts both phases and max_iter caps their sum.
+// step is below 1e-6 w or stops shrinking (at most 12), then continue in FP64 from that
+// iterate to the FP64 stop rule; `iters` counts both phases and max_iter caps their sum.
 __device__ __forceinline__ double w_ideal_newton(double al, double xi, double eta, int max_iter,
                                                  int& iters, bool& conv) {
   const double k1 = al * eta - 1.0;
@@ -151,14 +151,22 @@ __device__ __forceinline__ double w_ideal_newton(double al, double xi, double et
               f1 = f64_to_f32_bits(c1), f0 = f64_to_f32_bits(c0);
   float wf = fminf(fmaxf(f64_to_f32_bits(series), 1e-30f), 1.0f - 6e-8f);
   int it = 0;
-  const int max32 = max_iter - 2;  // the FP64 phase keeps at least two iterations
+  // At most 12 FP32 iterations (the FP64 phase keeps the rest, at least two).  Near |v| = 1
+  // the quartic is close to palindromic (c0 = c4, c1 ~ c3) and its root w < 1 has a partner
+  // 1/w close by; there FP32 rounding can keep the step above 1e-6 w for good, so the phase
+  // also ends once a step fails to shrink.
+  const int max32 = min(max_iter - 2, 12);
+  float dprev = 3.0e38f;
   while (it < max32) {
     const float Pw = fmaf(fmaf(fmaf(fmaf(f4, wf, f3), wf, f2), wf, f1), wf, f0);
     const float dP = fmaf(fmaf(fmaf(4.0f * f4, wf, 3.0f * f3), wf, 2.0f * f2), wf, f1);
     const float dw = Pw / dP;
+    const float adw = fabsf(dw);
     wf -= dw;
     ++it;
-    if (!(fabsf(dw) > 1e-6f * wf)) break;  // also leaves on NaN
+    if (!(adw > 1e-6f * wf)) break;  // also leaves on NaN
+    if (it > 2 && !(adw < dprev)) break;
+    dprev = adw;
   }
   double w = (wf > 0.0f && wf < 1.0f) ? f32_to_f64_bits(wf) : fmin(fmax(series, 1e-300), 1.0 - 1e-15);
   // FP64 phase; besides |dw| <= 1e-14 w it stops once the residual before the step is at the
@@ -331,7 +339,9 @@ static __device__ __noinline__ double W_tm_brent(double xi, double eta, int max_
     const float hi32 = fminf(x * x / (exm * (f64_to_f32_bits(eta) + x)) * 1.001f + 1e-30f, 39999.0f);
     const float fh32 = ff(hi32);
     if (fh32 > 0.0f) {
-      const int max32 = max_iter > 2 ? max_iter - 2 : 1;  // the FP64 phase keeps the rest
+      // the FP32 phase takes at most half the iterations: the FP64 polish or the FP64 Brent
+      // fallback keeps the rest
+      const int max32 = max_iter > 3 ? max_iter / 2 : 1;
       W32 = brent_cubic<float>(g1, g2, g3, 0.0f, hi32, g3, fh32, max32, 1.1920929e-07f, 1e-37f,
                                it32, conv32);
     }

@@ -1,6 +1,7 @@
 """The paper's Riemann problems on the GPU at the paper's resolutions (Sec. 4.2, 4.3), HLLC
-with the limiter: the 1D problems 2, 4 and 5 at p = 1 from 256 to 2048 cells against the exact
-solution (L1 errors fall; the table is printed with -s), and the three 2D problems at 256^2
+with the limiter: the 1D problems 2-5 and the Taub-Matthews blast with the three EOS of Fig. 9 at
+p = 1 from 256 to 2048 cells against the exact solution (L1 errors fall; the table is printed
+with -s), the ordering Fig. 9 shows between the three EOS, and the three 2D problems at 256^2
 to t = 0.8 (admissible throughout; the mirror-symmetric test 3 stays symmetric)."""
 import time
 
@@ -8,14 +9,19 @@ import numpy as np
 import pytest
 import torch
 
+import oracle
 import workloads as wl
 from oracle.exact_riemann import ExactRiemann
+from oracle.exact_riemann_general import GeneralExactRiemann
 
 pytestmark = pytest.mark.gpu
 
 
 def exact(spec):
     L, R, G = spec["left"], spec["right"], spec["gamma_ad"]
+    if spec["eos"] != "ideal" or L[2] != 0.0 or R[2] != 0.0:
+        return GeneralExactRiemann((L[0], L[1], L[2], L[4]), (R[0], R[1], R[2], R[4]),
+                                   spec["eos"], G, 0.5)
     if spec["bc"][0][1] == "reflect":
         return ExactRiemann((L[0], L[1], L[4]), (L[0], -L[1], L[4]), G, 1.0)
     return ExactRiemann((L[0], L[1], L[4]), (R[0], R[1], R[4]), G, 0.5)
@@ -38,11 +44,21 @@ def run(spec):
     return s, U, st, status, nsteps, el
 
 
-@pytest.mark.parametrize("problem", [2, 4, 5])
+BLAST_EOS = {"tm": ("tm", 4.0 / 3.0), "ideal4/3": ("ideal", 4.0 / 3.0),
+             "ideal5/3": ("ideal", 5.0 / 3.0)}
+
+
+def spec_of(problem, n, degree):
+    if problem in BLAST_EOS:
+        return wl.tm_blast(*BLAST_EOS[problem], n=n, degree=degree)
+    return wl.riemann_1d(problem, n=n, degree=degree)
+
+
+@pytest.mark.parametrize("problem", [2, 3, 4, 5, "tm", "ideal4/3", "ideal5/3"])
 def test_1d_riemann_problem_converges_on_the_gpu(gpu_lib, problem):
     rows = []
     for n in (256, 512, 1024, 2048):
-        spec = dict(wl.riemann_1d(problem, n=n, degree=1), limiter=True)
+        spec = dict(spec_of(problem, n, 1), limiter=True)
         s, U, st, status, nsteps, el = run(spec)
         assert st["mean_inadmissible_cells"] == 0 and st["c2p_invalid_input"] == 0
         X = s.node_coords()
@@ -50,12 +66,49 @@ def test_1d_riemann_problem_converges_on_the_gpu(gpu_lib, problem):
         w = quadrature_weights_1d(2)
         Ue = s.initial_state(exact(spec).sample(X[0], spec["t_final"])).cpu().numpy()
         l1 = (np.abs(U.cpu().numpy() - Ue) * w).sum(axis=(1, 2)) / (2 * n)
-        rows.append((n, l1[0], l1[1], l1[4], nsteps, el))
-    print(f"\nRiemann problem {problem}, p = 1, HLLC + limiter (n, L1 D, L1 S_x, L1 tau, steps, s)")
+        rows.append((n, l1[0], l1[1], l1[2], l1[4], nsteps, el))
+    print(f"\nRiemann problem {problem}, p = 1, HLLC + limiter "
+          "(n, L1 D, L1 S_x, L1 S_y, L1 tau, steps, s)")
     for r in rows:
-        print("  %5d  %.4e  %.4e  %.4e  %6d  %.2f" % r)
-    e = np.array([[r[1], r[2], r[3]] for r in rows])
+        print("  %5d  %.4e  %.4e  %.4e  %.4e  %6d  %.2f" % r)
+    e = np.array([[r[1], r[2], r[3], r[4]] for r in rows])
+    if problem in (2, 4, 5):
+        e = e[:, [0, 1, 3]]
     assert np.all(e[1:] < e[:-1])
+
+
+def test_tm_blast_ordering_of_fig9(gpu_lib):
+    """Fig. 9 at t = 0.7 on 2048 cells: the Taub-Matthews blast front lies ahead of both ideal
+    gases' (the front: the right-most node whose density exceeds twice the right state's), near
+    the exact shock, and its minimum transverse four-velocity is the lowest of the three; its
+    equivalent adiabatic index is 4/3 on the hot side and 5/3 on the cold side."""
+    front, umin = {}, {}
+    for k in BLAST_EOS:
+        spec = dict(spec_of(k, 2048, 1), limiter=True)
+        s, U, st, status, nsteps, el = run(spec)
+        assert status == 0 and st["mean_inadmissible_cells"] == 0
+        W = s.con2prim(U)
+        s.synchronize()
+        W = W.cpu().numpy()
+        x = s.node_coords()[0]
+        rho = W[0].reshape(-1)
+        front[k] = x.reshape(-1)[np.nonzero(rho > 2.0)[0].max()]
+        lor = 1.0 / np.sqrt(1.0 - (W[1:4] ** 2).sum(axis=0))
+        umin[k] = (lor * W[2]).min()
+        if k == "tm":
+            # Gamma_eq: 4/3 in the hot left state, 5/3 in the cold right one, between across
+            g = oracle.gamma_eq(spec, W[0].reshape(-1), W[4].reshape(-1))
+            xs = x.reshape(-1)
+            assert np.all((g > 4.0 / 3.0 - 1e-12) & (g < 5.0 / 3.0 + 1e-12))
+            assert np.all(np.abs(g[xs < 0.1] - 4.0 / 3.0) < 1e-3)
+            assert np.all(np.abs(g[xs > 0.95] - 5.0 / 3.0) < 1e-2)
+        # the thin shell behind the blast converges at first order in position: the front lies
+        # ahead of the exact shock by about 0.010 (5/3) and 0.007 (TM) at 2048 cells
+        ex = exact(spec)
+        assert -0.002 < front[k] - (0.5 + ex.Vs_R * spec["t_final"]) < 0.015
+    print("\nTM blast fronts at t = 0.7:", front, "min u_y:", umin)
+    assert front["tm"] > front["ideal4/3"] > front["ideal5/3"]
+    assert umin["tm"] < umin["ideal4/3"] and umin["tm"] < umin["ideal5/3"]
 
 
 @pytest.mark.parametrize("test,degree", [(1, 1), (2, 1), (3, 1), (3, 2)])

@@ -63,6 +63,30 @@ def test_backward_error(moderate_box, eos, c2p):
     assert (np.abs(Ur - U[eos]).max(axis=0) / scale).max() < tol
 
 
+@pytest.mark.parametrize("eos,G", [("ideal", 4.0 / 3.0), ("ideal", 5.0 / 3.0), ("tm", 5.0 / 3.0)])
+def test_hot_ultrarelativistic_round_trip(eos, G):
+    """Hot states near |v| = 1, gamma up to 100 and Theta from 10 to 1e3 (the states behind the
+    Taub-Matthews blast of Sec. 4.2): the iterative solver converges and recovers the primitive
+    from its exact conserved state.  rho = D / gamma is the ill-conditioned output: the root
+    w < 1 has a partner 1/w about 2/gamma away, so its rounding grows as gamma, and gamma's
+    sensitivity to w adds another factor gamma (about 20 eps gamma^2)."""
+    rng = np.random.default_rng(3)
+    n = 300
+    gam = np.exp(rng.uniform(np.log(5.0), np.log(100.0), n))
+    th = np.exp(rng.uniform(np.log(10.0), np.log(1e3), n))
+    rho = np.exp(rng.uniform(np.log(1e-2), np.log(1e2), n))
+    v = np.sqrt(1.0 - 1.0 / gam ** 2)
+    phi = rng.uniform(0.0, 2.0 * np.pi, n)
+    W = np.stack([rho, v * np.cos(phi), v * np.sin(phi), np.zeros(n), rho * th])
+    U = exact_cons(eos, G, W)
+    Wr, it, st = oracle.con2prim(spec_for(eos, "iterative", gamma_ad=G), U)
+    assert st["c2p_nonconverged"] == 0 and st["c2p_invalid_input"] == 0
+    assert vel_err(Wr, W).max() < 1e-14
+    assert (np.abs(Wr[0] - W[0]) / W[0] / gam ** 2).max() < 1e-14
+    kappa = (U[4] + np.linalg.norm(U[1:4], axis=0)) / W[4]
+    assert (np.abs(Wr[4] - W[4]) / W[4] / kappa).max() < 1e-14
+
+
 def test_solvers_agree(moderate_box):
     W, U = moderate_box
     a, _, _ = oracle.con2prim(spec_for("ideal", "analytic"), U["ideal"])

@@ -20,14 +20,17 @@ def test_taub_matthews_identity(theta):
 
 
 def test_equivalent_adiabatic_index_limits():
-    """Gamma_eq = (h - 1) / (h - 1 - Theta) runs from 5/3 (cold) to 4/3 (hot) (Sec. 2.2)."""
-    def geq(th):
-        h = oracle.enthalpy(TM, 1.0, th)
-        return (h - 1) / (h - 1 - th)
-    assert abs(geq(1e-6) - 5.0 / 3.0) < 1e-5
-    assert abs(geq(1e6) - 4.0 / 3.0) < 1e-5
-    gs = [geq(t) for t in np.logspace(-4, 4, 30)]
-    assert all(a >= b for a, b in zip(gs, gs[1:]))
+    """Gamma_eq = (h - 1) / (h - 1 - Theta) runs from 5/3 (cold) to 4/3 (hot) for the TM EOS and
+    is Gamma itself for the ideal EOS (Sec. 2.2; the diagnostic of Fig. 9)."""
+    th = np.logspace(-4, 4, 30)
+    gs = oracle.gamma_eq(TM, 1.0, th)
+    assert abs(oracle.gamma_eq(TM, 1.0, 1e-6) - 5.0 / 3.0) < 1e-5
+    assert abs(oracle.gamma_eq(TM, 1.0, 1e6) - 4.0 / 3.0) < 1e-5
+    assert np.all(np.diff(gs) <= 0.0)
+    # depends on Theta alone
+    assert np.allclose(oracle.gamma_eq(TM, 7.0, 7.0 * th), gs, rtol=1e-14, atol=0.0)
+    for G in (4.0 / 3.0, 5.0 / 3.0):
+        assert np.allclose(oracle.gamma_eq(dict(IDEAL, gamma_ad=G), 1.0, th), G, rtol=1e-12)
 
 
 @pytest.mark.parametrize("spec", [IDEAL, dict(IDEAL, gamma_ad=4.0 / 3.0), TM])

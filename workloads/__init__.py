@@ -114,6 +114,25 @@ def riemann_1d(problem: int, n: int = 128, degree: int = 1, flux: str = "hllc") 
                 left=left, right=right)
 
 
+# The blast wave with relativistic temperature on the left and a non-relativistic one on the
+# right (Sec. 4.2, the Taub-Matthews test): primitive (rho, vx, vy, vz, P), transverse velocity
+# on both sides, evolved to t = 0.7 with the Taub-Matthews EOS and the ideal EOS at 4/3 and 5/3.
+TM_BLAST = dict(left=(1.0, 0.0, 0.9, 0.0, 1e3), right=(1.0, 0.0, 0.99, 0.0, 1e-2), t_final=0.7)
+
+
+def tm_blast(eos: str = "tm", gamma_ad: float = 4.0 / 3.0, n: int = 128, degree: int = 1,
+             flux: str = "hllc") -> dict:
+    """The Taub-Matthews blast wave of Sec. 4.2 on [0, 1] with the interface at x = 0.5 and
+    Dirichlet ends; `eos` "tm" (gamma_ad unused) or "ideal" (4/3 or 5/3 in the paper); the
+    iterative con2prim, SSP-RK with p + 1 stages (at most 3), CFL 0.2."""
+    left, right = TM_BLAST["left"], TM_BLAST["right"]
+    return dict(name="riemann_1d", problem="tm_blast", dim=1, degree=degree, n_elem=[n],
+                lo=[0.0], hi=[1.0], eos=eos, gamma_ad=gamma_ad, c2p="iterative", flux=flux,
+                rk_stages=min(degree + 1, 3), bc=[("dirichlet", "dirichlet")],
+                bc_state=[[left, right]], enforce=True, cfl=0.2, t_final=TM_BLAST["t_final"],
+                left=left, right=right)
+
+
 def advected_wave(n: int = 512, degree: int = 3, flux: str = "llf", c2p: str = "default") -> dict:
     """2D advected density wave on the periodic unit square, Gamma = 4/3, SSPRK3."""
     return dict(name="advected_wave_2d", dim=2, degree=degree, n_elem=[n, n], lo=[0.0, 0.0],
