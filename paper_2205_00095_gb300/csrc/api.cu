@@ -321,8 +321,14 @@ bool valid_config(const dgsrhd_config* c) {
   if (!c) return false;
   if (c->dim < 1 || c->dim > 3) return false;
   if (c->degree < 0 || c->degree + 1 > dgsrhd::kMaxN) return false;
+  // fewer than 2^30 elements: element and face indices then fit the kernels' 32-bit division
+  long long E = 1;
   for (int d = 0; d < c->dim; ++d) {
-    if (c->n_elem[d] < 1) return false;
+    if (c->n_elem[d] < 1 || c->n_elem[d] >= (1LL << 30)) return false;
+    E *= c->n_elem[d];
+    if (E >= (1LL << 30)) return false;
+  }
+  for (int d = 0; d < c->dim; ++d) {
     if (!(c->hi[d] > c->lo[d])) return false;
     for (int s = 0; s < 2; ++s)
       if (c->bc[d][s] < 0 || c->bc[d][s] > DGSRHD_BC_REFLECT) return false;
@@ -346,6 +352,17 @@ bool valid_config(const dgsrhd_config* c) {
   if (c->limiter != 0 && c->limiter != 1) return false;
   if (c->limiter && !(c->limiter_alpha >= 0.0)) return false;
   return true;
+}
+
+// q = umulhi(x, m) >> s with s = floor(log2 d), m = ceil(2^(32+s)/d) (0 for a power of two)
+dgsrhd::FastDiv make_fastdiv(long long d) {
+  dgsrhd::FastDiv f;
+  unsigned s = 0;
+  while ((2LL << s) <= d) ++s;
+  f.s = s;
+  const unsigned long long ud = (unsigned long long)d;
+  f.m = (ud & (ud - 1)) == 0 ? 0u : (unsigned)(((1ULL << (32 + s)) + ud - 1) / ud);
+  return f;
 }
 
 template <class T>
@@ -385,6 +402,10 @@ int32_t dgsrhd_create(const dgsrhd_config* cfg, void* stream, dgsrhd_ctx** out) 
     p.inv_half_dx[d] = 2.0 / c->dx[d];
   }
   p.E = E;
+  for (int d = 0; d < 3; ++d) {
+    p.ndiv[d] = make_fastdiv(p.n[d]);
+    p.sdiv[d] = make_fastdiv(p.stride[d]);
+  }
   c->E = E;
   c->Nn = p.Nn;
   c->nstate = 5 * E * p.Nn;
@@ -957,6 +978,10 @@ bool params_from_config(const dgsrhd_config* cfg, Params* out, long long* n_trac
     p.inv_half_dx[d] = 2.0 / dx;
   }
   p.E = E;
+  for (int d = 0; d < 3; ++d) {
+    p.ndiv[d] = make_fastdiv(p.n[d]);
+    p.sdiv[d] = make_fastdiv(p.stride[d]);
+  }
   long long off = 0;
   for (int d = 0; d < 3; ++d) {
     if (d < dim) {

@@ -60,8 +60,13 @@ __device__ __forceinline__ int line_node(int d, int t, int a) {
   return d == 0 ? a + N * (t0 + N * t1) : (d == 1 ? t0 + N * (a + N * t1) : t0 + N * (t1 + N * a));
 }
 
+__device__ __forceinline__ unsigned fdiv(unsigned x, FastDiv f) {
+  return f.m ? __umulhi(x, f.m) >> f.s : x >> f.s;
+}
+
 __device__ __forceinline__ long long elem_coord(const Params& p, long long e, int d) {
-  return (e / p.stride[d]) % p.n[d];
+  const unsigned q = fdiv((unsigned)e, p.sdiv[d]);
+  return (long long)(q - fdiv(q, p.ndiv[d]) * (unsigned)p.n[d]);
 }
 
 // index of the face flux on the high side of element e along d
@@ -70,13 +75,16 @@ __device__ __forceinline__ long long high_face(const Params& p, long long e, int
   if (c < p.n[d] - 1) return e + p.stride[d];
   if (p.bc[d][1] == 0) return e - (p.n[d] - 1) * p.stride[d];
   // boundary face: enumerate the elements with c = n_d - 1 by their other coordinates
+  const unsigned ue = (unsigned)e;
   long long j;
-  if (d == 0)
-    j = e / p.n[0];
-  else if (d == 1)
-    j = (e % p.n[0]) + p.n[0] * (e / (p.n[0] * p.n[1]));
-  else
-    j = e % (p.n[0] * p.n[1]);
+  if (d == 0) {
+    j = fdiv(ue, p.ndiv[0]);
+  } else if (d == 1) {
+    const unsigned q0 = fdiv(ue, p.ndiv[0]);
+    j = (long long)(ue - q0 * (unsigned)p.n[0]) + p.n[0] * (long long)fdiv(ue, p.sdiv[2]);
+  } else {
+    j = (long long)(ue - fdiv(ue, p.sdiv[2]) * (unsigned)p.stride[2]);
+  }
   return p.E + j;
 }
 
@@ -244,12 +252,15 @@ __device__ __forceinline__ void face_point(const Params& p, const double* __rest
       eL = -1;
   } else {
     const long long j = f - p.E;
-    if (D == 0)
+    if (D == 0) {
       eL = (p.n[0] - 1) + p.n[0] * j;
-    else if (D == 1)
-      eL = (j % p.n[0]) + p.n[0] * ((p.n[1] - 1) + p.n[1] * (j / p.n[0]));
-    else
+    } else if (D == 1) {
+      const unsigned q0 = fdiv((unsigned)j, p.ndiv[0]);
+      eL = (long long)((unsigned)j - q0 * (unsigned)p.n[0]) +
+           p.n[0] * ((p.n[1] - 1) + p.n[1] * (long long)q0);
+    } else {
       eL = j + p.n[0] * p.n[1] * (p.n[2] - 1);
+    }
     eR = -1;
   }
   double WL[5], WR[5];
@@ -637,12 +648,16 @@ static cudaError_t launch_stage_kernels(const StageArgs& a) {
     if (a.op == Op::Volume) {
       const size_t smem = VolSmem<DIM, N>::TOTAL;
       cudaFuncSetAttribute(volume_kernel_split<DIM, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      volume_kernel_split<DIM, N><<<eblocks, SB, smem, a.stream>>>(p, a.U, a.Rvol, a.Tr, a.Fref);
+      // the split pair keeps R_vol as FP32 and the reference fluxes as FP32 head and tail in
+      // the FP64 buffers
+      volume_kernel_split<DIM, N><<<eblocks, SB, smem, a.stream>>>(
+          p, a.U, reinterpret_cast<float*>(a.Rvol), a.Tr, reinterpret_cast<float2*>(a.Fref));
     } else {
       const size_t smem = UpdSmem<DIM, N>::TOTAL;
       cudaFuncSetAttribute(update_kernel_split<DIM, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
       update_kernel_split<DIM, N><<<eblocks, SB, smem, a.stream>>>(
-          p, a.Rvol, a.Fs, a.Fref, a.Un, a.Uk, a.Uout, a.a_n, a.b_k, a.dt, a.mode, a.enforce, a.s_out);
+          p, reinterpret_cast<const float*>(a.Rvol), a.Fs, reinterpret_cast<const float2*>(a.Fref),
+          a.Un, a.Uk, a.Uout, a.a_n, a.b_k, a.dt, a.mode, a.enforce, a.s_out);
     }
     return cudaGetLastError();
   }

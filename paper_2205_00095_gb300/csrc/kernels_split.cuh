@@ -4,7 +4,10 @@
 // element means and the physicality operator stay in FP64.
 //
 // The contractions act on deviations from a per-element reference (the values at the element's
-// first node), formed in FP64 before the split.  The DG operator annihilates constants
+// first node).  A deviation is formed in FP32 from the FP32 heads and tails of the value and of
+// the reference (split.cuh: dev_f32), as accurate as the FP32 truncation of the exact FP64
+// difference and without an FP64 operation.  R_vol leaves the volume kernel as FP32 and the
+// update adds the FP32 lift to it before widening R to FP64 for the RK combination.  The DG operator annihilates constants
 // (summation by parts: sum_a Dhat[i][a] = phi_i(+1)/w_i - phi_i(-1)/w_i, the lift of a constant
 // flux on both faces), so with the same reference flux F_ref in the volume term and in the lift
 //   R = Dhat (F - F_ref) - lift(F* - F_ref)
@@ -39,9 +42,10 @@ struct VolSmem {
   static constexpr size_t BT = BV + sizeof(uint2) * DIM * 64;             // uint2 [8][8]
   static constexpr size_t OV = BT + sizeof(uint2) * 64;                   // float [DIM][5][BLOCK]
   static constexpr size_t OT = OV + sizeof(float) * DIM * 5 * BLOCK;      // float [DIM][2][5][LINES]
-  static constexpr size_t FR = OT + sizeof(float) * DIM * 2 * 5 * LINES;  // double [EPB][DIM][5]
-  static constexpr size_t WR = FR + sizeof(double) * Shape<DIM, N>::EPB * DIM * 5;  // double [EPB][5]
-  static constexpr size_t RED = WR + sizeof(double) * Shape<DIM, N>::EPB * 5;  // int [128]
+  static constexpr size_t FR = OT + sizeof(float) * DIM * 2 * 5 * LINES;  // F32Pair [EPB][DIM][5]
+  static constexpr size_t WR = FR + sizeof(F32Pair) * Shape<DIM, N>::EPB * DIM * 5;  // double [EPB][5]
+  static constexpr size_t WRP = WR + sizeof(double) * Shape<DIM, N>::EPB * 5;  // F32Pair [EPB][5]
+  static constexpr size_t RED = WRP + sizeof(F32Pair) * Shape<DIM, N>::EPB * 5;  // int [128]
   static constexpr size_t TOTAL = RED + sizeof(int) * 128;
 };
 
@@ -93,8 +97,8 @@ __device__ __forceinline__ void contract_tile(const uint2* __restrict__ src, con
 
 template <int DIM, int N>
 __global__ void __launch_bounds__(SplitShape<DIM, N>::BLOCK)
-    volume_kernel_split(Params p, const double* __restrict__ U, double* __restrict__ Rvol,
-                        double* __restrict__ Tr, double* __restrict__ Fref) {
+    volume_kernel_split(Params p, const double* __restrict__ U, float* __restrict__ Rvol,
+                        double* __restrict__ Tr, float2* __restrict__ Fref) {
   using S = Shape<DIM, N>;
   using Q = SplitShape<DIM, N>;
   using L = VolSmem<DIM, N>;
@@ -106,8 +110,9 @@ __global__ void __launch_bounds__(SplitShape<DIM, N>::BLOCK)
   uint2* shBT = reinterpret_cast<uint2*>(smem + L::BT);
   float* outV = reinterpret_cast<float*>(smem + L::OV);
   float* outT = reinterpret_cast<float*>(smem + L::OT);
-  double* shFR = reinterpret_cast<double*>(smem + L::FR);
+  F32Pair* shFR = reinterpret_cast<F32Pair*>(smem + L::FR);
   double* shWR = reinterpret_cast<double*>(smem + L::WR);
+  F32Pair* shWRp = reinterpret_cast<F32Pair*>(smem + L::WRP);
   int* shred = reinterpret_cast<int*>(smem + L::RED);
 
   const int tid = threadIdx.x;
@@ -143,16 +148,20 @@ __global__ void __launch_bounds__(SplitShape<DIM, N>::BLOCK)
     Wu[2] = W.lor * W.v[1];
     Wu[3] = W.lor * W.v[2];
     Wu[4] = W.P;
-    if (li == 0) {  // the element's first node is its reference
+    if (li == 0) {  // the element's first node is its reference, kept as FP32 head and tail
 #pragma unroll
       for (int d = 0; d < DIM; ++d)
 #pragma unroll
         for (int v = 0; v < 5; ++v) {
-          shFR[(le * DIM + d) * 5 + v] = F[d][v];
-          Fref[((long long)d * 5 + v) * p.E + e] = F[d][v];
+          const F32Pair r = f32_pair(F[d][v]);
+          shFR[(le * DIM + d) * 5 + v] = r;
+          Fref[((long long)d * 5 + v) * p.E + e] = make_float2(r.hi, r.lo);
         }
 #pragma unroll
-      for (int v = 0; v < 5; ++v) shWR[le * 5 + v] = Wu[v];
+      for (int v = 0; v < 5; ++v) {
+        shWR[le * 5 + v] = Wu[v];
+        shWRp[le * 5 + v] = f32_pair(Wu[v]);
+      }
     }
   }
   block_stats(p, iters, status, shred);  // contains __syncthreads
@@ -161,9 +170,11 @@ __global__ void __launch_bounds__(SplitShape<DIM, N>::BLOCK)
     for (int d = 0; d < DIM; ++d)
 #pragma unroll
       for (int v = 0; v < 5; ++v)
-        shF[(d * 5 + v) * BLOCK + tid] = as_u2(split_tf32_f64(F[d][v] - shFR[(le * DIM + d) * 5 + v]));
+        shF[(d * 5 + v) * BLOCK + tid] =
+            as_u2(split_tf32(dev_f32(f32_pair(F[d][v]), shFR[(le * DIM + d) * 5 + v])));
 #pragma unroll
-    for (int v = 0; v < 5; ++v) shW[v * BLOCK + tid] = as_u2(split_tf32_f64(Wu[v] - shWR[le * 5 + v]));
+    for (int v = 0; v < 5; ++v)
+      shW[v * BLOCK + tid] = as_u2(split_tf32(dev_f32(f32_pair(Wu[v]), shWRp[le * 5 + v])));
   } else {
 #pragma unroll
     for (int d = 0; d < DIM; ++d)
@@ -201,7 +212,7 @@ __global__ void __launch_bounds__(SplitShape<DIM, N>::BLOCK)
       float acc = 0.f;
 #pragma unroll
       for (int d = 0; d < DIM; ++d) acc += outV[(d * 5 + v) * BLOCK + tid];
-      Rvol[v * tot + g] = f32_to_f64_bits(acc);
+      Rvol[v * tot + g] = acc;  // FP32: the update adds the FP32 lift before widening
     }
     int guard = 0;
     for (int fp = li; fp < S::NFP; fp += Nn) {
@@ -212,7 +223,7 @@ __global__ void __launch_bounds__(SplitShape<DIM, N>::BLOCK)
 #pragma unroll
       for (int v = 0; v < 5; ++v)
         out[v] = shWR[le * 5 + v] + f32_to_f64_bits(outT[((d * 2 + side) * 5 + v) * LINES + le * Nt + t]);
-      if (!(out[0] > 0.0) || !(out[4] > 0.0)) {
+      if (!pos_bits(out[0]) || !pos_bits(out[4])) {
         const int node = le * Nn + line_node<DIM, N>(d, t, side ? N - 1 : 0);
 #pragma unroll
         for (int v = 0; v < 5; ++v) {
@@ -243,8 +254,8 @@ struct UpdSmem {
 
 template <int DIM, int N>
 __global__ void __launch_bounds__(SplitShape<DIM, N>::BLOCK)
-    update_kernel_split(Params p, const double* __restrict__ Rvol, const double* __restrict__ Fs,
-                        const double* __restrict__ Fref, const double* Un, const double* Uk,
+    update_kernel_split(Params p, const float* __restrict__ Rvol, const double* __restrict__ Fs,
+                        const float2* __restrict__ Fref, const double* Un, const double* Uk,
                         double* Uout, double a_n, double b_k, double dt, int mode, int enforce,
                         double* __restrict__ s_out) {
   using S = Shape<DIM, N>;
@@ -281,8 +292,9 @@ __global__ void __launch_bounds__(SplitShape<DIM, N>::BLOCK)
     uint2 val = make_uint2(0u, 0u);
     if (e < p.E) {
       const long long f = side == 0 ? e : high_face(p, e, d);
-      const double x = Fs[p.fs_off[d] + (v * p.nface[d] + f) * Nt + t] - Fref[((long long)d * 5 + v) * p.E + e];
-      val = as_u2(split_tf32_f64(x));
+      const float2 r = Fref[((long long)d * 5 + v) * p.E + e];
+      const F32Pair rp = {r.x, r.y};
+      val = as_u2(split_tf32(dev_f32(f32_pair(Fs[p.fs_off[d] + (v * p.nface[d] + f) * Nt + t]), rp)));
     }
     shFs[j] = val;
   }
@@ -336,7 +348,9 @@ __global__ void __launch_bounds__(SplitShape<DIM, N>::BLOCK)
       float lift = 0.f;
 #pragma unroll
       for (int d = 0; d < DIM; ++d) lift += outL[(d * 5 + v) * BLOCK + tid];
-      R[v] = Rvol[v * tot + g] + f32_to_f64_bits(lift);
+      // R_vol and the lift are FP32 sums of deviation products: their sum in FP32 keeps that
+      // accuracy and is widened once
+      R[v] = f32_to_f64_bits(__fadd_rn(Rvol[v * tot + g], lift));
     }
     if (mode == 0) {
 #pragma unroll

@@ -365,12 +365,15 @@ __device__ __forceinline__ void face_vjp_point(const Params& p, const double* __
       eL = -1;
   } else {
     const long long j = f - p.E;
-    if (D == 0)
+    if (D == 0) {
       eL = (p.n[0] - 1) + p.n[0] * j;
-    else if (D == 1)
-      eL = (j % p.n[0]) + p.n[0] * ((p.n[1] - 1) + p.n[1] * (j / p.n[0]));
-    else
+    } else if (D == 1) {
+      const unsigned q0 = fdiv((unsigned)j, p.ndiv[0]);
+      eL = (long long)((unsigned)j - q0 * (unsigned)p.n[0]) +
+           p.n[0] * ((p.n[1] - 1) + p.n[1] * (long long)q0);
+    } else {
       eL = j + p.n[0] * p.n[1] * (p.n[2] - 1);
+    }
     eR = -1;
   }
   const long long tot = p.E * Nn;

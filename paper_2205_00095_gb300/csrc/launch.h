@@ -14,10 +14,10 @@ struct StageArgs {
   const Params* p;
   cudaStream_t stream;
   const double* U;     // Volume: state whose RHS is formed
-  double* Rvol;        // volume term (also R of the VJP)
+  double* Rvol;        // volume term (also R of the VJP); the split kernels keep it as FP32
   double* Tr;          // face traces
   double* Fs;          // face fluxes
-  double* Fref;        // split precision: per-element reference flux [dim][5][E]
+  double* Fref;        // split precision: per-element reference flux [dim][5][E] as FP32 head and tail
   const double* Un;    // Update: U^n
   const double* Uk;    // Update: U^(k-1)
   double* Uout;        // Update: output; Enforce: state in place

@@ -29,10 +29,23 @@ enum StatSlot {
   kStatCount
 };
 
+// Division of a 32-bit index x by an invariant divisor d >= 1 without an integer division
+// instruction sequence: q = umulhi(x, m) >> s with s = floor(log2 d) and m = ceil(2^(32+s) / d)
+// (m = 0 when d is a power of two: q = x >> s).  Exact for x < 2^31: writing
+// m = 2^(32+s)/d + eps with 0 <= eps < 1, x m / 2^(32+s) = x/d + delta with
+// 0 <= delta < 2^31 / 2^(32+s) = 2^(-1-s) < 1/d, which cannot carry x/d past the next integer
+// (the method of Granlund & Montgomery, "Division by invariant integers using
+// multiplication", PLDI 1994).  Element and face indices stay below 2^31 because a
+// configuration has fewer than 2^30 elements.
+struct FastDiv {
+  unsigned m, s;
+};
+
 struct Params {
   int dim, N, Nn, Nt;        // nodes per axis, per element (N^dim), per face (N^(dim-1))
   long long n[3];            // elements per axis (1 for unused axes)
   long long stride[3];       // element index stride per axis: 1, n0, n0 n1
+  FastDiv ndiv[3], sdiv[3];  // dividers for n[d] and stride[d]
   long long E;               // elements
   long long nface[3];        // faces per axis: E (+ E/n_d boundary faces if not periodic)
   long long fs_off[3];       // offset of axis d in the face-flux buffer
