@@ -856,6 +856,7 @@ int32_t dgsrhd_step_stage(dgsrhd_ctx* c, const double* Un, const double* Uk, dou
   c->c2p_calls += c->E * c->Nn;
   StageArgs f{};
   f.op = Op::Face;
+  f.fp64_only = v.fp64_only;  // the update below reads the fluxes in the same precision
   f.Tr = v.Tr;
   f.Fs = c->Fs;
   f.tape = sv.tape;

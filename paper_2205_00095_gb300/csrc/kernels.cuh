@@ -231,10 +231,11 @@ __device__ __forceinline__ long long tape_base(const Params& p, int D) {
   return (p.fs_off[D] / 5) * (2 * kFaceTape);
 }
 
+// pairs: store each flux as its FP32 head and tail (float2, same footprint) for the split update
 template <int DIM, int N, int D, bool SAVE>
 __device__ __forceinline__ void face_point(const Params& p, const double* __restrict__ Tr,
                                            double* __restrict__ Fs, double* __restrict__ tape,
-                                           long long k) {
+                                           long long k, int pairs) {
   constexpr int Nt = Shape<DIM, N>::Nt;
   const long long nf = p.nface[D];
   if (k >= nf * Nt) return;
@@ -290,8 +291,17 @@ __device__ __forceinline__ void face_point(const Params& p, const double* __rest
   double F[5], rec[2][kFaceTape];
   numerical_flux<D>(p, WL, WR, F, rec[0], rec[1]);
   double* out = Fs + p.fs_off[D];
+  if (pairs) {
+    float2* outp = reinterpret_cast<float2*>(out);
 #pragma unroll
-  for (int v = 0; v < 5; ++v) out[(v * nf + f) * Nt + t] = F[v];
+    for (int v = 0; v < 5; ++v) {
+      const F32Pair q = f32_pair(F[v]);
+      outp[(v * nf + f) * Nt + t] = make_float2(q.hi, q.lo);
+    }
+  } else {
+#pragma unroll
+    for (int v = 0; v < 5; ++v) out[(v * nf + f) * Nt + t] = F[v];
+  }
   if (SAVE) {
     double* tp = tape + tape_base(p, D);
 #pragma unroll
@@ -303,11 +313,13 @@ __device__ __forceinline__ void face_point(const Params& p, const double* __rest
 template <int DIM, int N, bool SAVE>
 __global__ void __launch_bounds__(128) face_kernel(Params p, const double* __restrict__ Tr,
                                                    double* __restrict__ Fs,
-                                                   double* __restrict__ tape) {
+                                                   double* __restrict__ tape, int pairs) {
   const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (blockIdx.y == 0) face_point<DIM, N, 0, SAVE>(p, Tr, Fs, tape, k);
-  if (DIM > 1 && blockIdx.y == 1) face_point<DIM, N, (DIM > 1 ? 1 : 0), SAVE>(p, Tr, Fs, tape, k);
-  if (DIM > 2 && blockIdx.y == 2) face_point<DIM, N, (DIM > 2 ? 2 : 0), SAVE>(p, Tr, Fs, tape, k);
+  if (blockIdx.y == 0) face_point<DIM, N, 0, SAVE>(p, Tr, Fs, tape, k, pairs);
+  if (DIM > 1 && blockIdx.y == 1)
+    face_point<DIM, N, (DIM > 1 ? 1 : 0), SAVE>(p, Tr, Fs, tape, k, pairs);
+  if (DIM > 2 && blockIdx.y == 2)
+    face_point<DIM, N, (DIM > 2 ? 2 : 0), SAVE>(p, Tr, Fs, tape, k, pairs);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -653,10 +665,9 @@ static cudaError_t launch_stage_kernels(const StageArgs& a) {
       volume_kernel_split<DIM, N><<<eblocks, SB, smem, a.stream>>>(
           p, a.U, reinterpret_cast<float*>(a.Rvol), a.Tr, reinterpret_cast<float2*>(a.Fref));
     } else {
-      const size_t smem = UpdSmem<DIM, N>::TOTAL;
-      cudaFuncSetAttribute(update_kernel_split<DIM, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      update_kernel_split<DIM, N><<<eblocks, SB, smem, a.stream>>>(
-          p, reinterpret_cast<const float*>(a.Rvol), a.Fs, reinterpret_cast<const float2*>(a.Fref),
+      update_kernel_split<DIM, N><<<eblocks, S::BLOCK, 0, a.stream>>>(
+          p, reinterpret_cast<const float*>(a.Rvol), reinterpret_cast<const float2*>(a.Fs),
+          reinterpret_cast<const float2*>(a.Fref),
           a.Un, a.Uk, a.Uout, a.a_n, a.b_k, a.dt, a.mode, a.enforce, a.s_out);
     }
     return cudaGetLastError();
@@ -671,10 +682,11 @@ static cudaError_t launch_stage_kernels(const StageArgs& a) {
       for (int d = 0; d < DIM; ++d) mx = p.nface[d] > mx ? p.nface[d] : mx;
       const long long nthreads = mx * S::Nt;
       dim3 grid((unsigned)((nthreads + 127) / 128), DIM);
+      // the split update consumes the fluxes as FP32 head and tail
       if (a.tape)
-        face_kernel<DIM, N, true><<<grid, 128, 0, a.stream>>>(p, a.Tr, a.Fs, a.tape);
+        face_kernel<DIM, N, true><<<grid, 128, 0, a.stream>>>(p, a.Tr, a.Fs, a.tape, 0);
       else
-        face_kernel<DIM, N, false><<<grid, 128, 0, a.stream>>>(p, a.Tr, a.Fs, nullptr);
+        face_kernel<DIM, N, false><<<grid, 128, 0, a.stream>>>(p, a.Tr, a.Fs, nullptr, a.split);
       break;
     }
     case Op::Update:

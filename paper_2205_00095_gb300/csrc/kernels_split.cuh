@@ -1,20 +1,21 @@
-// Split-precision variants of the volume and update kernels: the volume term, the face-trace
-// extrapolation and the lift run on tensor cores (3xTF32, FP32 accumulation, see split.cuh);
-// con2prim, the nodal and numerical fluxes, the Lorentz factors, the RK combination, the
-// element means and the physicality operator stay in FP64.
+// Split-precision variants of the volume and update kernels.  The volume term and the
+// face-trace extrapolation run on tensor cores (3xTF32, FP32 accumulation, see split.cuh); the
+// lift, a rank-2 update per line, runs as FP32 FMAs.  con2prim, the nodal and numerical
+// fluxes, the Lorentz factors, the RK combination, the element means and the physicality
+// operator stay in FP64.
 //
 // The contractions act on deviations from a per-element reference (the values at the element's
-// first node).  A deviation is formed in FP32 from the FP32 heads and tails of the value and of
-// the reference (split.cuh: dev_f32), as accurate as the FP32 truncation of the exact FP64
-// difference and without an FP64 operation.  R_vol leaves the volume kernel as FP32 and the
-// update adds the FP32 lift to it before widening R to FP64 for the RK combination.  The DG operator annihilates constants
-// (summation by parts: sum_a Dhat[i][a] = phi_i(+1)/w_i - phi_i(-1)/w_i, the lift of a constant
-// flux on both faces), so with the same reference flux F_ref in the volume term and in the lift
+// first node).  The DG operator annihilates constants (summation by parts:
+// sum_a Dhat[i][a] = phi_i(+1)/w_i - phi_i(-1)/w_i, the lift of a constant flux on both faces),
+// so with the same reference flux F_ref in the volume term and in the lift
 //   R = Dhat (F - F_ref) - lift(F* - F_ref)
 // exactly, and the traces are W_ref + sum_i phi_i(+-1) (W_i - W_ref) (partition of unity).  The
-// TF32 parts then carry only the variation inside an element, O(dx |grad F|), instead of
-// |F| itself, which keeps the rounding of the split below the cancellation between volume and
-// surface terms.
+// FP32 and TF32 parts then carry only the variation inside an element, O(dx |grad F|), instead
+// of |F| itself, which keeps their rounding below the cancellation between volume and surface
+// terms.  A deviation is formed in FP32 from the FP32 heads and tails of the value and of the
+// reference (split.cuh: dev_f32), as accurate as the FP32 truncation of the exact FP64
+// difference and without an FP64 operation.  R_vol leaves the volume kernel as FP32 and the
+// update adds the FP32 lift to it before widening R to FP64 for the RK combination.
 #pragma once
 
 #include "kernels.cuh"
@@ -239,119 +240,60 @@ __global__ void __launch_bounds__(SplitShape<DIM, N>::BLOCK)
   }
 }
 
-// Byte offsets of the dynamic shared memory of the split update kernel.
+// Split update: R = R_vol + lift in FP32, widened once; then the SSP-RK combination and the
+// physicality operator in FP64, as in update_kernel.  The lift is a rank-2 update per line
+// (K = 2: the line's two face fluxes), far below a tensor-core tile, so it runs as FP32 FMAs on
+// the FP32 deviations F* - F_ref (exact products and one rounding each: at least the accuracy
+// of the 3xTF32 products).  The face fluxes arrive as FP32 head and tail (face_kernel with
+// pairs), the reference fluxes likewise (volume_kernel_split).
 template <int DIM, int N>
-struct UpdSmem {
-  using Q = SplitShape<DIM, N>;
-  static constexpr int BLOCK = Q::BLOCK;
-  using Enf = EnforceShared<DIM, N, BLOCK>;
-  static constexpr size_t E = 0;                                         // Enf
-  static constexpr size_t BL = (sizeof(Enf) + 15) / 16 * 16;             // uint2 [DIM][8][8]
-  static constexpr size_t OL = BL + sizeof(uint2) * DIM * 64;            // float [DIM][5][BLOCK]
-  static constexpr size_t FS = OL + sizeof(float) * DIM * 5 * BLOCK;     // uint2 [DIM][2][5][LINES]
-  static constexpr size_t TOTAL = FS + sizeof(uint2) * DIM * 2 * 5 * Q::LINES;
-};
-
-template <int DIM, int N>
-__global__ void __launch_bounds__(SplitShape<DIM, N>::BLOCK)
-    update_kernel_split(Params p, const float* __restrict__ Rvol, const double* __restrict__ Fs,
+__global__ void __launch_bounds__(Shape<DIM, N>::BLOCK)
+    update_kernel_split(Params p, const float* __restrict__ Rvol, const float2* __restrict__ Fs,
                         const float2* __restrict__ Fref, const double* Un, const double* Uk,
                         double* Uout, double a_n, double b_k, double dt, int mode, int enforce,
                         double* __restrict__ s_out) {
   using S = Shape<DIM, N>;
-  using Q = SplitShape<DIM, N>;
-  using L = UpdSmem<DIM, N>;
-  constexpr int Nn = S::Nn, Nt = S::Nt, BLOCK = Q::BLOCK, LINES = Q::LINES;
-  extern __shared__ __align__(16) unsigned char smem[];
-  typename L::Enf& sh = *reinterpret_cast<typename L::Enf*>(smem + L::E);
-  uint2* shBL = reinterpret_cast<uint2*>(smem + L::BL);
-  float* outL = reinterpret_cast<float*>(smem + L::OL);
-  uint2* shFs = reinterpret_cast<uint2*>(smem + L::FS);
+  constexpr int Nn = S::Nn;
+  __shared__ EnforceShared<DIM, N> sh;
+  __shared__ float shl[DIM][2][N];  // (2/dx_d) phi_i(-+1)/w_i per axis, rounded to FP32
   const int tid = threadIdx.x;
-  // lift coefficients B[k][n]: k = 0 low-face flux (+ (2/dx) phi_n(-1)/w_n),
-  // k = 1 high-face flux (- (2/dx) phi_n(+1)/w_n)
-  for (int j = tid; j < DIM * 64; j += BLOCK) {
-    const int d = j / 64, k = (j / 8) % 8, n = j % 8;
-    double v = 0.0;
-    if (n < N && k == 0) v = p.inv_half_dx[d] * p.lm[n];
-    if (n < N && k == 1) v = -p.inv_half_dx[d] * p.lp[n];
-    shBL[j] = as_u2(split_tf32_f64(v));
+  if (tid < DIM * N) {
+    const int d = tid / N, i = tid % N;
+    shl[d][0][i] = f64_to_f32_bits(p.inv_half_dx[d] * p.lm[i]);
+    shl[d][1][i] = f64_to_f32_bits(p.inv_half_dx[d] * p.lp[i]);
   }
   __syncthreads();
-
-  // stage the block's face fluxes minus the reference flux, TF32-split, in shared memory:
-  // shFs[d][side][v][line], side 0 = low face, 1 = high face; lines run fastest so that
-  // consecutive threads read consecutive face points
-  for (int j = tid; j < DIM * 2 * 5 * LINES; j += BLOCK) {
-    const int r = j % LINES;
-    const int v = (j / LINES) % 5;
-    const int side = (j / (5 * LINES)) % 2;
-    const int d = j / (10 * LINES);
-    const int lr = r / Nt, t = r - lr * Nt;
-    const long long e = (long long)blockIdx.x * S::EPB + lr;
-    uint2 val = make_uint2(0u, 0u);
-    if (e < p.E) {
-      const long long f = side == 0 ? e : high_face(p, e, d);
-      const float2 r = Fref[((long long)d * 5 + v) * p.E + e];
-      const F32Pair rp = {r.x, r.y};
-      val = as_u2(split_tf32(dev_f32(f32_pair(Fs[p.fs_off[d] + (v * p.nface[d] + f) * Nt + t]), rp)));
-    }
-    shFs[j] = val;
-  }
-  __syncthreads();
-
-  // lift on tensor cores: rows are the block's lines, k selects the low / high face flux
-  const int warp = tid >> 5, lane = tid & 31, gq = lane >> 2, tig = lane & 3;
-  constexpr int TASKS = DIM * 5 * Q::TILES;
-  for (int task = warp; task < TASKS; task += Q::WARPS) {
-    const int d = task / (5 * Q::TILES), v = (task / Q::TILES) % 5, tile = task % Q::TILES;
-    unsigned ahi[4] = {0u, 0u, 0u, 0u}, alo[4] = {0u, 0u, 0u, 0u};
-    if (tig < 2) {  // k = tig in {0, 1}; k = tig + 4 is padding
-#pragma unroll
-      for (int rr = 0; rr < 2; ++rr) {
-        const int r = tile * 16 + gq + 8 * rr;
-        if (r < LINES) {
-          const uint2 q = shFs[((d * 2 + tig) * 5 + v) * LINES + r];
-          ahi[rr] = q.x;
-          alo[rr] = q.y;
-        }
-      }
-    }
-    const uint2 b0 = shBL[d * 64 + tig * 8 + gq], b1 = shBL[d * 64 + (tig + 4) * 8 + gq];
-    const unsigned bhi[2] = {b0.x, b1.x}, blo[2] = {b0.y, b1.y};
-    float c[4] = {0.f, 0.f, 0.f, 0.f};
-    mma_3xtf32(c, ahi, alo, bhi, blo);
-    const int rows[2] = {tile * 16 + gq, tile * 16 + gq + 8};
-#pragma unroll
-    for (int rr = 0; rr < 2; ++rr)
-#pragma unroll
-      for (int cc = 0; cc < 2; ++cc) {
-        const int r = rows[rr], n = 2 * tig + cc;
-        if (r < LINES && n < N) {
-          const int lr = r / Nt, t = r - lr * Nt;
-          outL[(d * 5 + v) * BLOCK + lr * Nn + line_node<DIM, N>(d, t, n)] = c[rr * 2 + cc];
-        }
-      }
-  }
-  __syncthreads();
-
   const int le = tid / Nn, li = tid - le * Nn;
   const long long e = (long long)blockIdx.x * S::EPB + le;
-  const bool valid = tid < S::BLOCK && e < p.E;
+  const bool valid = e < p.E;
   const long long tot = p.E * Nn;
   const long long g = e * Nn + li;
   double u[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
   if (valid) {
+    int ijk[3];
+    node_ijk<DIM, N>(li, ijk);
+    float lift[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) {
+      const int t = tan_index<DIM, N>(ijk, d);
+      const long long nf = p.nface[d];
+      const float2* fs = Fs + p.fs_off[d];
+      const long long flo = e, fhi = high_face(p, e, d);
+      const float cp = shl[d][1][ijk[d]];
+      const float cm = shl[d][0][ijk[d]];
+#pragma unroll
+      for (int v = 0; v < 5; ++v) {
+        const float2 r = Fref[((long long)d * 5 + v) * p.E + e];
+        const float2 xh = fs[(v * nf + fhi) * S::Nt + t];
+        const float2 xl = fs[(v * nf + flo) * S::Nt + t];
+        const F32Pair rp{r.x, r.y};
+        lift[v] = fmaf(cm, dev_f32(F32Pair{xl.x, xl.y}, rp), lift[v]);
+        lift[v] = fmaf(-cp, dev_f32(F32Pair{xh.x, xh.y}, rp), lift[v]);
+      }
+    }
     double R[5];
 #pragma unroll
-    for (int v = 0; v < 5; ++v) {
-      float lift = 0.f;
-#pragma unroll
-      for (int d = 0; d < DIM; ++d) lift += outL[(d * 5 + v) * BLOCK + tid];
-      // R_vol and the lift are FP32 sums of deviation products: their sum in FP32 keeps that
-      // accuracy and is widened once
-      R[v] = f32_to_f64_bits(__fadd_rn(Rvol[v * tot + g], lift));
-    }
+    for (int v = 0; v < 5; ++v) R[v] = f32_to_f64_bits(__fadd_rn(Rvol[v * tot + g], lift[v]));
     if (mode == 0) {
 #pragma unroll
       for (int v = 0; v < 5; ++v) Uout[v * tot + g] = R[v];
@@ -359,13 +301,12 @@ __global__ void __launch_bounds__(SplitShape<DIM, N>::BLOCK)
 #pragma unroll
       for (int v = 0; v < 5; ++v) {
         const double x = fma(dt, R[v], Uk[v * tot + g]);
-        u[v] = (a_n != 0.0) ? fma(a_n, Un[v * tot + g], b_k * x) : b_k * x;
+        u[v] = (a_n != 0.0) ? fma(a_n, Un[v * tot + g], b_k * x) : (b_k == 1.0 ? x : b_k * x);
       }
     }
   }
-  if (mode == 0) return;
-  // enforce_block expects le/li of the FP64 layout; threads past S::BLOCK carry no node
-  if (enforce) enforce_block(p, u, valid, valid ? le : 0, valid ? li : 1, e, s_out, sh);
+  if (mode == 0) return;  // uniform over the grid
+  if (enforce) enforce_block(p, u, valid, le, li, e, s_out, sh);
   if (valid) {
 #pragma unroll
     for (int v = 0; v < 5; ++v) Uout[v * tot + g] = u[v];

@@ -16,7 +16,7 @@ struct StageArgs {
   const double* U;     // Volume: state whose RHS is formed
   double* Rvol;        // volume term (also R of the VJP); the split kernels keep it as FP32
   double* Tr;          // face traces
-  double* Fs;          // face fluxes
+  double* Fs;          // face fluxes (the split face/update pair: FP32 head and tail)
   double* Fref;        // split precision: per-element reference flux [dim][5][E] as FP32 head and tail
   const double* Un;    // Update: U^n
   const double* Uk;    // Update: U^(k-1)

@@ -35,33 +35,6 @@ __device__ __forceinline__ Tf32Pair split_tf32(float x) {
 
 __device__ __forceinline__ Tf32Pair split_tf32_f64(double x) { return split_tf32(f64_to_f32_bits(x)); }
 
-// x minus its FP32 truncation (f64_to_f32_bits keeps the top 23 of the 52 mantissa bits), as an
-// FP32 truncated to 24 significant bits, from the bit pattern alone: the low 29 mantissa bits,
-// normalised.  Zero when they are zero, for zeros, subnormals, infinities and NaNs, and where
-// the part falls below the FP32-normal range.
-__device__ __forceinline__ float f64_lo_f32_bits(double x) {
-  const int hw = __double2hiint(x);
-  const unsigned rem = (unsigned)__double2loint(x) & 0x1fffffffu;
-  const int e = (hw >> 20) & 0x7ff;
-  const int lz = __clz(rem);                  // 3..32; the leading one of rem at bit 31 - lz
-  const int ef = e - 917 - lz;                // FP32 biased exponent of that leading one
-  const unsigned mant = ((rem << (lz & 31)) >> 8) & 0x7fffffu;
-  const unsigned bits = ((unsigned)hw & 0x80000000u) | ((unsigned)ef << 23) | mant;
-  return (rem == 0u || e == 0x7ff || ef <= 0) ? 0.0f : __uint_as_float(bits);
-}
-
-// FP32 head and tail of an FP64 value (integer operations only)
-struct F32Pair {
-  float hi, lo;
-};
-
-__device__ __forceinline__ F32Pair f32_pair(double x) {
-  F32Pair q;
-  q.hi = f64_to_f32_bits(x);
-  q.lo = f64_lo_f32_bits(x);
-  return q;
-}
-
 // x - r in FP32 from the pairs: (x_hi - r_hi) + (x_lo - r_lo).  The head difference is exact
 // when x_hi and r_hi lie within a factor 2 of each other (Sterbenz) and within 2^-24 of itself
 // otherwise, so the result is within about 2^-23 of x - r, the accuracy of the FP32 truncation
