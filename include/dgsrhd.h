@@ -79,7 +79,7 @@ extern "C" {
 typedef struct dgsrhd_config {
   int32_t dim;                 /* 1, 2 or 3 */
   int32_t degree;              /* p in 0..4 (1..4 for Gauss-Lobatto); N = p + 1 nodes per axis */
-  int64_t n_elem[3];           /* elements per axis (unused axes: 1) */
+  int64_t n_elem[3];           /* elements per axis (unused axes: 1); fewer than 2^30 in total */
   double lo[3], hi[3];         /* domain box */
   int32_t eos;                 /* DGSRHD_EOS_* */
   double gamma_ad;             /* adiabatic index of the ideal EOS (ignored for TM) */

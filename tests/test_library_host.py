@@ -54,6 +54,9 @@ def base_spec():
     dict(bc=[("dirichlet", "outflow"), ("periodic", "periodic")],
          bc_state=[[(1.0, 1.2, 0.0, 0.0, 1.0), (1.0, 0.0, 0.0, 0.0, 1.0)]] * 2),
     dict(lo=[1.0, 0.0], hi=[0.0, 1.0]),
+    # 2^30 elements or more: the kernels divide element and face indices in 32 bits
+    dict(n_elem=[1 << 15, 1 << 15]), dict(dim=1, n_elem=[1 << 30]),
+    dict(dim=3, n_elem=[1 << 10, 1 << 10, 1 << 10]),
 ])
 def test_invalid_configuration_rejected_on_host(lib, bad):
     spec = base_spec()
