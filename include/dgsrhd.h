@@ -72,6 +72,16 @@ extern "C" {
 #define DGSRHD_NODES_GL 0
 #define DGSRHD_NODES_GLL 1
 
+/* limiter after every RK stage, before the physicality operator (Sec. 2.3 names the limiters of
+ * Moe et al. and the minmod limiter, printing neither); both scale each element toward its mean
+ * by one factor theta, so admissible nodes stay admissible and the mean is kept */
+#define DGSRHD_LIMITER_NONE 0
+#define DGSRHD_LIMITER_SCALING 1 /* theta keeps nodal and face values within the face
+                                    neighbours' means widened by limiter_alpha h^(3/2) */
+#define DGSRHD_LIMITER_MINMOD 2  /* theta keeps every face-mean deviation within the minmod bound
+                                    of the neighbour-mean differences; deviations below
+                                    limiter_alpha h^2 (the TVB constant M) are left alone */
+
 /* arithmetic of the basis contractions */
 #define DGSRHD_PREC_FP64 0
 #define DGSRHD_PREC_SPLIT 1      /* split-precision tensor-core contractions, FP64 elsewhere */
@@ -92,8 +102,9 @@ typedef struct dgsrhd_config {
   int32_t enforce;             /* 1: physicality operator after every RK stage */
   int32_t precision;           /* DGSRHD_PREC_* */
   int32_t nodes;               /* DGSRHD_NODES_*: node family of the collocated basis */
-  int32_t limiter;             /* 1: scaling limiter after every RK stage, before the operator */
-  double limiter_alpha;        /* limiter bound relaxation: alpha = limiter_alpha h^(3/2) */
+  int32_t limiter;             /* DGSRHD_LIMITER_* */
+  double limiter_alpha;        /* scaling: bound relaxation limiter_alpha h^(3/2); minmod: TVB
+                                  constant M, threshold M h^2 (h the smallest element width) */
 } dgsrhd_config;
 
 typedef struct dgsrhd_stats {

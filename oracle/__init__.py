@@ -87,6 +87,15 @@ def _enum(table, v):
     return v if isinstance(v, (int, np.integer)) else table[v]
 
 
+def _limiter(v) -> int:
+    """False / None: none; True or "moe": the scaling limiter; "minmod": the minmod limiter."""
+    if v is None:
+        return 0
+    if isinstance(v, str):
+        return {"none": 0, "moe": 1, "scaling": 1, "minmod": 2}[v]
+    return int(v)
+
+
 def make_config(spec: dict) -> Config:
     """Problem description (plain dict, see ``workloads``) -> oracle struct."""
     c = Config()
@@ -117,7 +126,7 @@ def make_config(spec: dict) -> Config:
                     c.bc_state[d][s][v] = float(bcs[d][s][v])
     c.enforce = int(bool(spec.get("enforce", True)))
     c.nodes = _enum(_NODES, spec.get("nodes", "gl"))
-    c.limiter = int(bool(spec.get("limiter", False)))
+    c.limiter = _limiter(spec.get("limiter", False))
     c.limiter_alpha = float(spec.get("limiter_alpha", 50.0))
     return c
 

@@ -44,8 +44,8 @@ typedef struct {
   double bc_state[3][2][5]; /* Dirichlet primitive (rho, vx, vy, vz, P) */
   int32_t enforce;        /* physicality operator after every stage */
   int32_t nodes;          /* 0 Gauss-Legendre, 1 Gauss-Lobatto-Legendre (degree >= 1) */
-  int32_t limiter;        /* 1: scaling limiter after every stage, before the operator */
-  double limiter_alpha;   /* bound relaxation alpha = limiter_alpha h^(3/2) */
+  int32_t limiter;        /* after every stage, before the operator: 1 scaling, 2 minmod */
+  double limiter_alpha;   /* 1: bound relaxation limiter_alpha h^(3/2); 2: TVB constant M (M h^2) */
 } or_config;
 
 typedef struct {
@@ -1086,6 +1086,114 @@ static void limit_all(const or_config *c, const mesh *m, double *U, or_stats *st
   free(mean);
 }
 
+/* ------------------------------------------------------------------------ */
+/* Minmod limiter (reading: Sec. 2.3 names the minmod limiter after van      */
+/* Leer but prints no formula).  The minmod bound of Cockburn and Shu on the */
+/* face deviations, applied through one factor per element so that every    */
+/* node stays a convex combination of itself and the element mean (applied  */
+/* to each conserved variable's slope on its own, it lost admissible means   */
+/* on every strong blast of Sec. 4.2 at p = 1).  For element e, conserved q  */
+/* and axis d:                                                                */
+/*   ub   the element's quadrature mean of q,                                */
+/*   a+_d = (quadrature mean of q's trace on the +d face) - ub,              */
+/*   a-_d = ub - (the same on the -d face),                                  */
+/*   D+_d = ub(+d neighbour) - ub, D-_d = ub - ub(-d neighbour)              */
+/*          (a non-periodic boundary contributes no difference),             */
+/*   mm(x, D+, D-) = x if |x| <= M h^2 + 2^-40 (|ub_D| + |ub_tau|) (h the    */
+/*          smallest dx: the TVB threshold, plus a floor at the rounding of  */
+/*          the element's energy scale, which bounds |S| as well),           */
+/*          else s min(|x|, |D+|, |D-|) if all share the sign s, else 0;     */
+/* theta = min(1, mm(a, D+_d, D-_d) / a over q, d and a in {a+_d, a-_d});    */
+/* U_i <- ub + theta (U_i - ub).  The mean is kept; linear data pass         */
+/* untouched; an element holding a strict extremum is flattened (theta = 0). */
+/* ------------------------------------------------------------------------ */
+static double minmod3(double x, const double *D, int nD, double thr) {
+  if (fabs(x) <= thr) return x;
+  double mag = fabs(x);
+  for (int k = 0; k < nD; ++k) {
+    if ((D[k] > 0.0) != (x > 0.0) || D[k] == 0.0) return 0.0;
+    mag = fmin(mag, fabs(D[k]));
+  }
+  return x > 0.0 ? mag : -mag;
+}
+
+static void minmod_all(const or_config *c, const mesh *m, double *U, or_stats *st) {
+  const int64_t tot = m->E * m->Nn;
+  double wsum = 0.0, h = 1e300;
+  for (int i = 0; i < m->Nn; ++i) wsum += node_weight(m, i);
+  for (int d = 0; d < m->dim; ++d) h = fmin(h, m->dx[d]);
+  const double thr = c->limiter_alpha * h * h;
+  double *mean = (double *)malloc(sizeof(double) * 5 * (size_t)m->E);
+  if (!mean) return;
+  for (int64_t e = 0; e < m->E; ++e)
+    for (int v = 0; v < 5; ++v) {
+      double acc = 0.0;
+      for (int i = 0; i < m->Nn; ++i) acc += node_weight(m, i) * U[v * tot + e * m->Nn + i];
+      mean[v * m->E + e] = acc / wsum;
+    }
+  int Nt = 1;
+  for (int d = 0; d < m->dim - 1; ++d) Nt *= m->N;
+  const double face_wsum = wsum / 2.0; /* the tangential weights sum to 2^(dim-1) */
+  for (int64_t e = 0; e < m->E; ++e) {
+    int64_t ec[3];
+    elem_coords(m, e, ec);
+    const double thr_e = thr + 0x1p-40 * (fabs(mean[e]) + fabs(mean[4 * m->E + e]));
+    double theta = 1.0;
+    for (int v = 0; v < 5; ++v) {
+      const double *q = &U[v * tot + e * m->Nn];
+      const double ub = mean[v * m->E + e];
+      for (int d = 0; d < m->dim; ++d) {
+        double D[2];
+        int nD = 0;
+        for (int side = 1; side >= 0; --side) {
+          int64_t nc[3] = {ec[0], ec[1], ec[2]};
+          nc[d] += side ? 1 : -1;
+          if (nc[d] < 0 || nc[d] >= m->n[d]) {
+            if (c->bc[d][side] != 0) continue;
+            nc[d] = (nc[d] + m->n[d]) % m->n[d];
+          }
+          const double un = mean[v * m->E + elem_index(m, nc)];
+          D[nD++] = side ? un - ub : ub - un;
+        }
+        double fm[2] = {0.0, 0.0};
+        for (int side = 0; side < 2; ++side)
+          for (int t = 0; t < Nt; ++t) {
+            int ijk[3] = {0, 0, 0}, rem = t;
+            double wt = 1.0;
+            for (int dd = 0; dd < m->dim; ++dd) {
+              if (dd == d) continue;
+              ijk[dd] = rem % m->N;
+              rem /= m->N;
+              wt *= m->w[ijk[dd]];
+            }
+            double tr = 0.0;
+            for (int a = 0; a < m->N; ++a) {
+              ijk[d] = a;
+              tr += (side ? m->ep[a] : m->em[a]) * q[node_index(m, ijk)];
+            }
+            fm[side] += wt * tr;
+          }
+        const double dev[2] = {fm[1] / face_wsum - ub, ub - fm[0] / face_wsum};
+        for (int k = 0; k < 2; ++k) {
+          const double mmv = minmod3(dev[k], D, nD, thr_e);
+          if (mmv != dev[k]) theta = fmin(theta, mmv / dev[k]);
+        }
+      }
+    }
+    if (theta < 1.0) {
+      if (st) st->limited_cells += 1;
+      for (int v = 0; v < 5; ++v) {
+        const double ub = mean[v * m->E + e];
+        for (int i = 0; i < m->Nn; ++i) {
+          double *q = &U[v * tot + e * m->Nn + i];
+          *q = ub + theta * (*q - ub);
+        }
+      }
+    }
+  }
+  free(mean);
+}
+
 int or_step(const or_config *c, double *U, double dt, int nsteps, or_stats *st) {
   mesh m;
   if (mesh_init(c, &m)) return 1;
@@ -1106,7 +1214,8 @@ int or_step(const or_config *c, double *U, double dt, int nsteps, or_stats *st) 
       if (rc) { free(U0); free(Uk); free(R); return rc; }
       double a = a_n[ns - 1][k], b = b_k[ns - 1][k];
       for (int64_t j = 0; j < n; ++j) Uk[j] = a * U0[j] + b * (Uk[j] + dt * R[j]);
-      if (c->limiter) limit_all(c, &m, Uk, st);
+      if (c->limiter == 1) limit_all(c, &m, Uk, st);
+      if (c->limiter == 2) minmod_all(c, &m, Uk, st);
       if (c->enforce) or_enforce(c, Uk, NULL, st);
     }
     memcpy(U, Uk, sizeof(double) * n);

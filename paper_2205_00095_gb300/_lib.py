@@ -132,6 +132,18 @@ def _enum(table, v):
     return int(v) if isinstance(v, int) else table[v]
 
 
+LIMITER = {"none": 0, "moe": 1, "scaling": 1, "minmod": 2}
+
+
+def _limiter(v) -> int:
+    """False / None: none; True or "moe": the scaling limiter; "minmod": the minmod limiter."""
+    if v is None:
+        return 0
+    if isinstance(v, str):
+        return LIMITER[v]
+    return int(v)
+
+
 def make_config(spec: dict) -> dgsrhd_config:
     """Problem description (plain dict) -> dgsrhd_config."""
     c = dgsrhd_config()
@@ -163,7 +175,7 @@ def make_config(spec: dict) -> dgsrhd_config:
     c.enforce = int(bool(spec.get("enforce", True)))
     c.precision = _enum(PRECISION, spec.get("precision", "fp64"))
     c.nodes = _enum(NODES, spec.get("nodes", "gl"))
-    c.limiter = int(bool(spec.get("limiter", False)))
+    c.limiter = _limiter(spec.get("limiter", False))
     c.limiter_alpha = float(spec.get("limiter_alpha", 50.0))
     return c
 

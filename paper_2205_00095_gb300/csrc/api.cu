@@ -349,7 +349,7 @@ bool valid_config(const dgsrhd_config* c) {
   if (c->precision != DGSRHD_PREC_FP64 && c->precision != DGSRHD_PREC_SPLIT) return false;
   if (c->nodes != DGSRHD_NODES_GL && c->nodes != DGSRHD_NODES_GLL) return false;
   if (c->nodes == DGSRHD_NODES_GLL && c->degree < 1) return false;
-  if (c->limiter != 0 && c->limiter != 1) return false;
+  if (c->limiter < DGSRHD_LIMITER_NONE || c->limiter > DGSRHD_LIMITER_MINMOD) return false;
   if (c->limiter && !(c->limiter_alpha >= 0.0)) return false;
   return true;
 }
@@ -440,7 +440,10 @@ int32_t dgsrhd_create(const dgsrhd_config* cfg, void* stream, dgsrhd_ctx** out) 
     double h = 1e300;
     for (int d = 0; d < cfg->dim; ++d) h = fmin(h, (cfg->hi[d] - cfg->lo[d]) / (double)cfg->n_elem[d]);
     p.limiter = cfg->limiter;
-    p.lim_alpha = cfg->limiter ? cfg->limiter_alpha * pow(h, 1.5) : 0.0;
+    // scaling limiter: bound relaxation alpha h^(3/2); minmod: TVB threshold M h^2
+    p.lim_alpha = cfg->limiter == DGSRHD_LIMITER_SCALING  ? cfg->limiter_alpha * pow(h, 1.5)
+                  : cfg->limiter == DGSRHD_LIMITER_MINMOD ? cfg->limiter_alpha * h * h
+                                                          : 0.0;
   }
   if (cfg->nodes == DGSRHD_NODES_GLL)
     gauss_lobatto(N, c->x, p.w);
@@ -1010,7 +1013,10 @@ bool params_from_config(const dgsrhd_config* cfg, Params* out, long long* n_trac
     double h = 1e300;
     for (int d = 0; d < cfg->dim; ++d) h = fmin(h, (cfg->hi[d] - cfg->lo[d]) / (double)cfg->n_elem[d]);
     p.limiter = cfg->limiter;
-    p.lim_alpha = cfg->limiter ? cfg->limiter_alpha * pow(h, 1.5) : 0.0;
+    // scaling limiter: bound relaxation alpha h^(3/2); minmod: TVB threshold M h^2
+    p.lim_alpha = cfg->limiter == DGSRHD_LIMITER_SCALING  ? cfg->limiter_alpha * pow(h, 1.5)
+                  : cfg->limiter == DGSRHD_LIMITER_MINMOD ? cfg->limiter_alpha * h * h
+                                                          : 0.0;
   }
   double x[kMaxN];
   if (cfg->nodes == DGSRHD_NODES_GLL)

@@ -508,14 +508,29 @@ __global__ void __launch_bounds__(Shape<DIM, N>::BLOCK)
 }
 
 // ---------------------------------------------------------------------------------------
-// Slope limiter (reading: a scaling limiter of the kind the paper takes from Moe et al. for
-// p >= 1, formula not printed).  means_kernel: the quadrature mean of every element.
-// limit_kernel: per element, bounds M = max(own and face-neighbour means) + alpha and
-// m = min(...) - alpha per conserved variable (non-periodic boundaries add no neighbour); the
-// element's extremes over its nodes and its face traces; one factor theta = min over the
-// variables of (M - mean)/(max - mean) and (mean - m)/(mean - min) (where exceeded), and
-// U_i <- mean + theta (U_i - mean); then the physicality operator when enabled.
+// Limiters (Sec. 2.3 names the limiters of Moe et al. and the minmod limiter, printing neither).
+// means_kernel: the quadrature mean of every element.  limit_kernel: one factor theta per
+// element, U_i <- mean + theta (U_i - mean), then the physicality operator when enabled.
+//   scaling (limiter 1): bounds M = max(own and face-neighbour means) + alpha and
+//     m = min(...) - alpha per conserved variable; the element's extremes over its nodes and
+//     face traces; theta = min over the variables of (M - mean)/(max - mean) and
+//     (mean - m)/(mean - min) where exceeded;
+//   minmod (limiter 2): per variable and axis the face-mean deviations a+ = (mean of the +d
+//     face traces) - mean and a- = mean - (the same on the -d face), the neighbour-mean
+//     differences D+ and D-, mm(a) = a if |a| <= M h^2 + 2^-40 (|mean D| + |mean tau|), else
+//     s min(|a|, |D+|, |D-|) if all share the sign s, else 0; theta = min of mm(a) / a.
+// Non-periodic boundaries add no neighbour.
 // ---------------------------------------------------------------------------------------
+__device__ __forceinline__ double minmod_bound(double x, const double* D, int nD, double thr) {
+  if (fabs(x) <= thr) return x;
+  double mag = fabs(x);
+  for (int k = 0; k < nD; ++k) {
+    if ((D[k] > 0.0) != (x > 0.0) || D[k] == 0.0) return 0.0;
+    mag = fmin(mag, fabs(D[k]));
+  }
+  return x > 0.0 ? mag : -mag;
+}
+
 template <int DIM, int N>
 __global__ void __launch_bounds__(Shape<DIM, N>::BLOCK)
     means_kernel(Params p, const double* __restrict__ U, double* __restrict__ means) {
@@ -584,7 +599,49 @@ __global__ void __launch_bounds__(Shape<DIM, N>::BLOCK)
     }
   }
   __syncthreads();
-  if (valid && li == 0) {
+  if (valid && li == 0 && p.limiter == 2) {
+    // minmod: tangential quadrature weights of the face points, summing to 2^(dim-1)
+    double theta = 1.0;
+    const double thr = p.lim_alpha + 0x1p-40 * (fabs(means[e]) + fabs(means[4 * p.E + e]));
+    const double face_wsum = 0.5 * p.wsum;
+    for (int v = 0; v < 5; ++v) {
+      const double ub = means[v * p.E + e];
+#pragma unroll
+      for (int d = 0; d < DIM; ++d) {
+        const long long c = elem_coord(p, e, d);
+        double D[2];
+        int nD = 0;
+        for (int side = 1; side >= 0; --side) {
+          long long ne;
+          if (side == 0)
+            ne = (c > 0) ? e - p.stride[d] : (p.bc[d][0] == 0 ? e + (p.n[d] - 1) * p.stride[d] : -1);
+          else
+            ne = (c < p.n[d] - 1) ? e + p.stride[d] : (p.bc[d][1] == 0 ? e - (p.n[d] - 1) * p.stride[d] : -1);
+          if (ne < 0) continue;
+          const double un = means[v * p.E + ne];
+          D[nD++] = side ? un - ub : ub - un;
+        }
+        double fm[2] = {0.0, 0.0};
+        for (int side = 0; side < 2; ++side)
+          for (int t = 0; t < Nt; ++t) {
+            int ijk[3];
+            node_ijk<DIM, N>(line_node<DIM, N>(d, t, 0), ijk);
+            double wt = 1.0;
+#pragma unroll
+            for (int dd = 0; dd < DIM; ++dd)
+              if (dd != d) wt *= p.w[ijk[dd]];
+            fm[side] += wt * tr[le][(d * 2 + side) * Nt + t][v];
+          }
+        const double dev[2] = {fm[1] / face_wsum - ub, ub - fm[0] / face_wsum};
+        for (int k = 0; k < 2; ++k) {
+          const double mmv = minmod_bound(dev[k], D, nD, thr);
+          if (mmv != dev[k]) theta = fmin(theta, mmv / dev[k]);
+        }
+      }
+    }
+    th[le] = theta;
+    if (theta < 1.0) atomicAdd(&p.stats[kStatLimited * 64 + (blockIdx.x & 63)], 1ULL);
+  } else if (valid && li == 0) {
     double theta = 1.0;
     for (int v = 0; v < 5; ++v) {
       const double ub = means[v * p.E + e];

@@ -237,6 +237,10 @@ def test_enforce(lib, dim, degree, n):
     (lambda c2p: dict(wl.riemann_1d(3, n=96, degree=1), limiter=True), "iterative"),
     (lambda c2p: dict(wl.tm_blast("tm", n=96, degree=1), limiter=True), "iterative"),
     (lambda c2p: wl.tm_blast("ideal", 4.0 / 3.0, n=64, degree=0), "iterative"),
+    # the minmod limiter
+    (lambda c2p: dict(wl.riemann_1d(2, n=96, degree=1), limiter="minmod", limiter_alpha=0.0), "iterative"),
+    (lambda c2p: dict(wl.tm_blast("tm", n=96, degree=2), limiter="minmod"), "iterative"),
+    (lambda c2p: dict(wl.kh_single(nx=12, ny=24, degree=2), limiter="minmod", limiter_alpha=0.0), "iterative"),
 ])
 def test_step_one_and_hundred(lib, spec_fn, c2p):
     spec = spec_fn(c2p)
@@ -563,10 +567,14 @@ def test_gll_blast_wave_needs_no_face_guard(lib):
 # ---------------------------------------------------------------------------------------
 # Test 1's colliding shocks amplify rounding-level differences quickly (the oracle alone breaks
 # its mirror symmetry by 6e-6 at p = 1, t = 0.8): one step at 1e-11, forty steps at 1e-4.
-@pytest.mark.parametrize("test,degree,steps,tol", [(1, 1, 1, 1e-11), (1, 1, 40, 1e-4),
-                                                   (2, 1, 40, 1e-9), (3, 2, 40, 1e-9)])
-def test_riemann_2d_against_oracle(lib, test, degree, steps, tol):
-    spec = wl.riemann_2d(test, n=20, degree=degree)
+@pytest.mark.parametrize("test,degree,steps,tol,limiter", [
+    (1, 1, 1, 1e-11, True), (1, 1, 40, 1e-4, True), (2, 1, 40, 1e-9, True),
+    (3, 2, 40, 1e-9, True),
+    (1, 1, 1, 1e-11, "minmod"), (1, 1, 40, 1e-4, "minmod"), (3, 2, 40, 1e-9, "minmod")])
+def test_riemann_2d_against_oracle(lib, test, degree, steps, tol, limiter):
+    spec = dict(wl.riemann_2d(test, n=20, degree=degree), limiter=limiter)
+    if limiter == "minmod":
+        spec["limiter_alpha"] = 0.0
     s = solver(spec, stream=torch.cuda.Stream())
     dt = s.cfl_dt(0.2)
     with torch.cuda.stream(s.stream):
