@@ -185,27 +185,31 @@ int32_t dgsrhd_enforce_vjp(dgsrhd_ctx* ctx, const double* s, const double* Ut_ba
                            double* U_bar);
 
 /* One Shu-Osher stage `stage` (0-based) of the configured scheme:
- * Uout = a_k Un + b_k (Uk + dt R(Uk)), followed (if enabled) by the physicality operator, whose
- * per-element factors go to s_out (nullable, [n_elem]).  Uout may alias Un or Uk.  Composing
+ * Uout = a_k Un + b_k (Uk + dt R(Uk)), followed (if configured) by the limiter and (if enabled)
+ * by the physicality operator, whose per-element factors go to s_out (nullable, [n_elem]).  Uout may alias Un or Uk.  Composing
  * the stages reproduces dgsrhd_step.  save (nullable, device, dgsrhd_stage_save_size doubles)
  * receives what dgsrhd_stage_vjp needs from the forward stage: the nodal (rho, u, P, gamma,
  * 1/gamma), the face traces, the face-state tape (per face state its roots and reciprocals, A,
- * B, K, rho (h - 1), U, r, the wavespeeds and the normal flux) and the face-guard flags; a stage
- * with save runs the FP64 kernels whatever the configured precision. */
+ * B, K, rho (h - 1), U, r, the wavespeeds and the normal flux), the face-guard flags and, with
+ * a limiter, its factor theta per element; a stage with save runs the FP64 kernels whatever the
+ * configured precision. */
 int32_t dgsrhd_step_stage(dgsrhd_ctx* ctx, const double* Un, const double* Uk, double* Uout,
                           int32_t stage, double dt, double* s_out, double* save);
 
 /* Doubles of the `save` buffer of dgsrhd_step_stage: 7 E Nn (nodal primitives) + 10 dim E Nt
  * (traces) + 52 (face points) (tape) + one byte per face point of every element (guard flags),
- * rounded up to whole doubles. */
+ * rounded up to whole doubles, + E (the limiter's factors, with a limiter). */
 int32_t dgsrhd_stage_save_size(const dgsrhd_ctx* ctx, int64_t* n);
 
 /* Reverse sweep of one stage (the transpose of dgsrhd_step_stage at its input Uk, with the
- * operator's factors s frozen; s NULL or enforcement off: no operator):
- *   Y_bar = enforce_vjp(s, Z_bar),  Un_bar += a_k Y_bar,
- *   Uk_bar += b_k (Y_bar + dt (dR/dU)^T Y_bar)  at U = Uk.
+ * operator's factors s and the limiter's factors theta frozen; s NULL or enforcement off: no
+ * operator):
+ *   Y_bar = enforce_vjp(theta, enforce_vjp(s, Z_bar)),  Un_bar += a_k Y_bar,
+ *   Uk_bar += b_k (Y_bar + dt (dR/dU)^T Y_bar)  at U = Uk
+ * (the limiter U_i <- mean + theta (U_i - mean) is the operator's linear map with theta for s).
  * saved (nullable): the `save` buffer of the forward stage; without it the forward quantities
- * are recomputed.  Both outputs ACCUMULATE (zero them first); they may alias each other but
+ * are recomputed, which a limited configuration cannot do (theta needs U^n): it returns
+ * DGSRHD_EINVAL.  Both outputs ACCUMULATE (zero them first); they may alias each other but
  * not Z_bar. */
 int32_t dgsrhd_stage_vjp(dgsrhd_ctx* ctx, const double* Uk, const double* s, const double* saved,
                          const double* Z_bar, double* Un_bar, double* Uk_bar, int32_t stage,

@@ -35,6 +35,7 @@ struct dgsrhd_ctx {
   double* Wv;   // VJP: nodal (rho, u, P)
   double* TrB;  // VJP: trace adjoints
   double* Yb;   // stage VJP: adjoint of the stage before the operator
+  double* Yb2;  // stage VJP: adjoint before the limiter (limited configurations)
   unsigned char* Gd;  // VJP: face-guard flag per face point [E][2 dim Nt]
   double* Mn;   // limiter: element means [5][E]
   long long fs_total;  // doubles of the face-flux buffer
@@ -232,7 +233,7 @@ cudaError_t volume_and_faces(dgsrhd_ctx* c, const double* U) {
 
 // The limiter after a stage: element means, then the limit kernel (which also applies the
 // physicality operator when it is enabled).
-cudaError_t limit_stage(dgsrhd_ctx* c, double* U, double* s_out) {
+cudaError_t limit_stage(dgsrhd_ctx* c, double* U, double* s_out, double* theta_out = nullptr) {
   StageArgs m{};
   m.op = Op::Means;
   m.Uout = U;
@@ -245,6 +246,7 @@ cudaError_t limit_stage(dgsrhd_ctx* c, double* U, double* s_out) {
   l.means = c->Mn;
   l.enforce = c->cfg.enforce;
   l.s_out = s_out;
+  l.theta_out = theta_out;
   return run_stage(c, l);
 }
 
@@ -467,6 +469,7 @@ int32_t dgsrhd_create(const dgsrhd_config* cfg, void* stream, dgsrhd_ctx** out) 
   if (e == cudaSuccess) e = alloc(&c->Wv, (long long)dgsrhd::kNodePrim * E * p.Nn);
   if (e == cudaSuccess) e = alloc(&c->TrB, ntr);
   if (e == cudaSuccess) e = alloc(&c->Yb, c->nstate);
+  if (e == cudaSuccess && cfg->limiter) e = alloc(&c->Yb2, c->nstate);
   if (e == cudaSuccess) e = alloc(&c->Gd, 2LL * c->dim * E * p.Nt);
   if (e == cudaSuccess && cfg->limiter) e = alloc(&c->Mn, 5LL * E);
   if (e == cudaSuccess) e = alloc(&c->stats, (size_t)dgsrhd::kStatCount * 64);
@@ -500,6 +503,7 @@ void dgsrhd_destroy(dgsrhd_ctx* c) {
   cudaFree(c->Wv);
   cudaFree(c->TrB);
   cudaFree(c->Yb);
+  cudaFree(c->Yb2);
   cudaFree(c->Gd);
   cudaFree(c->Mn);
   cudaFree(c->stats);
@@ -758,6 +762,7 @@ struct Saved {
   double* Tr;
   double* tape;
   unsigned char* guard;
+  double* theta;  // the limiter's factor per element (limited configurations)
 };
 Saved saved_sections(const dgsrhd_ctx* c, double* save) {
   Saved v{};
@@ -766,6 +771,7 @@ Saved saved_sections(const dgsrhd_ctx* c, double* save) {
   v.Tr = save + (long long)dgsrhd::kNodePrim * c->E * c->Nn;
   v.tape = v.Tr + trace_doubles(c);
   v.guard = reinterpret_cast<unsigned char*>(v.tape + tape_doubles(c));
+  v.theta = c->cfg.limiter ? v.tape + tape_doubles(c) + guard_doubles(c) : nullptr;
   return v;
 }
 
@@ -827,7 +833,7 @@ int32_t dgsrhd_rhs_vjp(dgsrhd_ctx* c, const double* U, const double* R_bar, doub
 int32_t dgsrhd_stage_save_size(const dgsrhd_ctx* c, int64_t* n) {
   if (!c || !n) return DGSRHD_EINVAL;
   *n = (long long)dgsrhd::kNodePrim * c->E * c->Nn + trace_doubles(c) + tape_doubles(c) +
-       guard_doubles(c);
+       guard_doubles(c) + (c->cfg.limiter ? c->E : 0);
   return DGSRHD_OK;
 }
 
@@ -879,7 +885,7 @@ int32_t dgsrhd_step_stage(dgsrhd_ctx* c, const double* Un, const double* Uk, dou
   u.enforce = c->cfg.enforce && !c->cfg.limiter;
   u.s_out = s_out;
   if (run_stage(c, u) != cudaSuccess) return DGSRHD_ECUDA;
-  if (c->cfg.limiter) return cuda_status(limit_stage(c, Uout, s_out));
+  if (c->cfg.limiter) return cuda_status(limit_stage(c, Uout, s_out, sv.theta));
   return DGSRHD_OK;
 }
 
@@ -889,13 +895,23 @@ int32_t dgsrhd_stage_vjp(dgsrhd_ctx* c, const double* Uk, const double* s, const
   if (!c || !Uk || !Z_bar || !Un_bar || !Uk_bar || stage < 0 || stage >= c->cfg.rk_stages)
     return DGSRHD_EINVAL;
   if (Z_bar == Un_bar || Z_bar == Uk_bar) return DGSRHD_EINVAL;
-  if (c->cfg.limiter) return DGSRHD_EINVAL;  // no reverse sweep of the limiter
+  // the limiter's factors exist only in the saved forward quantities (recomputing them would
+  // need U^n)
+  if (c->cfg.limiter && !saved) return DGSRHD_EINVAL;
   const int ns = c->cfg.rk_stages;
   const double* Yb = Z_bar;
   if (c->cfg.enforce && s) {
     int32_t st = dgsrhd_enforce_vjp(c, s, Z_bar, c->Yb);
     if (st != DGSRHD_OK) return st;
     Yb = c->Yb;
+  }
+  if (c->cfg.limiter) {
+    // U_i <- mean + theta (U_i - mean) with theta frozen: the same linear map as the operator's
+    Saved sv = saved_sections(c, const_cast<double*>(saved));
+    double* out = (Yb == c->Yb) ? c->Yb2 : c->Yb;
+    int32_t st = dgsrhd_enforce_vjp(c, sv.theta, Yb, out);
+    if (st != DGSRHD_OK) return st;
+    Yb = out;
   }
   // the node reverse sweep adds a_n Yb to Un_bar and b_k (Yb + dt (dR/dU)^T Yb) to Uk_bar
   const double a_n = kAn[ns - 1][stage], b_k = kBk[ns - 1][stage];

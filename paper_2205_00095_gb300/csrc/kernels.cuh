@@ -564,7 +564,7 @@ __global__ void __launch_bounds__(Shape<DIM, N>::BLOCK)
 template <int DIM, int N>
 __global__ void __launch_bounds__(Shape<DIM, N>::BLOCK)
     limit_kernel(Params p, double* U, const double* __restrict__ means, int enforce,
-                 double* __restrict__ s_out) {
+                 double* __restrict__ s_out, double* __restrict__ theta_out) {
   using S = Shape<DIM, N>;
   constexpr int Nn = S::Nn, Nt = S::Nt, NFP = S::NFP, EPB = S::EPB;
   __shared__ EnforceShared<DIM, N> sh;  // sh.a holds the nodal state first
@@ -680,6 +680,7 @@ __global__ void __launch_bounds__(Shape<DIM, N>::BLOCK)
     if (theta < 1.0) atomicAdd(&p.stats[kStatLimited * 64 + (blockIdx.x & 63)], 1ULL);
   }
   __syncthreads();
+  if (theta_out && valid && li == 0) theta_out[e] = th[le];  // kept for the reverse sweep
   if (valid && th[le] < 1.0) {
     const double t = th[le];
 #pragma unroll
@@ -773,7 +774,8 @@ static cudaError_t launch_stage_kernels(const StageArgs& a) {
       means_kernel<DIM, N><<<eblocks, S::BLOCK, 0, a.stream>>>(p, a.Uout, a.means);
       break;
     case Op::Limit:
-      limit_kernel<DIM, N><<<eblocks, S::BLOCK, 0, a.stream>>>(p, a.Uout, a.means, a.enforce, a.s_out);
+      limit_kernel<DIM, N><<<eblocks, S::BLOCK, 0, a.stream>>>(p, a.Uout, a.means, a.enforce,
+                                                               a.s_out, a.theta_out);
       break;
     default:
       return cudaErrorInvalidValue;

@@ -27,6 +27,7 @@ struct StageArgs {
   int split;           // Volume / Update: split-precision tensor-core contractions (set by the host)
   int fp64_only;       // force the FP64 kernels whatever the configured precision
   double* s_out;
+  double* theta_out;   // Limit: per-element limiter factor (nullable)
   // VJP buffers
   const double* Rbar;  // VjpFace / VjpNode: adjoint of R
   double* Ubar;        // VjpNode / EnforceVjp: output adjoint of U

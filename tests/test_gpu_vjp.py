@@ -210,8 +210,9 @@ def test_stage_vjp_with_saved_forward_equals_recompute(gpu_lib):
         assert torch.equal(a_un, b_un) and torch.equal(a_uk, b_uk)
 
 
-def test_stage_vjp_with_the_limiter_is_refused(gpu_lib):
-    """The limiter has no reverse sweep: dgsrhd_stage_vjp returns DGSRHD_EINVAL for it."""
+def test_stage_vjp_of_a_limited_stage_needs_the_saved_forward(gpu_lib):
+    """The limiter's factors exist only in the saved forward quantities (recomputing them would
+    need U^n): without saved, dgsrhd_stage_vjp returns DGSRHD_EINVAL for a limited stage."""
     from paper_2205_00095_gb300 import _lib
     spec = dict(wl.kh2d(nx=4, ny=8, degree=2), limiter=True)
     s = solver(spec)
@@ -222,3 +223,77 @@ def test_stage_vjp_with_the_limiter_is_refused(gpu_lib):
     st = s.lib.dgsrhd_stage_vjp(s.ctx, U.data_ptr(), None, None, Z.data_ptr(), a.data_ptr(),
                                 b.data_ptr(), 0, 1e-3)
     assert st == _lib.DGSRHD_EINVAL
+
+
+def frozen_scale(U, f, w):
+    """V -> mean + f (V - mean) per element (the limiter and the operator with frozen f)."""
+    mean = (U * w).sum(-1, keepdims=True) / w.sum()
+    return mean + f[None, :, None] * (U - mean)
+
+
+LIMITED_STAGES = [
+    (dict(wl.riemann_1d(4, n=24, degree=1), limiter=True, limiter_alpha=0.0), 1),
+    (dict(wl.riemann_1d(2, n=24, degree=2), limiter="minmod", limiter_alpha=0.0), 2),
+    (dict(wl.kh_single(nx=6, ny=12, degree=2), limiter="minmod", limiter_alpha=0.0), 2),
+]
+
+
+@pytest.mark.parametrize("spec,stage", LIMITED_STAGES)
+def test_limited_stage_vjp_is_the_transpose_of_the_frozen_stage(gpu_lib, spec, stage):
+    """With the limiter's theta and the operator's s frozen at their forward values a stage is
+    Z = L_s(L_theta(a Un + b (Uk + dt R(Uk)))); <Zbar, dZ/dUk V> by central differences of the
+    oracle's R (h = 1e-6) equals <Ukbar, V> from dgsrhd_stage_vjp, and Unbar = a L^T Zbar."""
+    s = solver(spec)
+    E, Nn = s.n_elem, s.shape[2]
+    U0 = s.initial_state(wl.initial_primitive(spec, s.node_coords()))
+    s.enforce(U0)
+    dt = s.cfl_dt(0.2)
+    s.step(U0, dt, 6)           # a few limited steps: structure near the discontinuities
+    Un = U0.clone()
+    X = [Un]
+    for k in range(stage):      # the inputs of stages 0..stage
+        out = torch.empty_like(Un)
+        s.step_stage(Un, X[k], out, k, dt)
+        X.append(out)
+    Uk = X[stage]
+    out = torch.empty_like(Un)
+    sf = torch.empty(E, dtype=torch.float64, device="cuda")
+    save = torch.empty(s.stage_save_size(), dtype=torch.float64, device="cuda")
+    s.step_stage(Un, Uk, out, stage, dt, sf, save)
+    torch.cuda.synchronize()
+    theta = save[-E:].cpu().numpy()
+    sfn = sf.cpu().numpy() if spec.get("enforce", True) else np.ones(E)
+    assert np.any(theta < 1.0), "the stage should be limited somewhere"
+    rng = np.random.default_rng(11)
+    Zb = rng.normal(size=tuple(U0.shape))
+    Ua = np.abs(Uk.cpu().numpy())
+    V = rng.normal(size=tuple(U0.shape)) * (Ua + 1e-3 * Ua.max(axis=(1, 2), keepdims=True))
+    Unb, Ukb = torch.zeros_like(Un), torch.zeros_like(Un)
+    s.stage_vjp(Uk, sf, torch.from_numpy(Zb).cuda(), Unb, Ukb, stage, dt, save)
+    torch.cuda.synchronize()
+    ns = spec["rk_stages"]
+    a_n = [[0.0], [0.0, 0.5], [0.0, 0.75, 1.0 / 3.0]][ns - 1][stage]
+    b_k = [[1.0], [1.0, 0.5], [1.0, 0.25, 2.0 / 3.0]][ns - 1][stage]
+    N = spec["degree"] + 1
+    w1 = np.polynomial.legendre.leggauss(N)[1]
+    w = w1
+    for _ in range(spec["dim"] - 1):
+        w = np.multiply.outer(w1, w).ravel()
+    Unp, Ukp = Un.cpu().numpy(), Uk.cpu().numpy()
+
+    def stage_map(Ukx):
+        R, _ = oracle.rhs(spec, Ukx)
+        Y = a_n * Unp + b_k * (Ukx + dt * R)
+        return frozen_scale(frozen_scale(Y, theta, w), sfn, w)
+
+    h = 1e-6
+    dZ = (stage_map(Ukp + h * V) - stage_map(Ukp - h * V)) / (2 * h)
+    lhs = float((Zb * dZ).sum())
+    rhs = float((Ukb.cpu().numpy() * V).sum())
+    assert abs(lhs - rhs) <= 1e-6 * max(abs(lhs), abs(rhs))
+    # Un enters linearly: Unbar = a_n L_theta^T L_s^T Zbar
+    Ln = frozen_scale(frozen_scale(Unp + V, theta, w), sfn, w) - frozen_scale(frozen_scale(Unp, theta, w), sfn, w)
+    if a_n != 0.0:
+        lhs_n = float((Zb * a_n * Ln).sum())
+        rhs_n = float((Unb.cpu().numpy() * V).sum())
+        assert abs(lhs_n - rhs_n) <= 1e-10 * max(abs(lhs_n), abs(rhs_n))
