@@ -8,12 +8,16 @@ It shares no code with the CUDA library and never imports it.
 The arithmetic lives in ``dgsrhd_oracle.c`` (plain loops, one routine per
 equation of the paper); this module compiles it with gcc on first use and wraps
 it with ctypes.  ``exact_riemann.py`` holds the exact 1D Riemann solution used
-to check the blast-wave problem.
+to check the blast-wave problem, ``exact_riemann_general.py`` the one with
+transverse velocity and either equation of state (Riemann problem 3 and the
+Taub-Matthews blast wave).
 
-Parity status per function (each is pinned by a ``-m "not gpu"`` test unless
-marked otherwise):
-  basis, EOS, prim2cons, the four con2prim solvers, wavespeeds, numerical flux,
-  rhs, enforce, step, cfl_dt: pinned.
+Parity status per function (each is pinned by a ``-m "not gpu"`` test):
+  basis (Gauss-Legendre and Gauss-Lobatto-Legendre), EOS, prim2cons, the four
+  con2prim solvers, wavespeeds, the LLF, HLL and HLLC fluxes, rhs (periodic,
+  Dirichlet, outflow and reflecting boundaries), enforce, the scaling and minmod
+  limiters, step, cfl_dt, mean_square_velocity, gamma_eq and both exact Riemann
+  solutions: pinned.
 """
 from __future__ import annotations
 
