@@ -47,3 +47,15 @@ def test_kh_single_grows_exponentially(gpu_lib):
     assert m[t >= 3.0 - 1e-9][0] > m[np.argmin(np.abs(t - 1.5))]
     assert r["growth_rate_fit_1p5_to_3"] > 0.0 and r["fit_r2"] > 0.9, r["fit_r2"]
 
+
+
+def test_kh_throughput_points(gpu_lib):
+    """The throughput study of Sec. 5 on two points: runs clean, and the paper's smallest mesh
+    updates more DOF per second than a 32 x 64 mesh (the small one cannot fill the GPU)."""
+    from paper_2205_00095_gb300 import kh_perf
+    small = kh_perf.measure(32, 64, 1, "hll", steps=20)
+    paper = kh_perf.measure(256, 512, 1, "hll", steps=20)
+    for r in (small, paper):
+        assert r["status"] == 0 and r["dof_updates_per_s"] > 0.0
+        assert r["rk_stages"] == 2 and r["dof"] == r["n_x"] * r["n_y"] * 4
+    assert paper["dof_updates_per_s"] > small["dof_updates_per_s"]

@@ -304,17 +304,26 @@ def test_blast_wave_full_run(lib):
     assert rel_inf(U.cpu().numpy(), Uo) < 1e-6
 
 
-def test_graph_replay_matches_direct_launches(lib):
+@pytest.mark.parametrize("nsteps", [5, 37])
+def test_graph_replay_matches_direct_launches(lib, nsteps):
+    """Captured steps (one-step graphs; 37 = two replays of the 16-step graph and five of the
+    one-step graph) give the bits of direct launches, and the launch count of the step."""
     spec = wl.kh2d(nx=8, ny=16, degree=3)
     a = solver(spec, stream=torch.cuda.Stream())
     U1 = gpu_state(a, spec)
     U2 = U1.clone()
     dt = a.cfl_dt(0.2)
-    a.step(U1, dt, 5)                         # captured graph
+    n0 = a.kernel_launches()
+    a.step(U1, dt, nsteps)                    # captured graphs
+    assert a.kernel_launches() - n0 == 9 * nsteps
     from paper_2205_00095_gb300 import Solver
     b = Solver(spec)                          # legacy stream: direct launches
     b.lib.dgsrhd_set_stream(b.ctx, None)
-    b.step(U2, dt, 5)
+    b.step(U2, dt, nsteps)
+    torch.cuda.synchronize()
+    assert torch.equal(U1, U2)
+    a.step(U1, dt, nsteps)                    # replay of the cached graphs
+    b.step(U2, dt, nsteps)
     torch.cuda.synchronize()
     assert torch.equal(U1, U2)
 
