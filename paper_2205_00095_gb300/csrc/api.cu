@@ -48,7 +48,6 @@ struct dgsrhd_ctx {
     cudaGraphExec_t exec;
     double dt;
     double* U;
-    int steps;  // steps captured in the graph
     unsigned long long used;
   };
   std::vector<StepGraph> graphs;
@@ -600,17 +599,11 @@ int32_t dgsrhd_step(dgsrhd_ctx* c, double* U, double dt, int32_t nsteps) {
     }
     return DGSRHD_OK;
   }
-  // One graph launch replays kBatch steps when there are that many: on small meshes a step's
-  // three kernels per stage take a few microseconds, and one launch per step would leave the
-  // GPU waiting on the host.
-  constexpr int kBatch = 16;
-  auto graph_for = [&](int steps, dgsrhd_ctx::StepGraph** out) -> int32_t {
-    for (auto& g : c->graphs)
-      if (g.U == U && g.dt == dt && g.steps == steps) {
-        *out = &g;
-        return DGSRHD_OK;
-      }
-    constexpr size_t kMaxGraphs = 8;
+  dgsrhd_ctx::StepGraph* hit = nullptr;
+  for (auto& g : c->graphs)
+    if (g.U == U && g.dt == dt) hit = &g;
+  if (!hit) {
+    constexpr size_t kMaxGraphs = 4;
     if (c->graphs.size() == kMaxGraphs) {
       size_t lru = 0;
       for (size_t i = 1; i < c->graphs.size(); ++i)
@@ -622,8 +615,7 @@ int32_t dgsrhd_step(dgsrhd_ctx* c, double* U, double dt, int32_t nsteps) {
     cudaError_t e = cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return DGSRHD_ECUDA;
     const long long l0 = c->launches, k0 = c->c2p_calls;
-    cudaError_t e1 = cudaSuccess;
-    for (int k = 0; k < steps && e1 == cudaSuccess; ++k) e1 = one_step(c, U, dt);
+    cudaError_t e1 = one_step(c, U, dt);
     e = cudaStreamEndCapture(c->stream, &g);
     c->launches = l0;  // captured, not launched
     c->c2p_calls = k0;
@@ -636,26 +628,13 @@ int32_t dgsrhd_step(dgsrhd_ctx* c, double* U, double dt, int32_t nsteps) {
     e = cudaGraphInstantiate(&exec, g, 0);
     cudaGraphDestroy(g);
     if (e != cudaSuccess) return DGSRHD_ECUDA;
-    c->graphs.push_back({exec, dt, U, steps, 0});
-    *out = &c->graphs.back();
-    return DGSRHD_OK;
-  };
-  int done = 0;
-  if (nsteps >= kBatch) {
-    dgsrhd_ctx::StepGraph* g = nullptr;
-    const int32_t st = graph_for(kBatch, &g);
-    if (st != DGSRHD_OK) return st;
-    g->used = ++c->graph_clock;
-    for (; done + kBatch <= nsteps; done += kBatch)
-      if (cudaGraphLaunch(g->exec, c->stream) != cudaSuccess) return DGSRHD_ECUDA;
+    c->graphs.push_back({exec, dt, U, 0});
+    hit = &c->graphs.back();
   }
-  if (done < nsteps) {
-    dgsrhd_ctx::StepGraph* g = nullptr;
-    const int32_t st = graph_for(1, &g);
-    if (st != DGSRHD_OK) return st;
-    g->used = ++c->graph_clock;
-    for (; done < nsteps; ++done)
-      if (cudaGraphLaunch(g->exec, c->stream) != cudaSuccess) return DGSRHD_ECUDA;
+  hit->used = ++c->graph_clock;
+  for (int s = 0; s < nsteps; ++s) {
+    cudaError_t e = cudaGraphLaunch(hit->exec, c->stream);
+    if (e != cudaSuccess) return DGSRHD_ECUDA;
   }
   c->launches += per_step * nsteps;
   c->c2p_calls += (long long)nsteps * c->cfg.rk_stages * c->E * c->Nn;

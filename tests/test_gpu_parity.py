@@ -306,8 +306,8 @@ def test_blast_wave_full_run(lib):
 
 @pytest.mark.parametrize("nsteps", [5, 37])
 def test_graph_replay_matches_direct_launches(lib, nsteps):
-    """Captured steps (one-step graphs; 37 = two replays of the 16-step graph and five of the
-    one-step graph) give the bits of direct launches, and the launch count of the step."""
+    """Captured steps (replays of the cached one-step graph) give the bits of direct launches,
+    and the launch count of the step."""
     spec = wl.kh2d(nx=8, ny=16, degree=3)
     a = solver(spec, stream=torch.cuda.Stream())
     U1 = gpu_state(a, spec)
