@@ -1,5 +1,6 @@
-"""Split-precision form: the volume term, trace extrapolation and lift on tensor cores (3xTF32,
-FP32 accumulation, on deviations from a per-element reference), everything else FP64.  Checked
+"""Split-precision form: the volume term and trace extrapolation on tensor cores (3xTF32, FP32
+accumulation), the lift as FP32 FMAs, all on deviations from a per-element reference;
+everything else FP64.  Checked
 against the FP64 oracle: the RHS to 1e-5 of its largest magnitude, and the state after 100
 SSPRK3 steps to an L1 difference below 1e-6 relative."""
 import numpy as np
@@ -42,12 +43,18 @@ CASES = [
     (3, [6, 5, 7], 3, "tm", "hll", None),
     (3, [4, 3, 5], 4, "ideal", "llf", None),
     (2, [20, 13], 0, "ideal", "llf", None),
+    (2, [9, 8], 2, "ideal", "hllc", [("reflect", "outflow"), ("periodic", "periodic")]),
+    (1, [33], 3, "tm", "hllc", [("reflect", "reflect")]),
 ]
 
 
 @pytest.mark.parametrize("dim,n,degree,eos,flux,bc", CASES)
-def test_split_rhs_against_oracle(gpu_lib, dim, n, degree, eos, flux, bc):
-    spec = wl.smooth_random(dim, n, degree, eos=eos, flux=flux, c2p="iterative", seed=5, bc=bc)
+@pytest.mark.parametrize("nodes", ["gl", "gll"])
+def test_split_rhs_against_oracle(gpu_lib, dim, n, degree, eos, flux, bc, nodes):
+    if nodes == "gll" and degree == 0:
+        pytest.skip("Gauss-Lobatto-Legendre needs degree >= 1")
+    spec = dict(wl.smooth_random(dim, n, degree, eos=eos, flux=flux, c2p="iterative", seed=5,
+                                 bc=bc), nodes=nodes)
     s = solver(spec)
     R = s.rhs(gpu_state(s, spec)).cpu().numpy()
     Ro, _ = oracle.rhs(spec, oracle_state(spec))
@@ -59,6 +66,10 @@ def test_split_rhs_against_oracle(gpu_lib, dim, n, degree, eos, flux, bc):
     lambda: wl.advected_wave(n=16, degree=3, c2p="analytic"),
     lambda: wl.kh2d(nx=12, ny=24, degree=3),
     lambda: wl.smooth_random(3, [5, 6, 4], 2, eos="tm", flux="hll", seed=8),
+    # limiters after the split update, HLLC
+    lambda: dict(wl.riemann_1d(4, n=96, degree=1), limiter=True),
+    lambda: dict(wl.tm_blast("tm", n=96, degree=2), limiter="minmod"),
+    lambda: dict(wl.kh_single(nx=12, ny=24, degree=2, flux="hllc"), limiter="minmod"),
 ])
 def test_split_hundred_steps_l1(gpu_lib, spec_fn):
     spec = spec_fn()
