@@ -151,3 +151,25 @@ def test_riemann_problem_converges_with_minmod(problem):
         l1.append(((np.abs(U - Ue) * w).sum(axis=(1, 2)) / (2 * n))[[0, 1, 4]])
     l1 = np.array(l1)
     assert np.all(l1[1:] < 0.9 * l1[:-1]), l1
+
+
+def test_wall_problem_5_at_p2_runs_and_converges_with_minmod():
+    """Riemann problem 5 (gamma = 224 flow into a reflecting wall) at p = 2: the scaling limiter
+    loses admissible element means there, the minmod limiter keeps them all and the L1 error
+    halves with each refinement."""
+    from tests.test_oracle_riemann import exact
+    l1 = []
+    for n in (64, 128, 256):
+        spec = dict(wl.riemann_1d(5, n=n, degree=2), limiter="minmod", limiter_alpha=0.0)
+        X = oracle.node_coords(spec)
+        U = oracle.prim2cons(spec, wl.initial_primitive(spec, X))
+        U, _, _ = oracle.enforce(spec, U)
+        T = spec["t_final"]
+        nsteps = int(np.ceil(T / oracle.cfl_dt(spec, spec["cfl"])))
+        U, st = oracle.step(spec, U, T / nsteps, nsteps)
+        assert st["mean_inadmissible_cells"] == 0 and st["c2p_invalid_input"] == 0
+        Ue = oracle.prim2cons(spec, exact(spec).sample(X[0], T))
+        w = np.polynomial.legendre.leggauss(3)[1]
+        l1.append(((np.abs(U - Ue) * w).sum(axis=(1, 2)) / (2 * n))[[0, 1, 4]])
+    l1 = np.array(l1)
+    assert np.all(l1[1:] < 0.6 * l1[:-1]), l1
