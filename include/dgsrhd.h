@@ -95,6 +95,9 @@ typedef struct dgsrhd_config {
   double gamma_ad;             /* adiabatic index of the ideal EOS (ignored for TM) */
   int32_t c2p;                 /* DGSRHD_C2P_* */
   int32_t c2p_max_iter;        /* <= 0: 30 Newton / 100 Brent iterations */
+  double c2p_rtol;             /* 0: the iterative solvers stop at their rounding-level rules;
+                                  in (0, 1): they also stop once Newton's step, or Brent's
+                                  bracket, is within c2p_rtol of the iterate */
   int32_t flux;                /* DGSRHD_FLUX_* */
   int32_t rk_stages;           /* 1 (forward Euler), 2 (SSPRK2), 3 (SSPRK3) */
   int32_t bc[3][2];            /* DGSRHD_BC_* for the low and high side of each axis */

@@ -38,6 +38,7 @@ typedef struct {
   double gamma_ad;        /* Gamma of the ideal EOS */
   int32_t c2p;            /* 0 analytic, 1 iterative, 2 default (ideal->analytic, TM->iterative) */
   int32_t c2p_max_iter;   /* <=0 : default (30 Newton, 100 Brent) */
+  double c2p_rtol;        /* >0: the iterative solvers also stop at this relative step / bracket */
   int32_t flux;           /* 0 LLF, 1 HLL, 2 HLLC */
   int32_t rk_stages;      /* 1, 2, 3 */
   int32_t bc[3][2];       /* 0 periodic, 1 Dirichlet, 2 outflow, 3 reflecting wall */
@@ -282,10 +283,11 @@ static double c2p_ideal_analytic_beta(double G, double xi, double eta) {
  * Reading: the printed "u" there is beta = |v|), started from the small-xi
  * series of Eq. iterative_cubic_approximation.
  * Reading (stop rule, not printed): stop when |dw| <= 1e-14 w (Newton's
- * quadratic convergence then leaves the iterate at the rounding floor); for
- * xi < 1e-4 take the series itself (its error is O(xi^5)).
+ * quadratic convergence then leaves the iterate at the rounding floor), or
+ * |dw| <= rtol w for a caller's tolerance rtol > 1e-14; for xi < 1e-4 take the
+ * series itself (its error is O(xi^5)).
  * Returns w; *iters gets the Newton iteration count, *conv 0/1. */
-static double c2p_ideal_iterative_w(double G, double xi, double eta, int max_iter,
+static double c2p_ideal_iterative_w(double G, double xi, double eta, int max_iter, double rtol,
                                     int *iters, int *conv) {
   double al = G / (G - 1.0);
   double k1 = al * eta - 1.0;
@@ -312,7 +314,7 @@ static double c2p_ideal_iterative_w(double G, double xi, double eta, int max_ite
     double dw = P / dP;
     w -= dw;
     *iters = it;
-    if (fabs(dw) <= 1e-14 * w || fabs(P) <= pres) { *conv = 1; break; }
+    if (fabs(dw) <= fmax(1e-14, rtol) * w || fabs(P) <= pres) { *conv = 1; break; }
   }
   return w;
 }
@@ -357,8 +359,10 @@ static double tm_cubic(double c1, double c2, double c3, double W) {
  * bracket gamma in [1, 200], i.e. W in [0, 200^2 - 1], upper end expanded
  * while there is no sign change (Sec. 3.2).
  * Reading: upper end x4 per expansion, at most 10 expansions; tolerance
- * 2 eps |b| + 1e-300; at most max_iter iterations. */
-static double c2p_tm_brent_W(double xi, double eta, int max_iter, int *iters, int *conv) {
+ * max(2 eps, rtol) |b| + 1e-300 (rtol: a caller's relative tolerance); at
+ * most max_iter iterations. */
+static double c2p_tm_brent_W(double xi, double eta, int max_iter, double rtol, int *iters,
+                             int *conv) {
   double c1, c2, c3;
   tm_cubic_coeffs(xi, eta, &c1, &c2, &c3);
   double a = 0.0, b = 200.0 * 200.0 - 1.0;
@@ -379,7 +383,7 @@ static double c2p_tm_brent_W(double xi, double eta, int max_iter, int *iters, in
       a = b; b = c; c = a;
       fa = fb; fb = fc; fc = fa;
     }
-    double tol = 2.0 * 0x1p-52 * fabs(b) + 1e-300;
+    double tol = fmax(2.0 * 0x1p-52, rtol) * fabs(b) + 1e-300;
     double m = 0.5 * (c - b);
     if (fabs(m) <= tol || fb == 0.0) { *conv = 1; return b; }
     if (fabs(e) >= tol && fabs(fa) > fabs(fb)) {
@@ -446,7 +450,7 @@ static int con2prim_point(const or_config *c, const double U[5], double W[5], in
     one_minus_ginv = beta * beta / (1.0 + ginv);
   } else if (c->eos == 0) {
     if (max_iter <= 0) max_iter = 30;
-    double w = c2p_ideal_iterative_w(c->gamma_ad, xi, eta, max_iter, iters, &conv);
+    double w = c2p_ideal_iterative_w(c->gamma_ad, xi, eta, max_iter, c->c2p_rtol, iters, &conv);
     beta = 2.0 * w / (1.0 + w * w);
     ginv = (1.0 - w * w) / (1.0 + w * w);
     one_minus_ginv = 2.0 * w * w / (1.0 + w * w);
@@ -457,7 +461,7 @@ static int con2prim_point(const or_config *c, const double U[5], double W[5], in
       Wl = c2p_tm_analytic_W(xi, eta);
     } else {
       if (max_iter <= 0) max_iter = 100;
-      Wl = c2p_tm_brent_W(xi, eta, max_iter, iters, &conv);
+      Wl = c2p_tm_brent_W(xi, eta, max_iter, c->c2p_rtol, iters, &conv);
     }
     if (!(Wl >= 0.0) || !isfinite(Wl)) conv = 0;
     /* gamma = sqrt(W + 1), beta = sqrt(W / (W + 1)) */

@@ -40,6 +40,7 @@ class dgsrhd_config(ctypes.Structure):
         ("gamma_ad", ctypes.c_double),
         ("c2p", ctypes.c_int32),
         ("c2p_max_iter", ctypes.c_int32),
+        ("c2p_rtol", ctypes.c_double),
         ("flux", ctypes.c_int32),
         ("rk_stages", ctypes.c_int32),
         ("bc", (ctypes.c_int32 * 2) * 3),
@@ -160,6 +161,7 @@ def make_config(spec: dict) -> dgsrhd_config:
     c.gamma_ad = float(spec.get("gamma_ad", 5.0 / 3.0))
     c.c2p = _enum(C2P, spec.get("c2p", "default"))
     c.c2p_max_iter = int(spec.get("c2p_max_iter", 0))
+    c.c2p_rtol = float(spec.get("c2p_rtol", 0.0))
     c.flux = _enum(FLUX, spec.get("flux", "llf"))
     c.rk_stages = int(spec.get("rk_stages", 3))
     bc = spec.get("bc", [("periodic", "periodic")] * c.dim)

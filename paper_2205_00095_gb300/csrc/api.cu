@@ -345,6 +345,7 @@ bool valid_config(const dgsrhd_config* c) {
   if (c->eos != DGSRHD_EOS_IDEAL && c->eos != DGSRHD_EOS_TAUB_MATTHEWS) return false;
   if (c->eos == DGSRHD_EOS_IDEAL && !(c->gamma_ad > 1.0)) return false;
   if (c->c2p < 0 || c->c2p > 2) return false;
+  if (!(c->c2p_rtol >= 0.0 && c->c2p_rtol < 1.0)) return false;
   if (c->flux != DGSRHD_FLUX_LLF && c->flux != DGSRHD_FLUX_HLL && c->flux != DGSRHD_FLUX_HLLC)
     return false;
   if (c->rk_stages < 1 || c->rk_stages > 3) return false;
@@ -437,6 +438,7 @@ int32_t dgsrhd_create(const dgsrhd_config* cfg, void* stream, dgsrhd_ctx** out) 
   p.alpha = cfg->eos == DGSRHD_EOS_IDEAL ? cfg->gamma_ad / (cfg->gamma_ad - 1.0) : 0.0;
   p.c2p = cfg->c2p == DGSRHD_C2P_DEFAULT ? (cfg->eos == DGSRHD_EOS_IDEAL ? 0 : 1) : cfg->c2p;
   p.max_iter = cfg->c2p_max_iter > 0 ? cfg->c2p_max_iter : (cfg->eos == DGSRHD_EOS_IDEAL ? 30 : 100);
+  p.c2p_rtol = cfg->c2p_rtol;
   p.flux = cfg->flux;
   {
     double h = 1e300;
@@ -1024,6 +1026,7 @@ bool params_from_config(const dgsrhd_config* cfg, Params* out, long long* n_trac
   p.alpha = cfg->eos == DGSRHD_EOS_IDEAL ? cfg->gamma_ad / (cfg->gamma_ad - 1.0) : 0.0;
   p.c2p = cfg->c2p == DGSRHD_C2P_DEFAULT ? (cfg->eos == DGSRHD_EOS_IDEAL ? 0 : 1) : cfg->c2p;
   p.max_iter = cfg->c2p_max_iter > 0 ? cfg->c2p_max_iter : (cfg->eos == DGSRHD_EOS_IDEAL ? 30 : 100);
+  p.c2p_rtol = cfg->c2p_rtol;
   p.flux = cfg->flux;
   {
     double h = 1e300;

@@ -133,7 +133,7 @@ __device__ __forceinline__ double beta_ideal_closed_form(double G, double xi, do
 // step is below 1e-6 w or stops shrinking (at most 12), then continue in FP64 from that
 // iterate to the FP64 stop rule; `iters` counts both phases and max_iter caps their sum.
 __device__ __forceinline__ double w_ideal_newton(double al, double xi, double eta, int max_iter,
-                                                 int& iters, bool& conv) {
+                                                 double rtol, int& iters, bool& conv) {
   const double k1 = al * eta - 1.0;
   const double ik1 = recip_nr(k1);
   const double ik1sq = ik1 * ik1;
@@ -181,7 +181,7 @@ __device__ __forceinline__ double w_ideal_newton(double al, double xi, double et
     const double dw = Pw * recip_nr(dP);
     w -= dw;
     ++it;
-    if (fabs(dw) <= 1e-14 * w || fabs(Pw) <= pres) {
+    if (fabs(dw) <= fmax(1e-14, rtol) * w || fabs(Pw) <= pres) {
       conv = true;
       break;
     }
@@ -314,8 +314,8 @@ __device__ __forceinline__ T brent_cubic(T c1, T c2, T c3, T a, T b, T fa, T fb,
 // change sign across that bracket, FP64 Brent runs on the paper's bracket instead.  Stop rule
 // |dW| <= 2 eps |W| + 1e-300 (Brent's tolerance); `iters` counts all iterations and
 // max_iter caps their sum.
-static __device__ __noinline__ double W_tm_brent(double xi, double eta, int max_iter, int& iters,
-                                                 bool& conv) {
+static __device__ __noinline__ double W_tm_brent(double xi, double eta, int max_iter, double rtol,
+                                                 int& iters, bool& conv) {
   const Cubic cc = tm_cubic(xi, eta);
   iters = 0;
   conv = false;
@@ -370,7 +370,7 @@ static __device__ __noinline__ double W_tm_brent(double xi, double eta, int max_
         const double Wn = W - f * recip_nr(df);
         // stop on a Newton step at rounding level before the bracket test: once W sits on
         // the root, rounding noise in f can move a bracket end onto W itself
-        if (fabs(Wn - W) <= 2.0 * 2.220446049250313e-16 * fabs(W) + 1e-300) {
+        if (fabs(Wn - W) <= fmax(2.0 * 2.220446049250313e-16, rtol) * fabs(W) + 1e-300) {
           W = Wn;
           conv = true;
           break;
@@ -390,8 +390,9 @@ static __device__ __noinline__ double W_tm_brent(double xi, double eta, int max_
   iters = it32;
   if (f0 * fhi > 0.0) return __longlong_as_double(0x7ff8000000000000LL);
   int it64 = 0;
-  const double W = brent_cubic<double>(cc.c1, cc.c2, cc.c3, 0.0, hi, f0, fhi,
-                                       max_iter - it32, 2.220446049250313e-16, 1e-300, it64, conv);
+  // tolerance 2 eps |b| + 1e-300, or rtol |b| for a caller's larger relative tolerance
+  const double W = brent_cubic<double>(cc.c1, cc.c2, cc.c3, 0.0, hi, f0, fhi, max_iter - it32,
+                                       fmax(2.220446049250313e-16, 0.5 * rtol), 1e-300, it64, conv);
   iters = it32 + it64;
   return W;
 }
@@ -448,7 +449,7 @@ __device__ __forceinline__ int con2prim(const Params& p, const double U[5], Prim
     ginv = om * lor;
     omg = b2 * recip_nr(1.0 + ginv);  // = b2 gamma / (gamma + 1)
   } else if (p.eos == 0) {
-    const double w = w_ideal_newton(p.alpha, xi, eta, p.max_iter, iters, conv);
+    const double w = w_ideal_newton(p.alpha, xi, eta, p.max_iter, p.c2p_rtol, iters, conv);
     const double w2 = w * w;
     // beta = 2w/(1 + w^2), 1/gamma = (1 - w^2)/(1 + w^2), gamma from the same division
     const double ap = 1.0 + w2, am = 1.0 - w2;
@@ -460,7 +461,8 @@ __device__ __forceinline__ int con2prim(const Params& p, const double U[5], Prim
     lor = t * ap * ap;
     conv = conv && dbits(w) > 0 && dbits(w) < dbits(1.0);  // 0 < w < 1
   } else {
-    Wl = (p.c2p == 0) ? W_tm_closed_form(xi, eta) : W_tm_brent(xi, eta, p.max_iter, iters, conv);
+    Wl = (p.c2p == 0) ? W_tm_closed_form(xi, eta)
+                      : W_tm_brent(xi, eta, p.max_iter, p.c2p_rtol, iters, conv);
     conv = conv && dbits(Wl) >= 0 && finite_bits(Wl);  // Wl >= 0 and finite
     const double q = Wl + 1.0;  // gamma^2
     ginv = rsqrt(q);

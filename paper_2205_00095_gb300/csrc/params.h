@@ -54,6 +54,7 @@ struct Params {
   double gamma_ad, alpha;    // Gamma, Gamma / (Gamma - 1)
   int c2p;                   // 0 closed form, 1 iterative (resolved)
   int max_iter;
+  double c2p_rtol;           // > 0: the iterative solvers also stop at this relative step
   int flux;                  // 0 LLF, 1 HLL
   int bc[3][2];              // 0 periodic, 1 Dirichlet, 2 outflow
   double ghost[3][2][5];     // Dirichlet ghost as (rho, u, P)

@@ -127,6 +127,28 @@ def test_con2prim_hot_ultrarelativistic_states(lib, eos, G):
     assert (np.abs(Wg[4] - Wo[4]) / Wo[4] / kappa).max() < 1e-9
 
 
+@pytest.mark.parametrize("eos", ["ideal", "tm"])
+def test_con2prim_relative_tolerance(lib, eos):
+    """c2p_rtol = 1e-6: every recovery converges in no more iterations than at the default
+    rules, and the velocity agrees with the oracle's (same tolerance) to 10 rtol gamma^2."""
+    n = 4000
+    spec = dict(dim=1, degree=0, n_elem=[n], eos=eos, gamma_ad=4.0 / 3.0, c2p="iterative")
+    W = wl.random_primitive_states(n, seed=42)[:, :, None]
+    Uo = oracle.prim2cons(spec, W)
+    s0, s1 = solver(spec), solver(dict(spec, c2p_rtol=1e-6))
+    _, it0 = s0.con2prim(to_dev(Uo), with_iters=True)
+    Wg, it1 = s1.con2prim(to_dev(Uo), with_iters=True)
+    status, st = s1.stats()
+    assert status == 0 and st["c2p_nonconverged"] == 0
+    assert float(it1.float().mean()) <= float(it0.float().mean())
+    Wo, _, sto = oracle.con2prim(dict(spec, c2p_rtol=1e-6), Uo)
+    assert sto["c2p_nonconverged"] == 0
+    Wg = Wg.cpu().numpy()
+    g2 = 1.0 / (1.0 - (Wo[1:4] ** 2).sum(0))
+    dv = np.linalg.norm(Wg[1:4] - Wo[1:4], axis=0) / np.maximum(np.linalg.norm(Wo[1:4], axis=0), 1e-300)
+    assert (dv / g2).max() < 1e-5
+
+
 def test_con2prim_invalid_and_cap(lib):
     spec = dict(dim=1, degree=0, n_elem=[5], eos="tm", gamma_ad=5.0 / 3.0, c2p="iterative")
     U = np.array([[-1.0, 1.0, 1.0, np.nan, 1.0],

@@ -57,6 +57,7 @@ def base_spec():
     # 2^30 elements or more: the kernels divide element and face indices in 32 bits
     dict(n_elem=[1 << 15, 1 << 15]), dict(dim=1, n_elem=[1 << 30]),
     dict(dim=3, n_elem=[1 << 10, 1 << 10, 1 << 10]),
+    dict(c2p_rtol=-1e-6), dict(c2p_rtol=1.0), dict(c2p_rtol=float("nan")),
 ])
 def test_invalid_configuration_rejected_on_host(lib, bad):
     spec = base_spec()

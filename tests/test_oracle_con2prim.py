@@ -186,3 +186,20 @@ def test_iteration_cap_counts_nonconvergence():
     U = exact_cons("tm", 5.0 / 3.0, W)
     _, it, st = oracle.con2prim(spec_for("tm", "iterative", 3), U)
     assert st["c2p_nonconverged"] > 0 and it.max() == 3
+
+
+@pytest.mark.parametrize("eos,rtol", [("ideal", 1e-6), ("tm", 1e-6), ("tm", 1e-9)])
+def test_relative_tolerance_stops_earlier_within_it(moderate_box, eos, rtol):
+    """c2p_rtol > 0: the iterative solvers stop once Newton's step or Brent's bracket is within
+    rtol of the iterate, in fewer iterations, and the recovered velocity stays within rtol of
+    the exact one (Newton's last step squares its error; Brent's bracket holds the root)."""
+    W, U = moderate_box
+    spec = spec_for(eos, "iterative")
+    Wr0, it0, _ = oracle.con2prim(spec, U[eos])
+    Wr, it, st = oracle.con2prim(dict(spec, c2p_rtol=rtol), U[eos])
+    assert st["c2p_nonconverged"] == 0
+    assert np.all(it <= it0) and it.mean() < it0.mean()
+    # W = gamma^2 - 1 (TM) or w (ideal) within rtol: |v| within rtol (times gamma^2 for TM)
+    g2 = 1.0 / (1.0 - (W[1:4] ** 2).sum(0))
+    assert (vel_err(Wr, W) / g2).max() < 10.0 * rtol
+    assert vel_err(Wr0, W).max() < 2e-13
