@@ -85,6 +85,7 @@ extern "C" {
 /* arithmetic of the basis contractions */
 #define DGSRHD_PREC_FP64 0
 #define DGSRHD_PREC_SPLIT 1      /* split-precision tensor-core contractions, FP64 elsewhere */
+#define DGSRHD_PREC_3XTF32 DGSRHD_PREC_SPLIT /* the same: its products are 3xTF32 */
 
 typedef struct dgsrhd_config {
   int32_t dim;                 /* 1, 2 or 3 */

@@ -24,7 +24,7 @@ EOS = {"ideal": 0, "tm": 1, "taub_matthews": 1}
 C2P = {"analytic": 0, "iterative": 1, "default": 2}
 FLUX = {"llf": 0, "hll": 1, "hllc": 2}
 BC = {"periodic": 0, "dirichlet": 1, "outflow": 2, "reflect": 3}
-PRECISION = {"fp64": 0, "split": 1}
+PRECISION = {"fp64": 0, "split": 1, "3xtf32": 1}
 NODES = {"gl": 0, "gll": 1}
 KERNEL_KINDS = ("volume", "face", "update", "enforce", "pointwise", "vjp")
 
