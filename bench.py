@@ -350,7 +350,7 @@ def ours(args, rank, world, local_rank):
         split = {"value": world * ndof * args.steps * stages / (sms * 1e-3), "unit": UNIT,
                  "ms_per_step": sms / args.steps, "speedup_vs_fp64": ms / sms,
                  "l1_rel_vs_fp64": l1, **exact, "device_status": sstatus,
-                 "contractions": "3xTF32 mma.sync m16n8k8, FP32 accumulation, deviation form",
+                 "contractions": "volume term and traces 3xTF32 mma.sync m16n8k8 with FP32 accumulation, lift as FP32 FMAs, deviation form",
                  "kernel_ms_per_launch": {k: round(v[0] / max(v[1], 1), 4) for k, v in sk.items() if v[1]}}
         ss.close()
 

@@ -84,8 +84,10 @@ extern "C" {
 
 /* arithmetic of the basis contractions */
 #define DGSRHD_PREC_FP64 0
-#define DGSRHD_PREC_SPLIT 1      /* split-precision tensor-core contractions, FP64 elsewhere */
-#define DGSRHD_PREC_3XTF32 DGSRHD_PREC_SPLIT /* the same: its products are 3xTF32 */
+#define DGSRHD_PREC_SPLIT 1      /* split precision: the volume term and face traces as 3xTF32
+                                    tensor-core products and the lift as FP32 FMAs, all on
+                                    deviations from a per-element reference; FP64 elsewhere */
+#define DGSRHD_PREC_3XTF32 DGSRHD_PREC_SPLIT /* the same */
 
 typedef struct dgsrhd_config {
   int32_t dim;                 /* 1, 2 or 3 */
