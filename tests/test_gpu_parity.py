@@ -263,6 +263,11 @@ def test_enforce(lib, dim, degree, n):
     (lambda c2p: dict(wl.riemann_1d(2, n=96, degree=1), limiter="minmod", limiter_alpha=0.0), "iterative"),
     (lambda c2p: dict(wl.tm_blast("tm", n=96, degree=2), limiter="minmod"), "iterative"),
     (lambda c2p: dict(wl.kh_single(nx=12, ny=24, degree=2), limiter="minmod", limiter_alpha=0.0), "iterative"),
+    # both limiters in 3D (every element limited at M = 0: extrema everywhere in random data)
+    (lambda c2p: dict(wl.smooth_random(3, [5, 6, 4], 2, eos="tm", flux="hllc", c2p=c2p, seed=8),
+                      limiter="minmod", limiter_alpha=0.0), "iterative"),
+    (lambda c2p: dict(wl.smooth_random(3, [5, 6, 4], 2, eos="tm", flux="hllc", c2p=c2p, seed=8),
+                      limiter=True, limiter_alpha=0.0), "iterative"),
 ])
 def test_step_one_and_hundred(lib, spec_fn, c2p):
     spec = spec_fn(c2p)
