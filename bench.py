@@ -436,8 +436,9 @@ def ours(args, rank, world, local_rank):
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": workload_desc(spec), "dof": ndof, "stages_per_step": stages,
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
-                       "l2": "inputs larger than L2 (state 168 MB + scratch)",
-                       "precision": "fp64"},
+                       "l2": f"inputs larger than L2 (state {40 * ndof / 1e6:.0f} MB + scratch)",
+                       "precision": "fp64",
+                       **({"seed": spec["seed"]} if "seed" in spec else {})},
             "roofline": roofline, "kernel_shares": shares,
             "split_precision": split,
             "adjoint": adj,
