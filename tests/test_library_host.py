@@ -89,3 +89,26 @@ def test_linear_wave_order_fit_recovers_a_known_order():
     dx = np.array([0.2, 0.1, 0.05, 0.025])
     p2, slope = linear_waves.fit_order(dx, 3e-9 + 2.0 * dx ** 3)
     assert abs(p2 - 3.0) < 1e-3 and slope > 2.8
+
+
+def test_checkpoint_round_trip(tmp_path):
+    """save/load keep the state's bits, the spec, the time and the step count; a file that is
+    not a checkpoint is refused."""
+    import torch
+
+    import workloads as wl
+    from paper_2205_00095_gb300 import checkpoint
+    spec = wl.kh_single(nx=4, ny=8, degree=2)
+    E, Nn = wl.shape(spec)
+    U = torch.from_numpy(wl.random_conserved_cells(E, Nn, seed=3))
+    p = tmp_path / "state.pt"
+    checkpoint.save(str(p), spec, U, t=0.125, step=7)
+    d = checkpoint.load(str(p))
+    assert torch.equal(d["U"], U) and d["U"].dtype == torch.float64
+    assert d["t"] == 0.125 and d["step"] == 7
+    assert d["spec"]["n_elem"] == spec["n_elem"] and d["spec"]["name"] == "kh_single"
+    torch.save({"not": "a checkpoint"}, str(tmp_path / "other.pt"))
+    with pytest.raises(ValueError):
+        checkpoint.load(str(tmp_path / "other.pt"))
+    with pytest.raises(ValueError):
+        checkpoint.save(str(p), spec, U.float())
