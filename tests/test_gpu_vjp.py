@@ -3,6 +3,8 @@ differences of the FP64 oracle: the RHS, con2prim, the frozen-factor physicality
 the gradient of the transverse kinetic energy after a checkpointed SSPRK3 rollout of the
 Kelvin-Helmholtz set-up with respect to the perturbation amplitude and the nodal initial v_x.
 Tolerance: 1e-6 relative (central differences with h = 1e-6)."""
+import os
+
 import numpy as np
 import pytest
 import torch
@@ -297,3 +299,38 @@ def test_limited_stage_vjp_is_the_transpose_of_the_frozen_stage(gpu_lib, spec, s
         lhs_n = float((Zb * a_n * Ln).sum())
         rhs_n = float((Unb.cpu().numpy() * V).sum())
         assert abs(lhs_n - rhs_n) <= 1e-10 * max(abs(lhs_n), abs(rhs_n))
+
+
+@pytest.mark.skipif(os.environ.get("DGSRHD_FULL_ADJOINT") != "1",
+                    reason="full-size check (two 200-step oracle runs, minutes of CPU): "
+                           "set DGSRHD_FULL_ADJOINT=1")
+def test_full_size_rollout_gradient_against_oracle_differences(gpu_lib):
+    """The benchmark's adjoint configuration itself: KH 128 x 256, p = 3, 200 SSPRK3 steps with a
+    checkpoint every 20; dJ/dA from the checkpointed adjoint against central differences of the
+    FP64 oracle (h = 1e-6 A), and the objective itself against the oracle's."""
+    from paper_2205_00095_gb300 import adjoint
+
+    spec = wl.kh2d(nx=128, ny=256, degree=3)
+    s = solver(spec)
+    spec["dt"] = s.cfl_dt(0.2)
+    nsteps, every, A = 200, 20, 0.01
+    X = s.node_coords()
+    W0 = wl.kh2d_ic(spec, X, amplitude=A)
+    U0 = s.initial_state(W0).requires_grad_(True)
+    J = adjoint.transverse_kinetic_energy(s, adjoint.rollout(s, U0, spec["dt"], nsteps, every))
+    J.backward()
+    torch.cuda.synchronize()
+    Ubar0 = U0.grad.cpu().numpy()
+    dW = np.zeros_like(W0)
+    dW[2] = wl.kh2d_ic(spec, X, amplitude=1.0)[2]
+    h = 1e-6
+    tang = (s.initial_state(W0 + h * dW).cpu().numpy() - s.initial_state(W0 - h * dW).cpu().numpy()) / (2 * h)
+    g_adj = float((Ubar0 * tang).sum())
+    hA = 1e-6 * A
+    Jp = oracle_objective(spec, A + hA, nsteps=nsteps)
+    Jm = oracle_objective(spec, A - hA, nsteps=nsteps)
+    g_fd = (Jp - Jm) / (2 * hA)
+    print(f"\nfull-size dJ/dA: adjoint {g_adj:.10e}, oracle differences {g_fd:.10e}, "
+          f"rel {abs(g_adj - g_fd) / abs(g_fd):.2e}; J {float(J):.10e}")
+    assert abs(float(J) - 0.5 * (Jp + Jm)) <= 1e-9 * abs(float(J))
+    assert abs(g_adj - g_fd) <= 1e-6 * abs(g_fd), (g_adj, g_fd)
