@@ -5,7 +5,9 @@ The paper's grid: 25 Lorentz factors log-spaced in [1, 100] x 25 pressures log-s
 [1e5, 1e10] N/m^2, D = 1 kg/m^3, c = 3e8 m/s (here in units c = 1); each primitive state goes
 prim -> cons -> prim and the relative error of the recovered velocity is recorded.  Timings use
 the paper's batch of 10^3 cells x 27 points per grid state and a large batch (the whole grid
-tiled to 2^24 recoveries) that fills the GPU.
+tiled to 2^24 recoveries) that fills the GPU.  The iterations the iterative solvers need to
+match the closed forms' accuracy (the paper's Fig. 3) come from reruns with iteration caps
+1, 2, ... (the caps count the FP32 and FP64 phases together).
 
     python -m paper_2205_00095_gb300.c2p_study [--reps R]   (prints one JSON object)
 """
@@ -47,6 +49,33 @@ def accuracy(eos: str, c2p: str, max_iter: int = 0, gamma_ad: float = 5.0 / 3.0)
     v = Wf[1]
     err = np.where(v > 0, np.abs(Wr[1] - v) / np.where(v > 0, v, 1.0), np.abs(Wr[1]))
     return err, it.cpu().numpy()[:, 0], lor
+
+
+def iterations_to_parity(eos: str, kmax: int = 40):
+    """Per grid state the smallest iteration cap at which the iterative solver's velocity error
+    is no larger than the closed form's (the paper's Fig. 3); -1 where no cap up to kmax gets
+    there, -2 where the closed form recovers the velocity exactly.  Returns (need, lor)."""
+    err_a, _, lor = accuracy(eos, "analytic")
+    need = np.where(err_a == 0.0, -2, -1)
+    for k in range(1, kmax + 1):
+        err_k, _, _ = accuracy(eos, "iterative", max_iter=k)
+        hit = (need == -1) & (err_k <= err_a)
+        need[hit] = k
+    return need, lor
+
+
+def parity_summary(need, lor) -> dict:
+    """Median and quartiles over the pressures at each Lorentz factor, and the extremes."""
+    gam = np.unique(lor)
+    rows = []
+    for g in gam:
+        k = need[(lor == g) & (need > 0)]
+        rows.append([float(g)] + ([float(np.median(k)), float(np.percentile(k, 25)),
+                                   float(np.percentile(k, 75))] if k.size else [None] * 3))
+    ok = need[need > 0]
+    return {"by_gamma_median_q1_q3": rows, "max": int(ok.max()) if ok.size else None,
+            "min": int(ok.min()) if ok.size else None,
+            "analytic_exact_states": int((need == -2).sum()), "unreached": int((need == -1).sum())}
 
 
 def throughput(eos: str, c2p: str, batch: int, reps: int = 20, gamma_ad: float = 5.0 / 3.0):
@@ -110,6 +139,8 @@ def study(reps: int = 20) -> dict:
         pst = per_state_throughput(eos, c2p)
         res[key]["recoveries_per_s_27000_per_state_median"] = float(np.median(pst))
         res[key]["recoveries_per_s_27000_per_state_min_max"] = [float(pst.min()), float(pst.max())]
+    for eos in ("ideal", "tm"):
+        res[f"{eos}_iterations_to_parity"] = parity_summary(*iterations_to_parity(eos))
     for eos in ("ideal", "tm"):
         a = res[f"{eos}_analytic"]["recoveries_per_s_batch_2^24"]
         i = res[f"{eos}_iterative"]["recoveries_per_s_batch_2^24"]

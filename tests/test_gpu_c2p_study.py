@@ -4,6 +4,7 @@ grid, prim -> cons -> prim, relative error of the recovered velocity
 import json
 import os
 
+import numpy as np
 import pytest
 
 pytestmark = pytest.mark.gpu
@@ -26,3 +27,27 @@ def test_gpu_throughput_is_measured(gpu_lib):
     from paper_2205_00095_gb300 import c2p_study
     r = c2p_study.throughput("ideal", "iterative", 1 << 20, reps=3)
     assert r > 1e9
+
+
+def test_iterations_to_parity(gpu_lib):
+    """The paper's Fig. 3 on GB300: iteration caps 1, 2, ... until the iterative solver's velocity
+    error is no larger than the closed form's.  Every state whose closed-form error is above the
+    rounding level gets there, the ideal Newton in fewer than 10 iterations (as the paper
+    reports) and more of them at higher Lorentz factors.  The Taub-Matthews closed form is at
+    the rounding level everywhere on this grid, so there parity means reaching it: Brent (FP32
+    phase included) gets there on most states, within 20 iterations."""
+    from paper_2205_00095_gb300 import c2p_study
+    for eos, kmax in (("ideal", 9), ("tm", 20)):
+        err_a, _, lor = c2p_study.accuracy(eos, "analytic")
+        need, _ = c2p_study.iterations_to_parity(eos, kmax=40)
+        # a few ulps: below it both solvers sit at the rounding level
+        above = err_a > 4e-15
+        assert np.all(need[above] > 0), (eos, np.sort(err_a[above & (need <= 0)]))
+        reached = need > 0
+        assert reached.sum() >= 0.8 * (need != -2).sum(), (eos, reached.sum())
+        assert need[reached].max() <= kmax, (eos, need[reached].max())
+        if eos == "ideal":
+            assert above.sum() > 100
+            k_low = np.median(need[reached & (lor < 3)])
+            k_high = np.median(need[reached & (lor > 30)])
+            assert k_high > k_low
