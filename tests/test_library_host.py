@@ -112,3 +112,16 @@ def test_checkpoint_round_trip(tmp_path):
         checkpoint.load(str(tmp_path / "other.pt"))
     with pytest.raises(ValueError):
         checkpoint.save(str(p), spec, U.float())
+
+
+def test_parity_summary_statistics():
+    """Host logic of the con2prim study: per-Lorentz-factor median and quartiles over the states
+    that reached parity, extremes, and the counts of exact and unreached states."""
+    from paper_2205_00095_gb300 import c2p_study
+    lor = np.repeat([1.0, 10.0, 100.0], 4)
+    need = np.array([-2, -2, -2, -2, 3, 4, 5, 6, 8, 8, -1, 9])
+    s = c2p_study.parity_summary(need, lor)
+    assert s["by_gamma_median_q1_q3"][0] == [1.0, None, None, None]
+    assert s["by_gamma_median_q1_q3"][1] == [10.0, 4.5, 3.75, 5.25]
+    assert s["by_gamma_median_q1_q3"][2][:2] == [100.0, 8.0]
+    assert (s["min"], s["max"], s["analytic_exact_states"], s["unreached"]) == (3, 9, 4, 1)
