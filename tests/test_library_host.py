@@ -125,3 +125,26 @@ def test_parity_summary_statistics():
     assert s["by_gamma_median_q1_q3"][1] == [10.0, 4.5, 3.75, 5.25]
     assert s["by_gamma_median_q1_q3"][2][:2] == [100.0, 8.0]
     assert (s["min"], s["max"], s["analytic_exact_states"], s["unreached"]) == (3, 9, 4, 1)
+
+
+def test_make_config_maps_every_field():
+    """The binding's spec -> dgsrhd_config map: names of the enumerations, defaults, and the
+    fields added over time (nodes, limiter, limiter_alpha, c2p_rtol)."""
+    spec = dict(dim=2, degree=2, n_elem=[3, 5], lo=[-1.0, 0.0], hi=[1.0, 2.0], eos="tm",
+                c2p="iterative", c2p_max_iter=17, c2p_rtol=1e-9, flux="hllc", rk_stages=2,
+                bc=[("reflect", "outflow"), ("periodic", "periodic")],
+                bc_state=[[(1.0, 0.1, 0.0, 0.0, 1.0), (0.5, 0.0, 0.0, 0.0, 0.4)]] * 2,
+                enforce=False, precision="3xtf32", nodes="gll", limiter="minmod",
+                limiter_alpha=2.5)
+    c = _lib.make_config(spec)
+    assert (c.dim, c.degree, c.n_elem[0], c.n_elem[1], c.n_elem[2]) == (2, 2, 3, 5, 1)
+    assert (c.lo[0], c.hi[1], c.eos, c.c2p, c.c2p_max_iter) == (-1.0, 2.0, 1, 1, 17)
+    assert (c.c2p_rtol, c.flux, c.rk_stages) == (1e-9, 2, 2)
+    assert (c.bc[0][0], c.bc[0][1], c.bc[1][0]) == (3, 2, 0)
+    assert (c.bc_state[0][1][4], c.enforce, c.precision, c.nodes) == (0.4, 0, 1, 1)
+    assert (c.limiter, c.limiter_alpha) == (2, 2.5)
+    d = _lib.make_config(dict(dim=1, degree=0, n_elem=[4]))
+    assert (d.eos, d.c2p, d.flux, d.rk_stages, d.enforce, d.precision) == (0, 2, 0, 3, 1, 0)
+    assert (d.limiter, d.c2p_rtol, d.nodes) == (0, 0.0, 0)
+    for name, code in (("moe", 1), ("scaling", 1), (True, 1), (False, 0), (None, 0)):
+        assert _lib.make_config(dict(dim=1, degree=1, n_elem=[4], limiter=name)).limiter == code
