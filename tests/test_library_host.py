@@ -148,3 +148,27 @@ def test_make_config_maps_every_field():
     assert (d.limiter, d.c2p_rtol, d.nodes) == (0, 0.0, 0)
     for name, code in (("moe", 1), ("scaling", 1), (True, 1), (False, 0), (None, 0)):
         assert _lib.make_config(dict(dim=1, degree=1, n_elem=[4], limiter=name)).limiter == code
+
+
+@pytest.mark.parametrize("spec", [
+    dict(dim=2, degree=2, n_elem=[3, 5], eos="tm", c2p="iterative", c2p_rtol=1e-9, flux="hllc",
+         rk_stages=2, bc=[("reflect", "outflow"), ("periodic", "periodic")],
+         bc_state=[[(1.0, 0.1, 0.0, 0.0, 1.0), (0.5, 0.0, 0.0, 0.0, 0.4)]] * 2,
+         nodes="gll", limiter="minmod", limiter_alpha=2.5),
+    dict(dim=1, degree=0, n_elem=[4]),
+    dict(dim=3, degree=1, n_elem=[2, 3, 4], eos="ideal", gamma_ad=1.4, c2p="analytic",
+         flux="hll", limiter=True, enforce=False),
+])
+def test_oracle_and_library_read_a_spec_alike(spec):
+    """The two bindings (they share no code) turn one problem description into the same
+    configuration, so every parity test compares the same problem."""
+    import oracle
+    a, b = _lib.make_config(spec), oracle.make_config(spec)
+    for f in ("dim", "degree", "eos", "gamma_ad", "c2p", "c2p_max_iter", "c2p_rtol", "flux",
+              "rk_stages", "enforce", "nodes", "limiter", "limiter_alpha"):
+        assert getattr(a, f) == getattr(b, f), f
+    for k in range(3):
+        assert a.n_elem[k] == b.n_elem[k] and a.lo[k] == b.lo[k] and a.hi[k] == b.hi[k]
+        for s in range(2):
+            assert a.bc[k][s] == b.bc[k][s]
+            assert list(a.bc_state[k][s]) == list(b.bc_state[k][s])
