@@ -3,14 +3,16 @@
  *
  * C ABI of the hot path of arXiv 2205.00095 (Glines et al., "A Robust, Performance-Portable
  * Discontinuous Galerkin Method for Relativistic Hydrodynamics"): conserved-to-primitive
- * recovery at the nodes, the nodal DG right-hand side with LLF/HLL face fluxes, the
- * physicality-enforcing operator, SSP Runge-Kutta steps, and the vector-Jacobian product of
- * the right-hand side.  Units c = 1.
+ * recovery at the nodes, the nodal DG right-hand side with LLF/HLL/HLLC face fluxes, the
+ * limiters and the physicality-enforcing operator, SSP Runge-Kutta steps, a split-precision
+ * form, and the vector-Jacobian products of the right-hand side and of whole stages.
+ * Units c = 1.
  *
  * Data layout (every state array):
  *   contiguous FP64, structure of arrays [var][elem][node];
  *   elem = ex + nx * (ey + ny * ez)              (x fastest)
- *   node = a + N * (b + N * c), N = degree + 1   (tensor Gauss-Legendre nodes, x fastest)
+ *   node = a + N * (b + N * c), N = degree + 1   (tensor nodes, Gauss-Legendre by default or
+ *                                                 Gauss-Lobatto-Legendre, x fastest)
  *   conserved U: var = (D, S_x, S_y, S_z, tau), tau = E - D   (Eq. primitive_to_conserved)
  *   primitive W: var = (rho, v_x, v_y, v_z, P)                 (Sec. 2.1)
  * Five variables are carried in every dimension.
@@ -24,6 +26,9 @@
  * DGSRHD_ECUDA.  Problems found on the device (non-converged or invalid con2prim,
  * inadmissible element means) are counted in device counters and reported by
  * dgsrhd_get_stats, which synchronises the stream.  No kernel traps.
+ *
+ * Threads: a context is used by one host thread at a time (its scratch, counters and cached
+ * CUDA graphs are not guarded); distinct contexts are independent.
  */
 #ifndef DGSRHD_H
 #define DGSRHD_H
