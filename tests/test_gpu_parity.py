@@ -698,3 +698,19 @@ def test_runs_are_bitwise_reproducible(lib, spec_fn):
     assert torch.equal(out[0], out[1])
     for k in ("c2p_iters_total", "enforced_cells", "limited_cells", "face_guard_hits"):
         assert stats[0][k] == stats[1][k]
+
+
+def test_zero_steps_are_a_no_op(lib):
+    """nsteps = 0: the state keeps its bits and no kernel is launched (device and host paths)."""
+    spec = wl.kh_single(nx=6, ny=12, degree=2)
+    s = solver(spec, stream=torch.cuda.Stream())
+    U = gpu_state(s, spec)
+    V = U.clone()
+    n0 = s.kernel_launches()
+    s.step(U, s.cfl_dt(0.2), 0)
+    Uh = V.cpu().pin_memory()
+    Wh = Uh.clone()
+    s.step_host(Uh, s.cfl_dt(0.2), 0)
+    s.synchronize()
+    assert torch.equal(U, V) and torch.equal(Uh, Wh)
+    assert s.kernel_launches() == n0
