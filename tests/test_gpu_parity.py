@@ -714,3 +714,24 @@ def test_zero_steps_are_a_no_op(lib):
     s.synchronize()
     assert torch.equal(U, V) and torch.equal(Uh, Wh)
     assert s.kernel_launches() == n0
+
+
+def test_newton_recovers_extreme_pressures(lib):
+    """Sec. 3.3: the iterative ideal solver keeps working at very high pressures (P/rho up to
+    1e22, where the closed form fails): velocity to 1e-14 and pressure to 1e-14 of its
+    conditioning, all converged, as in the oracle."""
+    th = np.repeat([1e16, 1e18, 1e20, 1e22], 3)
+    gam = np.tile([1.5, 10.0, 50.0], 4)
+    v = np.sqrt(1.0 - 1.0 / gam ** 2)
+    W = np.stack([np.ones_like(th), v, 0 * th, 0 * th, th])[:, :, None]
+    spec = dict(dim=1, degree=0, n_elem=[th.size], eos="ideal", gamma_ad=5.0 / 3.0,
+                c2p="iterative")
+    U = oracle.prim2cons(spec, W)
+    s = solver(spec)
+    Wg = s.con2prim(to_dev(U)).cpu().numpy()
+    status, st = s.stats()
+    assert status == 0 and st["c2p_nonconverged"] == 0
+    assert (np.abs(Wg[1] - W[1]) / W[1]).max() < 1e-14
+    # P = (Gamma - 1)(E - S.v - rho) cancels by about gamma^2: its conditioning (tau + |S|)/P
+    kappa = (U[4] + np.linalg.norm(U[1:4], axis=0)) / W[4]
+    assert (np.abs(Wg[4] - W[4]) / W[4] / kappa).max() < 1e-14

@@ -203,3 +203,22 @@ def test_relative_tolerance_stops_earlier_within_it(moderate_box, eos, rtol):
     g2 = 1.0 / (1.0 - (W[1:4] ** 2).sum(0))
     assert (vel_err(Wr, W) / g2).max() < 10.0 * rtol
     assert vel_err(Wr0, W).max() < 2e-13
+
+
+@pytest.mark.parametrize("theta", [1e16, 1e18, 1e20, 1e22])
+@pytest.mark.parametrize("gam", [1.5, 10.0])
+def test_extreme_pressure_closed_form_fails_newton_does_not(theta, gam):
+    """Sec. 3.3: at very high pressures the ideal closed form runs into negative radicands and
+    loses the velocity, while the iterative solver does not.  Here from P/rho = 1e16 on, the
+    closed form returns NaN (flagged as not converged) or a velocity off by more than 1e-9;
+    Newton recovers v to 1e-14 and P to 1e-12."""
+    v = np.sqrt(1.0 - 1.0 / gam ** 2)
+    W = np.array([[1.0], [v], [0.0], [0.0], [theta]])
+    U = exact_cons("ideal", 5.0 / 3.0, W)
+    Wa, _, sta = oracle.con2prim(spec_for("ideal", "analytic"), U)
+    ea = vel_err(Wa, W)[0]
+    assert not (ea <= 1e-9), ea
+    Wi, _, sti = oracle.con2prim(spec_for("ideal", "iterative"), U)
+    assert sti["c2p_nonconverged"] == 0
+    assert vel_err(Wi, W)[0] < 1e-14
+    assert abs(Wi[4, 0] - theta) / theta < 1e-12
