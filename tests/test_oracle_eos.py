@@ -67,3 +67,18 @@ def test_prim2cons_matches_definition(eos):
             scale = abs(r) if v in (0, 4) else float(mp.sqrt(ref[1] ** 2 + ref[2] ** 2 + ref[3] ** 2))
             # 1 - v^2 carries a relative rounding error of about eps gamma^2
             assert abs(U[v, k] - r) <= 4e-15 * lor2[k] * scale + 1e-300, (k, v, U[v, k], r)
+
+
+def test_taub_matthews_approximates_the_synge_gas():
+    """Sec. 2.2 and Fig. 1: the Taub-Matthews EOS approximates the Synge gas,
+    h = K_3(1/Theta) / K_2(1/Theta) (modified Bessel functions, here exponentially scaled:
+    the scale cancels in the ratio).  It agrees with it to a few per cent across Theta and
+    exactly in both limits (h -> 1 + 5/2 Theta cold, h -> 4 Theta hot)."""
+    from scipy.special import kve
+    th = np.logspace(-3, 3, 601)
+    synge = kve(3, 1.0 / th) / kve(2, 1.0 / th)
+    tm = np.array([oracle.enthalpy(TM, 1.0, t) for t in th])
+    rel = np.abs(tm - synge) / synge
+    assert rel.max() < 0.025
+    assert 0.3 < th[np.argmax(rel)] < 1.0        # the largest gap sits at Theta of order 1
+    assert rel[0] < 1e-5 and rel[-1] < 1e-5
