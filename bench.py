@@ -11,7 +11,13 @@ seconds (the definition of the paper's performance section).
 --gpus N > 1 runs one replica of the workload per rank (torchrun, one GPU each; the method has no
 cross-replica exchange), barrier + synchronize around the timed region, max time over ranks.
 --impl reference times the FP64 CPU oracle on the host cores on a bounded sample of the same
-workload.  One JSON line is printed by rank 0.
+workload.  One JSON line is printed by rank 0.  Besides the FP64 value it carries the split-
+precision form on the same workload (its rate, speed-up and L1 difference from FP64, and on the
+advected wave both L1 errors against the exact solution), the adjoint/forward time ratio of the
+checkpointed Kelvin-Helmholtz rollout, an end-to-end rate through dgsrhd_step_host with the
+state in pinned host memory, the oracle's rate on a sample (cpu_baseline), the dominant
+kernel's roofline, the per-kernel time shares, the kernel launch count and the SM clocks
+sampled during the timed region.
 """
 from __future__ import annotations
 
