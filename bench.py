@@ -152,9 +152,9 @@ def volume_kernel_flops_per_node(spec: dict, mean_iters: float = 0.0) -> float:
     return C2P_FLOPS[(spec["eos"], c2p)](mean_iters) + flux + volume + traces
 
 
-def measured_traffic(kernel: str, workload_name: str):
-    """DRAM bytes (read + write) per launch of `kernel` from the committed ncu capture of this
-    workload, or None when there is none or the kernel sources changed since it was taken."""
+def _capture_record(kernel: str, workload_name: str):
+    """The committed ncu record of `kernel` on this workload, or None when there is none or the
+    kernel sources changed since it was taken."""
     import hashlib
     path = os.path.join(ROOT, "profiles", "dram_traffic_advected_wave_512x512_p3.json")
     if workload_name != "advected_wave" or not os.path.exists(path):
@@ -165,8 +165,19 @@ def measured_traffic(kernel: str, workload_name: str):
         h.update(open(os.path.join(ROOT, f), "rb").read())
     if h.hexdigest() != d["source_sha1"] or kernel not in d["kernels"]:
         return None
-    k = d["kernels"][kernel]
-    return k["dram_bytes_read"] + k["dram_bytes_write"]
+    return d["kernels"][kernel]
+
+
+def measured_traffic(kernel: str, workload_name: str):
+    """DRAM bytes (read + write) per launch of `kernel` from the committed ncu capture."""
+    k = _capture_record(kernel, workload_name)
+    return None if k is None else k["dram_bytes_read"] + k["dram_bytes_write"]
+
+
+def measured_fp64_pipe(kernel: str, workload_name: str):
+    """Fraction of active cycles the FP64 pipe was busy in the committed ncu capture."""
+    k = _capture_record(kernel, workload_name)
+    return None if k is None or "fp64_pipe_busy_pct" not in k else k["fp64_pipe_busy_pct"] / 100.0
 
 
 def load_peaks():
@@ -426,6 +437,7 @@ def ours(args, rank, world, local_rank):
         roofline = {"kernel": "volume_kernel", "bound": "alu", "achieved": achieved,
                     "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
                     "traffic": measured_traffic("volume_kernel", args.workload),
+                    "fp64_pipe_busy_ncu": measured_fp64_pipe("volume_kernel", args.workload),
                     "peak_source": "GB300 nominal dense FP64 1.25 TFLOP/s (DFMA probe measured 1.256)",
                     "algorithmic_flops_per_node": fpn,
                     "avg_launch_ms": avg_s * 1e3}
