@@ -62,6 +62,7 @@ class dgsrhd_stats(ctypes.Structure):
     _fields_ = [(n, ctypes.c_int64) for n in STAT_FIELDS]
 
     def as_dict(self):
+        """The counters as {name: int}."""
         return {n: int(getattr(self, n)) for n in STAT_FIELDS}
 
 
@@ -190,6 +191,7 @@ class DGSRHDError(RuntimeError):
 
 
 def check(fn: str, status: int) -> int:
+    """Raise DGSRHDError unless status is DGSRHD_OK."""
     if status != DGSRHD_OK:
         raise DGSRHDError(fn, status)
     return status

@@ -58,6 +58,7 @@ class _RHS(torch.autograd.Function):
 
 
 def rhs(solver: Solver, U: torch.Tensor) -> torch.Tensor:
+    """R(U) = dU/dt, differentiable in U (its backward is dgsrhd_rhs_vjp)."""
     return _RHS.apply(U, solver)
 
 
@@ -176,6 +177,8 @@ class _Rollout(torch.autograd.Function):
 
 
 def rollout(solver: Solver, U0: torch.Tensor, dt: float, nsteps: int, every: int = 20) -> torch.Tensor:
+    """The state after nsteps SSP-RK steps of size dt from U0 (U0 is not modified),
+    differentiable in U0; the backward keeps a checkpoint every `every` steps."""
     return _Rollout.apply(U0, solver, float(dt), int(nsteps), int(every))
 
 
@@ -223,4 +226,5 @@ class _KineticY(torch.autograd.Function):
 
 
 def transverse_kinetic_energy(solver: Solver, U: torch.Tensor) -> torch.Tensor:
+    """J = sum of (prod_d dx_d/2) w_node rho gamma^2 v_y^2 over all nodes, differentiable in U."""
     return _KineticY.apply(U, solver, node_weights(solver))

@@ -34,6 +34,8 @@ SMALL_MESHES = [(16, 32), (32, 64), (64, 128), (128, 256)]
 
 def measure(nx: int, ny: int, degree: int, flux: str = "hll", steps: int = 50,
             warmup: int = 3) -> dict:
+    """Time `steps` steps of the single-layer Kelvin-Helmholtz problem on an n_x x n_y mesh at
+    basis order `degree` after `warmup` untimed steps; one result dict."""
     wl = _workloads()
     spec = wl.kh_single(nx=nx, ny=ny, degree=degree, flux=flux)
     stream = torch.cuda.Stream()
@@ -61,6 +63,7 @@ def measure(nx: int, ny: int, degree: int, flux: str = "hll", steps: int = 50,
 
 
 def sweep(steps: int = 50, fluxes=("hll", "hllc"), degrees=(0, 1, 2), small: bool = True):
+    """measure() over every flux, degree and mesh (the small meshes first when `small`)."""
     meshes = (SMALL_MESHES if small else []) + PAPER_MESHES
     for flux in fluxes:
         for degree in degrees:

@@ -29,6 +29,7 @@ def _workloads():
 
 
 def run(test: int, n: int = 1024, degree: int = 1, limiter: str = "moe") -> dict:
+    """Run 2D Riemann test 1, 2 or 3 on an n x n mesh to t = 0.8; one result dict."""
     wl = _workloads()
     spec = dict(wl.riemann_2d(test, n=n, degree=degree), limiter=limiter)
     stream = torch.cuda.Stream()

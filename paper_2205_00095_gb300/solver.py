@@ -78,6 +78,7 @@ class Solver:
         self.n_elem, self.n_node = ne.value, nn.value
 
     def close(self):
+        """Free the library context (its scratch and cached graphs); later calls are invalid."""
         if getattr(self, "ctx", None):
             self.lib.dgsrhd_destroy(self.ctx)
             self.ctx = None
@@ -90,22 +91,27 @@ class Solver:
 
     # -- helpers -----------------------------------------------------------------------
     def empty(self) -> torch.Tensor:
+        """An uninitialised state tensor of the context's shape, allocated on its stream."""
         with torch.cuda.stream(self.stream):
             return torch.empty(self.shape, dtype=torch.float64, device=self.device)
 
     def node_coords(self) -> np.ndarray:
+        """Physical node coordinates as a host array, shape (dim, n_elem, n_node)."""
         X = np.zeros((int(self.spec["dim"]), self.n_elem, self.n_node))
         check("dgsrhd_node_coords", self.lib.dgsrhd_node_coords(self.ctx, X.ctypes.data))
         return X
 
     # -- the C ABI ---------------------------------------------------------------------
     def prim2cons(self, W: torch.Tensor, out: torch.Tensor | None = None) -> torch.Tensor:
+        """Conserved state from the primitive (rho, v_x, v_y, v_z, P) at every node."""
         U = self.empty() if out is None else out
         check("dgsrhd_prim2cons", self.lib.dgsrhd_prim2cons(
             self.ctx, _dev_ptr(W, "W", self.shape), _dev_ptr(U, "U", self.shape)))
         return U
 
     def con2prim(self, U: torch.Tensor, with_iters: bool = False):
+        """Primitive (rho, v_x, v_y, v_z, P) at every node by the configured solver; with_iters
+        also returns the iteration count of every node."""
         W = self.empty()
         with torch.cuda.stream(self.stream):
             it = torch.empty(self.shape[1:], dtype=torch.int32, device=self.device) if with_iters else None
@@ -115,12 +121,14 @@ class Solver:
         return (W, it) if with_iters else W
 
     def rhs(self, U: torch.Tensor, out: torch.Tensor | None = None) -> torch.Tensor:
+        """The DG right-hand side R(U) (no physicality operator)."""
         R = self.empty() if out is None else out
         check("dgsrhd_rhs", self.lib.dgsrhd_rhs(self.ctx, _dev_ptr(U, "U", self.shape),
                                                 _dev_ptr(R, "R", self.shape)))
         return R
 
     def enforce(self, U: torch.Tensor, with_s: bool = False):
+        """The physicality operator in place; with_s also returns each element's factor s."""
         with torch.cuda.stream(self.stream):
             s = torch.empty(self.n_elem, dtype=torch.float64, device=self.device) if with_s else None
         check("dgsrhd_enforce", self.lib.dgsrhd_enforce(
@@ -128,11 +136,14 @@ class Solver:
         return (U, s) if with_s else U
 
     def step(self, U: torch.Tensor, dt: float, nsteps: int = 1) -> torch.Tensor:
+        """nsteps SSP-RK steps of size dt in place (limiter and operator after every stage)."""
         check("dgsrhd_step", self.lib.dgsrhd_step(self.ctx, _dev_ptr(U, "U", self.shape),
                                                   float(dt), int(nsteps)))
         return U
 
     def step_host(self, U_host: torch.Tensor, dt: float, nsteps: int = 1) -> torch.Tensor:
+        """As step, with the state in host memory; synchronises the stream.  Pinned memory is
+        read and written by the kernels over the host link, other memory is copied."""
         if U_host.is_cuda or U_host.dtype != torch.float64 or not U_host.is_contiguous() or \
                 tuple(U_host.shape) != tuple(self.shape):
             raise ValueError("U_host must be a contiguous float64 CPU tensor of the state shape")
@@ -141,6 +152,7 @@ class Solver:
         return U_host
 
     def rhs_vjp(self, U: torch.Tensor, R_bar: torch.Tensor, out: torch.Tensor | None = None):
+        """(dR/dU)^T R_bar at U."""
         Ub = self.empty() if out is None else out
         check("dgsrhd_rhs_vjp", self.lib.dgsrhd_rhs_vjp(
             self.ctx, _dev_ptr(U, "U", self.shape), _dev_ptr(R_bar, "R_bar", self.shape),
@@ -148,6 +160,7 @@ class Solver:
         return Ub
 
     def enforce_vjp(self, s: torch.Tensor, Ut_bar: torch.Tensor, out: torch.Tensor | None = None):
+        """Transpose of the operator with the element factors s frozen."""
         Ub = self.empty() if out is None else out
         if not s.is_cuda or s.dtype != torch.float64 or s.numel() != self.n_elem:
             raise ValueError("s must be a float64 CUDA tensor with one factor per element")
@@ -157,6 +170,7 @@ class Solver:
         return Ub
 
     def stage_save_size(self) -> int:
+        """Doubles of the save buffer step_stage fills for stage_vjp."""
         n = ctypes.c_int64()
         check("dgsrhd_stage_save_size", self.lib.dgsrhd_stage_save_size(self.ctx, ctypes.byref(n)))
         return n.value
@@ -164,6 +178,8 @@ class Solver:
     def step_stage(self, Un: torch.Tensor, Uk: torch.Tensor, Uout: torch.Tensor, stage: int,
                    dt: float, s_out: torch.Tensor | None = None,
                    save: torch.Tensor | None = None) -> torch.Tensor:
+        """One Shu-Osher stage into Uout; optionally also the operator's element factors (s_out)
+        and the forward quantities stage_vjp needs (save)."""
         if save is not None and (not save.is_cuda or save.dtype != torch.float64 or
                                  save.numel() < self.stage_save_size()):
             raise ValueError("save must be a float64 CUDA tensor of stage_save_size() doubles")
@@ -177,6 +193,7 @@ class Solver:
     def stage_vjp(self, Uk: torch.Tensor, s: torch.Tensor | None, Z_bar: torch.Tensor,
                   Un_bar: torch.Tensor, Uk_bar: torch.Tensor, stage: int, dt: float,
                   saved: torch.Tensor | None = None):
+        """Reverse of one stage at Uk; Un_bar and Uk_bar accumulate."""
         check("dgsrhd_stage_vjp", self.lib.dgsrhd_stage_vjp(
             self.ctx, _dev_ptr(Uk, "Uk", self.shape), s.data_ptr() if s is not None else None,
             saved.data_ptr() if saved is not None else None,
@@ -184,6 +201,7 @@ class Solver:
             _dev_ptr(Uk_bar, "Uk_bar", self.shape), int(stage), float(dt)))
 
     def con2prim_vjp(self, U: torch.Tensor, W_bar: torch.Tensor, out: torch.Tensor | None = None):
+        """(dU/dW)^{-T} W_bar at the recovered primitive of U."""
         Ub = self.empty() if out is None else out
         check("dgsrhd_con2prim_vjp", self.lib.dgsrhd_con2prim_vjp(
             self.ctx, _dev_ptr(U, "U", self.shape), _dev_ptr(W_bar, "W_bar", self.shape),
@@ -199,6 +217,7 @@ class Solver:
         return out.value
 
     def cfl_dt(self, cfl: float | None = None) -> float:
+        """The time step for a CFL number (default: the spec's 'cfl', else 0.2)."""
         dt = ctypes.c_double()
         check("dgsrhd_cfl_dt", self.lib.dgsrhd_cfl_dt(self.ctx, float(cfl or self.spec.get("cfl", 0.2)),
                                                       ctypes.byref(dt)))
@@ -213,9 +232,11 @@ class Solver:
         return status, st.as_dict()
 
     def kernel_launches(self) -> int:
+        """Kernel launches issued by this context so far."""
         return int(self.lib.dgsrhd_kernel_launches(self.ctx))
 
     def set_profiling(self, enable: bool):
+        """Time every kernel launch with CUDA events (launches are not captured in graphs then)."""
         check("dgsrhd_set_profiling", self.lib.dgsrhd_set_profiling(self.ctx, int(bool(enable))))
 
     def kernel_times(self, reset: bool = True) -> dict:
@@ -243,4 +264,5 @@ class Solver:
         return self.prim2cons(W)
 
     def synchronize(self):
+        """Wait for the context's stream."""
         self.stream.synchronize()
