@@ -27,6 +27,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -70,10 +71,10 @@ class ClockSampler:
              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, gpu_index: int):
+    def __init__(self, gpu_index: int, log_dir: str | None = None):
         self.gpu = gpu_index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{gpu_index}.csv")
+        self.path = os.path.join(log_dir or tempfile.gettempdir(), f"clocks_bench_{gpu_index}.csv")
 
     def __enter__(self):
         try:
@@ -299,7 +300,7 @@ def ours(args, rank, world, local_rank):
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
     barrier()
-    with ClockSampler(local_rank) as clk:
+    with ClockSampler(local_rank, args.clock_log_dir) as clk:
         ev0.record(stream)
         s.step(U, dt, args.steps)
         ev1.record(stream)
@@ -483,6 +484,9 @@ def main():
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end timing")
     ap.add_argument("--no-split", action="store_true", help="skip the split-precision run")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint/forward timing")
+    ap.add_argument("--clock-log-dir", default=None,
+                    help="where the nvidia-smi clock samples of the timed region are written "
+                         "(default: the system temporary directory)")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
