@@ -25,11 +25,29 @@ def _stream_handle(stream) -> int:
     return int(stream.cuda_stream)
 
 
-def _dev_ptr(t: torch.Tensor, name: str, shape=None) -> int:
+def _dev_ptr(t: torch.Tensor, name: str, shape=None, device: torch.device | None = None) -> int:
+    """The device address of t after checking it is a contiguous float64 CUDA tensor of the
+    given shape on the given device: the library dereferences it in its kernels."""
     if not t.is_cuda or t.dtype != torch.float64 or not t.is_contiguous():
         raise ValueError(f"{name} must be a contiguous float64 CUDA tensor")
     if shape is not None and tuple(t.shape) != tuple(shape):
         raise ValueError(f"{name} has shape {tuple(t.shape)}, expected {tuple(shape)}")
+    if device is not None and t.device != device:
+        raise ValueError(f"{name} is on {t.device}, the solver on {device}")
+    return t.data_ptr()
+
+
+def _vec_ptr(t: torch.Tensor | None, name: str, n: int, device: torch.device | None = None,
+             at_least: bool = False) -> int | None:
+    """As _dev_ptr for a flat buffer of n doubles (at least n when at_least); None stays None."""
+    if t is None:
+        return None
+    if not t.is_cuda or t.dtype != torch.float64 or not t.is_contiguous():
+        raise ValueError(f"{name} must be a contiguous float64 CUDA tensor")
+    if t.numel() < n or (t.numel() != n and not at_least):
+        raise ValueError(f"{name} holds {t.numel()} doubles, expected {'at least ' if at_least else ''}{n}")
+    if device is not None and t.device != device:
+        raise ValueError(f"{name} is on {t.device}, the solver on {device}")
     return t.data_ptr()
 
 
@@ -63,6 +81,10 @@ class Solver:
         self.lib = _lib.load()
         self.spec = dict(spec)
         self.device = torch.device(device or "cuda")
+        if self.device.type != "cuda":
+            raise ValueError(f"the solver runs on a CUDA device, not {self.device}")
+        if self.device.index is None:
+            self.device = torch.device("cuda", torch.cuda.current_device())
         self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
         self.cfg = _lib.make_config(spec)
         ctx = ctypes.c_void_p()
@@ -90,6 +112,17 @@ class Solver:
             pass
 
     # -- helpers -----------------------------------------------------------------------
+    def _ptr(self, t: torch.Tensor, name: str) -> int:
+        return _dev_ptr(t, name, self.shape, self.device)
+
+    def _elem_ptr(self, t: torch.Tensor | None, name: str) -> int | None:
+        return _vec_ptr(t, name, self.n_elem, self.device)
+
+    def _save_ptr(self, t: torch.Tensor | None, name: str) -> int | None:
+        if t is None:
+            return None
+        return _vec_ptr(t, name, self.stage_save_size(), self.device, at_least=True)
+
     def empty(self) -> torch.Tensor:
         """An uninitialised state tensor of the context's shape, allocated on its stream."""
         with torch.cuda.stream(self.stream):
@@ -106,7 +139,7 @@ class Solver:
         """Conserved state from the primitive (rho, v_x, v_y, v_z, P) at every node."""
         U = self.empty() if out is None else out
         check("dgsrhd_prim2cons", self.lib.dgsrhd_prim2cons(
-            self.ctx, _dev_ptr(W, "W", self.shape), _dev_ptr(U, "U", self.shape)))
+            self.ctx, self._ptr(W, "W"), self._ptr(U, "U")))
         return U
 
     def con2prim(self, U: torch.Tensor, with_iters: bool = False):
@@ -116,15 +149,15 @@ class Solver:
         with torch.cuda.stream(self.stream):
             it = torch.empty(self.shape[1:], dtype=torch.int32, device=self.device) if with_iters else None
         check("dgsrhd_con2prim", self.lib.dgsrhd_con2prim(
-            self.ctx, _dev_ptr(U, "U", self.shape), _dev_ptr(W, "W", self.shape),
+            self.ctx, self._ptr(U, "U"), self._ptr(W, "W"),
             it.data_ptr() if it is not None else None))
         return (W, it) if with_iters else W
 
     def rhs(self, U: torch.Tensor, out: torch.Tensor | None = None) -> torch.Tensor:
         """The DG right-hand side R(U) (no physicality operator)."""
         R = self.empty() if out is None else out
-        check("dgsrhd_rhs", self.lib.dgsrhd_rhs(self.ctx, _dev_ptr(U, "U", self.shape),
-                                                _dev_ptr(R, "R", self.shape)))
+        check("dgsrhd_rhs", self.lib.dgsrhd_rhs(self.ctx, self._ptr(U, "U"),
+                                                self._ptr(R, "R")))
         return R
 
     def enforce(self, U: torch.Tensor, with_s: bool = False):
@@ -132,12 +165,12 @@ class Solver:
         with torch.cuda.stream(self.stream):
             s = torch.empty(self.n_elem, dtype=torch.float64, device=self.device) if with_s else None
         check("dgsrhd_enforce", self.lib.dgsrhd_enforce(
-            self.ctx, _dev_ptr(U, "U", self.shape), s.data_ptr() if s is not None else None))
+            self.ctx, self._ptr(U, "U"), s.data_ptr() if s is not None else None))
         return (U, s) if with_s else U
 
     def step(self, U: torch.Tensor, dt: float, nsteps: int = 1) -> torch.Tensor:
         """nsteps SSP-RK steps of size dt in place (limiter and operator after every stage)."""
-        check("dgsrhd_step", self.lib.dgsrhd_step(self.ctx, _dev_ptr(U, "U", self.shape),
+        check("dgsrhd_step", self.lib.dgsrhd_step(self.ctx, self._ptr(U, "U"),
                                                   float(dt), int(nsteps)))
         return U
 
@@ -155,18 +188,16 @@ class Solver:
         """(dR/dU)^T R_bar at U."""
         Ub = self.empty() if out is None else out
         check("dgsrhd_rhs_vjp", self.lib.dgsrhd_rhs_vjp(
-            self.ctx, _dev_ptr(U, "U", self.shape), _dev_ptr(R_bar, "R_bar", self.shape),
-            _dev_ptr(Ub, "U_bar", self.shape)))
+            self.ctx, self._ptr(U, "U"), self._ptr(R_bar, "R_bar"),
+            self._ptr(Ub, "U_bar")))
         return Ub
 
     def enforce_vjp(self, s: torch.Tensor, Ut_bar: torch.Tensor, out: torch.Tensor | None = None):
         """Transpose of the operator with the element factors s frozen."""
         Ub = self.empty() if out is None else out
-        if not s.is_cuda or s.dtype != torch.float64 or s.numel() != self.n_elem:
-            raise ValueError("s must be a float64 CUDA tensor with one factor per element")
         check("dgsrhd_enforce_vjp", self.lib.dgsrhd_enforce_vjp(
-            self.ctx, s.data_ptr(), _dev_ptr(Ut_bar, "Ut_bar", self.shape),
-            _dev_ptr(Ub, "U_bar", self.shape)))
+            self.ctx, self._elem_ptr(s, "s"), self._ptr(Ut_bar, "Ut_bar"),
+            self._ptr(Ub, "U_bar")))
         return Ub
 
     def stage_save_size(self) -> int:
@@ -180,14 +211,10 @@ class Solver:
                    save: torch.Tensor | None = None) -> torch.Tensor:
         """One Shu-Osher stage into Uout; optionally also the operator's element factors (s_out)
         and the forward quantities stage_vjp needs (save)."""
-        if save is not None and (not save.is_cuda or save.dtype != torch.float64 or
-                                 save.numel() < self.stage_save_size()):
-            raise ValueError("save must be a float64 CUDA tensor of stage_save_size() doubles")
         check("dgsrhd_step_stage", self.lib.dgsrhd_step_stage(
-            self.ctx, _dev_ptr(Un, "Un", self.shape), _dev_ptr(Uk, "Uk", self.shape),
-            _dev_ptr(Uout, "Uout", self.shape), int(stage), float(dt),
-            s_out.data_ptr() if s_out is not None else None,
-            save.data_ptr() if save is not None else None))
+            self.ctx, self._ptr(Un, "Un"), self._ptr(Uk, "Uk"),
+            self._ptr(Uout, "Uout"), int(stage), float(dt),
+            self._elem_ptr(s_out, "s_out"), self._save_ptr(save, "save")))
         return Uout
 
     def stage_vjp(self, Uk: torch.Tensor, s: torch.Tensor | None, Z_bar: torch.Tensor,
@@ -195,17 +222,17 @@ class Solver:
                   saved: torch.Tensor | None = None):
         """Reverse of one stage at Uk; Un_bar and Uk_bar accumulate."""
         check("dgsrhd_stage_vjp", self.lib.dgsrhd_stage_vjp(
-            self.ctx, _dev_ptr(Uk, "Uk", self.shape), s.data_ptr() if s is not None else None,
-            saved.data_ptr() if saved is not None else None,
-            _dev_ptr(Z_bar, "Z_bar", self.shape), _dev_ptr(Un_bar, "Un_bar", self.shape),
-            _dev_ptr(Uk_bar, "Uk_bar", self.shape), int(stage), float(dt)))
+            self.ctx, self._ptr(Uk, "Uk"), self._elem_ptr(s, "s"),
+            self._save_ptr(saved, "saved"),
+            self._ptr(Z_bar, "Z_bar"), self._ptr(Un_bar, "Un_bar"),
+            self._ptr(Uk_bar, "Uk_bar"), int(stage), float(dt)))
 
     def con2prim_vjp(self, U: torch.Tensor, W_bar: torch.Tensor, out: torch.Tensor | None = None):
         """(dU/dW)^{-T} W_bar at the recovered primitive of U."""
         Ub = self.empty() if out is None else out
         check("dgsrhd_con2prim_vjp", self.lib.dgsrhd_con2prim_vjp(
-            self.ctx, _dev_ptr(U, "U", self.shape), _dev_ptr(W_bar, "W_bar", self.shape),
-            _dev_ptr(Ub, "U_bar", self.shape)))
+            self.ctx, self._ptr(U, "U"), self._ptr(W_bar, "W_bar"),
+            self._ptr(Ub, "U_bar")))
         return Ub
 
     def mean_square_velocity(self, U: torch.Tensor, axis: int = 1) -> float:
@@ -213,7 +240,7 @@ class Solver:
         evaluated by the library; synchronises the solver's stream."""
         out = ctypes.c_double()
         check("dgsrhd_mean_square_velocity", self.lib.dgsrhd_mean_square_velocity(
-            self.ctx, _dev_ptr(U, "U", self.shape), int(axis), ctypes.byref(out)))
+            self.ctx, self._ptr(U, "U"), int(axis), ctypes.byref(out)))
         return out.value
 
     def cfl_dt(self, cfl: float | None = None) -> float:

@@ -172,3 +172,48 @@ def test_oracle_and_library_read_a_spec_alike(spec):
         for s in range(2):
             assert a.bc[k][s] == b.bc[k][s]
             assert list(a.bc_state[k][s]) == list(b.bc_state[k][s])
+
+
+class _FakeTensor:
+    """Stands in for a tensor in the binding's pointer checks (no GPU needed)."""
+
+    def __init__(self, shape, dtype=None, cuda=True, contiguous=True, index=0):
+        import torch
+        self.shape = tuple(shape)
+        self.dtype = torch.float64 if dtype is None else dtype
+        self.is_cuda = cuda
+        self._contiguous = contiguous
+        self.device = torch.device("cuda", index) if cuda else torch.device("cpu")
+
+    def is_contiguous(self):
+        return self._contiguous
+
+    def numel(self):
+        return int(np.prod(self.shape))
+
+    def data_ptr(self):
+        return 4096
+
+
+def test_binding_checks_every_pointer_it_hands_the_kernels():
+    """A host tensor, another dtype, a strided view, another shape or size, or a tensor on
+    another GPU is refused before any library call."""
+    import torch
+    from paper_2205_00095_gb300.solver import _dev_ptr, _vec_ptr
+    dev = torch.device("cuda", 0)
+    shape = (5, 12, 4)
+    assert _dev_ptr(_FakeTensor(shape), "U", shape, dev) == 4096
+    for bad in (_FakeTensor(shape, cuda=False), _FakeTensor(shape, dtype=torch.float32),
+                _FakeTensor(shape, contiguous=False), _FakeTensor((5, 12, 3)),
+                _FakeTensor(shape, index=1)):
+        with pytest.raises(ValueError):
+            _dev_ptr(bad, "U", shape, dev)
+    assert _vec_ptr(None, "s", 12, dev) is None
+    assert _vec_ptr(_FakeTensor((12,)), "s", 12, dev) == 4096
+    assert _vec_ptr(_FakeTensor((20,)), "save", 12, dev, at_least=True) == 4096
+    for bad, at_least in ((_FakeTensor((11,)), False), (_FakeTensor((13,)), False),
+                          (_FakeTensor((11,)), True), (_FakeTensor((12,), cuda=False), False),
+                          (_FakeTensor((12,), dtype=torch.int64), False),
+                          (_FakeTensor((12,), index=1), False)):
+        with pytest.raises(ValueError):
+            _vec_ptr(bad, "s", 12, dev, at_least=at_least)
