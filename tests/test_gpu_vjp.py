@@ -147,7 +147,7 @@ def test_checkpointed_rollout_gradient_against_oracle_differences(gpu_lib):
     assert st["enforced_cells"] == 0
 
     # forward objective agrees with the oracle
-    assert abs(float(J) - oracle_objective(spec, A, nsteps=nsteps)) <= 1e-11 * abs(float(J))
+    assert abs(float(J.detach()) - oracle_objective(spec, A, nsteps=nsteps)) <= 1e-11 * abs(float(J.detach()))
 
     def tangent(dW):
         h = 1e-6
@@ -179,7 +179,7 @@ def test_checkpointed_rollout_gradient_against_oracle_differences(gpu_lib):
         eps = 1e-6
         g_fd = (oracle_objective(spec, A, d, eps, nsteps) - oracle_objective(spec, A, d, -eps, nsteps)) / (2 * eps)
         # floor: the rounding of J (a sum over ~2000 nodes) divided by 2 eps
-        floor = 1e-8 * abs(float(J))
+        floor = 1e-8 * abs(float(J.detach()))
         assert abs(g_adj - g_fd) <= 1e-6 * abs(g_fd) + floor, (g_adj, g_fd)
 
 
@@ -331,6 +331,6 @@ def test_full_size_rollout_gradient_against_oracle_differences(gpu_lib):
     Jm = oracle_objective(spec, A - hA, nsteps=nsteps)
     g_fd = (Jp - Jm) / (2 * hA)
     print(f"\nfull-size dJ/dA: adjoint {g_adj:.10e}, oracle differences {g_fd:.10e}, "
-          f"rel {abs(g_adj - g_fd) / abs(g_fd):.2e}; J {float(J):.10e}")
-    assert abs(float(J) - 0.5 * (Jp + Jm)) <= 1e-9 * abs(float(J))
+          f"rel {abs(g_adj - g_fd) / abs(g_fd):.2e}; J {float(J.detach()):.10e}")
+    assert abs(float(J.detach()) - 0.5 * (Jp + Jm)) <= 1e-9 * abs(float(J.detach()))
     assert abs(g_adj - g_fd) <= 1e-6 * abs(g_fd), (g_adj, g_fd)
