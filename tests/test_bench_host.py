@@ -1,0 +1,98 @@
+"""Host-side arithmetic of bench.py, on CPU: the algorithmic work per node behind the roofline,
+the committed ncu record and its staleness check, the clock-sample summary and the bounded
+oracle sample."""
+import json
+import os
+import shutil
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+
+import bench  # noqa: E402
+
+RECORD = os.path.join("profiles", "dram_traffic_advected_wave_512x512_p3.json")
+
+
+def test_volume_kernel_work_per_node_of_the_bench_workload():
+    """2D, p = 3, ideal EOS, closed-form recovery: 120 (con2prim) + 14 (two nodal fluxes of 7)
+    + 80 (2 N flops x 5 variables x 2 directions) + 40 (four face lines of N = 4 nodes among
+    16, 5 variables, 2 N flops each) = 254 flops per node."""
+    spec = bench.make_spec("advected_wave")
+    assert (spec["dim"], spec["degree"], spec["eos"], spec["c2p"]) == (2, 3, "ideal", "analytic")
+    assert bench.volume_kernel_flops_per_node(spec) == 254.0
+    # the iterative solvers grow by their per-iteration cost
+    it = dict(spec, c2p="iterative")
+    assert bench.volume_kernel_flops_per_node(it, 5.0) - bench.volume_kernel_flops_per_node(it, 4.0) == 19.0
+    tm = dict(spec, eos="tm", c2p="iterative")
+    assert bench.volume_kernel_flops_per_node(tm, 3.0) - bench.volume_kernel_flops_per_node(tm, 2.0) == 14.0
+
+
+def _copy_record_tree(dst):
+    d = json.load(open(os.path.join(ROOT, RECORD)))
+    for f in [RECORD] + d["source_files"]:
+        os.makedirs(os.path.join(dst, os.path.dirname(f)), exist_ok=True)
+        shutil.copy(os.path.join(ROOT, f), os.path.join(dst, f))
+    return d
+
+
+def test_capture_record_is_dropped_when_a_kernel_source_changes(tmp_path, monkeypatch):
+    d = _copy_record_tree(str(tmp_path))
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    fresh = bench.measured_traffic("volume_kernel", "advected_wave")
+    k = d["kernels"]["volume_kernel"]
+    # the record matches the sources as committed, or is already stale: either way the
+    # value is the record's or None, never anything else
+    assert fresh in (None, k["dram_bytes_read"] + k["dram_bytes_write"])
+    assert bench.measured_traffic("volume_kernel", "kh2d") is None
+    assert bench.measured_traffic("no_such_kernel", "advected_wave") is None
+    if fresh is not None:
+        assert bench.measured_fp64_pipe("volume_kernel", "advected_wave") == pytest.approx(
+            k["fp64_pipe_busy_pct"] / 100.0)
+    with open(tmp_path / d["source_files"][0], "ab") as fh:
+        fh.write(b"\n// changed\n")
+    assert bench.measured_traffic("volume_kernel", "advected_wave") is None
+    assert bench.measured_fp64_pipe("volume_kernel", "advected_wave") is None
+
+
+def test_capture_record_traffic_covers_the_state():
+    """The volume kernel reads the whole state (5 doubles per node) at least once: a record below
+    that would be a mis-scaled capture."""
+    d = json.load(open(os.path.join(ROOT, RECORD)))
+    spec = bench.make_spec("advected_wave")
+    state = 5 * 8 * bench.dof(spec)
+    k = d["kernels"]["volume_kernel"]
+    assert k["dram_bytes_read"] >= 0.95 * state
+    assert 0.0 < k["fp64_pipe_busy_pct"] <= 100.0
+
+
+def test_clock_summary_takes_the_median_and_the_active_reasons(tmp_path):
+    c = bench.ClockSampler(0, str(tmp_path))
+    rows = [
+        "0, 2070, 2070, 900.1, 0x0, Not Active, Not Active, Not Active, Not Active",
+        "0, 2055, 2070, 1010.0, 0x4, Not Active, Not Active, Not Active, Active",
+        "0, 2070, 2070, 1005.3, 0x0, Not Active, Not Active, Not Active, Not Active",
+        "0, [N/A], 2070, 1.0, 0x0, Not Active, Not Active, Not Active, Not Active",
+        "garbage",
+    ]
+    open(c.path, "w").write("\n".join(rows) + "\n")
+    c.proc = object()  # as if nvidia-smi had run
+    s = c.summary()
+    assert s["sm_mhz"] == 2070.0 and s["sm_max_mhz"] == 2070.0 and s["samples"] == 3
+    assert s["reasons"] == ["sw_power_cap"]
+    assert os.path.dirname(c.path) == str(tmp_path)
+    assert bench.ClockSampler(0).summary()["sm_mhz"] is None  # never started
+
+
+def test_job_throughput_counts_every_replica():
+    assert bench.job_throughput(1, 1000, 10, 3, 1000.0) == 30000.0
+    assert bench.job_throughput(4, 1000, 10, 3, 1000.0) == 4 * 30000.0
+
+
+def test_oracle_sample_never_exceeds_the_workload():
+    spec = dict(bench.make_spec("advected_wave"), n_elem=[12, 12])
+    s = bench.oracle_sample_spec(spec, target_s=0.05)
+    assert all(2 <= a <= b for a, b in zip(s["n_elem"], spec["n_elem"]))
+    assert {k: v for k, v in s.items() if k != "n_elem"} == {k: v for k, v in spec.items() if k != "n_elem"}
