@@ -117,3 +117,57 @@ def test_binding_codes_match_the_header(c_layout):
         assert set(table) == set(names), group
         for key, const in names.items():
             assert table[key] == c[const], (group, key)
+
+
+def header_prototypes():
+    """{name: (return type, [parameter types])} of every function include/dgsrhd.h declares."""
+    text = re.sub(r"/\*.*?\*/", "", open(HEADER).read(), flags=re.S)
+    protos = {}
+    for ret, name, params in re.findall(
+            r"^\s*((?:const\s+)?[a-z_0-9]+\s*\**)\s*(dgsrhd_[a-z_0-9]+)\s*\(([^)]*)\)\s*;",
+            text, flags=re.M):
+        types = []
+        for prm in params.split(","):
+            prm = " ".join(prm.split())
+            if prm in ("", "void"):
+                continue
+            # drop the parameter's name: the last identifier not followed by '*'
+            types.append(re.sub(r"\s*\b[a-zA-Z_][a-zA-Z_0-9]*$", "", prm).replace(" *", "*"))
+        protos[name] = (" ".join(ret.split()).replace(" *", "*"), types)
+    return protos
+
+
+SCALARS = {"int32_t": ctypes.c_int32, "int64_t": ctypes.c_int64, "double": ctypes.c_double}
+POINTEES = dict(SCALARS, dgsrhd_config=_lib.dgsrhd_config, dgsrhd_stats=_lib.dgsrhd_stats)
+
+
+def _check_type(ctype, ctext, where):
+    ctext = ctext.replace("const ", "")
+    if ctext.endswith("*"):
+        pointee = ctext[:-1].strip()
+        if ctype is ctypes.c_void_p:
+            return  # an address: any pointer
+        if ctype is ctypes.c_char_p:
+            assert pointee == "char", where
+            return
+        assert hasattr(ctype, "_type_") and issubclass(ctype, ctypes._Pointer), where
+        if pointee.endswith("*"):     # a pointer to a pointer (an out-handle)
+            assert ctype._type_ is ctypes.c_void_p, where
+        else:
+            assert ctype._type_ is POINTEES[pointee], where
+    elif ctext == "void":
+        assert ctype is None, where
+    else:
+        assert ctype is SCALARS[ctext], where
+
+
+def test_function_signatures_match_the_header():
+    lib = _lib.load()
+    protos = header_prototypes()
+    assert sorted(protos) == sorted(_lib.exported_symbols())
+    for name, (ret, params) in protos.items():
+        fn = getattr(lib, name)
+        assert fn.argtypes is not None and len(fn.argtypes) == len(params), name
+        _check_type(fn.restype, ret, f"{name} return")
+        for k, (ct, pt) in enumerate(zip(fn.argtypes, params)):
+            _check_type(ct, pt, f"{name} argument {k}")
