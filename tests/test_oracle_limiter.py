@@ -54,3 +54,21 @@ def test_limiter_bounds_a_discontinuity_and_keeps_means(degree):
             nb = [mU[v, e]] + [mU[v, k] for k in (e - 1, e + 1) if 0 <= k < n]
             assert V[v, e].max() <= max(nb) + alpha + 1e-12 * abs(max(nb))
             assert V[v, e].min() >= min(nb) - alpha - 1e-12 * abs(min(nb))
+    # the factor is the largest that keeps the bounds: in a limited element some variable's
+    # extreme over the nodes and the two face traces (phi_i(-1), phi_i(+1) from the Lagrange
+    # basis on the Gauss-Legendre nodes) lands on its relaxed bound
+    xg = np.polynomial.legendre.leggauss(degree + 1)[0]
+    lag = [np.polynomial.Polynomial.fromroots(np.delete(xg, i)) for i in range(degree + 1)]
+    em = np.array([p(-1.0) / p(xg[i]) for i, p in enumerate(lag)])
+    ep = np.array([p(1.0) / p(xg[i]) for i, p in enumerate(lag)])
+    limited = [e for e in range(n) if not np.array_equal(V[:, e], U[:, e])]
+    assert len(limited) == st["limited_cells"]
+    for e in limited:
+        touches = False
+        for v in range(5):
+            nb = [mU[v, e]] + [mU[v, k] for k in (e - 1, e + 1) if 0 <= k < n]
+            vals = np.concatenate([V[v, e], [em @ V[v, e], ep @ V[v, e]]])
+            tol = 1e-12 * max(abs(max(nb)), abs(min(nb)), alpha)
+            touches |= abs(vals.max() - (max(nb) + alpha)) <= tol
+            touches |= abs(vals.min() - (min(nb) - alpha)) <= tol
+        assert touches, f"element {e} is limited further than its bounds require"
