@@ -1,0 +1,104 @@
+"""The pins catch plausible mistakes in the oracle (CPU, no GPU).
+
+Each case plants one mistake in a copy of oracle/dgsrhd_oracle.c (a wrong Runge-Kutta weight,
+a flipped dissipation sign, a transposed or swapped basis table, a wrong wavespeed, enthalpy,
+pressure or quadratic factor, the operator's other root or a missing margin, the limiter's bound
+scaling), builds the copy in a temporary directory, and runs the fast pin files against it in
+a child process whose oracle module loads that copy.  Every planted mistake must make at least
+one pin fail, and an unmodified copy must pass them all, so a failure here means a pin has
+stopped testing what it claims to.  The planted copies never leave the temporary directory.
+"""
+import os
+import subprocess
+import sys
+from concurrent.futures import ThreadPoolExecutor
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+SOURCE = os.path.join(ROOT, "oracle", "dgsrhd_oracle.c")
+
+# (what is wrong, exact text in the source, the mistaken text)
+MUTATIONS = [
+    ("SSPRK3 final-stage weight", "{0.0, 0.75, 1.0 / 3.0}", "{0.0, 0.75, 0.3}"),
+    ("LLF dissipation sign", "- 0.5 * a * (UR[v] - UL[v])", "+ 0.5 * a * (UR[v] - UL[v])"),
+    ("HLL dissipation sign", "sL * sR * (UR[v] - UL[v])", "sL * sR * (UL[v] - UR[v])"),
+    ("lift with phi(+1) at the low face", "+= scale * (m.em[a] / m.w[a]) * Fs[v]",
+     "+= scale * (m.ep[a] / m.w[a]) * Fs[v]"),
+    ("volume table transposed", "w[a] * lagrange_deriv(N, x, i, x[a]) / w[i]",
+     "w[i] * lagrange_deriv(N, x, a, x[i]) / w[a]"),
+    ("wavespeed sigma with one Lorentz factor", "cs2 / (gam * gam * (1.0 - cs2))",
+     "cs2 / (gam * (1.0 - cs2))"),
+    ("operator takes the other root", "double den = -b + sqrt(b * b - 4.0 * a * c0);",
+     "double den = -b - sqrt(b * b - 4.0 * a * c0);"),
+    ("operator without its margin", "s *= (1.0 - 1e-12);", "s *= 1.0;"),
+    ("Taub-Matthews enthalpy constant",
+     "1.5 * th * th / (sqrt(th * th + 4.0 / 9.0) + 2.0 / 3.0)",
+     "1.5 * th * th / (sqrt(th * th + 4.0 / 9.0) + 1.0 / 3.0)"),
+    ("ideal enthalpy factor", "c->gamma_ad / (c->gamma_ad - 1.0) * th",
+     "1.0 / (c->gamma_ad - 1.0) * th"),
+    ("ideal pressure from con2prim", "P = (c->gamma_ad - 1.0) * e_minus_rho;",
+     "P = c->gamma_ad * e_minus_rho;"),
+    ("Taub-Matthews pressure from con2prim", "P = e_minus_rho * (Ev + rho) / (3.0 * Ev);",
+     "P = e_minus_rho * (Ev + rho) / (2.0 * Ev);"),
+    ("the quartic's other quadratic factor", "double C = 0.5 * (x - sqrt(x * x - 4.0 * a0));",
+     "double C = 0.5 * (x + sqrt(x * x - 4.0 * a0));"),
+    ("limiter bound scaling h^(3/2)", "pow(h, 1.5)", "pow(h, 2.0)"),
+]
+
+PINS = [
+    "tests/test_oracle_basis.py", "tests/test_oracle_eos.py", "tests/test_oracle_flux.py",
+    "tests/test_oracle_enforce.py", "tests/test_oracle_rhs.py", "tests/test_oracle_con2prim.py",
+    "tests/test_oracle_step.py", "tests/test_oracle_limiter.py",
+]
+
+# The child imports the oracle package, points its source and build paths at the copy before
+# anything loads the shared object, and runs the pins; the pin modules import the same package.
+CHILD = """
+import os, sys
+sys.path.insert(0, {root!r})
+import oracle
+oracle._SRC = sys.argv[1]
+oracle._BUILD = sys.argv[2]
+oracle._LIBPATH = os.path.join(sys.argv[2], "liboracle.so")
+import pytest
+sys.exit(pytest.main(["-x", "-q", "-p", "no:cacheprovider", "-m", "not gpu and not slow",
+                      *sys.argv[3:]]))
+"""
+
+
+def _run(tmp, k, text):
+    d = os.path.join(tmp, f"case{k:02d}")
+    os.makedirs(d)
+    src = os.path.join(d, "dgsrhd_oracle.c")
+    with open(src, "w") as f:
+        f.write(text)
+    proc = subprocess.run(
+        [sys.executable, "-c", CHILD.format(root=ROOT), src, os.path.join(d, "_build"), *PINS],
+        cwd=ROOT, capture_output=True, text=True, timeout=600)
+    return proc.returncode, (proc.stdout + proc.stderr)[-1500:]
+
+
+@pytest.fixture(scope="module")
+def outcomes(tmp_path_factory):
+    tmp = str(tmp_path_factory.mktemp("planted"))
+    original = open(SOURCE).read()
+    jobs = {"unmodified": original}
+    for name, old, new in MUTATIONS:
+        assert original.count(old) == 1, f"{name}: the text to replace must occur exactly once"
+        jobs[name] = original.replace(old, new)
+    with ThreadPoolExecutor(max_workers=max(1, min(6, (os.cpu_count() or 2) - 1))) as ex:
+        futures = {name: ex.submit(_run, tmp, k, text) for k, (name, text) in enumerate(jobs.items())}
+        return {name: fut.result() for name, fut in futures.items()}
+
+
+def test_unmodified_copy_passes_the_pins(outcomes):
+    rc, tail = outcomes["unmodified"]
+    assert rc == 0, tail
+
+
+@pytest.mark.parametrize("name", [m[0] for m in MUTATIONS])
+def test_planted_mistake_fails_a_pin(outcomes, name):
+    rc, tail = outcomes[name]
+    # pytest's exit code 1: tests ran and some failed (not a crash or a collection error)
+    assert rc == 1, f"{name}: exit {rc}\n{tail}"
