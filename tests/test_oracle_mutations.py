@@ -1,9 +1,10 @@
 """The pins catch plausible mistakes in the oracle (CPU, no GPU).
 
 Each case plants one mistake in a copy of oracle/dgsrhd_oracle.c (a wrong Runge-Kutta weight,
-a flipped dissipation sign, a transposed or swapped basis table, a wrong wavespeed, enthalpy,
-pressure or quadratic factor, the operator's other root or a missing margin, the limiter's bound
-scaling), builds the copy in a temporary directory, and runs the fast pin files against it in
+a flipped dissipation sign, a transposed or swapped basis table, face traces from the wrong
+face, a wrong wavespeed, enthalpy, pressure or quadratic factor, a looser Newton stop, the HLLC
+star state on the wrong side or with a wrong sign, the operator's other root or a missing
+margin, the limiter's bound scaling), builds the copy in a temporary directory, and runs the fast pin files against it in
 a child process whose oracle module loads that copy.  Every planted mistake must make at least
 one pin fail, and an unmodified copy must pass them all, so a failure here means a pin has
 stopped testing what it claims to.  The planted copies never leave the temporary directory.
@@ -44,6 +45,13 @@ MUTATIONS = [
     ("the quartic's other quadratic factor", "double C = 0.5 * (x - sqrt(x * x - 4.0 * a0));",
      "double C = 0.5 * (x + sqrt(x * x - 4.0 * a0));"),
     ("limiter bound scaling h^(3/2)", "pow(h, 1.5)", "pow(h, 2.0)"),
+    ("HLLC star state on the wrong side of the contact", "const int left = xs >= 0.0;",
+     "const int left = xs < 0.0;"),
+    ("HLLC tau* pressure work sign", "Us[4] = (U[4] * (lam - v) + ps * xs - p * v) / den;",
+     "Us[4] = (U[4] * (lam - v) + ps * xs + p * v) / den;"),
+    ("looser Newton stop", "fabs(dw) <= fmax(1e-14, rtol) * w", "fabs(dw) <= fmax(1e-6, rtol) * w"),
+    ("face traces from the opposite face", "const double *coef = side ? m->ep : m->em;",
+     "const double *coef = side ? m->em : m->ep;"),
 ]
 
 PINS = [
