@@ -4,7 +4,9 @@ Each case plants one mistake in a copy of oracle/dgsrhd_oracle.c (a wrong Runge-
 a flipped dissipation sign, a transposed or swapped basis table, face traces from the wrong
 face, a wrong wavespeed, enthalpy, pressure or quadratic factor, a looser Newton stop, the HLLC
 star state on the wrong side or with a wrong sign, the operator's other root or a missing
-margin, the limiter's bound scaling), builds the copy in a temporary directory, and runs the fast pin files against it in
+margin, the limiter's bound scaling), or in a copy of oracle/exact_riemann_general.py (the
+rarefaction ODE, the isentrope, the shock speed, the transverse invariant behind a shock), builds
+the copy in a temporary directory, and runs the fast pin files against it in
 a child process whose oracle module loads that copy.  Every planted mistake must make at least
 one pin fail, and an unmodified copy must pass them all, so a failure here means a pin has
 stopped testing what it claims to.  The planted copies never leave the temporary directory.
@@ -54,6 +56,19 @@ MUTATIONS = [
      "const double *coef = side ? m->em : m->ep;"),
 ]
 
+# the same for the exact Riemann solution with transverse velocity (a Python module)
+EXACT_SOURCE = os.path.join(ROOT, "oracle", "exact_riemann_general.py")
+EXACT_MUTATIONS = [
+    ("rarefaction ODE without c_s^2 on v_t^2", "math.sqrt(1.0 - vx * vx - c2 * vt * vt)",
+     "math.sqrt(1.0 - vx * vx - vt * vt)"),
+    ("isentrope without h", "return [p / (rho * h * c2),", "return [p / (rho * c2),"),
+    ("shock speed sign under the root", "math.sqrt(j2 + m2 * (1.0 - vx_a * vx_a))",
+     "math.sqrt(j2 + m2 * (1.0 + vx_a * vx_a))"),
+    ("transverse invariant behind a shock without h", "A = h_a * lor_a * vt_a",
+     "A = lor_a * vt_a"),
+]
+EXACT_PINS = ["tests/test_exact_riemann_general.py"]
+
 PINS = [
     "tests/test_oracle_basis.py", "tests/test_oracle_eos.py", "tests/test_oracle_flux.py",
     "tests/test_oracle_enforce.py", "tests/test_oracle_rhs.py", "tests/test_oracle_con2prim.py",
@@ -75,37 +90,62 @@ sys.exit(pytest.main(["-x", "-q", "-p", "no:cacheprovider", "-m", "not gpu and n
 """
 
 
-def _run(tmp, k, text):
+# For the Python module the child loads the copy under the module's own name before the pins
+# import it.
+CHILD_EXACT = """
+import importlib.util, sys
+sys.path.insert(0, {root!r})
+import oracle
+spec = importlib.util.spec_from_file_location("oracle.exact_riemann_general", sys.argv[1])
+mod = importlib.util.module_from_spec(spec)
+sys.modules[spec.name] = mod
+spec.loader.exec_module(mod)
+oracle.exact_riemann_general = mod
+import pytest
+sys.exit(pytest.main(["-x", "-q", "-p", "no:cacheprovider", "-m", "not gpu and not slow",
+                      *sys.argv[2:]]))
+"""
+
+
+def _run(tmp, k, kind, text):
     d = os.path.join(tmp, f"case{k:02d}")
     os.makedirs(d)
-    src = os.path.join(d, "dgsrhd_oracle.c")
+    if kind == "c":
+        src = os.path.join(d, "dgsrhd_oracle.c")
+        argv = [CHILD.format(root=ROOT), src, os.path.join(d, "_build"), *PINS]
+    else:
+        src = os.path.join(d, "exact_riemann_general.py")
+        argv = [CHILD_EXACT.format(root=ROOT), src, *EXACT_PINS]
     with open(src, "w") as f:
         f.write(text)
-    proc = subprocess.run(
-        [sys.executable, "-c", CHILD.format(root=ROOT), src, os.path.join(d, "_build"), *PINS],
-        cwd=ROOT, capture_output=True, text=True, timeout=600)
+    proc = subprocess.run([sys.executable, "-c", *argv], cwd=ROOT, capture_output=True,
+                          text=True, timeout=600)
     return proc.returncode, (proc.stdout + proc.stderr)[-1500:]
 
 
 @pytest.fixture(scope="module")
 def outcomes(tmp_path_factory):
     tmp = str(tmp_path_factory.mktemp("planted"))
-    original = open(SOURCE).read()
-    jobs = {"unmodified": original}
-    for name, old, new in MUTATIONS:
-        assert original.count(old) == 1, f"{name}: the text to replace must occur exactly once"
-        jobs[name] = original.replace(old, new)
+    jobs = {}
+    for kind, path, mutations in (("c", SOURCE, MUTATIONS), ("py", EXACT_SOURCE, EXACT_MUTATIONS)):
+        original = open(path).read()
+        jobs[f"unmodified {kind}"] = (kind, original)
+        for name, old, new in mutations:
+            assert original.count(old) == 1, f"{name}: the text to replace must occur exactly once"
+            jobs[name] = (kind, original.replace(old, new))
     with ThreadPoolExecutor(max_workers=max(1, min(6, (os.cpu_count() or 2) - 1))) as ex:
-        futures = {name: ex.submit(_run, tmp, k, text) for k, (name, text) in enumerate(jobs.items())}
+        futures = {name: ex.submit(_run, tmp, k, kind, text)
+                   for k, (name, (kind, text)) in enumerate(jobs.items())}
         return {name: fut.result() for name, fut in futures.items()}
 
 
-def test_unmodified_copy_passes_the_pins(outcomes):
-    rc, tail = outcomes["unmodified"]
+@pytest.mark.parametrize("kind", ["c", "py"])
+def test_unmodified_copy_passes_the_pins(outcomes, kind):
+    rc, tail = outcomes[f"unmodified {kind}"]
     assert rc == 0, tail
 
 
-@pytest.mark.parametrize("name", [m[0] for m in MUTATIONS])
+@pytest.mark.parametrize("name", [m[0] for m in MUTATIONS + EXACT_MUTATIONS])
 def test_planted_mistake_fails_a_pin(outcomes, name):
     rc, tail = outcomes[name]
     # pytest's exit code 1: tests ran and some failed (not a crash or a collection error)
