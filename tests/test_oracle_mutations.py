@@ -4,7 +4,8 @@ Each case plants one mistake in a copy of oracle/dgsrhd_oracle.c (a wrong Runge-
 a flipped dissipation sign, a transposed or swapped basis table, face traces from the wrong
 face, a wrong wavespeed, enthalpy, pressure or quadratic factor, a looser Newton stop, the HLLC
 star state on the wrong side or with a wrong sign, the operator's other root or a missing
-margin, the limiter's bound scaling), or in a copy of oracle/exact_riemann_general.py (the
+margin, the limiter's bound scaling, the minmod limiter's threshold, sign test and differences),
+or in a copy of oracle/exact_riemann_general.py (the
 rarefaction ODE, the isentrope, the shock speed, the transverse invariant behind a shock), builds
 the copy in a temporary directory, and runs the fast pin files against it in
 a child process whose oracle module loads that copy.  Every planted mistake must make at least
@@ -54,6 +55,15 @@ MUTATIONS = [
     ("looser Newton stop", "fabs(dw) <= fmax(1e-14, rtol) * w", "fabs(dw) <= fmax(1e-6, rtol) * w"),
     ("face traces from the opposite face", "const double *coef = side ? m->ep : m->em;",
      "const double *coef = side ? m->em : m->ep;"),
+    ("minmod TVB threshold scaled by h", "const double thr = c->limiter_alpha * h * h;",
+     "const double thr = c->limiter_alpha * h;"),
+    ("minmod ignores the signs of the neighbour differences",
+     "if ((D[k] > 0.0) != (x > 0.0) || D[k] == 0.0) return 0.0;", "if (D[k] == 0.0) return 0.0;"),
+    ("minmod backward difference with the wrong sign", "D[nD++] = side ? un - ub : ub - un;",
+     "D[nD++] = un - ub;"),
+    ("minmod low-face deviation with the wrong sign",
+     "const double dev[2] = {fm[1] / face_wsum - ub, ub - fm[0] / face_wsum};",
+     "const double dev[2] = {fm[1] / face_wsum - ub, fm[0] / face_wsum - ub};"),
 ]
 
 # the same for the exact Riemann solution with transverse velocity (a Python module)
@@ -73,7 +83,10 @@ PINS = [
     "tests/test_oracle_basis.py", "tests/test_oracle_eos.py", "tests/test_oracle_flux.py",
     "tests/test_oracle_enforce.py", "tests/test_oracle_rhs.py", "tests/test_oracle_con2prim.py",
     "tests/test_oracle_step.py", "tests/test_oracle_limiter.py",
-]
+] + [f"tests/test_oracle_minmod.py::{t}" for t in (
+    "test_linear_data_untouched", "test_local_extremum_is_flattened_and_means_kept",
+    "test_limited_elements_scale_toward_the_mean_within_the_minmod_bound",
+    "test_tvb_threshold_keeps_small_deviations", "test_riemann_problem_converges_with_minmod")]
 
 # The child imports the oracle package, points its source and build paths at the copy before
 # anything loads the shared object, and runs the pins; the pin modules import the same package.
