@@ -101,6 +101,14 @@ def _limiter(v) -> int:
     return int(v)
 
 
+def _enforce(v) -> int:
+    """Physicality operator: False/0 off, True/1 on the nodes, "faces"/2 on the nodes and the
+    face points of the element's conserved polynomial."""
+    if v == "faces" or v == 2:
+        return 2
+    return int(bool(v))
+
+
 def make_config(spec: dict) -> Config:
     """Problem description (plain dict, see ``workloads``) -> oracle struct."""
     c = Config()
@@ -130,7 +138,7 @@ def make_config(spec: dict) -> Config:
             for s in range(2):
                 for v in range(5):
                     c.bc_state[d][s][v] = float(bcs[d][s][v])
-    c.enforce = int(bool(spec.get("enforce", True)))
+    c.enforce = _enforce(spec.get("enforce", True))
     c.nodes = _enum(_NODES, spec.get("nodes", "gl"))
     c.limiter = _limiter(spec.get("limiter", False))
     c.limiter_alpha = float(spec.get("limiter_alpha", 50.0))
@@ -274,7 +282,7 @@ def cfl_dt(spec: dict, cfl: float) -> float:
 
 
 def mean_square_velocity(spec: dict, U: np.ndarray, axis: int = 1) -> float:
-    """<v_axis^2> = (1/|Omega|) int v_axis^2 dV by the nodal quadrature (Sec. 4.4)."""
+    """<v_axis^2> = (1/|Omega|) int v_axis^2 dV by the nodal quadrature (Sec. 4.5)."""
     U = _f64(U)
     return float(_load().or_mean_square_velocity(ctypes.byref(make_config(spec)), _ptr(U), int(axis)))
 
@@ -312,7 +320,7 @@ def cs2(spec: dict, rho: float, P: float) -> float:
 
 def gamma_eq(spec: dict, rho, P):
     """Equivalent adiabatic index Gamma_eq = (h - 1) / (h - 1 - Theta), Theta = P / rho, c = 1
-    (Sec. 2.2 and the Taub-Matthews test of Sec. 4.2, Fig. 9): Gamma for the ideal EOS; between
+    (Sec. 2.2 and the Taub-Matthews test of Sec. 4.3, Fig. 9): Gamma for the ideal EOS; between
     4/3 (hot) and 5/3 (cold) for Taub-Matthews.  A diagnostic; rho and P may be arrays."""
     rho, P = np.broadcast_arrays(np.asarray(rho, dtype=np.float64), np.asarray(P, dtype=np.float64))
     hm1 = np.vectorize(lambda r, p: enthalpy(spec, r, p) - 1.0)(rho, P)

@@ -43,7 +43,7 @@ typedef struct {
   int32_t rk_stages;      /* 1, 2, 3 */
   int32_t bc[3][2];       /* 0 periodic, 1 Dirichlet, 2 outflow, 3 reflecting wall */
   double bc_state[3][2][5]; /* Dirichlet primitive (rho, vx, vy, vz, P) */
-  int32_t enforce;        /* physicality operator after every stage */
+  int32_t enforce;        /* physicality operator after every stage: 1 nodes, 2 nodes and face points */
   int32_t nodes;          /* 0 Gauss-Legendre, 1 Gauss-Lobatto-Legendre (degree >= 1) */
   int32_t limiter;        /* after every stage, before the operator: 1 scaling, 2 minmod */
   double limiter_alpha;   /* 1: bound relaxation limiter_alpha h^(3/2); 2: TVB constant M (M h^2) */
@@ -906,24 +906,89 @@ static double positivity_factor(double X, double Xbar) {
   return Xbar / (Xbar - X);
 }
 
-/* The operator on one element, following the four-step procedure of
- * Sec. 2.5 (flag, check the mean, per-node s_i in two stages, s = min s_i,
- * smooth towards the mean, Eq. smoothed_states).
+/* Largest factor s_i in [0, 1] for one point with conserved state Ui and admissible element mean
+ * Ub: the two stages of Sec. 2.5 (Eqs. first_stage_positivity, first_stage_smoothed_state,
+ * second_stage_quatratic, second_stage_coefficients, second_stage_solution).
  * Readings: the stage-2 coefficients with Delta = U~(1) - Ubar are
  *   a = dE^2 - dD^2 - |dS|^2, b = 2 (Ebar dE - Dbar dD - Sbar.dS),
  *   c0 = Ebar^2 - Dbar^2 - |Sbar|^2
  * and the root of Eq. second_stage_solution is evaluated in the equivalent
- * form 2 c0 / (-b + sqrt(b^2 - 4 a c0)), clamped to [0, 1]; a flagged
- * element uses s (1 - 1e-12) so that the smoothed nodes are strictly
- * inside the admissible set; an element whose mean is inadmissible is left
- * unchanged and counted. Returns the element's s. */
-static double enforce_element(const mesh *m, double *U, int64_t e, or_stats *st) {
+ * form 2 c0 / (-b + sqrt(b^2 - 4 a c0)), clamped to [0, 1]. */
+static double point_factor(const double Ui[5], const double Ub[5]) {
+  double Dbar = Ub[0], Ebar = Ub[4] + Ub[0];
+  /* stage 1: positivity of D and E (Eq. first_stage_positivity) */
+  double sD = positivity_factor(Ui[0], Dbar);
+  double sE = positivity_factor(Ui[4] + Ui[0], Ebar);
+  double s1 = fmin(sD, sE);
+  double U1[5];
+  for (int v = 0; v < 5; ++v) U1[v] = s1 * Ui[v] + (1.0 - s1) * Ub[v];
+  if (admissible(U1)) return s1;
+  /* stage 2: the quadratic of Eq. second_stage_quatratic */
+  /* In the stored variables (E = tau + D):
+   *   a  = dE^2 - dD^2 - |dS|^2          = dtau (dtau + 2 dD) - |dS|^2
+   *   b  = 2 (Ebar dE - Dbar dD - Sbar.dS) = 2 (taubar (dtau + dD) + Dbar dtau - Sbar.dS)
+   *   c0 = Ebar^2 - Dbar^2 - |Sbar|^2     = taubar (taubar + 2 Dbar) - |Sbar|^2 */
+  double taubar = Ub[4];
+  double dD = U1[0] - Ub[0];
+  double dtau = U1[4] - Ub[4];
+  double dS[3] = {U1[1] - Ub[1], U1[2] - Ub[2], U1[3] - Ub[3]};
+  double a = dtau * (dtau + 2.0 * dD) - (dS[0] * dS[0] + dS[1] * dS[1] + dS[2] * dS[2]);
+  double b = 2.0 * (taubar * (dtau + dD) + Dbar * dtau
+                    - (Ub[1] * dS[0] + Ub[2] * dS[1] + Ub[3] * dS[2]));
+  double c0 = taubar * (taubar + 2.0 * Dbar) - (Ub[1] * Ub[1] + Ub[2] * Ub[2] + Ub[3] * Ub[3]);
+  double den = -b + sqrt(b * b - 4.0 * a * c0);
+  double s2 = (den > 0.0) ? 2.0 * c0 / den : 1.0;
+  if (s2 > 1.0) s2 = 1.0;
+  if (s2 < 0.0) s2 = 0.0;
+  return s1 * s2;
+}
+
+/* Conserved state of element e at face point `fp` (fp = (d * 2 + side) * Nt + t, t the
+ * tangential node index with the d-th coordinate left out, the remaining axes in order):
+ * the element's conserved polynomial sum_a phi_a(-+1) U_a along the normal line through t. */
+static void face_point_state(const mesh *m, const double *U, int64_t e, int fp, double out[5]) {
   int64_t tot = m->E * m->Nn;
+  int Nt = m->Nn / m->N;
+  int d = fp / (2 * Nt), side = (fp / Nt) % 2, t = fp % Nt;
+  int ijk[3] = {0, 0, 0}, k = 0;
+  for (int a = 0; a < m->dim; ++a) {
+    if (a == d) continue;
+    ijk[a] = (k == 0) ? t % m->N : t / m->N;
+    ++k;
+  }
+  const double *coef = (side == 1) ? m->ep : m->em;
+  for (int v = 0; v < 5; ++v) out[v] = 0.0;
+  for (int a = 0; a < m->N; ++a) {
+    ijk[d] = a;
+    int node = node_index(m, ijk);
+    for (int v = 0; v < 5; ++v) out[v] += coef[a] * U[v * tot + e * m->Nn + node];
+  }
+}
+
+/* The operator on one element, following the four-step procedure of
+ * Sec. 2.5 (flag, check the mean, per-point s_i in two stages, s = min s_i,
+ * smooth towards the mean, Eq. smoothed_states).
+ * Readings: a flagged element uses s (1 - 1e-12) so that the smoothed points
+ * are strictly inside the admissible set; an element whose mean is
+ * inadmissible is left unchanged and counted.  With `faces` (the face-point
+ * variant) the points are the nodes and the 2 dim N^(dim-1) face points of
+ * the element's conserved polynomial: since the basis reproduces constants
+ * (sum_a phi_a(-+1) = 1), smoothing the nodes smooths every face point by the
+ * same s, so the minimum over both makes the polynomial admissible at the
+ * faces too.  Returns the element's s. */
+static double enforce_element(const mesh *m, double *U, int64_t e, or_stats *st, int faces) {
+  int64_t tot = m->E * m->Nn;
+  int nfp = faces ? 2 * m->dim * (m->Nn / m->N) : 0;
   int flagged = 0;
   for (int i = 0; i < m->Nn; ++i) {
     double Ui[5];
     for (int v = 0; v < 5; ++v) Ui[v] = U[v * tot + e * m->Nn + i];
     if (!admissible(Ui)) flagged = 1;
+  }
+  for (int fp = 0; fp < nfp; ++fp) {
+    double Uf[5];
+    face_point_state(m, U, e, fp, Uf);
+    if (!admissible(Uf)) flagged = 1;
   }
   if (!flagged) return 1.0;
   double Ub[5] = {0, 0, 0, 0, 0}, wsum = 0.0;
@@ -937,38 +1002,17 @@ static double enforce_element(const mesh *m, double *U, int64_t e, or_stats *st)
     if (st) st->mean_inadmissible_cells++;
     return 1.0;
   }
-  double Dbar = Ub[0], Ebar = Ub[4] + Ub[0];
   double s = 1.0;
   for (int i = 0; i < m->Nn; ++i) {
     double Ui[5];
     for (int v = 0; v < 5; ++v) Ui[v] = U[v * tot + e * m->Nn + i];
-    /* stage 1: positivity of D and E (Eq. first_stage_positivity) */
-    double sD = positivity_factor(Ui[0], Dbar);
-    double sE = positivity_factor(Ui[4] + Ui[0], Ebar);
-    double s1 = fmin(sD, sE);
-    double U1[5];
-    for (int v = 0; v < 5; ++v) U1[v] = s1 * Ui[v] + (1.0 - s1) * Ub[v];
-    double si = s1;
-    if (!admissible(U1)) {
-      /* stage 2: the quadratic of Eq. second_stage_quatratic */
-      /* In the stored variables (E = tau + D):
-       *   a  = dE^2 - dD^2 - |dS|^2          = dtau (dtau + 2 dD) - |dS|^2
-       *   b  = 2 (Ebar dE - Dbar dD - Sbar.dS) = 2 (taubar (dtau + dD) + Dbar dtau - Sbar.dS)
-       *   c0 = Ebar^2 - Dbar^2 - |Sbar|^2     = taubar (taubar + 2 Dbar) - |Sbar|^2 */
-      double taubar = Ub[4];
-      double dD = U1[0] - Ub[0];
-      double dtau = U1[4] - Ub[4];
-      double dS[3] = {U1[1] - Ub[1], U1[2] - Ub[2], U1[3] - Ub[3]};
-      double a = dtau * (dtau + 2.0 * dD) - (dS[0] * dS[0] + dS[1] * dS[1] + dS[2] * dS[2]);
-      double b = 2.0 * (taubar * (dtau + dD) + Dbar * dtau
-                        - (Ub[1] * dS[0] + Ub[2] * dS[1] + Ub[3] * dS[2]));
-      double c0 = taubar * (taubar + 2.0 * Dbar) - (Ub[1] * Ub[1] + Ub[2] * Ub[2] + Ub[3] * Ub[3]);
-      double den = -b + sqrt(b * b - 4.0 * a * c0);
-      double s2 = (den > 0.0) ? 2.0 * c0 / den : 1.0;
-      if (s2 > 1.0) s2 = 1.0;
-      if (s2 < 0.0) s2 = 0.0;
-      si = s1 * s2;
-    }
+    double si = point_factor(Ui, Ub);
+    if (si < s) s = si;
+  }
+  for (int fp = 0; fp < nfp; ++fp) {
+    double Uf[5];
+    face_point_state(m, U, e, fp, Uf);
+    double si = point_factor(Uf, Ub);
     if (si < s) s = si;
   }
   s *= (1.0 - 1e-12);
@@ -985,7 +1029,7 @@ int or_enforce(const or_config *c, double *U, double *s_out, or_stats *st) {
   mesh m;
   if (mesh_init(c, &m)) return 1;
   for (int64_t e = 0; e < m.E; ++e) {
-    double s = enforce_element(&m, U, e, st);
+    double s = enforce_element(&m, U, e, st, c->enforce == 2);
     if (s_out) s_out[e] = s;
   }
   return 0;
@@ -1263,7 +1307,7 @@ int or_phys_flux(const or_config *c, const double *Wv, int d, double *F) {
 }
 
 /* ------------------------------------------------------------------------ */
-/* Diagnostic of the Kelvin-Helmholtz study (Sec. 4.4): the spatial mean of  */
+/* Diagnostic of the Kelvin-Helmholtz study (Sec. 4.5): the spatial mean of  */
 /* the squared velocity component `axis`, <v_a^2> = (1/|Omega|) int v_a^2 dV, */
 /* by the nodal quadrature of the basis: sum over elements and nodes of      */
 /* (prod_d dx_d / 2) w_node v_a^2 with v from con2prim at the node.          */

@@ -1,7 +1,7 @@
 """Exact solution of the 1D special-relativistic Riemann problem with transverse velocity, for the
 ideal and the Taub-Matthews equations of state.  TEST INFRASTRUCTURE ONLY (part of the oracle):
 it is the reference for the paper's Riemann problem 3 (Sec. 4.2, a blast into a state moving
-transversally at 0.99) and for the Taub-Matthews blast wave (Sec. 4.2, the test after the 1D
+transversally at 0.99) and for the Taub-Matthews blast wave (Sec. 4.3, the test after the 1D
 Riemann problems: transverse velocity on both sides, the three equations of state compared).
 
 States are primitive (rho, v_x, v_t, P), c = 1; v_t is the velocity along y.

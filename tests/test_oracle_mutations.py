@@ -4,7 +4,8 @@ Each case plants one mistake in a copy of oracle/dgsrhd_oracle.c (a wrong Runge-
 a flipped dissipation sign, a transposed or swapped basis table, face traces from the wrong
 face, a wrong wavespeed, enthalpy, pressure or quadratic factor, a looser Newton stop, the HLLC
 star state on the wrong side or with a wrong sign, the operator's other root or a missing
-margin, the limiter's bound scaling, the minmod limiter's threshold, sign test and differences),
+margin, its face-point variant without the face points or with the end nodes for them, the
+limiter's bound scaling, the minmod limiter's threshold, sign test and differences),
 or in a copy of oracle/exact_riemann_general.py (the
 rarefaction ODE, the isentrope, the shock speed, the transverse invariant behind a shock), builds
 the copy in a temporary directory, and runs the fast pin files against it in
@@ -55,6 +56,11 @@ MUTATIONS = [
     ("looser Newton stop", "fabs(dw) <= fmax(1e-14, rtol) * w", "fabs(dw) <= fmax(1e-6, rtol) * w"),
     ("face traces from the opposite face", "const double *coef = side ? m->ep : m->em;",
      "const double *coef = side ? m->em : m->ep;"),
+    ("face-point operator leaves the face points out of the minimum",
+     "    double si = point_factor(Uf, Ub);\n", "    double si = 1.0;\n"),
+    ("face-point operator takes the end node for the face value",
+     "out[v] += coef[a] * U[v * tot + e * m->Nn + node];",
+     "out[v] += (a == (side ? m->N - 1 : 0)) * U[v * tot + e * m->Nn + node];"),
     ("minmod TVB threshold scaled by h", "const double thr = c->limiter_alpha * h * h;",
      "const double thr = c->limiter_alpha * h;"),
     ("minmod ignores the signs of the neighbour differences",
@@ -81,7 +87,8 @@ EXACT_PINS = ["tests/test_exact_riemann_general.py"]
 
 PINS = [
     "tests/test_oracle_basis.py", "tests/test_oracle_eos.py", "tests/test_oracle_flux.py",
-    "tests/test_oracle_enforce.py", "tests/test_oracle_rhs.py", "tests/test_oracle_con2prim.py",
+    "tests/test_oracle_enforce.py", "tests/test_oracle_enforce_faces.py", "tests/test_oracle_rhs.py",
+    "tests/test_oracle_con2prim.py",
     "tests/test_oracle_step.py", "tests/test_oracle_limiter.py",
 ] + [f"tests/test_oracle_minmod.py::{t}" for t in (
     "test_linear_data_untouched", "test_local_extremum_is_flattened_and_means_kept",
