@@ -87,12 +87,25 @@ extern "C" {
                                     of the neighbour-mean differences; deviations below
                                     limiter_alpha h^2 (the TVB constant M) are left alone */
 
+/* physicality operator (Sec. 2.5) after every RK stage */
+#define DGSRHD_ENFORCE_OFF 0
+#define DGSRHD_ENFORCE_NODES 1   /* the paper's operator: s = min over the element's nodes */
+#define DGSRHD_ENFORCE_FACES 2   /* the minimum also over the face points of the element's conserved
+                                    polynomial (sum_a phi_a(-+1) U_a along each normal line), which
+                                    the same s smooths toward the mean, so the polynomial is left
+                                    admissible at the faces too (with Gauss-Legendre nodes the
+                                    faces hold no node) */
+
 /* arithmetic of the basis contractions */
 #define DGSRHD_PREC_FP64 0
 #define DGSRHD_PREC_SPLIT 1      /* split precision: the volume term and face traces as 3xTF32
                                     tensor-core products and the lift as FP32 FMAs, all on
                                     deviations from a per-element reference; FP64 elsewhere */
 #define DGSRHD_PREC_3XTF32 DGSRHD_PREC_SPLIT /* the same */
+/* No BF16x3 precision is offered, deliberately: its two-part split of each operand keeps 16
+ * significant bits against 3xTF32's 22, and the tensor-core contractions are not what bounds the
+ * split kernels (the FP64 con2prim and fluxes are), so it would lose accuracy for no speed.  The
+ * code 2 is rejected with DGSRHD_EINVAL like any other unknown precision. */
 
 typedef struct dgsrhd_config {
   int32_t dim;                 /* 1, 2 or 3 */
@@ -110,7 +123,7 @@ typedef struct dgsrhd_config {
   int32_t rk_stages;           /* 1 (forward Euler), 2 (SSPRK2), 3 (SSPRK3) */
   int32_t bc[3][2];            /* DGSRHD_BC_* for the low and high side of each axis */
   double bc_state[3][2][5];    /* Dirichlet primitive (rho, vx, vy, vz, P) per side */
-  int32_t enforce;             /* 1: physicality operator after every RK stage */
+  int32_t enforce;             /* DGSRHD_ENFORCE_*: physicality operator after every RK stage */
   int32_t precision;           /* DGSRHD_PREC_* */
   int32_t nodes;               /* DGSRHD_NODES_*: node family of the collocated basis */
   int32_t limiter;             /* DGSRHD_LIMITER_* */
@@ -265,20 +278,25 @@ int32_t dgsrhd_kernel_times(dgsrhd_ctx* ctx, double* ms, int64_t* counts, int32_
  * deployments that must fix their device footprint at load time.  The paper has no
  * counterpart; this is a deployment variant of the right-hand side.
  *
- * Computes R = dU/dt exactly as dgsrhd_rhs does for the configuration `cfg`, on `stream`
- * (a cudaStream_t, NULL = legacy default stream), with no context.  U (input) and R (output)
- * are caller-owned device arrays in the state layout above; they must not alias.  The scratch
- * is a fixed 64 MiB array in device global memory (8,388,608 doubles) that every GPU loading
- * the library holds until the process exits.  A configuration needs
- *   5 E Nn + 10 dim E Nt + 5 Nt sum_d nface_d + 512 doubles,
- * with Nn = (p+1)^dim, Nt = (p+1)^(dim-1) and nface_d = E (periodic axis) or E + E/n_d; a
- * larger mesh, an invalid configuration or a NULL/aliased array returns DGSRHD_EINVAL before
- * any GPU work.  No call allocates: no cudaMalloc, no cudaFree, no allocating library routine.
+ * Computes R = dU/dt exactly as dgsrhd_rhs does for the configuration `cfg` (the split-precision
+ * kernels for precision = DGSRHD_PREC_SPLIT, the FP64 ones otherwise), on `stream` (a
+ * cudaStream_t, NULL = legacy default stream), with no context.  U (input) and R (output) are
+ * caller-owned device arrays in the state layout above; they must not alias.  The scratch is a
+ * fixed 64 MiB array in device global memory (8,388,608 doubles) that every GPU loading the
+ * library holds until the process exits.  A configuration needs
+ *   5 E Nn + 10 dim E Nt + 5 Nt sum_d nface_d + 576 doubles (+ 5 dim E with split precision),
+ * with Nn = (p+1)^dim, Nt = (p+1)^(dim-1), nface_d = E (periodic axis) or E + E/n_d, and 576 =
+ * 64 slots for each of the 9 device counters; a larger mesh, an invalid configuration or a
+ * NULL/aliased array returns DGSRHD_EINVAL before any GPU work.  No call allocates: no
+ * cudaMalloc, no cudaFree, no allocating library routine.
  *
- * The first call on each device (with that device current) looks up the array's device address
- * and caches it; make that first call before any stream capture.  All calls share the one array
- * and leave their intermediate results in it, so calls whose GPU work can overlap (different
- * streams, or several host threads) race and must be serialised by the caller.
+ * Every call made outside stream capture looks up the array's device address on the current
+ * device (a device reset or another context loads the library's module at a new address); a
+ * call made while `stream` is being captured reuses the address of the last call made outside
+ * capture on that device, and returns DGSRHD_ECUDA if there was none, so make one call before
+ * capturing, and again after a device reset.  All calls share the one array and leave their
+ * intermediate results in it, so calls whose GPU work can overlap (different streams, or
+ * several host threads) race and must be serialised by the caller.
  *
  * stats_out (nullable, HOST): when given, the call synchronises `stream`, fills the con2prim and
  * face-guard counters of this call and returns DGSRHD_EBADSTATE / DGSRHD_EC2P_NOCONV as
@@ -287,7 +305,7 @@ int32_t dgsrhd_rhs_noalloc(const dgsrhd_config* cfg, void* stream, const double*
                            dgsrhd_stats* stats_out);
 
 /* Spatial mean of a squared velocity component, <v_a^2> = (1/|Omega|) int v_a^2 dV, the
- * diagnostic of the Kelvin-Helmholtz study (Sec. 4.4, the mean of v_y^2 whose growth rate the
+ * diagnostic of the Kelvin-Helmholtz study (Sec. 4.5, the mean of v_y^2 whose growth rate the
  * paper fits), by the nodal quadrature of the basis with con2prim at every node.
  * U: DEVICE state [5][E][Nn]; axis: 0, 1 or 2 (v_x, v_y, v_z); out: HOST double.
  * Synchronises the context's stream (the per-block partial sums are added on the host in a
@@ -296,14 +314,44 @@ int32_t dgsrhd_rhs_noalloc(const dgsrhd_config* cfg, void* stream, const double*
  * axis, DGSRHD_ECUDA on a CUDA error; a state con2prim cannot invert gives NaN. */
 int32_t dgsrhd_mean_square_velocity(dgsrhd_ctx* ctx, const double* U, int32_t axis, double* out);
 
-/* Diagnostic (no paper counterpart): the library's FP64 reciprocal and square root primitives
- * next to CUDA's own, for checking the former against the latter.
- * x:   DEVICE, n doubles.  out: DEVICE, 4 n doubles, written as four blocks of n:
+/* Diagnostic (no paper counterpart): the library's FP64 reciprocal and root primitives next to
+ * CUDA's own, for checking the former against the latter.
+ * x:   DEVICE, n doubles.  out: DEVICE, 6 n doubles, written as six blocks of n:
  *      [ reciprocal 1/x by Newton-Raphson refinement of an FP32 seed | 1.0 / x (division) |
- *        sqrt(x) as x rsqrt(x) | sqrt(x) ].
+ *        the library's sqrt(x) | sqrt(x) | the library's x^(-1/3) | rcbrt(x) ]
+ *      (the last two are 0 at x = 0).
  * stream: cudaStream_t or NULL for the default stream; the call only queues the kernel.
  * Returns DGSRHD_EINVAL for null pointers or n < 0, DGSRHD_ECUDA on a launch failure. */
 int32_t dgsrhd_math_check(const double* x, int64_t n, double* out, void* stream);
+
+/* Diagnostic (no paper counterpart): arithmetic throughput probe, the denominator of the FP64
+ * roofline and the cost of the library's FP64 primitives.  Launches one kernel of `threads`
+ * threads (a positive multiple of 256, at most 256 x 65535) on `stream` (cudaStream_t, NULL =
+ * default); each thread runs four independent chains of `iters` applications of one
+ * operation, x <- op(x):
+ *   DGSRHD_PROBE_DFMA    x <- fma(x, a, b) in FP64 (2 flops each: the FP64 peak)
+ *   DGSRHD_PROBE_DDIV    x <- b / x (CUDA's FP64 division)
+ *   DGSRHD_PROBE_DSQRT, DGSRHD_PROBE_DRSQRT, DGSRHD_PROBE_DRCBRT   CUDA's sqrt, rsqrt, rcbrt
+ *   DGSRHD_PROBE_RECIP, DGSRHD_PROBE_SQRT, DGSRHD_PROBE_RCBRT
+ *                        the library's reciprocal, square root and reciprocal cube root (FP32
+ *                        seed, FP64 correction)
+ *   DGSRHD_PROBE_FFMA    x <- fmaf(x, a, b) in FP32.
+ * sink: DEVICE, `threads` doubles (each thread stores its chains' sum).  *ops (nullable, HOST)
+ * receives the number of operations, 4 threads iters; the caller times the kernel (CUDA events
+ * on `stream`) and divides.  Returns DGSRHD_EINVAL for a bad kind, iters < 1, a NULL sink or a
+ * bad thread count, DGSRHD_ECUDA on a launch failure; only queues the kernel. */
+#define DGSRHD_PROBE_DFMA 0
+#define DGSRHD_PROBE_DDIV 1
+#define DGSRHD_PROBE_DSQRT 2
+#define DGSRHD_PROBE_DRSQRT 3
+#define DGSRHD_PROBE_DRCBRT 4
+#define DGSRHD_PROBE_RECIP 5
+#define DGSRHD_PROBE_SQRT 6
+#define DGSRHD_PROBE_RCBRT 7
+#define DGSRHD_PROBE_FFMA 8
+#define DGSRHD_PROBE_KINDS 9
+int32_t dgsrhd_arith_probe(int32_t kind, int64_t iters, double* sink, int64_t threads,
+                           void* stream, int64_t* ops);
 
 /* Human-readable name of a status code. */
 const char* dgsrhd_status_string(int32_t status);

@@ -27,6 +27,8 @@ BC = {"periodic": 0, "dirichlet": 1, "outflow": 2, "reflect": 3}
 PRECISION = {"fp64": 0, "split": 1, "3xtf32": 1}
 NODES = {"gl": 0, "gll": 1}
 KERNEL_KINDS = ("volume", "face", "update", "enforce", "pointwise", "vjp")
+PROBE = {"dfma": 0, "ddiv": 1, "dsqrt": 2, "drsqrt": 3, "drcbrt": 4, "recip": 5, "sqrt": 6,
+         "rcbrt": 7, "ffma": 8}
 
 
 class dgsrhd_config(ctypes.Structure):
@@ -108,6 +110,7 @@ def load() -> ctypes.CDLL:
         "dgsrhd_con2prim_vjp": (i32, [vp, vp, vp, vp]),
         "dgsrhd_math_check": (i32, [vp, i64, vp, vp]),
         "dgsrhd_mean_square_velocity": (i32, [vp, vp, i32, P(d)]),
+        "dgsrhd_arith_probe": (i32, [i32, i64, vp, i64, vp, P(i64)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -127,6 +130,7 @@ def exported_symbols():
         "dgsrhd_set_profiling", "dgsrhd_kernel_times", "dgsrhd_status_string",
         "dgsrhd_rhs_noalloc", "dgsrhd_step_stage", "dgsrhd_stage_save_size", "dgsrhd_stage_vjp",
         "dgsrhd_con2prim_vjp", "dgsrhd_math_check", "dgsrhd_mean_square_velocity",
+        "dgsrhd_arith_probe",
     ]
 
 
@@ -135,6 +139,15 @@ def _enum(table, v):
 
 
 LIMITER = {"none": 0, "moe": 1, "scaling": 1, "minmod": 2}
+ENFORCE = {"off": 0, "nodes": 1, "faces": 2}
+
+
+def _enforce(v) -> int:
+    """Physicality operator of a spec: False/0 off, True/1 on the nodes, "faces"/2 on the nodes
+    and the face points of the element's conserved polynomial."""
+    if isinstance(v, str):
+        return ENFORCE[v]
+    return 2 if v == 2 else int(bool(v))
 
 
 def _limiter(v) -> int:
@@ -175,7 +188,7 @@ def make_config(spec: dict) -> dgsrhd_config:
             for s in range(2):
                 for v in range(5):
                     c.bc_state[k][s][v] = float(bcs[k][s][v])
-    c.enforce = int(bool(spec.get("enforce", True)))
+    c.enforce = _enforce(spec.get("enforce", True))
     c.precision = _enum(PRECISION, spec.get("precision", "fp64"))
     c.nodes = _enum(NODES, spec.get("nodes", "gl"))
     c.limiter = _limiter(spec.get("limiter", False))

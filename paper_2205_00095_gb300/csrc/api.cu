@@ -353,6 +353,7 @@ bool valid_config(const dgsrhd_config* c) {
   if (c->nodes != DGSRHD_NODES_GL && c->nodes != DGSRHD_NODES_GLL) return false;
   if (c->nodes == DGSRHD_NODES_GLL && c->degree < 1) return false;
   if (c->limiter < DGSRHD_LIMITER_NONE || c->limiter > DGSRHD_LIMITER_MINMOD) return false;
+  if (c->enforce < 0 || c->enforce > DGSRHD_ENFORCE_FACES) return false;
   if (c->limiter && !(c->limiter_alpha >= 0.0)) return false;
   return true;
 }
@@ -387,80 +388,18 @@ int32_t dgsrhd_create(const dgsrhd_config* cfg, void* stream, dgsrhd_ctx** out) 
   c->stream = (cudaStream_t)stream;
   c->dim = cfg->dim;
   c->N = cfg->degree + 1;
-  const int N = c->N;
+  long long ntr = 0, fs_total = 0;
+  if (!dgsrhd::params_from_config(cfg, &c->p, &ntr, &fs_total, c->x)) {
+    delete c;
+    return DGSRHD_EINVAL;
+  }
   Params& p = c->p;
-  memset(&p, 0, sizeof p);
-  p.dim = c->dim;
-  p.N = N;
-  p.Nn = 1;
-  p.Nt = 1;
-  for (int d = 0; d < c->dim; ++d) p.Nn *= N;
-  for (int d = 0; d < c->dim - 1; ++d) p.Nt *= N;
-  long long E = 1;
-  for (int d = 0; d < 3; ++d) {
-    p.n[d] = d < c->dim ? cfg->n_elem[d] : 1;
-    p.stride[d] = E;
-    E *= p.n[d];
-    c->dx[d] = d < c->dim ? (cfg->hi[d] - cfg->lo[d]) / (double)p.n[d] : 1.0;
-    p.inv_half_dx[d] = 2.0 / c->dx[d];
-  }
-  p.E = E;
-  for (int d = 0; d < 3; ++d) {
-    p.ndiv[d] = make_fastdiv(p.n[d]);
-    p.sdiv[d] = make_fastdiv(p.stride[d]);
-  }
+  for (int d = 0; d < 3; ++d) c->dx[d] = d < c->dim ? (cfg->hi[d] - cfg->lo[d]) / (double)p.n[d] : 1.0;
+  const long long E = p.E;
   c->E = E;
   c->Nn = p.Nn;
   c->nstate = 5 * E * p.Nn;
-  long long off = 0;
-  for (int d = 0; d < 3; ++d) {
-    if (d < c->dim) {
-      p.nface[d] = E + (cfg->bc[d][0] == DGSRHD_BC_PERIODIC ? 0 : E / p.n[d]);
-      p.fs_off[d] = off;
-      off += 5 * p.nface[d] * p.Nt;
-    }
-    for (int s = 0; s < 2; ++s) p.bc[d][s] = d < c->dim ? cfg->bc[d][s] : 0;
-    for (int s = 0; s < 2; ++s) {
-      const double* b = cfg->bc_state[d][s];
-      const double v2 = b[1] * b[1] + b[2] * b[2] + b[3] * b[3];
-      const double lor = (v2 < 1.0) ? 1.0 / sqrt(1.0 - v2) : 1.0;
-      p.ghost[d][s][0] = b[0];
-      p.ghost[d][s][1] = lor * b[1];
-      p.ghost[d][s][2] = lor * b[2];
-      p.ghost[d][s][3] = lor * b[3];
-      p.ghost[d][s][4] = b[4];
-    }
-  }
-  const long long fs_total = off;
   c->fs_total = fs_total;
-  p.eos = cfg->eos;
-  p.gamma_ad = cfg->gamma_ad;
-  p.alpha = cfg->eos == DGSRHD_EOS_IDEAL ? cfg->gamma_ad / (cfg->gamma_ad - 1.0) : 0.0;
-  p.c2p = cfg->c2p == DGSRHD_C2P_DEFAULT ? (cfg->eos == DGSRHD_EOS_IDEAL ? 0 : 1) : cfg->c2p;
-  p.max_iter = cfg->c2p_max_iter > 0 ? cfg->c2p_max_iter : (cfg->eos == DGSRHD_EOS_IDEAL ? 30 : 100);
-  p.c2p_rtol = cfg->c2p_rtol;
-  p.flux = cfg->flux;
-  {
-    double h = 1e300;
-    for (int d = 0; d < cfg->dim; ++d) h = fmin(h, (cfg->hi[d] - cfg->lo[d]) / (double)cfg->n_elem[d]);
-    p.limiter = cfg->limiter;
-    // scaling limiter: bound relaxation alpha h^(3/2); minmod: TVB threshold M h^2
-    p.lim_alpha = cfg->limiter == DGSRHD_LIMITER_SCALING  ? cfg->limiter_alpha * pow(h, 1.5)
-                  : cfg->limiter == DGSRHD_LIMITER_MINMOD ? cfg->limiter_alpha * h * h
-                                                          : 0.0;
-  }
-  if (cfg->nodes == DGSRHD_NODES_GLL)
-    gauss_lobatto(N, c->x, p.w);
-  else
-    gauss_legendre(N, c->x, p.w);
-  basis_tables(N, c->x, p.w, p.Dhat, p.em, p.ep);
-  for (int i = 0; i < N; ++i) {
-    p.lm[i] = p.em[i] / p.w[i];
-    p.lp[i] = p.ep[i] / p.w[i];
-  }
-  p.wsum = (double)(1 << c->dim);
-
-  const long long ntr = 2LL * c->dim * 5 * E * p.Nt;
   cudaError_t e = cudaSuccess;
   if (e == cudaSuccess) e = alloc(&c->A, c->nstate);
   if (e == cudaSuccess) e = alloc(&c->Rv, c->nstate);
@@ -958,6 +897,15 @@ int32_t dgsrhd_math_check(const double* x, int64_t n, double* out, void* stream)
   return cuda_status(dgsrhd::launch_math_check((cudaStream_t)stream, n, x, out));
 }
 
+int32_t dgsrhd_arith_probe(int32_t kind, int64_t iters, double* sink, int64_t threads,
+                           void* stream, int64_t* ops) {
+  if (kind < 0 || kind >= DGSRHD_PROBE_KINDS || iters < 1 || !sink || threads < 256 ||
+      threads % 256 != 0 || threads > (int64_t)256 * 65535)
+    return DGSRHD_EINVAL;
+  if (ops) *ops = 4 * threads * iters;
+  return cuda_status(dgsrhd::launch_fp64_probe((cudaStream_t)stream, kind, iters, threads, sink));
+}
+
 const char* dgsrhd_status_string(int32_t s) {
   switch (s) {
     case DGSRHD_OK: return "ok";
@@ -974,13 +922,13 @@ const char* dgsrhd_status_string(int32_t s) {
 }  // extern "C"
 
 // ---------------------------------------------------------------------------------------
-// Launch parameters straight from a configuration, for callers without a context (the
-// static-scratch right-hand side).  Same tables and layout as dgsrhd_create.
+// Launch parameters of a configuration: mesh, face-flux layout, method choices and the basis
+// tables.  dgsrhd_create and the static-scratch right-hand side both take them from here.
 // ---------------------------------------------------------------------------------------
 namespace dgsrhd {
 
 bool params_from_config(const dgsrhd_config* cfg, Params* out, long long* n_trace,
-                        long long* n_face_flux) {
+                        long long* n_face_flux, double* nodes) {
   if (!valid_config(cfg) || !out) return false;
   Params p;
   memset(&p, 0, sizeof p);
@@ -1024,10 +972,21 @@ bool params_from_config(const dgsrhd_config* cfg, Params* out, long long* n_trac
   p.eos = cfg->eos;
   p.gamma_ad = cfg->gamma_ad;
   p.alpha = cfg->eos == DGSRHD_EOS_IDEAL ? cfg->gamma_ad / (cfg->gamma_ad - 1.0) : 0.0;
+  {
+    const double G = cfg->gamma_ad;
+    p.gm1 = G - 1.0;
+    p.gm1sq = p.gm1 * p.gm1;
+    p.m2G = -2.0 * G;
+    p.m2Ggm1 = -2.0 * G * p.gm1;
+    p.G2 = G * G;
+    p.tgm1 = 2.0 * p.gm1;
+    p.amG = p.alpha - G;
+  }
   p.c2p = cfg->c2p == DGSRHD_C2P_DEFAULT ? (cfg->eos == DGSRHD_EOS_IDEAL ? 0 : 1) : cfg->c2p;
   p.max_iter = cfg->c2p_max_iter > 0 ? cfg->c2p_max_iter : (cfg->eos == DGSRHD_EOS_IDEAL ? 30 : 100);
   p.c2p_rtol = cfg->c2p_rtol;
   p.flux = cfg->flux;
+  p.enforce_faces = cfg->enforce == DGSRHD_ENFORCE_FACES;
   {
     double h = 1e300;
     for (int d = 0; d < cfg->dim; ++d) h = fmin(h, (cfg->hi[d] - cfg->lo[d]) / (double)cfg->n_elem[d]);
@@ -1049,6 +1008,8 @@ bool params_from_config(const dgsrhd_config* cfg, Params* out, long long* n_trac
   }
   p.wsum = (double)(1 << dim);
   *out = p;
+  if (nodes)
+    for (int i = 0; i < N; ++i) nodes[i] = x[i];
   if (n_trace) *n_trace = 2LL * dim * 5 * E * p.Nt;
   if (n_face_flux) *n_face_flux = off;
   return true;

@@ -1,4 +1,4 @@
-// FP64 <-> FP32 conversions on the bit patterns, and two FP64 primitives built on them.
+// FP64 <-> FP32 conversions on the bit patterns, and the FP64 reciprocal and roots built on them.
 //
 // On this GPU FP64<->FP32 conversion instructions issue on the FP64 pipe at the DFMA rate,
 // which is the bottleneck of every FP64 kernel here, so conversions are done with integer
@@ -92,10 +92,46 @@ __device__ __forceinline__ double recip_nr(double x) {
   return fma(r, t, r);
 }
 
-// sqrt(y) as y rsqrt(y) (about 1.7 DFMA-equivalents cheaper than sqrt here) for finite y > 0,
-// within a few ulp of sqrt; y for y = +-0, NaN for y < 0, y = +inf or NaN.
-__device__ __forceinline__ double sqrt_rs(double y) {
-  return (__double_as_longlong(y) << 1) == 0 ? y : y * rsqrt(y);
+// Roots from an FP32 seed and one third-order correction.  The seed r0 ~ x^(-1/2) (MUFU's FP32
+// reciprocal square root, within 2 FP32 ulp) or r0 ~ |x|^(-1/3) (below) has relative error below
+// 2^-20; with h = 1 - x r0^2 (resp. 1 - |x| r0^3), formed by one fused multiply-add, the
+// binomial series
+//   (1 - h)^(-1/2) = 1 + h/2 + 3h^2/8 + O(h^3),   (1 - h)^(-1/3) = 1 + h/3 + 2h^2/9 + O(h^3)
+// gives sqrt(x) = x r0 (1 - h)^(-1/2) and x^(-1/3) = r0 (1 - h)^(-1/3) with a truncation error
+// O(h^3) < 2^-60: the result is within about one ulp, from five or six FP64 instructions where
+// CUDA's sqrt and rcbrt take more (CUDA's rsqrt already costs about five, and is used as is).
+// Outside [2^-120, 2^120] (where the FP32 seed would not be a normal number), for zero, negative
+// (square root), infinite or NaN arguments, CUDA's own function is used.
+__device__ __forceinline__ bool seed_range(double x) {
+  const int e = (__double2hiint(x) >> 20) & 0x7ff;
+  return e >= 1023 - 120 && e <= 1023 + 120;
+}
+
+// sqrt(y) for y >= 0 (y itself for +-0, NaN for y < 0)
+__device__ __forceinline__ double sqrt_nr(double y) {
+  if (__double2hiint(y) < 0 || !seed_range(y))
+    return (__double_as_longlong(y) << 1) == 0 ? y : y * rsqrt(y);
+  const double r0 = f32_to_f64_bits(rsqrtf(f64_to_f32_bits(y)));
+  const double s0 = y * r0;
+  const double h = fma(-s0, r0, 1.0);
+  return fma(s0, h * fma(h, 0.375, 0.5), s0);
+}
+
+// y^(-1/3) with the sign of y (y != 0).  FP32 seed: the bit pattern of |y|^(-1/3) is about
+// K - bits(|y|)/3 with K = (4/3) 127 2^23 (the exponent field read as a logarithm), refined by
+// three FP32 Newton steps r <- r (4 - a r^3)/3 to within ~5e-7.
+__device__ __forceinline__ double rcbrt_nr(double y) {
+  if (!seed_range(y)) return rcbrt(y);
+  const long long sign = __double_as_longlong(y) & (long long)0x8000000000000000ULL;
+  const double ay = __longlong_as_double(__double_as_longlong(y) ^ sign);  // |y|
+  const float a = f64_to_f32_bits(ay);
+  float r = __uint_as_float(0x54aaaaaau - __float_as_uint(a) / 3u);
+#pragma unroll
+  for (int k = 0; k < 3; ++k) r = r * (4.0f - (a * r) * (r * r)) * (1.0f / 3.0f);
+  const double r0 = f32_to_f64_bits(r);
+  const double h = fma(-(ay * r0), r0 * r0, 1.0);
+  const double q = fma(r0, h * fma(h, 2.0 / 9.0, 1.0 / 3.0), r0);
+  return __longlong_as_double(__double_as_longlong(q) | sign);
 }
 
 }  // namespace dgsrhd

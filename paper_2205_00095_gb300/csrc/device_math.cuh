@@ -86,44 +86,49 @@ __device__ __forceinline__ bool admissible(const double U[5]) {
 // Conserved -> primitive (Sec. 3).  xi = |S|/D, eta = E/D.
 // ---------------------------------------------------------------------------------------
 
-// Ideal EOS, closed form: monic quartic beta^4 + a3 beta^3 + a2 beta^2 + a1 beta + a0 with
-// the coefficients of Sec. 3.1, its resolvent cubic (i1, i2, i3), Cardano's root x of the
-// resolvent (trigonometric form when T < 0), the quadratic factor beta^2 + B beta + C.
-__device__ __forceinline__ double beta_ideal_closed_form(double G, double xi, double eta,
-                                                         double inv) {
-  // inv = 1 / ((G - 1)^2 (1 + xi^2)) is passed in (formed with 1/D from one division)
-  const double gm1 = G - 1.0;
-  const double a1 = -2.0 * G * xi * eta * inv;
-  const double a3 = gm1 * a1;
-  const double a2 = (G * G * eta * eta + 2.0 * gm1 * xi * xi - gm1 * gm1) * inv;
-  const double a0 = xi * xi * inv;
+// Ideal EOS, closed form (Sec. 3.1): the monic quartic beta^4 + a3 beta^3 + a2 beta^2 + a1 beta
+// + a0 in beta = |v|, its resolvent cubic (i1, i2, i3), Cardano's root x of the resolvent
+// (trigonometric form when T < 0), and the quadratic factors beta^2 + B beta + C.  The section's
+// coefficients, in xi = |S|/D and eta = E/D over (G - 1)^2 (1 + xi^2), are multiplied through by
+// D^2 so that they come from (D^2, |S|, E) and the one reciprocal w = 1/((G - 1)^2 (D^2 + |S|^2)):
+//   a0 = |S|^2 w,  a1 = -2 G |S| E w,  a3 = (G - 1) a1,
+//   a2 = (G^2 E^2 + 2 (G - 1) |S|^2 - (G - 1)^2 D^2) w.
+// B and C are carried doubled (B' = 2B, C' = 2C), which moves the factors 1/2 into the final
+// 1/4: beta = (sqrt(B'^2 - 8 C') - B') / 4 (scalings by powers of two are exact).
+__device__ __forceinline__ double beta_ideal_closed_form(const Params& p, double D2, double S2,
+                                                         double S, double E, double w) {
+  const double a0 = S2 * w;
+  const double SEw = (S * E) * w;
+  const double a1 = p.m2G * SEw;
+  const double a3 = p.m2Ggm1 * SEw;
+  const double a2 = fma(p.G2, E * E, fma(p.tgm1, S2, -p.gm1sq * D2)) * w;
   const double i1 = -a2;
   const double i2 = a3 * a1 - 4.0 * a0;
   const double i3 = 4.0 * a2 * a0 - a1 * a1 - a3 * a3 * a0;
   const double R = (9.0 * i1 * i2 - 27.0 * i3 - 2.0 * i1 * i1 * i1) * (1.0 / 54.0);
-  const double S = (3.0 * i2 - i1 * i1) * (1.0 / 9.0);
-  const double T = R * R + S * S * S;
+  const double Sq = (3.0 * i2 - i1 * i1) * (1.0 / 9.0);
+  const double T = R * R + Sq * Sq * Sq;
   double x;
   if (dbits(T) < 0 && dbits(T) != (long long)0x8000000000000000ULL) {  // T < 0
     x = 2.0 * pow(R * R - T, 1.0 / 6.0) * cos(atan2(sqrt(-T), R) * (1.0 / 3.0)) - i1 * (1.0 / 3.0);
   } else {
-    // Cardano's pair cbrt(R + sqrt(T)) + cbrt(R - sqrt(T)): their product is -S, so with
-    // y = R + sign(R) sqrt(T) (no cancellation) the pair is y^(1/3) - S y^(-1/3), both from
+    // Cardano's pair cbrt(R + sqrt(T)) + cbrt(R - sqrt(T)): their product is -Sq, so with
+    // y = R + sign(R) sqrt(T) (no cancellation) the pair is y^(1/3) - Sq y^(-1/3), both from
     // one reciprocal cube root r = y^(-1/3): y^(1/3) = y r^2.
-    const double y = R + copysign(sqrt_rs(T), R);
+    const double y = R + copysign(sqrt_nr(T), R);
     if (y == 0.0) {
       x = -i1 * (1.0 / 3.0);
     } else {
-      const double r = rcbrt(y);
-      x = fma(y * r, r, -S * r) - i1 * (1.0 / 3.0);
+      const double r = rcbrt_nr(y);
+      x = fma(y * r, r, -Sq * r) - i1 * (1.0 / 3.0);
     }
   }
   // The three radicands are non-negative for an admissible state; as xi -> 0 they shrink to
   // rounding level and can round below zero, so a negative one is taken as zero.
-  auto root0 = [](double r) { return sqrt_rs(dbits(r) < 0 ? 0.0 : r); };
-  const double B = 0.5 * (a3 + root0(a3 * a3 - 4.0 * a2 + 4.0 * x));
-  const double C = 0.5 * (x - root0(x * x - 4.0 * a0));
-  return 0.5 * (-B + root0(B * B - 4.0 * C));
+  auto root0 = [](double r) { return sqrt_nr(dbits(r) < 0 ? 0.0 : r); };
+  const double Bp = a3 + root0(fma(a3, a3, 4.0 * (x - a2)));
+  const double Cp = x - root0(fma(x, x, -4.0 * a0));
+  return 0.25 * (root0(fma(Bp, Bp, -8.0 * Cp)) - Bp);
 }
 
 // Ideal EOS, Newton-Raphson on the Riccardi quartic in w, beta = 2w/(1 + w^2)
@@ -229,11 +234,11 @@ __device__ __forceinline__ double W_tm_closed_form(double xi, double eta) {
     // Cardano's pair cbrt(R + sqrt(d)) + cbrt(R - sqrt(d)): the product of the two is -Q, so
     // with y = R + sign(R) sqrt(d) (no cancellation) the pair is y^(1/3) - Q y^(-1/3), from one
     // reciprocal cube root
-    const double y = R + copysign(sqrt_rs(d), R);
+    const double y = R + copysign(sqrt_nr(d), R);
     if (y == 0.0) {
       W = -c.c1 * (1.0 / 3.0);
     } else {
-      const double r = rcbrt(y);
+      const double r = rcbrt_nr(y);
       W = fma(y * r, r, -Q * r) - c.c1 * (1.0 / 3.0);
     }
   }
@@ -418,20 +423,6 @@ __device__ __forceinline__ int con2prim(const Params& p, const double U[5], Prim
   const double rS = moving ? rsqrt(S2) : 0.0;  // 1/|S|
   const double S = S2 * rS;
   const bool closed_ideal = p.eos == 0 && p.c2p == 0;
-  double iD, inv = 0.0;
-  if (closed_ideal) {
-    // 1/D and the quartic's 1/((G - 1)^2 (1 + xi^2)) = D^2/((G - 1)^2 (D^2 + S^2)) from one
-    // division: t = 1/(D (G - 1)^2 (D^2 + S^2))
-    const double gm1 = p.gamma_ad - 1.0;
-    const double q = gm1 * gm1 * fma(D, D, S2);
-    const double t = recip_nr(D * q);
-    iD = t * q;
-    inv = t * D * D * D;
-  } else {
-    iD = recip_nr(D);
-  }
-  const double xi = S * iD;
-  const double eta = fma(tau, iD, 1.0);
   // beta = |v|, ginv = 1/gamma, omg = 1 - 1/gamma (cancellation-free per method)
   double beta, ginv, lor, omg = 0.0, Wl = 0.0;
   bool conv = true;
@@ -440,34 +431,40 @@ __device__ __forceinline__ int con2prim(const Params& p, const double U[5], Prim
     ginv = 1.0;
     lor = 1.0;
   } else if (closed_ideal) {
-    beta = beta_ideal_closed_form(p.gamma_ad, xi, eta, inv);
+    const double D2 = D * D;
+    beta = beta_ideal_closed_form(p, D2, S2, S, tau + D, recip_nr(p.gm1sq * (D2 + S2)));
     conv = dbits(beta) >= 0 && dbits(beta) < dbits(1.0);  // 0 <= beta < 1
-    // gamma = (1 - beta^2)^(-1/2) from rsqrt; 1 - 1/gamma = beta^2 gamma / (gamma + 1)
+    // gamma = (1 - beta^2)^(-1/2); 1 - 1/gamma = beta^2 gamma / (gamma + 1)
     const double b2 = beta * beta;
     const double om = 1.0 - b2;
     lor = rsqrt(om);
     ginv = om * lor;
     omg = b2 * recip_nr(1.0 + ginv);  // = b2 gamma / (gamma + 1)
-  } else if (p.eos == 0) {
-    const double w = w_ideal_newton(p.alpha, xi, eta, p.max_iter, p.c2p_rtol, iters, conv);
-    const double w2 = w * w;
-    // beta = 2w/(1 + w^2), 1/gamma = (1 - w^2)/(1 + w^2), gamma from the same division
-    const double ap = 1.0 + w2, am = 1.0 - w2;
-    const double t = recip_nr(ap * am);
-    const double i1w2 = t * am;
-    beta = 2.0 * w * i1w2;
-    ginv = am * i1w2;
-    omg = 2.0 * w2 * i1w2;
-    lor = t * ap * ap;
-    conv = conv && dbits(w) > 0 && dbits(w) < dbits(1.0);  // 0 < w < 1
   } else {
-    Wl = (p.c2p == 0) ? W_tm_closed_form(xi, eta)
-                      : W_tm_brent(xi, eta, p.max_iter, p.c2p_rtol, iters, conv);
-    conv = conv && dbits(Wl) >= 0 && finite_bits(Wl);  // Wl >= 0 and finite
-    const double q = Wl + 1.0;  // gamma^2
-    ginv = rsqrt(q);
-    lor = q * ginv;
-    beta = sqrt_rs(Wl) * ginv;
+    const double iD = recip_nr(D);
+    const double xi = S * iD;
+    const double eta = fma(tau, iD, 1.0);
+    if (p.eos == 0) {
+      const double w = w_ideal_newton(p.alpha, xi, eta, p.max_iter, p.c2p_rtol, iters, conv);
+      const double w2 = w * w;
+      // beta = 2w/(1 + w^2), 1/gamma = (1 - w^2)/(1 + w^2), gamma from the same division
+      const double ap = 1.0 + w2, am = 1.0 - w2;
+      const double t = recip_nr(ap * am);
+      const double i1w2 = t * am;
+      beta = 2.0 * w * i1w2;
+      ginv = am * i1w2;
+      omg = 2.0 * w2 * i1w2;
+      lor = t * ap * ap;
+      conv = conv && dbits(w) > 0 && dbits(w) < dbits(1.0);  // 0 < w < 1
+    } else {
+      Wl = (p.c2p == 0) ? W_tm_closed_form(xi, eta)
+                        : W_tm_brent(xi, eta, p.max_iter, p.c2p_rtol, iters, conv);
+      conv = conv && dbits(Wl) >= 0 && finite_bits(Wl);  // Wl >= 0 and finite
+      const double q = Wl + 1.0;  // gamma^2
+      ginv = rsqrt(q);
+      lor = q * ginv;
+      beta = sqrt_nr(Wl) * ginv;
+    }
   }
   const double rho = D * ginv;
   const double vs = beta * rS;  // v = beta S / |S|
@@ -478,7 +475,7 @@ __device__ __forceinline__ int con2prim(const Params& p, const double U[5], Prim
   double P;
   if (p.eos == 0) {
     const double e_m_rho = tau - Sv + D * omg;  // E - S.v - rho
-    P = (p.gamma_ad - 1.0) * e_m_rho;
+    P = p.gm1 * e_m_rho;
   } else {
     // 1 - 1/gamma = W/(gamma (gamma + 1)) and P = (E - S.v - rho)(E - S.v + rho)/(3(E - S.v)):
     // 1/(gamma + 1) and 1/(3(E - S.v)) from one division
@@ -544,7 +541,7 @@ __device__ __forceinline__ void face_state_core(const Params& p, const double Wu
   c.P = P;
   if (p.eos == 0) {
     c.A = p.gamma_ad * P;
-    c.K = __dsub_rn(fma(p.alpha, P, rho), c.A);
+    c.K = fma(p.amG, P, rho);  // rho + (alpha - Gamma) P
     c.sg = c.isg = c.Z = c.iZ = 0.0;
   } else {
     const double x2 = fma(P, P, (4.0 / 9.0) * rho * rho);
@@ -597,7 +594,7 @@ __device__ __forceinline__ void wavespeeds_full(const FaceState& c, double& lm, 
                                                 const double* ir_saved) {
   const double vd = c.v[D];
   X = c.A * fma(c.B, fma(-vd, vd, 1.0), c.A);
-  ir = ir_saved ? *ir_saved : (X > 0.0 ? rsqrt(X) : 0.0);
+  ir = ir_saved ? *ir_saved : (pos_bits(X) ? rsqrt(X) : 0.0);
   r = X * ir;
   lm = fma(vd, c.B, -r) * c.i;
   lp = fma(vd, c.B, r) * c.i;
@@ -673,13 +670,14 @@ __device__ __forceinline__ void hllc_flux(const FaceState& L, const FaceState& R
   for (int k = 0; k < 5; ++k) Fs[k] = fma(lam, Us[k] - UK[k], FK[k]);
 }
 
-// Numerical flux along axis D between face states given as (rho, u, P).  HLL: S_L =
-// min(lambda_L, 0), S_R = max(lambda_R, 0), (S_R F_L - S_L F_R + S_L S_R (U_R - U_L)) /
-// (S_R - S_L) (the average when both vanish); LLF: (F_L + F_R)/2 - a (U_R - U_L)/2 with
-// a = max |lambda|.
+// Numerical flux along axis D between face states given as (rho, u, P), returned DOUBLED (2 F*:
+// the factor 1/2 of LLF and of the HLL denominator moves into the lift coefficients, which
+// are exact powers-of-two scalings of the tables).  HLL: S_L = min(lambda_L, 0), S_R =
+// max(lambda_R, 0), F* = (S_R F_L - S_L F_R + S_L S_R (U_R - U_L)) / (S_R - S_L) (the average when
+// both vanish); LLF: F* = (F_L + F_R)/2 - a (U_R - U_L)/2 with a = max |lambda|; HLLC as above.
 template <int D>
 __device__ __forceinline__ void numerical_flux(const Params& p, const double WL[5],
-                                               const double WR[5], double Fs[5],
+                                               const double WR[5], double Fs2[5],
                                                double recL[kFaceTape], double recR[kFaceTape]) {
   FaceState L, R;
   face_state(p, WL, L);
@@ -698,18 +696,21 @@ __device__ __forceinline__ void numerical_flux(const Params& p, const double WL[
     const double den = sR - sL;
     if (den == 0.0) {
 #pragma unroll
-      for (int v = 0; v < 5; ++v) Fs[v] = 0.5 * (FL[v] + FR[v]);
+      for (int v = 0; v < 5; ++v) Fs2[v] = FL[v] + FR[v];
     } else {
-      const double id = recip_nr(den);
+      const double id2 = recip_nr(0.5 * den);  // 2 / (S_R - S_L)
 #pragma unroll
-      for (int v = 0; v < 5; ++v) Fs[v] = (sR * FL[v] - sL * FR[v] + sL * sR * (R.U[v] - L.U[v])) * id;
+      for (int v = 0; v < 5; ++v) Fs2[v] = (sR * FL[v] - sL * FR[v] + sL * sR * (R.U[v] - L.U[v])) * id2;
     }
   } else if (p.flux == 2) {
+    double Fs[5];
     hllc_flux<D>(L, R, FL, FR, lamL, lamR, Fs);
+#pragma unroll
+    for (int v = 0; v < 5; ++v) Fs2[v] = 2.0 * Fs[v];
   } else {
     const double a = fmax(fabs(lamL), fabs(lamR));
 #pragma unroll
-    for (int v = 0; v < 5; ++v) Fs[v] = 0.5 * (FL[v] + FR[v]) - 0.5 * a * (R.U[v] - L.U[v]);
+    for (int v = 0; v < 5; ++v) Fs2[v] = fma(-a, R.U[v] - L.U[v], FL[v] + FR[v]);
   }
 }
 

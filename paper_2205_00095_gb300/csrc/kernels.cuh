@@ -6,7 +6,8 @@
 //                   R_vol[i] = sum_d (2/dx_d) sum_a Dhat[i_d][a] F^d[.. a ..] (Eq. quad-vol-flux at
 //                   the nodes), and the primitive (rho, u, P) extrapolated to the 2 dim faces of the
 //                   element, sum_i phi_i(+-1) W_i along each normal line (Sec. 2.3).
-//   face_kernel   : one thread per face point; LLF/HLL flux of the two traces (Sec. 2.4).
+//   face_kernel   : one thread per face point; LLF/HLL flux of the two traces (Sec. 2.4), stored
+//                   doubled (2 F*; the lift tables carry the 1/2).
 //   update_kernel : per element, one thread per node; R = R_vol - lift of the face fluxes
 //                   (Eq. quad-surface-flux), the Shu-Osher combination, and the physicality
 //                   operator of Sec. 2.5.
@@ -289,7 +290,7 @@ __device__ __forceinline__ void face_point(const Params& p, const double* __rest
     if (p.bc[D][1] == 3) WR[1 + D] = -WR[1 + D];
   }
   double F[5], rec[2][kFaceTape];
-  numerical_flux<D>(p, WL, WR, F, rec[0], rec[1]);
+  numerical_flux<D>(p, WL, WR, F, rec[0], rec[1]);  // F = 2 F*
   double* out = Fs + p.fs_off[D];
   if (pairs) {
     float2* outp = reinterpret_cast<float2*>(out);
@@ -324,23 +325,89 @@ __global__ void __launch_bounds__(128) face_kernel(Params p, const double* __res
 
 // ---------------------------------------------------------------------------------------
 // Physicality operator on the elements of one block (Sec. 2.5).  u holds this thread's node
-// state; on return it holds the smoothed state.  Every thread of the block must call it.
+// state; on return it holds the smoothed state.  Every thread of the block must call it.  With
+// p.enforce_faces the element's points are its nodes and the face points of its conserved
+// polynomial (sum_a phi_a(-+1) U_a along each normal line): smoothing the nodes by s smooths
+// every face point by the same s (the basis reproduces constants), so the minimum over both
+// leaves the polynomial admissible at the faces too.
 // ---------------------------------------------------------------------------------------
 template <int DIM, int N, int BLOCKSZ = Shape<DIM, N>::BLOCK>
 struct EnforceShared {
   double a[5][BLOCKSZ];
+  double u[5][BLOCKSZ];  // the nodal states themselves (face-point variant)
   double mean[Shape<DIM, N>::EPB][5];
   double s[Shape<DIM, N>::EPB];
   int flag[Shape<DIM, N>::EPB];
 };
 
+// Largest factor s_i in [0, 1] for one point with conserved state X and admissible element
+// mean m: the two stages of Sec. 2.5 (Eqs. first_stage_positivity, first_stage_smoothed_state,
+// second_stage_quatratic with the coefficients of Eq. second_stage_coefficients in the stored
+// variables, the root of Eq. second_stage_solution as 2 c0 / (-b + sqrt(b^2 - 4 a c0)) clamped to
+// [0, 1]).
+__device__ __forceinline__ double point_factor(const double X[5], const double m[5]) {
+  const double Db = m[0], taub = m[4], Eb = m[4] + m[0];
+  // stage 1: largest factors keeping D and E positive (Eq. first_stage_positivity)
+  const double sD = X[0] >= 0.0 ? 1.0 : Db / (Db - X[0]);
+  const double Ei = X[4] + X[0];
+  const double sE = Ei >= 0.0 ? 1.0 : Eb / (Eb - Ei);
+  const double s1 = fmin(sD, sE);
+  double U1[5];
+#pragma unroll
+  for (int v = 0; v < 5; ++v) U1[v] = s1 * X[v] + (1.0 - s1) * m[v];
+  if (admissible(U1)) return s1;
+  // stage 2 quadratic a s^2 + b s + c0 > 0 in the stored variables (Eq.
+  // second_stage_coefficients with E = tau + D)
+  const double dD = U1[0] - Db, dtau = U1[4] - taub;
+  const double d1 = U1[1] - m[1], d2 = U1[2] - m[2], d3 = U1[3] - m[3];
+  const double qa = dtau * (dtau + 2.0 * dD) - (d1 * d1 + d2 * d2 + d3 * d3);
+  const double qb = 2.0 * (taub * (dtau + dD) + Db * dtau - (m[1] * d1 + m[2] * d2 + m[3] * d3));
+  const double qc = taub * (taub + 2.0 * Db) - (m[1] * m[1] + m[2] * m[2] + m[3] * m[3]);
+  const double den = -qb + sqrt(qb * qb - 4.0 * qa * qc);
+  double s2 = den > 0.0 ? 2.0 * qc / den : 1.0;
+  s2 = fmin(fmax(s2, 0.0), 1.0);
+  return s1 * s2;
+}
+
+// Conserved state of the block-local element le at its face point fp (= (d 2 + side) Nt + t),
+// from the nodal states in shared memory.
 template <int DIM, int N, int BLOCKSZ>
+__device__ __forceinline__ void face_point_state(const Params& p, const double (&su)[5][BLOCKSZ],
+                                                 int le, int fp, double out[5]) {
+  constexpr int Nn = Shape<DIM, N>::Nn, Nt = Shape<DIM, N>::Nt;
+  const int d = fp / (2 * Nt), side = (fp / Nt) & 1, t = fp % Nt;
+#pragma unroll
+  for (int v = 0; v < 5; ++v) out[v] = 0.0;
+#pragma unroll
+  for (int a = 0; a < N; ++a) {
+    const int node = le * Nn + line_node<DIM, N>(d, t, a);
+    const double c = side ? p.ep[a] : p.em[a];
+#pragma unroll
+    for (int v = 0; v < 5; ++v) out[v] = fma(c, su[v][node], out[v]);
+  }
+}
+
+// FACES: the face-point variant (p.enforce_faces), a template parameter so that the nodal
+// operator's kernels carry none of its registers.
+template <bool FACES, int DIM, int N, int BLOCKSZ>
 __device__ __forceinline__ void enforce_block(const Params& p, double u[5], bool valid, int le,
                                               int li, long long e, double* s_out,
                                               EnforceShared<DIM, N, BLOCKSZ>& sh) {
-  constexpr int Nn = Shape<DIM, N>::Nn;
+  constexpr int Nn = Shape<DIM, N>::Nn, NFP = Shape<DIM, N>::NFP;
   const int tid = threadIdx.x;
-  const bool bad = valid && !admissible(u);
+  bool bad = valid && !admissible(u);
+  if (FACES) {
+#pragma unroll
+    for (int v = 0; v < 5; ++v) sh.u[v][tid] = valid ? u[v] : 0.0;
+    __syncthreads();
+    if (valid) {
+      for (int fp = li; fp < NFP; fp += Nn) {
+        double X[5];
+        face_point_state<DIM, N, BLOCKSZ>(p, sh.u, le, fp, X);
+        if (!admissible(X)) bad = true;
+      }
+    }
+  }
   if (!__syncthreads_or(bad)) {
     if (valid && li == 0 && s_out) s_out[e] = 1.0;
     return;
@@ -369,30 +436,13 @@ __device__ __forceinline__ void enforce_block(const Params& p, double u[5], bool
   const int fl = valid ? sh.flag[le] : 0;
   double si = 1.0;
   if (fl == 2) {
-    const double* m = sh.mean[le];
-    const double Db = m[0], taub = m[4], Eb = m[4] + m[0];
-    // stage 1: largest factors keeping D and E positive (Eq. first_stage_positivity)
-    const double sD = u[0] >= 0.0 ? 1.0 : Db / (Db - u[0]);
-    const double Ei = u[4] + u[0];
-    const double sE = Ei >= 0.0 ? 1.0 : Eb / (Eb - Ei);
-    const double s1 = fmin(sD, sE);
-    double U1[5];
-#pragma unroll
-    for (int v = 0; v < 5; ++v) U1[v] = s1 * u[v] + (1.0 - s1) * m[v];
-    si = s1;
-    if (!admissible(U1)) {
-      // stage 2 quadratic a s^2 + b s + c0 > 0 in the stored variables (Eq.
-      // second_stage_coefficients with E = tau + D), root of Eq. second_stage_solution in
-      // the form 2 c0 / (-b + sqrt(b^2 - 4 a c0)), clamped to [0, 1]
-      const double dD = U1[0] - Db, dtau = U1[4] - taub;
-      const double d1 = U1[1] - m[1], d2 = U1[2] - m[2], d3 = U1[3] - m[3];
-      const double qa = dtau * (dtau + 2.0 * dD) - (d1 * d1 + d2 * d2 + d3 * d3);
-      const double qb = 2.0 * (taub * (dtau + dD) + Db * dtau - (m[1] * d1 + m[2] * d2 + m[3] * d3));
-      const double qc = taub * (taub + 2.0 * Db) - (m[1] * m[1] + m[2] * m[2] + m[3] * m[3]);
-      const double den = -qb + sqrt(qb * qb - 4.0 * qa * qc);
-      double s2 = den > 0.0 ? 2.0 * qc / den : 1.0;
-      s2 = fmin(fmax(s2, 0.0), 1.0);
-      si = s1 * s2;
+    si = point_factor(u, sh.mean[le]);
+    if (FACES) {
+      for (int fp = li; fp < NFP; fp += Nn) {
+        double X[5];
+        face_point_state<DIM, N, BLOCKSZ>(p, sh.u, le, fp, X);
+        si = fmin(si, point_factor(X, sh.mean[le]));
+      }
     }
   }
   sh.a[0][tid] = si;
@@ -422,7 +472,7 @@ __device__ __forceinline__ void enforce_block(const Params& p, double u[5], bool
 // Uout = a_n Un + b_k (Uk + dt R) followed (if enforce) by the physicality operator.
 // Uout may alias Uk or Un (each thread reads its own node before the block writes).
 // ---------------------------------------------------------------------------------------
-template <int DIM, int N>
+template <int DIM, int N, bool FACES>
 __global__ void __launch_bounds__(Shape<DIM, N>::BLOCK)
     update_kernel(Params p, const double* __restrict__ Rvol, const double* __restrict__ Fs,
                   const double* Un, const double* Uk, double* Uout, double a_n, double b_k,
@@ -430,12 +480,13 @@ __global__ void __launch_bounds__(Shape<DIM, N>::BLOCK)
   using S = Shape<DIM, N>;
   constexpr int Nn = S::Nn;
   __shared__ EnforceShared<DIM, N> sh;
-  __shared__ double shl[DIM][2][N];  // (2/dx_d) phi_i(-+1)/w_i per axis
+  // (2/dx_d) phi_i(-+1)/w_i per axis, halved: the face kernel stores 2 F*
+  __shared__ double shl[DIM][2][N];
   const int tid = threadIdx.x;
   if (tid < DIM * N) {
     const int d = tid / N, i = tid % N;
-    shl[d][0][i] = p.inv_half_dx[d] * p.lm[i];
-    shl[d][1][i] = p.inv_half_dx[d] * p.lp[i];
+    shl[d][0][i] = 0.5 * p.inv_half_dx[d] * p.lm[i];
+    shl[d][1][i] = 0.5 * p.inv_half_dx[d] * p.lp[i];
   }
   __syncthreads();
   const int le = tid / Nn, li = tid - le * Nn;
@@ -477,7 +528,7 @@ __global__ void __launch_bounds__(Shape<DIM, N>::BLOCK)
     }
   }
   if (mode == 0) return;  // uniform over the grid
-  if (enforce) enforce_block(p, u, valid, le, li, e, s_out, sh);
+  if (enforce) enforce_block<FACES>(p, u, valid, le, li, e, s_out, sh);
   if (valid) {
 #pragma unroll
     for (int v = 0; v < 5; ++v) Uout[v * tot + g] = u[v];
@@ -501,7 +552,10 @@ __global__ void __launch_bounds__(Shape<DIM, N>::BLOCK)
   if (valid)
 #pragma unroll
     for (int v = 0; v < 5; ++v) u[v] = U[v * tot + g];
-  enforce_block(p, u, valid, le, li, e, s_out, sh);
+  if (p.enforce_faces)
+    enforce_block<true>(p, u, valid, le, li, e, s_out, sh);
+  else
+    enforce_block<false>(p, u, valid, le, li, e, s_out, sh);
   if (valid)
 #pragma unroll
     for (int v = 0; v < 5; ++v) U[v * tot + g] = u[v];
@@ -689,7 +743,10 @@ __global__ void __launch_bounds__(Shape<DIM, N>::BLOCK)
       u[v] = fma(t, u[v] - ub, ub);
     }
   }
-  if (enforce) enforce_block(p, u, valid, le, li, e, s_out, sh);
+  if (enforce && p.enforce_faces)
+    enforce_block<true>(p, u, valid, le, li, e, s_out, sh);
+  else if (enforce)
+    enforce_block<false>(p, u, valid, le, li, e, s_out, sh);
   if (valid)
 #pragma unroll
     for (int v = 0; v < 5; ++v) U[v * tot + g] = u[v];
@@ -723,7 +780,8 @@ static cudaError_t launch_stage_kernels(const StageArgs& a) {
       volume_kernel_split<DIM, N><<<eblocks, SB, smem, a.stream>>>(
           p, a.U, reinterpret_cast<float*>(a.Rvol), a.Tr, reinterpret_cast<float2*>(a.Fref));
     } else {
-      update_kernel_split<DIM, N><<<eblocks, S::BLOCK, 0, a.stream>>>(
+      auto kern = p.enforce_faces ? update_kernel_split<DIM, N, true> : update_kernel_split<DIM, N, false>;
+      kern<<<eblocks, S::BLOCK, 0, a.stream>>>(
           p, reinterpret_cast<const float*>(a.Rvol), reinterpret_cast<const float2*>(a.Fs),
           reinterpret_cast<const float2*>(a.Fref),
           a.Un, a.Uk, a.Uout, a.a_n, a.b_k, a.dt, a.mode, a.enforce, a.s_out);
@@ -747,10 +805,12 @@ static cudaError_t launch_stage_kernels(const StageArgs& a) {
         face_kernel<DIM, N, false><<<grid, 128, 0, a.stream>>>(p, a.Tr, a.Fs, nullptr, a.split);
       break;
     }
-    case Op::Update:
-      update_kernel<DIM, N><<<eblocks, S::BLOCK, 0, a.stream>>>(
-          p, a.Rvol, a.Fs, a.Un, a.Uk, a.Uout, a.a_n, a.b_k, a.dt, a.mode, a.enforce, a.s_out);
+    case Op::Update: {
+      auto kern = p.enforce_faces ? update_kernel<DIM, N, true> : update_kernel<DIM, N, false>;
+      kern<<<eblocks, S::BLOCK, 0, a.stream>>>(p, a.Rvol, a.Fs, a.Un, a.Uk, a.Uout, a.a_n, a.b_k,
+                                               a.dt, a.mode, a.enforce, a.s_out);
       break;
+    }
     case Op::Enforce:
       enforce_kernel<DIM, N><<<eblocks, S::BLOCK, 0, a.stream>>>(p, a.Uout, a.s_out);
       break;

@@ -156,7 +156,8 @@ __global__ void __launch_bounds__(SplitShape<DIM, N>::BLOCK)
         for (int v = 0; v < 5; ++v) {
           const F32Pair r = f32_pair(F[d][v]);
           shFR[(le * DIM + d) * 5 + v] = r;
-          Fref[((long long)d * 5 + v) * p.E + e] = make_float2(r.hi, r.lo);
+          // doubled for the update kernel, which lifts 2 F* - 2 F_ref (exact scaling)
+          Fref[((long long)d * 5 + v) * p.E + e] = make_float2(2.0f * r.hi, 2.0f * r.lo);
         }
 #pragma unroll
       for (int v = 0; v < 5; ++v) {
@@ -246,7 +247,7 @@ __global__ void __launch_bounds__(SplitShape<DIM, N>::BLOCK)
 // the FP32 deviations F* - F_ref (exact products and one rounding each: at least the accuracy
 // of the 3xTF32 products).  The face fluxes arrive as FP32 head and tail (face_kernel with
 // pairs), the reference fluxes likewise (volume_kernel_split).
-template <int DIM, int N>
+template <int DIM, int N, bool FACES>
 __global__ void __launch_bounds__(Shape<DIM, N>::BLOCK)
     update_kernel_split(Params p, const float* __restrict__ Rvol, const float2* __restrict__ Fs,
                         const float2* __restrict__ Fref, const double* Un, const double* Uk,
@@ -255,12 +256,14 @@ __global__ void __launch_bounds__(Shape<DIM, N>::BLOCK)
   using S = Shape<DIM, N>;
   constexpr int Nn = S::Nn;
   __shared__ EnforceShared<DIM, N> sh;
-  __shared__ float shl[DIM][2][N];  // (2/dx_d) phi_i(-+1)/w_i per axis, rounded to FP32
+  // (2/dx_d) phi_i(-+1)/w_i per axis, rounded to FP32 and halved: the face kernel stores 2 F*
+  // and the volume kernel 2 F_ref
+  __shared__ float shl[DIM][2][N];
   const int tid = threadIdx.x;
   if (tid < DIM * N) {
     const int d = tid / N, i = tid % N;
-    shl[d][0][i] = f64_to_f32_bits(p.inv_half_dx[d] * p.lm[i]);
-    shl[d][1][i] = f64_to_f32_bits(p.inv_half_dx[d] * p.lp[i]);
+    shl[d][0][i] = 0.5f * f64_to_f32_bits(p.inv_half_dx[d] * p.lm[i]);
+    shl[d][1][i] = 0.5f * f64_to_f32_bits(p.inv_half_dx[d] * p.lp[i]);
   }
   __syncthreads();
   const int le = tid / Nn, li = tid - le * Nn;
@@ -306,7 +309,7 @@ __global__ void __launch_bounds__(Shape<DIM, N>::BLOCK)
     }
   }
   if (mode == 0) return;  // uniform over the grid
-  if (enforce) enforce_block(p, u, valid, le, li, e, s_out, sh);
+  if (enforce) enforce_block<FACES>(p, u, valid, le, li, e, s_out, sh);
   if (valid) {
 #pragma unroll
     for (int v = 0; v < 5; ++v) Uout[v * tot + g] = u[v];

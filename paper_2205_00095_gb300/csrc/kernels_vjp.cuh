@@ -112,8 +112,7 @@ __device__ __forceinline__ void face_rev(const Params& p, const FaceFwd& f, cons
   rhob += Db * f.lor;
   // equation of state
   if (p.eos == 0) {
-    const double c = rho + f.rho_hm1 - f.A;
-    qb += Bb * c;
+    qb += Bb * f.K;  // B = q K, K = rho + (alpha - Gamma) P
     rhob += Bb * f.q;
     rhm1b += Bb * f.q;
     Ab -= Bb * f.q;

@@ -55,6 +55,8 @@ cudaError_t launch_con2prim(const Params& p, cudaStream_t s, long long n, const 
 cudaError_t launch_velocity_square(const Params& p, cudaStream_t s, long long n, int Nn,
                                    const double* U, int axis, double* partial, int blocks);
 cudaError_t launch_math_check(cudaStream_t s, long long n, const double* x, double* out);
+cudaError_t launch_fp64_probe(cudaStream_t s, int kind, long long iters, long long threads,
+                              double* sink);
 cudaError_t launch_con2prim_vjp(const Params& p, cudaStream_t s, long long n, const double* U,
                                 const double* Wb, double* Ub);
 
@@ -63,8 +65,9 @@ cudaError_t launch_con2prim_vjp(const Params& p, cudaStream_t s, long long n, co
 struct dgsrhd_config;
 
 namespace dgsrhd {
-// Launch parameters of a configuration without a context; false for an invalid one.
-// n_trace / n_face_flux receive the sizes (in doubles) of the trace and face-flux buffers.
+// Launch parameters of a configuration; false for an invalid one.  n_trace / n_face_flux
+// receive the sizes (in doubles) of the trace and face-flux buffers, nodes (nullable, degree + 1
+// doubles) the 1D nodes of the basis.
 bool params_from_config(const ::dgsrhd_config* cfg, Params* out, long long* n_trace,
-                        long long* n_face_flux);
+                        long long* n_face_flux, double* nodes = nullptr);
 }  // namespace dgsrhd

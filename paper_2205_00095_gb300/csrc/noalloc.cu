@@ -29,19 +29,27 @@ std::mutex g_setup_mutex;
 double* g_scratch_addr[kMaxDevices] = {nullptr};
 
 // Device address of the scratch array on the current device.  The symbol's host-side name is
-// only a stand-in, so the address is looked up once per device with cudaGetSymbolAddress
-// (with that device current) and cached.
-cudaError_t scratch_address(double** out) {
+// only a stand-in, so the address comes from cudaGetSymbolAddress with the device current.  It
+// is looked up again on every call made outside stream capture (a device reset, or another
+// context on the same device, loads the module at another address) and kept per device for
+// calls made while `stream` is being captured, which reuse the address of the last call made
+// outside capture on that device.
+cudaError_t scratch_address(cudaStream_t stream, double** out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  e = cudaStreamIsCapturing(stream, &cap);
+  if (e != cudaSuccess) return e;
   std::lock_guard<std::mutex> lock(g_setup_mutex);
-  if (!g_scratch_addr[dev]) {
+  if (cap == cudaStreamCaptureStatusNone) {
     void* ptr = nullptr;
     e = cudaGetSymbolAddress(&ptr, g_rhs_scratch);
     if (e != cudaSuccess) return e;
     g_scratch_addr[dev] = static_cast<double*>(ptr);
+  } else if (!g_scratch_addr[dev]) {
+    return cudaErrorStreamCaptureUnsupported;  // no address taken outside capture yet
   }
   *out = g_scratch_addr[dev];
   return cudaSuccess;
@@ -56,19 +64,23 @@ extern "C" int32_t dgsrhd_rhs_noalloc(const dgsrhd_config* cfg, void* stream, co
   Params p;
   long long n_trace = 0, n_face_flux = 0;
   if (!params_from_config(cfg, &p, &n_trace, &n_face_flux)) return DGSRHD_EINVAL;
+  const bool split = cfg->precision == DGSRHD_PREC_SPLIT;
   const long long n_state = 5 * p.E * p.Nn;
+  // split precision: the per-element reference fluxes, FP32 head and tail in one double each
+  const long long n_ref = split ? 5LL * p.dim * p.E : 0;
   const long long n_stats = (long long)kStatCount * 64;  // unsigned long long slots
-  const long long need = n_state + n_trace + n_face_flux + n_stats;
+  const long long need = n_state + n_trace + n_face_flux + n_ref + n_stats;
   if (need > kScratchDoubles) return DGSRHD_EINVAL;  // mesh too large for the fixed scratch
 
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
   double* base = nullptr;
-  if (scratch_address(&base) != cudaSuccess) return DGSRHD_ECUDA;
+  if (scratch_address(s, &base) != cudaSuccess) return DGSRHD_ECUDA;
   double* Rvol = base;
   double* Tr = Rvol + n_state;
   double* Fs = Tr + n_trace;
-  unsigned long long* stats = reinterpret_cast<unsigned long long*>(Fs + n_face_flux);
+  double* Fref = Fs + n_face_flux;
+  unsigned long long* stats = reinterpret_cast<unsigned long long*>(Fref + n_ref);
   p.stats = stats;
-  cudaStream_t s = static_cast<cudaStream_t>(stream);
   // the counters accumulate with atomics and must start at zero on every call
   if (cudaMemsetAsync(stats, 0, sizeof(unsigned long long) * n_stats, s) != cudaSuccess)
     return DGSRHD_ECUDA;
@@ -82,6 +94,9 @@ extern "C" int32_t dgsrhd_rhs_noalloc(const dgsrhd_config* cfg, void* stream, co
   a.Fs = Fs;
   a.Uout = R;
   a.mode = 0;
+  // the split configuration runs the split kernels, as dgsrhd_rhs does
+  a.split = split ? 1 : 0;
+  a.Fref = split ? Fref : nullptr;
   const Op ops[3] = {Op::Volume, Op::Face, Op::Update};
   for (Op op : ops) {
     a.op = op;

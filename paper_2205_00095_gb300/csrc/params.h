@@ -52,6 +52,9 @@ struct Params {
   double inv_half_dx[3];     // 2 / dx_d
   int eos;                   // 0 ideal, 1 Taub-Matthews
   double gamma_ad, alpha;    // Gamma, Gamma / (Gamma - 1)
+  // constants of the ideal EOS formed once on the host: Gamma - 1, (Gamma - 1)^2, -2 Gamma,
+  // -2 Gamma (Gamma - 1), Gamma^2, 2 (Gamma - 1), alpha - Gamma
+  double gm1, gm1sq, m2G, m2Ggm1, G2, tgm1, amG;
   int c2p;                   // 0 closed form, 1 iterative (resolved)
   int max_iter;
   double c2p_rtol;           // > 0: the iterative solvers also stop at this relative step
@@ -65,6 +68,7 @@ struct Params {
   double lm[kMaxN], lp[kMaxN];   // phi_i(-1)/w_i, phi_i(+1)/w_i
   double wsum;               // sum of tensor weights = 2^dim
   unsigned long long* stats; // device counters [kStatCount]
+  int enforce_faces;         // physicality operator over the nodes and the face points
   int limiter;               // 1: scaling limiter after every stage
   double lim_alpha;          // its bound relaxation (already times h^(3/2))
 };

@@ -84,7 +84,7 @@ __global__ void __launch_bounds__(256) con2prim_vjp_kernel(Params p, long long n
   }
 }
 
-// Partial sums of the quadrature of v_axis^2 (the Kelvin-Helmholtz diagnostic of Sec. 4.4):
+// Partial sums of the quadrature of v_axis^2 (the Kelvin-Helmholtz diagnostic of Sec. 4.5):
 // con2prim at every node, weight prod_d w[node index along d]; one partial per block (fixed
 // assignment of nodes to threads and fixed reduction tree, so the sums are reproducible).
 __global__ void __launch_bounds__(256) velocity_square_kernel(Params p, long long n, int Nn,
@@ -118,7 +118,7 @@ __global__ void __launch_bounds__(256) velocity_square_kernel(Params p, long lon
   if (threadIdx.x == 0) partial[blockIdx.x] = sh[0];
 }
 
-// The library's reciprocal and square root next to CUDA's, for the diagnostic entry point.
+// The library's reciprocal and roots next to CUDA's, for the diagnostic entry point.
 __global__ void __launch_bounds__(256) math_check_kernel(long long n, const double* __restrict__ x,
                                                          double* __restrict__ out) {
   for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < n;
@@ -126,9 +126,76 @@ __global__ void __launch_bounds__(256) math_check_kernel(long long n, const doub
     const double v = x[k];
     out[k] = recip_nr(v);
     out[n + k] = 1.0 / v;
-    out[2 * n + k] = sqrt_rs(v);
+    out[2 * n + k] = sqrt_nr(v);
     out[3 * n + k] = sqrt(v);
+    out[4 * n + k] = v == 0.0 ? 0.0 : rcbrt_nr(v);
+    out[5 * n + k] = v == 0.0 ? 0.0 : rcbrt(v);
   }
+}
+
+// Throughput probe of one arithmetic operation: every thread runs four independent chains of
+// `iters` applications, x <- op(x), so that enough operations are in flight to keep the
+// operation's pipe busy; the chains' sum is stored so that none is removed.  kind: 0 FP64 FMA
+// x <- fma(x, a, b); 1 FP64 division x <- b / x; 2 sqrt; 3 rsqrt; 4 rcbrt; the library's
+// 5 reciprocal (recip_nr), 6 square root (sqrt_nr), 7 reciprocal cube root (rcbrt_nr); 8 FP32
+// FMA.  a and b are kernel arguments (not constants
+// the compiler could fold); every chain stays bounded.
+template <int KIND>
+__device__ __forceinline__ double probe_op(double x, double a, double b) {
+  if (KIND == 0) return fma(x, a, b);
+  if (KIND == 1) return b / x;
+  if (KIND == 2) return sqrt(x);
+  if (KIND == 3) return rsqrt(x);
+  if (KIND == 4) return rcbrt(x);
+  if (KIND == 5) return recip_nr(x);
+  if (KIND == 6) return sqrt_nr(x);
+  return rcbrt_nr(x);
+}
+
+template <int KIND>
+__global__ void __launch_bounds__(256) fp64_probe_kernel(long long iters, double a, double b,
+                                                         double* __restrict__ sink) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  double x0 = 1.0 + 1e-7 * (double)(t & 1023), x1 = x0 + 0.25, x2 = x0 + 0.5, x3 = x0 + 0.75;
+  for (long long k = 0; k < iters; ++k) {
+    x0 = probe_op<KIND>(x0, a, b);
+    x1 = probe_op<KIND>(x1, a, b);
+    x2 = probe_op<KIND>(x2, a, b);
+    x3 = probe_op<KIND>(x3, a, b);
+  }
+  sink[t] = (x0 + x1) + (x2 + x3);
+}
+
+__global__ void __launch_bounds__(256) fp32_probe_kernel(long long iters, float a, float b,
+                                                         double* __restrict__ sink) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  float x0 = 1.0f + 1e-4f * (float)(t & 1023), x1 = x0 + 0.25f, x2 = x0 + 0.5f, x3 = x0 + 0.75f;
+  for (long long k = 0; k < iters; ++k) {
+    x0 = fmaf(x0, a, b);
+    x1 = fmaf(x1, a, b);
+    x2 = fmaf(x2, a, b);
+    x3 = fmaf(x3, a, b);
+  }
+  sink[t] = (double)((x0 + x1) + (x2 + x3));
+}
+
+cudaError_t launch_fp64_probe(cudaStream_t s, int kind, long long iters, long long threads,
+                              double* sink) {
+  const unsigned blocks = (unsigned)(threads / 256);
+  const double a = 0.999999, b = 1e-6;
+  switch (kind) {
+    case 0: fp64_probe_kernel<0><<<blocks, 256, 0, s>>>(iters, a, b, sink); break;
+    case 1: fp64_probe_kernel<1><<<blocks, 256, 0, s>>>(iters, a, 1.5, sink); break;
+    case 2: fp64_probe_kernel<2><<<blocks, 256, 0, s>>>(iters, a, b, sink); break;
+    case 3: fp64_probe_kernel<3><<<blocks, 256, 0, s>>>(iters, a, b, sink); break;
+    case 4: fp64_probe_kernel<4><<<blocks, 256, 0, s>>>(iters, a, b, sink); break;
+    case 5: fp64_probe_kernel<5><<<blocks, 256, 0, s>>>(iters, a, b, sink); break;
+    case 6: fp64_probe_kernel<6><<<blocks, 256, 0, s>>>(iters, a, b, sink); break;
+    case 7: fp64_probe_kernel<7><<<blocks, 256, 0, s>>>(iters, a, b, sink); break;
+    case 8: fp32_probe_kernel<<<blocks, 256, 0, s>>>(iters, 0.999999f, 1e-6f, sink); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
 }
 
 static unsigned grid_for(long long n) {

@@ -236,7 +236,7 @@ class Solver:
         return Ub
 
     def mean_square_velocity(self, U: torch.Tensor, axis: int = 1) -> float:
-        """<v_axis^2> = (1/|Omega|) int v_axis^2 dV (the Kelvin-Helmholtz diagnostic of Sec. 4.4),
+        """<v_axis^2> = (1/|Omega|) int v_axis^2 dV (the Kelvin-Helmholtz diagnostic of Sec. 4.5),
         evaluated by the library; synchronises the solver's stream."""
         out = ctypes.c_double()
         check("dgsrhd_mean_square_velocity", self.lib.dgsrhd_mean_square_velocity(
@@ -293,3 +293,17 @@ class Solver:
     def synchronize(self):
         """Wait for the context's stream."""
         self.stream.synchronize()
+
+
+def arith_probe(kind: str, iters: int, sink: torch.Tensor, stream=None) -> int:
+    """Queue the library's arithmetic throughput probe (dgsrhd_arith_probe) on `stream`: one
+    kernel of sink.numel() threads (a multiple of 256), each running four independent chains of
+    `iters` applications of the operation `kind` (a key of _lib.PROBE).  Returns the number of
+    operations; the caller times the kernel with CUDA events on the same stream."""
+    lib = _lib.load()
+    ops = ctypes.c_int64()
+    ptr = _vec_ptr(sink, "sink", sink.numel())
+    check("dgsrhd_arith_probe", lib.dgsrhd_arith_probe(_lib.PROBE[kind], int(iters), ptr,
+                                                       sink.numel(), _stream_handle(stream),
+                                                       ctypes.byref(ops)))
+    return ops.value

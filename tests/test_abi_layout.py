@@ -111,6 +111,13 @@ def test_binding_codes_match_the_header(c_layout):
         "NODES": {"gl": "DGSRHD_NODES_GL", "gll": "DGSRHD_NODES_GLL"},
         "LIMITER": {"none": "DGSRHD_LIMITER_NONE", "moe": "DGSRHD_LIMITER_SCALING",
                     "scaling": "DGSRHD_LIMITER_SCALING", "minmod": "DGSRHD_LIMITER_MINMOD"},
+        "ENFORCE": {"off": "DGSRHD_ENFORCE_OFF", "nodes": "DGSRHD_ENFORCE_NODES",
+                    "faces": "DGSRHD_ENFORCE_FACES"},
+        "PROBE": {"dfma": "DGSRHD_PROBE_DFMA", "ddiv": "DGSRHD_PROBE_DDIV",
+                  "dsqrt": "DGSRHD_PROBE_DSQRT", "drsqrt": "DGSRHD_PROBE_DRSQRT",
+                  "drcbrt": "DGSRHD_PROBE_DRCBRT", "recip": "DGSRHD_PROBE_RECIP",
+                  "sqrt": "DGSRHD_PROBE_SQRT", "rcbrt": "DGSRHD_PROBE_RCBRT",
+                  "ffma": "DGSRHD_PROBE_FFMA"},
     }
     for group, names in groups.items():
         table = getattr(_lib, group)

@@ -73,3 +73,27 @@ def test_noalloc_rhs_rejects_meshes_beyond_the_fixed_scratch(gpu_lib):
     assert lib.dgsrhd_rhs_noalloc(ctypes.byref(cfg), None, _ptr(U), _ptr(R), None) == _lib.DGSRHD_EINVAL
     assert lib.dgsrhd_rhs_noalloc(ctypes.byref(cfg), None, _ptr(U), _ptr(U), None) == _lib.DGSRHD_EINVAL
     assert lib.dgsrhd_rhs_noalloc(None, None, _ptr(U), _ptr(R), None) == _lib.DGSRHD_EINVAL
+
+
+def test_noalloc_rhs_runs_the_split_kernels_for_a_split_configuration(gpu_lib):
+    """precision = split: the same split-precision kernels as the context's dgsrhd_rhs (the
+    per-element reference fluxes live in the fixed scratch too), so the two R agree bit for bit,
+    and they differ from the FP64 R at the split form's rounding level."""
+    from paper_2205_00095_gb300 import Solver, _lib
+
+    lib = gpu_lib
+    spec = dict(wl.kh2d(nx=16, ny=32, degree=3), precision="split")
+    s = Solver(spec)
+    s64 = Solver(dict(spec, precision="fp64"))
+    U = s.initial_state(wl.kh2d_ic(spec, s.node_coords()))
+    cfg = _lib.make_config(spec)
+    for _ in range(2):
+        R_ref = s.rhs(U)
+        R = torch.full_like(U, float("nan"))
+        assert lib.dgsrhd_rhs_noalloc(ctypes.byref(cfg), None, _ptr(U), _ptr(R), None) == _lib.DGSRHD_OK
+        torch.cuda.synchronize()
+        assert torch.equal(R, R_ref)
+    R64 = s64.rhs(U)
+    torch.cuda.synchronize()
+    d = (R - R64).abs().max().item() / R64.abs().max().item()
+    assert 0.0 < d < 1e-4, d
