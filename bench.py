@@ -10,19 +10,39 @@ seconds (the definition of the paper's performance section).
 
 --gpus N > 1 runs one replica of the workload per rank (torchrun, one GPU each; the method has no
 cross-replica exchange), barrier + synchronize around the timed region, max time over ranks.
---impl reference times the FP64 CPU oracle on the host cores on a bounded sample of the same
-workload.  One JSON line is printed by rank 0.  Besides the FP64 value it carries the split-
-precision form on the same workload (its rate, speed-up and L1 difference from FP64, and on the
-advected wave both L1 errors against the exact solution), the adjoint/forward time ratio of the
-checkpointed Kelvin-Helmholtz rollout, an end-to-end rate through dgsrhd_step_host with the
-state in pinned host memory, the oracle's rate on a sample (cpu_baseline), the dominant
-kernel's roofline, the per-kernel time shares, the kernel launch count and the SM clocks
-sampled during the timed region.
+--impl reference times the FP64 CPU oracle on all host cores (one process per core, each
+stepping its own copy of a bounded sample of the same workload).  One JSON line is printed by
+rank 0.  Keys beyond the common ones:
+  value / ms_per_step  K steps replayed from the captured CUDA graph (the production path of
+                       dgsrhd_step), CUDA events on the solver's stream;
+  kernel_timing        a second pass of K steps with every kernel bracketed by CUDA events
+                       (launched directly): per-kernel mean launch time and share, and that
+                       pass's own ms_per_step;
+  roofline / rooflines the dominant kernel's and every stage kernel's algorithmic FP64 rate
+                       against the FP64 peak measured by the library's DFMA probe in this run
+                       (fp64_peak), with the counting rule;
+  fp64_peak            DFMA throughput (and FP32 FMA), the cost of division, square root,
+                       reciprocal square root and reciprocal cube root in DFMA-equivalents, and
+                       the SM clock during the probe;
+  split_precision      the split-precision form on the same workload (rate, speed-up, L1
+                       difference from FP64; on the advected wave both L1 errors against the
+                       exact solution);
+  workloads            the 2D Taub-Matthews Kelvin-Helmholtz problem at 256 x 512 and the 3D one
+                       at 128^3 (FP64 and split rates, L1 difference, con2prim iterations,
+                       volume-kernel roofline);
+  adjoint              adjoint/forward time ratio of the checkpointed 128 x 256 Kelvin-Helmholtz
+                       rollout, with its dJ/dA against the oracle's central differences stored in
+                       tests/golden/kh_adjoint_c4.json;
+  e2e                  the same metric through dgsrhd_step_host with the state in pinned host
+                       memory (host link traffic inside the timed region);
+  cpu_baseline         the oracle on all host cores and on one thread;
+  clocks               SM clocks sampled with nvidia-smi during the timed region.
 """
 from __future__ import annotations
 
 import argparse
 import json
+import multiprocessing as mp
 import os
 import statistics
 import subprocess
@@ -39,7 +59,6 @@ import workloads as wl  # noqa: E402
 
 METRIC = "DOF-updates/s at p=3 (FP64 vs split-precision, fixed L1 error); adjoint/forward ratio"
 UNIT = "DOF-updates/s"
-FP64_PEAK_TFLOPS = 1.25  # GB300 nominal dense FP64 (no FP64 figure in MEASURED_PEAKS.json)
 
 
 def make_spec(name: str, c2p: str | None = None) -> dict:
@@ -71,10 +90,10 @@ class ClockSampler:
              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, gpu_index: int, log_dir: str | None = None):
+    def __init__(self, gpu_index: int, log_dir: str | None = None, tag: str = "bench"):
         self.gpu = gpu_index
         self.proc = None
-        self.path = os.path.join(log_dir or tempfile.gettempdir(), f"clocks_bench_{gpu_index}.csv")
+        self.path = os.path.join(log_dir or tempfile.gettempdir(), f"clocks_{tag}_{gpu_index}.csv")
 
     def __enter__(self):
         try:
@@ -99,32 +118,37 @@ class ClockSampler:
     def summary(self):
         if self.proc is None or not os.path.exists(self.path):
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
-        sm, smmax, reasons = [], [], set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for line in open(self.path):
-            f = [x.strip() for x in line.split(",")]
-            if len(f) < 9:
-                continue
-            try:
-                sm.append(float(f[1]))
-                smmax.append(float(f[2]))
-            except ValueError:
-                continue
-            for name, val in zip(names, f[5:9]):
-                if val.lower() == "active":
-                    reasons.add(name)
-        if not sm:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
-        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smmax), "reasons": sorted(reasons),
-                "samples": len(sm)}
+        return summarize_clock_lines(open(self.path).read().splitlines())
+
+
+def summarize_clock_lines(lines):
+    """Median SM clock, max clock and the throttle reasons seen in nvidia-smi CSV samples."""
+    sm, smmax, reasons = [], [], set()
+    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    for line in lines:
+        f = [x.strip() for x in line.split(",")]
+        if len(f) < 9:
+            continue
+        try:
+            sm.append(float(f[1]))
+            smmax.append(float(f[2]))
+        except ValueError:
+            continue
+        for name, val in zip(names, f[5:9]):
+            if val.lower() == "active":
+                reasons.add(name)
+    if not sm:
+        return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+    return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smmax), "reasons": sorted(reasons),
+            "samples": len(sm)}
 
 
 # ----------------------------------------------------------------------------------------
-# algorithmic work (per DOF update, p = 3, 2D) used for the roofline of the volume kernel
+# algorithmic work per unit of each stage kernel (FP64 roofline)
 # ----------------------------------------------------------------------------------------
-# Algorithmic FP64 operations per node of the volume kernel, counted from the method's arithmetic
-# as the oracle writes it (add, sub, mul, div = 1; fma = 2; sqrt, cbrt and other library calls
-# = 1 each; comparisons not counted):
+# Counting rule: the method's arithmetic as the oracle writes it, each add, sub, mul, div,
+# sqrt, cbrt or library call = 1 flop, a fused multiply-add = 2, comparisons not counted.
+# Volume kernel, per node:
 #   con2prim, closed-form ideal quartic:    12 (xi, eta, admissibility) + 87 (quartic
 #       coefficients, resolvent cubic, Cardano root, two quadratic factors) + 21 (rho, v, P)
 #   con2prim, Newton on the Riccardi quartic: 12 + 20 (series start) + 19 per iteration
@@ -132,33 +156,74 @@ class ClockSampler:
 #   con2prim, Taub-Matthews cubic closed form: 12 + 25 (coefficients) + 16 (Cardano) + 24
 #   con2prim, Taub-Matthews Brent: 12 + 25 + 14 per iteration (cubic value 6, interpolation 8)
 #       + 24
-#   nodal flux 7 per axis; volume term 2 N 5 per axis (pre-scaled Dhat); face traces 2 N 5 per
-#   face point, 2 dim N^(dim-1) face points per N^dim nodes.
+#   nodal flux 7 per axis; volume term 2 N 5 per axis; face traces 2 N 5 per face point,
+#   2 dim N^(dim-1) face points per N^dim nodes.
+# Face kernel, per face point: two face states from (rho, u, P) (u^2 5, gamma 2, v_d 1, h - 1 2
+#   ideal / 9 Taub-Matthews, D 1, rho h gamma^2 3, S 3, tau 7: 24 / 31), their normal fluxes
+#   (7 each), their wavespeeds (sound speed 2 ideal / 10 Taub-Matthews, sigma 3, root 5,
+#   lambda 5: 15 / 23), and the combination: LLF 26 (5 x (sum, difference, two products,
+#   difference) + a/2), HLL 32 (5 x 6 + S_L S_R + the denominator), HLLC 72 (HLL averages 40,
+#   contact speed 8, star state and flux 24).
+# Update kernel, per node: lift 2 x 2 x 5 per axis, Shu-Osher combination 2 per variable in the
+#   first stage and 5 in the later ones (averaged over the stages), admissibility test 8.
 C2P_FLOPS = {
     ("ideal", "analytic"): lambda it: 120.0,
     ("ideal", "iterative"): lambda it: 12.0 + 20.0 + 19.0 * it + 17.0,
     ("tm", "analytic"): lambda it: 12.0 + 25.0 + 16.0 + 24.0,
     ("tm", "iterative"): lambda it: 12.0 + 25.0 + 14.0 * it + 24.0,
 }
+FACE_STATE_FLOPS = {"ideal": 24.0 + 7.0 + 15.0, "tm": 31.0 + 7.0 + 23.0}
+FACE_COMBINE_FLOPS = {"llf": 26.0, "hll": 32.0, "hllc": 72.0}
+COUNTING_RULE = ("algorithmic FP64 flops of the method as the oracle writes it (add, sub, mul, div, "
+                 "sqrt, cbrt, library call = 1; fma = 2; comparisons 0); per node for the volume and "
+                 "update kernels, per face point for the face kernel; peak = 2 x the DFMA rate of "
+                 "the library's probe measured in this run")
+
+
+def resolved_c2p(spec: dict) -> str:
+    c2p = spec["c2p"]
+    if c2p == "default":
+        c2p = "analytic" if spec["eos"] == "ideal" else "iterative"
+    return c2p
 
 
 def volume_kernel_flops_per_node(spec: dict, mean_iters: float = 0.0) -> float:
     d, N = spec["dim"], spec["degree"] + 1
-    c2p = spec["c2p"]
-    if c2p == "default":
-        c2p = "analytic" if spec["eos"] == "ideal" else "iterative"
     flux = 7.0 * d
     volume = 2.0 * N * 5 * d
     traces = (2.0 * d * N ** (d - 1) / N ** d) * 5 * 2.0 * N
-    return C2P_FLOPS[(spec["eos"], c2p)](mean_iters) + flux + volume + traces
+    return C2P_FLOPS[(spec["eos"], resolved_c2p(spec))](mean_iters) + flux + volume + traces
+
+
+def face_kernel_flops_per_point(spec: dict) -> float:
+    return 2.0 * FACE_STATE_FLOPS[spec["eos"]] + FACE_COMBINE_FLOPS[spec["flux"]]
+
+
+def update_kernel_flops_per_node(spec: dict) -> float:
+    d, ns = spec["dim"], spec["rk_stages"]
+    rk = (2.0 * 5 + (ns - 1) * 5.0 * 5) / ns
+    return 20.0 * d + rk + 8.0
+
+
+def face_points(spec: dict) -> int:
+    """Face points of one face-kernel launch: every face of every axis, N^(dim-1) points each
+    (a non-periodic axis has n_d + 1 faces per line of elements)."""
+    E, _ = wl.shape(spec)
+    d, N = spec["dim"], spec["degree"] + 1
+    total = 0
+    for a in range(d):
+        bc = (spec.get("bc") or [("periodic", "periodic")] * d)[a]
+        nf = E + (0 if bc[0] == "periodic" else E // spec["n_elem"][a])
+        total += nf * N ** (d - 1)
+    return total
 
 
 def _capture_record(kernel: str, workload_name: str):
     """The committed ncu record of `kernel` on this workload, or None when there is none or the
     kernel sources changed since it was taken."""
     import hashlib
-    path = os.path.join(ROOT, "profiles", "dram_traffic_advected_wave_512x512_p3.json")
-    if workload_name != "advected_wave" or not os.path.exists(path):
+    path = os.path.join(ROOT, "profiles", f"dram_traffic_{workload_name}_512x512_p3.json")
+    if not os.path.exists(path):
         return None
     d = json.load(open(path))
     h = hashlib.sha1()
@@ -189,9 +254,28 @@ def load_peaks():
         return None
 
 
+def kernel_roofline(name: str, flops_per_unit: float, units: int, avg_ms: float, peak_tflops: float,
+                    traffic=None, pipe=None) -> dict:
+    """Algorithmic FP64 rate of one kernel: flops_per_unit x units per launch / mean launch
+    time, against the measured FP64 peak."""
+    achieved = flops_per_unit * units / (avg_ms * 1e-3) / 1e12 if avg_ms > 0 else None
+    return {"kernel": name, "bound": "alu", "achieved": achieved, "peak": peak_tflops,
+            "unit": "TFLOP/s", "frac": None if achieved is None else achieved / peak_tflops,
+            "traffic": traffic, "fp64_pipe_busy_ncu": pipe,
+            "algorithmic_flops_per_unit": flops_per_unit, "units_per_launch": units,
+            "avg_launch_ms": avg_ms}
+
+
 # ----------------------------------------------------------------------------------------
-# reference arm / CPU baseline: the oracle on a bounded sample
+# reference arm / CPU baseline: the oracle on a bounded sample, on all host cores
 # ----------------------------------------------------------------------------------------
+def host_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
 def oracle_sample_spec(spec: dict, target_s: float = 1.0):
     """A sample of the workload (same field, p, EOS, solver) small enough for one oracle step to
     take about target_s seconds on one core."""
@@ -225,6 +309,19 @@ def run_oracle(spec: dict, steps: int, warmup: int):
     return dof(spec) * steps * spec["rk_stages"] / t, t
 
 
+def _oracle_worker(args):
+    spec, steps, warmup = args
+    return run_oracle(spec, steps, warmup)
+
+
+def run_oracle_all_cores(spec: dict, steps: int, warmup: int, procs: int):
+    """procs oracle processes (spawned), each stepping its own copy of `spec`: the summed
+    DOF-updates/s and the slowest process's time."""
+    with mp.get_context("spawn").Pool(procs) as pool:
+        res = pool.map(_oracle_worker, [(spec, steps, warmup)] * procs, chunksize=1)
+    return sum(r[0] for r in res), max(r[1] for r in res)
+
+
 def reduce_max_over_ranks(x: float, world: int, device) -> float:
     """The largest x over the ranks (the slowest replica's time); x itself on one rank."""
     if world == 1:
@@ -246,16 +343,17 @@ def reference_arm(args, rank, world):
     if rank != 0:
         return
     spec = make_spec(args.workload, args.c2p)
+    procs = host_cores()
     sample = oracle_sample_spec(spec, target_s=min(20.0, 60.0 / max(1, args.steps + args.warmup)))
-    value, t = run_oracle(sample, args.steps, args.warmup)
+    value, t = run_oracle_all_cores(sample, args.steps, args.warmup, procs)
     desc = (f"{args.steps} oracle SSPRK steps on {'x'.join(map(str, sample['n_elem']))} elements of the "
-            f"same workload ({dof(sample)} DOF), 1 thread")
+            f"same workload ({dof(sample)} DOF) in each of {procs} processes, one per host core")
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic", "config": {"workload": workload_desc(spec), "sample": desc},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": procs, "kind": "oracle", "sample": desc},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -264,57 +362,273 @@ def reference_arm(args, rank, world):
 # ----------------------------------------------------------------------------------------
 # our arm
 # ----------------------------------------------------------------------------------------
+PROBE_KINDS = ("dfma", "ffma", "ddiv", "dsqrt", "drsqrt", "drcbrt", "recip", "sqrt", "rcbrt")
+
+
+def measure_fp64_peak(dev, stream, clock_dir, local_rank, target_ms=150.0):
+    """Throughput of the library's arithmetic probe kernels (one kernel per operation, four
+    independent chains per thread, 8 blocks of 256 threads per SM), timed with CUDA events."""
+    import torch
+    from paper_2205_00095_gb300.solver import arith_probe
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    sink = torch.empty(sms * 8 * 256, dtype=torch.float64, device=dev)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    rates = {}
+    with ClockSampler(local_rank, clock_dir, tag="probe") as clk:
+        for kind in PROBE_KINDS:
+            iters = 64
+            with torch.cuda.stream(stream):
+                arith_probe(kind, iters, sink, stream)  # warm-up
+            for _ in range(2):  # calibrate to ~target_ms, then time
+                ev0.record(stream)
+                ops = arith_probe(kind, iters, sink, stream)
+                ev1.record(stream)
+                torch.cuda.synchronize(dev)
+                ms = ev0.elapsed_time(ev1)
+                if ms >= 0.5 * target_ms:
+                    break
+                iters = max(iters, int(iters * target_ms / max(ms, 1e-3)))
+            rates[kind] = ops / (ms * 1e-3)
+    dfma = rates["dfma"]
+    return {
+        "dfma_per_s": dfma, "tflops": 2.0 * dfma / 1e12, "ffma_tflops": 2.0 * rates["ffma"] / 1e12,
+        "fp32_fp64_fma_ratio": rates["ffma"] / dfma,
+        "dfma_equivalents": {k: dfma / rates[k] for k in PROBE_KINDS if k not in ("dfma", "ffma")},
+        "method": (f"dgsrhd_arith_probe: {sms * 8 * 256} threads x 4 independent chains, "
+                   f"~{target_ms:.0f} ms per operation, CUDA events"),
+        "clocks": clk.summary(),
+    }
+
+
+class Timed:
+    """K steps of one workload: graph replay (value), then a profiling pass with per-kernel
+    CUDA events."""
+
+    def __init__(self, spec, steps, warmup, dev, stream, barrier, clock=None):
+        import torch
+        from paper_2205_00095_gb300 import Solver
+        self.spec, self.steps = spec, steps
+        self.s = Solver(spec, stream=stream, device=dev)
+        with torch.cuda.stream(stream):
+            self.U0 = self.s.initial_state(wl.initial_primitive(spec, self.s.node_coords_device()))
+            self.s.enforce(self.U0)
+            self.U = self.U0.clone()
+        self.dt = self.s.cfl_dt(0.2)
+        s = self.s
+        s.step(self.U, self.dt, max(1, warmup))  # warm-up, captures the step graph
+        torch.cuda.synchronize(dev)
+        s.stats(reset=True)
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        l0 = s.kernel_launches()
+        barrier()
+        if clock is not None:
+            clock.__enter__()
+        ev0.record(stream)
+        s.step(self.U, self.dt, steps)
+        ev1.record(stream)
+        torch.cuda.synchronize(dev)
+        if clock is not None:
+            clock.__exit__()
+        barrier()
+        self.ms = ev0.elapsed_time(ev1)
+        self.launches = s.kernel_launches() - l0
+        self.status, self.st = s.stats(reset=True)
+        # second pass: every kernel bracketed by CUDA events (launched directly)
+        s.set_profiling(True)
+        s.kernel_times(reset=True)
+        V = self.U.clone()
+        barrier()
+        ev0.record(stream)
+        s.step(V, self.dt, steps)
+        ev1.record(stream)
+        torch.cuda.synchronize(dev)
+        barrier()
+        self.ms_prof = ev0.elapsed_time(ev1)
+        self.ktimes = s.kernel_times(reset=True)
+        s.set_profiling(False)
+        del V
+
+    def mean_iters(self):
+        return self.st["c2p_iters_total"] / max(self.st["c2p_calls"], 1)
+
+    def rooflines(self, peak, workload_name):
+        spec, nd = self.spec, dof(self.spec)
+        out = {}
+        for kind, kname, fpu, units in (
+                ("volume", "volume_kernel", volume_kernel_flops_per_node(spec, self.mean_iters()), nd),
+                ("face", "face_kernel", face_kernel_flops_per_point(spec), face_points(spec)),
+                ("update", "update_kernel", update_kernel_flops_per_node(spec), nd)):
+            ms, n = self.ktimes[kind]
+            if n:
+                out[kind] = kernel_roofline(kname, fpu, units, ms / n, peak,
+                                            measured_traffic(kname, workload_name),
+                                            measured_fp64_pipe(kname, workload_name))
+        return out
+
+    def shares(self):
+        tot = sum(v[0] for v in self.ktimes.values())
+        return {k: round(v[0] / max(tot, 1e-12), 4) for k, v in self.ktimes.items() if v[1]}
+
+    def close(self):
+        self.s.close()
+
+
+def run_split(spec, U0, U_fp64, dt, steps, warmup, dev, stream, barrier):
+    """The split-precision form from the same initial state: (ms, solver stats, L1 difference
+    from the FP64 state, per-kernel ms per launch, final state)."""
+    import torch
+    from paper_2205_00095_gb300 import Solver
+    ss = Solver(dict(spec, precision="split"), stream=stream, device=dev)
+    with torch.cuda.stream(stream):
+        V = U0.clone()
+    ss.step(V, dt, max(1, warmup))
+    torch.cuda.synchronize(dev)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    ev0.record(stream)
+    ss.step(V, dt, steps)
+    ev1.record(stream)
+    torch.cuda.synchronize(dev)
+    barrier()
+    sms = ev0.elapsed_time(ev1)
+    # per-kernel times in a separate pass (on a copy; V keeps the graph-replayed state)
+    ss.set_profiling(True)
+    ss.kernel_times(reset=True)
+    with torch.cuda.stream(stream):
+        V2 = V.clone()
+    ss.step(V2, dt, steps)
+    sk = ss.kernel_times(reset=True)
+    ss.set_profiling(False)
+    del V2
+    with torch.cuda.stream(stream):
+        l1 = float(((V - U_fp64).abs().sum() / U_fp64.abs().sum()).item())
+    sstatus, _ = ss.stats()
+    ss.close()
+    return sms, sstatus, l1, {k: round(v[0] / max(v[1], 1), 4) for k, v in sk.items() if v[1]}, V
+
+
+def run_workload_entry(spec, steps, warmup, dev, stream, barrier, peak, world, with_split=True):
+    """FP64 and split rates of one extra workload, its volume-kernel roofline and con2prim
+    iterations."""
+    import torch
+    T = Timed(spec, steps, warmup, dev, stream, barrier)
+    nd, stages = dof(spec), spec["rk_stages"]
+    rl = T.rooflines(peak, spec["name"])
+    entry = {"workload": workload_desc(spec), "dof": nd, "steps": steps,
+             "value": job_throughput(world, nd, steps, stages, T.ms), "unit": UNIT,
+             "ms_per_step": T.ms / steps, "mean_c2p_iterations": T.mean_iters(),
+             "device_status": T.status, "stats": T.st,
+             "volume_roofline": rl.get("volume"), "kernel_shares": T.shares()}
+    if "seed" in spec:
+        entry["seed"] = spec["seed"]
+    if with_split:
+        sms, sstatus, l1, sk, V = run_split(spec, T.U0, T.U, T.dt, steps, warmup, dev, stream, barrier)
+        del V
+        entry["split_precision"] = {"value": job_throughput(world, nd, steps, stages, sms),
+                                    "ms_per_step": sms / steps, "speedup_vs_fp64": T.ms / sms,
+                                    "l1_rel_vs_fp64": l1, "device_status": sstatus,
+                                    "kernel_ms_per_launch": sk}
+    T.close()
+    torch.cuda.empty_cache()
+    return entry
+
+
+def adjoint_block(dev, stream, barrier):
+    """Adjoint/forward time ratio of the checkpointed Kelvin-Helmholtz rollout (128 x 256, p = 3,
+    200 SSPRK3 steps, checkpoint every 20), and its dJ/dA against the oracle's stored central
+    differences."""
+    import torch
+    from paper_2205_00095_gb300 import Solver
+    from paper_2205_00095_gb300 import adjoint as adjm
+    spec4 = wl.kh2d(nx=128, ny=256, degree=3)
+    sa = Solver(spec4, stream=stream, device=dev)
+    X = sa.node_coords_device()
+    with torch.cuda.stream(stream):
+        W0 = wl.kh2d_ic(spec4, X)
+        A0 = sa.initial_state(W0)
+        Af = A0.clone()
+    dta = sa.cfl_dt(0.2)
+    sa.step(Af, dta, 3)  # warm-up and graph capture
+    with torch.cuda.stream(stream):
+        Af.copy_(A0)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    ev0.record(stream)
+    sa.step(Af, dta, 200)
+    ev1.record(stream)
+    torch.cuda.synchronize(dev)
+    fwd_ms = ev0.elapsed_time(ev1)
+    barrier()
+    # untimed warm-up rollout: one checkpoint segment, so that the stage buffers of a segment
+    # come from the allocator's cache in the timed run
+    with torch.cuda.stream(stream):
+        Uw = A0.clone().requires_grad_(True)
+        adjm.transverse_kinetic_energy(sa, adjm.rollout(sa, Uw, dta, 40, 20)).backward()
+        del Uw
+        U0g = A0.clone().requires_grad_(True)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    with torch.cuda.stream(stream):
+        UT = adjm.rollout(sa, U0g, dta, 200, 20)
+        Jv = adjm.transverse_kinetic_energy(sa, UT)
+        Jv.backward()
+    torch.cuda.synchronize(dev)
+    adj_ms = 1e3 * (time.perf_counter() - t0)
+    ast, ast_counts = sa.stats()
+    # dJ/dA: the adjoint contracted with the tangent of prim -> cons along dW/dA (v_y only)
+    with torch.cuda.stream(stream):
+        dW = torch.zeros_like(W0)
+        dW[2] = wl.kh2d_ic(spec4, X, amplitude=1.0)[2]
+        h = 1e-6
+        tang = (sa.initial_state(W0 + h * dW) - sa.initial_state(W0 - h * dW)) / (2 * h)
+        g_adj = float((U0g.grad * tang).sum().item())
+        J = float(Jv.detach().item())
+    torch.cuda.synchronize(dev)
+    adj = {"workload": "kh_2d 128x256 elements p=3 TM Brent HLL SSPRK3, 200 steps, checkpoint every 20",
+           "objective": "sum rho gamma^2 v_y^2 at t_final", "forward_ms": fwd_ms,
+           "forward_plus_adjoint_ms": adj_ms, "adjoint_forward_ratio": adj_ms / fwd_ms,
+           "J": J, "dJ_dA_adjoint": g_adj, "grad_norm": float(U0g.grad.norm()),
+           "enforced_cells": ast_counts["enforced_cells"], "device_status": ast}
+    golden = os.path.join(ROOT, "tests", "golden", "kh_adjoint_c4.json")
+    if os.path.exists(golden):
+        g = json.load(open(golden))
+        fd = g["dJ_dA"]["fd_h"]
+        adj.update({"dJ_dA_oracle_fd": fd, "rel_err_vs_oracle_fd": abs(g_adj - fd) / abs(fd),
+                    "J_rel_err_vs_oracle": abs(J - g["J"]) / abs(g["J"]),
+                    "oracle_dt": g["configuration"]["dt"], "dt": dta})
+    sa.close()
+    return adj
+
+
 def ours(args, rank, world, local_rank):
     import torch
     import torch.distributed as dist
-    from paper_2205_00095_gb300 import Solver, build
+    from paper_2205_00095_gb300 import build
 
     build.build()
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
-    spec = make_spec(args.workload, args.c2p)
     stream = torch.cuda.Stream(device=dev)
-    s = Solver(spec, stream=stream, device=dev)
-    with torch.cuda.stream(stream):
-        U0 = s.initial_state(wl.initial_primitive(spec, s.node_coords_device()))
-        s.enforce(U0)
-        U = U0.clone()
-    dt = s.cfl_dt(0.2)
-    stages = spec["rk_stages"]
-    ndof = dof(spec)
-
-    # warm-up (also captures the step graph)
-    s.step(U, dt, max(1, args.warmup))
-    torch.cuda.synchronize(dev)
-    s.stats(reset=True)
 
     def barrier():
         if world > 1:
             dist.barrier()
         torch.cuda.synchronize(dev)
 
-    # timed region: K steps with every kernel bracketed by CUDA events on the solver's stream
-    s.set_profiling(True)
-    s.kernel_times(reset=True)
-    launches0 = s.kernel_launches()
-    ev0 = torch.cuda.Event(enable_timing=True)
-    ev1 = torch.cuda.Event(enable_timing=True)
-    barrier()
-    with ClockSampler(local_rank, args.clock_log_dir) as clk:
-        ev0.record(stream)
-        s.step(U, dt, args.steps)
-        ev1.record(stream)
-        torch.cuda.synchronize(dev)
-    barrier()
-    ms = ev0.elapsed_time(ev1)
-    launches = s.kernel_launches() - launches0
-    ktimes = s.kernel_times(reset=True)
-    s.set_profiling(False)
-    status, st = s.stats()
-    t_max = reduce_max_over_ranks(ms, world, dev)
+    # FP64 peak of this GPU, measured before the workload
+    probe = measure_fp64_peak(dev, stream, args.clock_log_dir, local_rank)
+    peak = probe["tflops"]
+
+    spec = make_spec(args.workload, args.c2p)
+    stages = spec["rk_stages"]
+    ndof = dof(spec)
+    clk = ClockSampler(local_rank, args.clock_log_dir)
+    T = Timed(spec, args.steps, args.warmup, dev, stream, barrier, clock=clk)
+    s, U0, U, dt = T.s, T.U0, T.U, T.dt
+    t_max = reduce_max_over_ranks(T.ms, world, dev)
     value = job_throughput(world, ndof, args.steps, stages, t_max)
 
-    # end to end through the C ABI with a pinned host state: per step H2D, one step (graph), D2H
+    # end to end through the C ABI with a pinned host state: per step H2D, one step, D2H
     e2e = None
     if not args.no_e2e:
         Uh = U0.cpu().pin_memory()
@@ -337,23 +651,7 @@ def ours(args, rank, world, local_rank):
     # split-precision form on the same workload: tensor-core contractions, FP64 elsewhere
     split = None
     if not args.no_split:
-        ss = Solver(dict(spec, precision="split"), stream=stream, device=dev)
-        with torch.cuda.stream(stream):
-            V = U0.clone()
-        ss.step(V, dt, max(1, args.warmup))
-        ss.set_profiling(True)
-        ss.kernel_times(reset=True)
-        barrier()
-        ev0.record(stream)
-        ss.step(V, dt, args.steps)
-        ev1.record(stream)
-        torch.cuda.synchronize(dev)
-        barrier()
-        sms = ev0.elapsed_time(ev1)
-        sk = ss.kernel_times(reset=True)
-        ss.set_profiling(False)
-        with torch.cuda.stream(stream):
-            l1 = float(((V - U).abs().sum() / U.abs().sum()).item())
+        sms, sstatus, l1, sk, V = run_split(spec, U0, U, dt, args.steps, args.warmup, dev, stream, barrier)
         exact = {}
         if args.workload == "advected_wave":
             # both runs against the translated wave at t = (warm-up + timed steps) dt
@@ -364,89 +662,52 @@ def ours(args, rank, world, local_rank):
                 exact = {"t": t_end,
                          "l1_err_vs_exact_fp64": float(((U - Ue).abs().sum() / nrm).item()),
                          "l1_err_vs_exact_split": float(((V - Ue).abs().sum() / nrm).item())}
-        sstatus, _ = ss.stats()
-        split = {"value": world * ndof * args.steps * stages / (sms * 1e-3), "unit": UNIT,
-                 "ms_per_step": sms / args.steps, "speedup_vs_fp64": ms / sms,
+        del V
+        split = {"value": job_throughput(world, ndof, args.steps, stages, sms), "unit": UNIT,
+                 "ms_per_step": sms / args.steps, "speedup_vs_fp64": T.ms / sms,
                  "l1_rel_vs_fp64": l1, **exact, "device_status": sstatus,
                  "contractions": "volume term and traces 3xTF32 mma.sync m16n8k8 with FP32 accumulation, lift as FP32 FMAs, deviation form",
-                 "kernel_ms_per_launch": {k: round(v[0] / max(v[1], 1), 4) for k, v in sk.items() if v[1]}}
-        ss.close()
+                 "kernel_ms_per_launch": sk}
 
-    # adjoint: gradient of the transverse kinetic energy after 200 SSPRK3 steps of the 2D
-    # Kelvin-Helmholtz set-up at 128 x 256, p = 3, checkpoint every 20 steps, against the forward
-    adj = None
-    if not args.no_adjoint:
-        from paper_2205_00095_gb300 import adjoint as adjm
-        spec4 = wl.kh2d(nx=128, ny=256, degree=3)
-        sa = Solver(spec4, stream=stream, device=dev)
-        with torch.cuda.stream(stream):
-            A0 = sa.initial_state(wl.kh2d_ic(spec4, sa.node_coords_device()))
-            sa.enforce(A0)
-            Af = A0.clone()
-        dta = sa.cfl_dt(0.2)
-        sa.step(Af, dta, 3)  # warm-up and graph capture
-        with torch.cuda.stream(stream):
-            Af.copy_(A0)
-        barrier()
-        ev0.record(stream)
-        sa.step(Af, dta, 200)
-        ev1.record(stream)
-        torch.cuda.synchronize(dev)
-        fwd_ms = ev0.elapsed_time(ev1)
-        barrier()
-        # untimed warm-up rollout: one checkpoint segment, so that the stage buffers of a
-        # segment come from the allocator's cache in the timed run
-        with torch.cuda.stream(stream):
-            Uw = A0.clone().requires_grad_(True)
-            adjm.transverse_kinetic_energy(sa, adjm.rollout(sa, Uw, dta, 40, 20)).backward()
-            del Uw
-            U0g = A0.clone().requires_grad_(True)
-        torch.cuda.synchronize(dev)
-        t0 = time.perf_counter()
-        with torch.cuda.stream(stream):
-            UT = adjm.rollout(sa, U0g, dta, 200, 20)
-            Jv = adjm.transverse_kinetic_energy(sa, UT)
-            Jv.backward()
-        torch.cuda.synchronize(dev)
-        adj_ms = 1e3 * (time.perf_counter() - t0)
-        ast, ast_counts = sa.stats()
-        adj = {"workload": "kh_2d 128x256 elements p=3 TM Brent HLL SSPRK3, 200 steps, checkpoint every 20",
-               "objective": "sum rho gamma^2 v_y^2 at t_final", "forward_ms": fwd_ms,
-               "forward_plus_adjoint_ms": adj_ms, "adjoint_forward_ratio": adj_ms / fwd_ms,
-               "grad_norm": float(U0g.grad.norm()), "enforced_cells": ast_counts["enforced_cells"]}
-        sa.close()
+    rooflines = T.rooflines(peak, args.workload)
+    shares = T.shares()
+    ktimes = T.ktimes
+    launches, status, st = T.launches, T.status, T.st
+    T.close()
+    del s, U0, U
+    torch.cuda.empty_cache()
 
-    # oracle on the host cores (rank 0, N = 1 only)
+    # the larger configurations: 2D Taub-Matthews KH 256 x 512 and 3D KH 128^3
+    extra = None
+    if not args.no_workloads:
+        extra = {}
+        for name, steps in (("kh2d", args.steps), ("kh3d", min(args.steps, 20))):
+            if name == args.workload:
+                continue
+            extra[name] = run_workload_entry(make_spec(name), steps, args.warmup, dev, stream, barrier,
+                                             peak, world, with_split=not args.no_split)
+
+    adj = None if args.no_adjoint else adjoint_block(dev, stream, barrier)
+
+    # oracle on the host cores (rank 0, N = 1 only): all cores and one thread
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        procs = host_cores()
         sample = oracle_sample_spec(spec, target_s=5.0)
-        cv, ct = run_oracle(sample, 2, 0)
-        cpu = {"value": cv, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": f"2 oracle SSPRK3 steps on {'x'.join(map(str, sample['n_elem']))} elements of the "
-                         f"same workload ({dof(sample)} DOF, {ct:.1f} s), 1 thread"}
+        v1, t1 = run_oracle(sample, 2, 0)
+        vn, tn = run_oracle_all_cores(sample, 2, 0, procs)
+        n = "x".join(map(str, sample["n_elem"]))
+        cpu = {"value": vn, "unit": UNIT, "cores": procs, "kind": "oracle",
+               "sample": f"2 oracle SSPRK3 steps on {n} elements of the same workload ({dof(sample)} DOF) "
+                         f"in each of {procs} processes, one per host core ({tn:.1f} s)",
+               "single_thread": {"value": v1, "cores": 1,
+                                 "sample": f"2 oracle SSPRK3 steps on {n} elements, one process ({t1:.1f} s)"}}
 
-    # roofline of the dominant kernel (largest share of the timed region)
-    dom = max(ktimes, key=lambda k: ktimes[k][0])
-    dom_ms, dom_n = ktimes[dom]
-    avg_s = dom_ms / max(dom_n, 1) * 1e-3
-    roofline = None
-    if dom == "volume":
-        mean_it = st["c2p_iters_total"] / max(st["c2p_calls"], 1)
-        fpn = volume_kernel_flops_per_node(spec, mean_it)
-        flops = fpn * ndof
-        achieved = flops / avg_s / 1e12
-        roofline = {"kernel": "volume_kernel", "bound": "alu", "achieved": achieved,
-                    "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
-                    "traffic": measured_traffic("volume_kernel", args.workload),
-                    "fp64_pipe_busy_ncu": measured_fp64_pipe("volume_kernel", args.workload),
-                    "peak_source": "GB300 nominal dense FP64 1.25 TFLOP/s (DFMA probe measured 1.256)",
-                    "algorithmic_flops_per_node": fpn,
-                    "avg_launch_ms": avg_s * 1e3}
-    else:
-        roofline = {"kernel": dom, "bound": "alu", "achieved": None, "peak": FP64_PEAK_TFLOPS,
-                    "unit": "TFLOP/s", "frac": None, "traffic": None, "avg_launch_ms": avg_s * 1e3}
-    shares = {k: round(v[0] / max(sum(x[0] for x in ktimes.values()), 1e-12), 4)
-              for k, v in ktimes.items() if v[1]}
+    # roofline of the dominant kernel (largest share of the profiled pass)
+    dom = max(("volume", "face", "update"), key=lambda k: ktimes[k][0])
+    roofline = dict(rooflines[dom], peak_source=(
+        f"measured in this run: DFMA probe {probe['tflops']:.4f} TFLOP/s "
+        f"(SM clock {probe['clocks'].get('sm_mhz')} MHz); {COUNTING_RULE}"))
 
     if rank == 0:
         line = {
@@ -456,10 +717,18 @@ def ours(args, rank, world, local_rank):
             "config": {"workload": workload_desc(spec), "dof": ndof, "stages_per_step": stages,
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                        "l2": f"inputs larger than L2 (state {40 * ndof / 1e6:.0f} MB + scratch)",
-                       "precision": "fp64",
+                       "precision": "fp64", "timed_path": "dgsrhd_step graph replay",
                        **({"seed": spec["seed"]} if "seed" in spec else {})},
-            "roofline": roofline, "kernel_shares": shares,
+            "roofline": roofline, "rooflines": rooflines, "fp64_peak": probe,
+            "kernel_timing": {"pass": "second pass of the same K steps, every kernel launched directly "
+                                      "between CUDA events (no graph)",
+                              "ms_per_step": T.ms_prof / args.steps,
+                              "graph_gain": T.ms_prof / T.ms,
+                              "kernel_shares": shares,
+                              "kernel_ms_per_launch": {k: round(v[0] / max(v[1], 1), 4)
+                                                       for k, v in ktimes.items() if v[1]}},
             "split_precision": split,
+            "workloads": extra,
             "adjoint": adj,
             "cpu_baseline": cpu,
             "e2e": e2e,
@@ -482,10 +751,12 @@ def main():
                     help="con2prim solver (default: the workload's)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end timing")
-    ap.add_argument("--no-split", action="store_true", help="skip the split-precision run")
+    ap.add_argument("--no-split", action="store_true", help="skip the split-precision runs")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint/forward timing")
+    ap.add_argument("--no-workloads", action="store_true",
+                    help="skip the 2D and 3D Kelvin-Helmholtz workloads")
     ap.add_argument("--clock-log-dir", default=None,
-                    help="where the nvidia-smi clock samples of the timed region are written "
+                    help="where the nvidia-smi clock samples are written "
                          "(default: the system temporary directory)")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))

@@ -96,3 +96,34 @@ def test_oracle_sample_never_exceeds_the_workload():
     s = bench.oracle_sample_spec(spec, target_s=0.05)
     assert all(2 <= a <= b for a, b in zip(s["n_elem"], spec["n_elem"]))
     assert {k: v for k, v in s.items() if k != "n_elem"} == {k: v for k, v in spec.items() if k != "n_elem"}
+
+
+def test_face_and_update_kernel_work_of_the_bench_workload():
+    """Face kernel: two ideal face states (24 + 7 + 15 flops each) and the LLF combination (26)
+    = 118 flops per face point; 512 x 512 periodic elements carry 2 x 262144 x 4 face points.
+    Update kernel: lift 40 + Shu-Osher (10 + 25 + 25)/3 + admissibility 8 = 68 per node."""
+    spec = bench.make_spec("advected_wave")
+    assert bench.face_kernel_flops_per_point(spec) == 118.0
+    assert bench.face_points(spec) == 2 * 512 * 512 * 4
+    assert bench.update_kernel_flops_per_node(spec) == 68.0
+    # a non-periodic axis adds one face per line of elements along it
+    s = dict(spec, n_elem=[8, 4], bc=[("outflow", "outflow"), ("periodic", "periodic")])
+    assert bench.face_points(s) == (32 + 4) * 4 + 32 * 4
+    assert bench.face_kernel_flops_per_point(dict(spec, eos="tm", flux="hll")) == 2 * 61.0 + 32.0
+
+
+def test_kernel_roofline_is_flops_over_time_against_the_peak():
+    r = bench.kernel_roofline("face_kernel", 122.0, 2_097_152, 0.5, 1.25)
+    assert r["achieved"] == pytest.approx(122.0 * 2_097_152 / 0.5e-3 / 1e12)
+    assert r["frac"] == pytest.approx(r["achieved"] / 1.25)
+    assert r["bound"] == "alu" and r["unit"] == "TFLOP/s"
+    assert bench.kernel_roofline("x", 1.0, 1, 0.0, 1.0)["achieved"] is None
+
+
+def test_oracle_on_all_cores_adds_the_processes(monkeypatch):
+    """Every process steps its own copy of the sample: the job's rate is the sum of theirs."""
+    spec = dict(bench.make_spec("advected_wave"), n_elem=[4, 4])
+    v1, _ = bench.run_oracle(spec, 1, 0)
+    vn, tn = bench.run_oracle_all_cores(spec, 1, 0, 2)
+    assert vn > v1 and tn > 0.0
+    assert bench.host_cores() >= 1
