@@ -15,8 +15,6 @@ from __future__ import annotations
 
 import argparse
 import json
-import os
-import sys
 
 import numpy as np
 import torch
@@ -27,10 +25,7 @@ METHODS = [("ideal", "analytic"), ("ideal", "iterative"), ("tm", "analytic"), ("
 
 
 def _grid():
-    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-    if root not in sys.path:
-        sys.path.insert(0, root)
-    import workloads as wl
+    import workloads as wl  # the repository's input generators (repository root on the path)
     W, lor, P_si = wl.e2_grid()
     return W.reshape(5, -1), np.tile(lor, 25), np.repeat(P_si, 25)
 

@@ -1,4 +1,4 @@
-"""Growth of the Kelvin-Helmholtz instability in the paper's set-up (Sec. 4.4) on GB300: the
+"""Growth of the Kelvin-Helmholtz instability in the paper's set-up (Sec. 4.5) on GB300: the
 spatial mean <v_y^2>(t) sampled during the run, and the growth rate r from a least-squares fit
 of log <v_y^2> = A + r t over t in [1.5, 3.0], the window the paper fits.
 
@@ -9,8 +9,6 @@ from __future__ import annotations
 
 import argparse
 import json
-import os
-import sys
 import time
 
 import numpy as np
@@ -20,10 +18,7 @@ from .solver import Solver
 
 
 def _workloads():
-    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-    if root not in sys.path:
-        sys.path.insert(0, root)
-    import workloads as wl
+    import workloads as wl  # the repository's input generators (repository root on the path)
     return wl
 
 

@@ -1,4 +1,4 @@
-"""Throughput of the paper's Kelvin-Helmholtz set-up on GB300 (the performance study of Sec. 5):
+"""Throughput of the paper's Kelvin-Helmholtz set-up on GB300 (the performance study of Sec. 4.6):
 DOF-updates/s = DOF x steps x stages / time with DOF = n_x n_y (p + 1)^2, for the paper's
 resolutions 256 x 512, 512 x 1024 and 1024 x 2048, basis orders p = 0, 1, 2 paired with RK1,
 SSPRK2 and SSPRK3, HLL and HLLC, plus smaller meshes that show where the GPU saturates.  Each
@@ -11,8 +11,6 @@ from __future__ import annotations
 
 import argparse
 import json
-import os
-import sys
 
 import torch
 
@@ -20,10 +18,7 @@ from .solver import Solver
 
 
 def _workloads():
-    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-    if root not in sys.path:
-        sys.path.insert(0, root)
-    import workloads as wl
+    import workloads as wl  # the repository's input generators (repository root on the path)
     return wl
 
 

@@ -14,8 +14,6 @@ from __future__ import annotations
 import argparse
 import json
 import math
-import os
-import sys
 
 import numpy as np
 import torch
@@ -27,10 +25,7 @@ NAMES = ("D", "S_x", "S_y", "S_z", "E", "rho", "u_x", "u_y", "u_z", "P")
 
 
 def _workloads():
-    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-    if root not in sys.path:
-        sys.path.insert(0, root)
-    import workloads as wl
+    import workloads as wl  # the repository's input generators (repository root on the path)
     return wl
 
 

@@ -1,4 +1,4 @@
-"""The paper's 2D Riemann problems (Sec. 4.3) at a chosen resolution on GB300: quadrant states
+"""The paper's 2D Riemann problems (Sec. 4.4) at a chosen resolution on GB300: quadrant states
 on [-1, 1]^2, ideal EOS Gamma = 5/3, HLLC, a limiter and the physicality operator, to t = 0.8.
 Reports the step count, time and DOF-updates/s, the device counters, the smallest density
 and pressure at the nodes, and for test 3 (symmetric about the diagonal x = y) the largest
@@ -11,8 +11,6 @@ from __future__ import annotations
 
 import argparse
 import json
-import os
-import sys
 
 import numpy as np
 import torch
@@ -21,10 +19,7 @@ from .solver import Solver
 
 
 def _workloads():
-    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-    if root not in sys.path:
-        sys.path.insert(0, root)
-    import workloads as wl
+    import workloads as wl  # the repository's input generators (repository root on the path)
     return wl
 
 

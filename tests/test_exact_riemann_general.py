@@ -1,5 +1,5 @@
 """Pins for the exact 1D SRHD Riemann solution with transverse velocity and the Taub-Matthews
-EOS (test infrastructure for Riemann problem 3 and the Taub-Matthews blast wave of Sec. 4.2):
+EOS (test infrastructure for Riemann problem 3 and the Taub-Matthews blast wave of Sec. 4.3):
 agreement with the independent solver without transverse velocity, the rarefaction ODE against
 the acoustic eigenvectors of the system's own Jacobian, the Rankine-Hugoniot conditions at
 every shock, the integral conservation law of the whole self-similar solution, the simple-wave
@@ -160,7 +160,7 @@ def test_fans_are_self_similar_isentropic_with_h_u_t_constant(L, R, eos, G):
 
 
 def test_paper_reading_of_the_taub_matthews_blast():
-    """Fig. 9 (Sec. 4.2): the Taub-Matthews blast runs slightly ahead of both ideal gases, and
+    """Fig. 9 (Sec. 4.3): the Taub-Matthews blast runs slightly ahead of both ideal gases, and
     its transverse velocity behind the blast is the lowest of the three."""
     g = json.load(open(GOLDEN))
     L, R = g["left"], g["right"]

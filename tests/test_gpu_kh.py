@@ -1,4 +1,4 @@
-"""The Kelvin-Helmholtz diagnostic <v_y^2> (Sec. 4.4) through the C ABI against the oracle and
+"""The Kelvin-Helmholtz diagnostic <v_y^2> (Sec. 4.5) through the C ABI against the oracle and
 a closed form, and the growth of the instability in the paper's set-up."""
 import numpy as np
 import pytest
@@ -50,7 +50,7 @@ def test_kh_single_grows_exponentially(gpu_lib):
 
 
 def test_kh_throughput_points(gpu_lib):
-    """The throughput study of Sec. 5 on two points: runs clean, and the paper's smallest mesh
+    """The throughput study of Sec. 4.6 on two points: runs clean, and the paper's smallest mesh
     updates more DOF per second than a 32 x 64 mesh (the small one cannot fill the GPU)."""
     from paper_2205_00095_gb300 import kh_perf
     small = kh_perf.measure(32, 64, 1, "hll", steps=20)

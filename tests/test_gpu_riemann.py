@@ -1,4 +1,4 @@
-"""The paper's Riemann problems on the GPU at the paper's resolutions (Sec. 4.2, 4.3), HLLC
+"""The paper's Riemann problems on the GPU at the paper's resolutions (Sec. 4.2, 4.4), HLLC
 with the limiter: the 1D problems 2-5 and the Taub-Matthews blast with the three EOS of Fig. 9 at
 p = 1 from 256 to 2048 cells against the exact solution (L1 errors fall; the table is printed
 with -s), the ordering Fig. 9 shows between the three EOS, and the three 2D problems at 256^2

@@ -66,7 +66,7 @@ def test_backward_error(moderate_box, eos, c2p):
 @pytest.mark.parametrize("eos,G", [("ideal", 4.0 / 3.0), ("ideal", 5.0 / 3.0), ("tm", 5.0 / 3.0)])
 def test_hot_ultrarelativistic_round_trip(eos, G):
     """Hot states near |v| = 1, gamma up to 100 and Theta from 10 to 1e3 (the states behind the
-    Taub-Matthews blast of Sec. 4.2): the iterative solver converges and recovers the primitive
+    Taub-Matthews blast of Sec. 4.3): the iterative solver converges and recovers the primitive
     from its exact conserved state.  rho = D / gamma is the ill-conditioned output: the root
     w < 1 has a partner 1/w about 2/gamma away, so its rounding grows as gamma, and gamma's
     sensitivity to w adds another factor gamma (about 20 eps gamma^2)."""

@@ -1,4 +1,4 @@
-"""Oracle pins of the Kelvin-Helmholtz diagnostic <v_a^2> = (1/|Omega|) int v_a^2 dV (Sec. 4.4)
+"""Oracle pins of the Kelvin-Helmholtz diagnostic <v_a^2> = (1/|Omega|) int v_a^2 dV (Sec. 4.5)
 and of the paper's Kelvin-Helmholtz initial field."""
 import math
 

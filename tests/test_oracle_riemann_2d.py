@@ -1,4 +1,4 @@
-"""The paper's 2D Riemann problems (Sec. 4.3) in the oracle, HLLC with the limiter: the
+"""The paper's 2D Riemann problems (Sec. 4.4) in the oracle, HLLC with the limiter: the
 workloads hold the paper's states, every test runs to t = 0.8 with admissible means at p = 1,
 and the tests whose set-up is symmetric under the mirror x <-> y (v_x <-> v_y) keep that
 symmetry (test 3 to rounding; test 1 to 1e-4, whose colliding shocks amplify the rounding-level

@@ -16,12 +16,12 @@ A problem description is a plain dict:
 The workloads follow the problems of the paper:
   blast_wave      -- 1D relativistic blast wave (Sec. 4.2, problem 1)
   riemann_1d      -- 1D Riemann problems 2-5 of Sec. 4.2 (problem 5: a reflecting wall)
-  riemann_2d      -- the three 2D Riemann problems of Sec. 4.3 (four quadrants)
+  riemann_2d      -- the three 2D Riemann problems of Sec. 4.4 (four quadrants)
   advected_wave   -- 2D smooth density wave, periodic (smooth convergence case)
-  kh2d            -- 2D relativistic Kelvin-Helmholtz, double shear layer (Sec. 4.4 set-up
+  kh2d            -- 2D relativistic Kelvin-Helmholtz, double shear layer (Sec. 4.5 set-up
                      recast as periodic with two layers), Taub-Matthews EOS
   kh3d            -- 3D high-Lorentz-factor Kelvin-Helmholtz, Taub-Matthews EOS
-  kh_single       -- the paper's own Kelvin-Helmholtz set-up (Sec. 4.4): one shear layer,
+  kh_single       -- the paper's own Kelvin-Helmholtz set-up (Sec. 4.5): one shear layer,
                      ideal EOS, outflow in y
   linear_wave     -- linear waves of Sec. 4.1 in grid-aligned and oblique periodic boxes
   e2_grid         -- the 25 x 25 (gamma, P) grid of the con2prim accuracy study (Sec. 3.3)
@@ -66,7 +66,7 @@ RIEMANN_1D = {
 }
 
 
-# The paper's 2D Riemann problems (Sec. 4.3): primitive (rho, vx, vy, P) in the quadrants
+# The paper's 2D Riemann problems (Sec. 4.4): primitive (rho, vx, vy, P) in the quadrants
 # Q1 = [0,1]x[0,1], Q2 = [-1,0]x[0,1], Q3 = [-1,0]x[-1,0], Q4 = [0,1]x[-1,0].
 RIEMANN_2D = {
     1: [(0.035145216124503, 0.0, 0.0, 0.162931056509027), (0.1, 0.7, 0.0, 1.0),
@@ -79,7 +79,7 @@ RIEMANN_2D = {
 
 def riemann_2d(test: int, n: int = 128, degree: int = 1, flux: str = "hllc",
                limiter: bool = True) -> dict:
-    """2D Riemann problem `test` (1-3) of Sec. 4.3 on [-1,1]^2: ideal EOS Gamma = 5/3 with the
+    """2D Riemann problem `test` (1-3) of Sec. 4.4 on [-1,1]^2: ideal EOS Gamma = 5/3 with the
     iterative con2prim, transmissive (outflow) boundaries, HLLC and the limiter, to t = 0.8."""
     return dict(name="riemann_2d", test=test, dim=2, degree=degree, n_elem=[n, n],
                 lo=[-1.0, -1.0], hi=[1.0, 1.0], eos="ideal", gamma_ad=5.0 / 3.0, c2p="iterative",
@@ -115,14 +115,14 @@ def riemann_1d(problem: int, n: int = 128, degree: int = 1, flux: str = "hllc") 
 
 
 # The blast wave with relativistic temperature on the left and a non-relativistic one on the
-# right (Sec. 4.2, the Taub-Matthews test): primitive (rho, vx, vy, vz, P), transverse velocity
+# right (Sec. 4.3, the Taub-Matthews test): primitive (rho, vx, vy, vz, P), transverse velocity
 # on both sides, evolved to t = 0.7 with the Taub-Matthews EOS and the ideal EOS at 4/3 and 5/3.
 TM_BLAST = dict(left=(1.0, 0.0, 0.9, 0.0, 1e3), right=(1.0, 0.0, 0.99, 0.0, 1e-2), t_final=0.7)
 
 
 def tm_blast(eos: str = "tm", gamma_ad: float = 4.0 / 3.0, n: int = 128, degree: int = 1,
              flux: str = "hllc") -> dict:
-    """The Taub-Matthews blast wave of Sec. 4.2 on [0, 1] with the interface at x = 0.5 and
+    """The Taub-Matthews blast wave of Sec. 4.3 on [0, 1] with the interface at x = 0.5 and
     Dirichlet ends; `eos` "tm" (gamma_ad unused) or "ideal" (4/3 or 5/3 in the paper); the
     iterative con2prim, SSP-RK with p + 1 stages (at most 3), CFL 0.2."""
     left, right = TM_BLAST["left"], TM_BLAST["right"]
@@ -150,7 +150,7 @@ def kh2d(nx: int = 256, ny: int = 512, degree: int = 3, flux: str = "hll",
 
 def kh_single(nx: int = 256, ny: int = 512, degree: int = 1, flux: str = "hll",
               c2p: str = "iterative") -> dict:
-    """The paper's Kelvin-Helmholtz set-up (Sec. 4.4): [-0.5,0.5] x [-1,1], one shear layer at
+    """The paper's Kelvin-Helmholtz set-up (Sec. 4.5): [-0.5,0.5] x [-1,1], one shear layer at
     y = 0 of thickness a = 0.01 with shear velocity 0.25 (c = 1), rho0 = 1, P0 = 1, ideal EOS
     Gamma = 4/3 with the iterative con2prim, perturbation amplitude A = 0.05 at k = 2 pi;
     periodic in x, outflow in y; SSP-RK with p + 1 stages (at most 3)."""
