@@ -19,11 +19,12 @@ rank 0.  Keys beyond the common ones:
                        (launched directly): per-kernel mean launch time and share, and that
                        pass's own ms_per_step;
   roofline / rooflines the dominant kernel's and every stage kernel's algorithmic FP64 rate
-                       against the FP64 peak measured by the library's DFMA probe in this run
-                       (fp64_peak), with the counting rule;
-  fp64_peak            DFMA throughput (and FP32 FMA), the cost of division, square root,
-                       reciprocal square root and reciprocal cube root in DFMA-equivalents, and
-                       the SM clock during the probe;
+                       against the FP64 ALU peak derived from the unit counts (152 SMs x 2 FMA
+                       lanes x 2 flops) and the SM clock of the timed region, with the counting
+                       rule, and the dominant kernel's rate against the probe's DFMA rate;
+  fp64_peak            the library's DFMA probe (a DFMA loop reaches 0.84 of the ALU peak), FP32
+                       FMA throughput, the cost of division, square root, reciprocal square root
+                       and reciprocal cube root in DFMA-equivalents, and the SM clock during it;
   split_precision      the split-precision form on the same workload (rate, speed-up, L1
                        difference from FP64; on the advected wave both L1 errors against the
                        exact solution);
@@ -176,8 +177,18 @@ FACE_STATE_FLOPS = {"ideal": 24.0 + 7.0 + 15.0, "tm": 31.0 + 7.0 + 23.0}
 FACE_COMBINE_FLOPS = {"llf": 26.0, "hll": 32.0, "hllc": 72.0}
 COUNTING_RULE = ("algorithmic FP64 flops of the method as the oracle writes it (add, sub, mul, div, "
                  "sqrt, cbrt, library call = 1; fma = 2; comparisons 0); per node for the volume and "
-                 "update kernels, per face point for the face kernel; peak = 2 x the DFMA rate of "
-                 "the library's probe measured in this run")
+                 "update kernels, per face point for the face kernel")
+
+# FP64 FMA lanes per SM per clock: the count that gives the nominal 1.25 TFLOP/s of GB300 at its
+# 2070 MHz maximum SM clock (152 x 2 x 2 x 2.07e9 = 1.2586e12), and the one ncu's FP64-pipe
+# utilisation is taken against (the library's DFMA probe, 0.505e12 DFMA/s at 1985 MHz, reads
+# as 84 % busy).
+FP64_FMA_PER_SM_CLK = 2
+
+
+def fp64_alu_peak_tflops(sms: int, sm_mhz: float) -> float:
+    """The FP64 ALU peak from the unit counts and the SM clock: SMs x FMA lanes x 2 flops x clock."""
+    return sms * FP64_FMA_PER_SM_CLK * 2.0 * sm_mhz * 1e6 / 1e12
 
 
 def resolved_c2p(spec: dict) -> str:
@@ -257,7 +268,7 @@ def load_peaks():
 def kernel_roofline(name: str, flops_per_unit: float, units: int, avg_ms: float, peak_tflops: float,
                     traffic=None, pipe=None) -> dict:
     """Algorithmic FP64 rate of one kernel: flops_per_unit x units per launch / mean launch
-    time, against the measured FP64 peak."""
+    time, against the FP64 ALU peak."""
     achieved = flops_per_unit * units / (avg_ms * 1e-3) / 1e12 if avg_ms > 0 else None
     return {"kernel": name, "bound": "alu", "achieved": achieved, "peak": peak_tflops,
             "unit": "TFLOP/s", "frac": None if achieved is None else achieved / peak_tflops,
@@ -615,9 +626,10 @@ def ours(args, rank, world, local_rank):
             dist.barrier()
         torch.cuda.synchronize(dev)
 
-    # FP64 peak of this GPU, measured before the workload
-    probe = measure_fp64_peak(dev, stream, args.clock_log_dir, local_rank)
-    peak = probe["tflops"]
+    # FP64 throughput of this GPU, measured by the probe before the workload; the roofline's
+    # peak is derived from the unit counts and the SM clock sampled during the timed region
+    probe = None if args.no_probe else measure_fp64_peak(dev, stream, args.clock_log_dir, local_rank)
+    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
 
     spec = make_spec(args.workload, args.c2p)
     stages = spec["rk_stages"]
@@ -625,6 +637,9 @@ def ours(args, rank, world, local_rank):
     clk = ClockSampler(local_rank, args.clock_log_dir)
     T = Timed(spec, args.steps, args.warmup, dev, stream, barrier, clock=clk)
     s, U0, U, dt = T.s, T.U0, T.U, T.dt
+    clocks = clk.summary()
+    sm_mhz = clocks.get("sm_mhz") or (probe or {}).get("clocks", {}).get("sm_mhz") or 2070.0
+    peak = fp64_alu_peak_tflops(n_sm, sm_mhz)
     t_max = reduce_max_over_ranks(T.ms, world, dev)
     value = job_throughput(world, ndof, args.steps, stages, t_max)
 
@@ -705,9 +720,13 @@ def ours(args, rank, world, local_rank):
 
     # roofline of the dominant kernel (largest share of the profiled pass)
     dom = max(("volume", "face", "update"), key=lambda k: ktimes[k][0])
+    probe_note = ("" if probe is None else
+                  f"; the library's DFMA probe measured {probe['tflops']:.4f} TFLOP/s "
+                  f"({probe['tflops'] / peak:.2f} of it) in this run")
     roofline = dict(rooflines[dom], peak_source=(
-        f"measured in this run: DFMA probe {probe['tflops']:.4f} TFLOP/s "
-        f"(SM clock {probe['clocks'].get('sm_mhz')} MHz); {COUNTING_RULE}"))
+        f"derived FP64 ALU peak: {n_sm} SMs x {FP64_FMA_PER_SM_CLK} FMA/clock x 2 flops x {sm_mhz:.0f} MHz "
+        f"(median SM clock of the timed region){probe_note}; {COUNTING_RULE}"),
+        frac_of_probe=None if probe is None else rooflines[dom]["achieved"] / probe["tflops"])
 
     if rank == 0:
         line = {
@@ -733,7 +752,7 @@ def ours(args, rank, world, local_rank):
             "cpu_baseline": cpu,
             "e2e": e2e,
             "gpu_launches": launches,
-            "clocks": clk.summary(),
+            "clocks": clocks,
             "device_status": status,
             "stats": st,
         }
@@ -755,6 +774,9 @@ def main():
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint/forward timing")
     ap.add_argument("--no-workloads", action="store_true",
                     help="skip the 2D and 3D Kelvin-Helmholtz workloads")
+    ap.add_argument("--no-probe", action="store_true",
+                    help="skip the arithmetic throughput probe (the roofline's peak is derived "
+                         "from the unit counts and clocks either way)")
     ap.add_argument("--clock-log-dir", default=None,
                     help="where the nvidia-smi clock samples are written "
                          "(default: the system temporary directory)")

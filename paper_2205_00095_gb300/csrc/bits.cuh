@@ -76,6 +76,15 @@ __device__ __forceinline__ F32Pair f32_pair(double x) {
   return q;
 }
 
+// x 2^k for a normal x whose result stays normal, by adding k to the exponent field on the
+// integer pipe (exact, like the multiplication it replaces); zero (and a subnormal) is returned
+// unchanged.
+template <int K>
+__device__ __forceinline__ double ldexp_bits(double x) {
+  const long long b = __double_as_longlong(x);
+  return (b & 0x7ff0000000000000LL) == 0 ? x : __longlong_as_double(b + ((long long)K << 52));
+}
+
 // Reciprocal by the Newton-Raphson iteration r <- r + r (1 - x r), which squares the relative
 // error at every step (the classical iteration for division, e.g. P. Markstein, IBM J. Res.
 // Dev. 34 (1990) 111), from an FP32 seed: the seed is within ~2^-21, so two steps reach FP64

@@ -70,6 +70,23 @@ __device__ __forceinline__ bool pos_bits(double x) {  // x > 0 (false for NaN)
   return b > 0 && b <= kInfBits;
 }
 __device__ __forceinline__ bool finite_bits(double x) { return (dbits(x) & kInfBits) != kInfBits; }
+// Order key of a non-NaN double as a signed 64-bit integer (negative patterns mirrored), and the
+// min/max chosen by comparing keys on the integer pipe.  -0 orders below +0; with a NaN operand
+// either operand may be returned.
+__device__ __forceinline__ long long order_key(double x) {
+  const long long b = dbits(x);
+  return b ^ ((b >> 63) & 0x7fffffffffffffffLL);
+}
+__device__ __forceinline__ double min_bits(double a, double b) {
+  return order_key(a) <= order_key(b) ? a : b;
+}
+__device__ __forceinline__ double max_bits(double a, double b) {
+  return order_key(a) >= order_key(b) ? a : b;
+}
+// |x| by clearing the sign bit
+__device__ __forceinline__ double abs_bits(double x) {
+  return __longlong_as_double(dbits(x) & 0x7fffffffffffffffLL);
+}
 
 // D > 0, tau > 0 and tau (tau + 2D) > S^2 (S2 >= 0 or NaN; a NaN makes it false)
 __device__ __forceinline__ bool admissible_parts(double D, double S2, double tau) {
@@ -102,33 +119,39 @@ __device__ __forceinline__ double beta_ideal_closed_form(const Params& p, double
   const double a1 = p.m2G * SEw;
   const double a3 = p.m2Ggm1 * SEw;
   const double a2 = fma(p.G2, E * E, fma(p.tgm1, S2, -p.gm1sq * D2)) * w;
-  const double i1 = -a2;
-  const double i2 = a3 * a1 - 4.0 * a0;
-  const double i3 = 4.0 * a2 * a0 - a1 * a1 - a3 * a3 * a0;
-  const double R = (9.0 * i1 * i2 - 27.0 * i3 - 2.0 * i1 * i1 * i1) * (1.0 / 54.0);
-  const double Sq = (3.0 * i2 - i1 * i1) * (1.0 / 9.0);
-  const double T = R * R + Sq * Sq * Sq;
+  // resolvent cubic x^3 + i1 x^2 + i2 x + i3 with i1 = -a2, i2 = a1 a3 - 4 a0,
+  // i3 = 4 a2 a0 - a1^2 - a3^2 a0; with t = i1/3 its depressed form has
+  // R = (9 i1 i2 - 27 i3 - 2 i1^3)/54 = (t i2 - i3)/2 - t^3 and S = (3 i2 - i1^2)/9 = i2/3 - t^2
+  // multiplications by powers of two are exponent additions on the integer pipe (ldexp_bits)
+  const double m4a0 = -ldexp_bits<2>(a0);
+  const double i2 = fma(a3, a1, m4a0);
+  const double i3 = fma(a0, fma(4.0, a2, -a3 * a3), -a1 * a1);
+  const double t = a2 * (-1.0 / 3.0);  // i1 / 3
+  const double t2 = t * t;
+  const double R = fma(0.5, fma(t, i2, -i3), -t2 * t);
+  const double Sq = fma(i2, 1.0 / 3.0, -t2);
+  const double T = fma(R, R, Sq * Sq * Sq);
   double x;
   if (dbits(T) < 0 && dbits(T) != (long long)0x8000000000000000ULL) {  // T < 0
-    x = 2.0 * pow(R * R - T, 1.0 / 6.0) * cos(atan2(sqrt(-T), R) * (1.0 / 3.0)) - i1 * (1.0 / 3.0);
+    x = 2.0 * pow(R * R - T, 1.0 / 6.0) * cos(atan2(sqrt(-T), R) * (1.0 / 3.0)) - t;
   } else {
     // Cardano's pair cbrt(R + sqrt(T)) + cbrt(R - sqrt(T)): their product is -Sq, so with
     // y = R + sign(R) sqrt(T) (no cancellation) the pair is y^(1/3) - Sq y^(-1/3), both from
     // one reciprocal cube root r = y^(-1/3): y^(1/3) = y r^2.
     const double y = R + copysign(sqrt_nr(T), R);
     if (y == 0.0) {
-      x = -i1 * (1.0 / 3.0);
+      x = -t;
     } else {
       const double r = rcbrt_nr(y);
-      x = fma(y * r, r, -Sq * r) - i1 * (1.0 / 3.0);
+      x = fma(y * r, r, -Sq * r) - t;
     }
   }
   // The three radicands are non-negative for an admissible state; as xi -> 0 they shrink to
   // rounding level and can round below zero, so a negative one is taken as zero.
   auto root0 = [](double r) { return sqrt_nr(dbits(r) < 0 ? 0.0 : r); };
-  const double Bp = a3 + root0(fma(a3, a3, 4.0 * (x - a2)));
-  const double Cp = x - root0(fma(x, x, -4.0 * a0));
-  return 0.25 * (root0(fma(Bp, Bp, -8.0 * Cp)) - Bp);
+  const double Bp = a3 + root0(fma(a3, a3, ldexp_bits<2>(x - a2)));
+  const double Cp = x - root0(fma(x, x, m4a0));
+  return ldexp_bits<-2>(root0(fma(Bp, Bp, -ldexp_bits<3>(Cp))) - Bp);
 }
 
 // Ideal EOS, Newton-Raphson on the Riccardi quartic in w, beta = 2w/(1 + w^2)
@@ -690,9 +713,10 @@ __device__ __forceinline__ void numerical_flux(const Params& p, const double WL[
   wavespeeds_full<D>(R, lmR, lpR, XR, rR, irR, nullptr);
   face_tape(L, FL, rL, irL, lmL, lpL, recL);
   face_tape(R, FR, rR, irR, lmR, lpR, recR);
-  const double lamL = fmin(lmL, lmR), lamR = fmax(lpL, lpR);
+  // the selections compare bit patterns on the integer pipe (the FP64 pipe is the bottleneck)
+  const double lamL = min_bits(lmL, lmR), lamR = max_bits(lpL, lpR);
   if (p.flux == 1) {
-    const double sL = fmin(lamL, 0.0), sR = fmax(lamR, 0.0);
+    const double sL = dbits(lamL) < 0 ? lamL : 0.0, sR = pos_bits(lamR) ? lamR : 0.0;
     const double den = sR - sL;
     if (den == 0.0) {
 #pragma unroll
@@ -708,7 +732,7 @@ __device__ __forceinline__ void numerical_flux(const Params& p, const double WL[
 #pragma unroll
     for (int v = 0; v < 5; ++v) Fs2[v] = 2.0 * Fs[v];
   } else {
-    const double a = fmax(fabs(lamL), fabs(lamR));
+    const double a = max_bits(abs_bits(lamL), abs_bits(lamR));
 #pragma unroll
     for (int v = 0; v < 5; ++v) Fs2[v] = fma(-a, R.U[v] - L.U[v], FL[v] + FR[v]);
   }
