@@ -21,8 +21,10 @@ Stored:
     (4 D(h) - D(2h))/3, whose error is O(h^4).
 The difference between the h and 2h values bounds the error of the stored differences (their
 truncation error grows as h^2, their rounding as 1/h); the script requires it below 1e-8
-relative for dJ/dA and the directions, and below 1e-5 for the nodes (whose Richardson value
-removes the h^2 term), so that a check at 1e-6 relative measures the adjoint.
+relative for dJ/dA and the directions.  For the nodes it is the h^2 term itself (about 7e-5 at
+h = 1e-4), which the Richardson value removes, leaving O(h^4) and a rounding of about one unit
+of J's last place over 2h (5e-9 of the derivative); the script requires it below 1e-3, so
+that a check at 1e-6 relative measures the adjoint.
 
 Only the oracle and the input generators are used.  Run from the repository root:
     python tests/golden/make_kh_adjoint_c4.py [--procs N]
@@ -138,9 +140,9 @@ def main():
     dir_entries = [{"seed": s, "field": "v_x sin^2(2 pi x) exp(-2 y^2/0.01) (1 + r/2), r = numpy "
                     "RandomState(seed).standard_normal((E, Nn))", **entry("dir", s, H)} for s in SEEDS]
     dA = entry("A", None, H)
-    # keep the stored differences whose h and 2h values agree (1e-8 relative at h = 1e-6, 1e-5
-    # for the Richardson-corrected nodes)
-    kept = [n for n in node_entries if n["rel_diff_h_2h"] < 1e-5]
+    # keep the stored differences whose h and 2h values agree (1e-8 relative at h = 1e-6; for
+    # the Richardson-corrected nodes, whose h^2 term is removed, 1e-3)
+    kept = [n for n in node_entries if n["rel_diff_h_2h"] < 1e-3]
     bad = [x for x in [dA] + dir_entries if not x["rel_diff_h_2h"] < 1e-8]
 
     spec = spec_c4()
