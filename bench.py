@@ -87,13 +87,17 @@ def dof(spec: dict) -> int:
 # clocks during the timed region
 # ----------------------------------------------------------------------------------------
 class ClockSampler:
+    """nvidia-smi samples every 50 ms, each stamped with its wall-clock time. The sampler starts
+    before the warm-up (nvidia-smi itself takes a while to start), and `begin()` / `end()` mark
+    the timed region: the summary keeps the samples inside it."""
     QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
-             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap,timestamp")
 
     def __init__(self, gpu_index: int, log_dir: str | None = None, tag: str = "bench"):
         self.gpu = gpu_index
         self.proc = None
+        self.window = None
         self.path = os.path.join(log_dir or tempfile.gettempdir(), f"clocks_{tag}_{gpu_index}.csv")
 
     def __enter__(self):
@@ -102,10 +106,21 @@ class ClockSampler:
             self.fh = open(self.path, "w")
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.QUERY}", "--format=csv,noheader,nounits",
-                 "-lms", "200"], stdout=self.fh, stderr=subprocess.DEVNULL)
+                 "-lms", "50"], stdout=self.fh, stderr=subprocess.DEVNULL)
         except (OSError, FileNotFoundError):
             self.proc = None
+            return self
+        t0 = time.time()  # wait (3 s at most) for the first sample, so the timed region is covered
+        while self.proc.poll() is None and time.time() - t0 < 3.0 and os.path.getsize(self.path) == 0:
+            time.sleep(0.02)
         return self
+
+    def begin(self):
+        self.window = [time.time(), None]
+
+    def end(self):
+        if self.window is not None:
+            self.window[1] = time.time()
 
     def __exit__(self, *a):
         if self.proc is not None:
@@ -119,29 +134,46 @@ class ClockSampler:
     def summary(self):
         if self.proc is None or not os.path.exists(self.path):
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
-        return summarize_clock_lines(open(self.path).read().splitlines())
+        w = tuple(self.window) if self.window and self.window[1] is not None else None
+        return summarize_clock_lines(open(self.path).read().splitlines(), w)
 
 
-def summarize_clock_lines(lines):
-    """Median SM clock, max clock and the throttle reasons seen in nvidia-smi CSV samples."""
-    sm, smmax, reasons = [], [], set()
-    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+def _stamp(text):
+    """nvidia-smi's timestamp field ("2026/12/04 10:11:12.345", local time) in seconds."""
+    import datetime
+    try:
+        return datetime.datetime.strptime(text.strip(), "%Y/%m/%d %H:%M:%S.%f").timestamp()
+    except ValueError:
+        return None
+
+
+def summarize_clock_lines(lines, window=None):
+    """Median SM clock, max clock and the throttle reasons seen in nvidia-smi CSV samples; with a
+    (begin, end) window, only the samples stamped inside it (the nearest one if none is)."""
+    rows = []
     for line in lines:
         f = [x.strip() for x in line.split(",")]
         if len(f) < 9:
             continue
         try:
-            sm.append(float(f[1]))
-            smmax.append(float(f[2]))
+            sm, smmax = float(f[1]), float(f[2])
         except ValueError:
             continue
-        for name, val in zip(names, f[5:9]):
-            if val.lower() == "active":
-                reasons.add(name)
-    if not sm:
+        rows.append((sm, smmax, f[5:9], _stamp(f[9]) if len(f) > 9 else None))
+    scope = "all samples"
+    if window is not None and rows and all(r[3] is not None for r in rows):
+        inside = [r for r in rows if window[0] <= r[3] <= window[1]]
+        if inside:
+            rows, scope = inside, "timed region"
+        else:
+            mid = 0.5 * (window[0] + window[1])
+            rows, scope = [min(rows, key=lambda r: abs(r[3] - mid))], "nearest sample to the timed region"
+    if not rows:
         return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
-    return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smmax), "reasons": sorted(reasons),
-            "samples": len(sm)}
+    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    reasons = {n for r in rows for n, v in zip(names, r[2]) if v.lower() == "active"}
+    return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
+            "reasons": sorted(reasons), "samples": len(rows), "scope": scope}
 
 
 # ----------------------------------------------------------------------------------------
@@ -426,6 +458,8 @@ class Timed:
             self.U = self.U0.clone()
         self.dt = self.s.cfl_dt(0.2)
         s = self.s
+        if clock is not None:
+            clock.__enter__()
         s.step(self.U, self.dt, max(1, warmup))  # warm-up, captures the step graph
         torch.cuda.synchronize(dev)
         s.stats(reset=True)
@@ -433,12 +467,13 @@ class Timed:
         l0 = s.kernel_launches()
         barrier()
         if clock is not None:
-            clock.__enter__()
+            clock.begin()
         ev0.record(stream)
         s.step(self.U, self.dt, steps)
         ev1.record(stream)
         torch.cuda.synchronize(dev)
         if clock is not None:
+            clock.end()
             clock.__exit__()
         barrier()
         self.ms = ev0.elapsed_time(ev1)

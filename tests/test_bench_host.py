@@ -86,6 +86,26 @@ def test_clock_summary_takes_the_median_and_the_active_reasons(tmp_path):
     assert bench.ClockSampler(0).summary()["sm_mhz"] is None  # never started
 
 
+def test_clock_summary_keeps_the_timed_region(tmp_path):
+    """Samples carry nvidia-smi's timestamp; only those inside the marked window count, and the
+    nearest one stands in when the window is shorter than the sampling interval."""
+    import datetime
+    base = datetime.datetime(2026, 1, 2, 3, 4, 5)
+
+    def row(ms, clock, cap):
+        t = (base + datetime.timedelta(milliseconds=ms)).strftime("%Y/%m/%d %H:%M:%S.%f")[:-3]
+        return f"0, {clock}, 2070, 1000.0, 0x0, Not Active, Not Active, Not Active, {cap}, {t}"
+    lines = [row(0, 1400, "Active"), row(50, 2070, "Not Active"), row(100, 2055, "Not Active"),
+             row(150, 2070, "Not Active"), row(200, 1500, "Active")]
+    t0 = base.timestamp()
+    s = bench.summarize_clock_lines(lines, (t0 + 0.04, t0 + 0.16))
+    assert s["samples"] == 3 and s["sm_mhz"] == 2070.0 and s["reasons"] == [] and s["scope"] == "timed region"
+    s = bench.summarize_clock_lines(lines, (t0 + 0.101, t0 + 0.109))
+    assert s["samples"] == 1 and s["sm_mhz"] == 2055.0 and s["scope"].startswith("nearest")
+    s = bench.summarize_clock_lines(lines)
+    assert s["samples"] == 5 and s["reasons"] == ["sw_power_cap"]
+
+
 def test_job_throughput_counts_every_replica():
     assert bench.job_throughput(1, 1000, 10, 3, 1000.0) == 30000.0
     assert bench.job_throughput(4, 1000, 10, 3, 1000.0) == 4 * 30000.0
