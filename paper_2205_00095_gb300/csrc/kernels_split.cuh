@@ -246,9 +246,11 @@ __global__ void __launch_bounds__(SplitShape<DIM, N>::BLOCK)
 // (K = 2: the line's two face fluxes), far below a tensor-core tile, so it runs as FP32 FMAs on
 // the FP32 deviations F* - F_ref (exact products and one rounding each: at least the accuracy
 // of the 3xTF32 products).  The face fluxes arrive as FP32 head and tail (face_kernel with
-// pairs), the reference fluxes likewise (volume_kernel_split).
+// pairs), the reference fluxes likewise (volume_kernel_split).  The kernel waits on its loads
+// (few FP64 instructions per node hide little), so it is held to 48 registers for five resident
+// blocks per SM (three with the face points, which need more registers).
 template <int DIM, int N, bool FACES>
-__global__ void __launch_bounds__(Shape<DIM, N>::BLOCK)
+__global__ void __launch_bounds__(Shape<DIM, N>::BLOCK, FACES ? 3 : 5)
     update_kernel_split(Params p, const float* __restrict__ Rvol, const float2* __restrict__ Fs,
                         const float2* __restrict__ Fref, const double* Un, const double* Uk,
                         double* Uout, double a_n, double b_k, double dt, int mode, int enforce,
@@ -259,18 +261,22 @@ __global__ void __launch_bounds__(Shape<DIM, N>::BLOCK)
   // (2/dx_d) phi_i(-+1)/w_i per axis, rounded to FP32 and halved: the face kernel stores 2 F*
   // and the volume kernel 2 F_ref
   __shared__ float shl[DIM][2][N];
+  // the element's reference fluxes, read once per element rather than once per node
+  __shared__ float2 shref[S::EPB][DIM * 5];
   const int tid = threadIdx.x;
   if (tid < DIM * N) {
     const int d = tid / N, i = tid % N;
     shl[d][0][i] = 0.5f * f64_to_f32_bits(p.inv_half_dx[d] * p.lm[i]);
     shl[d][1][i] = 0.5f * f64_to_f32_bits(p.inv_half_dx[d] * p.lp[i]);
   }
-  __syncthreads();
   const int le = tid / Nn, li = tid - le * Nn;
   const long long e = (long long)blockIdx.x * S::EPB + le;
   const bool valid = e < p.E;
   const long long tot = p.E * Nn;
   const long long g = e * Nn + li;
+  if (valid)
+    for (int j = li; j < DIM * 5; j += Nn) shref[le][j] = Fref[(long long)j * p.E + e];
+  __syncthreads();
   double u[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
   if (valid) {
     int ijk[3];
@@ -286,7 +292,7 @@ __global__ void __launch_bounds__(Shape<DIM, N>::BLOCK)
       const float cm = shl[d][0][ijk[d]];
 #pragma unroll
       for (int v = 0; v < 5; ++v) {
-        const float2 r = Fref[((long long)d * 5 + v) * p.E + e];
+        const float2 r = shref[le][d * 5 + v];
         const float2 xh = fs[(v * nf + fhi) * S::Nt + t];
         const float2 xl = fs[(v * nf + flo) * S::Nt + t];
         const F32Pair rp{r.x, r.y};
