@@ -612,13 +612,20 @@ __device__ __forceinline__ void face_state(const Params& p, const double Wu[5], 
 // (v_d B +- r) i with r = sqrt(X), X = A (B (1 - v_d^2) + A), and i = 1/(A + B) from the face
 // state.  Also returns X, r and 1/r (0 where r = 0); 1/r is read from `ir_saved` when given.
 template <int D>
-__device__ __forceinline__ void wavespeeds_full(const FaceState& c, double& lm, double& lp,
-                                                double& X, double& r, double& ir,
-                                                const double* ir_saved) {
+__device__ __forceinline__ void wave_root(const FaceState& c, double& X, double& r, double& ir,
+                                          const double* ir_saved) {
   const double vd = c.v[D];
   X = c.A * fma(c.B, fma(-vd, vd, 1.0), c.A);
   ir = ir_saved ? *ir_saved : (pos_bits(X) ? rsqrt(X) : 0.0);
   r = X * ir;
+}
+
+template <int D>
+__device__ __forceinline__ void wavespeeds_full(const FaceState& c, double& lm, double& lp,
+                                                double& X, double& r, double& ir,
+                                                const double* ir_saved) {
+  wave_root<D>(c, X, r, ir, ir_saved);
+  const double vd = c.v[D];
   lm = fma(vd, c.B, -r) * c.i;
   lp = fma(vd, c.B, r) * c.i;
 }
@@ -698,7 +705,8 @@ __device__ __forceinline__ void hllc_flux(const FaceState& L, const FaceState& R
 // are exact powers-of-two scalings of the tables).  HLL: S_L = min(lambda_L, 0), S_R =
 // max(lambda_R, 0), F* = (S_R F_L - S_L F_R + S_L S_R (U_R - U_L)) / (S_R - S_L) (the average when
 // both vanish); LLF: F* = (F_L + F_R)/2 - a (U_R - U_L)/2 with a = max |lambda|; HLLC as above.
-template <int D>
+// TAPE: also fill recL / recR with the face-state tape (the forward pass of the reverse sweep).
+template <int D, bool TAPE>
 __device__ __forceinline__ void numerical_flux(const Params& p, const double WL[5],
                                                const double WR[5], double Fs2[5],
                                                double recL[kFaceTape], double recR[kFaceTape]) {
@@ -708,6 +716,19 @@ __device__ __forceinline__ void numerical_flux(const Params& p, const double WL[
   double FL[5], FR[5];
   phys_flux_dir<D>(L.U, L.v, L.P, FL);
   phys_flux_dir<D>(R.U, R.v, R.P, FR);
+  if (!TAPE && p.flux == 0) {
+    // LLF needs a = max |lambda| only.  Per side, with r >= 0 and (A + B) > 0, the larger of
+    // |v_d B - r| and |v_d B + r| is |v_d| B + r, and rounding is monotone and symmetric, so
+    // (|v_d| B + r) i is bit for bit the larger of |lambda_-| and |lambda_+|; the largest
+    // |lambda| over both sides is that of max(lambda_+) or min(lambda_-), as below.
+    double XL, rL, irL, XR, rR, irR;
+    wave_root<D>(L, XL, rL, irL, nullptr);
+    wave_root<D>(R, XR, rR, irR, nullptr);
+    const double a = max_bits(fma(abs_bits(L.v[D]), L.B, rL) * L.i, fma(abs_bits(R.v[D]), R.B, rR) * R.i);
+#pragma unroll
+    for (int v = 0; v < 5; ++v) Fs2[v] = fma(-a, R.U[v] - L.U[v], FL[v] + FR[v]);
+    return;
+  }
   double lmL, lpL, lmR, lpR, XL, rL, irL, XR, rR, irR;
   wavespeeds_full<D>(L, lmL, lpL, XL, rL, irL, nullptr);
   wavespeeds_full<D>(R, lmR, lpR, XR, rR, irR, nullptr);

@@ -290,7 +290,7 @@ __device__ __forceinline__ void face_point(const Params& p, const double* __rest
     if (p.bc[D][1] == 3) WR[1 + D] = -WR[1 + D];
   }
   double F[5], rec[2][kFaceTape];
-  numerical_flux<D>(p, WL, WR, F, rec[0], rec[1]);  // F = 2 F*
+  numerical_flux<D, SAVE>(p, WL, WR, F, rec[0], rec[1]);  // F = 2 F*
   double* out = Fs + p.fs_off[D];
   if (pairs) {
     float2* outp = reinterpret_cast<float2*>(out);
