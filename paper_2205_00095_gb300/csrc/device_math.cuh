@@ -567,12 +567,14 @@ __device__ __forceinline__ void face_state_core(const Params& p, const double Wu
     c.K = fma(p.amG, P, rho);  // rho + (alpha - Gamma) P
     c.sg = c.isg = c.Z = c.iZ = 0.0;
   } else {
-    const double x2 = fma(P, P, (4.0 / 9.0) * rho * rho);
+    const double rho2 = rho * rho;
+    const double x2 = fma(P, P, (4.0 / 9.0) * rho2);
     c.isg = rec ? rec[1] : rsqrt(x2);
     c.sg = x2 * c.isg;
     c.Z = fma(2.0 / 3.0, rho, c.sg);
     c.A = P * fma(3.0, P, 5.0 * c.sg);
-    c.K = __dsub_rn(fma(12.0 * P, __dadd_rn(P, c.sg), 2.0 * rho * rho), c.A);
+    // 12 P (P + s) + 2 rho^2 - A = 9 P^2 + 7 P s + 2 rho^2: positive terms only
+    c.K = fma(P, fma(9.0, P, 7.0 * c.sg), ldexp_bits<1>(rho2));
   }
   c.B = c.q * c.K;
   const double L1 = __dadd_rn(c.lor, 1.0), AB = __dadd_rn(c.A, c.B);
@@ -591,7 +593,7 @@ __device__ __forceinline__ void face_state_core(const Params& p, const double Wu
     c.id1 = t * c.Z * AB;
     c.i = t * ZL;
   }
-  c.rho_hm1 = p.eos == 0 ? p.alpha * P : fma(1.5 * P * P, c.iZ, 2.5 * P);
+  c.rho_hm1 = p.eos == 0 ? p.alpha * P : P * fma(1.5 * P, c.iZ, 2.5);
   const double D = c.lor * rho;
   const double rhoh_lor = __dadd_rn(rho, c.rho_hm1) * c.lor;  // S = rho h gamma u
   c.U[0] = D;
@@ -744,8 +746,9 @@ __device__ __forceinline__ void numerical_flux(const Params& p, const double WL[
       for (int v = 0; v < 5; ++v) Fs2[v] = FL[v] + FR[v];
     } else {
       const double id2 = recip_nr(0.5 * den);  // 2 / (S_R - S_L)
+      const double cR = sR * id2, cL = sL * id2, cLR = sL * cR;
 #pragma unroll
-      for (int v = 0; v < 5; ++v) Fs2[v] = (sR * FL[v] - sL * FR[v] + sL * sR * (R.U[v] - L.U[v])) * id2;
+      for (int v = 0; v < 5; ++v) Fs2[v] = fma(cR, FL[v], fma(-cL, FR[v], cLR * (R.U[v] - L.U[v])));
     }
   } else if (p.flux == 2) {
     double Fs[5];
