@@ -339,9 +339,10 @@ __device__ __forceinline__ T brent_cubic(T c1, T c2, T c3, T a, T b, T fa, T fb,
 // that leaves the bracket is replaced by bisection, and the bracket shrinks with the sign of
 // the cubic.  The bracket holds the unique non-negative root, so the polish cannot stray to
 // another root (the reason Sec. 3.2 gives for a bracketed solver).  When the cubic does not
-// change sign across that bracket, FP64 Brent runs on the paper's bracket instead.  Stop rule
-// |dW| <= 2 eps |W| + 1e-300 (Brent's tolerance); `iters` counts all iterations and
-// max_iter caps their sum.
+// change sign across that bracket, FP64 Brent runs on the paper's bracket instead.  The polish
+// stops once the step, or the error left after it (Newton's quadratic error term), is within
+// 2 eps |W| + 1e-300 (Brent's tolerance); `iters` counts all iterations and max_iter caps
+// their sum.
 static __device__ __noinline__ double W_tm_brent(double xi, double eta, int max_iter, double rtol,
                                                  int& iters, bool& conv) {
   const Cubic cc = tm_cubic(xi, eta);
@@ -381,8 +382,14 @@ static __device__ __noinline__ double W_tm_brent(double xi, double eta, int max_
     const double fa = cubic_at(cc, a), fb = cubic_at(cc, b);
     if (fa * fb <= 0.0) {
       const bool rising = fa < 0.0;  // the cubic runs from fa to fb across [a, b]
+      const double tol = fmax(2.0 * 2.220446049250313e-16, rtol);
+      const double c1x2 = 2.0 * cc.c1;
       double W = W32d;
       int it = it32;
+      // The first step from the FP32 root is of the FP32 rounding size, far above the FP64
+      // tolerance, so the stop test starts with the second (with the first for a caller's
+      // relative tolerance, which that step may already meet).
+      bool test = rtol > 0.0;
       while (it < max_iter) {
         ++it;
         const double f = cubic_at(cc, W);
@@ -394,15 +401,27 @@ static __device__ __noinline__ double W_tm_brent(double xi, double eta, int max_
           a = W;
         else
           b = W;
-        const double df = fma(fma(3.0, W, 2.0 * cc.c1), W, cc.c2);
-        const double Wn = W - f * recip_nr(df);
-        // stop on a Newton step at rounding level before the bracket test: once W sits on
-        // the root, rounding noise in f can move a bracket end onto W itself
-        if (fabs(Wn - W) <= fmax(2.0 * 2.220446049250313e-16, rtol) * fabs(W) + 1e-300) {
-          W = Wn;
-          conv = true;
-          break;
+        const double r = recip_nr(fma(fma(3.0, W, c1x2), W, cc.c2));  // 1 / f'(W)
+        const double dW = f * r;
+        const double Wn = W - dW;
+        if (test) {
+          // Stop once the step, or the error it leaves, is within the tolerance; the latter
+          // spares the last iteration, whose own step would be at rounding level.  For the
+          // monic cubic a Newton step from W* + e leaves (f''(W*) e^2 / 2 + 2 e^3) / f'(W),
+          // bounded here with e ~ dW, |f''(W*)| <= |f''(W)| + 6|e| and a factor 4 to spare.
+          // Both sides are non-negative, so the comparison runs on the bit patterns (integer
+          // pipe); the step is taken before the bracket test: once W sits on the root,
+          // rounding noise in f can move a bracket end onto W itself.
+          const double adW = fabs(dW);
+          const double est = fabs(r) * (adW * adW) * fma(2.0, fabs(fma(6.0, W, c1x2)), 20.0 * adW);
+          const long long thr = dbits(fma(tol, fabs(W), 1e-300));
+          if (min(dbits(adW), dbits(est)) <= thr) {
+            W = Wn;
+            conv = true;
+            break;
+          }
         }
+        test = true;
         W = (Wn > a && Wn < b) ? Wn : 0.5 * (a + b);
       }
       iters = it;
