@@ -727,6 +727,23 @@ __device__ __forceinline__ void hllc_flux(const FaceState& L, const FaceState& R
 // max(lambda_R, 0), F* = (S_R F_L - S_L F_R + S_L S_R (U_R - U_L)) / (S_R - S_L) (the average when
 // both vanish); LLF: F* = (F_L + F_R)/2 - a (U_R - U_L)/2 with a = max |lambda|; HLLC as above.
 // TAPE: also fill recL / recR with the face-state tape (the forward pass of the reverse sweep).
+// wL F_L + wR F_R + c (U_R - U_L) along D from the two face states, with the normal fluxes
+// (U v_d; S_D v_d + P; (tau + P) v_d) folded into the weights rather than formed first.
+template <int D>
+__device__ __forceinline__ void flux_mix(const FaceState& L, const FaceState& R, double wL,
+                                         double wR, double c, double out[5]) {
+  const double aL = wL * L.v[D], aR = wR * R.v[D];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const double t = c * (R.U[k] - L.U[k]);
+    out[k] = (k == 1 + D) ? fma(L.U[k], aL, fma(R.U[k], aR, fma(wL, L.P, fma(wR, R.P, t))))
+                          : fma(L.U[k], aL, fma(R.U[k], aR, t));
+  }
+  out[4] = fma(L.U[4] + L.P, aL, fma(R.U[4] + R.P, aR, c * (R.U[4] - L.U[4])));
+}
+
+// TAPE: also fill recL / recR with the face-state tape (the forward pass of the reverse sweep).
+// Both variants give the same bits.
 template <int D, bool TAPE>
 __device__ __forceinline__ void numerical_flux(const Params& p, const double WL[5],
                                                const double WR[5], double Fs2[5],
@@ -734,9 +751,6 @@ __device__ __forceinline__ void numerical_flux(const Params& p, const double WL[
   FaceState L, R;
   face_state(p, WL, L);
   face_state(p, WR, R);
-  double FL[5], FR[5];
-  phys_flux_dir<D>(L.U, L.v, L.P, FL);
-  phys_flux_dir<D>(R.U, R.v, R.P, FR);
   if (!TAPE && p.flux == 0) {
     // LLF needs a = max |lambda| only.  Per side, with r >= 0 and (A + B) > 0, the larger of
     // |v_d B - r| and |v_d B + r| is |v_d| B + r, and rounding is monotone and symmetric, so
@@ -746,28 +760,32 @@ __device__ __forceinline__ void numerical_flux(const Params& p, const double WL[
     wave_root<D>(L, XL, rL, irL, nullptr);
     wave_root<D>(R, XR, rR, irR, nullptr);
     const double a = max_bits(fma(abs_bits(L.v[D]), L.B, rL) * L.i, fma(abs_bits(R.v[D]), R.B, rR) * R.i);
-#pragma unroll
-    for (int v = 0; v < 5; ++v) Fs2[v] = fma(-a, R.U[v] - L.U[v], FL[v] + FR[v]);
+    flux_mix<D>(L, R, 1.0, 1.0, -a, Fs2);
     return;
   }
   double lmL, lpL, lmR, lpR, XL, rL, irL, XR, rR, irR;
   wavespeeds_full<D>(L, lmL, lpL, XL, rL, irL, nullptr);
   wavespeeds_full<D>(R, lmR, lpR, XR, rR, irR, nullptr);
-  face_tape(L, FL, rL, irL, lmL, lpL, recL);
-  face_tape(R, FR, rR, irR, lmR, lpR, recR);
+  double FL[5], FR[5];  // the normal fluxes, for HLLC and the tape
+  if (TAPE || p.flux == 2) {
+    phys_flux_dir<D>(L.U, L.v, L.P, FL);
+    phys_flux_dir<D>(R.U, R.v, R.P, FR);
+  }
+  if (TAPE) {
+    face_tape(L, FL, rL, irL, lmL, lpL, recL);
+    face_tape(R, FR, rR, irR, lmR, lpR, recR);
+  }
   // the selections compare bit patterns on the integer pipe (the FP64 pipe is the bottleneck)
   const double lamL = min_bits(lmL, lmR), lamR = max_bits(lpL, lpR);
   if (p.flux == 1) {
     const double sL = dbits(lamL) < 0 ? lamL : 0.0, sR = pos_bits(lamR) ? lamR : 0.0;
     const double den = sR - sL;
     if (den == 0.0) {
-#pragma unroll
-      for (int v = 0; v < 5; ++v) Fs2[v] = FL[v] + FR[v];
+      flux_mix<D>(L, R, 1.0, 1.0, 0.0, Fs2);
     } else {
       const double id2 = recip_nr(0.5 * den);  // 2 / (S_R - S_L)
-      const double cR = sR * id2, cL = sL * id2, cLR = sL * cR;
-#pragma unroll
-      for (int v = 0; v < 5; ++v) Fs2[v] = fma(cR, FL[v], fma(-cL, FR[v], cLR * (R.U[v] - L.U[v])));
+      const double cR = sR * id2, cL = sL * id2;
+      flux_mix<D>(L, R, cR, -cL, sL * cR, Fs2);
     }
   } else if (p.flux == 2) {
     double Fs[5];
@@ -776,8 +794,7 @@ __device__ __forceinline__ void numerical_flux(const Params& p, const double WL[
     for (int v = 0; v < 5; ++v) Fs2[v] = 2.0 * Fs[v];
   } else {
     const double a = max_bits(abs_bits(lamL), abs_bits(lamR));
-#pragma unroll
-    for (int v = 0; v < 5; ++v) Fs2[v] = fma(-a, R.U[v] - L.U[v], FL[v] + FR[v]);
+    flux_mix<D>(L, R, 1.0, 1.0, -a, Fs2);
   }
 }
 
