@@ -721,12 +721,6 @@ __device__ __forceinline__ void hllc_flux(const FaceState& L, const FaceState& R
   for (int k = 0; k < 5; ++k) Fs[k] = fma(lam, Us[k] - UK[k], FK[k]);
 }
 
-// Numerical flux along axis D between face states given as (rho, u, P), returned DOUBLED (2 F*:
-// the factor 1/2 of LLF and of the HLL denominator moves into the lift coefficients, which
-// are exact powers-of-two scalings of the tables).  HLL: S_L = min(lambda_L, 0), S_R =
-// max(lambda_R, 0), F* = (S_R F_L - S_L F_R + S_L S_R (U_R - U_L)) / (S_R - S_L) (the average when
-// both vanish); LLF: F* = (F_L + F_R)/2 - a (U_R - U_L)/2 with a = max |lambda|; HLLC as above.
-// TAPE: also fill recL / recR with the face-state tape (the forward pass of the reverse sweep).
 // wL F_L + wR F_R + c (U_R - U_L) along D from the two face states, with the normal fluxes
 // (U v_d; S_D v_d + P; (tau + P) v_d) folded into the weights rather than formed first.
 template <int D>
@@ -742,6 +736,11 @@ __device__ __forceinline__ void flux_mix(const FaceState& L, const FaceState& R,
   out[4] = fma(L.U[4] + L.P, aL, fma(R.U[4] + R.P, aR, c * (R.U[4] - L.U[4])));
 }
 
+// Numerical flux along axis D between face states given as (rho, u, P), returned DOUBLED (2 F*:
+// the factor 1/2 of LLF and of the HLL denominator moves into the lift coefficients, which
+// are exact powers-of-two scalings of the tables).  HLL: S_L = min(lambda_L, 0), S_R =
+// max(lambda_R, 0), F* = (S_R F_L - S_L F_R + S_L S_R (U_R - U_L)) / (S_R - S_L) (the average when
+// both vanish); LLF: F* = (F_L + F_R)/2 - a (U_R - U_L)/2 with a = max |lambda|; HLLC as above.
 // TAPE: also fill recL / recR with the face-state tape (the forward pass of the reverse sweep).
 // Both variants give the same bits.
 template <int D, bool TAPE>
