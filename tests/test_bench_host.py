@@ -153,3 +153,14 @@ def test_fp64_alu_peak_from_unit_counts_and_clock():
     """152 SMs x 2 FMA lanes x 2 flops x 2070 MHz = 1.2586 TFLOP/s, GB300's nominal 1.25."""
     assert bench.fp64_alu_peak_tflops(152, 2070.0) == pytest.approx(1.258560)
     assert bench.fp64_alu_peak_tflops(152, 1035.0) == pytest.approx(1.258560 / 2)
+
+
+def test_smaller_capture_cases_keep_the_workload_and_drop_the_traffic_record():
+    """--n shrinks a workload for a profiler capture (n x n, n x 2n, n^3) without changing its
+    method choices, and the committed ncu record (taken at the benchmark size) is not applied."""
+    for name, n, shape in (("advected_wave", 64, [64, 64]), ("kh2d", 32, [32, 64]), ("kh3d", 16, [16, 16, 16])):
+        big, small = bench.make_spec(name), bench.make_spec(name, None, n)
+        assert small["n_elem"] == shape
+        assert {k: v for k, v in small.items() if k != "n_elem"} == {k: v for k, v in big.items() if k != "n_elem"}
+    assert bench.measured_traffic("volume_kernel", "advected_wave_n64") is None
+    assert bench.measured_traffic("volume_kernel", "advected_wave") is not None
