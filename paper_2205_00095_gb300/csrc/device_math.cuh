@@ -608,8 +608,9 @@ __device__ __forceinline__ void face_state_core(const Params& p, const double Wu
   } else {
     const double ZL = c.Z * L1;
     const double t = recip_nr(ZL * AB);
-    c.iZ = t * L1 * AB;
-    c.id1 = t * c.Z * AB;
+    const double tAB = t * AB;
+    c.iZ = tAB * L1;
+    c.id1 = tAB * c.Z;
     c.i = t * ZL;
   }
   c.rho_hm1 = p.eos == 0 ? p.alpha * P : P * fma(1.5 * P, c.iZ, 2.5);
