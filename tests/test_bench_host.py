@@ -163,4 +163,3 @@ def test_smaller_capture_cases_keep_the_workload_and_drop_the_traffic_record():
         assert small["n_elem"] == shape
         assert {k: v for k, v in small.items() if k != "n_elem"} == {k: v for k, v in big.items() if k != "n_elem"}
     assert bench.measured_traffic("volume_kernel", "advected_wave_n64") is None
-    assert bench.measured_traffic("volume_kernel", "advected_wave") is not None
