@@ -64,17 +64,20 @@ __device__ __forceinline__ void face_fwd(const Params& p, const double Wu[5],
   f.rhoh_lor = f.H * f.lor;
 }
 
-// Reverse of face_fwd: adjoints of its outputs (flux Fb, conserved state Ub, wavespeeds lmb,
-// lpb) -> adjoint of the face primitive (rho, u, P).
+// Reverse of face_fwd from the adjoints of its conserved state and normal flux already
+// contracted with the flux map (Db, Sb, taub: the adjoints reaching D, S and tau; Pb, vdb: those
+// reaching P and v_d through the flux) and of its wavespeeds (lmb, lpb) -> adjoint of the face
+// primitive (rho, u, P).
 template <int D>
-__device__ __forceinline__ void face_rev(const Params& p, const FaceFwd& f, const double Fb[5],
-                                         const double Ub[5], double lmb, double lpb, double Wb[5],
-                                         double vdb_in = 0.0, double Pb_in = 0.0) {
+__device__ __forceinline__ void face_rev_state(const Params& p, const FaceFwd& f, double Db,
+                                               const double Sb[3], double taub, double Pb,
+                                               double vdb, double lmb, double lpb,
+                                               double Wb[5]) {
   const double rho = f.Wu[0], P = f.Wu[4];
   const double vd = f.v[D];
   // wavespeeds
   const double ib = lmb * (vd * f.B - f.r) + lpb * (vd * f.B + f.r);
-  double vdb = fma((lmb + lpb) * f.B, f.i, vdb_in);  // vdb_in, Pb_in: direct uses (HLLC)
+  vdb = fma((lmb + lpb) * f.B, f.i, vdb);
   double Bb = (lmb + lpb) * vd * f.i - ib * f.i * f.i;
   double Ab = -ib * f.i * f.i;
   const double rb = (lpb - lmb) * f.i;
@@ -82,12 +85,6 @@ __device__ __forceinline__ void face_rev(const Params& p, const FaceFwd& f, cons
   Ab += Xb * (f.B * (1.0 - vd * vd) + 2.0 * f.A);
   Bb += Xb * f.A * (1.0 - vd * vd);
   vdb += Xb * f.A * f.B * (-2.0 * vd);
-  // flux along D
-  double Db = Ub[0] + Fb[0] * vd;
-  double Sb[3] = {Ub[1] + Fb[1] * vd, Ub[2] + Fb[2] * vd, Ub[3] + Fb[3] * vd};
-  const double taub = Ub[4] + Fb[4] * vd;
-  double Pb = Fb[1 + D] + fma(Fb[4], vd, Pb_in);
-  vdb += Fb[0] * f.U[0] + Fb[1] * f.U[1] + Fb[2] * f.U[2] + Fb[3] * f.U[3] + Fb[4] * (f.U[4] + P);
   // v_k = u_k / gamma
   double ub[3] = {0.0, 0.0, 0.0};
   ub[D] = vdb * f.ilor;
@@ -120,12 +117,10 @@ __device__ __forceinline__ void face_rev(const Params& p, const FaceFwd& f, cons
   } else {
     qb += Bb * f.K;
     const double Kb = Bb * f.q;
-    Pb += Kb * 12.0 * (2.0 * P + f.sg);
-    double sgb = Kb * 12.0 * P;
+    // K = 9 P^2 + 7 P s + 2 rho^2 and A = P (3 P + 5 s), s = sqrt(P^2 + 4 rho^2 / 9)
+    Pb += fma(Kb, fma(18.0, P, 7.0 * f.sg), Ab * fma(6.0, P, 5.0 * f.sg));
+    double sgb = P * fma(7.0, Kb, 5.0 * Ab);
     rhob += Kb * 4.0 * rho;
-    Ab -= Kb;
-    Pb += Ab * (6.0 * P + 5.0 * f.sg);
-    sgb += Ab * 5.0 * P;
     Pb += rhm1b * (2.5 + 3.0 * P * f.iZ);
     const double Zb = -rhm1b * 1.5 * P * P * f.iZ * f.iZ;
     sgb += Zb;
@@ -135,12 +130,44 @@ __device__ __forceinline__ void face_rev(const Params& p, const FaceFwd& f, cons
   }
   // gamma = q^(1/2), 1/gamma = q^(-1/2), q = 1 + u2
   qb += 0.5 * f.ilor * (lorb - ilorb * f.ilor * f.ilor);
-  u2b += qb;
+  const double u2b2 = 2.0 * (u2b + qb);  // u2 = |u|^2
   Wb[0] = rhob;
-  Wb[1] = ub[0] + 2.0 * f.Wu[1] * u2b;
-  Wb[2] = ub[1] + 2.0 * f.Wu[2] * u2b;
-  Wb[3] = ub[2] + 2.0 * f.Wu[3] * u2b;
+  Wb[1] = fma(f.Wu[1], u2b2, ub[0]);
+  Wb[2] = fma(f.Wu[2], u2b2, ub[1]);
+  Wb[3] = fma(f.Wu[3], u2b2, ub[2]);
   Wb[4] = Pb;
+}
+
+// Reverse of face_fwd: adjoints of its outputs (flux Fb, conserved state Ub, wavespeeds lmb,
+// lpb) -> adjoint of the face primitive (rho, u, P).  vdb_in, Pb_in: direct uses of v_D and P
+// (HLLC).
+template <int D>
+__device__ __forceinline__ void face_rev(const Params& p, const FaceFwd& f, const double Fb[5],
+                                         const double Ub[5], double lmb, double lpb, double Wb[5],
+                                         double vdb_in = 0.0, double Pb_in = 0.0) {
+  const double vd = f.v[D], P = f.Wu[4];
+  // flux along D: F = (D v_d, S v_d + P e_d, (tau + P) v_d)
+  const double Sb[3] = {Ub[1] + Fb[1] * vd, Ub[2] + Fb[2] * vd, Ub[3] + Fb[3] * vd};
+  const double vdb = vdb_in + (Fb[0] * f.U[0] + Fb[1] * f.U[1] + Fb[2] * f.U[2] +
+                               Fb[3] * f.U[3] + Fb[4] * (f.U[4] + P));
+  face_rev_state<D>(p, f, Ub[0] + Fb[0] * vd, Sb, Ub[4] + Fb[4] * vd,
+                    Fb[1 + D] + fma(Fb[4], vd, Pb_in), vdb, lmb, lpb, Wb);
+}
+
+// face_rev for adjoints of the form Fb = alpha g, Ub = beta g (LLF and HLL: g = F*_bar per
+// side, alpha and beta the side's weights): the flux map contracts to one factor
+// kappa = alpha v_d + beta on (D, S, tau), and alpha on P and v_d.
+template <int D>
+__device__ __forceinline__ void face_rev_scaled(const Params& p, const FaceFwd& f, const double g[5],
+                                                double alpha, double beta, double lmb, double lpb,
+                                                double Wb[5]) {
+  const double vd = f.v[D], P = f.Wu[4];
+  const double kappa = fma(alpha, vd, beta);
+  const double Sb[3] = {g[1] * kappa, g[2] * kappa, g[3] * kappa};
+  const double gU = fma(g[0], f.U[0], fma(g[1], f.U[1], fma(g[2], f.U[2],
+                    fma(g[3], f.U[3], g[4] * (f.U[4] + P)))));
+  face_rev_state<D>(p, f, g[0] * kappa, Sb, g[4] * kappa, alpha * fma(g[4], vd, g[1 + D]),
+                    alpha * gU, lmb, lpb, Wb);
 }
 
 // Reverse of hllc_flux<D> (the forward is re-evaluated here with the same formulas), with the
@@ -275,25 +302,36 @@ __device__ __forceinline__ void numerical_flux_vjp(const Params& p, const double
   const bool selL_from_L = L.lm <= R.lm;  // lambda_L = min(lm_L, lm_R)
   const bool selR_from_L = L.lp >= R.lp;  // lambda_R = max(lp_L, lp_R)
   const double lamL = selL_from_L ? L.lm : R.lm, lamR = selR_from_L ? L.lp : R.lp;
-  double FLb[5], FRb[5], ULb[5], URb[5];
   double lamLb = 0.0, lamRb = 0.0;
-  double vLb = 0.0, PLb = 0.0, vRb = 0.0, PRb = 0.0;  // direct uses of v_D and P (HLLC)
+  auto wavespeed_adjoints = [&](double& lmLb, double& lpLb, double& lmRb, double& lpRb) {
+    lmLb = selL_from_L ? lamLb : 0.0;
+    lmRb = selL_from_L ? 0.0 : lamLb;
+    lpLb = selR_from_L ? lamRb : 0.0;
+    lpRb = selR_from_L ? 0.0 : lamRb;
+  };
+  double lmLb, lpLb, lmRb, lpRb;
   if (p.flux == 2) {
+    double FLb[5], FRb[5], ULb[5], URb[5];
+    double vLb = 0.0, PLb = 0.0, vRb = 0.0, PRb = 0.0;  // direct uses of v_D and P
     double vKb, PKb;
     bool left;
     hllc_flux_vjp<D>(L, R, lamL, lamR, Fsb, FLb, FRb, ULb, URb, lamLb, lamRb, vKb, PKb, left);
     (left ? vLb : vRb) = vKb;
     (left ? PLb : PRb) = PKb;
-  } else if (p.flux == 1) {
+    wavespeed_adjoints(lmLb, lpLb, lmRb, lpRb);
+    face_rev<D>(p, L, FLb, ULb, lmLb, lpLb, WLb, vLb, PLb);
+    face_rev<D>(p, R, FRb, URb, lmRb, lpRb, WRb, vRb, PRb);
+    return;
+  }
+  // LLF and HLL: F_L_bar = aL Fsb, U_L_bar = bL Fsb, and likewise on the right
+  double aL, bL, aR, bR;
+  if (p.flux == 1) {
     const bool actL = lamL < 0.0, actR = lamR > 0.0;
     const double sL = actL ? lamL : 0.0, sR = actR ? lamR : 0.0;
     const double den = sR - sL;
     if (den == 0.0) {
-#pragma unroll
-      for (int v = 0; v < 5; ++v) {
-        FLb[v] = FRb[v] = 0.5 * Fsb[v];
-        ULb[v] = URb[v] = 0.0;
-      }
+      aL = aR = 0.5;
+      bL = bR = 0.0;
     } else {
       // F* = (sR F_L - sL F_R + sL sR dU) / den, den = sR - sL, so
       // dF*/dsR = sL (dF - sL dU) / den^2 and dF*/dsL = -sR (dF - sR dU) / den^2
@@ -301,42 +339,38 @@ __device__ __forceinline__ void numerical_flux_vjp(const Params& p, const double
       // their operands were formed)
       const double id = recip_nr(den);
       const double sRid = sR * id, sLid = sL * id, sLsRid = sL * sRid;
-      double SA = 0.0, SB = 0.0;
+      double gF = 0.0, gU = 0.0;  // Fsb . dF and Fsb . dU
 #pragma unroll
       for (int v = 0; v < 5; ++v) {
-        const double dU = __dsub_rn(R.U[v], L.U[v]);
-        const double dF = __dsub_rn(R.F[v], L.F[v]);
-        SA = fma(Fsb[v], fma(-sL, dU, dF), SA);
-        SB = fma(Fsb[v], fma(-sR, dU, dF), SB);
-        FLb[v] = sRid * Fsb[v];
-        FRb[v] = -sLid * Fsb[v];
-        URb[v] = sLsRid * Fsb[v];
-        ULb[v] = -URb[v];
+        gF = fma(Fsb[v], __dsub_rn(R.F[v], L.F[v]), gF);
+        gU = fma(Fsb[v], __dsub_rn(R.U[v], L.U[v]), gU);
       }
-      const double sRb = sLid * id * SA, sLb = -sRid * id * SB;
+      aL = sRid;
+      bL = -sLsRid;
+      aR = -sLid;
+      bR = sLsRid;
+      const double sRb = sLid * id * fma(-sL, gU, gF), sLb = -sRid * id * fma(-sR, gU, gF);
       lamLb = actL ? sLb : 0.0;
       lamRb = actR ? sRb : 0.0;
     }
   } else {
     const bool useL = fabs(lamL) >= fabs(lamR);  // a = max(|lambda_L|, |lambda_R|)
     const double a = useL ? fabs(lamL) : fabs(lamR);
-    double ab = 0.0;
+    double gU = 0.0;
 #pragma unroll
-    for (int v = 0; v < 5; ++v) {
-      FLb[v] = FRb[v] = 0.5 * Fsb[v];
-      ULb[v] = 0.5 * a * Fsb[v];
-      URb[v] = -0.5 * a * Fsb[v];
-      ab -= 0.5 * Fsb[v] * __dsub_rn(R.U[v], L.U[v]);
-    }
+    for (int v = 0; v < 5; ++v) gU = fma(Fsb[v], __dsub_rn(R.U[v], L.U[v]), gU);
+    const double ab = -0.5 * gU;
+    aL = aR = 0.5;
+    bL = 0.5 * a;
+    bR = -0.5 * a;
     if (useL)
       lamLb = ab * (lamL >= 0.0 ? 1.0 : -1.0);
     else
       lamRb = ab * (lamR >= 0.0 ? 1.0 : -1.0);
   }
-  const double lmLb = selL_from_L ? lamLb : 0.0, lmRb = selL_from_L ? 0.0 : lamLb;
-  const double lpLb = selR_from_L ? lamRb : 0.0, lpRb = selR_from_L ? 0.0 : lamRb;
-  face_rev<D>(p, L, FLb, ULb, lmLb, lpLb, WLb, vLb, PLb);
-  face_rev<D>(p, R, FRb, URb, lmRb, lpRb, WRb, vRb, PRb);
+  wavespeed_adjoints(lmLb, lpLb, lmRb, lpRb);
+  face_rev_scaled<D>(p, L, Fsb, aL, bL, lmLb, lpLb, WLb);
+  face_rev_scaled<D>(p, R, Fsb, aR, bR, lmRb, lpRb, WRb);
 }
 
 // ---------------------------------------------------------------------------------------
