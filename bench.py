@@ -407,7 +407,8 @@ def reference_arm(args, rank, world):
 # ----------------------------------------------------------------------------------------
 # our arm
 # ----------------------------------------------------------------------------------------
-PROBE_KINDS = ("dfma", "ffma", "ddiv", "dsqrt", "drsqrt", "drcbrt", "recip", "sqrt", "rcbrt")
+PROBE_KINDS = ("dfma", "ffma", "ddiv", "dsqrt", "drsqrt", "drcbrt", "recip", "sqrt", "rcbrt",
+               "rsqrt")
 
 
 def measure_fp64_peak(dev, stream, clock_dir, local_rank, target_ms=150.0):

@@ -316,10 +316,11 @@ int32_t dgsrhd_mean_square_velocity(dgsrhd_ctx* ctx, const double* U, int32_t ax
 
 /* Diagnostic (no paper counterpart): the library's FP64 reciprocal and root primitives next to
  * CUDA's own, for checking the former against the latter.
- * x:   DEVICE, n doubles.  out: DEVICE, 6 n doubles, written as six blocks of n:
- *      [ reciprocal 1/x by Newton-Raphson refinement of an FP32 seed | 1.0 / x (division) |
- *        the library's sqrt(x) | sqrt(x) | the library's x^(-1/3) | rcbrt(x) ]
- *      (the last two are 0 at x = 0).
+ * x:   DEVICE, n doubles.  out: DEVICE, 8 n doubles, written as eight blocks of n:
+ *      [ reciprocal 1/x by a third-order correction of an FP32 seed | 1.0 / x (division) |
+ *        the library's sqrt(x) | sqrt(x) | the library's x^(-1/3) | rcbrt(x) |
+ *        the library's 1/sqrt(x) | rsqrt(x) ]
+ *      (the two cube-root blocks are 0 at x = 0).
  * stream: cudaStream_t or NULL for the default stream; the call only queues the kernel.
  * Returns DGSRHD_EINVAL for null pointers or n < 0, DGSRHD_ECUDA on a launch failure. */
 int32_t dgsrhd_math_check(const double* x, int64_t n, double* out, void* stream);
@@ -332,9 +333,9 @@ int32_t dgsrhd_math_check(const double* x, int64_t n, double* out, void* stream)
  *   DGSRHD_PROBE_DFMA    x <- fma(x, a, b) in FP64 (2 flops each: the FP64 peak)
  *   DGSRHD_PROBE_DDIV    x <- b / x (CUDA's FP64 division)
  *   DGSRHD_PROBE_DSQRT, DGSRHD_PROBE_DRSQRT, DGSRHD_PROBE_DRCBRT   CUDA's sqrt, rsqrt, rcbrt
- *   DGSRHD_PROBE_RECIP, DGSRHD_PROBE_SQRT, DGSRHD_PROBE_RCBRT
- *                        the library's reciprocal, square root and reciprocal cube root (FP32
- *                        seed, FP64 correction)
+ *   DGSRHD_PROBE_RECIP, DGSRHD_PROBE_SQRT, DGSRHD_PROBE_RCBRT, DGSRHD_PROBE_RSQRT
+ *                        the library's reciprocal, square root, reciprocal cube root and
+ *                        reciprocal square root (FP32 seed, FP64 correction)
  *   DGSRHD_PROBE_FFMA    x <- fmaf(x, a, b) in FP32.
  * sink: DEVICE, `threads` doubles (each thread stores its chains' sum).  *ops (nullable, HOST)
  * receives the number of operations, 4 threads iters; the caller times the kernel (CUDA events
@@ -349,7 +350,8 @@ int32_t dgsrhd_math_check(const double* x, int64_t n, double* out, void* stream)
 #define DGSRHD_PROBE_SQRT 6
 #define DGSRHD_PROBE_RCBRT 7
 #define DGSRHD_PROBE_FFMA 8
-#define DGSRHD_PROBE_KINDS 9
+#define DGSRHD_PROBE_RSQRT 9
+#define DGSRHD_PROBE_KINDS 10
 int32_t dgsrhd_arith_probe(int32_t kind, int64_t iters, double* sink, int64_t threads,
                            void* stream, int64_t* ops);
 

@@ -28,7 +28,7 @@ PRECISION = {"fp64": 0, "split": 1, "3xtf32": 1}
 NODES = {"gl": 0, "gll": 1}
 KERNEL_KINDS = ("volume", "face", "update", "enforce", "pointwise", "vjp")
 PROBE = {"dfma": 0, "ddiv": 1, "dsqrt": 2, "drsqrt": 3, "drcbrt": 4, "recip": 5, "sqrt": 6,
-         "rcbrt": 7, "ffma": 8}
+         "rcbrt": 7, "ffma": 8, "rsqrt": 9}
 
 
 class dgsrhd_config(ctypes.Structure):

@@ -85,20 +85,20 @@ __device__ __forceinline__ double ldexp_bits(double x) {
   return (b & 0x7ff0000000000000LL) == 0 ? x : __longlong_as_double(b + ((long long)K << 52));
 }
 
-// Reciprocal by the Newton-Raphson iteration r <- r + r (1 - x r), which squares the relative
-// error at every step (the classical iteration for division, e.g. P. Markstein, IBM J. Res.
-// Dev. 34 (1990) 111), from an FP32 seed: the seed is within ~2^-21, so two steps reach FP64
-// rounding (each step is two DFMAs, against the ~8.6 DFMA-equivalents of a division here).
-// For |x| outside [2^-100, 2^100] (where the FP32 seed would not be normal), and for zero,
-// infinity or NaN, the reciprocal is a true division.
+// Reciprocal from an FP32 seed r0 and one third-order correction: with h = 1 - x r0 (one fused
+// multiply-add), 1/x = r0 / (1 - h) = r0 (1 + h + h^2 + h^3 + ...), so r0 + r0 (h + h^2) leaves
+// a truncation error h^3.  The seed is within ~2^-21 (the FP32 truncation of x and MUFU's
+// reciprocal), so h^3 < 2^-63 and the result is within one rounding of 1/x: three FP64
+// instructions, where two Newton-Raphson steps r + r (1 - x r) (the classical iteration for
+// division, e.g. P. Markstein, IBM J. Res. Dev. 34 (1990) 111) take four and CUDA's division
+// about eight DFMA-equivalents.  For |x| outside [2^-100, 2^100] (where the FP32 seed would not
+// be normal), and for zero, infinity or NaN, the reciprocal is a true division.
 __device__ __forceinline__ double recip_nr(double x) {
   const int e = (__double2hiint(x) >> 20) & 0x7ff;
   if (e < 1023 - 100 || e > 1023 + 100) return 1.0 / x;
-  double r = f32_to_f64_bits(__fdividef(1.0f, f64_to_f32_bits(x)));
-  double t = fma(-x, r, 1.0);
-  r = fma(r, t, r);
-  t = fma(-x, r, 1.0);
-  return fma(r, t, r);
+  const double r0 = f32_to_f64_bits(__fdividef(1.0f, f64_to_f32_bits(x)));
+  const double h = fma(-x, r0, 1.0);
+  return fma(r0, fma(h, h, h), r0);
 }
 
 // Roots from an FP32 seed and one third-order correction.  The seed r0 ~ x^(-1/2) (MUFU's FP32
@@ -106,14 +106,23 @@ __device__ __forceinline__ double recip_nr(double x) {
 // 2^-20; with h = 1 - x r0^2 (resp. 1 - |x| r0^3), formed by one fused multiply-add, the
 // binomial series
 //   (1 - h)^(-1/2) = 1 + h/2 + 3h^2/8 + O(h^3),   (1 - h)^(-1/3) = 1 + h/3 + 2h^2/9 + O(h^3)
-// gives sqrt(x) = x r0 (1 - h)^(-1/2) and x^(-1/3) = r0 (1 - h)^(-1/3) with a truncation error
-// O(h^3) < 2^-60: the result is within about one ulp, from five or six FP64 instructions where
-// CUDA's sqrt and rcbrt take more (CUDA's rsqrt already costs about five, and is used as is).
+// gives x^(-1/2) = r0 (1 - h)^(-1/2), sqrt(x) = x r0 (1 - h)^(-1/2) and x^(-1/3) = r0 (1 - h)^(-1/3)
+// with a truncation error O(h^3) < 2^-60: the result is within about one ulp.  The second-order
+// term lies below 2^-40, so FP32 carries it to within 2^-62: it is formed from h truncated to
+// FP32 and added to the FP64 first-order term by one fused multiply-add.  That leaves four FP64
+// instructions for the square root and the reciprocal square root and five for the reciprocal
+// cube root, where CUDA's sqrt, rsqrt and rcbrt take about 7.5, 4.8 and 15 DFMA-equivalents.
 // Outside [2^-120, 2^120] (where the FP32 seed would not be a normal number), for zero, negative
-// (square root), infinite or NaN arguments, CUDA's own function is used.
+// (square roots), infinite or NaN arguments, CUDA's own function is used.
 __device__ __forceinline__ bool seed_range(double x) {
   const int e = (__double2hiint(x) >> 20) & 0x7ff;
   return e >= 1023 - 120 && e <= 1023 + 120;
+}
+
+// c h^2 for |h| < 2^-18, in FP32 (h truncated to FP32; zero once h^2 leaves the FP32-normal range)
+__device__ __forceinline__ double sq_term_f32(double h, float c) {
+  const float hf = f64_to_f32_bits(h);
+  return f32_to_f64_bits(c * hf * hf);
 }
 
 // sqrt(y) for y >= 0 (y itself for +-0, NaN for y < 0)
@@ -123,7 +132,16 @@ __device__ __forceinline__ double sqrt_nr(double y) {
   const double r0 = f32_to_f64_bits(rsqrtf(f64_to_f32_bits(y)));
   const double s0 = y * r0;
   const double h = fma(-s0, r0, 1.0);
-  return fma(s0, h * fma(h, 0.375, 0.5), s0);
+  return fma(s0, fma(h, 0.5, sq_term_f32(h, 0.375f)), s0);
+}
+
+// 1/sqrt(y), with CUDA's rsqrt semantics outside the seed range (+inf at +0, -inf at -0, NaN
+// below zero, 0 at +inf)
+__device__ __forceinline__ double rsqrt_nr(double y) {
+  if (__double2hiint(y) < 0 || !seed_range(y)) return rsqrt(y);
+  const double r0 = f32_to_f64_bits(rsqrtf(f64_to_f32_bits(y)));
+  const double h = fma(-(y * r0), r0, 1.0);
+  return fma(r0, fma(h, 0.5, sq_term_f32(h, 0.375f)), r0);
 }
 
 // y^(-1/3) with the sign of y (y != 0).  FP32 seed: the bit pattern of |y|^(-1/3) is about
@@ -139,7 +157,7 @@ __device__ __forceinline__ double rcbrt_nr(double y) {
   for (int k = 0; k < 3; ++k) r = r * (4.0f - (a * r) * (r * r)) * (1.0f / 3.0f);
   const double r0 = f32_to_f64_bits(r);
   const double h = fma(-(ay * r0), r0 * r0, 1.0);
-  const double q = fma(r0, h * fma(h, 2.0 / 9.0, 1.0 / 3.0), r0);
+  const double q = fma(r0, fma(h, 1.0 / 3.0, sq_term_f32(h, 2.0f / 9.0f)), r0);
   return __longlong_as_double(__double_as_longlong(q) | sign);
 }
 

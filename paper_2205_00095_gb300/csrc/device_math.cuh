@@ -249,8 +249,8 @@ __device__ __forceinline__ double W_tm_closed_form(double xi, double eta) {
   const double d = Q * Q * Q + R * R;
   double W;
   if (d < 0.0) {
-    // (d < 0 implies Q < 0) sqrt(-Q^3) and sqrt(-Q) from one rsqrt(-Q)
-    const double rq = rsqrt(-Q);
+    // (d < 0 implies Q < 0) sqrt(-Q^3) and sqrt(-Q) from one reciprocal square root of -Q
+    const double rq = rsqrt_nr(-Q);
     const double iota = acos(R * rq * rq * rq);
     W = 2.0 * (-Q) * rq * cos(iota * (1.0 / 3.0)) - c.c1 * (1.0 / 3.0);
   } else {
@@ -462,7 +462,7 @@ __device__ __forceinline__ int con2prim(const Params& p, const double U[5], Prim
     return 1;
   }
   const bool moving = dbits(S2) != 0;  // S2 > 0 (S2 is finite and >= 0 here)
-  const double rS = moving ? rsqrt(S2) : 0.0;  // 1/|S|
+  const double rS = moving ? rsqrt_nr(S2) : 0.0;  // 1/|S|
   const double S = S2 * rS;
   const bool closed_ideal = p.eos == 0 && p.c2p == 0;
   // beta = |v|, ginv = 1/gamma, omg = 1 - 1/gamma (cancellation-free per method)
@@ -479,7 +479,7 @@ __device__ __forceinline__ int con2prim(const Params& p, const double U[5], Prim
     // gamma = (1 - beta^2)^(-1/2); 1 - 1/gamma = beta^2 gamma / (gamma + 1)
     const double b2 = beta * beta;
     const double om = 1.0 - b2;
-    lor = rsqrt(om);
+    lor = rsqrt_nr(om);
     ginv = om * lor;
     omg = b2 * recip_nr(1.0 + ginv);  // = b2 gamma / (gamma + 1)
   } else {
@@ -503,7 +503,7 @@ __device__ __forceinline__ int con2prim(const Params& p, const double U[5], Prim
                         : W_tm_brent(xi, eta, p.max_iter, p.c2p_rtol, iters, conv);
       conv = conv && dbits(Wl) >= 0 && finite_bits(Wl);  // Wl >= 0 and finite
       const double q = Wl + 1.0;  // gamma^2
-      ginv = rsqrt(q);
+      ginv = rsqrt_nr(q);
       lor = q * ginv;
       beta = sqrt_nr(Wl) * ginv;
     }
@@ -567,7 +567,8 @@ struct FaceState {
 };
 
 // Face state from (rho, u, P).  The three reciprocals 1/Z, 1/(gamma + 1) and 1/(A + B) come
-// from one division of their product, and the roots from rsqrt (the root itself is x rsqrt(x)).
+// from one division of their product, and the roots from the reciprocal square root rsqrt_nr
+// (the root itself is x rsqrt_nr(x)).
 // With `rec` given, the roots and reciprocals are read from it instead (values saved by an
 // earlier evaluation on the same state), and no root or division is evaluated.
 __device__ __forceinline__ void face_state_core(const Params& p, const double Wu[5], FaceState& c,
@@ -578,7 +579,7 @@ __device__ __forceinline__ void face_state_core(const Params& p, const double Wu
   const double rho = Wu[0], P = Wu[4];
   c.u2 = fma(Wu[1], Wu[1], fma(Wu[2], Wu[2], Wu[3] * Wu[3]));
   c.q = __dadd_rn(1.0, c.u2);  // gamma^2
-  c.ilor = rec ? rec[0] : rsqrt(c.q);
+  c.ilor = rec ? rec[0] : rsqrt_nr(c.q);
   c.lor = c.q * c.ilor;
   c.P = P;
   if (p.eos == 0) {
@@ -588,7 +589,7 @@ __device__ __forceinline__ void face_state_core(const Params& p, const double Wu
   } else {
     const double rho2 = rho * rho;
     const double x2 = fma(P, P, (4.0 / 9.0) * rho2);
-    c.isg = rec ? rec[1] : rsqrt(x2);
+    c.isg = rec ? rec[1] : rsqrt_nr(x2);
     c.sg = x2 * c.isg;
     c.Z = fma(2.0 / 3.0, rho, c.sg);
     c.A = P * fma(3.0, P, 5.0 * c.sg);
@@ -638,7 +639,7 @@ __device__ __forceinline__ void wave_root(const FaceState& c, double& X, double&
                                           const double* ir_saved) {
   const double vd = c.v[D];
   X = c.A * fma(c.B, fma(-vd, vd, 1.0), c.A);
-  ir = ir_saved ? *ir_saved : (pos_bits(X) ? rsqrt(X) : 0.0);
+  ir = ir_saved ? *ir_saved : (pos_bits(X) ? rsqrt_nr(X) : 0.0);
   r = X * ir;
 }
 
@@ -722,19 +723,22 @@ __device__ __forceinline__ void hllc_flux(const FaceState& L, const FaceState& R
   for (int k = 0; k < 5; ++k) Fs[k] = fma(lam, Us[k] - UK[k], FK[k]);
 }
 
-// wL F_L + wR F_R + c (U_R - U_L) along D from the two face states, with the normal fluxes
-// (U v_d; S_D v_d + P; (tau + P) v_d) folded into the weights rather than formed first.
+// wL F_L + wR F_R + c (U_R - U_L) along D from the two face states.  With the normal fluxes
+// F = (U v_d; S_D v_d + P; (tau + P) v_d) every conserved component regroups per side as
+// U_L (wL v_L - c) + U_R (wR v_R + c), plus the pressure terms wL P_L + wR P_R (momentum along
+// D) and wL P_L v_L + wR P_R v_R (energy): two fused multiply-adds per component, with the
+// side weights bL = wL v_L - c and bR = wR v_R + c formed once.
 template <int D>
 __device__ __forceinline__ void flux_mix(const FaceState& L, const FaceState& R, double wL,
                                          double wR, double c, double out[5]) {
   const double aL = wL * L.v[D], aR = wR * R.v[D];
+  const double bL = aL - c, bR = aR + c;
+  const double pp = fma(wL, L.P, wR * R.P);
+  const double pv = fma(aL, L.P, aR * R.P);
 #pragma unroll
-  for (int k = 0; k < 4; ++k) {
-    const double t = c * (R.U[k] - L.U[k]);
-    out[k] = (k == 1 + D) ? fma(L.U[k], aL, fma(R.U[k], aR, fma(wL, L.P, fma(wR, R.P, t))))
-                          : fma(L.U[k], aL, fma(R.U[k], aR, t));
-  }
-  out[4] = fma(L.U[4] + L.P, aL, fma(R.U[4] + R.P, aR, c * (R.U[4] - L.U[4])));
+  for (int k = 0; k < 4; ++k)
+    out[k] = fma(L.U[k], bL, (k == 1 + D) ? fma(R.U[k], bR, pp) : R.U[k] * bR);
+  out[4] = fma(L.U[4], bL, fma(R.U[4], bR, pv));
 }
 
 // Numerical flux along axis D between face states given as (rho, u, P), returned DOUBLED (2 F*:
@@ -822,7 +826,7 @@ __device__ __forceinline__ void c2p_adjoint(const Params& p, double rho, const d
     w_P = p.alpha;
   } else {
     const double x2 = fma(P, P, (4.0 / 9.0) * rho * rho);
-    const double isg = rsqrt(x2);
+    const double isg = rsqrt_nr(x2);
     const double sg = x2 * isg;
     w = fma(2.5, P, 1.5 * sg);
     w_r = (2.0 / 3.0) * rho * isg;

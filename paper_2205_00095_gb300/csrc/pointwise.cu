@@ -130,6 +130,8 @@ __global__ void __launch_bounds__(256) math_check_kernel(long long n, const doub
     out[3 * n + k] = sqrt(v);
     out[4 * n + k] = v == 0.0 ? 0.0 : rcbrt_nr(v);
     out[5 * n + k] = v == 0.0 ? 0.0 : rcbrt(v);
+    out[6 * n + k] = rsqrt_nr(v);
+    out[7 * n + k] = rsqrt(v);
   }
 }
 
@@ -138,7 +140,7 @@ __global__ void __launch_bounds__(256) math_check_kernel(long long n, const doub
 // operation's pipe busy; the chains' sum is stored so that none is removed.  kind: 0 FP64 FMA
 // x <- fma(x, a, b); 1 FP64 division x <- b / x; 2 sqrt; 3 rsqrt; 4 rcbrt; the library's
 // 5 reciprocal (recip_nr), 6 square root (sqrt_nr), 7 reciprocal cube root (rcbrt_nr); 8 FP32
-// FMA.  a and b are kernel arguments (not constants
+// FMA; 9 the library's reciprocal square root (rsqrt_nr).  a and b are kernel arguments (not constants
 // the compiler could fold); every chain stays bounded.
 template <int KIND>
 __device__ __forceinline__ double probe_op(double x, double a, double b) {
@@ -149,6 +151,7 @@ __device__ __forceinline__ double probe_op(double x, double a, double b) {
   if (KIND == 4) return rcbrt(x);
   if (KIND == 5) return recip_nr(x);
   if (KIND == 6) return sqrt_nr(x);
+  if (KIND == 9) return rsqrt_nr(x);
   return rcbrt_nr(x);
 }
 
@@ -193,6 +196,7 @@ cudaError_t launch_fp64_probe(cudaStream_t s, int kind, long long iters, long lo
     case 6: fp64_probe_kernel<6><<<blocks, 256, 0, s>>>(iters, a, b, sink); break;
     case 7: fp64_probe_kernel<7><<<blocks, 256, 0, s>>>(iters, a, b, sink); break;
     case 8: fp32_probe_kernel<<<blocks, 256, 0, s>>>(iters, 0.999999f, 1e-6f, sink); break;
+    case 9: fp64_probe_kernel<9><<<blocks, 256, 0, s>>>(iters, a, b, sink); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();

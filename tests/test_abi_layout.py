@@ -117,7 +117,7 @@ def test_binding_codes_match_the_header(c_layout):
                   "dsqrt": "DGSRHD_PROBE_DSQRT", "drsqrt": "DGSRHD_PROBE_DRSQRT",
                   "drcbrt": "DGSRHD_PROBE_DRCBRT", "recip": "DGSRHD_PROBE_RECIP",
                   "sqrt": "DGSRHD_PROBE_SQRT", "rcbrt": "DGSRHD_PROBE_RCBRT",
-                  "ffma": "DGSRHD_PROBE_FFMA"},
+                  "ffma": "DGSRHD_PROBE_FFMA", "rsqrt": "DGSRHD_PROBE_RSQRT"},
     }
     for group, names in groups.items():
         table = getattr(_lib, group)

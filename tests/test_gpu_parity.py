@@ -524,8 +524,8 @@ def test_con2prim_zero_and_tiny_momentum(lib, eos, c2p):
 
 
 # ---------------------------------------------------------------------------------------
-# the library's FP64 reciprocal (Newton-Raphson from an FP32 seed) and roots (FP32 seed and one
-# third-order correction) against CUDA's division, sqrt, rsqrt and rcbrt
+# the library's FP64 reciprocal and roots (FP32 seed and one third-order correction) against
+# CUDA's division, sqrt, rsqrt and rcbrt
 # ---------------------------------------------------------------------------------------
 def test_reciprocal_and_sqrt_primitives_against_cuda(lib):
     from paper_2205_00095_gb300 import _lib
@@ -535,10 +535,10 @@ def test_reciprocal_and_sqrt_primitives_against_cuda(lib):
                      np.ldexp(1.5, -101), np.ldexp(1.5, 101), 5e-324, 2.2e-308, 1.7e308])
     x = np.concatenate([mags, -mags[:1000], edge, -edge, [0.0, -0.0, np.inf, -np.inf, np.nan]])
     xd = to_dev(x)
-    out = torch.empty(6 * x.size, dtype=torch.float64, device="cuda")
+    out = torch.empty(8 * x.size, dtype=torch.float64, device="cuda")
     assert lib.dgsrhd_math_check(xd.data_ptr(), x.size, out.data_ptr(), None) == 0
     torch.cuda.synchronize()
-    o = out.cpu().numpy().reshape(6, x.size)
+    o = out.cpu().numpy().reshape(8, x.size)
 
     def ulps(a, b):
         ia, ib = a.view(np.int64), b.view(np.int64)
@@ -559,6 +559,15 @@ def test_reciprocal_and_sqrt_primitives_against_cuda(lib):
     ref = (1.0 / np.cbrt(x[nz].astype(np.longdouble))).astype(np.float64)
     assert ulps(o[4][nz], ref).max() <= 2
     assert np.array_equal(np.signbit(o[4][nz]), np.signbit(x[nz]))
+    # reciprocal square root: within 2 ulp of CUDA's and of 1/sqrt(x) in extended precision;
+    # CUDA's values (infinities, NaN, zero) at +-0, x < 0, +inf and NaN
+    ref = (1.0 / np.sqrt(x[pos].astype(np.longdouble))).astype(np.float64)
+    assert ulps(o[6][pos], o[7][pos]).max() <= 2
+    assert ulps(o[6][pos], ref).max() <= 2
+    rest = ~pos
+    assert np.array_equal(np.isnan(o[6][rest]), np.isnan(o[7][rest]))
+    keep = rest & ~np.isnan(o[7])
+    assert np.array_equal(o[6][keep], o[7][keep])
     assert lib.dgsrhd_math_check(None, 1, out.data_ptr(), None) == _lib.DGSRHD_EINVAL
     assert lib.dgsrhd_math_check(xd.data_ptr(), -1, out.data_ptr(), None) == _lib.DGSRHD_EINVAL
 

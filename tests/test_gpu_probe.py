@@ -51,11 +51,12 @@ def test_library_primitives_beat_cuda_division_and_sqrt(gpu_lib):
     sms = torch.cuda.get_device_properties(0).multi_processor_count
     sink = torch.empty(sms * 8 * 256, dtype=torch.float64, device="cuda")
     r = {k: _rate(k, 2000, sink, stream)[0]
-         for k in ("dfma", "ddiv", "recip", "dsqrt", "sqrt", "drcbrt", "rcbrt")}
+         for k in ("dfma", "ddiv", "recip", "dsqrt", "sqrt", "drsqrt", "rsqrt", "drcbrt", "rcbrt")}
     cost = {k: r["dfma"] / v for k, v in r.items()}
     print("\nDFMA-equivalents:", {k: round(v, 2) for k, v in cost.items()},
           f"DFMA {2 * r['dfma'] / 1e12:.3f} TFLOP/s")
     assert cost["recip"] < cost["ddiv"]
     assert cost["sqrt"] < cost["dsqrt"]
     assert cost["rcbrt"] < cost["drcbrt"]
+    assert cost["rsqrt"] < cost["drsqrt"]
     assert np.isfinite(list(cost.values())).all()
