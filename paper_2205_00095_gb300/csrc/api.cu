@@ -214,13 +214,15 @@ cudaError_t run_stage(dgsrhd_ctx* c, StageArgs& a) {
   return e;
 }
 
-// R_vol and face traces, then face fluxes (the first two kernels of every RHS)
-cudaError_t volume_and_faces(dgsrhd_ctx* c, const double* U) {
+// R_vol and face traces, then face fluxes (the first two kernels of every RHS); rscale as in
+// StageArgs (nonzero only when the update that follows is a stage given the same scale)
+cudaError_t volume_and_faces(dgsrhd_ctx* c, const double* U, double rscale = 0.0) {
   StageArgs a{};
   a.op = Op::Volume;
   a.U = U;
   a.Rvol = c->Rv;
   a.Tr = c->Tr;
+  a.rscale = rscale;
   cudaError_t e = run_stage(c, a);
   if (e != cudaSuccess) return e;
   c->c2p_calls += c->E * c->Nn;
@@ -259,7 +261,8 @@ cudaError_t one_step(dgsrhd_ctx* c, double* U, double dt) {
   for (int k = 0; k < ns; ++k) {
     const double* Uin = (k == 0) ? U : c->A;
     double* Uout = (k == ns - 1) ? U : c->A;
-    cudaError_t e = volume_and_faces(c, Uin);
+    const double rscale = kBk[ns - 1][k] * dt;  // b_k dt, folded into R_vol and the lift
+    cudaError_t e = volume_and_faces(c, Uin, rscale);
     if (e != cudaSuccess) return e;
     StageArgs u{};
     u.op = Op::Update;
@@ -271,6 +274,7 @@ cudaError_t one_step(dgsrhd_ctx* c, double* U, double dt) {
     u.a_n = kAn[ns - 1][k];
     u.b_k = kBk[ns - 1][k];
     u.dt = dt;
+    u.rscale = rscale;
     u.mode = 1;
     u.enforce = c->cfg.enforce && !c->cfg.limiter;
     e = run_stage(c, u);
@@ -288,12 +292,14 @@ cudaError_t one_step(dgsrhd_ctx* c, double* U, double dt) {
 cudaError_t one_step_host(dgsrhd_ctx* c, double* Uh, double dt) {
   const int ns = c->cfg.rk_stages;
   for (int k = 0; k < ns; ++k) {
+    const double rscale = kBk[ns - 1][k] * dt;  // b_k dt, folded into R_vol and the lift
     StageArgs a{};
     a.op = Op::Volume;
     a.U = (k == 0) ? Uh : c->A;
     a.Rvol = c->Rv;
     a.Tr = c->Tr;
     a.Ucopy = (k == 0) ? c->Ud : nullptr;
+    a.rscale = rscale;
     cudaError_t e = run_stage(c, a);
     if (e != cudaSuccess) return e;
     c->c2p_calls += c->E * c->Nn;
@@ -312,6 +318,7 @@ cudaError_t one_step_host(dgsrhd_ctx* c, double* Uh, double dt) {
     u.a_n = kAn[ns - 1][k];
     u.b_k = kBk[ns - 1][k];
     u.dt = dt;
+    u.rscale = rscale;
     u.mode = 1;
     u.enforce = c->cfg.enforce;
     if ((e = run_stage(c, u)) != cudaSuccess) return e;
@@ -801,6 +808,7 @@ int32_t dgsrhd_step_stage(dgsrhd_ctx* c, const double* Un, const double* Uk, dou
   v.Tr = save ? sv.Tr : c->Tr;
   v.Wstore = sv.W;
   v.guard = sv.guard;
+  v.rscale = kBk[ns - 1][stage] * dt;  // b_k dt, as in a step
   if (save) v.fp64_only = 1;  // the saved quantities feed the FP64 reverse sweep
   if (run_stage(c, v) != cudaSuccess) return DGSRHD_ECUDA;
   c->c2p_calls += c->E * c->Nn;
@@ -822,6 +830,7 @@ int32_t dgsrhd_step_stage(dgsrhd_ctx* c, const double* Un, const double* Uk, dou
   u.a_n = kAn[ns - 1][stage];
   u.b_k = kBk[ns - 1][stage];
   u.dt = dt;
+  u.rscale = v.rscale;
   u.mode = 1;
   u.enforce = c->cfg.enforce && !c->cfg.limiter;
   u.s_out = s_out;

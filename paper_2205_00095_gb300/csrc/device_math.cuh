@@ -95,8 +95,38 @@ __device__ __forceinline__ bool admissible_parts(double D, double S2, double tau
          dbits(tau * (tau + 2.0 * D)) > s2;
 }
 
+// The same decision as admissible_parts, screened in FP32 first.  With D, tau and S2 truncated
+// to FP32 (relative error below 2^-23) and three FP32 operations, tau (tau + 2D) comes out within
+// a relative 2^-21 of its exact value and S2 within 2^-23 of the FP64 one, so
+// tau (tau + 2D) > S2 (1 + 2^-14) in FP32, with D, tau > 0 and tau (tau + 2D) inside
+// [2^-100, 1e38] (clear of FP32 underflow and overflow), implies the FP64 test by a wide margin.
+// Every other state, including NaN and infinite ones, takes the FP64 test.
+__device__ __forceinline__ bool admissible_parts_screen(double D, double S2, double tau) {
+  const float Df = f64_to_f32_bits(D), tf = f64_to_f32_bits(tau), sf = f64_to_f32_bits(S2);
+  const float lhs = tf * (tf + 2.0f * Df);
+  if (Df > 0.0f && tf > 0.0f && lhs >= 0x1p-100f && lhs <= 1e38f && lhs > sf * (1.0f + 0x1p-14f))
+    return true;
+  return admissible_parts(D, S2, tau);
+}
+
 __device__ __forceinline__ bool admissible(const double U[5]) {
   return admissible_parts(U[0], U[1] * U[1] + U[2] * U[2] + U[3] * U[3], U[4]);
+}
+
+// The same decision as admissible(U), screened in FP32 first: with every input truncated to FP32
+// (relative error below 2^-23) and five FP32 operations, tau (tau + 2D) and |S|^2 come out within
+// a relative 2^-20 of their exact values, so tau (tau + 2D) > |S|^2 (1 + 2^-14) in FP32, with
+// D, tau > 0 and tau (tau + 2D) inside [2^-100, 1e38] (clear of FP32 underflow and overflow),
+// implies the exact inequality by a wide margin and hence the FP64 test.  Every other state,
+// including NaN and infinite ones, takes the FP64 test, so the result never differs from it.
+__device__ __forceinline__ bool admissible_screen(const double U[5]) {
+  const float D = f64_to_f32_bits(U[0]), tau = f64_to_f32_bits(U[4]);
+  const float s1 = f64_to_f32_bits(U[1]), s2 = f64_to_f32_bits(U[2]), s3 = f64_to_f32_bits(U[3]);
+  const float lhs = tau * (tau + 2.0f * D);
+  const float S2 = fmaf(s1, s1, fmaf(s2, s2, s3 * s3));
+  if (D > 0.0f && tau > 0.0f && lhs >= 0x1p-100f && lhs <= 1e38f && lhs > S2 * (1.0f + 0x1p-14f))
+    return true;
+  return admissible(U);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -457,7 +487,7 @@ __device__ __forceinline__ int con2prim(const Params& p, const double U[5], Prim
   const double S2 = U[1] * U[1] + U[2] * U[2] + U[3] * U[3];
   iters = 0;
   const double nanv = __longlong_as_double(0x7ff8000000000000LL);
-  if (!admissible_parts(D, S2, tau) || !finite_bits(S2) || !finite_bits(tau)) {
+  if (!admissible_parts_screen(D, S2, tau) || !finite_bits(S2) || !finite_bits(tau)) {
     W.rho = W.v[0] = W.v[1] = W.v[2] = W.P = W.lor = nanv;
     return 1;
   }

@@ -127,15 +127,19 @@ template <int DIM, int N>
 __global__ void __launch_bounds__(Shape<DIM, N>::BLOCK)
     volume_kernel(Params p, const double* __restrict__ U, double* __restrict__ Rvol,
                   double* __restrict__ Tr, double* __restrict__ Wout,
-                  unsigned char* __restrict__ guard_out, double* __restrict__ Ucopy) {
+                  unsigned char* __restrict__ guard_out, double* __restrict__ Ucopy,
+                  double rscale) {
   using S = Shape<DIM, N>;
   constexpr int Nn = S::Nn, Nt = S::Nt, BLOCK = S::BLOCK;
   __shared__ double shF[DIM][5][BLOCK];
   __shared__ double shW[5][BLOCK];
-  __shared__ double shD[DIM][N * N];  // (2/dx_d) Dhat per axis
+  __shared__ double shD[DIM][N * N];  // (2/dx_d) Dhat per axis, times rscale when it is nonzero
   __shared__ int shred[4 * 32];
   const int tid = threadIdx.x;
-  if (tid < DIM * N * N) shD[tid / (N * N)][tid % (N * N)] = p.inv_half_dx[tid / (N * N)] * p.Dhat[tid % (N * N)];
+  if (tid < DIM * N * N) {
+    const double c = p.inv_half_dx[tid / (N * N)] * p.Dhat[tid % (N * N)];
+    shD[tid / (N * N)][tid % (N * N)] = rscale != 0.0 ? c * rscale : c;
+  }
   const int le = tid / Nn, li = tid - le * Nn;
   const long long e = (long long)blockIdx.x * S::EPB + le;
   const bool valid = e < p.E;
@@ -395,7 +399,7 @@ __device__ __forceinline__ void enforce_block(const Params& p, double u[5], bool
                                               EnforceShared<DIM, N, BLOCKSZ>& sh) {
   constexpr int Nn = Shape<DIM, N>::Nn, NFP = Shape<DIM, N>::NFP;
   const int tid = threadIdx.x;
-  bool bad = valid && !admissible(u);
+  bool bad = valid && !admissible_screen(u);
   if (FACES) {
 #pragma unroll
     for (int v = 0; v < 5; ++v) sh.u[v][tid] = valid ? u[v] : 0.0;
@@ -404,7 +408,7 @@ __device__ __forceinline__ void enforce_block(const Params& p, double u[5], bool
       for (int fp = li; fp < NFP; fp += Nn) {
         double X[5];
         face_point_state<DIM, N, BLOCKSZ>(p, sh.u, le, fp, X);
-        if (!admissible(X)) bad = true;
+        if (!admissible_screen(X)) bad = true;
       }
     }
   }
@@ -469,24 +473,28 @@ __device__ __forceinline__ void enforce_block(const Params& p, double u[5], bool
 
 // ---------------------------------------------------------------------------------------
 // Update kernel: R = R_vol - lift; mode 0 writes R, mode 1 writes the RK stage
-// Uout = a_n Un + b_k (Uk + dt R) followed (if enforce) by the physicality operator.
+// Uout = a_n Un + b_k (Uk + dt R) followed (if enforce) by the physicality operator.  With
+// rscale nonzero (mode 1 only), R_vol arrives times rscale = b_k dt and the lift is scaled the
+// same way, so the stage is a_n Un + b_k Uk + R: one fused multiply-add per variable fewer.
 // Uout may alias Uk or Un (each thread reads its own node before the block writes).
 // ---------------------------------------------------------------------------------------
 template <int DIM, int N, bool FACES>
 __global__ void __launch_bounds__(Shape<DIM, N>::BLOCK)
     update_kernel(Params p, const double* __restrict__ Rvol, const double* __restrict__ Fs,
                   const double* Un, const double* Uk, double* Uout, double a_n, double b_k,
-                  double dt, int mode, int enforce, double* __restrict__ s_out) {
+                  double dt, int mode, int enforce, double* __restrict__ s_out, double rscale) {
   using S = Shape<DIM, N>;
   constexpr int Nn = S::Nn;
   __shared__ EnforceShared<DIM, N> sh;
-  // (2/dx_d) phi_i(-+1)/w_i per axis, halved: the face kernel stores 2 F*
+  // (2/dx_d) phi_i(-+1)/w_i per axis, halved (the face kernel stores 2 F*), times rscale when
+  // it is nonzero
   __shared__ double shl[DIM][2][N];
   const int tid = threadIdx.x;
   if (tid < DIM * N) {
     const int d = tid / N, i = tid % N;
-    shl[d][0][i] = 0.5 * p.inv_half_dx[d] * p.lm[i];
-    shl[d][1][i] = 0.5 * p.inv_half_dx[d] * p.lp[i];
+    const double cm = 0.5 * p.inv_half_dx[d] * p.lm[i], cp = 0.5 * p.inv_half_dx[d] * p.lp[i];
+    shl[d][0][i] = rscale != 0.0 ? cm * rscale : cm;
+    shl[d][1][i] = rscale != 0.0 ? cp * rscale : cp;
   }
   __syncthreads();
   const int le = tid / Nn, li = tid - le * Nn;
@@ -519,6 +527,17 @@ __global__ void __launch_bounds__(Shape<DIM, N>::BLOCK)
     if (mode == 0) {
 #pragma unroll
       for (int v = 0; v < 5; ++v) Uout[v * tot + g] = R[v];
+    } else if (rscale != 0.0) {  // R = b_k dt (R_vol - lift); the branches are uniform
+      if (a_n != 0.0) {
+#pragma unroll
+        for (int v = 0; v < 5; ++v) u[v] = fma(a_n, Un[v * tot + g], fma(b_k, Uk[v * tot + g], R[v]));
+      } else if (b_k == 1.0) {
+#pragma unroll
+        for (int v = 0; v < 5; ++v) u[v] = Uk[v * tot + g] + R[v];
+      } else {
+#pragma unroll
+        for (int v = 0; v < 5; ++v) u[v] = fma(b_k, Uk[v * tot + g], R[v]);
+      }
     } else {
 #pragma unroll
       for (int v = 0; v < 5; ++v) {
@@ -791,7 +810,7 @@ static cudaError_t launch_stage_kernels(const StageArgs& a) {
   switch (a.op) {
     case Op::Volume:
       volume_kernel<DIM, N><<<eblocks, S::BLOCK, 0, a.stream>>>(p, a.U, a.Rvol, a.Tr, a.Wstore,
-                                                                 a.guard, a.Ucopy);
+                                                                 a.guard, a.Ucopy, a.rscale);
       break;
     case Op::Face: {
       long long mx = 0;
@@ -808,7 +827,8 @@ static cudaError_t launch_stage_kernels(const StageArgs& a) {
     case Op::Update: {
       auto kern = p.enforce_faces ? update_kernel<DIM, N, true> : update_kernel<DIM, N, false>;
       kern<<<eblocks, S::BLOCK, 0, a.stream>>>(p, a.Rvol, a.Fs, a.Un, a.Uk, a.Uout, a.a_n, a.b_k,
-                                               a.dt, a.mode, a.enforce, a.s_out);
+                                               a.dt, a.mode, a.enforce, a.s_out,
+                                               a.mode == 1 ? a.rscale : 0.0);
       break;
     }
     case Op::Enforce:

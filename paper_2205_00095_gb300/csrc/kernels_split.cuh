@@ -306,12 +306,16 @@ __global__ void __launch_bounds__(Shape<DIM, N>::BLOCK, FACES ? 3 : 5)
     if (mode == 0) {
 #pragma unroll
       for (int v = 0; v < 5; ++v) Uout[v * tot + g] = R[v];
+    } else if (a_n != 0.0) {  // the branches are uniform: no b_k x is formed where b_k = 1
+#pragma unroll
+      for (int v = 0; v < 5; ++v)
+        u[v] = fma(a_n, Un[v * tot + g], b_k * fma(dt, R[v], Uk[v * tot + g]));
+    } else if (b_k == 1.0) {
+#pragma unroll
+      for (int v = 0; v < 5; ++v) u[v] = fma(dt, R[v], Uk[v * tot + g]);
     } else {
 #pragma unroll
-      for (int v = 0; v < 5; ++v) {
-        const double x = fma(dt, R[v], Uk[v * tot + g]);
-        u[v] = (a_n != 0.0) ? fma(a_n, Un[v * tot + g], b_k * x) : (b_k == 1.0 ? x : b_k * x);
-      }
+      for (int v = 0; v < 5; ++v) u[v] = b_k * fma(dt, R[v], Uk[v * tot + g]);
     }
   }
   if (mode == 0) return;  // uniform over the grid

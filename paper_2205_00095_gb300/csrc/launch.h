@@ -22,6 +22,9 @@ struct StageArgs {
   const double* Uk;    // Update: U^(k-1)
   double* Uout;        // Update: output; Enforce: state in place
   double a_n, b_k, dt;
+  // Volume / Update, FP64 kernels: when nonzero, R_vol and the lift are formed times rscale
+  // (the stage's b_k dt), and the update forms a_n U^n + b_k U^(k-1) + rscale R; 0 = unscaled
+  double rscale;
   int mode;            // Update: 0 = write R, 1 = RK stage
   int enforce;
   int split;           // Volume / Update: split-precision tensor-core contractions (set by the host)
