@@ -1,8 +1,9 @@
 // Split-precision variants of the volume and update kernels.  The volume term and the
 // face-trace extrapolation run on tensor cores (3xTF32, FP32 accumulation, see split.cuh); the
-// lift, a rank-2 update per line, runs as FP32 FMAs.  con2prim, the nodal and numerical
-// fluxes, the Lorentz factors, the RK combination, the element means and the physicality
-// operator stay in FP64.
+// lift, a rank-2 update per line, runs as FP32 FMAs.  The nodal flux, which enters only the
+// volume contraction, is formed as FP32 head-and-tail pairs from those of U, v and P (within
+// about 2^-46 of the FP64 flux).  con2prim, the numerical flux, the Lorentz factors, the RK
+// combination, the element means and the physicality operator stay in FP64.
 //
 // The contractions act on deviations from a per-element reference (the values at the element's
 // first node).  The DG operator annihilates constants (summation by parts:
@@ -30,6 +31,9 @@ struct SplitShape {
   static constexpr int WARPS = BLOCK / 32;
   static constexpr int LINES = S::EPB * S::Nt;              // lines per axis in a block
   static constexpr int TILES = (LINES + 15) / 16;           // 16-line row tiles
+  // resident blocks per SM asked of the register allocator for the volume kernel: its shared
+  // memory admits at least three 256-thread blocks, which 85 registers per thread keep
+  static constexpr int VOL_MIN_BLOCKS = 3;
 };
 
 // Byte offsets of the dynamic shared memory of the split volume kernel.
@@ -97,7 +101,7 @@ __device__ __forceinline__ void contract_tile(const uint2* __restrict__ src, con
 }
 
 template <int DIM, int N>
-__global__ void __launch_bounds__(SplitShape<DIM, N>::BLOCK)
+__global__ void __launch_bounds__(SplitShape<DIM, N>::BLOCK, SplitShape<DIM, N>::VOL_MIN_BLOCKS)
     volume_kernel_split(Params p, const double* __restrict__ U, float* __restrict__ Rvol,
                         double* __restrict__ Tr, float2* __restrict__ Fref) {
   using S = Shape<DIM, N>;
@@ -135,34 +139,53 @@ __global__ void __launch_bounds__(SplitShape<DIM, N>::BLOCK)
   const long long g = e * Nn + li;
 
   int iters = 0, status = 0;
-  double F[DIM][5], Wu[5];
   if (valid) {
     double u[5];
 #pragma unroll
     for (int v = 0; v < 5; ++v) u[v] = U[v * tot + g];
     Prim W;
     status = con2prim(p, u, W, iters);
+    // nodal flux (D v_d, S v_d + P e_d, (tau + P) v_d) as FP32 pairs (its terms share one sign),
+    // parked in the node's slots of shF until the element's reference is known
+    F32Pair up[5];
 #pragma unroll
-    for (int d = 0; d < DIM; ++d) phys_flux(u, W.v, W.P, d, F[d]);
-    Wu[0] = W.rho;
-    Wu[1] = W.lor * W.v[0];
-    Wu[2] = W.lor * W.v[1];
-    Wu[3] = W.lor * W.v[2];
-    Wu[4] = W.P;
-    if (li == 0) {  // the element's first node is its reference, kept as FP32 head and tail
+    for (int v = 0; v < 5; ++v) {
+      // an empty statement that reads con2prim's result: the pair of u[v] is formed after the
+      // recovery, so that it does not hold registers through it
+      double uv = u[v];
+      asm("" : "+d"(uv) : "d"(W.P));
+      up[v] = f32_pair(uv);
+    }
+    const F32Pair Pp = f32_pair(W.P);
 #pragma unroll
-      for (int d = 0; d < DIM; ++d)
-#pragma unroll
-        for (int v = 0; v < 5; ++v) {
-          const F32Pair r = f32_pair(F[d][v]);
-          shFR[(le * DIM + d) * 5 + v] = r;
-          // doubled for the update kernel, which lifts 2 F* - 2 F_ref (exact scaling)
-          Fref[((long long)d * 5 + v) * p.E + e] = make_float2(2.0f * r.hi, 2.0f * r.lo);
-        }
+    for (int d = 0; d < DIM; ++d) {
+      const F32Pair vp = f32_pair(W.v[d]);
 #pragma unroll
       for (int v = 0; v < 5; ++v) {
+        F32Pair F;
+        if (v < 4) {
+          F = mul_pair(up[v], vp);
+          if (v == 1 + d) F = add_pair(F, Pp);
+        } else {
+          F = add_pair(mul_pair(up[4], vp), mul_pair(Pp, vp));
+        }
+        shF[(d * 5 + v) * BLOCK + tid] = make_uint2(__float_as_uint(F.hi), __float_as_uint(F.lo));
+        if (li == 0) {  // the element's first node is its reference
+          shFR[(le * DIM + d) * 5 + v] = F;
+          // doubled for the update kernel, which lifts 2 F* - 2 F_ref (exact scaling)
+          Fref[((long long)d * 5 + v) * p.E + e] = make_float2(2.0f * F.hi, 2.0f * F.lo);
+        }
+      }
+    }
+    const double Wu[5] = {W.rho, W.lor * W.v[0], W.lor * W.v[1], W.lor * W.v[2], W.P};
+#pragma unroll
+    for (int v = 0; v < 5; ++v) {
+      // (rho, u, P) as FP32 head and tail, parked in the node's slot of shW like the fluxes
+      const F32Pair w = f32_pair(Wu[v]);
+      shW[v * BLOCK + tid] = make_uint2(__float_as_uint(w.hi), __float_as_uint(w.lo));
+      if (li == 0) {  // the element's first node is its reference
         shWR[le * 5 + v] = Wu[v];
-        shWRp[le * 5 + v] = f32_pair(Wu[v]);
+        shWRp[le * 5 + v] = w;
       }
     }
   }
@@ -171,12 +194,17 @@ __global__ void __launch_bounds__(SplitShape<DIM, N>::BLOCK)
 #pragma unroll
     for (int d = 0; d < DIM; ++d)
 #pragma unroll
-      for (int v = 0; v < 5; ++v)
-        shF[(d * 5 + v) * BLOCK + tid] =
-            as_u2(split_tf32(dev_f32(f32_pair(F[d][v]), shFR[(le * DIM + d) * 5 + v])));
+      for (int v = 0; v < 5; ++v) {
+        const uint2 f = shF[(d * 5 + v) * BLOCK + tid];  // this thread's own slot
+        shF[(d * 5 + v) * BLOCK + tid] = as_u2(split_tf32(
+            dev_f32(F32Pair{__uint_as_float(f.x), __uint_as_float(f.y)}, shFR[(le * DIM + d) * 5 + v])));
+      }
 #pragma unroll
-    for (int v = 0; v < 5; ++v)
-      shW[v * BLOCK + tid] = as_u2(split_tf32(dev_f32(f32_pair(Wu[v]), shWRp[le * 5 + v])));
+    for (int v = 0; v < 5; ++v) {
+      const uint2 w = shW[v * BLOCK + tid];  // this thread's own slot
+      shW[v * BLOCK + tid] = as_u2(split_tf32(
+          dev_f32(F32Pair{__uint_as_float(w.x), __uint_as_float(w.y)}, shWRp[le * 5 + v])));
+    }
   } else {
 #pragma unroll
     for (int d = 0; d < DIM; ++d)
