@@ -19,6 +19,7 @@
 #pragma once
 
 #include "kernels.cuh"
+#include "split.cuh"
 
 namespace dgsrhd {
 
@@ -467,14 +468,22 @@ __device__ __forceinline__ void face_vjp_point(const Params& p, const double* __
 #pragma unroll
     for (int v = 0; v < 5; ++v) WLb[v] += WRb[v];
   }
-  double* tbL = TrB + ((long long)D * 2 + 1) * side_stride;
-  double* tbR = TrB + ((long long)D * 2 + 0) * side_stride;
+  // the trace adjoints leave as FP32 head and tail (the node kernel contracts them in pair
+  // arithmetic), in the footprint of the FP64 buffer
+  float2* tbL = reinterpret_cast<float2*>(TrB) + ((long long)D * 2 + 1) * side_stride;
+  float2* tbR = reinterpret_cast<float2*>(TrB) + ((long long)D * 2 + 0) * side_stride;
   if (eL >= 0)
 #pragma unroll
-    for (int v = 0; v < 5; ++v) tbL[(v * p.E + eL) * Nt + t] = WLb[v];
+    for (int v = 0; v < 5; ++v) {
+      const F32Pair q = f32_pair(WLb[v]);
+      tbL[(v * p.E + eL) * Nt + t] = make_float2(q.hi, q.lo);
+    }
   if (eR >= 0)
 #pragma unroll
-    for (int v = 0; v < 5; ++v) tbR[(v * p.E + eR) * Nt + t] = WRb[v];
+    for (int v = 0; v < 5; ++v) {
+      const F32Pair q = f32_pair(WRb[v]);
+      tbR[(v * p.E + eR) * Nt + t] = make_float2(q.hi, q.lo);
+    }
 }
 
 template <int DIM, int N>
@@ -528,26 +537,39 @@ __device__ __forceinline__ void node_adjoint(const Params& p, const double U[5],
 
 // With Ukb null: Ub = U_bar.  Otherwise the stage combination of the SSP-RK reverse sweep is
 // fused in: Unb += a_n R_bar and Ukb += b_k (R_bar + dt U_bar) (Unb and Ukb may be the same).
+// Three resident 256-thread blocks per SM in 1D and 2D (at most 85 registers per thread); in 3D
+// that bound would spill, and two are asked for.
 template <int DIM, int N>
-__global__ void __launch_bounds__(Shape<DIM, N>::BLOCK)
+__global__ void __launch_bounds__(Shape<DIM, N>::BLOCK, DIM == 3 ? 2 : 3)
     node_vjp_kernel(Params p, const double* __restrict__ U, const double* __restrict__ Wst,
                     const unsigned char* __restrict__ guard, const double* __restrict__ Rb,
                     const double* __restrict__ TrB, double* __restrict__ Ub, double* Unb,
                     double* Ukb, double a_n, double b_k, double dt) {
   using S = Shape<DIM, N>;
   constexpr int Nn = S::Nn, Nt = S::Nt, BLOCK = S::BLOCK;
-  __shared__ double shR[5][BLOCK];
-  __shared__ double shD[DIM][N * N];  // (2/dx_d) Dhat per axis
+  // R_bar and the coefficients (2/dx_d) Dhat as FP32 head-and-tail pairs: the transposed volume
+  // term is formed in pair arithmetic (products by Dekker's two-product, sums by Knuth's
+  // two-sum), within about 2^-44 of the FP64 contraction relative to its terms, on the FP32
+  // pipe instead of the FP64 one
+  __shared__ F32Pair shR[5][BLOCK];
+  __shared__ F32Pair shD[DIM][N * N];
+  __shared__ F32Pair shE[2][N];  // phi_i(-1), phi_i(+1)
   const int tid = threadIdx.x;
-  if (tid < DIM * N * N) shD[tid / (N * N)][tid % (N * N)] = p.inv_half_dx[tid / (N * N)] * p.Dhat[tid % (N * N)];
+  if (tid < DIM * N * N)
+    shD[tid / (N * N)][tid % (N * N)] = f32_pair(p.inv_half_dx[tid / (N * N)] * p.Dhat[tid % (N * N)]);
+  if (tid < 2 * N) shE[tid / N][tid % N] = f32_pair(tid < N ? p.em[tid] : p.ep[tid - N]);
   const int le = tid / Nn, li = tid - le * Nn;
   const long long e = (long long)blockIdx.x * S::EPB + le;
   const bool valid = e < p.E;
   const long long tot = p.E * Nn;
   const long long g = e * Nn + li;
+  double y[5];  // this node's R_bar, for the fused stage combination
   if (valid) {
 #pragma unroll
-    for (int v = 0; v < 5; ++v) shR[v][tid] = Rb[v * tot + g];
+    for (int v = 0; v < 5; ++v) {
+      y[v] = Rb[v * tot + g];
+      shR[v][tid] = f32_pair(y[v]);
+    }
   }
   __syncthreads();
   if (!valid) return;
@@ -560,31 +582,37 @@ __global__ void __launch_bounds__(Shape<DIM, N>::BLOCK)
     const int ns = node_stride<N>(d);
     const int base = tid - ijk[d] * ns;
 #pragma unroll
-    for (int v = 0; v < 5; ++v) Fb[d][v] = 0.0;
+    for (int v = 0; v < 5; ++v) {
+      F32Pair acc = mul_pair(shD[d][ijk[d]], shR[v][base]);
 #pragma unroll
-    for (int i = 0; i < N; ++i) {
-      const double c = shD[d][i * N + ijk[d]];
-#pragma unroll
-      for (int v = 0; v < 5; ++v) Fb[d][v] = fma(c, shR[v][base + i * ns], Fb[d][v]);
+      for (int i = 1; i < N; ++i) acc = add_pair(acc, mul_pair(shD[d][i * N + ijk[d]], shR[v][base + i * ns]));
+      Fb[d][v] = f32_to_f64_bits(acc.hi) + f32_to_f64_bits(acc.lo);
     }
   }
-  // transposed trace extrapolation; a guarded face point took the end node's primitive
-  double Wub[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+  // transposed trace extrapolation, in pair arithmetic on the trace adjoints' FP32 heads and
+  // tails; a guarded face point took the end node's primitive (weight 1 there, 0 elsewhere)
+  F32Pair wacc[5];
+#pragma unroll
+  for (int v = 0; v < 5; ++v) wacc[v] = F32Pair{0.0f, 0.0f};
+  const float2* trb = reinterpret_cast<const float2*>(TrB);
 #pragma unroll
   for (int d = 0; d < DIM; ++d) {
     const int t = tan_index<DIM, N>(ijk, d);
 #pragma unroll
     for (int side = 0; side < 2; ++side) {
       const bool guarded = guard[e * S::NFP + (d * 2 + side) * Nt + t] != 0;
-      const double w = guarded ? ((ijk[d] == (side ? N - 1 : 0)) ? 1.0 : 0.0)
-                               : (side ? p.ep[ijk[d]] : p.em[ijk[d]]);
-      if (w != 0.0) {
+      if (guarded && ijk[d] != (side ? N - 1 : 0)) continue;
+      const F32Pair w = guarded ? F32Pair{1.0f, 0.0f} : shE[side][ijk[d]];
 #pragma unroll
-        for (int v = 0; v < 5; ++v)
-          Wub[v] = fma(w, TrB[((((long long)d * 2 + side) * 5 + v) * p.E + e) * Nt + t], Wub[v]);
+      for (int v = 0; v < 5; ++v) {
+        const float2 x = trb[((((long long)d * 2 + side) * 5 + v) * p.E + e) * Nt + t];
+        wacc[v] = add_pair(wacc[v], mul_pair(w, F32Pair{x.x, x.y}));
       }
     }
   }
+  double Wub[5];
+#pragma unroll
+  for (int v = 0; v < 5; ++v) Wub[v] = f32_to_f64_bits(wacc[v].hi) + f32_to_f64_bits(wacc[v].lo);
   double u[5], Wu[5], out[5];
 #pragma unroll
   for (int v = 0; v < 5; ++v) {
@@ -599,9 +627,8 @@ __global__ void __launch_bounds__(Shape<DIM, N>::BLOCK)
   } else {
 #pragma unroll
     for (int v = 0; v < 5; ++v) {
-      const double y = shR[v][tid];
-      if (a_n != 0.0) Unb[v * tot + g] += a_n * y;
-      Ukb[v * tot + g] += b_k * fma(dt, out[v], y);  // re-read: Ukb may be Unb
+      if (a_n != 0.0) Unb[v * tot + g] += a_n * y[v];
+      Ukb[v * tot + g] += b_k * fma(dt, out[v], y[v]);  // re-read: Ukb may be Unb
     }
   }
 }
