@@ -76,6 +76,26 @@ __device__ __forceinline__ F32Pair f32_pair(double x) {
   return q;
 }
 
+// Products and sums of FP32 head-and-tail pairs (the value is hi + lo), on the FP32 pipe, for
+// quantities that need about 44 bits rather than FP64's 53 (those the split-precision path
+// feeds its FP32 deviations with, and the adjoint's transposed contractions).  mul_pair: the product of
+// the heads, its rounding error by one fused multiply-add (exact, Dekker's two-product) and the
+// two cross terms; the lo x lo term and the roundings of the cross terms leave it within about
+// 2^-46 of the exact product.  add_pair: Knuth's two-sum of the heads (the exact sum as s + e)
+// with both tails added to e; it is within about 2^-46 (|a| + |b|) of the exact sum (relative
+// to the sum itself for addends of one sign).
+__device__ __forceinline__ F32Pair mul_pair(F32Pair a, F32Pair b) {
+  const float h = __fmul_rn(a.hi, b.hi);
+  return F32Pair{h, fmaf(a.hi, b.lo, fmaf(a.lo, b.hi, fmaf(a.hi, b.hi, -h)))};
+}
+
+__device__ __forceinline__ F32Pair add_pair(F32Pair a, F32Pair b) {
+  const float s = __fadd_rn(a.hi, b.hi);
+  const float bb = __fsub_rn(s, a.hi);
+  const float e = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, bb)), __fsub_rn(b.hi, bb));
+  return F32Pair{s, __fadd_rn(e, __fadd_rn(a.lo, b.lo))};
+}
+
 // x 2^k for a normal x whose result stays normal, by adding k to the exponent field on the
 // integer pipe (exact, like the multiplication it replaces); zero (and a subnormal) is returned
 // unchanged.

@@ -771,6 +771,28 @@ __device__ __forceinline__ void flux_mix(const FaceState& L, const FaceState& R,
   out[4] = fma(L.U[4], bL, fma(R.U[4], bR, pv));
 }
 
+// The same combination as FP32 head-and-tail pairs (the split-precision update consumes the face
+// flux in that form): the side weights and the pressure terms in FP64 (five FP64 operations for
+// LLF), the products and sums in pair arithmetic, within about 2^-46 of the FP64 combination
+// relative to the magnitudes of its terms.
+template <int D>
+__device__ __forceinline__ void flux_mix(const FaceState& L, const FaceState& R, double wL,
+                                         double wR, double c, F32Pair out[5]) {
+  const double aL = wL * L.v[D], aR = wR * R.v[D];
+  const F32Pair bL = f32_pair(aL - c), bR = f32_pair(aR + c);
+  const F32Pair pp = f32_pair(fma(wL, L.P, wR * R.P));
+  const F32Pair pv = f32_pair(fma(aL, L.P, aR * R.P));
+#pragma unroll
+  for (int k = 0; k < 5; ++k) {
+    const F32Pair x = add_pair(mul_pair(f32_pair(L.U[k]), bL), mul_pair(f32_pair(R.U[k]), bR));
+    out[k] = (k == 1 + D) ? add_pair(x, pp) : (k == 4 ? add_pair(x, pv) : x);
+  }
+}
+
+// 2 F* stored into a flux output of either form
+__device__ __forceinline__ void put_flux(double& o, double x) { o = x; }
+__device__ __forceinline__ void put_flux(F32Pair& o, double x) { o = f32_pair(x); }
+
 // Numerical flux along axis D between face states given as (rho, u, P), returned DOUBLED (2 F*:
 // the factor 1/2 of LLF and of the HLL denominator moves into the lift coefficients, which
 // are exact powers-of-two scalings of the tables).  HLL: S_L = min(lambda_L, 0), S_R =
@@ -778,9 +800,11 @@ __device__ __forceinline__ void flux_mix(const FaceState& L, const FaceState& R,
 // both vanish); LLF: F* = (F_L + F_R)/2 - a (U_R - U_L)/2 with a = max |lambda|; HLLC as above.
 // TAPE: also fill recL / recR with the face-state tape (the forward pass of the reverse sweep).
 // Both variants give the same bits.
-template <int D, bool TAPE>
+// O: double, or F32Pair for the split-precision update (LLF and HLL then combine in pair
+// arithmetic; HLLC forms its flux in FP64 and splits it).
+template <int D, bool TAPE, class O = double>
 __device__ __forceinline__ void numerical_flux(const Params& p, const double WL[5],
-                                               const double WR[5], double Fs2[5],
+                                               const double WR[5], O Fs2[5],
                                                double recL[kFaceTape], double recR[kFaceTape]) {
   FaceState L, R;
   face_state(p, WL, L);
@@ -825,7 +849,7 @@ __device__ __forceinline__ void numerical_flux(const Params& p, const double WL[
     double Fs[5];
     hllc_flux<D>(L, R, FL, FR, lamL, lamR, Fs);
 #pragma unroll
-    for (int v = 0; v < 5; ++v) Fs2[v] = 2.0 * Fs[v];
+    for (int v = 0; v < 5; ++v) put_flux(Fs2[v], 2.0 * Fs[v]);
   } else {
     const double a = max_bits(abs_bits(lamL), abs_bits(lamR));
     flux_mix<D>(L, R, 1.0, 1.0, -a, Fs2);

@@ -236,11 +236,11 @@ __device__ __forceinline__ long long tape_base(const Params& p, int D) {
   return (p.fs_off[D] / 5) * (2 * kFaceTape);
 }
 
-// pairs: store each flux as its FP32 head and tail (float2, same footprint) for the split update
-template <int DIM, int N, int D, bool SAVE>
+// PAIRS: store each flux as its FP32 head and tail (float2, same footprint) for the split update
+template <int DIM, int N, int D, bool SAVE, bool PAIRS>
 __device__ __forceinline__ void face_point(const Params& p, const double* __restrict__ Tr,
                                            double* __restrict__ Fs, double* __restrict__ tape,
-                                           long long k, int pairs) {
+                                           long long k) {
   constexpr int Nt = Shape<DIM, N>::Nt;
   const long long nf = p.nface[D];
   if (k >= nf * Nt) return;
@@ -293,20 +293,19 @@ __device__ __forceinline__ void face_point(const Params& p, const double* __rest
     for (int v = 0; v < 5; ++v) WR[v] = (p.bc[D][1] == 1) ? p.ghost[D][1][v] : WL[v];
     if (p.bc[D][1] == 3) WR[1 + D] = -WR[1 + D];
   }
-  double F[5], rec[2][kFaceTape];
-  numerical_flux<D, SAVE>(p, WL, WR, F, rec[0], rec[1]);  // F = 2 F*
   double* out = Fs + p.fs_off[D];
-  if (pairs) {
+  if (PAIRS) {
+    F32Pair Fp[5];
+    numerical_flux<D, false, F32Pair>(p, WL, WR, Fp, nullptr, nullptr);  // Fp = 2 F*
     float2* outp = reinterpret_cast<float2*>(out);
 #pragma unroll
-    for (int v = 0; v < 5; ++v) {
-      const F32Pair q = f32_pair(F[v]);
-      outp[(v * nf + f) * Nt + t] = make_float2(q.hi, q.lo);
-    }
-  } else {
-#pragma unroll
-    for (int v = 0; v < 5; ++v) out[(v * nf + f) * Nt + t] = F[v];
+    for (int v = 0; v < 5; ++v) outp[(v * nf + f) * Nt + t] = make_float2(Fp[v].hi, Fp[v].lo);
+    return;
   }
+  double F[5], rec[2][kFaceTape];
+  numerical_flux<D, SAVE>(p, WL, WR, F, rec[0], rec[1]);  // F = 2 F*
+#pragma unroll
+  for (int v = 0; v < 5; ++v) out[(v * nf + f) * Nt + t] = F[v];
   if (SAVE) {
     double* tp = tape + tape_base(p, D);
 #pragma unroll
@@ -314,17 +313,19 @@ __device__ __forceinline__ void face_point(const Params& p, const double* __rest
   }
 }
 
-// SAVE: also write the face-state tape for the reverse sweep.
-template <int DIM, int N, bool SAVE>
+// SAVE: also write the face-state tape for the reverse sweep.  PAIRS (never with SAVE): write
+// the fluxes as FP32 head and tail for the split update.
+template <int DIM, int N, bool SAVE, bool PAIRS = false>
 __global__ void __launch_bounds__(128) face_kernel(Params p, const double* __restrict__ Tr,
                                                    double* __restrict__ Fs,
-                                                   double* __restrict__ tape, int pairs) {
+                                                   double* __restrict__ tape) {
+  static_assert(!(SAVE && PAIRS), "the tape is written by the FP64 face kernel only");
   const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (blockIdx.y == 0) face_point<DIM, N, 0, SAVE>(p, Tr, Fs, tape, k, pairs);
+  if (blockIdx.y == 0) face_point<DIM, N, 0, SAVE, PAIRS>(p, Tr, Fs, tape, k);
   if (DIM > 1 && blockIdx.y == 1)
-    face_point<DIM, N, (DIM > 1 ? 1 : 0), SAVE>(p, Tr, Fs, tape, k, pairs);
+    face_point<DIM, N, (DIM > 1 ? 1 : 0), SAVE, PAIRS>(p, Tr, Fs, tape, k);
   if (DIM > 2 && blockIdx.y == 2)
-    face_point<DIM, N, (DIM > 2 ? 2 : 0), SAVE>(p, Tr, Fs, tape, k, pairs);
+    face_point<DIM, N, (DIM > 2 ? 2 : 0), SAVE, PAIRS>(p, Tr, Fs, tape, k);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -819,9 +820,11 @@ static cudaError_t launch_stage_kernels(const StageArgs& a) {
       dim3 grid((unsigned)((nthreads + 127) / 128), DIM);
       // the split update consumes the fluxes as FP32 head and tail
       if (a.tape)
-        face_kernel<DIM, N, true><<<grid, 128, 0, a.stream>>>(p, a.Tr, a.Fs, a.tape, 0);
+        face_kernel<DIM, N, true><<<grid, 128, 0, a.stream>>>(p, a.Tr, a.Fs, a.tape);
+      else if (a.split)
+        face_kernel<DIM, N, false, true><<<grid, 128, 0, a.stream>>>(p, a.Tr, a.Fs, nullptr);
       else
-        face_kernel<DIM, N, false><<<grid, 128, 0, a.stream>>>(p, a.Tr, a.Fs, nullptr, a.split);
+        face_kernel<DIM, N, false><<<grid, 128, 0, a.stream>>>(p, a.Tr, a.Fs, nullptr);
       break;
     }
     case Op::Update: {

@@ -43,24 +43,6 @@ __device__ __forceinline__ float dev_f32(F32Pair x, F32Pair r) {
   return __fadd_rn(__fsub_rn(x.hi, r.hi), __fsub_rn(x.lo, r.lo));
 }
 
-// Products and sums of FP32 head-and-tail pairs (the value is hi + lo), for quantities that
-// enter the split contractions only through their FP32 deviations.  mul_pair: the product of
-// the heads, its rounding error by one fused multiply-add (exact, Dekker's two-product) and the
-// two cross terms; the lo x lo term and the roundings of the cross terms leave it within about
-// 2^-46 of the exact product.  add_pair: Knuth's two-sum of the heads (the exact sum as s + e)
-// with both tails added to e; for addends of one sign it is within about 2^-46 of the exact sum.
-__device__ __forceinline__ F32Pair mul_pair(F32Pair a, F32Pair b) {
-  const float h = __fmul_rn(a.hi, b.hi);
-  return F32Pair{h, fmaf(a.hi, b.lo, fmaf(a.lo, b.hi, fmaf(a.hi, b.hi, -h)))};
-}
-
-__device__ __forceinline__ F32Pair add_pair(F32Pair a, F32Pair b) {
-  const float s = __fadd_rn(a.hi, b.hi);
-  const float bb = __fsub_rn(s, a.hi);
-  const float e = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, bb)), __fsub_rn(b.hi, bb));
-  return F32Pair{s, __fadd_rn(e, __fadd_rn(a.lo, b.lo))};
-}
-
 // D (16x8, f32) += A (16x8, tf32, row) * B (8x8, tf32, col)
 __device__ __forceinline__ void mma_tf32(float c[4], const unsigned a[4], const unsigned b[2]) {
   asm volatile(
