@@ -96,6 +96,21 @@ __device__ __forceinline__ F32Pair add_pair(F32Pair a, F32Pair b) {
   return F32Pair{s, __fadd_rn(e, __fadd_rn(a.lo, b.lo))};
 }
 
+// x 2^k for a runtime k in [-1023, 1023]: exponent arithmetic on the integer pipe for a normal x
+// (zero when the result leaves the normal range downwards, infinity upwards), x itself for zero,
+// infinity and NaN, and one FP64 multiplication for a subnormal x.
+__device__ __forceinline__ double scale_pow2(double x, int k) {
+  const long long b = __double_as_longlong(x);
+  const int ex = (int)((b >> 52) & 0x7ff);
+  if (ex == 0x7ff || (b << 1) == 0) return x;
+  if (ex == 0) return x * __longlong_as_double((long long)(1023 + k) << 52);
+  const long long sign = b & (long long)0x8000000000000000ULL;
+  const int ne = ex + k;
+  if (ne <= 0) return __longlong_as_double(sign);
+  if (ne >= 0x7ff) return __longlong_as_double(sign | 0x7ff0000000000000LL);
+  return __longlong_as_double(b + ((long long)k << 52));
+}
+
 // x 2^k for a normal x whose result stays normal, by adding k to the exponent field on the
 // integer pipe (exact, like the multiplication it replaces); zero (and a subnormal) is returned
 // unchanged.

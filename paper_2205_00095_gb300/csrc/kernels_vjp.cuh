@@ -468,22 +468,14 @@ __device__ __forceinline__ void face_vjp_point(const Params& p, const double* __
 #pragma unroll
     for (int v = 0; v < 5; ++v) WLb[v] += WRb[v];
   }
-  // the trace adjoints leave as FP32 head and tail (the node kernel contracts them in pair
-  // arithmetic), in the footprint of the FP64 buffer
-  float2* tbL = reinterpret_cast<float2*>(TrB) + ((long long)D * 2 + 1) * side_stride;
-  float2* tbR = reinterpret_cast<float2*>(TrB) + ((long long)D * 2 + 0) * side_stride;
+  double* tbL = TrB + ((long long)D * 2 + 1) * side_stride;
+  double* tbR = TrB + ((long long)D * 2 + 0) * side_stride;
   if (eL >= 0)
 #pragma unroll
-    for (int v = 0; v < 5; ++v) {
-      const F32Pair q = f32_pair(WLb[v]);
-      tbL[(v * p.E + eL) * Nt + t] = make_float2(q.hi, q.lo);
-    }
+    for (int v = 0; v < 5; ++v) tbL[(v * p.E + eL) * Nt + t] = WLb[v];
   if (eR >= 0)
 #pragma unroll
-    for (int v = 0; v < 5; ++v) {
-      const F32Pair q = f32_pair(WRb[v]);
-      tbR[(v * p.E + eR) * Nt + t] = make_float2(q.hi, q.lo);
-    }
+    for (int v = 0; v < 5; ++v) tbR[(v * p.E + eR) * Nt + t] = WRb[v];
 }
 
 template <int DIM, int N>
@@ -547,29 +539,48 @@ __global__ void __launch_bounds__(Shape<DIM, N>::BLOCK, DIM == 3 ? 2 : 3)
                     double* Ukb, double a_n, double b_k, double dt) {
   using S = Shape<DIM, N>;
   constexpr int Nn = S::Nn, Nt = S::Nt, BLOCK = S::BLOCK;
-  // R_bar and the coefficients (2/dx_d) Dhat as FP32 head-and-tail pairs: the transposed volume
-  // term is formed in pair arithmetic (products by Dekker's two-product, sums by Knuth's
-  // two-sum), within about 2^-44 of the FP64 contraction relative to its terms, on the FP32
-  // pipe instead of the FP64 one
+  // The transposed volume term runs in FP32 head-and-tail pair arithmetic (products by Dekker's
+  // two-product, sums by Knuth's two-sum), within about 2^-44 of the FP64 contraction relative
+  // to its terms, on the FP32 pipe instead of the FP64 one.  FP32 spans far fewer binades than
+  // FP64: when every |R_bar| of the block is zero or inside [2^-100, 2^100] the pairs hold it in
+  // full; otherwise (a block-uniform branch) each element's R_bar is first scaled by the power
+  // of two that brings its largest component into [1, 2) (exact), and the sums are scaled back
+  // in FP64, where components below 2^-100 of the element's largest lose digits, a negligible
+  // share of every sum they enter.
   __shared__ F32Pair shR[5][BLOCK];
-  __shared__ F32Pair shD[DIM][N * N];
-  __shared__ F32Pair shE[2][N];  // phi_i(-1), phi_i(+1)
+  __shared__ F32Pair shD[DIM][N * N];  // (2/dx_d) Dhat per axis
+  __shared__ int shX[S::EPB];          // largest biased FP64 exponent of R_bar per element
   const int tid = threadIdx.x;
   if (tid < DIM * N * N)
     shD[tid / (N * N)][tid % (N * N)] = f32_pair(p.inv_half_dx[tid / (N * N)] * p.Dhat[tid % (N * N)]);
-  if (tid < 2 * N) shE[tid / N][tid % N] = f32_pair(tid < N ? p.em[tid] : p.ep[tid - N]);
+  if (tid < S::EPB) shX[tid] = 0;
   const int le = tid / Nn, li = tid - le * Nn;
   const long long e = (long long)blockIdx.x * S::EPB + le;
   const bool valid = e < p.E;
   const long long tot = p.E * Nn;
   const long long g = e * Nn + li;
   double y[5];  // this node's R_bar, for the fused stage combination
+  int ex = 0;
+  bool inside = true;
   if (valid) {
 #pragma unroll
     for (int v = 0; v < 5; ++v) {
       y[v] = Rb[v * tot + g];
-      shR[v][tid] = f32_pair(y[v]);
+      const int b = (__double2hiint(y[v]) >> 20) & 0x7ff;
+      ex = max(ex, b);
+      inside = inside && ((__double_as_longlong(y[v]) << 1) == 0 || (b >= 1023 - 100 && b <= 1023 + 100));
     }
+  }
+  const bool whole = __syncthreads_and(inside);  // also orders the tables' set-up
+  int X = 1023;
+  if (!whole) {
+    if (valid && ex > 0) atomicMax(&shX[le], ex);
+    __syncthreads();
+    X = valid ? shX[le] : 1023;
+  }
+  if (valid) {
+#pragma unroll
+    for (int v = 0; v < 5; ++v) shR[v][tid] = f32_pair(whole ? y[v] : scale_pow2(y[v], 1023 - X));
   }
   __syncthreads();
   if (!valid) return;
@@ -589,30 +600,29 @@ __global__ void __launch_bounds__(Shape<DIM, N>::BLOCK, DIM == 3 ? 2 : 3)
       Fb[d][v] = f32_to_f64_bits(acc.hi) + f32_to_f64_bits(acc.lo);
     }
   }
-  // transposed trace extrapolation, in pair arithmetic on the trace adjoints' FP32 heads and
-  // tails; a guarded face point took the end node's primitive (weight 1 there, 0 elsewhere)
-  F32Pair wacc[5];
+  if (!whole) {
 #pragma unroll
-  for (int v = 0; v < 5; ++v) wacc[v] = F32Pair{0.0f, 0.0f};
-  const float2* trb = reinterpret_cast<const float2*>(TrB);
+    for (int d = 0; d < DIM; ++d)
+#pragma unroll
+      for (int v = 0; v < 5; ++v) Fb[d][v] = scale_pow2(Fb[d][v], X - 1023);
+  }
+  // transposed trace extrapolation; a guarded face point took the end node's primitive
+  double Wub[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
 #pragma unroll
   for (int d = 0; d < DIM; ++d) {
     const int t = tan_index<DIM, N>(ijk, d);
 #pragma unroll
     for (int side = 0; side < 2; ++side) {
       const bool guarded = guard[e * S::NFP + (d * 2 + side) * Nt + t] != 0;
-      if (guarded && ijk[d] != (side ? N - 1 : 0)) continue;
-      const F32Pair w = guarded ? F32Pair{1.0f, 0.0f} : shE[side][ijk[d]];
+      const double w = guarded ? ((ijk[d] == (side ? N - 1 : 0)) ? 1.0 : 0.0)
+                               : (side ? p.ep[ijk[d]] : p.em[ijk[d]]);
+      if (w != 0.0) {
 #pragma unroll
-      for (int v = 0; v < 5; ++v) {
-        const float2 x = trb[((((long long)d * 2 + side) * 5 + v) * p.E + e) * Nt + t];
-        wacc[v] = add_pair(wacc[v], mul_pair(w, F32Pair{x.x, x.y}));
+        for (int v = 0; v < 5; ++v)
+          Wub[v] = fma(w, TrB[((((long long)d * 2 + side) * 5 + v) * p.E + e) * Nt + t], Wub[v]);
       }
     }
   }
-  double Wub[5];
-#pragma unroll
-  for (int v = 0; v < 5; ++v) Wub[v] = f32_to_f64_bits(wacc[v].hi) + f32_to_f64_bits(wacc[v].lo);
   double u[5], Wu[5], out[5];
 #pragma unroll
   for (int v = 0; v < 5; ++v) {

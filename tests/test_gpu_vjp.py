@@ -62,6 +62,37 @@ def test_rhs_vjp_against_oracle_differences(gpu_lib, dim, n, degree, eos, flux, 
     assert abs(got - fd) <= 1e-6 * abs(fd), (got, fd)
 
 
+@pytest.mark.parametrize("dim,n,degree,eos,flux", [(2, [6, 5], 3, "tm", "hll"),
+                                                    (3, [3, 3, 2], 3, "ideal", "llf")])
+def test_rhs_vjp_is_homogeneous_in_r_bar_over_the_fp64_range(gpu_lib, dim, n, degree, eos, flux):
+    """The VJP is linear in R_bar.  Its transposed volume term runs in FP32 pair arithmetic on
+    R_bar scaled per element by a power of two, so scaling R_bar by 2^k, far outside FP32's
+    range, must scale U_bar by exactly 2^k, bit for bit, with elements of very different
+    magnitudes side by side."""
+    spec = wl.smooth_random(dim, n, degree, eos=eos, flux=flux, c2p="iterative", seed=5)
+    W = wl.smooth_random_ic(spec, oracle.node_coords(spec))
+    s = solver(spec)
+    U = s.initial_state(W)
+    rng = np.random.default_rng(11)
+    E = int(np.prod(n))
+    Rb = rng.normal(size=(5, E, (degree + 1) ** dim))
+    # elements whose R_bar differs by 2^300 from its neighbours'
+    Rb[:, ::2] *= 2.0 ** 300
+    base = s.rhs_vjp(U, dev(Rb)).cpu().numpy()
+    assert np.all(np.isfinite(base)) and np.abs(base).max() > 0.0
+    for k in (-600, -300, 200, 400):
+        got = s.rhs_vjp(U, dev(Rb * 2.0 ** k)).cpu().numpy()
+        assert np.array_equal(got, base * 2.0 ** k), k
+    # R_bar of moderate size everywhere takes the unscaled pairs; scaled far down, the rescaled
+    # ones: the same bits either way
+    Rm = Rb.copy()
+    Rm[:, ::2] *= 2.0 ** -300
+    assert np.abs(Rm).min() > 2.0 ** -90 and np.abs(Rm).max() < 2.0 ** 90
+    mid = s.rhs_vjp(U, dev(Rm)).cpu().numpy()
+    low = s.rhs_vjp(U, dev(Rm * 2.0 ** -500)).cpu().numpy()
+    assert np.array_equal(low, mid * 2.0 ** -500)
+
+
 @pytest.mark.parametrize("eos,c2p", [("ideal", "analytic"), ("ideal", "iterative"),
                                      ("tm", "analytic"), ("tm", "iterative")])
 def test_con2prim_vjp_against_oracle_differences(gpu_lib, eos, c2p):
