@@ -140,22 +140,25 @@ __device__ __forceinline__ bool admissible_screen(const double U[5]) {
 // D^2 so that they come from (D^2, |S|, E) and the one reciprocal w = 1/((G - 1)^2 (D^2 + |S|^2)):
 //   a0 = |S|^2 w,  a1 = -2 G |S| E w,  a3 = (G - 1) a1,
 //   a2 = (G^2 E^2 + 2 (G - 1) |S|^2 - (G - 1)^2 D^2) w.
+// g1 = (G - 1)^2 D^2 is passed in (the caller forms w's denominator from it), and a3^2 is taken
+// as (G - 1)^2 a1^2.
 // B and C are carried doubled (B' = 2B, C' = 2C), which moves the factors 1/2 into the final
 // 1/4: beta = (sqrt(B'^2 - 8 C') - B') / 4 (scalings by powers of two are exact).
-__device__ __forceinline__ double beta_ideal_closed_form(const Params& p, double D2, double S2,
+__device__ __forceinline__ double beta_ideal_closed_form(const Params& p, double g1, double S2,
                                                          double S, double E, double w) {
   const double a0 = S2 * w;
   const double SEw = (S * E) * w;
   const double a1 = p.m2G * SEw;
   const double a3 = p.m2Ggm1 * SEw;
-  const double a2 = fma(p.G2, E * E, fma(p.tgm1, S2, -p.gm1sq * D2)) * w;
+  const double a2 = fma(p.G2, E * E, fma(p.tgm1, S2, -g1)) * w;
   // resolvent cubic x^3 + i1 x^2 + i2 x + i3 with i1 = -a2, i2 = a1 a3 - 4 a0,
   // i3 = 4 a2 a0 - a1^2 - a3^2 a0; with t = i1/3 its depressed form has
   // R = (9 i1 i2 - 27 i3 - 2 i1^3)/54 = (t i2 - i3)/2 - t^3 and S = (3 i2 - i1^2)/9 = i2/3 - t^2
   // multiplications by powers of two are exponent additions on the integer pipe (ldexp_bits)
   const double m4a0 = -ldexp_bits<2>(a0);
   const double i2 = fma(a3, a1, m4a0);
-  const double i3 = fma(a0, fma(4.0, a2, -a3 * a3), -a1 * a1);
+  const double A1 = a1 * a1;
+  const double i3 = fma(a0, fma(-p.gm1sq, A1, ldexp_bits<2>(a2)), -A1);
   const double t = a2 * (-1.0 / 3.0);  // i1 / 3
   const double t2 = t * t;
   const double R = fma(0.5, fma(t, i2, -i3), -t2 * t);
@@ -503,8 +506,8 @@ __device__ __forceinline__ int con2prim(const Params& p, const double U[5], Prim
     ginv = 1.0;
     lor = 1.0;
   } else if (closed_ideal) {
-    const double D2 = D * D;
-    beta = beta_ideal_closed_form(p, D2, S2, S, tau + D, recip_nr(p.gm1sq * (D2 + S2)));
+    const double g1 = p.gm1sq * (D * D);  // (G - 1)^2 D^2
+    beta = beta_ideal_closed_form(p, g1, S2, S, tau + D, recip_nr(fma(p.gm1sq, S2, g1)));
     conv = dbits(beta) >= 0 && dbits(beta) < dbits(1.0);  // 0 <= beta < 1
     // gamma = (1 - beta^2)^(-1/2); 1 - 1/gamma = beta^2 gamma / (gamma + 1)
     const double b2 = beta * beta;
