@@ -1014,6 +1014,10 @@ bool params_from_config(const dgsrhd_config* cfg, Params* out, long long* n_trac
   for (int i = 0; i < N; ++i) {
     p.lm[i] = p.em[i] / p.w[i];
     p.lp[i] = p.ep[i] / p.w[i];
+    for (int d = 0; d < dim; ++d) {
+      p.slm[d][i] = p.inv_half_dx[d] * p.lm[i];
+      p.slp[d][i] = p.inv_half_dx[d] * p.lp[i];
+    }
   }
   p.wsum = (double)(1 << dim);
   *out = p;

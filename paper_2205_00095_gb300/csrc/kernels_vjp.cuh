@@ -300,8 +300,9 @@ __device__ __forceinline__ void numerical_flux_vjp(const Params& p, const double
   FaceFwd L, R;
   face_fwd<D>(p, WL, tL, ts, L);
   face_fwd<D>(p, WR, tR, ts, R);
-  const bool selL_from_L = L.lm <= R.lm;  // lambda_L = min(lm_L, lm_R)
-  const bool selR_from_L = L.lp >= R.lp;  // lambda_R = max(lp_L, lp_R)
+  // the forward's selections, on the bit patterns (integer pipe) as min_bits / max_bits take them
+  const bool selL_from_L = order_key(L.lm) <= order_key(R.lm);  // lambda_L = min(lm_L, lm_R)
+  const bool selR_from_L = order_key(L.lp) >= order_key(R.lp);  // lambda_R = max(lp_L, lp_R)
   const double lamL = selL_from_L ? L.lm : R.lm, lamR = selR_from_L ? L.lp : R.lp;
   double lamLb = 0.0, lamRb = 0.0;
   auto wavespeed_adjoints = [&](double& lmLb, double& lpLb, double& lmRb, double& lpRb) {
@@ -327,10 +328,10 @@ __device__ __forceinline__ void numerical_flux_vjp(const Params& p, const double
   // LLF and HLL: F_L_bar = aL Fsb, U_L_bar = bL Fsb, and likewise on the right
   double aL, bL, aR, bR;
   if (p.flux == 1) {
-    const bool actL = lamL < 0.0, actR = lamR > 0.0;
+    const bool actL = dbits(lamL) < 0, actR = pos_bits(lamR);  // as the forward's S_L, S_R
     const double sL = actL ? lamL : 0.0, sR = actR ? lamR : 0.0;
     const double den = sR - sL;
-    if (den == 0.0) {
+    if ((dbits(den) << 1) == 0) {  // den = +-0
       aL = aR = 0.5;
       bL = bR = 0.0;
     } else {
@@ -355,8 +356,9 @@ __device__ __forceinline__ void numerical_flux_vjp(const Params& p, const double
       lamRb = actR ? sRb : 0.0;
     }
   } else {
-    const bool useL = fabs(lamL) >= fabs(lamR);  // a = max(|lambda_L|, |lambda_R|)
-    const double a = useL ? fabs(lamL) : fabs(lamR);
+    // a = max(|lambda_L|, |lambda_R|), chosen on the bit patterns as the forward chooses it
+    const bool useL = order_key(abs_bits(lamL)) >= order_key(abs_bits(lamR));
+    const double a = useL ? abs_bits(lamL) : abs_bits(lamR);
     double gU = 0.0;
 #pragma unroll
     for (int v = 0; v < 5; ++v) gU = fma(Fsb[v], __dsub_rn(R.U[v], L.U[v]), gU);
@@ -365,9 +367,9 @@ __device__ __forceinline__ void numerical_flux_vjp(const Params& p, const double
     bL = 0.5 * a;
     bR = -0.5 * a;
     if (useL)
-      lamLb = ab * (lamL >= 0.0 ? 1.0 : -1.0);
+      lamLb = dbits(lamL) >= 0 ? ab : -ab;
     else
-      lamRb = ab * (lamR >= 0.0 ? 1.0 : -1.0);
+      lamRb = dbits(lamR) >= 0 ? ab : -ab;
   }
   wavespeed_adjoints(lmLb, lpLb, lmRb, lpRb);
   face_rev_scaled<D>(p, L, Fsb, aL, bL, lmLb, lpLb, WLb);
@@ -435,18 +437,17 @@ __device__ __forceinline__ void face_vjp_point(const Params& p, const double* __
     for (int v = 0; v < 5; ++v) WR[v] = (p.bc[D][1] == 1) ? p.ghost[D][1][v] : WL[v];
     if (p.bc[D][1] == 3) WR[1 + D] = -WR[1 + D];
   }
-  // transposed lift: R_left -= s l+ F*, R_right += s l- F*
-  const double sc = p.inv_half_dx[D];
+  // transposed lift: R_left -= s l+ F*, R_right += s l- F* (s = 2/dx_D, in the tables)
 #pragma unroll
   for (int v = 0; v < 5; ++v) {
     double acc = 0.0;
 #pragma unroll
     for (int a = 0; a < N; ++a) {
       const int node = line_node<DIM, N>(D, t, a);
-      if (eR >= 0) acc += p.lm[a] * Rb[v * tot + eR * Nn + node];
-      if (eL >= 0) acc -= p.lp[a] * Rb[v * tot + eL * Nn + node];
+      if (eR >= 0) acc = fma(p.slm[D][a], Rb[v * tot + eR * Nn + node], acc);
+      if (eL >= 0) acc = fma(-p.slp[D][a], Rb[v * tot + eL * Nn + node], acc);
     }
-    Fsb[v] = sc * acc;
+    Fsb[v] = acc;
   }
   double WLb[5], WRb[5];
   if (tape) {

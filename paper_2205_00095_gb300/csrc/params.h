@@ -66,6 +66,7 @@ struct Params {
   double Dhat[kMaxN * kMaxN];// Dhat[i*N + a] = w_a phi_i'(x_a) / w_i
   double em[kMaxN], ep[kMaxN];   // phi_i(-1), phi_i(+1)
   double lm[kMaxN], lp[kMaxN];   // phi_i(-1)/w_i, phi_i(+1)/w_i
+  double slm[3][kMaxN], slp[3][kMaxN];  // (2/dx_d) lm, (2/dx_d) lp: the transposed lift per axis
   double wsum;               // sum of tensor weights = 2^dim
   unsigned long long* stats; // device counters [kStatCount]
   int enforce_faces;         // physicality operator over the nodes and the face points
