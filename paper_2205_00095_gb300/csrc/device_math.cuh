@@ -172,7 +172,7 @@ __device__ __forceinline__ double beta_ideal_closed_form(const Params& p, double
     // y = R + sign(R) sqrt(T) (no cancellation) the pair is y^(1/3) - Sq y^(-1/3), both from
     // one reciprocal cube root r = y^(-1/3): y^(1/3) = y r^2.
     const double y = R + copysign(sqrt_nr(T), R);
-    if (y == 0.0) {
+    if ((dbits(y) << 1) == 0) {  // y = +-0
       x = -t;
     } else {
       const double r = rcbrt_nr(y);

@@ -528,11 +528,12 @@ __global__ void __launch_bounds__(Shape<DIM, N>::BLOCK)
     if (mode == 0) {
 #pragma unroll
       for (int v = 0; v < 5; ++v) Uout[v * tot + g] = R[v];
-    } else if (rscale != 0.0) {  // R = b_k dt (R_vol - lift); the branches are uniform
-      if (a_n != 0.0) {
+    } else if ((dbits(rscale) << 1) != 0) {  // R = b_k dt (R_vol - lift)
+      // the branches are uniform, and their tests read the bit patterns (integer pipe)
+      if ((dbits(a_n) << 1) != 0) {
 #pragma unroll
         for (int v = 0; v < 5; ++v) u[v] = fma(a_n, Un[v * tot + g], fma(b_k, Uk[v * tot + g], R[v]));
-      } else if (b_k == 1.0) {
+      } else if (dbits(b_k) == dbits(1.0)) {
 #pragma unroll
         for (int v = 0; v < 5; ++v) u[v] = Uk[v * tot + g] + R[v];
       } else {

@@ -334,11 +334,12 @@ __global__ void __launch_bounds__(Shape<DIM, N>::BLOCK, FACES ? 3 : 5)
     if (mode == 0) {
 #pragma unroll
       for (int v = 0; v < 5; ++v) Uout[v * tot + g] = R[v];
-    } else if (a_n != 0.0) {  // the branches are uniform: no b_k x is formed where b_k = 1
+    } else if ((dbits(a_n) << 1) != 0) {  // uniform branches on the bit patterns; no b_k x
+      // is formed where b_k = 1
 #pragma unroll
       for (int v = 0; v < 5; ++v)
         u[v] = fma(a_n, Un[v * tot + g], b_k * fma(dt, R[v], Uk[v * tot + g]));
-    } else if (b_k == 1.0) {
+    } else if (dbits(b_k) == dbits(1.0)) {
 #pragma unroll
       for (int v = 0; v < 5; ++v) u[v] = fma(dt, R[v], Uk[v * tot + g]);
     } else {

@@ -617,7 +617,7 @@ __global__ void __launch_bounds__(Shape<DIM, N>::BLOCK, DIM == 3 ? 2 : 3)
       const bool guarded = guard[e * S::NFP + (d * 2 + side) * Nt + t] != 0;
       const double w = guarded ? ((ijk[d] == (side ? N - 1 : 0)) ? 1.0 : 0.0)
                                : (side ? p.ep[ijk[d]] : p.em[ijk[d]]);
-      if (w != 0.0) {
+      if ((dbits(w) << 1) != 0) {  // w != 0, on the integer pipe
 #pragma unroll
         for (int v = 0; v < 5; ++v)
           Wub[v] = fma(w, TrB[((((long long)d * 2 + side) * 5 + v) * p.E + e) * Nt + t], Wub[v]);
